@@ -1,0 +1,262 @@
+"""Oracle: nonlinear ODEs by Lemma 2 (Section 3.2) and Newton's method (Eq. 3.2.1).
+
+TEST INFRASTRUCTURE ONLY -- see ``oracle/__init__.py``.
+
+Problem family ('nl' in ``core``):  y^(p) = f(t, y, y^(p-1)) with
+    f = P(y) - delta * y^(p-1) [p = 2 only] + g cos(omega t),
+    P(y) = c0 + c1 y + c2 y^2 + c3 y^3.
+This covers y' = 1 - y^2 (tanh), the logistic equation and the Duffing equation.
+
+Eq. 2.2 / Appendix A.4 "Proof 2": unknowns (omega, b, lambda_1..lambda_p, y_2..y_n),
+    L = 1/2 |omega|^2 + gamma/2 sum e_i^2 + gamma/2 sum xi_i^2 + sum_k lambda_k h_k
+    e_i  = omega^T phi^(p)(t_i) - f(t_i, y_i, omega^T phi^(p-1)(t_i))
+    xi_i = y_i - omega^T phi(t_i) - b
+    h_1  = omega^T phi(t_1) + b - v_1,  h_2 = omega^T phi'(t_1) - v_2.
+The system F = grad L = 0 (Y_1..Y_{p+3} of Lemma 2) is solved by Newton's method.
+
+Readings (also in the design doc):
+ * Only y_i is an auxiliary unknown; the derivative y^(p-1) inside f is
+   omega^T phi^(p-1)(t_i) (as in the worked Problem 15 of Appendix A.6).
+ * Start: omega = 0, b = v_1, lambda = 0, y_i = v_1.  Undamped steps.
+ * Full Newton; an iteration falls back to the Gauss-Newton Hessian (the
+   e_i * P''(y_i) term dropped) when some diagonal entry
+   d_i = gamma (P'(y_i)^2 - e_i P''(y_i) + 1) <= 1e-12 * gamma, or when the
+   y-eliminated Hessian is not positive definite on the null space of the
+   constraints.
+ * Stop when |dx|_2 <= tol (1 + |x|_2) for x = (omega, b) and
+   |F|_2 <= tol * max(1, |F(x_0)|_2); the iteration count is the number of
+   Newton steps taken.
+"""
+import numpy as np
+
+from . import core
+
+
+def poly(prob, y):
+    """P(y), P'(y), P''(y) of the polynomial part of f."""
+    c0, c1, c2, c3 = prob["P"]
+    P = c0 + c1 * y + c2 * y ** 2 + c3 * y ** 3
+    dP = c1 + 2 * c2 * y + 3 * c3 * y ** 2
+    d2P = 2 * c2 + 6 * c3 * y
+    return P, dP, d2P
+
+
+def forcing(prob, t):
+    return prob.get("g", 0.0) * np.cos(prob.get("omega", 0.0) * t)
+
+
+class Pieces:
+    """Feature matrices of one nonlinear problem (fixed during Newton)."""
+
+    def __init__(self, prob, tau=core.TAU_DEFAULT):
+        if prob["kind"] != "nl":
+            raise ValueError("newton oracle needs kind 'nl'")
+        p = prob["p"]
+        if p == 1 and prob.get("delta", 0.0) != 0.0:
+            raise ValueError("delta term needs p = 2")
+        self.prob = prob
+        self.st = core.setup(prob, tau)
+        st = self.st
+        t, s, W = st["t"], st["s"], st["W"]
+        sg = prob["sigma"]
+        self.ti = t[1:]
+        self.Phi = core.features(self.ti, s, sg, W, 0)
+        Pp = core.features(self.ti, s, sg, W, p)
+        if p == 2:
+            Pp = Pp + prob.get("delta", 0.0) * core.features(self.ti, s, sg, W, 1)
+        self.Q = Pp                           # d e_i / d omega
+        self.C = np.zeros((p, W.shape[0] + 1))  # constraint rows on (omega, b)
+        for k in range(p):
+            self.C[k, :W.shape[0]] = core.features(t[:1], s, sg, W, k)[0]
+        self.C[0, W.shape[0]] = 1.0
+        self.v = np.asarray(prob["v"][:p], dtype=np.float64)
+        self.rho = forcing(prob, self.ti)
+        self.me = W.shape[0]
+        self.p = p
+        self.n1 = len(self.ti)
+        self.gamma = prob["gamma"]
+
+    # unpack x = (omega, b, lambda, y)
+    def split(self, x):
+        me, p = self.me, self.p
+        return x[:me], x[me], x[me + 1:me + 1 + p], x[me + 1 + p:]
+
+    def residuals(self, x):
+        om, b, lam, y = self.split(x)
+        P, dP, d2P = poly(self.prob, y)
+        e = self.Q @ om - P - self.rho
+        xi = y - self.Phi @ om - b
+        h = self.C @ np.r_[om, b] - self.v
+        return e, xi, h, P, dP, d2P
+
+    def lagrangian(self, x):
+        """Scalar L of Appendix A.4 evaluated from its definition."""
+        om, b, lam, y = self.split(x)
+        e, xi, h, *_ = self.residuals(x)
+        g = self.gamma
+        return 0.5 * om @ om + 0.5 * g * e @ e + 0.5 * g * xi @ xi + lam @ h
+
+    def F(self, x):
+        """F = grad L = (Y_1, Y_2, Y_3..Y_{p+2}, Y_{p+3}) of Lemma 2."""
+        om, b, lam, y = self.split(x)
+        e, xi, h, P, dP, d2P = self.residuals(x)
+        g = self.gamma
+        me = self.me
+        Y1 = om + g * self.Q.T @ e - g * self.Phi.T @ xi + self.C[:, :me].T @ lam
+        Y2 = -g * xi.sum() + lam[0]
+        Yy = -g * e * dP + g * xi
+        return np.concatenate([Y1, [Y2], h, Yy])
+
+    def diag_yy(self, x, gauss_newton):
+        e, xi, h, P, dP, d2P = self.residuals(x)
+        curv = 0.0 if gauss_newton else e * d2P
+        return self.gamma * (dP ** 2 - curv + 1.0)
+
+    def J(self, x, gauss_newton=False):
+        """Dense (m+n+p) Jacobian of F (the matrix of Lemma 2)."""
+        om, b, lam, y = self.split(x)
+        e, xi, h, P, dP, d2P = self.residuals(x)
+        g = self.gamma
+        me, p, n1 = self.me, self.p, self.n1
+        N = me + 1 + p + n1
+        Jm = np.zeros((N, N))
+        Jm[:me, :me] = np.eye(me) + g * self.Q.T @ self.Q + g * self.Phi.T @ self.Phi
+        Jm[:me, me] = g * self.Phi.sum(axis=0)
+        Jm[me, :me] = Jm[:me, me]
+        Jm[me, me] = g * n1
+        Jm[:me, me + 1:me + 1 + p] = self.C[:, :me].T
+        Jm[me + 1:me + 1 + p, :me] = self.C[:, :me]
+        Jm[me, me + 1] = 1.0
+        Jm[me + 1, me] = 1.0
+        oy = me + 1 + p
+        Jwy = -g * dP[None, :] * self.Q.T - g * self.Phi.T   # d Y1 / d y
+        Jm[:me, oy:] = Jwy
+        Jm[oy:, :me] = Jwy.T
+        Jm[me, oy:] = -g
+        Jm[oy:, me] = -g
+        Jm[oy + np.arange(n1), oy + np.arange(n1)] = self.diag_yy(x, gauss_newton)
+        return Jm
+
+    # ---- y-eliminated (Schur) form: identical Newton steps -----------------
+    def reduced(self, x, gauss_newton=False):
+        """Schur complement of the diagonal y-block (exact elimination).
+
+        Returns (S, rhs_x, d, w_rows, Fy) with S the (m+1)x(m+1) reduced
+        Hessian on (omega, b); the step solves [S C^T; C 0][dx; dlam] =
+        [rhs_x; -h] and then dy_i = -(Fy_i + w_i^T dx) / d_i.
+        """
+        om, b, lam, y = self.split(x)
+        e, xi, h, P, dP, d2P = self.residuals(x)
+        g = self.gamma
+        me = self.me
+        Fx = self.F(x)
+        Fxb = Fx[:me + 1]
+        Fy = Fx[me + 1 + self.p:]
+        d = self.diag_yy(x, gauss_newton)
+        Qt = np.concatenate([self.Q, np.zeros((self.n1, 1))], axis=1)
+        St = np.concatenate([self.Phi, np.ones((self.n1, 1))], axis=1)
+        Wr = -g * (dP[:, None] * Qt + St)          # rows w_i
+        S = g * Qt.T @ Qt + g * St.T @ St - (Wr / d[:, None]).T @ Wr
+        S[:me, :me] += np.eye(me)
+        rhs_x = -Fxb + Wr.T @ (Fy / d)
+        return S, rhs_x, d, Wr, Fy, h
+
+    def projected_pd(self, S):
+        """Is S positive definite on the null space of the constraint rows?"""
+        Q, _ = np.linalg.qr(self.C.T, mode="complete")
+        Z = Q[:, self.p:]
+        try:
+            np.linalg.cholesky(Z.T @ S @ Z)
+            return True
+        except np.linalg.LinAlgError:
+            return False
+
+
+def x0(pc):
+    """Start of Newton (reading above): omega = 0, b = v_1, lambda = 0, y_i = v_1."""
+    v1 = pc.v[0]
+    return np.concatenate([np.zeros(pc.me), [v1], np.zeros(pc.p), np.full(pc.n1, v1)])
+
+
+def use_gauss_newton(pc, x):
+    d = pc.diag_yy(x, False)
+    if np.any(d <= 1e-12 * pc.gamma):
+        return True
+    S = pc.reduced(x, False)[0]
+    return not pc.projected_pd(S)
+
+
+def step_dense(pc, x, gn):
+    """Newton step of Eq. 3.2.1 with the dense Jacobian (constraint rows scaled)."""
+    Jm = pc.J(x, gn)
+    F = pc.F(x)
+    me, p = pc.me, pc.p
+    # move the constraint block (rows/cols me+1..me+p) to the end and scale it
+    N = len(F)
+    perm = np.r_[np.arange(me + 1), np.arange(me + 1 + p, N), np.arange(me + 1, me + 1 + p)]
+    Jp = Jm[np.ix_(perm, perm)]
+    nx = N - p
+    dxp, dlam = core.solve_kkt_scaled(Jp, -F[perm], nx)
+    dx = np.zeros(N)
+    dx[perm[:nx]] = dxp
+    dx[me + 1:me + 1 + p] = dlam
+    return dx
+
+
+def step_reduced(pc, x, gn):
+    """The same step through the y-eliminated system (O(n m^2) per iteration)."""
+    S, rhs_x, d, Wr, Fy, h = pc.reduced(x, gn)
+    me, p = pc.me, pc.p
+    K = np.zeros((me + 1 + p, me + 1 + p))
+    K[:me + 1, :me + 1] = S
+    K[:me + 1, me + 1:] = pc.C.T
+    K[me + 1:, :me + 1] = pc.C
+    dxb, dlam = core.solve_kkt_scaled(K, np.r_[rhs_x, -h], me + 1)
+    dy = -(Fy + Wr @ dxb) / d
+    return np.concatenate([dxb, dlam, dy])
+
+
+def solve(prob, tol=1e-10, max_iter=50, dense=None, tau=core.TAU_DEFAULT,
+          history=False):
+    """Newton's method on Lemma 2's system (Eq. 3.2.1) with the stopping rule above.
+
+    dense=None picks the dense Jacobian for n <= 600, else the reduced form.
+    Returns dict(omega, b, lam, y_aux, iters, converged, y (fit on grid), ...).
+    """
+    pc = Pieces(prob, tau)
+    if dense is None:
+        dense = prob["n"] <= 600
+    x = x0(pc)
+    me = pc.me
+    F0n = None
+    dxb_prev = None
+    hist = []
+    converged = False
+    it = 0
+    for k in range(max_iter + 1):
+        F = pc.F(x)
+        nF = np.linalg.norm(F)
+        if k == 0:
+            F0n = nF
+        xb = x[:me + 1]
+        if history:
+            hist.append(dict(x=x.copy(), nF=nF))
+        if k > 0 and (np.linalg.norm(dxb_prev) <= tol * (1 + np.linalg.norm(xb))
+                      and nF <= tol * max(1.0, F0n)):
+            converged = True
+            it = k
+            break
+        if k == max_iter:
+            it = k
+            break
+        gn = use_gauss_newton(pc, x)
+        dx = step_dense(pc, x, gn) if dense else step_reduced(pc, x, gn)
+        x = x + dx
+        dxb_prev = dx[:me + 1]
+    om, b, lam, y = pc.split(x)
+    sol = dict(pc.st, omega=om, b=b, lam=lam, y_aux=y, iters=it,
+               converged=converged, m_eff=me, pieces=pc)
+    sol["y"] = core.evaluate(prob, sol, pc.st["t"], 0)
+    if history:
+        sol["history"] = hist
+    return sol
