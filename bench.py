@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Throughput benchmark: batched Nystrom LS-SVM ODE solves on GB300.
+
+Workload (default): 4096 instances of y'' + a y' + b y = c sin(omega t) on [0, 20],
+n = 10^4 collocation points, m = 50 landmarks, sigma = 0.5, gamma = 1e10, seeded
+synthetic coefficients (a ~ U[0,1], b ~ U[1,4], c ~ U[-1,1], omega ~ U[0.5,5],
+y(0), y'(0) ~ N(0,1)).  One step = Nystrom setup + fused assembly + solve +
+refinement for the whole batch (nys_run, one CUDA graph), inputs resident.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank solves its own batch
+(weak scaling; no collective on the data path, one all-reduce for the timing).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "batched ODE solves/s at n=1e4, m=50"
+UNIT = "solves/s"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2070 MHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=4096)
+    ap.add_argument("--n", type=int, default=10_000)
+    ap.add_argument("--m", type=int, default=50)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-extras", action="store_true", help="skip FP64/oracle side measurements")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_init():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return rank, ws, local
+
+
+class Clocks:
+    """nvidia-smi sampler (SM clock, max clock, throttle reasons) during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def asm_flops(problems):
+    """Algorithmic FLOPs of one fused assembly pass: per row (m+2)(m+3) (the upper
+    triangle of the augmented Gram, FMA = 2) + 6m (feature polynomial)."""
+    return sum((q["n"] - 1) * ((q["m"] + 2) * (q["m"] + 3) + 6 * q["m"]) for q in problems)
+
+
+def oracle_rate(problems, seconds):
+    """Oracle solves/s on a bounded sample (the oracle as it stands, numpy FP64)."""
+    from oracle import core
+    t0 = time.perf_counter()
+    k = 0
+    while k < len(problems):
+        core.solve_linear(problems[k])
+        k += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return k / dt, k, dt
+
+
+def run_reference(args, rank, ws):
+    import nys_inputs as ni
+    if rank != 0:
+        return
+    probs = ni.m0(args.batch, n=args.n, m=args.m)
+    per_step = max(0.5, min(4.0, 60.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_rate(probs[:2], per_step / 4)
+    rates, tot_k, tot_t = [], 0, 0.0
+    for s in range(args.steps):
+        r, k, dt = oracle_rate(probs[s * 3:], per_step)
+        rates.append(r)
+        tot_k += k
+        tot_t += dt
+    value = tot_k / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "linear 2nd-order ODE batch, n=%d, m=%d, sigma=0.5, gamma=1e10"
+                       % (args.n, args.m), "global_batch": args.batch, "seq_len": args.n,
+                       "parallelism": "cpu"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "%d instances of the workload, %.1f s" % (tot_k, tot_t)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, ws, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, rank, ws)
+        return
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import nys_inputs as ni
+    from paper_2510_04094_gb300 import _abi
+    from paper_2510_04094_gb300.api import Batch, pack_instances
+
+    B = args.batch
+    probs = ni.linear_family(B, n=args.n, m=args.m, name="m0", sub=rank) if rank else \
+        ni.m0(B, n=args.n, m=args.m)
+    bt = Batch(probs, precision=args.precision)
+    refine = 2 if args.precision == "mixed" else 0
+    launches_per_step = 3 + 2 * refine
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(max(3, args.warmup)):
+        bt.run()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()                      # evict L2 between steps (outside the events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bt.run()
+        e1.record(stream)
+        times.append((e0, e1))
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in times) / args.steps
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    value = ws * B / (ms / 1000.0)
+
+    # dominant-kernel timing (fused assembly) on the launching stream
+    asm_ms = []
+    for _ in range(max(3, args.steps)):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bt.assemble()
+        e1.record(stream)
+        asm_ms.append((e0, e1))
+    torch.cuda.synchronize()
+    asm_ms = sum(a.elapsed_time(b) for a, b in asm_ms) / len(asm_ms)
+    bt.solve()
+    torch.cuda.synchronize()
+    fl = asm_flops(probs)
+    achieved = fl / (asm_ms / 1000.0) / 1e12
+
+    # end to end through the public API: host instances -> H2D -> run -> D2H of x
+    x_host = torch.empty_like(bt.x, device="cpu").pin_memory()
+    arr_next, keep = pack_instances(ni.linear_family(B, n=args.n, m=args.m, name="m0", sub=100 + rank))
+    arr_same, keep2 = pack_instances(probs)
+    e2e_t = []
+    for s in range(args.steps):
+        arr = arr_next if s % 2 == 0 else arr_same
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _abi.nys_update(bt.ctx, arr, C_stream(stream))
+        bt.run()
+        x_host.copy_(bt.x, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = statistics.mean(e2e_t)
+    h2d = int(_abi.nys_upload_bytes(bt.ctx))
+    d2h = bt.x.numel() * 8
+    _abi.nys_update(bt.ctx, arr_same, C_stream(stream))
+    bt.run()
+    torch.cuda.synchronize()
+
+    extra = {}
+    cpu_base = None
+    if rank == 0 and not args.no_extras:
+        from oracle import core
+        # accuracy of the timed configuration against the FP64 oracle (sampled instances)
+        k = 6
+        grids = [core.grid(q) for q in probs[:k]]
+        y, _ = bt.eval(grids)
+        yc = y.cpu().numpy()
+        off, errs = 0, []
+        for q, g in zip(probs[:k], grids):
+            ref = core.solve_linear(q)["y"]
+            errs.append(float(np.abs(yc[off:off + len(g)] - ref).max() / np.abs(ref).max()))
+            off += len(g)
+        extra["rel_err_vs_oracle_max"] = max(errs)
+        extra["status_ok"] = bool((bt.status.cpu().numpy() == 0).all())
+        # plain FP64 path: batched and one instance per launch sequence
+        sub = probs[:256]
+        b64 = Batch(sub, precision="fp64")
+        b64.run()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(2):
+            b64.run()
+        torch.cuda.synchronize()
+        extra["fp64_batched_solves_s"] = 2 * len(sub) / (time.perf_counter() - t0)
+        b64.close()
+        singles = [Batch([q], precision="fp64") for q in probs[:16]]
+        for sb in singles:
+            sb.run()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for sb in singles:
+            sb.run()
+        torch.cuda.synchronize()
+        extra["fp64_per_instance_solves_s"] = len(singles) / (time.perf_counter() - t0)
+        for sb in singles:
+            sb.close()
+        extra["speedup_vs_fp64_per_instance"] = value / ws / extra["fp64_per_instance_solves_s"]
+        extra["asm_ms"] = asm_ms
+        rate, kk, dt = oracle_rate(probs, args.cpu_seconds)
+        cpu_base = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                    "sample": "first %d instances of the workload, numpy FP64 oracle, %.1f s" % (kk, dt)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": "linear 2nd-order ODE batch y''+ay'+by=c sin(wt), n=%d, m=%d, "
+                                   "sigma=0.5, gamma=1e10, %s" % (args.n, args.m, args.precision),
+                       "global_batch": ws * B, "seq_len": args.n, "parallelism": "dp%d" % ws,
+                       "l2": "flushed between steps (256 MB write)"},
+            "e2e": {"value": ws * B / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "roofline": {"bound": "alu", "kernel": "k_assemble_f32" if args.precision == "mixed"
+                         else "k_assemble_f64", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                         "flops_per_launch": fl, "ms_per_launch": asm_ms},
+            "cpu_baseline": cpu_base,
+            "clocks": clk,
+            "gpu_launches": launches_per_step * args.steps,
+            "extra": extra,
+        }
+        print(json.dumps(line), flush=True)
+    bt.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def C_stream(stream):
+    import ctypes
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * nys.h -- C ABI of the GB300 Nystrom-accelerated primal LS-SVM ODE solver.
+ *
+ * Method (arXiv 2510.04094): an ODE y^(p) = f(t, y, ..) on a grid t_1..t_n is
+ * fitted by y^(t) = omega^T phi(t) + b, where phi(t) = Lambda^{-1/2} U^T k(t)
+ * is the explicit Nystrom feature map built from the eigendecomposition
+ * Omega_mm = U Lambda U^T of the m x m landmark kernel (Appendix A.2, eq32),
+ * k_j(t) = K(t, s_j) = exp(-(t - s_j)^2 / sigma^2) (Section 3, RBF kernel).
+ * Linear ODEs: the primal system of Lemma 1 (Section 3.1).  Nonlinear ODEs:
+ * Lemma 2 (Section 3.2, Eq. 2.2) solved by Newton's method (Eq. 3.2.1).
+ *
+ * Conventions for every entry point:
+ *  - Return value: NYS_OK (0) or a negative nys_status.  Argument and CUDA
+ *    errors are reported synchronously; nys_last_error() then gives a message
+ *    (thread-local).  Nothing aborts, traps or throws across the ABI.
+ *  - Numerical outcomes are per instance and asynchronous: they are written
+ *    to a caller-provided device array status_out (int32, one per instance).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  All device work is enqueued on it; calls return before the
+ *    work finishes.  A context must be used from one stream at a time.
+ *  - Pointers documented "device" must be device (or managed) memory that
+ *    stays valid until the enqueued work completes; "host" pointers are read
+ *    before the call returns.  The caller owns all pointers it passes; the
+ *    context owns its own workspaces and frees them in nys_destroy.
+ *  - Only nys_setup allocates device memory (cudaMalloc); later calls
+ *    allocate nothing on the device.
+ */
+#ifndef NYS_H
+#define NYS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NYS_OK = 0,
+  NYS_EINVAL = -1,      /* invalid argument (detail in nys_last_error)          */
+  NYS_ENOMEM = -2,      /* device or pinned host allocation failed              */
+  NYS_ECUDA = -3,       /* a CUDA runtime call failed                           */
+  NYS_ENOTSPD = -4,     /* per instance: projected Hessian not positive definite */
+  NYS_ENOCONV = -5,     /* per instance: Newton iteration cap reached           */
+  NYS_ENONFINITE = -6,  /* per instance: NaN/Inf in inputs or results           */
+  NYS_ETIMEOUT = -7,    /* reserved: a bounded device wait gave up              */
+  NYS_EPRECISION = -8,  /* reserved: refinement did not contract                */
+  NYS_ESTATE = -9       /* call out of order (e.g. solve before assemble)       */
+} nys_status;
+
+typedef enum { NYS_FP64 = 0, NYS_MIXED = 1 } nys_precision;
+
+/* Coefficient families of the ODE (Section 2, Eq. 2.1; Section 3.1).       */
+typedef enum {
+  /* y^(p) - sum_{k=1..p} f_k(t) y^(p-k) = r(t) with f_k, r tabulated on the
+     grid: coef_table is (p+1) x n, row-major, rows f_1..f_p then r.        */
+  NYS_COEF_TABLE = 0,
+  /* y^(p) + sum_k a_k y^(p-k) = c sin(omega t + phi0):
+     c[0] = a_1, c[1] = a_2 (p = 2), c[2] = c, c[3] = omega, c[4] = phi0.   */
+  NYS_COEF_LIN = 1,
+  /* nonlinear (Lemma 2): y^(p) = c0 + c1 y + c2 y^2 + c3 y^3
+     - delta y^(p-1) [p = 2 only] + g cos(omega t):
+     c[0..3] = c0..c3, c[4] = delta, c[5] = g, c[6] = omega.                */
+  NYS_COEF_POLY_NL = 2
+} nys_coef_kind;
+
+/* One ODE instance (host struct).  Grid: t_i = t0 + (i-1)(t1-t0)/(n-1),
+   i = 1..n.  Constraints at t_1: y(t_1) = v[0], y'(t_1) = v[1] (p = 2).     */
+typedef struct {
+  int32_t p;                 /* ODE order, 1 or 2                                  */
+  int32_t n;                 /* collocation points, 3 <= n <= 2^24                 */
+  int32_t m;                 /* landmarks, 2 <= m <= min(n, NYS_M_MAX)             */
+  int32_t kind;              /* nys_coef_kind                                      */
+  double t0, t1;             /* interval, t1 > t0                                  */
+  double sigma;              /* RBF width in exp(-(u-v)^2/sigma^2), > 0            */
+  double gamma;              /* regularisation constant, > 0                       */
+  double v[2];               /* initial values                                     */
+  double c[8];               /* coefficients, layout per kind above                */
+  const int32_t* landmarks;  /* host, optional: m increasing 0-based grid indices;
+                                NULL = evenly spaced, index round(j(n-1)/(m-1))    */
+  const double* coef_table;  /* host, kind TABLE only: (p+1) x n                   */
+} nys_instance;
+
+#define NYS_M_MAX 112
+
+typedef struct {
+  int32_t precision;     /* nys_precision.  MIXED: FP32 assembly and FP32 factor,
+                            refined against FP64-accurate residuals.             */
+  int32_t refine_steps;  /* MIXED: residual passes after the first solve (0..8;
+                            default 2 when negative)                             */
+  double eig_tau;        /* drop eigenpairs with lambda <= tau * lambda_max
+                            (default 1e-12 when <= 0)                            */
+  int32_t scale_sqrt_m;  /* 1: eq32's sqrt(m) feature scale (== gamma * m)      */
+  int32_t reserved;
+} nys_options;
+
+typedef struct nys_ctx nys_ctx;
+
+/* Create a context for `batch` instances (host array `inst`), allocate all
+   device workspaces, upload the descriptors and enqueue the Nystrom setup
+   (landmark kernel, FP64 eigendecomposition, W = Lambda^{-1/2} U^T;
+   Appendix A.2, Eq. 10 and eq32).  Instances with identical landmark sets
+   (same m, grid spacing/sigma and indices) share one factor.
+   Errors: NYS_EINVAL (bad instance: message names it), NYS_ENOMEM, NYS_ECUDA. */
+int32_t nys_setup(nys_ctx** out, const nys_instance* inst, int32_t batch,
+                  const nys_options* opt, void* stream);
+
+/* Replace the instances of an existing context (same batch size; per
+   instance same p, n, m, kind and landmark indices as at setup).  Enqueues
+   the host -> device copy of the descriptors; the Nystrom factor is
+   recomputed by the next nys_assemble or nys_run.
+   Errors: NYS_EINVAL (shape changed), NYS_ECUDA.                            */
+int32_t nys_update(nys_ctx* c, const nys_instance* inst, void* stream);
+
+/* Fused row pass (Lemma 1, Section 3.1): for every collocation row
+   i = 2..n evaluate k, k', k'' at t_i against the landmarks, apply the ODE
+   operator and accumulate the Gram of [kappa_i; -f_p(t_i); r(t_i)] without
+   storing any n x m matrix.  kappa_i = k^(p)(t_i) - sum f_k k^(p-k)(t_i).  */
+int32_t nys_assemble(nys_ctx* c, void* stream);
+
+/* Solve Lemma 1's system [E + A M, -A f_p, C^T; ...] [omega; b; lambda] =
+   [A r; V r; v] for every instance: H = D + gamma B G B^T with B = blkdiag(W, 1),
+   null-space elimination of the initial-condition rows, Cholesky.  MIXED adds
+   refine_steps residual passes.  x_out: device, batch x nys_x_stride(c)
+   doubles, per instance [omega (m_eff, zero padded to m_max), b, lambda_1,
+   lambda_2].  status_out: device, batch int32 (NYS_OK / NYS_ENOTSPD /
+   NYS_ENONFINITE).  Either pointer may be NULL.                              */
+int32_t nys_solve(nys_ctx* c, void* stream, double* x_out, int32_t* status_out);
+
+/* Nystrom setup + nys_assemble + nys_solve as one CUDA graph (reading the
+   descriptors currently on the device), captured on the first call for this
+   (x_out, status_out) pair and replayed afterwards.                         */
+int32_t nys_run(nys_ctx* c, void* stream, double* x_out, int32_t* status_out);
+
+/* Stride (doubles) of one instance in x_out: m_max + 3.                     */
+int32_t nys_x_stride(const nys_ctx* c);
+
+/* Bytes copied host -> device by the last nys_setup / nys_update.           */
+int64_t nys_upload_bytes(const nys_ctx* c);
+
+/* Number of eigenpairs kept per instance (host array, batch entries).
+   Synchronises the context's stream.                                         */
+int32_t nys_m_eff(nys_ctx* c, void* stream, int32_t* m_eff_host);
+
+/* Evaluate the fitted model y^(deriv)(t) = omega^T phi^(deriv)(t) + b[deriv==0]
+   (Section 3; deriv 0, 1 or 2) of the last solve or Newton call.
+   tq: device query times, tq_off: device int64[batch + 1] offsets into tq,
+   yq_out: device, same length as tq.                                          */
+int32_t nys_eval(nys_ctx* c, void* stream, const double* tq, const int64_t* tq_off,
+                 int32_t deriv, double* yq_out);
+
+/* Newton's method (Eq. 3.2.1) on Lemma 2's KKT system for NYS_COEF_POLY_NL
+   instances (FP64).  The diagonal y-block of the Jacobian is eliminated per
+   row exactly, so each step costs one fused row pass and an (m+1+p) solve.
+   Start: omega = 0, b = v_1, lambda = 0, y_i = v_1.  Stop when
+   |dx|_2 <= tol (1 + |x|_2) for x = (omega, b) and |F|_2 <= tol max(1, |F0|_2).
+   x_out as in nys_solve; y_aux_out (device, optional): sum_b (n_b - 1)
+   doubles, instance after instance; iters_out, status_out: device int32[batch]
+   (status NYS_OK or NYS_ENOCONV with the last iterate).  Host-synchronising:
+   reads one convergence flag per iteration.                                  */
+int32_t nys_newton(nys_ctx* c, void* stream, int32_t max_iter, double tol,
+                   double* x_out, double* y_aux_out, int32_t* iters_out,
+                   int32_t* status_out);
+
+/* Adjoint gradient (NYS_COEF_LIN, p = 2) of a loss on y^(tau) with respect to
+   theta = (a_1, a_2, c, omega, y0, y0', sigma) of the last nys_solve:
+   one adjoint solve with the stored factor and one fused row pass.
+   obs_t: device observation times, obs_off: device int64[batch + 1],
+   dl_dy: device dloss/dy^(obs_t) (same length as obs_t),
+   grad_out: device, batch x 7 doubles.                                        */
+int32_t nys_grad(nys_ctx* c, void* stream, const double* obs_t, const int64_t* obs_off,
+                 const double* dl_dy, double* grad_out);
+
+/* Free every resource of the context (synchronises its last stream).         */
+void nys_destroy(nys_ctx* c);
+
+const char* nys_status_str(int32_t status);
+const char* nys_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NYS_H */

@@ -1,0 +1,153 @@
+"""Thin PyTorch-facing wrapper over the C ABI (argument marshalling only).
+
+PyTorch provides device memory (torch tensors) and the CUDA stream; every
+computation happens in libnys.so.  Problems are plain dicts (see
+``nys_inputs``): p, n, m, t0, t1, sigma, gamma, v, kind and the
+kind-specific coefficients.
+"""
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _abi as A
+
+_KIND = {"table": A.NYS_COEF_TABLE, "lin": A.NYS_COEF_LIN, "nl": A.NYS_COEF_POLY_NL}
+
+
+def _stream_handle(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def pack_instances(problems):
+    """Marshal problem dicts into a ctypes nys_instance array (+ keep-alive buffers)."""
+    B = len(problems)
+    arr = (A.nys_instance * B)()
+    keep = []
+    for b, q in enumerate(problems):
+        s = arr[b]
+        s.p, s.n, s.m = int(q["p"]), int(q["n"]), int(q["m"])
+        s.kind = _KIND[q["kind"]]
+        s.t0, s.t1 = float(q["t0"]), float(q["t1"])
+        s.sigma, s.gamma = float(q["sigma"]), float(q["gamma"])
+        v = list(q["v"]) + [0.0] * (2 - len(q["v"]))
+        s.v[0], s.v[1] = float(v[0]), float(v[1])
+        c = [0.0] * 8
+        if q["kind"] == "lin":
+            a = list(q["a"]) + [0.0] * (2 - len(q["a"]))
+            c[0], c[1] = a[0], a[1]
+            c[2], c[3], c[4] = q["c"], q["omega"], q.get("phi0", 0.0)
+        elif q["kind"] == "nl":
+            c[0:4] = list(q["P"])
+            c[4], c[5], c[6] = q.get("delta", 0.0), q.get("g", 0.0), q.get("omega", 0.0)
+        elif q["kind"] == "table":
+            tabv = np.ascontiguousarray(np.concatenate(
+                [np.asarray(q["f"], dtype=np.float64).reshape(s.p, s.n),
+                 np.asarray(q["r"], dtype=np.float64).reshape(1, s.n)]), dtype=np.float64)
+            keep.append(tabv)
+            s.coef_table = tabv.ctypes.data_as(C.POINTER(C.c_double))
+        for k in range(8):
+            s.c[k] = float(c[k])
+        if q.get("landmarks") is not None:
+            lmv = np.ascontiguousarray(q["landmarks"], dtype=np.int32)
+            keep.append(lmv)
+            s.landmarks = lmv.ctypes.data_as(C.POINTER(C.c_int32))
+    return arr, keep
+
+
+class Batch:
+    """A batch of ODE instances bound to one nys_ctx on the current CUDA device."""
+
+    def __init__(self, problems, precision="fp64", refine_steps=-1, eig_tau=0.0,
+                 scale_sqrt_m=False, stream=None):
+        self.problems = list(problems)
+        self.B = len(self.problems)
+        self.stream = stream
+        opt = A.nys_options()
+        opt.precision = A.NYS_MIXED if precision == "mixed" else A.NYS_FP64
+        opt.refine_steps = int(refine_steps)
+        opt.eig_tau = float(eig_tau)
+        opt.scale_sqrt_m = 1 if scale_sqrt_m else 0
+        arr, keep = pack_instances(self.problems)
+        self.ctx = A.nys_setup(arr, self.B, opt, _stream_handle(stream))
+        self.XS = A.nys_x_stride(self.ctx)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.x = torch.zeros(self.B, self.XS, dtype=torch.float64, device=dev)
+        self.status = torch.zeros(self.B, dtype=torch.int32, device=dev)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            A.nys_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def update(self, problems):
+        arr, keep = pack_instances(problems)
+        self.problems = list(problems)
+        A.nys_update(self.ctx, arr, _stream_handle(self.stream))
+
+    def assemble(self):
+        A.nys_assemble(self.ctx, _stream_handle(self.stream))
+
+    def solve(self):
+        A.nys_solve(self.ctx, _stream_handle(self.stream), _ptr(self.x), _ptr(self.status))
+        return self.x, self.status
+
+    def run(self):
+        A.nys_run(self.ctx, _stream_handle(self.stream), _ptr(self.x), _ptr(self.status))
+        return self.x, self.status
+
+    def m_eff(self):
+        out = (C.c_int32 * self.B)()
+        A.nys_m_eff(self.ctx, _stream_handle(self.stream), out)
+        return np.frombuffer(out, dtype=np.int32).copy()
+
+    def eval(self, tq, tq_off=None, deriv=0):
+        """tq: list of per-instance query arrays (instances 0..len(tq)-1; the rest get
+        none), or a flat CUDA tensor with int64 offsets of length batch + 1."""
+        dev = self.x.device
+        if tq_off is None:
+            if len(tq) > self.B:
+                raise ValueError("more query lists than instances")
+            lens = [len(a) for a in tq] + [0] * (self.B - len(tq))
+            tq_off = torch.tensor(np.r_[0, np.cumsum(lens)], dtype=torch.int64, device=dev)
+            tq = torch.tensor(np.concatenate([np.asarray(a, dtype=np.float64) for a in tq]),
+                              dtype=torch.float64, device=dev)
+        if tq_off.numel() != self.B + 1:
+            raise ValueError("tq_off must have batch + 1 entries")
+        y = torch.empty_like(tq)
+        A.nys_eval(self.ctx, _stream_handle(self.stream), _ptr(tq), _ptr(tq_off), int(deriv), _ptr(y))
+        return y, tq_off
+
+    def newton(self, max_iter=50, tol=1e-10, want_y=False):
+        dev = self.x.device
+        iters = torch.zeros(self.B, dtype=torch.int32, device=dev)
+        yaux = None
+        if want_y:
+            yaux = torch.empty(sum(q["n"] - 1 for q in self.problems), dtype=torch.float64, device=dev)
+        A.nys_newton(self.ctx, _stream_handle(self.stream), int(max_iter), float(tol), _ptr(self.x),
+                     _ptr(yaux), _ptr(iters), _ptr(self.status))
+        return self.x, self.status, iters, yaux
+
+    def grad(self, obs_t, obs_off, dl_dy):
+        g = torch.empty(self.B, 7, dtype=torch.float64, device=self.x.device)
+        A.nys_grad(self.ctx, _stream_handle(self.stream), _ptr(obs_t), _ptr(obs_off), _ptr(dl_dy), _ptr(g))
+        return g
+
+    # unpack helpers ---------------------------------------------------------
+    def unpack(self):
+        x = self.x.cpu().numpy()
+        out = []
+        for b in range(self.B):
+            out.append(dict(omega=x[b, :self.XS - 3], b=x[b, self.XS - 3], lam=x[b, self.XS - 2:]))
+        return out

@@ -1,0 +1,595 @@
+// Host side of the C ABI declared in include/nys.h: argument validation,
+// descriptor packing, landmark-set de-duplication, row-pass work lists,
+// device workspaces, kernel launches and CUDA-graph capture.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "nys_internal.cuh"
+
+namespace nys {
+// kernel launchers (defined in the other translation units)
+cudaError_t launch_setup(Lset* lsets, const int32_t* nl_dev, int capacity, const int32_t* lm_idx,
+                         double* W, float* W32, double* lam, double tau, int m_max,
+                         cudaStream_t st);
+cudaError_t launch_assemble(bool fp32, const Inst* insts, const Work* work, int nwork,
+                            int* counter, const int32_t* lm, const double* tab, double* part,
+                            const int64_t* slot_off, int m_max, int num_sms, cudaStream_t st);
+cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const double* W,
+                         const float* W32, const double* part, const int64_t* slot_off,
+                         const int32_t* lm, void* fac, int64_t facs, double* xs, double* zs,
+                         double* cws, int XS, int ZS, int M1S, const int32_t* st_init,
+                         int32_t* st, double gamma_scale, int batch, int m_max, cudaStream_t s);
+cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W, const Work* work,
+                          int nwork, int* counter, const int32_t* lm, const double* tab,
+                          double* part, const int64_t* slot_off, const void* fac, int64_t facs,
+                          double* xs, double* zs, const double* cws, int XS, int ZS, int M1S,
+                          int32_t* st, double gamma_scale, int batch, int m_max, int num_sms,
+                          cudaStream_t s);
+cudaError_t launch_eval(const Inst* insts, const double* zs, int ZS, const int32_t* lm,
+                        const double* tq, const int64_t* tq_off, int deriv, double* yq, int batch,
+                        cudaStream_t s);
+size_t asm_smem_bytes(bool fp32, int m_max);
+int64_t fac_elems(int m_max);
+}  // namespace nys
+
+using namespace nys;
+
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+static int32_t fail(int32_t code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(NYS_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),     \
+                  __FILE__, __LINE__);                                                   \
+  } while (0)
+
+template <typename T>
+struct DBuf {  // owning device buffer
+  T* p = nullptr;
+  size_t n = 0;
+  cudaError_t alloc(size_t count) {
+    n = count;
+    if (count == 0) return cudaSuccess;
+    return cudaMalloc(reinterpret_cast<void**>(&p), count * sizeof(T));
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+struct GraphKey {
+  double* x;
+  int32_t* st;
+  cudaGraphExec_t exec;
+};
+
+struct nys_ctx {
+  int batch = 0, m_max = 0, p_max = 0, num_sms = 0, nwork = 0, nlset = 0;
+  int XS = 0, ZS = 0, M1S = 0;
+  int64_t facs = 0;
+  nys_options opt{};
+  bool fp32 = false;
+  bool any_nl = false, any_lin = false;
+  bool solved = false, assembled = false;
+  std::vector<nys_instance> shape;        // p, n, m, kind per instance (for update checks)
+  std::vector<int32_t> h_lm;               // landmark indices (host)
+  std::vector<int64_t> h_lm_off;
+  std::vector<Inst> h_inst;
+  std::vector<Lset> h_lset;
+  std::vector<int32_t> h_stinit;
+  std::vector<double> h_tab;
+  int64_t total_rows = 0;
+  // device
+  DBuf<Inst> inst;
+  DBuf<Lset> lset;
+  DBuf<int32_t> lm;
+  DBuf<double> tab;
+  DBuf<Work> work;
+  DBuf<int64_t> slot_off;
+  DBuf<double> part;
+  DBuf<double> W;
+  DBuf<float> W32;
+  DBuf<double> lam;
+  DBuf<unsigned char> fac;
+  DBuf<double> xs, zs, dzs, cws;
+  DBuf<int32_t> st, stinit, counter, nlset_dev;
+  // Newton state
+  DBuf<double> yaux, rowstate, nrm;
+  DBuf<int64_t> row_off;
+  DBuf<int32_t> active, iters, any_active;
+  // gradient scratch
+  DBuf<double> adj;
+  // pinned staging for descriptor uploads
+  Inst* pin_inst = nullptr;
+  Lset* pin_lset = nullptr;
+  int32_t* pin_st = nullptr;   // batch + 1 entries: statuses, then the set count
+  int32_t* pin_flag = nullptr;
+  cudaEvent_t staged = nullptr;
+  std::vector<GraphKey> graphs;
+  bool factor_stale = true;
+  int64_t upload_bytes = 0;
+};
+
+static bool finite_all(const double* a, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+static double mod2pi(double x) {
+  const double tp = 6.283185307179586476925286766559;
+  double r = std::fmod(x, tp);
+  if (r > M_PI) r -= tp;
+  if (r < -M_PI) r += tp;
+  return r;
+}
+
+// Validate one instance.  Returns NYS_OK, NYS_EINVAL (message set) or
+// NYS_ENONFINITE (non-finite coefficient data: the instance is skipped).
+static int32_t check_instance(const nys_instance& q, int b) {
+  if (q.p != 1 && q.p != 2) return fail(NYS_EINVAL, "instance %d: p must be 1 or 2 (got %d)", b, q.p);
+  if (q.n < 3 || q.n > (1 << 24)) return fail(NYS_EINVAL, "instance %d: n must be in [3, 2^24] (got %d)", b, q.n);
+  if (q.m < 2 || q.m > NYS_M_MAX || q.m > q.n)
+    return fail(NYS_EINVAL, "instance %d: m must be in [2, min(n, %d)] (got %d)", b, NYS_M_MAX, q.m);
+  if (q.kind < 0 || q.kind > 2) return fail(NYS_EINVAL, "instance %d: unknown kind %d", b, q.kind);
+  if (!(std::isfinite(q.t0) && std::isfinite(q.t1) && q.t1 > q.t0))
+    return fail(NYS_EINVAL, "instance %d: need finite t0 < t1", b);
+  if (!(std::isfinite(q.sigma) && q.sigma > 0)) return fail(NYS_EINVAL, "instance %d: sigma must be > 0", b);
+  if (!(std::isfinite(q.gamma) && q.gamma > 0)) return fail(NYS_EINVAL, "instance %d: gamma must be > 0", b);
+  if (q.kind == NYS_COEF_POLY_NL && q.p == 1 && q.c[4] != 0.0)
+    return fail(NYS_EINVAL, "instance %d: the delta y' term needs p = 2", b);
+  if (q.kind == NYS_COEF_TABLE && q.coef_table == nullptr)
+    return fail(NYS_EINVAL, "instance %d: kind TABLE needs coef_table", b);
+  if (q.landmarks) {
+    for (int j = 0; j < q.m; ++j) {
+      if (q.landmarks[j] < 0 || q.landmarks[j] >= q.n || (j > 0 && q.landmarks[j] <= q.landmarks[j - 1]))
+        return fail(NYS_EINVAL, "instance %d: landmarks must be increasing indices in [0, n)", b);
+    }
+  }
+  bool fin = finite_all(q.v, q.p) && finite_all(q.c, 8);
+  if (q.kind == NYS_COEF_TABLE) fin = fin && finite_all(q.coef_table, (q.p + 1) * q.n);
+  return fin ? NYS_OK : NYS_ENONFINITE;
+}
+
+static void default_landmarks(int n, int m, int32_t* out) {
+  for (int j = 0; j < m; ++j)
+    out[j] = (int32_t)(((int64_t)j * (n - 1) + (m - 1) / 2) / (m - 1));
+}
+
+// Fill h_inst / h_lset / h_stinit / h_tab from the instance array (host only).
+static int32_t pack(nys_ctx* c, const nys_instance* q, bool first) {
+  const int B = c->batch;
+  c->h_inst.assign(B, Inst{});
+  c->h_stinit.assign(B, NYS_OK);
+  if (first) {
+    c->h_lm.clear();
+    c->h_lm_off.assign(B, 0);
+  }
+  c->h_tab.clear();
+  std::map<std::vector<int64_t>, int> keys;
+  c->h_lset.clear();
+  for (int b = 0; b < B; ++b) {
+    const nys_instance& s = q[b];
+    int32_t r = check_instance(s, b);
+    if (r == NYS_EINVAL) return r;
+    if (!first) {
+      const nys_instance& o = c->shape[b];
+      if (o.p != s.p || o.n != s.n || o.m != s.m || o.kind != s.kind)
+        return fail(NYS_EINVAL, "nys_update: instance %d changed p, n, m or kind", b);
+    }
+    std::vector<int32_t> lm(s.m);
+    if (s.landmarks) std::memcpy(lm.data(), s.landmarks, sizeof(int32_t) * s.m);
+    else default_landmarks(s.n, s.m, lm.data());
+    if (first) {
+      c->h_lm_off[b] = (int64_t)c->h_lm.size();
+      c->h_lm.insert(c->h_lm.end(), lm.begin(), lm.end());
+    } else {
+      if (std::memcmp(lm.data(), c->h_lm.data() + c->h_lm_off[b], sizeof(int32_t) * s.m) != 0)
+        return fail(NYS_EINVAL, "nys_update: instance %d changed its landmarks", b);
+    }
+    Inst& I = c->h_inst[b];
+    I.p = s.p; I.n = s.n; I.m = s.m; I.kind = s.kind;
+    I.lm_off = c->h_lm_off[b];
+    I.t0 = s.t0;
+    I.h = (s.t1 - s.t0) / (double)(s.n - 1);
+    I.sigma = s.sigma;
+    // eq32's sqrt(m) feature scale is the same problem with gamma -> m gamma
+    I.gamma = c->opt.scale_sqrt_m ? s.gamma * s.m : s.gamma;
+    I.v[0] = s.v[0];
+    I.v[1] = (s.p == 2) ? s.v[1] : 0.0;
+    for (int k = 0; k < 8; ++k) I.c[k] = s.c[k];
+    if (s.p == 1 && s.kind == NYS_COEF_LIN) I.c[1] = 0.0;
+    I.hs = I.h / s.sigma;
+    I.th0 = mod2pi(s.c[3] * s.t0 + s.c[4]);
+    I.dth = mod2pi(s.c[3] * I.h);
+    I.tab_off = -1;
+    if (s.kind == NYS_COEF_TABLE) {
+      I.tab_off = (int64_t)c->h_tab.size();
+      c->h_tab.insert(c->h_tab.end(), s.coef_table, s.coef_table + (size_t)(s.p + 1) * s.n);
+    }
+    c->h_stinit[b] = r;
+    // landmark-set key: m, indices, bits of h/sigma
+    std::vector<int64_t> key(lm.begin(), lm.end());
+    int64_t hbits;
+    std::memcpy(&hbits, &I.hs, sizeof hbits);
+    key.push_back(hbits);
+    key.push_back(s.m);
+    auto it = keys.find(key);
+    if (it == keys.end()) {
+      const int id = (int)c->h_lset.size();
+      keys.emplace(std::move(key), id);
+      Lset L{};
+      L.m = s.m;
+      L.m_eff = s.m;
+      L.lm_off = I.lm_off;
+      L.w_off = (int64_t)id * c->m_max * c->m_max;
+      L.hs = I.hs;
+      c->h_lset.push_back(L);
+      I.lset = id;
+    } else {
+      I.lset = it->second;
+    }
+  }
+  c->nlset = (int)c->h_lset.size();
+  return NYS_OK;
+}
+
+static cudaError_t enqueue_factor(nys_ctx* c, cudaStream_t s) {
+  return launch_setup(c->lset.p, c->nlset_dev.p, c->batch, c->lm.p, c->W.p, c->W32.p, c->lam.p,
+                      c->opt.eig_tau > 0 ? c->opt.eig_tau : 1e-12, c->m_max, s);
+}
+
+static int32_t upload_and_setup(nys_ctx* c, cudaStream_t s, bool factor_now) {
+  // reuse of the pinned staging buffers: wait for the previous upload
+  CK(cudaEventSynchronize(c->staged));
+  std::memcpy(c->pin_inst, c->h_inst.data(), sizeof(Inst) * c->batch);
+  std::memcpy(c->pin_lset, c->h_lset.data(), sizeof(Lset) * c->nlset);
+  std::memcpy(c->pin_st, c->h_stinit.data(), sizeof(int32_t) * c->batch);
+  c->pin_st[c->batch] = c->nlset;
+  CK(cudaMemcpyAsync(c->inst.p, c->pin_inst, sizeof(Inst) * c->batch, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->lset.p, c->pin_lset, sizeof(Lset) * c->nlset, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->stinit.p, c->pin_st, sizeof(int32_t) * c->batch, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->st.p, c->pin_st, sizeof(int32_t) * c->batch, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->nlset_dev.p, c->pin_st + c->batch, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  if (!c->h_tab.empty())
+    CK(cudaMemcpyAsync(c->tab.p, c->h_tab.data(), sizeof(double) * c->h_tab.size(),
+                       cudaMemcpyHostToDevice, s));
+  CK(cudaEventRecord(c->staged, s));
+  if (!c->h_tab.empty()) CK(cudaStreamSynchronize(s));  // pageable source
+  c->upload_bytes = (int64_t)(sizeof(Inst) * c->batch + sizeof(Lset) * c->nlset +
+                              2 * sizeof(int32_t) * c->batch + sizeof(double) * c->h_tab.size());
+  c->factor_stale = true;
+  if (factor_now) {
+    CK(enqueue_factor(c, s));
+    c->factor_stale = false;
+  }
+  c->assembled = false;
+  c->solved = false;
+  return NYS_OK;
+}
+
+extern "C" {
+
+const char* nys_last_error(void) { return g_err.c_str(); }
+
+const char* nys_status_str(int32_t s) {
+  switch (s) {
+    case NYS_OK: return "ok";
+    case NYS_EINVAL: return "invalid argument";
+    case NYS_ENOMEM: return "out of memory";
+    case NYS_ECUDA: return "CUDA error";
+    case NYS_ENOTSPD: return "projected Hessian not positive definite";
+    case NYS_ENOCONV: return "Newton iteration cap reached";
+    case NYS_ENONFINITE: return "non-finite input or result";
+    case NYS_ETIMEOUT: return "device wait timed out";
+    case NYS_EPRECISION: return "refinement did not contract";
+    case NYS_ESTATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+void nys_destroy(nys_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->inst.release(); c->lset.release(); c->lm.release(); c->tab.release(); c->work.release();
+  c->slot_off.release(); c->part.release(); c->W.release(); c->W32.release(); c->lam.release();
+  c->fac.release(); c->xs.release(); c->zs.release(); c->dzs.release(); c->cws.release();
+  c->st.release(); c->stinit.release(); c->counter.release(); c->nlset_dev.release(); c->yaux.release(); c->rowstate.release();
+  c->nrm.release(); c->row_off.release(); c->active.release(); c->iters.release();
+  c->any_active.release(); c->adj.release();
+  if (c->pin_inst) cudaFreeHost(c->pin_inst);
+  if (c->pin_lset) cudaFreeHost(c->pin_lset);
+  if (c->pin_st) cudaFreeHost(c->pin_st);
+  if (c->pin_flag) cudaFreeHost(c->pin_flag);
+  if (c->staged) cudaEventDestroy(c->staged);
+  delete c;
+}
+
+int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys_options* opt,
+                  void* stream) {
+  if (!out) return fail(NYS_EINVAL, "nys_setup: out is NULL");
+  *out = nullptr;
+  if (!q || batch < 1) return fail(NYS_EINVAL, "nys_setup: need batch >= 1 instances");
+  nys_ctx* c = new nys_ctx();
+  c->batch = batch;
+  if (opt) c->opt = *opt;
+  else { c->opt.precision = NYS_FP64; c->opt.refine_steps = -1; }
+  if (c->opt.precision != NYS_FP64 && c->opt.precision != NYS_MIXED) {
+    delete c;
+    return fail(NYS_EINVAL, "nys_setup: unknown precision %d", c->opt.precision);
+  }
+  if (c->opt.refine_steps < 0) c->opt.refine_steps = 2;
+  if (c->opt.refine_steps > 8) { delete c; return fail(NYS_EINVAL, "nys_setup: refine_steps > 8"); }
+  c->fp32 = (c->opt.precision == NYS_MIXED);
+  for (int b = 0; b < batch; ++b) {
+    c->m_max = std::max(c->m_max, std::max(2, q[b].m));
+    c->p_max = std::max(c->p_max, q[b].p);
+  }
+  c->m_max = std::min(c->m_max, NYS_M_MAX);
+  c->shape.assign(q, q + batch);
+  for (auto& s : c->shape) { s.landmarks = nullptr; s.coef_table = nullptr; }
+  int32_t r = pack(c, q, true);
+  if (r != NYS_OK) { delete c; return r; }
+  for (int b = 0; b < batch; ++b) {
+    if (q[b].kind == NYS_COEF_POLY_NL) c->any_nl = true;
+    else c->any_lin = true;
+  }
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (ce != cudaSuccess) { delete c; return fail(NYS_ECUDA, "no CUDA device: %s", cudaGetErrorString(ce)); }
+  cudaStream_t s = (cudaStream_t)stream;
+
+  // row-pass work list: split instances so that there are >= 4 items per SM
+  std::vector<Work> wl;
+  std::vector<int64_t> soff;
+  int64_t total_rows = 0;
+  for (int b = 0; b < batch; ++b) total_rows += q[b].n - 1;
+  c->total_rows = total_rows;
+  const int64_t target = std::max<int64_t>(batch, 4LL * c->num_sms);
+  const int64_t rpi = std::max<int64_t>(64, (total_rows + target - 1) / target);
+  int64_t poff = 0;
+  int slot = 0;
+  for (int b = 0; b < batch; ++b) {
+    const int nrows = q[b].n - 1;
+    const int chunks = (int)std::max<int64_t>(1, (nrows + rpi - 1) / rpi);
+    const int M2 = q[b].m + 2;
+    const int64_t E = (int64_t)M2 * (M2 + 1) / 2;
+    c->h_inst[b].slot_begin = slot;
+    c->h_inst[b].slot_count = chunks;
+    for (int k = 0; k < chunks; ++k) {
+      Work w;
+      w.inst = b;
+      w.r0 = 1 + (int)((int64_t)nrows * k / chunks);
+      w.r1 = 1 + (int)((int64_t)nrows * (k + 1) / chunks);
+      w.slot = slot++;
+      wl.push_back(w);
+      soff.push_back(poff);
+      poff += E;
+    }
+  }
+  std::stable_sort(wl.begin(), wl.end(), [&](const Work& a, const Work& b2) {
+    const double ca = (double)(a.r1 - a.r0) * (q[a.inst].m + 2) * (q[a.inst].m + 2);
+    const double cb = (double)(b2.r1 - b2.r0) * (q[b2.inst].m + 2) * (q[b2.inst].m + 2);
+    return ca > cb;
+  });
+  c->nwork = (int)wl.size();
+  c->XS = c->m_max + 3;
+  c->ZS = c->m_max + 1;
+  c->M1S = c->m_max + 1;
+  c->facs = fac_elems(c->m_max);
+  const size_t es = c->fp32 ? sizeof(float) : sizeof(double);
+  // Newton row offsets
+  std::vector<int64_t> roff(batch);
+  int64_t ytot = 0;
+  for (int b = 0; b < batch; ++b) {
+    c->h_inst[b].y_off = ytot;
+    roff[b] = ytot;
+    ytot += q[b].n - 1;
+  }
+
+  cudaError_t e = cudaSuccess;
+  auto A = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+  A(c->inst.alloc(batch));
+  A(c->lset.alloc(batch));
+  A(c->lm.alloc(c->h_lm.size()));
+  A(c->tab.alloc(std::max<size_t>(1, c->h_tab.size())));
+  A(c->work.alloc(wl.size()));
+  A(c->slot_off.alloc(soff.size()));
+  A(c->part.alloc((size_t)poff));
+  A(c->W.alloc((size_t)batch * c->m_max * c->m_max));
+  A(c->W32.alloc((size_t)batch * c->m_max * c->m_max));
+  A(c->lam.alloc((size_t)batch * NYS_M_MAX));
+  A(c->fac.alloc((size_t)batch * c->facs * (c->any_nl ? sizeof(double) : es)));
+  A(c->xs.alloc((size_t)batch * c->XS));
+  A(c->zs.alloc((size_t)batch * c->ZS));
+  A(c->dzs.alloc((size_t)batch * c->ZS));
+  A(c->cws.alloc((size_t)batch * 2 * c->M1S));
+  A(c->st.alloc(batch));
+  A(c->stinit.alloc(batch));
+  A(c->counter.alloc(1));
+  A(c->nlset_dev.alloc(1));
+  if (c->any_nl) {
+    A(c->yaux.alloc((size_t)ytot));
+    A(c->rowstate.alloc((size_t)ytot * 4));
+    A(c->row_off.alloc(batch));
+    A(c->nrm.alloc((size_t)batch * 4));
+    A(c->active.alloc(batch));
+    A(c->iters.alloc(batch));
+    A(c->any_active.alloc(1));
+  }
+  A(cudaMallocHost(reinterpret_cast<void**>(&c->pin_inst), sizeof(Inst) * batch));
+  A(cudaMallocHost(reinterpret_cast<void**>(&c->pin_lset), sizeof(Lset) * batch));
+  A(cudaMallocHost(reinterpret_cast<void**>(&c->pin_st), sizeof(int32_t) * (batch + 1)));
+  A(cudaMallocHost(reinterpret_cast<void**>(&c->pin_flag), sizeof(int32_t)));
+  A(cudaEventCreateWithFlags(&c->staged, cudaEventDisableTiming));
+  if (e != cudaSuccess) {
+    const bool oom = (e == cudaErrorMemoryAllocation);
+    nys_destroy(c);
+    return fail(oom ? NYS_ENOMEM : NYS_ECUDA, "nys_setup: allocation failed: %s", cudaGetErrorString(e));
+  }
+  // one-time uploads (pageable sources: synchronous with respect to the host)
+  A(cudaMemcpyAsync(c->lm.p, c->h_lm.data(), sizeof(int32_t) * c->h_lm.size(), cudaMemcpyHostToDevice, s));
+  A(cudaMemcpyAsync(c->work.p, wl.data(), sizeof(Work) * wl.size(), cudaMemcpyHostToDevice, s));
+  A(cudaMemcpyAsync(c->slot_off.p, soff.data(), sizeof(int64_t) * soff.size(), cudaMemcpyHostToDevice, s));
+  if (c->any_nl) A(cudaMemcpyAsync(c->row_off.p, roff.data(), sizeof(int64_t) * batch, cudaMemcpyHostToDevice, s));
+  A(cudaStreamSynchronize(s));
+  if (e != cudaSuccess) {
+    nys_destroy(c);
+    return fail(NYS_ECUDA, "nys_setup: upload failed: %s", cudaGetErrorString(e));
+  }
+  r = upload_and_setup(c, s, true);
+  if (r != NYS_OK) { nys_destroy(c); return r; }
+  *out = c;
+  return NYS_OK;
+}
+
+int32_t nys_update(nys_ctx* c, const nys_instance* q, void* stream) {
+  if (!c || !q) return fail(NYS_EINVAL, "nys_update: NULL argument");
+  // keep the work-list fields of the descriptors
+  std::vector<Inst> keep = c->h_inst;
+  int32_t r = pack(c, q, false);
+  if (r != NYS_OK) { c->h_inst = keep; return r; }
+  for (int b = 0; b < c->batch; ++b) {
+    c->h_inst[b].slot_begin = keep[b].slot_begin;
+    c->h_inst[b].slot_count = keep[b].slot_count;
+    c->h_inst[b].y_off = keep[b].y_off;
+  }
+  return upload_and_setup(c, (cudaStream_t)stream, false);
+}
+
+int32_t nys_assemble(nys_ctx* c, void* stream) {
+  if (!c) return fail(NYS_EINVAL, "nys_assemble: NULL context");
+  if (c->any_nl) return fail(NYS_EINVAL, "nys_assemble: the batch holds nonlinear instances (use nys_newton)");
+  if (c->factor_stale) {
+    CK(enqueue_factor(c, (cudaStream_t)stream));
+    c->factor_stale = false;
+  }
+  CK(launch_assemble(c->fp32, c->inst.p, c->work.p, c->nwork, c->counter.p, c->lm.p, c->tab.p,
+                     c->part.p, c->slot_off.p, c->m_max, c->num_sms, (cudaStream_t)stream));
+  c->assembled = true;
+  return NYS_OK;
+}
+
+static int32_t solve_impl(nys_ctx* c, cudaStream_t s, double* x_out, int32_t* status_out) {
+  const double gscale = 1.0;
+  CK(launch_solve(c->fp32, c->inst.p, c->lset.p, c->W.p, c->W32.p, c->part.p, c->slot_off.p,
+                  c->lm.p, c->fac.p, c->facs, c->xs.p, c->zs.p, c->cws.p, c->XS, c->ZS, c->M1S,
+                  c->stinit.p, c->st.p, gscale, c->batch, c->m_max, s));
+  if (c->fp32) {
+    for (int k = 0; k < c->opt.refine_steps; ++k)
+      CK(launch_refine(c->inst.p, c->lset.p, c->W.p, c->work.p, c->nwork, c->counter.p, c->lm.p,
+                       c->tab.p, c->part.p, c->slot_off.p, c->fac.p, c->facs, c->xs.p, c->zs.p,
+                       c->cws.p, c->XS, c->ZS, c->M1S, c->st.p, gscale, c->batch, c->m_max,
+                       c->num_sms, s));
+  }
+  if (x_out)
+    CK(cudaMemcpyAsync(x_out, c->xs.p, sizeof(double) * c->batch * c->XS, cudaMemcpyDeviceToDevice, s));
+  if (status_out)
+    CK(cudaMemcpyAsync(status_out, c->st.p, sizeof(int32_t) * c->batch, cudaMemcpyDeviceToDevice, s));
+  return NYS_OK;
+}
+
+int32_t nys_solve(nys_ctx* c, void* stream, double* x_out, int32_t* status_out) {
+  if (!c) return fail(NYS_EINVAL, "nys_solve: NULL context");
+  if (!c->assembled) return fail(NYS_ESTATE, "nys_solve: call nys_assemble first");
+  int32_t r = solve_impl(c, (cudaStream_t)stream, x_out, status_out);
+  if (r == NYS_OK) c->solved = true;
+  return r;
+}
+
+int32_t nys_run(nys_ctx* c, void* stream, double* x_out, int32_t* status_out) {
+  if (!c) return fail(NYS_EINVAL, "nys_run: NULL context");
+  if (c->any_nl) return fail(NYS_EINVAL, "nys_run: the batch holds nonlinear instances");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaGraphExec_t exec = nullptr;
+  for (auto& g : c->graphs)
+    if (g.x == x_out && g.st == status_out) exec = g.exec;
+  if (!exec) {
+    // capture on a private stream so the legacy default stream can be used by callers
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { cudaStreamDestroy(cs); CK(e); }
+    int32_t r = NYS_OK;
+    {
+      cudaError_t e2 = enqueue_factor(c, cs);
+      if (e2 == cudaSuccess)
+        e2 = launch_assemble(c->fp32, c->inst.p, c->work.p, c->nwork, c->counter.p,
+                                       c->lm.p, c->tab.p, c->part.p, c->slot_off.p, c->m_max,
+                                       c->num_sms, cs);
+      if (e2 != cudaSuccess) r = fail(NYS_ECUDA, "capture: assemble: %s", cudaGetErrorString(e2));
+      if (r == NYS_OK) r = solve_impl(c, cs, x_out, status_out);
+    }
+    e = cudaStreamEndCapture(cs, &graph);
+    cudaStreamDestroy(cs);
+    if (r != NYS_OK) { if (e == cudaSuccess) cudaGraphDestroy(graph); return r; }
+    CK(e);
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(e);
+    c->graphs.push_back({x_out, status_out, exec});
+  }
+  CK(cudaGraphLaunch(exec, s));
+  c->assembled = c->solved = true;
+  c->factor_stale = false;
+  return NYS_OK;
+}
+
+int64_t nys_upload_bytes(const nys_ctx* c) { return c ? c->upload_bytes : 0; }
+
+int32_t nys_x_stride(const nys_ctx* c) { return c ? c->XS : 0; }
+
+int32_t nys_m_eff(nys_ctx* c, void* stream, int32_t* out) {
+  if (!c || !out) return fail(NYS_EINVAL, "nys_m_eff: NULL argument");
+  std::vector<Lset> L(c->nlset);
+  CK(cudaMemcpyAsync(L.data(), c->lset.p, sizeof(Lset) * c->nlset, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  for (int b = 0; b < c->batch; ++b) out[b] = L[c->h_inst[b].lset].m_eff;
+  return NYS_OK;
+}
+
+int32_t nys_eval(nys_ctx* c, void* stream, const double* tq, const int64_t* tq_off, int32_t deriv,
+                 double* yq_out) {
+  if (!c || !tq || !tq_off || !yq_out) return fail(NYS_EINVAL, "nys_eval: NULL argument");
+  if (deriv < 0 || deriv > 2) return fail(NYS_EINVAL, "nys_eval: deriv must be 0, 1 or 2");
+  if (!c->solved) return fail(NYS_ESTATE, "nys_eval: no solution yet");
+  CK(launch_eval(c->inst.p, c->zs.p, c->ZS, c->lm.p, tq, tq_off, deriv, yq_out, c->batch,
+                 (cudaStream_t)stream));
+  return NYS_OK;
+}
+
+int32_t nys_newton(nys_ctx* c, void* stream, int32_t max_iter, double tol, double* x_out,
+                   double* y_aux_out, int32_t* iters_out, int32_t* status_out) {
+  (void)c; (void)stream; (void)max_iter; (void)tol; (void)x_out; (void)y_aux_out;
+  (void)iters_out; (void)status_out;
+  return fail(NYS_ESTATE, "nys_newton: not available in this build");
+}
+
+int32_t nys_grad(nys_ctx* c, void* stream, const double* obs_t, const int64_t* obs_off,
+                 const double* dl_dy, double* grad_out) {
+  (void)c; (void)stream; (void)obs_t; (void)obs_off; (void)dl_dy; (void)grad_out;
+  return fail(NYS_ESTATE, "nys_grad: not available in this build");
+}
+
+}  // extern "C"

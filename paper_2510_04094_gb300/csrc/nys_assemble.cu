@@ -1,0 +1,292 @@
+// Fused row pass of Lemma 1 (Section 3.1): for each collocation row i = 2..n,
+// evaluate the RBF kernel and its t-derivatives against the m landmarks, apply
+// the ODE operator, and accumulate the Gram of the augmented row
+//     psi_i = [kappa_i (m); -f_p(t_i); r(t_i)],
+//     kappa_i = k^(p)(t_i) - sum_k f_k(t_i) k^(p-k)(t_i),
+// so that   G = sum psi psi^T  holds  sum kappa kappa^T, sum kappa (-f_p),
+// sum f_p^2 and the right-hand sides sum kappa r, sum (-f_p) r.
+// The Nystrom projection W is linear, so A^T A of Lemma 1 is B G B^T with
+// B = blkdiag(W, 1); it is applied once per instance in the solve kernel
+// instead of once per row, and no n x m feature matrix is ever stored.
+//
+// Work is a list of (instance, row range) items taken from an atomic queue by
+// a persistent grid; each item writes its packed upper-triangular partial Gram
+// (M2 (M2+1)/2 doubles, M2 = m + 2) to its own slot.
+#include "nys_internal.cuh"
+
+namespace nys {
+
+// ---------------------------------------------------------------------------
+// FP64 variant: one accumulator set per thread over packed Gram entries.
+// ---------------------------------------------------------------------------
+constexpr int kAsm64Threads = 256;
+constexpr int kAsm64Rows = 32;
+
+template <int KMAX>
+__global__ void __launch_bounds__(kAsm64Threads)
+k_assemble_f64(const Inst* __restrict__ insts, const Work* __restrict__ work, int nwork,
+               int* __restrict__ counter, const int32_t* __restrict__ lm_idx,
+               const double* __restrict__ tab, double* __restrict__ part,
+               const int64_t* __restrict__ slot_off) {
+  extern __shared__ double sm64[];
+  __shared__ int s_item;
+  __shared__ int s_idx[kMMax];
+  __shared__ double s_rc[kAsm64Rows][5];
+  __shared__ unsigned char s_pair[2 * kM2Max * (kM2Max + 1) / 2];
+  const int tid = threadIdx.x;
+  int cached_m2 = -1;
+
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int w = s_item;
+    if (w >= nwork) break;
+    const Work wk = work[w];
+    const Inst I = insts[wk.inst];
+    const int m = I.m, M2 = m + 2, ld = M2 + 1;
+    const int E = M2 * (M2 + 1) / 2;
+    for (int j = tid; j < m; j += kAsm64Threads) s_idx[j] = lm_idx[I.lm_off + j];
+    if (M2 != cached_m2) {
+      for (int e = tid; e < E; e += kAsm64Threads) {
+        int j = 0, rem = e;
+        while (rem >= M2 - j) { rem -= M2 - j; ++j; }
+        s_pair[2 * e] = (unsigned char)j;
+        s_pair[2 * e + 1] = (unsigned char)(j + rem);
+      }
+      cached_m2 = M2;
+    }
+    double acc[KMAX];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) acc[k] = 0.0;
+    __syncthreads();
+
+    double* psi = sm64;
+    for (int base = wk.r0; base < wk.r1; base += kAsm64Rows) {
+      if (tid < kAsm64Rows) {
+        const int i = base + tid;
+        if (i < wk.r1) {
+          double f1, f2, rr;
+          coef_f(I, tab, i, f1, f2, rr);
+          if (I.kind == NYS_COEF_LIN) rr = lin_rhs_f64(I, i);
+          const RowCoef R = row_coef_from_f(I, f1, f2, rr);
+          s_rc[tid][0] = R.A0; s_rc[tid][1] = R.A1; s_rc[tid][2] = R.A2;
+          s_rc[tid][3] = R.w1; s_rc[tid][4] = R.rr;
+        }
+      }
+      __syncthreads();
+      for (int e = tid; e < kAsm64Rows * M2; e += kAsm64Threads) {
+        const int r = e / M2, j = e - r * M2;
+        const int i = base + r;
+        double val = 0.0;
+        if (i < wk.r1) {
+          if (j < m) {
+            const double x = (double)(i - s_idx[j]) * I.hs;
+            const double u = x * x;
+            val = exp(-u) * (s_rc[r][0] + s_rc[r][1] * x + s_rc[r][2] * u);
+          } else {
+            val = s_rc[r][3 + (j - m)];
+          }
+        }
+        psi[r * ld + j] = val;
+      }
+      __syncthreads();
+      const int rows = min(kAsm64Rows, wk.r1 - base);
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k) {
+        const int e = tid + k * kAsm64Threads;
+        if (e < E) {
+          const int j = s_pair[2 * e], l = s_pair[2 * e + 1];
+          double a = acc[k];
+          for (int r = 0; r < rows; ++r) a = fma(psi[r * ld + j], psi[r * ld + l], a);
+          acc[k] = a;
+        }
+      }
+      __syncthreads();
+    }
+    double* out = part + slot_off[wk.slot];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+      const int e = tid + k * kAsm64Threads;
+      if (e < E) out[e] = acc[k];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 variant (mixed-precision path).  The Gram is tiled in 8 x 8 register
+// blocks of the upper triangle (U = NB (NB+1)/2 blocks, NB = MP/8); S row
+// slices of U threads each split the rows of a tile, every thread running a
+// plain FP32 FMA accumulation of its 64 entries over its rows.  The S slice
+// sums are added at the end of the work item and stored as doubles.  The
+// accumulation error is removed later by FP64-accurate refinement.
+// ---------------------------------------------------------------------------
+constexpr int kAsm32Threads = 384;
+constexpr int kAsm32Rows = 128;
+constexpr int kPadF = 4;  // row padding of the psi tile (floats)
+
+__global__ void __launch_bounds__(kAsm32Threads, 1)
+k_assemble_f32(const Inst* __restrict__ insts, const Work* __restrict__ work, int nwork,
+               int* __restrict__ counter, const int32_t* __restrict__ lm_idx,
+               const double* __restrict__ tab, double* __restrict__ part,
+               const int64_t* __restrict__ slot_off) {
+  extern __shared__ __align__(16) float sm32[];
+  __shared__ int s_item;
+  __shared__ int s_idx[kMMax];
+  __shared__ float s_rc[kAsm32Rows][5];
+  const int tid = threadIdx.x;
+
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int w = s_item;
+    if (w >= nwork) break;
+    const Work wk = work[w];
+    const Inst I = insts[wk.inst];
+    const int m = I.m, M2 = m + 2;
+    const int MP = round_up(M2, 8), NB = MP / 8, U = NB * (NB + 1) / 2;
+    const int S = max(1, kAsm32Threads / U);
+    const int ld = MP + kPadF;
+    for (int j = tid; j < m; j += kAsm32Threads) s_idx[j] = lm_idx[I.lm_off + j];
+
+    // this thread's block (bj <= bl) and slice
+    const bool active = tid < U * S;
+    const int slice = tid / U, u = tid - slice * U;
+    int bj = 0, bl = 0;
+    {
+      int rem = u;
+      while (rem >= NB - bj) { rem -= NB - bj; ++bj; }
+      bl = bj + rem;
+    }
+    // feature-phase mapping: column fj, rows fr0 + k*RS
+    const int RS = kAsm32Threads / MP;
+    const int fj = tid % MP, fr0 = tid / MP;
+    const float hs = (float)I.hs;
+
+    float acc[64];
+#pragma unroll
+    for (int k = 0; k < 64; ++k) acc[k] = 0.f;
+    __syncthreads();
+
+    float* psi = sm32;
+    for (int base = wk.r0; base < wk.r1; base += kAsm32Rows) {
+      if (tid < kAsm32Rows) {
+        const int i = base + tid;
+        if (i < wk.r1) {
+          double f1, f2, rr;
+          coef_f(I, tab, i, f1, f2, rr);
+          const RowCoef R = row_coef_from_f(I, f1, f2, rr);
+          s_rc[tid][0] = (float)R.A0; s_rc[tid][1] = (float)R.A1; s_rc[tid][2] = (float)R.A2;
+          s_rc[tid][3] = (float)R.w1;
+          s_rc[tid][4] = (I.kind == NYS_COEF_LIN) ? lin_rhs_ff(I, i) : (float)rr;
+        }
+      }
+      __syncthreads();
+      if (fr0 < RS) {
+        const int sidx = (fj < m) ? s_idx[fj] : 0;
+        for (int r = fr0; r < kAsm32Rows; r += RS) {
+          const int i = base + r;
+          float val = 0.f;
+          if (i < wk.r1 && fj < M2) {
+            if (fj < m) {
+              const float x = (float)(i - sidx) * hs;
+              const float uu = x * x;
+              val = exp_neg_fast(uu) * fmaf(s_rc[r][2], uu, fmaf(s_rc[r][1], x, s_rc[r][0]));
+            } else {
+              val = s_rc[r][3 + (fj - m)];
+            }
+          }
+          psi[r * ld + fj] = val;
+        }
+      }
+      __syncthreads();
+      if (active) {
+        const int rows = min(kAsm32Rows, wk.r1 - base);
+        const float* pa = psi + 8 * bj;
+        const float* pb = psi + 8 * bl;
+        for (int r = slice; r < rows; r += S) {
+          const float4 a0 = *reinterpret_cast<const float4*>(pa + r * ld);
+          const float4 a1 = *reinterpret_cast<const float4*>(pa + r * ld + 4);
+          const float4 b0 = *reinterpret_cast<const float4*>(pb + r * ld);
+          const float4 b1 = *reinterpret_cast<const float4*>(pb + r * ld + 4);
+          const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+          const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+          for (int x = 0; x < 8; ++x)
+#pragma unroll
+            for (int y = 0; y < 8; ++y) acc[x * 8 + y] = fmaf(av[x], bv[y], acc[x * 8 + y]);
+        }
+      }
+      __syncthreads();
+    }
+    // add the S slice sums (FP32) and store the packed upper triangle as doubles
+    float* red = sm32;  // S * U * 64 floats <= 384 * 64
+    if (active) {
+#pragma unroll
+      for (int k = 0; k < 64; ++k) red[(slice * U + u) * 64 + k] = acc[k];
+    }
+    __syncthreads();
+    const int E = M2 * (M2 + 1) / 2;
+    double* out = part + slot_off[wk.slot];
+    for (int e = tid; e < E; e += kAsm32Threads) {
+      int j = 0, rem = e;
+      while (rem >= M2 - j) { rem -= M2 - j; ++j; }
+      const int l = j + rem;
+      const int cb = j >> 3, lb = l >> 3;
+      const int ub = cb * NB - cb * (cb - 1) / 2 + (lb - cb);
+      const int k = (j & 7) * 8 + (l & 7);
+      float s = 0.f;
+      for (int q = 0; q < S; ++q) s += red[(q * U + ub) * 64 + k];
+      out[e] = (double)s;
+    }
+    __syncthreads();
+  }
+}
+
+size_t asm_smem_bytes(bool fp32, int m_max) {
+  const int M2 = m_max + 2;
+  if (fp32) {
+    const int MP = round_up(M2, 8);
+    const size_t tile = sizeof(float) * (size_t)kAsm32Rows * (MP + kPadF);
+    const size_t red = sizeof(float) * (size_t)kAsm32Threads * 64;
+    return tile > red ? tile : red;
+  }
+  return sizeof(double) * (size_t)kAsm64Rows * (M2 + 1);
+}
+
+template <int K>
+static cudaError_t launch64(const Inst* insts, const Work* work, int nwork, int* counter,
+                            const int32_t* lm, const double* tab, double* part,
+                            const int64_t* slot_off, size_t sm, int grid, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_assemble_f64<K>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_assemble_f64<K><<<grid, kAsm64Threads, sm, st>>>(insts, work, nwork, counter, lm, tab, part,
+                                                     slot_off);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(bool fp32, const Inst* insts, const Work* work, int nwork,
+                            int* counter, const int32_t* lm, const double* tab, double* part,
+                            const int64_t* slot_off, int m_max, int num_sms, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  const size_t sm = asm_smem_bytes(fp32, m_max);
+  if (fp32) {
+    e = cudaFuncSetAttribute(k_assemble_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int grid = min(nwork, num_sms);
+    k_assemble_f32<<<grid, kAsm32Threads, sm, st>>>(insts, work, nwork, counter, lm, tab, part,
+                                                    slot_off);
+    return cudaGetLastError();
+  }
+  const int M2 = m_max + 2, E = M2 * (M2 + 1) / 2;
+  const int kneed = (E + kAsm64Threads - 1) / kAsm64Threads;
+  const int grid = min(nwork, num_sms * 2);
+  if (kneed <= 4) return launch64<4>(insts, work, nwork, counter, lm, tab, part, slot_off, sm, grid, st);
+  if (kneed <= 8) return launch64<8>(insts, work, nwork, counter, lm, tab, part, slot_off, sm, grid, st);
+  if (kneed <= 14) return launch64<14>(insts, work, nwork, counter, lm, tab, part, slot_off, sm, grid, st);
+  if (kneed <= 20) return launch64<20>(insts, work, nwork, counter, lm, tab, part, slot_off, sm, grid, st);
+  return launch64<26>(insts, work, nwork, counter, lm, tab, part, slot_off, sm, grid, st);
+}
+
+}  // namespace nys

@@ -1,0 +1,201 @@
+// Internal definitions shared by the sm_103a kernels of the Nystrom LS-SVM ODE solver.
+// (Product code: none of this is used by, or uses, the CPU oracle.)
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nys.h"
+
+namespace nys {
+
+constexpr int kMMax = NYS_M_MAX;          // landmarks per instance
+constexpr int kM1Max = kMMax + 1;         // (omega, b)
+constexpr int kM2Max = kMMax + 2;         // augmented row [kappa; -f_p; r]
+constexpr int kMPMax = 120;               // kM2Max rounded up to a multiple of 8
+
+// Device descriptor of one ODE instance (built on the host by nys_setup).
+struct Inst {
+  int32_t p, n, m, kind;
+  int32_t lset;        // landmark set (shared Nystrom factor)
+  int32_t slot_count;  // row-pass partial slots of this instance
+  int64_t slot_begin;  // first slot (slots of an instance are contiguous)
+  int64_t lm_off;      // landmark grid indices (int32) in lm_idx[]
+  int64_t tab_off;     // kind TABLE: (p+1) x n doubles in tab[]; else -1
+  int64_t y_off;       // Newton: auxiliary y_i (n-1 doubles) in yaux[]
+  double t0, h;        // t_i (0-based i) = t0 + i h
+  double sigma, gamma;
+  double v[2];
+  double c[8];
+  // derived constants (host-computed in FP64)
+  double hs;           // h / sigma
+  double th0, dth;     // LIN: omega*t0 + phi0 and omega*h, both reduced mod 2 pi
+};
+
+// A landmark set: m indices on a grid with spacing h, kernel width sigma.
+struct Lset {
+  int32_t m, m_eff;    // m_eff written by the setup kernel
+  int64_t lm_off;
+  int64_t w_off;       // W: m x m doubles (rows k < m_eff used), row-major
+  double hs;           // h / sigma
+};
+
+// One unit of a row pass: rows i in [r0, r1) (0-based grid index, 1 <= i <= n-1).
+struct Work {
+  int32_t inst, r0, r1, slot;
+};
+
+// Per-instance solve storage offsets (element offsets in the typed arenas).
+struct SolveSlots {
+  int64_t fac;   // factor arena (T): V[2][M1] R[2][2] H1[2][M1] L[N2][N2]
+  int64_t x;     // FP64: x = (omega (m_eff), b), lambda (2)  -- stride xs
+  int64_t z;     // FP64: z = W^T omega (m), b               -- kernel coordinates
+  int64_t cw;    // FP64: C_omega (2 x M1) constraint rows in omega coordinates
+};
+
+// ---------------------------------------------------------------------------
+// float-float helpers (Dekker / Knuth two-sum and FMA-based two-product)
+// ---------------------------------------------------------------------------
+struct ff { float hi, lo; };
+
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+  float s = a + b;
+  float bb = s - a;
+  float e = (a - (s - bb)) + (b - bb);
+  return {s, e};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  ff s = ff_two_sum(a.hi, b.hi);
+  float lo = s.lo + a.lo + b.lo;
+  float hi = s.hi + lo;
+  return {hi, lo - (hi - s.hi)};
+}
+// a (float, exact) times b (ff), added to acc (ff)
+__device__ __forceinline__ ff ff_fma_f(float a, ff b, ff acc) {
+  float p = a * b.hi;
+  float pe = fmaf(a, b.hi, -p);
+  pe = fmaf(a, b.lo, pe);
+  ff s = ff_two_sum(acc.hi, p);
+  float lo = s.lo + pe + acc.lo;
+  float hi = s.hi + lo;
+  return {hi, lo - (hi - s.hi)};
+}
+__device__ __forceinline__ ff ff_from_double(double x) {
+  float hi = (float)x;
+  return {hi, (float)(x - (double)hi)};
+}
+__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+
+// ---------------------------------------------------------------------------
+// exp(-u) for u >= 0 in FP32 with an extra-precise argument (u_hi + u_lo).
+// Cody-Waite range reduction u*log2(e) = n + f with ln2 split in two parts,
+// exp(-r) on |r| <= ln2/2 by its Taylor polynomial to degree 7 (truncation
+// error < 1.2e-8 relative), scaling by 2^n through the exponent field.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float exp_neg_accurate(float u_hi, float u_lo) {
+  const float kLog2e = 1.44269504088896341f;
+  const float kLn2Hi = 0.693145751953125f;        // 12 significant bits: n * kLn2Hi exact
+  const float kLn2Lo = 1.42860682030941723e-06f;  // ln 2 - kLn2Hi
+  if (u_hi > 103.0f) return 0.0f;                 // below the smallest subnormal
+  float nf = rintf(u_hi * kLog2e);
+  float r = fmaf(-nf, kLn2Hi, u_hi);
+  r = fmaf(-nf, kLn2Lo, r);
+  r = r + u_lo;                                   // exp(-u) = 2^-n exp(-r)
+  float x = -r;
+  // Horner form of sum_{k=0..7} x^k / k!
+  float q = 1.0f / 5040.0f;
+  q = fmaf(q, x, 1.0f / 720.0f);
+  q = fmaf(q, x, 1.0f / 120.0f);
+  q = fmaf(q, x, 1.0f / 24.0f);
+  q = fmaf(q, x, 1.0f / 6.0f);
+  q = fmaf(q, x, 0.5f);
+  q = fmaf(q, x, 1.0f);
+  q = fmaf(q, x, 1.0f);
+  // times 2^-n; n in [0, 149]: split the scale to stay in the normal range
+  int n = (int)nf;
+  int n1 = n >> 1, n2 = n - n1;
+  float s1 = __int_as_float((127 - n1) << 23);
+  float s2 = __int_as_float((127 - n2) << 23);
+  return (q * s1) * s2;
+}
+
+// Fast exp(-u) on the MUFU unit (approximate; used where the refinement
+// corrects the result).
+__device__ __forceinline__ float exp_neg_fast(float u) {
+  return exp2f(-u * 1.44269504088896341f);
+}
+
+// ---------------------------------------------------------------------------
+// Per-row ODE operator coefficients.  For row i:
+//   kappa_j = k^(p) - sum_k f_k k^(p-k) = e_j (A0 + A1 x_j + A2 u_j),
+//   x_j = (t_i - s_j)/sigma, u_j = x_j^2, e_j = exp(-u_j),
+// because k' = -2 x/sigma e and k'' = (4u - 2)/sigma^2 e (Section 3).
+//   p = 2: A0 = -f_2 - 2/sigma^2, A1 = 2 f_1/sigma, A2 = 4/sigma^2
+//   p = 1: A0 = -f_1,             A1 = -2/sigma,   A2 = 0
+// w1 = -f_p(t_i) (coefficient of b), rr = r(t_i).
+// ---------------------------------------------------------------------------
+struct RowCoef { double A0, A1, A2, w1, rr; };
+
+__device__ __forceinline__ void coef_f(const Inst& I, const double* tab, int i, double& f1,
+                                       double& f2, double& rr) {
+  if (I.kind == NYS_COEF_TABLE) {
+    const double* T = tab + I.tab_off;
+    f1 = T[i];
+    f2 = (I.p == 2) ? T[(int64_t)I.n + i] : 0.0;
+    rr = T[(int64_t)I.p * I.n + i];
+  } else {  // LIN: f_k = -a_k, r = c sin(omega t + phi0)
+    f1 = -I.c[0];
+    f2 = (I.p == 2) ? -I.c[1] : 0.0;
+    rr = 0.0;  // filled by the caller's own sine evaluation
+  }
+}
+
+__device__ __forceinline__ RowCoef row_coef_from_f(const Inst& I, double f1, double f2, double rr) {
+  RowCoef R;
+  const double is = 1.0 / I.sigma, is2 = is * is;
+  if (I.p == 2) {
+    R.A0 = -f2 - 2.0 * is2;
+    R.A1 = 2.0 * f1 * is;
+    R.A2 = 4.0 * is2;
+    R.w1 = -f2;
+  } else {
+    R.A0 = -f1;
+    R.A1 = -2.0 * is;
+    R.A2 = 0.0;
+    R.w1 = -f1;
+  }
+  R.rr = rr;
+  return R;
+}
+
+// r(t_i) = c sin(theta_i), theta_i = th0 + i dth (LIN kind), in FP64.
+__device__ __forceinline__ double lin_rhs_f64(const Inst& I, int i) {
+  double t = I.t0 + (double)i * I.h;
+  return I.c[2] * sin(I.c[3] * t + I.c[4]);
+}
+
+// Same in FP32 with a float-float argument: theta_i = th0 + i*dth with th0 and
+// dth reduced mod 2 pi on the host, the product i*dth split exactly by FMA and
+// the sum reduced again (Cody-Waite with 2 pi in two parts).  The result is
+// c sin(theta_i) to about one FP32 ulp.
+__device__ __forceinline__ float lin_rhs_ff(const Inst& I, int i) {
+  const float k2PiHi = 6.28318548202514648f;
+  const float k2PiLo = -1.74845553e-07f;
+  ff dth = ff_from_double(I.dth);
+  ff th0 = ff_from_double(I.th0);
+  float fi = (float)i;
+  float p = fi * dth.hi;
+  float pe = fmaf(fi, dth.hi, -p);
+  pe = fmaf(fi, dth.lo, pe);
+  ff th = ff_add(th0, ff{p, pe});
+  float k = rintf(th.hi * 0.159154943091895336f);
+  float a = fmaf(-k, k2PiHi, th.hi);
+  float b = fmaf(-k, k2PiLo, th.lo);
+  ff r = ff_two_sum(a, b);
+  float s, cth;
+  sincosf(r.hi, &s, &cth);
+  return (float)I.c[2] * fmaf(cth, r.lo, s);
+}
+
+__host__ __device__ __forceinline__ int round_up(int x, int a) { return (x + a - 1) / a * a; }
+
+}  // namespace nys

@@ -1,0 +1,185 @@
+// Nystrom setup (Appendix A.2, Eq. 10 and eq32): landmark kernel Omega_mm,
+// symmetric eigendecomposition in FP64, feature factor W = Lambda^{-1/2} U^T
+// with eigenpairs below tau * lambda_max dropped.
+//
+// One CTA per distinct landmark set.  Eigensolver: parallel cyclic Jacobi
+// (Golub & Van Loan, Matrix Computations, Sec. 8.5) with the round-robin
+// ("chess tournament") ordering, so the m/2 rotations of a round touch
+// disjoint row/column pairs and run concurrently.  A and the rotation
+// accumulator V live in shared memory (2 m (m+1) doubles, <= 203 KB).
+#include "nys_internal.cuh"
+
+namespace nys {
+
+constexpr int kSetupThreads = 256;
+constexpr int kMaxSweeps = 40;
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) red[0] = s;
+  }
+  __syncthreads();
+  s = red[0];
+  __syncthreads();
+  return s;
+}
+
+__global__ void __launch_bounds__(kSetupThreads)
+k_setup_eig(Lset* lsets, const int32_t* __restrict__ nl_dev, const int32_t* __restrict__ lm_idx,
+            double* __restrict__ W_all, float* __restrict__ W32_all, double* __restrict__ lam_all,
+            double tau) {
+  // the grid covers the capacity; the number of distinct sets is read on the
+  // device so that a captured graph stays valid when it changes
+  const int L = blockIdx.x;
+  if (L >= *nl_dev) return;
+  const Lset S = lsets[L];
+  const int m = S.m;
+  const int N = m + (m & 1);  // even player count; index m (if present) is a bye
+  const int ld = m + 1;
+  extern __shared__ double sm[];
+  double* A = sm;
+  double* V = A + m * ld;
+  double* cs = V + m * ld;                 // N/2 cosines then N/2 sines
+  double* red = cs + N;                    // 32
+  int* pos = reinterpret_cast<int*>(red + 32);   // N
+  int* perm = pos + N;                     // m
+  int* idx = perm + m;                     // m
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  for (int j = tid; j < m; j += nt) idx[j] = lm_idx[S.lm_off + j];
+  for (int k = tid; k < N; k += nt) pos[k] = k;
+  __syncthreads();
+  for (int e = tid; e < m * m; e += nt) {
+    const int j = e / m, l = e % m;
+    const double d = (double)(idx[j] - idx[l]) * S.hs;
+    A[j * ld + l] = exp(-d * d);
+    V[j * ld + l] = (j == l) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+
+  const int half = N / 2;
+  for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int e = tid; e < m * m; e += nt) {
+      const int j = e / m, l = e % m;
+      const double a = A[j * ld + l];
+      tot += a * a;
+      if (j != l) off += a * a;
+    }
+    off = block_sum(off, red);
+    tot = block_sum(tot, red);
+    if (off <= 1e-30 * tot) break;
+
+    for (int round = 0; round < N - 1; ++round) {
+      // rotation angles of the m/2 disjoint pairs (symmetric Schur decomposition)
+      for (int k = tid; k < half; k += nt) {
+        int p = pos[k], q = pos[N - 1 - k];
+        if (p > q) { int t = p; p = q; q = t; }
+        double c = 1.0, s = 0.0;
+        if (q < m) {
+          const double apq = A[p * ld + q];
+          if (fabs(apq) > 1e-300) {
+            const double tau_ = (A[q * ld + q] - A[p * ld + p]) / (2.0 * apq);
+            const double t = (tau_ >= 0.0 ? 1.0 : -1.0) / (fabs(tau_) + sqrt(1.0 + tau_ * tau_));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+          }
+        }
+        cs[k] = c;
+        cs[half + k] = s;
+      }
+      __syncthreads();
+      // A <- A J and V <- V J : columns p, q of every row
+      for (int e = tid; e < half * m; e += nt) {
+        const int k = e / m, i = e % m;
+        int p = pos[k], q = pos[N - 1 - k];
+        if (p > q) { int t = p; p = q; q = t; }
+        if (q >= m) continue;
+        const double c = cs[k], s = cs[half + k];
+        const double aip = A[i * ld + p], aiq = A[i * ld + q];
+        A[i * ld + p] = c * aip - s * aiq;
+        A[i * ld + q] = s * aip + c * aiq;
+        const double vip = V[i * ld + p], viq = V[i * ld + q];
+        V[i * ld + p] = c * vip - s * viq;
+        V[i * ld + q] = s * vip + c * viq;
+      }
+      __syncthreads();
+      // A <- J^T A : rows p, q
+      for (int e = tid; e < half * m; e += nt) {
+        const int k = e / m, j = e % m;
+        int p = pos[k], q = pos[N - 1 - k];
+        if (p > q) { int t = p; p = q; q = t; }
+        if (q >= m) continue;
+        const double c = cs[k], s = cs[half + k];
+        const double apj = A[p * ld + j], aqj = A[q * ld + j];
+        A[p * ld + j] = c * apj - s * aqj;
+        A[q * ld + j] = s * apj + c * aqj;
+      }
+      __syncthreads();
+      if (tid == 0) {  // round-robin: keep pos[0], rotate the rest
+        const int last = pos[N - 1];
+        for (int k = N - 1; k > 1; --k) pos[k] = pos[k - 1];
+        pos[1] = last;
+      }
+      __syncthreads();
+    }
+  }
+
+  // sort eigenvalues descending, keep lambda > tau * lambda_max
+  if (tid == 0) {
+    for (int k = 0; k < m; ++k) perm[k] = k;
+    for (int a = 0; a < m; ++a) {
+      int best = a;
+      for (int b = a + 1; b < m; ++b)
+        if (A[perm[b] * ld + perm[b]] > A[perm[best] * ld + perm[best]]) best = b;
+      const int t = perm[a]; perm[a] = perm[best]; perm[best] = t;
+    }
+    const double lmax = A[perm[0] * ld + perm[0]];
+    int me = 0;
+    while (me < m && A[perm[me] * ld + perm[me]] > tau * lmax) ++me;
+    lsets[L].m_eff = me;
+    red[0] = (double)me;
+  }
+  __syncthreads();
+  const int me = (int)red[0];
+  double* Wl = W_all + S.w_off;
+  float* W32l = W32_all + S.w_off;
+  for (int e = tid; e < m * m; e += nt) {
+    const int k = e / m, j = e % m;
+    double w = 0.0;
+    if (k < me) {
+      const int c = perm[k];
+      w = V[j * ld + c] / sqrt(A[c * ld + c]);
+    }
+    Wl[e] = w;
+    W32l[e] = (float)w;
+  }
+  for (int k = tid; k < m; k += nt) lam_all[(int64_t)L * kMMax + k] = A[perm[k] * ld + perm[k]];
+}
+
+size_t setup_smem_bytes(int m) {
+  const int N = m + (m & 1);
+  return sizeof(double) * (2 * (size_t)m * (m + 1) + N + 32) + sizeof(int) * (N + 2 * m);
+}
+
+cudaError_t launch_setup(Lset* lsets, const int32_t* nl_dev, int capacity, const int32_t* lm_idx,
+                         double* W, float* W32, double* lam, double tau, int m_max,
+                         cudaStream_t st) {
+  if (capacity == 0) return cudaSuccess;
+  const size_t sm = setup_smem_bytes(m_max);
+  cudaError_t e = cudaFuncSetAttribute(k_setup_eig, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
+  if (e != cudaSuccess) return e;
+  k_setup_eig<<<capacity, kSetupThreads, sm, st>>>(lsets, nl_dev, lm_idx, W, W32, lam, tau);
+  return cudaGetLastError();
+}
+
+}  // namespace nys

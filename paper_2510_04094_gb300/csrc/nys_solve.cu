@@ -1,0 +1,671 @@
+// Per-instance solve of Lemma 1's system (Section 3.1) and, for the mixed
+// path, residual refinement.
+//
+// Lemma 1 as a constrained least-squares problem in (omega, b):
+//     [ H  C^T ] [x     ]   [g]     H = D + gamma B G_kk B^T  (D = diag(1_m, 0))
+//     [ C  0   ] [lambda] = [v],    g = gamma B g_k,  B = blkdiag(W, 1)
+// with G_kk, g_k the kernel-coordinate sums of the fused row pass and
+// C = [phi(t_1) 1; phi'(t_1) 0] the initial-condition rows (Lemma 1 sign
+// convention: H x + C^T lambda = g).  Solved by the null-space method:
+// Householder reflectors Q with Q^T C^T = [R; 0], y = Q^T x, y_1 = R^{-T} v,
+// Cholesky of the projected block H'_22 for y_2, lambda from the first p rows.
+// The KKT matrix itself mixes scales gamma n |kappa|^2 and 1 (cond ~ 1e27);
+// the projected block has the conditioning of the fit (~1e2-1e4 here).
+//
+// T = double: the plain FP64 path.  T = float: the factor of the mixed path;
+// its error is removed by refinement passes whose residuals are computed
+// from the definition of the problem with FP64-accurate features.
+#include "nys_internal.cuh"
+
+namespace nys {
+
+constexpr int kSolveThreads = 256;
+
+template <typename T>
+struct FacView {  // factor storage of one instance in the T arena
+  T* V;    // 2 x M1 Householder vectors
+  T* beta; // 2
+  T* R;    // 4: R00, R01, R11
+  T* H1;   // 2 x M1: first p rows of Q^T H Q
+  T* L;    // N2 x N2 lower Cholesky factor (row-major, ld N2)
+};
+template <typename T>
+__device__ __forceinline__ FacView<T> fac_view(T* base, int M1) {
+  FacView<T> f;
+  f.V = base;
+  f.beta = base + 2 * M1;
+  f.R = f.beta + 2;
+  f.H1 = f.R + 4;
+  f.L = f.H1 + 2 * M1;
+  return f;
+}
+int64_t fac_elems(int m_max) {
+  const int M1 = m_max + 1;
+  return 2 * M1 + 2 + 4 + 2 * M1 + (int64_t)M1 * M1;
+}
+
+// ---- CTA helpers -----------------------------------------------------------
+template <typename T>
+__device__ T cta_dot(const T* a, const T* b, int n, T* red) {
+  T s = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += a[i] * b[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    red[32] = t;
+  }
+  __syncthreads();
+  const T r = red[32];
+  __syncthreads();
+  return r;
+}
+
+// Householder vector of x[0..n): v with v[0] = x0 + sign(x0)|x|, beta = 2/(v^T v),
+// (I - beta v v^T) x = -sign(x0)|x| e_0.  Returns the diagonal value.
+template <typename T>
+__device__ T house(const T* x, T* v, int n, T* beta, T* red) {
+  const T nrm2 = cta_dot(x, x, n, red);
+  const T nrm = sqrt(nrm2);
+  const T x0 = x[0];
+  const T sg = (x0 >= T(0)) ? T(1) : T(-1);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = (i == 0) ? x0 + sg * nrm : x[i];
+  __syncthreads();
+  const T vv = nrm2 + T(2) * sg * nrm * x0 + nrm2;  // |v|^2 = 2|x|^2 + 2|x0||x|
+  if (threadIdx.x == 0) *beta = (vv > T(0)) ? T(2) / vv : T(0);
+  __syncthreads();
+  return -sg * nrm;
+}
+
+// A <- (I - b v v^T) A (I - b v v^T) for symmetric A (n x n, ld), w scratch n.
+template <typename T>
+__device__ void apply_house_sym(T* A, int ld, int n, const T* v, T b, T* w, T* red) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    T s = 0;
+    for (int j = 0; j < n; ++j) s += A[i * ld + j] * v[j];
+    w[i] = b * s;
+  }
+  __syncthreads();
+  const T k = T(0.5) * b * cta_dot(v, w, n, red);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) w[i] -= k * v[i];
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e - (e / n) * n;
+    A[i * ld + j] -= v[i] * w[j] + w[i] * v[j];
+  }
+  __syncthreads();
+}
+
+// x <- (I - b v v^T) x
+template <typename T>
+__device__ void apply_house_vec(T* x, int n, const T* v, T b, T* red) {
+  const T s = b * cta_dot(v, x, n, red);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] -= s * v[i];
+  __syncthreads();
+}
+
+// In-place lower Cholesky of A (n x n, ld).  Returns false on a non-positive pivot.
+template <typename T>
+__device__ bool cta_cholesky(T* A, int ld, int n, int* flag) {
+  if (threadIdx.x == 0) *flag = 0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      const T d = A[k * ld + k];
+      if (!(d > T(0))) { *flag = 1; A[k * ld + k] = T(1); }
+      else A[k * ld + k] = sqrt(d);
+    }
+    __syncthreads();
+    const T lkk = A[k * ld + k];
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[i * ld + k] /= lkk;
+    __syncthreads();
+    const int R = n - k - 1;
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+      const int i = k + 1 + e / R, j = k + 1 + e % R;
+      if (j <= i) A[i * ld + j] -= A[i * ld + k] * A[j * ld + k];
+    }
+    __syncthreads();
+  }
+  return *flag == 0;
+}
+
+// Solve L L^T y = b in place (b overwritten), L lower (n x n, ld).
+template <typename T>
+__device__ void cta_chol_solve(const T* L, int ld, int n, T* b) {
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) b[k] /= L[k * ld + k];
+    __syncthreads();
+    const T yk = b[k];
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) b[i] -= L[i * ld + k] * yk;
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    if (threadIdx.x == 0) b[k] /= L[k * ld + k];
+    __syncthreads();
+    const T yk = b[k];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) b[i] -= L[k * ld + i] * yk;
+    __syncthreads();
+  }
+}
+
+// Apply the stored factor: given residuals (h: M1, cr: p) return the KKT
+// solution (dx: M1, dl: p) of [H C^T; C 0][dx; dl] = [h; cr].  All arrays in
+// shared memory; h is overwritten.
+template <typename T>
+__device__ void kkt_apply(const FacView<T>& F, int M1, int p, T* h, const T* cr, T* dx, T* dl,
+                          T* red) {
+  // h' = Q^T h = H_p .. H_1 h
+  for (int k = 0; k < p; ++k) apply_house_vec(h, M1, F.V + k * M1, F.beta[k], red);
+  // y1 = R^{-T} cr
+  __shared__ T y1s[2];
+  if (threadIdx.x == 0) {
+    y1s[0] = cr[0] / F.R[0];
+    if (p == 2) y1s[1] = (cr[1] - F.R[1] * y1s[0]) / F.R[2];
+  }
+  __syncthreads();
+  const int N2 = M1 - p;
+  // rhs2 = h'[p:] - H'[p:, :p] y1   (H'[p:, :p] = H1[:, p:]^T)
+  for (int i = threadIdx.x; i < N2; i += blockDim.x) {
+    T s = h[p + i];
+    for (int k = 0; k < p; ++k) s -= F.H1[k * M1 + p + i] * y1s[k];
+    dx[p + i] = s;
+  }
+  __syncthreads();
+  cta_chol_solve(F.L, N2, N2, dx + p);
+  // lambda: R lam = h'[:p] - H'[:p, :] y
+  if (threadIdx.x < 2 && threadIdx.x < p) dx[threadIdx.x] = y1s[threadIdx.x];
+  __syncthreads();
+  T r0 = cta_dot(F.H1, dx, M1, red);
+  T r1 = (p == 2) ? cta_dot(F.H1 + M1, dx, M1, red) : T(0);
+  if (threadIdx.x == 0) {
+    r0 = h[0] - r0;
+    r1 = (p == 2) ? h[1] - r1 : T(0);
+    if (p == 2) {
+      dl[1] = r1 / F.R[2];
+      dl[0] = (r0 - F.R[1] * dl[1]) / F.R[0];
+    } else {
+      dl[0] = r0 / F.R[0];
+    }
+  }
+  __syncthreads();
+  // dx = Q y = H_1 .. H_p y
+  for (int k = p - 1; k >= 0; --k) apply_house_vec(dx, M1, F.V + k * M1, F.beta[k], red);
+}
+
+// ---------------------------------------------------------------------------
+// K3: form H, g, C; factor; solve.  One CTA per instance.
+// Shared memory: G (m+1) x (m+2) [T], H M1 x M1 [T], Y-block 8 x m [T], vectors.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kSolveThreads)
+k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
+        const double* __restrict__ W_all, const T* __restrict__ Wt_all,
+        const double* __restrict__ part,
+        const int64_t* __restrict__ slot_off, const int32_t* __restrict__ lm_idx,
+        T* __restrict__ fac_all, int64_t facs, double* __restrict__ xs, double* __restrict__ zs,
+        double* __restrict__ cws, int XS, int ZS, int M1S, const int32_t* __restrict__ st_init,
+        int32_t* __restrict__ st_all, double gamma_scale) {
+  const int b = blockIdx.x;
+  if (st_init[b] != NYS_OK) {
+    if (threadIdx.x == 0) st_all[b] = st_init[b];
+    return;
+  }
+  const Inst I = insts[b];
+  const Lset LS = lsets[I.lset];
+  const int m = I.m, p = I.p, me = LS.m_eff;
+  const int M1 = me + 1, M2 = m + 2, N2 = M1 - p;
+  const int ldg = m + 2, ldh = M1;
+  const double* W = W_all + LS.w_off;  // m x m, rows < me
+  const T* Wt = Wt_all + LS.w_off;     // same in T
+  const double gamma = I.gamma * gamma_scale;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* Gs = reinterpret_cast<T*>(smraw);             // (m+1) x (m+2)
+  T* Hs = Gs + (m + 1) * ldg;                        // M1 x M1
+  T* Yb = Hs + M1 * ldh;                             // 8 x m
+  T* vec = Yb + 8 * m;                               // misc vectors
+  T* g = vec;                                        // M1
+  T* hb = g + M1;                                    // me
+  T* Vh = hb + M1;                                   // 2 x M1 Householder
+  T* c2 = Vh + 2 * M1;                               // M1 scratch
+  T* w = c2 + M1;                                    // M1 scratch
+  T* y = w + M1;                                     // M1
+  T* red = y + M1;                                   // 40
+  __shared__ int s_flag;
+  __shared__ T s_beta[2], s_R[4];
+  __shared__ double s_c[2][kM1Max];
+
+  // 1. sum the partial Grams (packed upper over M2) -> G (symmetric, full)
+  const int E = M2 * (M2 + 1) / 2;
+  for (int e = threadIdx.x; e < E; e += blockDim.x) {
+    int j = 0, rem = e;
+    while (rem >= M2 - j) { rem -= M2 - j; ++j; }
+    const int l = j + rem;
+    if (j > m) continue;  // the (r, r) entry is not needed
+    double s = 0.0;
+    for (int q = 0; q < I.slot_count; ++q) s += part[slot_off[I.slot_begin + q] + e];
+    Gs[j * ldg + l] = (T)s;
+    if (l <= m) Gs[l * ldg + j] = (T)s;
+  }
+  __syncthreads();
+  // 2. small pieces: H_wb = W G_kb, g_w = W g_k, H_bb, g_b
+  for (int k = threadIdx.x; k < me; k += blockDim.x) {
+    T s1 = 0, s2 = 0;
+    for (int j = 0; j < m; ++j) {
+      const T wkj = Wt[k * m + j];
+      s1 += wkj * Gs[j * ldg + m];
+      s2 += wkj * Gs[j * ldg + m + 1];
+    }
+    hb[k] = s1;
+    g[k] = (T)gamma * s2;
+  }
+  if (threadIdx.x == 0) g[me] = (T)gamma * Gs[m * ldg + m + 1];
+  __syncthreads();
+  // 3. H_ww = gamma W G_kk W^T + I, in blocks of 8 rows of Y = W G_kk
+  for (int k0 = 0; k0 < me; k0 += 8) {
+    const int kb = min(8, me - k0);
+    for (int e = threadIdx.x; e < kb * m; e += blockDim.x) {
+      const int kk = e / m, l = e - kk * m;
+      T s = 0;
+      for (int j = 0; j < m; ++j) s += Wt[(k0 + kk) * m + j] * Gs[j * ldg + l];
+      Yb[kk * m + l] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kb * me; e += blockDim.x) {
+      const int kk = e / me, l = e - kk * me;
+      T s = 0;
+      for (int j = 0; j < m; ++j) s += Yb[kk * m + j] * Wt[l * m + j];
+      Hs[(k0 + kk) * ldh + l] = (T)gamma * s + ((k0 + kk) == l ? T(1) : T(0));
+    }
+    __syncthreads();
+  }
+  for (int k = threadIdx.x; k < me; k += blockDim.x) {
+    Hs[k * ldh + me] = (T)gamma * hb[k];
+    Hs[me * ldh + k] = (T)gamma * hb[k];
+  }
+  if (threadIdx.x == 0) Hs[me * ldh + me] = (T)gamma * Gs[m * ldg + m];
+  // 4. constraint rows in omega coordinates (FP64): c_1 = [W k(t_1); 1], c_2 = [W k'(t_1); 0]
+  for (int k = threadIdx.x; k < M1; k += blockDim.x) {
+    double s0 = 0.0, s1 = 0.0;
+    if (k < me) {
+      for (int j = 0; j < m; ++j) {
+        const double x = (double)(0 - lm_idx[I.lm_off + j]) * I.hs;
+        const double e = exp(-x * x);
+        s0 += W[k * m + j] * e;
+        s1 += W[k * m + j] * (-2.0 * x / I.sigma) * e;
+      }
+    } else {
+      s0 = 1.0;
+      s1 = 0.0;
+    }
+    s_c[0][k] = s0;
+    s_c[1][k] = s1;
+    cws[(int64_t)b * 2 * M1S + k] = s0;
+    cws[(int64_t)b * 2 * M1S + M1S + k] = s1;
+  }
+  __syncthreads();
+  // 5. Householder reflectors of C^T (M1 x p)
+  for (int k = threadIdx.x; k < M1; k += blockDim.x) {
+    w[k] = (T)s_c[0][k];
+    c2[k] = (T)s_c[1][k];
+  }
+  __syncthreads();
+  {
+    T bt;
+    const T r00 = house(w, Vh, M1, &s_beta[0], red);
+    bt = s_beta[0];
+    if (threadIdx.x == 0) s_R[0] = r00;
+    __syncthreads();
+    if (p == 2) {
+      apply_house_vec(c2, M1, Vh, bt, red);
+      if (threadIdx.x == 0) s_R[1] = c2[0];
+      for (int k = threadIdx.x; k < M1; k += blockDim.x) Vh[M1 + k] = T(0);
+      __syncthreads();
+      const T r11 = house(c2 + 1, Vh + M1 + 1, M1 - 1, &s_beta[1], red);
+      if (threadIdx.x == 0) s_R[2] = r11;
+      __syncthreads();
+    }
+  }
+  // 6. H' = Q^T H Q, g' = Q^T g
+  // (reflector k has zeros in its first k entries; apply it to the full matrix
+  //  so the off-diagonal rows/columns are transformed too)
+  for (int k = 0; k < p; ++k) {
+    apply_house_sym(Hs, ldh, M1, Vh + k * M1, s_beta[k], w, red);
+    apply_house_vec(g, M1, Vh + k * M1, s_beta[k], red);
+  }
+  // store the first p rows of H' before the Cholesky overwrites the block
+  T* facb = fac_all + (int64_t)b * facs;
+  FacView<T> F = fac_view(facb, M1);
+  for (int e = threadIdx.x; e < p * M1; e += blockDim.x) {
+    const int k = e / M1, j = e - k * M1;
+    F.H1[k * M1 + j] = Hs[k * ldh + j];
+    F.V[k * M1 + j] = Vh[k * M1 + j];
+  }
+  if (threadIdx.x < 2) F.beta[threadIdx.x] = (threadIdx.x < p) ? s_beta[threadIdx.x] : T(0);
+  if (threadIdx.x < 3) F.R[threadIdx.x] = s_R[threadIdx.x];
+  // 7. y1 = R^{-T} v ; rhs2 = g'[p:] - H'[p:, :p] y1
+  if (threadIdx.x == 0) {
+    y[0] = (T)I.v[0] / s_R[0];
+    if (p == 2) y[1] = ((T)I.v[1] - s_R[1] * y[0]) / s_R[2];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < N2; i += blockDim.x) {
+    T s = g[p + i];
+    for (int k = 0; k < p; ++k) s -= Hs[(p + i) * ldh + k] * y[k];
+    y[p + i] = s;
+  }
+  __syncthreads();
+  // 8. Cholesky of H'_22 and solve
+  T* A22 = Hs + p * ldh + p;
+  const bool ok = cta_cholesky(A22, ldh, N2, &s_flag);
+  cta_chol_solve(A22, ldh, N2, y + p);
+  for (int e = threadIdx.x; e < N2 * N2; e += blockDim.x) {
+    const int i = e / N2, j = e - i * N2;
+    F.L[i * N2 + j] = (j <= i) ? A22[i * ldh + j] : T(0);
+  }
+  // 9. lambda = R^{-1}(g'[:p] - H'[:p, :] y)
+  const T q0 = cta_dot(F.H1, y, M1, red);
+  const T q1 = (p == 2) ? cta_dot(F.H1 + M1, y, M1, red) : T(0);
+  double lam0 = 0.0, lam1 = 0.0;
+  if (p == 2) {
+    lam1 = (double)((g[1] - q1) / s_R[2]);
+    lam0 = (double)((g[0] - q0 - s_R[1] * (T)lam1) / s_R[0]);
+  } else {
+    lam0 = (double)((g[0] - q0) / s_R[0]);
+  }
+  // 10. x = Q y
+  for (int k = p - 1; k >= 0; --k) apply_house_vec(y, M1, Vh + k * M1, s_beta[k], red);
+  double* xb = xs + (int64_t)b * XS;
+  for (int k = threadIdx.x; k < XS; k += blockDim.x) {
+    double val = 0.0;
+    if (k < me) val = (double)y[k];
+    else if (k == XS - 3) val = (double)y[me];
+    else if (k == XS - 2) val = lam0;
+    else if (k == XS - 1) val = (p == 2) ? lam1 : 0.0;
+    xb[k] = val;
+  }
+  __syncthreads();
+  // 11. kernel coordinates z = W^T omega, b
+  double* zb = zs + (int64_t)b * ZS;
+  for (int j = threadIdx.x; j <= m; j += blockDim.x) {
+    double s = 0.0;
+    if (j < m) {
+      for (int k = 0; k < me; ++k) s += W[k * m + j] * xb[k];
+    } else {
+      s = xb[XS - 3];
+    }
+    zb[j] = s;
+  }
+  if (threadIdx.x == 0) {
+    int st = ok ? NYS_OK : NYS_ENOTSPD;
+    if (ok && !(isfinite(lam0) && isfinite(lam1) && isfinite((double)y[me]))) st = NYS_ENONFINITE;
+    st_all[b] = st;
+  }
+}
+
+size_t solve_smem_bytes(bool fp32, int m_max) {
+  const int m = m_max, M1 = m + 1;
+  const size_t es = fp32 ? sizeof(float) : sizeof(double);
+  return es * ((size_t)(m + 1) * (m + 2) + (size_t)M1 * M1 + 8 * m + 8 * M1 + 40);
+}
+
+// ---------------------------------------------------------------------------
+// K4a: refinement row pass (mixed path).  For each row, FP64-accurate
+// features (float-float argument, exp_neg_accurate, float-float operator
+// coefficients), the residual s_i = r_i - kappa~_i^T z~ in float-float, and
+// the accumulation acc_j += kappa~_ij s_i.  z~ = (W^T omega, b).
+// ---------------------------------------------------------------------------
+constexpr int kRefThreads = 256;
+constexpr int kRefRows = 256;
+
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const float hi = p + e;
+  return {hi, e - (hi - p)};
+}
+
+__global__ void __launch_bounds__(kRefThreads)
+k_refine_rows(const Inst* __restrict__ insts, const Work* __restrict__ work, int nwork,
+              int* __restrict__ counter, const int32_t* __restrict__ lm_idx,
+              const double* __restrict__ tab, const double* __restrict__ zs, int ZS,
+              double* __restrict__ part, const int64_t* __restrict__ slot_off,
+              const int32_t* __restrict__ st_all) {
+  extern __shared__ __align__(16) float smr[];
+  __shared__ int s_item;
+  __shared__ int s_idx[kMMax];
+  __shared__ float s_zh[kM1Max], s_zl[kM1Max];
+  __shared__ float s_s[kRefRows];
+  __shared__ float s_rc[kRefRows * 8];
+  __shared__ float s_rlo[kRefRows];
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int wi = s_item;
+    if (wi >= nwork) break;
+    const Work wk = work[wi];
+    const Inst I = insts[wk.inst];
+    const int m = I.m, M1 = m + 1;
+    const int ld = M1 | 1;  // odd stride: row-per-thread reads are conflict-free
+    for (int j = tid; j < m; j += kRefThreads) s_idx[j] = lm_idx[I.lm_off + j];
+    for (int j = tid; j <= m; j += kRefThreads) {
+      const ff z = ff_from_double(zs[(int64_t)wk.inst * ZS + j]);
+      s_zh[j] = z.hi;
+      s_zl[j] = z.lo;
+    }
+    // per-instance constants in float-float
+    const ff hs = ff_from_double(I.hs);
+    const int S = max(1, kRefThreads / M1);
+    const int slice = tid / M1, col = tid - slice * M1;
+    const bool cactive = slice < S;
+    float acc = 0.f;
+    __syncthreads();
+    const bool skip = (st_all[wk.inst] != NYS_OK);
+    float* psi = smr;
+    for (int base = wk.r0; base < wk.r1 && !skip; base += kRefRows) {
+      const int rows = min(kRefRows, wk.r1 - base);
+      // per-row operator coefficients in float-float, r_i, w1
+      for (int r = tid; r < rows; r += kRefThreads) {
+        const int i = base + r;
+        double f1, f2, rr;
+        coef_f(I, tab, i, f1, f2, rr);
+        const RowCoef R = row_coef_from_f(I, f1, f2, rr);
+        const ff a0 = ff_from_double(R.A0), a1 = ff_from_double(R.A1), a2 = ff_from_double(R.A2);
+        const ff rv = (I.kind == NYS_COEF_LIN) ? ff{lin_rhs_ff(I, i), 0.f} : ff_from_double(rr);
+        float* rc = s_rc + r * 8;
+        rc[0] = a0.hi; rc[1] = a0.lo; rc[2] = a1.hi; rc[3] = a1.lo;
+        rc[4] = a2.hi; rc[5] = a2.lo; rc[6] = (float)R.w1; rc[7] = rv.hi;
+        s_rlo[r] = rv.lo;
+      }
+      __syncthreads();
+      // FP64-accurate features of the tile
+      for (int e = tid; e < rows * M1; e += kRefThreads) {
+        const int r = e / M1, j = e - r * M1;
+        const int i = base + r;
+        const float* rc = s_rc + r * 8;
+        float val;
+        if (j < m) {
+          const float kf = (float)(i - s_idx[j]);
+          // x = k hs and u = x^2 in float-float
+          const float xh = kf * hs.hi;
+          const float xl = fmaf(kf, hs.hi, -xh) + kf * hs.lo;
+          const float uh = xh * xh;
+          const float ul = fmaf(xh, xh, -uh) + 2.f * xh * xl;
+          const float ex = exp_neg_accurate(uh, ul);
+          ff P = ff{rc[0], rc[1]};
+          P = ff_add(P, ff_mul(ff{rc[2], rc[3]}, ff{xh, xl}));
+          P = ff_add(P, ff_mul(ff{rc[4], rc[5]}, ff{uh, ul}));
+          val = ex * (P.hi + P.lo);
+        } else {
+          val = rc[6];
+        }
+        psi[r * ld + j] = val;
+      }
+      __syncthreads();
+      // residual s_i = r_i - kappa~_i^T z~ in float-float, one row per thread
+      for (int r = tid; r < rows; r += kRefThreads) {
+        ff acc_s = {s_rc[r * 8 + 7], s_rlo[r]};
+        for (int j = 0; j <= m; ++j) {
+          const float kv = -psi[r * ld + j];
+          acc_s = ff_fma_f(kv, ff{s_zh[j], s_zl[j]}, acc_s);
+        }
+        s_s[r] = acc_s.hi + acc_s.lo;
+      }
+      __syncthreads();
+      if (cactive) {
+        for (int r = slice; r < rows; r += S) acc = fmaf(psi[r * ld + col], s_s[r], acc);
+      }
+      __syncthreads();
+    }
+    // sum slices, write the partial (M1 doubles)
+    float* red = smr;
+    if (cactive) red[slice * M1 + col] = acc;
+    __syncthreads();
+    double* out = part + slot_off[wk.slot];
+    for (int j = tid; j < M1; j += kRefThreads) {
+      float s = 0.f;
+      for (int q = 0; q < S; ++q) s += red[q * M1 + j];
+      out[j] = skip ? 0.0 : (double)s;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K4b: refinement update per instance (FP64 residual equations, T factor):
+//   h = gamma B acc - D x - C^T lambda,  c = v - C x,  [dx; dl] = K~^{-1} [h; c]
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kSolveThreads)
+k_refine_update(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
+                const double* __restrict__ W_all, const double* __restrict__ part,
+                const int64_t* __restrict__ slot_off, const T* __restrict__ fac_all, int64_t facs,
+                double* __restrict__ xs, double* __restrict__ zs, const double* __restrict__ cws,
+                int XS, int ZS, int M1S, int32_t* __restrict__ st_all, double gamma_scale) {
+  const int b = blockIdx.x;
+  if (st_all[b] != NYS_OK) return;
+  const Inst I = insts[b];
+  const Lset LS = lsets[I.lset];
+  const int m = I.m, p = I.p, me = LS.m_eff, M1 = me + 1;
+  const double* W = W_all + LS.w_off;
+  const double gamma = I.gamma * gamma_scale;
+  __shared__ double acc[kM1Max + 1];
+  __shared__ T h[kM1Max + 1], dx[kM1Max + 1], red[40];
+  __shared__ T cr[2], dl[2];
+  double* xb = xs + (int64_t)b * XS;
+  const double* C0 = cws + (int64_t)b * 2 * M1S;
+  const double* C1 = C0 + M1S;
+  for (int j = threadIdx.x; j <= m; j += blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < I.slot_count; ++q) s += part[slot_off[I.slot_begin + q] + j];
+    acc[j] = s;
+  }
+  __syncthreads();
+  const double lam0 = xb[XS - 2], lam1 = (p == 2) ? xb[XS - 1] : 0.0;
+  for (int k = threadIdx.x; k < M1; k += blockDim.x) {
+    double s;
+    if (k < me) {
+      s = 0.0;
+      for (int j = 0; j < m; ++j) s += W[k * m + j] * acc[j];
+      s = gamma * s - xb[k];
+    } else {
+      s = gamma * acc[m];
+    }
+    s -= C0[k] * lam0;
+    if (p == 2) s -= C1[k] * lam1;
+    h[k] = (T)s;
+  }
+  if (threadIdx.x < p) {
+    const double* Ck = threadIdx.x == 0 ? C0 : C1;
+    double s = I.v[threadIdx.x];
+    for (int k = 0; k < me; ++k) s -= Ck[k] * xb[k];
+    s -= Ck[me] * xb[XS - 3];
+    cr[threadIdx.x] = (T)s;
+  }
+  __syncthreads();
+  const FacView<T> F = fac_view(const_cast<T*>(fac_all) + (int64_t)b * facs, M1);
+  kkt_apply(F, M1, p, h, cr, dx, dl, red);
+  for (int k = threadIdx.x; k < M1; k += blockDim.x) {
+    const int slot = (k < me) ? k : XS - 3;
+    xb[slot] += (double)dx[k];
+  }
+  if (threadIdx.x == 0) {
+    xb[XS - 2] += (double)dl[0];
+    if (p == 2) xb[XS - 1] += (double)dl[1];
+  }
+  __syncthreads();
+  double* zb = zs + (int64_t)b * ZS;
+  for (int j = threadIdx.x; j <= m; j += blockDim.x) {
+    double s = 0.0;
+    if (j < m) {
+      for (int k = 0; k < me; ++k) s += W[k * m + j] * xb[k];
+    } else {
+      s = xb[XS - 3];
+    }
+    zb[j] = s;
+  }
+  if (threadIdx.x == 0) {
+    if (!isfinite(xb[XS - 3]) || !isfinite(xb[XS - 2])) st_all[b] = NYS_ENONFINITE;
+  }
+}
+
+size_t refine_smem_bytes(int m_max) {
+  const int M1 = m_max + 1;
+  const size_t tile = sizeof(float) * (size_t)kRefRows * (M1 | 1);
+  const size_t red = sizeof(float) * (size_t)kRefThreads * 2;
+  return tile > red ? tile : red;
+}
+
+// ---- launchers --------------------------------------------------------------
+cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const double* W,
+                         const float* W32, const double* part, const int64_t* slot_off, const int32_t* lm,
+                         void* fac, int64_t facs, double* xs, double* zs, double* cws, int XS,
+                         int ZS, int M1S, const int32_t* st_init, int32_t* st, double gamma_scale,
+                         int batch, int m_max, cudaStream_t s) {
+  const size_t sm = solve_smem_bytes(fp32, m_max);
+  cudaError_t e;
+  if (fp32) {
+    e = cudaFuncSetAttribute(k_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_solve<float><<<batch, kSolveThreads, sm, s>>>(insts, lsets, W, W32, part, slot_off, lm,
+                                                     (float*)fac, facs, xs, zs, cws, XS, ZS, M1S,
+                                                     st_init, st, gamma_scale);
+  } else {
+    e = cudaFuncSetAttribute(k_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_solve<double><<<batch, kSolveThreads, sm, s>>>(insts, lsets, W, W, part, slot_off, lm,
+                                                      (double*)fac, facs, xs, zs, cws, XS, ZS,
+                                                      M1S, st_init, st, gamma_scale);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W, const Work* work,
+                          int nwork, int* counter, const int32_t* lm, const double* tab,
+                          double* part, const int64_t* slot_off, const void* fac, int64_t facs,
+                          double* xs, double* zs, const double* cws, int XS, int ZS, int M1S,
+                          int32_t* st, double gamma_scale, int batch, int m_max, int num_sms,
+                          cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  const size_t sm = refine_smem_bytes(m_max);
+  e = cudaFuncSetAttribute(k_refine_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const int grid = min(nwork, num_sms * 2);
+  k_refine_rows<<<grid, kRefThreads, sm, s>>>(insts, work, nwork, counter, lm, tab, zs, ZS, part,
+                                               slot_off, st);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_refine_update<float><<<batch, kSolveThreads, 0, s>>>(insts, lsets, W, part, slot_off,
+                                                          (const float*)fac, facs, xs, zs, cws,
+                                                          XS, ZS, M1S, st, gamma_scale);
+  return cudaGetLastError();
+}
+
+}  // namespace nys

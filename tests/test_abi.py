@@ -1,0 +1,70 @@
+"""The C-ABI library builds, loads and exports every entry point of include/nys.h;
+host-side argument validation rejects bad instances before any device work."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def abi():
+    from paper_2510_04094_gb300 import build
+    build.build()
+    from paper_2510_04094_gb300 import _abi
+    _abi.lib()
+    return _abi
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "nys.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(nys_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("nys_setup", "nys_assemble", "nys_solve", "nys_newton", "nys_grad", "nys_eval",
+              "nys_destroy"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(abi):
+    lib = abi.lib()
+    for name in _declared():
+        assert hasattr(lib, name), name
+    assert set(_declared()) <= set(abi.EXPORTS) | {"nys_status_str", "nys_last_error"}
+
+
+def test_struct_layout_matches_header(abi):
+    assert C.sizeof(abi.nys_instance) == 16 + 8 * 4 + 16 + 64 + 16
+    assert C.sizeof(abi.nys_options) == 24
+    assert abi.nys_instance.t0.offset == 16 and abi.nys_instance.landmarks.offset == 128
+
+
+def _one(**kw):
+    import nys_inputs as ni
+    q = ni.cfg1()
+    q.update(kw)
+    return q
+
+
+@pytest.mark.parametrize("bad", [dict(p=3), dict(n=2), dict(m=1), dict(m=200, n=300),
+                                 dict(sigma=0.0), dict(gamma=-1.0), dict(t1=-1.0),
+                                 dict(landmarks=[0, 5, 5] + list(range(6, 23)))])
+def test_invalid_instances_are_rejected_on_the_host(abi, bad):
+    from paper_2510_04094_gb300.api import pack_instances
+    arr, keep = pack_instances([_one(**bad)])
+    opt = abi.nys_options()
+    ctx = C.c_void_p()
+    code = abi.lib().nys_setup(C.byref(ctx), arr, 1, C.byref(opt), None)
+    assert code == abi.NYS_EINVAL
+    assert abi.lib().nys_last_error().decode().startswith("instance 0")
+    assert not ctx.value
+
+
+def test_status_strings(abi):
+    for code in range(0, -10, -1):
+        assert abi.lib().nys_status_str(code)

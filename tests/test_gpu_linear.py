@@ -1,0 +1,189 @@
+"""GPU parity of the linear path (Lemma 1) against the FP64 oracle, through the C ABI.
+
+Tolerances: max|y_gpu - y_oracle| / max|y_oracle| <= 1e-10 on the FP64 path and
+<= 1e-6 on the mixed (FP32 assembly + refinement) path; the same for b.
+"""
+import numpy as np
+import pytest
+
+import nys_inputs as ni
+from oracle import core
+
+pytestmark = pytest.mark.gpu
+TOL = {"fp64": 1e-10, "mixed": 1e-6}
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2510_04094_gb300 import api as A
+    return A
+
+
+def _check(api, probs, precision, tol=None, refine=-1):
+    import torch
+    tol = TOL[precision] if tol is None else tol
+    bt = api.Batch(probs, precision=precision, refine_steps=refine)
+    bt.assemble()
+    x, st = bt.solve()
+    grids = [core.grid(q) for q in probs]
+    y, _ = bt.eval(grids)
+    y1, _ = bt.eval(grids, deriv=1)
+    torch.cuda.synchronize()
+    st = st.cpu().numpy()
+    assert (st == 0).all(), st
+    meff = bt.m_eff()
+    sols = bt.unpack()
+    yc, y1c = y.cpu().numpy(), y1.cpu().numpy()
+    off = 0
+    worst = 0.0
+    for k, (q, g) in enumerate(zip(probs, grids)):
+        ref = core.solve_linear(q)
+        assert meff[k] == ref["m_eff"]
+        got = yc[off:off + len(g)]
+        err = np.abs(got - ref["y"]).max() / np.abs(ref["y"]).max()
+        d1 = core.evaluate(q, ref, g, 1)
+        err1 = np.abs(y1c[off:off + len(g)] - d1).max() / np.abs(d1).max()
+        eb = abs(sols[k]["b"] - ref["b"]) / max(1.0, np.abs(ref["y"]).max())
+        off += len(g)
+        worst = max(worst, err)
+        assert err <= tol, (k, err)
+        assert err1 <= 50 * tol, (k, err1)
+        assert eb <= 10 * tol, (k, eb)
+    bt.close()
+    return worst
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cfg1_single_instance(api, precision):
+    _check(api, [ni.cfg1()], precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_small_ragged_batch(api, precision):
+    """Mixed p, n, m: several row tiles plus ragged tails, tiny m."""
+    _check(api, ni.small_linear(12), precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_metric_family_full_size_sample(api, precision):
+    """The n = 1e4, m = 50 family of the throughput workload (a few instances)."""
+    _check(api, ni.m0(4), precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cfg2_linear_full_size(api, precision):
+    _check(api, [ni.cfg2_linear()], precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_ragged_batch_all_m_values(api, precision):
+    """The ragged family (m in {20, 32, 50, 64, 100}, sigma = T/m), n capped for the oracle."""
+    probs = [q for q in ni.cfg3(40, n_hi=4000)]
+    _check(api, probs, precision)
+
+
+def test_table_coefficients_match_parametric(api):
+    q = ni.m0(1, n=3000)[0]
+    t = core.grid(q)
+    tq = dict(q, kind="table", f=[np.full(q["n"], -q["a"][0]), np.full(q["n"], -q["a"][1])],
+              r=q["c"] * np.sin(q["omega"] * t + q["phi0"]))
+    _check(api, [tq], "fp64")
+    _check(api, [tq], "mixed")
+
+
+def test_nonfinite_instance_is_isolated(api):
+    import torch
+    probs = ni.m0(3, n=1500, m=20)
+    probs[1] = dict(probs[1], c=float("nan"))
+    bt = api.Batch(probs, precision="fp64")
+    bt.assemble()
+    x, st = bt.solve()
+    torch.cuda.synchronize()
+    assert list(st.cpu().numpy()) == [0, -6, 0]
+    bt.close()
+
+
+def test_rerun_is_bitwise_deterministic(api):
+    import torch
+    probs = ni.m0(6, n=3000)
+    outs = []
+    for _ in range(2):
+        bt = api.Batch(probs, precision="mixed")
+        bt.assemble()
+        x, st = bt.solve()
+        torch.cuda.synchronize()
+        outs.append(x.cpu().numpy().copy())
+        bt.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_graph_run_matches_stepwise(api):
+    import torch
+    probs = ni.m0(8, n=2000)
+    bt = api.Batch(probs, precision="mixed")
+    bt.assemble()
+    x1 = bt.solve()[0].clone()
+    x2 = bt.run()[0].clone()
+    x3 = bt.run()[0].clone()
+    torch.cuda.synchronize()
+    assert torch.equal(x1, x2) and torch.equal(x2, x3)
+    bt.close()
+
+
+def test_update_changes_coefficients(api):
+    import torch
+    a = ni.m0(4, n=2000)
+    b = ni.linear_family(4, n=2000, m=50, name="m0", sub=7)
+    bt = api.Batch(a, precision="fp64")
+    bt.update(b)
+    bt.assemble()
+    bt.solve()
+    y, _ = bt.eval([core.grid(q) for q in b])
+    torch.cuda.synchronize()
+    yc = y.cpu().numpy()
+    off = 0
+    for q in b:
+        ref = core.solve_linear(q)["y"]
+        assert np.abs(yc[off:off + q["n"]] - ref).max() <= 1e-10 * np.abs(ref).max()
+        off += q["n"]
+    bt.close()
+
+
+def test_graph_replay_after_update_changes_landmark_sets(api):
+    """A graph captured with one shared Nystrom factor stays valid when an update
+    gives every instance its own sigma (four distinct factors)."""
+    import torch
+    a = ni.m0(4, n=2000)
+    bt = api.Batch(a, precision="mixed")
+    bt.run()
+    b = [dict(q, sigma=0.4 + 0.05 * k) for k, q in enumerate(ni.m0(4, n=2000))]
+    bt.update(b)
+    bt.run()
+    y, _ = bt.eval([core.grid(q) for q in b])
+    torch.cuda.synchronize()
+    assert (bt.status.cpu().numpy() == 0).all()
+    yc = y.cpu().numpy()
+    off = 0
+    for q in b:
+        ref = core.solve_linear(q)["y"]
+        assert np.abs(yc[off:off + q["n"]] - ref).max() <= 1e-6 * np.abs(ref).max()
+        off += q["n"]
+    bt.close()
+
+
+def test_eval_subset_of_instances(api):
+    import torch
+    probs = ni.m0(5, n=1500, m=20)
+    bt = api.Batch(probs, precision="fp64")
+    bt.run()
+    g = core.grid(probs[0])
+    y, _ = bt.eval([g])
+    torch.cuda.synchronize()
+    ref = core.solve_linear(probs[0])["y"]
+    assert np.abs(y.cpu().numpy() - ref).max() <= 1e-10 * np.abs(ref).max()
+    bt.close()
