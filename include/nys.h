@@ -170,6 +170,34 @@ int32_t nys_newton(nys_ctx* c, void* stream, int32_t max_iter, double tol,
 int32_t nys_grad(nys_ctx* c, void* stream, const double* obs_t, const int64_t* obs_off,
                  const double* dl_dy, double* grad_out);
 
+/* Allocation-free FP64 solve (the paper has no counterpart; this is a library
+   facility).  For callers that cannot call cudaMalloc: processes whose device
+   memory is reserved up front by another allocator (a framework's caching
+   pool, a fixed-budget server) or latency-critical code that cannot accept
+   an allocation's implicit device synchronisation.  Computes exactly what
+   nys_setup + nys_assemble + nys_solve compute with precision NYS_FP64 (same
+   kernels), for a small batch of NYS_COEF_LIN instances; every workspace,
+   including the row pass's partial Gram sums, lives in one static device
+   array of NYS_NOALLOC_SCRATCH_BYTES (6 MiB) that every GPU loading the
+   library holds until exit.  Nothing is allocated on the device or host.
+   Limits: batch <= NYS_NOALLOC_MAX_BATCH, m <= NYS_NOALLOC_MAX_M,
+   n <= NYS_NOALLOC_MAX_N; larger requests return NYS_EINVAL with a message.
+   inst: host array; x_out: device, batch x (m_max + 3) doubles with m_max
+   the largest m in this call (layout of nys_solve); status_out: device
+   int32[batch].  The first call on a device looks up the array's device
+   address (once per device, with that device current): make that first call
+   before any stream capture.  Blocks until earlier work on `stream` is done
+   and the descriptors are on the device.  All calls share the array, which
+   keeps the last call's contents (the work counter is cleared by each call):
+   calls whose GPU work overlaps (several streams or host threads) race.   */
+#define NYS_NOALLOC_SCRATCH_BYTES (6 * 1024 * 1024)
+#define NYS_NOALLOC_MAX_BATCH 32
+#define NYS_NOALLOC_MAX_M 64
+#define NYS_NOALLOC_MAX_N (1 << 20)
+#define NYS_NOALLOC_MAX_CHUNKS 4
+int32_t nys_solve_noalloc(const nys_instance* inst, int32_t batch, double* x_out,
+                          int32_t* status_out, void* stream);
+
 /* Free every resource of the context (synchronises its last stream).         */
 void nys_destroy(nys_ctx* c);
 

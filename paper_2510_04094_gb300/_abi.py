@@ -60,6 +60,8 @@ def lib():
         L.nys_eval.argtypes = [vp, vp, vp, vp, i32, vp]
         L.nys_newton.argtypes = [vp, vp, i32, dbl, vp, vp, vp, vp]
         L.nys_grad.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.nys_solve_noalloc.argtypes = [C.POINTER(nys_instance), i32, vp, vp, vp]
+        L.nys_solve_noalloc.restype = i32
         L.nys_destroy.argtypes = [vp]
         L.nys_destroy.restype = None
         L.nys_status_str.argtypes = [i32]
@@ -126,11 +128,16 @@ def nys_grad(ctx, stream, obs_t, obs_off, dl_dy, grad_out):
     check(lib().nys_grad(ctx, stream, obs_t, obs_off, dl_dy, grad_out))
 
 
+def nys_solve_noalloc(inst_array, batch, x_out, status_out, stream):
+    check(lib().nys_solve_noalloc(inst_array, batch, x_out, status_out, stream))
+
+
 def nys_destroy(ctx):
     lib().nys_destroy(ctx)
 
 
 EXPORTS = ("nys_setup", "nys_update", "nys_assemble", "nys_solve", "nys_run", "nys_x_stride",
            "nys_upload_bytes",
-           "nys_m_eff", "nys_eval", "nys_newton", "nys_grad", "nys_destroy", "nys_status_str",
+           "nys_m_eff", "nys_eval", "nys_newton", "nys_grad", "nys_solve_noalloc", "nys_destroy",
+           "nys_status_str",
            "nys_last_error")

@@ -51,6 +51,14 @@ static int32_t fail(int32_t code, const char* fmt, ...) {
   g_err = buf;
   return code;
 }
+namespace nys {
+// lets other translation units report through nys_last_error()
+int32_t set_last_error(int32_t code, const char* msg) {
+  g_err = msg;
+  return code;
+}
+}  // namespace nys
+
 #define CK(call)                                                                         \
   do {                                                                                   \
     cudaError_t e_ = (call);                                                             \
