@@ -14,9 +14,8 @@
 
 namespace nys {
 // kernel launchers (defined in the other translation units)
-cudaError_t launch_setup(Lset* lsets, const int32_t* nl_dev, int capacity, const int32_t* lm_idx,
-                         double* W, float* W32, double* lam, double tau, int m_max,
-                         cudaStream_t st);
+cudaError_t launch_setup(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
+                         double* lam, float* lag, double tau, int m_max, cudaStream_t st);
 cudaError_t launch_assemble(bool fp32, const Inst* insts, const Work* work, int nwork,
                             int* counter, const int32_t* lm, const double* tab, double* part,
                             const int64_t* slot_off, int m_max, int num_sms, cudaStream_t st);
@@ -25,12 +24,13 @@ cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const 
                          const int32_t* lm, void* fac, int64_t facs, double* xs, double* zs,
                          double* cws, int XS, int ZS, int M1S, const int32_t* st_init,
                          int32_t* st, double gamma_scale, int batch, int m_max, cudaStream_t s);
-cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W, const Work* work,
-                          int nwork, int* counter, const int32_t* lm, const double* tab,
+cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W, const float* lag,
+                          const Work* work, int nwork, int* counter, const int32_t* lm,
+                          const double* tab,
                           double* part, const int64_t* slot_off, const void* fac, int64_t facs,
                           double* xs, double* zs, const double* cws, int XS, int ZS, int M1S,
-                          int32_t* st, double gamma_scale, int batch, int m_max, int num_sms,
-                          cudaStream_t s);
+                          int32_t* st, double gamma_scale, int batch, int m_max, int k_max,
+                          int num_sms, cudaStream_t s);
 cudaError_t launch_eval(const Inst* insts, const double* zs, int ZS, const int32_t* lm,
                         const double* tq, const int64_t* tq_off, int deriv, double* yq, int batch,
                         cudaStream_t s);
@@ -104,7 +104,10 @@ struct nys_ctx {
   std::vector<Lset> h_lset;
   std::vector<int32_t> h_stinit;
   std::vector<double> h_tab;
+  std::vector<int64_t> h_lagcap;           // lag-table offset of slot b (floats)
   int64_t total_rows = 0;
+  int64_t lag_floats = 0;
+  int k_max = 0;                  // largest lag-table length of the current sets
   // device
   DBuf<Inst> inst;
   DBuf<Lset> lset;
@@ -115,10 +118,11 @@ struct nys_ctx {
   DBuf<double> part;
   DBuf<double> W;
   DBuf<float> W32;
+  DBuf<float> lag;
   DBuf<double> lam;
   DBuf<unsigned char> fac;
   DBuf<double> xs, zs, dzs, cws;
-  DBuf<int32_t> st, stinit, counter, nlset_dev;
+  DBuf<int32_t> st, stinit, counter;
   // Newton state
   DBuf<double> yaux, rowstate, nrm;
   DBuf<int64_t> row_off;
@@ -133,7 +137,10 @@ struct nys_ctx {
   cudaEvent_t staged = nullptr;
   std::vector<GraphKey> graphs;
   bool factor_stale = true;
+  bool join_pending = false;     // factor running on the side stream
   int64_t upload_bytes = 0;
+  cudaStream_t side = nullptr;   // runs the Nystrom setup beside the row pass
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 static bool finite_all(const double* a, int n) {
@@ -194,6 +201,8 @@ static int32_t pack(nys_ctx* c, const nys_instance* q, bool first) {
   c->h_tab.clear();
   std::map<std::vector<int64_t>, int> keys;
   c->h_lset.clear();
+  c->nlset = 0;
+  c->k_max = 0;
   for (int b = 0; b < B; ++b) {
     const nys_instance& s = q[b];
     int32_t r = check_instance(s, b);
@@ -234,55 +243,72 @@ static int32_t pack(nys_ctx* c, const nys_instance* q, bool first) {
       c->h_tab.insert(c->h_tab.end(), s.coef_table, s.coef_table + (size_t)(s.p + 1) * s.n);
     }
     c->h_stinit[b] = r;
-    // landmark-set key: m, indices, bits of h/sigma
+    // landmark-set key: n, m, indices, bits of h/sigma.  Slot b is the set of
+    // instance b; only the first instance with a given key is active.
     std::vector<int64_t> key(lm.begin(), lm.end());
     int64_t hbits;
     std::memcpy(&hbits, &I.hs, sizeof hbits);
     key.push_back(hbits);
     key.push_back(s.m);
+    key.push_back(s.n);
+    Lset L{};
+    L.m = s.m;
+    L.m_eff = s.m;
+    L.n = s.n;
+    L.K = (int)std::min<double>(s.n - 1, std::ceil(std::sqrt(kLagU) / I.hs));
+    L.lm_off = I.lm_off;
+    L.w_off = (int64_t)b * c->m_max * c->m_max;
+    L.lag_off = c->h_lagcap[b];
+    L.hs = I.hs;
     auto it = keys.find(key);
     if (it == keys.end()) {
-      const int id = (int)c->h_lset.size();
-      keys.emplace(std::move(key), id);
-      Lset L{};
-      L.m = s.m;
-      L.m_eff = s.m;
-      L.lm_off = I.lm_off;
-      L.w_off = (int64_t)id * c->m_max * c->m_max;
-      L.hs = I.hs;
-      c->h_lset.push_back(L);
-      I.lset = id;
+      keys.emplace(std::move(key), b);
+      L.active = 1;
+      I.lset = b;
+      ++c->nlset;
     } else {
+      L.active = 0;
       I.lset = it->second;
     }
+    c->h_lset.push_back(L);
+    c->k_max = std::max(c->k_max, L.K);
   }
-  c->nlset = (int)c->h_lset.size();
   return NYS_OK;
 }
 
 static cudaError_t enqueue_factor(nys_ctx* c, cudaStream_t s) {
-  return launch_setup(c->lset.p, c->nlset_dev.p, c->batch, c->lm.p, c->W.p, c->W32.p, c->lam.p,
+  return launch_setup(c->lset.p, c->batch, c->lm.p, c->W.p, c->W32.p, c->lam.p, c->lag.p,
                       c->opt.eig_tau > 0 ? c->opt.eig_tau : 1e-12, c->m_max, s);
+}
+
+// Fork the Nystrom setup onto the side stream: the row pass works in kernel
+// coordinates and does not need W, so the two overlap; the solve joins.
+static cudaError_t fork_factor(nys_ctx* c, cudaStream_t s) {
+  cudaError_t e = cudaEventRecord(c->ev_fork, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+  if (e == cudaSuccess) e = enqueue_factor(c, c->side);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
+  return e;
 }
 
 static int32_t upload_and_setup(nys_ctx* c, cudaStream_t s, bool factor_now) {
   // reuse of the pinned staging buffers: wait for the previous upload
   CK(cudaEventSynchronize(c->staged));
   std::memcpy(c->pin_inst, c->h_inst.data(), sizeof(Inst) * c->batch);
-  std::memcpy(c->pin_lset, c->h_lset.data(), sizeof(Lset) * c->nlset);
+  std::memcpy(c->pin_lset, c->h_lset.data(), sizeof(Lset) * c->batch);
   std::memcpy(c->pin_st, c->h_stinit.data(), sizeof(int32_t) * c->batch);
-  c->pin_st[c->batch] = c->nlset;
+
   CK(cudaMemcpyAsync(c->inst.p, c->pin_inst, sizeof(Inst) * c->batch, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(c->lset.p, c->pin_lset, sizeof(Lset) * c->nlset, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->lset.p, c->pin_lset, sizeof(Lset) * c->batch, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(c->stinit.p, c->pin_st, sizeof(int32_t) * c->batch, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(c->st.p, c->pin_st, sizeof(int32_t) * c->batch, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(c->nlset_dev.p, c->pin_st + c->batch, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+
   if (!c->h_tab.empty())
     CK(cudaMemcpyAsync(c->tab.p, c->h_tab.data(), sizeof(double) * c->h_tab.size(),
                        cudaMemcpyHostToDevice, s));
   CK(cudaEventRecord(c->staged, s));
   if (!c->h_tab.empty()) CK(cudaStreamSynchronize(s));  // pageable source
-  c->upload_bytes = (int64_t)(sizeof(Inst) * c->batch + sizeof(Lset) * c->nlset +
+  c->upload_bytes = (int64_t)(sizeof(Inst) * c->batch + sizeof(Lset) * c->batch +
                               2 * sizeof(int32_t) * c->batch + sizeof(double) * c->h_tab.size());
   c->factor_stale = true;
   if (factor_now) {
@@ -320,8 +346,8 @@ void nys_destroy(nys_ctx* c) {
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
   c->inst.release(); c->lset.release(); c->lm.release(); c->tab.release(); c->work.release();
   c->slot_off.release(); c->part.release(); c->W.release(); c->W32.release(); c->lam.release();
-  c->fac.release(); c->xs.release(); c->zs.release(); c->dzs.release(); c->cws.release();
-  c->st.release(); c->stinit.release(); c->counter.release(); c->nlset_dev.release(); c->yaux.release(); c->rowstate.release();
+  c->fac.release(); c->lag.release(); c->xs.release(); c->zs.release(); c->dzs.release(); c->cws.release();
+  c->st.release(); c->stinit.release(); c->counter.release(); c->yaux.release(); c->rowstate.release();
   c->nrm.release(); c->row_off.release(); c->active.release(); c->iters.release();
   c->any_active.release(); c->adj.release();
   if (c->pin_inst) cudaFreeHost(c->pin_inst);
@@ -329,6 +355,9 @@ void nys_destroy(nys_ctx* c) {
   if (c->pin_st) cudaFreeHost(c->pin_st);
   if (c->pin_flag) cudaFreeHost(c->pin_flag);
   if (c->staged) cudaEventDestroy(c->staged);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->side) cudaStreamDestroy(c->side);
   delete c;
 }
 
@@ -354,6 +383,15 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   }
   c->m_max = std::min(c->m_max, NYS_M_MAX);
   c->shape.assign(q, q + batch);
+  c->h_lagcap.assign(batch, 0);
+  {
+    int64_t o = 0;
+    for (int b = 0; b < batch; ++b) {
+      c->h_lagcap[b] = o;
+      o += 6LL * std::max(3, q[b].n);
+    }
+    c->lag_floats = o;
+  }
   for (auto& s : c->shape) { s.landmarks = nullptr; s.coef_table = nullptr; }
   int32_t r = pack(c, q, true);
   if (r != NYS_OK) { delete c; return r; }
@@ -426,6 +464,7 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   A(c->part.alloc((size_t)poff));
   A(c->W.alloc((size_t)batch * c->m_max * c->m_max));
   A(c->W32.alloc((size_t)batch * c->m_max * c->m_max));
+  if (c->fp32) A(c->lag.alloc((size_t)c->lag_floats));
   A(c->lam.alloc((size_t)batch * NYS_M_MAX));
   A(c->fac.alloc((size_t)batch * c->facs * (c->any_nl ? sizeof(double) : es)));
   A(c->xs.alloc((size_t)batch * c->XS));
@@ -435,7 +474,6 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   A(c->st.alloc(batch));
   A(c->stinit.alloc(batch));
   A(c->counter.alloc(1));
-  A(c->nlset_dev.alloc(1));
   if (c->any_nl) {
     A(c->yaux.alloc((size_t)ytot));
     A(c->rowstate.alloc((size_t)ytot * 4));
@@ -450,6 +488,9 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   A(cudaMallocHost(reinterpret_cast<void**>(&c->pin_st), sizeof(int32_t) * (batch + 1)));
   A(cudaMallocHost(reinterpret_cast<void**>(&c->pin_flag), sizeof(int32_t)));
   A(cudaEventCreateWithFlags(&c->staged, cudaEventDisableTiming));
+  A(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  A(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  A(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
   if (e != cudaSuccess) {
     const bool oom = (e == cudaErrorMemoryAllocation);
     nys_destroy(c);
@@ -489,8 +530,9 @@ int32_t nys_assemble(nys_ctx* c, void* stream) {
   if (!c) return fail(NYS_EINVAL, "nys_assemble: NULL context");
   if (c->any_nl) return fail(NYS_EINVAL, "nys_assemble: the batch holds nonlinear instances (use nys_newton)");
   if (c->factor_stale) {
-    CK(enqueue_factor(c, (cudaStream_t)stream));
+    CK(fork_factor(c, (cudaStream_t)stream));
     c->factor_stale = false;
+    c->join_pending = true;
   }
   CK(launch_assemble(c->fp32, c->inst.p, c->work.p, c->nwork, c->counter.p, c->lm.p, c->tab.p,
                      c->part.p, c->slot_off.p, c->m_max, c->num_sms, (cudaStream_t)stream));
@@ -505,10 +547,10 @@ static int32_t solve_impl(nys_ctx* c, cudaStream_t s, double* x_out, int32_t* st
                   c->stinit.p, c->st.p, gscale, c->batch, c->m_max, s));
   if (c->fp32) {
     for (int k = 0; k < c->opt.refine_steps; ++k)
-      CK(launch_refine(c->inst.p, c->lset.p, c->W.p, c->work.p, c->nwork, c->counter.p, c->lm.p,
-                       c->tab.p, c->part.p, c->slot_off.p, c->fac.p, c->facs, c->xs.p, c->zs.p,
+      CK(launch_refine(c->inst.p, c->lset.p, c->W.p, c->lag.p, c->work.p, c->nwork, c->counter.p,
+                       c->lm.p, c->tab.p, c->part.p, c->slot_off.p, c->fac.p, c->facs, c->xs.p, c->zs.p,
                        c->cws.p, c->XS, c->ZS, c->M1S, c->st.p, gscale, c->batch, c->m_max,
-                       c->num_sms, s));
+                       c->k_max, c->num_sms, s));
   }
   if (x_out)
     CK(cudaMemcpyAsync(x_out, c->xs.p, sizeof(double) * c->batch * c->XS, cudaMemcpyDeviceToDevice, s));
@@ -520,6 +562,10 @@ static int32_t solve_impl(nys_ctx* c, cudaStream_t s, double* x_out, int32_t* st
 int32_t nys_solve(nys_ctx* c, void* stream, double* x_out, int32_t* status_out) {
   if (!c) return fail(NYS_EINVAL, "nys_solve: NULL context");
   if (!c->assembled) return fail(NYS_ESTATE, "nys_solve: call nys_assemble first");
+  if (c->join_pending) {
+    CK(cudaStreamWaitEvent((cudaStream_t)stream, c->ev_join, 0));
+    c->join_pending = false;
+  }
   int32_t r = solve_impl(c, (cudaStream_t)stream, x_out, status_out);
   if (r == NYS_OK) c->solved = true;
   return r;
@@ -541,11 +587,12 @@ int32_t nys_run(nys_ctx* c, void* stream, double* x_out, int32_t* status_out) {
     if (e != cudaSuccess) { cudaStreamDestroy(cs); CK(e); }
     int32_t r = NYS_OK;
     {
-      cudaError_t e2 = enqueue_factor(c, cs);
+      cudaError_t e2 = fork_factor(c, cs);
       if (e2 == cudaSuccess)
         e2 = launch_assemble(c->fp32, c->inst.p, c->work.p, c->nwork, c->counter.p,
                                        c->lm.p, c->tab.p, c->part.p, c->slot_off.p, c->m_max,
                                        c->num_sms, cs);
+      if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(cs, c->ev_join, 0);
       if (e2 != cudaSuccess) r = fail(NYS_ECUDA, "capture: assemble: %s", cudaGetErrorString(e2));
       if (r == NYS_OK) r = solve_impl(c, cs, x_out, status_out);
     }
@@ -557,6 +604,10 @@ int32_t nys_run(nys_ctx* c, void* stream, double* x_out, int32_t* status_out) {
     cudaGraphDestroy(graph);
     CK(e);
     c->graphs.push_back({x_out, status_out, exec});
+  }
+  if (c->join_pending) {  // a setup forked by an earlier nys_assemble
+    CK(cudaStreamWaitEvent(s, c->ev_join, 0));
+    c->join_pending = false;
   }
   CK(cudaGraphLaunch(exec, s));
   c->assembled = c->solved = true;
@@ -570,8 +621,8 @@ int32_t nys_x_stride(const nys_ctx* c) { return c ? c->XS : 0; }
 
 int32_t nys_m_eff(nys_ctx* c, void* stream, int32_t* out) {
   if (!c || !out) return fail(NYS_EINVAL, "nys_m_eff: NULL argument");
-  std::vector<Lset> L(c->nlset);
-  CK(cudaMemcpyAsync(L.data(), c->lset.p, sizeof(Lset) * c->nlset, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  std::vector<Lset> L(c->batch);
+  CK(cudaMemcpyAsync(L.data(), c->lset.p, sizeof(Lset) * c->batch, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   for (int b = 0; b < c->batch; ++b) out[b] = L[c->h_inst[b].lset].m_eff;
   return NYS_OK;

@@ -161,6 +161,7 @@ k_assemble_f32(const Inst* __restrict__ insts, const Work* __restrict__ work, in
     const int RS = kAsm32Threads / MP;
     const int fj = tid % MP, fr0 = tid / MP;
     const float hs = (float)I.hs;
+    const RowConst RK = row_const(I);
 
     float acc[64];
 #pragma unroll
@@ -172,12 +173,10 @@ k_assemble_f32(const Inst* __restrict__ insts, const Work* __restrict__ work, in
       if (tid < kAsm32Rows) {
         const int i = base + tid;
         if (i < wk.r1) {
-          double f1, f2, rr;
-          coef_f(I, tab, i, f1, f2, rr);
-          const RowCoef R = row_coef_from_f(I, f1, f2, rr);
-          s_rc[tid][0] = (float)R.A0; s_rc[tid][1] = (float)R.A1; s_rc[tid][2] = (float)R.A2;
-          s_rc[tid][3] = (float)R.w1;
-          s_rc[tid][4] = (I.kind == NYS_COEF_LIN) ? lin_rhs_ff(I, i) : (float)rr;
+          ff c5[5];
+          row_coef_ff(I, RK, tab, i, c5);
+#pragma unroll
+          for (int q = 0; q < 5; ++q) s_rc[tid][q] = c5[q].hi;
         }
       }
       __syncthreads();

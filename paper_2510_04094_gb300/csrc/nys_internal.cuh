@@ -31,13 +31,20 @@ struct Inst {
   double th0, dth;     // LIN: omega*t0 + phi0 and omega*h, both reduced mod 2 pi
 };
 
-// A landmark set: m indices on a grid with spacing h, kernel width sigma.
+// A landmark set: m indices on a grid of n points with spacing h, kernel width
+// sigma.  Slot b of the set array belongs to instance b; it is active when b is
+// the first instance with this set (the others point to it through Inst::lset).
 struct Lset {
   int32_t m, m_eff;    // m_eff written by the setup kernel
+  int32_t n, K;        // K: largest tabulated lag, exp(-(K h/sigma)^2) < 1e-34
+  int32_t active, pad;
   int64_t lm_off;
   int64_t w_off;       // W: m x m doubles (rows k < m_eff used), row-major
+  int64_t lag_off;     // lag tables (floats): 6 per lag k = 0..K, see k_setup_lag
   double hs;           // h / sigma
 };
+// Largest lag whose kernel value is kept: (K hs)^2 <= kLagU.
+constexpr double kLagU = 80.0;
 
 // One unit of a row pass: rows i in [r0, r1) (0-based grid index, 1 <= i <= n-1).
 struct Work {
@@ -78,6 +85,14 @@ __device__ __forceinline__ ff ff_fma_f(float a, ff b, ff acc) {
   float lo = s.lo + pe + acc.lo;
   float hi = s.hi + lo;
   return {hi, lo - (hi - s.hi)};
+}
+__device__ __forceinline__ ff ff_mul_ff(ff a, ff b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const float hi = p + e;
+  return {hi, e - (hi - p)};
 }
 __device__ __forceinline__ ff ff_from_double(double x) {
   float hi = (float)x;
@@ -173,27 +188,78 @@ __device__ __forceinline__ double lin_rhs_f64(const Inst& I, int i) {
   return I.c[2] * sin(I.c[3] * t + I.c[4]);
 }
 
-// Same in FP32 with a float-float argument: theta_i = th0 + i*dth with th0 and
-// dth reduced mod 2 pi on the host, the product i*dth split exactly by FMA and
-// the sum reduced again (Cody-Waite with 2 pi in two parts).  The result is
-// c sin(theta_i) to about one FP32 ulp.
-__device__ __forceinline__ float lin_rhs_ff(const Inst& I, int i) {
+// Per-work-item constants of an instance in float-float, so that the per-row
+// work of the FP32 kernels needs no FP64 arithmetic or conversion.
+struct RowConst {
+  ff A0, A1, A2, w1;   // constant-coefficient operator (kind LIN)
+  ff is, is2;          // 1/sigma, 1/sigma^2
+  ff th0, dth;         // r(t_i) = c sin(th0 + i dth)
+  float c;
+};
+
+__device__ __forceinline__ RowConst row_const(const Inst& I) {
+  RowConst K;
+  double f1 = -I.c[0], f2 = (I.p == 2) ? -I.c[1] : 0.0, rr = 0.0;
+  const RowCoef R = row_coef_from_f(I, f1, f2, rr);
+  K.A0 = ff_from_double(R.A0);
+  K.A1 = ff_from_double(R.A1);
+  K.A2 = ff_from_double(R.A2);
+  K.w1 = ff_from_double(R.w1);
+  K.is = ff_from_double(1.0 / I.sigma);
+  K.is2 = ff_from_double(1.0 / (I.sigma * I.sigma));
+  K.th0 = ff_from_double(I.th0);
+  K.dth = ff_from_double(I.dth);
+  K.c = (float)I.c[2];
+  return K;
+}
+
+// c sin(theta_i) in FP32 with a float-float argument: theta_i = th0 + i dth
+// with th0 and dth reduced mod 2 pi on the host, the product i dth split exactly
+// by FMA and the sum reduced again (Cody-Waite with 2 pi in two parts); about
+// one FP32 ulp.
+__device__ __forceinline__ float lin_rhs_ff(const RowConst& K, int i) {
   const float k2PiHi = 6.28318548202514648f;
   const float k2PiLo = -1.74845553e-07f;
-  ff dth = ff_from_double(I.dth);
-  ff th0 = ff_from_double(I.th0);
-  float fi = (float)i;
-  float p = fi * dth.hi;
-  float pe = fmaf(fi, dth.hi, -p);
-  pe = fmaf(fi, dth.lo, pe);
-  ff th = ff_add(th0, ff{p, pe});
-  float k = rintf(th.hi * 0.159154943091895336f);
-  float a = fmaf(-k, k2PiHi, th.hi);
-  float b = fmaf(-k, k2PiLo, th.lo);
-  ff r = ff_two_sum(a, b);
+  const float fi = (float)i;
+  const float p = fi * K.dth.hi;
+  float pe = fmaf(fi, K.dth.hi, -p);
+  pe = fmaf(fi, K.dth.lo, pe);
+  const ff th = ff_add(K.th0, ff{p, pe});
+  const float k = rintf(th.hi * 0.159154943091895336f);
+  const float a = fmaf(-k, k2PiHi, th.hi);
+  const float b = fmaf(-k, k2PiLo, th.lo);
+  const ff r = ff_two_sum(a, b);
   float s, cth;
   sincosf(r.hi, &s, &cth);
-  return (float)I.c[2] * fmaf(cth, r.lo, s);
+  return K.c * fmaf(cth, r.lo, s);
+}
+
+// Operator coefficients of row i in float-float (TABLE kind reads the FP64
+// table and converts; LIN uses the constants).  Returns A0, A1, A2, w1, r.
+__device__ __forceinline__ void row_coef_ff(const Inst& I, const RowConst& K,
+                                            const double* __restrict__ tab, int i, ff* out) {
+  if (I.kind == NYS_COEF_TABLE) {
+    const double* T = tab + I.tab_off;
+    const ff f1 = ff_from_double(T[i]);
+    const ff f2 = (I.p == 2) ? ff_from_double(T[(int64_t)I.n + i]) : ff{0.f, 0.f};
+    const ff rr = ff_from_double(T[(int64_t)I.p * I.n + i]);
+    if (I.p == 2) {
+      out[0] = ff_add(ff{-f2.hi, -f2.lo}, ff{-2.f * K.is2.hi, -2.f * K.is2.lo});
+      const ff t = ff_mul_ff(f1, K.is);
+      out[1] = ff{2.f * t.hi, 2.f * t.lo};
+      out[2] = ff{4.f * K.is2.hi, 4.f * K.is2.lo};
+      out[3] = ff{-f2.hi, -f2.lo};
+    } else {
+      out[0] = ff{-f1.hi, -f1.lo};
+      out[1] = ff{-2.f * K.is.hi, -2.f * K.is.lo};
+      out[2] = ff{0.f, 0.f};
+      out[3] = ff{-f1.hi, -f1.lo};
+    }
+    out[4] = rr;
+  } else {
+    out[0] = K.A0; out[1] = K.A1; out[2] = K.A2; out[3] = K.w1;
+    out[4] = ff{lin_rhs_ff(K, i), 0.f};
+  }
 }
 
 __host__ __device__ __forceinline__ int round_up(int x, int a) { return (x + a - 1) / a * a; }

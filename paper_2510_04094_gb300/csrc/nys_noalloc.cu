@@ -22,9 +22,8 @@
 #include "nys_internal.cuh"
 
 namespace nys {
-cudaError_t launch_setup(Lset* lsets, const int32_t* nl_dev, int capacity, const int32_t* lm_idx,
-                         double* W, float* W32, double* lam, double tau, int m_max,
-                         cudaStream_t st);
+cudaError_t launch_setup(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
+                         double* lam, float* lag, double tau, int m_max, cudaStream_t st);
 cudaError_t launch_assemble(bool fp32, const Inst* insts, const Work* work, int nwork,
                             int* counter, const int32_t* lm, const double* tab, double* part,
                             const int64_t* slot_off, int m_max, int num_sms, cudaStream_t st);
@@ -147,6 +146,8 @@ extern "C" int32_t nys_solve_noalloc(const nys_instance* q, int32_t batch, doubl
     L = Lset{};
     L.m = s.m;
     L.m_eff = s.m;
+    L.n = s.n;
+    L.active = 1;   // no lag tables on this path (FP64 features are computed directly)
     L.lm_off = I.lm_off;
     L.w_off = (int64_t)nl * m_max * m_max;
     L.hs = I.hs;
@@ -208,9 +209,9 @@ extern "C" int32_t nys_solve_noalloc(const nys_instance* q, int32_t batch, doubl
   Lset* d_lset = reinterpret_cast<Lset*>(B + o_lset);
   const int32_t* d_lm = reinterpret_cast<const int32_t*>(B + o_lm);
   const int32_t* d_stinit = reinterpret_cast<const int32_t*>(B + o_st);
-  NA_CK(launch_setup(d_lset, d_stinit + batch, nl, d_lm, reinterpret_cast<double*>(B + o_W),
+  NA_CK(launch_setup(d_lset, nl, d_lm, reinterpret_cast<double*>(B + o_W),
                      reinterpret_cast<float*>(B + o_W32), reinterpret_cast<double*>(B + o_lam),
-                     1e-12, m_max, st));
+                     nullptr, 1e-12, m_max, st));
   // the work counter is cleared inside launch_assemble before the kernel
   NA_CK(launch_assemble(false, d_inst, reinterpret_cast<const Work*>(B + o_work), nwork,
                         reinterpret_cast<int*>(B + o_cnt), d_lm, nullptr,

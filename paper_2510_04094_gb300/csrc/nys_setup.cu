@@ -33,14 +33,14 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 __global__ void __launch_bounds__(kSetupThreads)
-k_setup_eig(Lset* lsets, const int32_t* __restrict__ nl_dev, const int32_t* __restrict__ lm_idx,
-            double* __restrict__ W_all, float* __restrict__ W32_all, double* __restrict__ lam_all,
-            double tau) {
-  // the grid covers the capacity; the number of distinct sets is read on the
-  // device so that a captured graph stays valid when it changes
+k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict__ W_all,
+            float* __restrict__ W32_all, double* __restrict__ lam_all, double tau) {
+  // the grid covers every slot; inactive slots (instances that share another
+  // instance's set) return at once, so a captured graph stays valid when an
+  // update changes which instances share
   const int L = blockIdx.x;
-  if (L >= *nl_dev) return;
   const Lset S = lsets[L];
+  if (!S.active) return;
   const int m = S.m;
   const int N = m + (m & 1);  // even player count; index m (if present) is a bye
   const int ld = m + 1;
@@ -165,20 +165,46 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ nl_dev, const int32_t* __re
   for (int k = tid; k < m; k += nt) lam_all[(int64_t)L * kMMax + k] = A[perm[k] * ld + perm[k]];
 }
 
+// Lag tables of a landmark set on its uniform grid.  Every feature value of
+// Section 3 depends on t_i - s_j = k h only (landmarks are grid points), so for
+// k = 0..K the setup stores, in FP64 rounded to float-float,
+//     b0(k) = e,  b1(k) = x e,  b2(k) = u e,   x = k h/sigma, u = x^2, e = exp(-u)
+// (b0, b2 even and b1 odd in k).  kappa of any row is A0 b0 + A1 b1 + A2 b2.
+__global__ void __launch_bounds__(256)
+k_setup_lag(const Lset* __restrict__ lsets, float* __restrict__ lag) {
+  const Lset S = lsets[blockIdx.x];
+  if (!S.active) return;
+  float* T = lag + S.lag_off;
+  for (int k = blockIdx.y * blockDim.x + threadIdx.x; k <= S.K; k += gridDim.y * blockDim.x) {
+    const double x = (double)k * S.hs;
+    const double u = x * x;
+    const double e = exp(-u);
+    const double b[3] = {e, x * e, u * e};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float hi = (float)b[q];
+      T[6 * k + 2 * q] = hi;
+      T[6 * k + 2 * q + 1] = (float)(b[q] - (double)hi);
+    }
+  }
+}
+
 size_t setup_smem_bytes(int m) {
   const int N = m + (m & 1);
   return sizeof(double) * (2 * (size_t)m * (m + 1) + N + 32) + sizeof(int) * (N + 2 * m);
 }
 
-cudaError_t launch_setup(Lset* lsets, const int32_t* nl_dev, int capacity, const int32_t* lm_idx,
-                         double* W, float* W32, double* lam, double tau, int m_max,
-                         cudaStream_t st) {
+cudaError_t launch_setup(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
+                         double* lam, float* lag, double tau, int m_max, cudaStream_t st) {
   if (capacity == 0) return cudaSuccess;
   const size_t sm = setup_smem_bytes(m_max);
   cudaError_t e = cudaFuncSetAttribute(k_setup_eig, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sm);
   if (e != cudaSuccess) return e;
-  k_setup_eig<<<capacity, kSetupThreads, sm, st>>>(lsets, nl_dev, lm_idx, W, W32, lam, tau);
+  k_setup_eig<<<capacity, kSetupThreads, sm, st>>>(lsets, lm_idx, W, W32, lam, tau);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || lag == nullptr) return e;
+  k_setup_lag<<<dim3(capacity, 8), 256, 0, st>>>(lsets, lag);
   return cudaGetLastError();
 }
 

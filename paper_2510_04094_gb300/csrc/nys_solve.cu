@@ -413,36 +413,50 @@ size_t solve_smem_bytes(bool fp32, int m_max) {
 }
 
 // ---------------------------------------------------------------------------
-// K4a: refinement row pass (mixed path).  For each row, FP64-accurate
-// features (float-float argument, exp_neg_accurate, float-float operator
-// coefficients), the residual s_i = r_i - kappa~_i^T z~ in float-float, and
-// the accumulation acc_j += kappa~_ij s_i.  z~ = (W^T omega, b).
+// K4a: refinement row pass (mixed path).  For each row the residual
+//     s_i = r_i - kappa~_i^T z~,   z~ = (W^T omega, b)   (kernel coordinates)
+// with FP64-accurate features, in float-float, then acc_j += kappa~_ij s_i.
+// Features come from the landmark set's lag tables (k_setup_lag): kappa_ij =
+// A0 b0(k) + A1 b1(k) + A2 b2(k), k = i - idx_j.  For constant coefficients
+// (kind LIN) the combination is folded once per work item into a kappa(k)
+// table in shared memory; otherwise (kind TABLE, or a table too large for
+// shared memory) it is formed per entry from the global tables.
 // ---------------------------------------------------------------------------
 constexpr int kRefThreads = 256;
 constexpr int kRefRows = 256;
+constexpr int kRefLagMax = 10000;   // largest K of the shared-memory kappa table
 
-__device__ __forceinline__ ff ff_mul(ff a, ff b) {
-  const float p = a.hi * b.hi;
-  float e = fmaf(a.hi, b.hi, -p);
-  e = fmaf(a.hi, b.lo, e);
-  e = fmaf(a.lo, b.hi, e);
-  const float hi = p + e;
-  return {hi, e - (hi - p)};
+__device__ __forceinline__ ff ff_mul(ff a, ff b) { return ff_mul_ff(a, b); }
+
+// kappa of lag k from the global lag tables and float-float coefficients
+__device__ __forceinline__ ff kappa_lag(const float* __restrict__ T, int K, int k, ff A0, ff A1,
+                                        ff A2) {
+  const int a = k < 0 ? -k : k;
+  if (a > K) return {0.f, 0.f};
+  const float* t = T + 6 * a;
+  ff b1 = {t[2], t[3]};
+  if (k < 0) { b1.hi = -b1.hi; b1.lo = -b1.lo; }
+  ff r = ff_mul(A0, ff{t[0], t[1]});
+  r = ff_add(r, ff_mul(A1, b1));
+  r = ff_add(r, ff_mul(A2, ff{t[4], t[5]}));
+  return r;
 }
 
 __global__ void __launch_bounds__(kRefThreads)
-k_refine_rows(const Inst* __restrict__ insts, const Work* __restrict__ work, int nwork,
+k_refine_rows(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
+              const float* __restrict__ lag, const Work* __restrict__ work, int nwork,
               int* __restrict__ counter, const int32_t* __restrict__ lm_idx,
               const double* __restrict__ tab, const double* __restrict__ zs, int ZS,
               double* __restrict__ part, const int64_t* __restrict__ slot_off,
-              const int32_t* __restrict__ st_all) {
+              const int32_t* __restrict__ st_all, int k_cap) {
+  // k_cap: capacity of the shared-memory kappa table (fixed at launch, so a
+  // graph captured earlier stays safe when an update lengthens the tables)
   extern __shared__ __align__(16) float smr[];
   __shared__ int s_item;
   __shared__ int s_idx[kMMax];
   __shared__ float s_zh[kM1Max], s_zl[kM1Max];
-  __shared__ float s_s[kRefRows];
-  __shared__ float s_rc[kRefRows * 8];
-  __shared__ float s_rlo[kRefRows];
+  __shared__ float s_sh[kRefRows], s_sl[kRefRows];   // residuals (float-float)
+  __shared__ float s_rc[kRefRows * 10];  // per row: A0 A1 A2 w1 r, each as hi/lo
   const int tid = threadIdx.x;
   for (;;) {
     if (tid == 0) s_item = atomicAdd(counter, 1);
@@ -451,87 +465,103 @@ k_refine_rows(const Inst* __restrict__ insts, const Work* __restrict__ work, int
     if (wi >= nwork) break;
     const Work wk = work[wi];
     const Inst I = insts[wk.inst];
-    const int m = I.m, M1 = m + 1;
-    const int ld = M1 | 1;  // odd stride: row-per-thread reads are conflict-free
+    const Lset L = lsets[I.lset];
+    const float* T = lag + L.lag_off;
+    const int m = I.m, M1 = m + 1, K = L.K;
+    const bool folded = (I.kind == NYS_COEF_LIN) && (K <= k_cap);
+    float* khi = smr;
+    float* klo = smr + (2 * K + 1);
     for (int j = tid; j < m; j += kRefThreads) s_idx[j] = lm_idx[I.lm_off + j];
     for (int j = tid; j <= m; j += kRefThreads) {
       const ff z = ff_from_double(zs[(int64_t)wk.inst * ZS + j]);
       s_zh[j] = z.hi;
       s_zl[j] = z.lo;
     }
-    // per-instance constants in float-float
-    const ff hs = ff_from_double(I.hs);
+    const bool skip = (st_all[wk.inst] != NYS_OK);
+    const RowConst RK = row_const(I);
+    if (folded && !skip) {  // constant operator: kappa(k) for k = -K..K
+      for (int t = tid; t <= 2 * K; t += kRefThreads) {
+        const ff kv = kappa_lag(T, K, t - K, RK.A0, RK.A1, RK.A2);
+        khi[t] = kv.hi;
+        klo[t] = kv.lo;
+      }
+    }
     const int S = max(1, kRefThreads / M1);
     const int slice = tid / M1, col = tid - slice * M1;
     const bool cactive = slice < S;
-    float acc = 0.f;
+    const int cidx = (cactive && col < m) ? s_idx[col] : 0;
+    // The sums acc_j = sum_i kappa~_ij s_i cancel almost completely at the
+    // solution (the residual is orthogonal to the features up to the
+    // regularisation), so they are accumulated in float-float.
+    ff acc = {0.f, 0.f};
     __syncthreads();
-    const bool skip = (st_all[wk.inst] != NYS_OK);
-    float* psi = smr;
     for (int base = wk.r0; base < wk.r1 && !skip; base += kRefRows) {
       const int rows = min(kRefRows, wk.r1 - base);
-      // per-row operator coefficients in float-float, r_i, w1
+      // per-row coefficients (float-float)
+      for (int r = tid; r < rows; r += kRefThreads) {
+        ff c5[5];
+        row_coef_ff(I, RK, tab, base + r, c5);
+        float* rc = s_rc + r * 10;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) { rc[2 * q] = c5[q].hi; rc[2 * q + 1] = c5[q].lo; }
+      }
+      __syncthreads();
+      // residual of each row, one row per thread
       for (int r = tid; r < rows; r += kRefThreads) {
         const int i = base + r;
-        double f1, f2, rr;
-        coef_f(I, tab, i, f1, f2, rr);
-        const RowCoef R = row_coef_from_f(I, f1, f2, rr);
-        const ff a0 = ff_from_double(R.A0), a1 = ff_from_double(R.A1), a2 = ff_from_double(R.A2);
-        const ff rv = (I.kind == NYS_COEF_LIN) ? ff{lin_rhs_ff(I, i), 0.f} : ff_from_double(rr);
-        float* rc = s_rc + r * 8;
-        rc[0] = a0.hi; rc[1] = a0.lo; rc[2] = a1.hi; rc[3] = a1.lo;
-        rc[4] = a2.hi; rc[5] = a2.lo; rc[6] = (float)R.w1; rc[7] = rv.hi;
-        s_rlo[r] = rv.lo;
-      }
-      __syncthreads();
-      // FP64-accurate features of the tile
-      for (int e = tid; e < rows * M1; e += kRefThreads) {
-        const int r = e / M1, j = e - r * M1;
-        const int i = base + r;
-        const float* rc = s_rc + r * 8;
-        float val;
-        if (j < m) {
-          const float kf = (float)(i - s_idx[j]);
-          // x = k hs and u = x^2 in float-float
-          const float xh = kf * hs.hi;
-          const float xl = fmaf(kf, hs.hi, -xh) + kf * hs.lo;
-          const float uh = xh * xh;
-          const float ul = fmaf(xh, xh, -uh) + 2.f * xh * xl;
-          const float ex = exp_neg_accurate(uh, ul);
-          ff P = ff{rc[0], rc[1]};
-          P = ff_add(P, ff_mul(ff{rc[2], rc[3]}, ff{xh, xl}));
-          P = ff_add(P, ff_mul(ff{rc[4], rc[5]}, ff{uh, ul}));
-          val = ex * (P.hi + P.lo);
-        } else {
-          val = rc[6];
+        const float* rc = s_rc + r * 10;
+        ff sres = {rc[8], rc[9]};
+        const ff A0 = {rc[0], rc[1]}, A1 = {rc[2], rc[3]}, A2 = {rc[4], rc[5]};
+        for (int j = 0; j < m; ++j) {
+          const int k = i - s_idx[j];
+          ff kv;
+          if (folded) {
+            const int t = k + K;
+            kv = (t >= 0 && t <= 2 * K) ? ff{khi[t], klo[t]} : ff{0.f, 0.f};
+          } else {
+            kv = kappa_lag(T, K, k, A0, A1, A2);
+          }
+          const ff pz = ff_mul(kv, ff{s_zh[j], s_zl[j]});
+          sres = ff_add(sres, ff{-pz.hi, -pz.lo});
         }
-        psi[r * ld + j] = val;
+        const ff pb = ff_mul(ff{rc[6], rc[7]}, ff{s_zh[m], s_zl[m]});
+        sres = ff_add(sres, ff{-pb.hi, -pb.lo});
+        s_sh[r] = sres.hi;
+        s_sl[r] = sres.lo;
       }
       __syncthreads();
-      // residual s_i = r_i - kappa~_i^T z~ in float-float, one row per thread
-      for (int r = tid; r < rows; r += kRefThreads) {
-        ff acc_s = {s_rc[r * 8 + 7], s_rlo[r]};
-        for (int j = 0; j <= m; ++j) {
-          const float kv = -psi[r * ld + j];
-          acc_s = ff_fma_f(kv, ff{s_zh[j], s_zl[j]}, acc_s);
-        }
-        s_s[r] = acc_s.hi + acc_s.lo;
-      }
-      __syncthreads();
+      // acc_j += kappa~_ij s_i  (column per thread, rows split in S slices)
       if (cactive) {
-        for (int r = slice; r < rows; r += S) acc = fmaf(psi[r * ld + col], s_s[r], acc);
+        for (int r = slice; r < rows; r += S) {
+          const int i = base + r;
+          const float* rc = s_rc + r * 10;
+          ff kv;
+          if (col == m) {
+            kv = ff{rc[6], rc[7]};
+          } else if (folded) {
+            const int t = i - cidx + K;
+            kv = (t >= 0 && t <= 2 * K) ? ff{khi[t], klo[t]} : ff{0.f, 0.f};
+          } else {
+            kv = kappa_lag(T, K, i - cidx, ff{rc[0], rc[1]}, ff{rc[2], rc[3]}, ff{rc[4], rc[5]});
+          }
+          acc = ff_add(acc, ff_mul(kv, ff{s_sh[r], s_sl[r]}));
+        }
       }
       __syncthreads();
     }
-    // sum slices, write the partial (M1 doubles)
+    // sum the slices in FP64, write the partial (M1 doubles)
     float* red = smr;
-    if (cactive) red[slice * M1 + col] = acc;
+    __syncthreads();
+    if (cactive) {
+      red[2 * (slice * M1 + col)] = acc.hi;
+      red[2 * (slice * M1 + col) + 1] = acc.lo;
+    }
     __syncthreads();
     double* out = part + slot_off[wk.slot];
     for (int j = tid; j < M1; j += kRefThreads) {
-      float s = 0.f;
-      for (int q = 0; q < S; ++q) s += red[q * M1 + j];
-      out[j] = skip ? 0.0 : (double)s;
+      double sum = 0.0;
+      for (int q = 0; q < S; ++q) sum += (double)red[2 * (q * M1 + j)] + (double)red[2 * (q * M1 + j) + 1];
+      out[j] = skip ? 0.0 : sum;
     }
     __syncthreads();
   }
@@ -615,11 +645,11 @@ k_refine_update(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   }
 }
 
-size_t refine_smem_bytes(int m_max) {
-  const int M1 = m_max + 1;
-  const size_t tile = sizeof(float) * (size_t)kRefRows * (M1 | 1);
-  const size_t red = sizeof(float) * (size_t)kRefThreads * 2;
-  return tile > red ? tile : red;
+size_t refine_smem_bytes(int k_max) {
+  const int K = k_max < kRefLagMax ? k_max : kRefLagMax;
+  const size_t table = sizeof(float) * 2 * (size_t)(2 * K + 1);
+  const size_t red = sizeof(float) * (size_t)kRefThreads * 2 + 64;
+  return table > red ? table : red;
 }
 
 // ---- launchers --------------------------------------------------------------
@@ -646,20 +676,21 @@ cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const 
   return cudaGetLastError();
 }
 
-cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W, const Work* work,
-                          int nwork, int* counter, const int32_t* lm, const double* tab,
-                          double* part, const int64_t* slot_off, const void* fac, int64_t facs,
-                          double* xs, double* zs, const double* cws, int XS, int ZS, int M1S,
-                          int32_t* st, double gamma_scale, int batch, int m_max, int num_sms,
-                          cudaStream_t s) {
+cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W, const float* lag,
+                          const Work* work, int nwork, int* counter, const int32_t* lm,
+                          const double* tab, double* part, const int64_t* slot_off,
+                          const void* fac, int64_t facs, double* xs, double* zs, const double* cws,
+                          int XS, int ZS, int M1S, int32_t* st, double gamma_scale, int batch,
+                          int m_max, int k_max, int num_sms, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  const size_t sm = refine_smem_bytes(m_max);
+  const int k_cap = k_max < kRefLagMax ? k_max : kRefLagMax;
+  const size_t sm = refine_smem_bytes(k_cap);
   e = cudaFuncSetAttribute(k_refine_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   const int grid = min(nwork, num_sms * 2);
-  k_refine_rows<<<grid, kRefThreads, sm, s>>>(insts, work, nwork, counter, lm, tab, zs, ZS, part,
-                                               slot_off, st);
+  k_refine_rows<<<grid, kRefThreads, sm, s>>>(insts, lsets, lag, work, nwork, counter, lm, tab, zs,
+                                               ZS, part, slot_off, st, k_cap);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_refine_update<float><<<batch, kSolveThreads, 0, s>>>(insts, lsets, W, part, slot_off,
