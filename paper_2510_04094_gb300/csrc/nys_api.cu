@@ -16,9 +16,13 @@ namespace nys {
 // kernel launchers (defined in the other translation units)
 cudaError_t launch_setup(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
                          double* lam, float* lag, double tau, int m_max, cudaStream_t st);
-cudaError_t launch_assemble(bool fp32, const Inst* insts, const Work* work, int nwork,
-                            int* counter, const int32_t* lm, const double* tab, double* part,
-                            const int64_t* slot_off, int m_max, int num_sms, cudaStream_t st);
+cudaError_t launch_lag(const Lset* lsets, int capacity, float* lag, cudaStream_t st);
+cudaError_t launch_eig(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
+                       double* lam, double tau, int m_max, cudaStream_t st);
+cudaError_t launch_assemble(bool fp32, const Inst* insts, const Lset* lsets, const float* lag,
+                            const Work* work, int nwork, int* counter, const int32_t* lm,
+                            const double* tab, double* part, const int64_t* slot_off, int m_max,
+                            int k_max, int num_sms, cudaStream_t st);
 cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const double* W,
                          const float* W32, const double* part, const int64_t* slot_off,
                          const int32_t* lm, void* fac, int64_t facs, double* xs, double* zs,
@@ -34,7 +38,7 @@ cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W,
 cudaError_t launch_eval(const Inst* insts, const double* zs, int ZS, const int32_t* lm,
                         const double* tq, const int64_t* tq_off, int deriv, double* yq, int batch,
                         cudaStream_t s);
-size_t asm_smem_bytes(bool fp32, int m_max);
+
 int64_t fac_elems(int m_max);
 }  // namespace nys
 
@@ -281,12 +285,16 @@ static cudaError_t enqueue_factor(nys_ctx* c, cudaStream_t s) {
                       c->opt.eig_tau > 0 ? c->opt.eig_tau : 1e-12, c->m_max, s);
 }
 
-// Fork the Nystrom setup onto the side stream: the row pass works in kernel
-// coordinates and does not need W, so the two overlap; the solve joins.
+// The lag tables (read by the row passes) go on the caller's stream; the
+// eigendecomposition is forked onto the side stream: the row pass works in
+// kernel coordinates and does not need W, so the two overlap; the solve joins.
 static cudaError_t fork_factor(nys_ctx* c, cudaStream_t s) {
-  cudaError_t e = cudaEventRecord(c->ev_fork, s);
+  cudaError_t e = launch_lag(c->lset.p, c->batch, c->lag.p, s);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev_fork, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
-  if (e == cudaSuccess) e = enqueue_factor(c, c->side);
+  if (e == cudaSuccess)
+    e = launch_eig(c->lset.p, c->batch, c->lm.p, c->W.p, c->W32.p, c->lam.p,
+                   c->opt.eig_tau > 0 ? c->opt.eig_tau : 1e-12, c->m_max, c->side);
   if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
   return e;
 }
@@ -534,8 +542,9 @@ int32_t nys_assemble(nys_ctx* c, void* stream) {
     c->factor_stale = false;
     c->join_pending = true;
   }
-  CK(launch_assemble(c->fp32, c->inst.p, c->work.p, c->nwork, c->counter.p, c->lm.p, c->tab.p,
-                     c->part.p, c->slot_off.p, c->m_max, c->num_sms, (cudaStream_t)stream));
+  CK(launch_assemble(c->fp32, c->inst.p, c->fp32 ? c->lset.p : nullptr, c->lag.p, c->work.p,
+                     c->nwork, c->counter.p, c->lm.p, c->tab.p, c->part.p, c->slot_off.p, c->m_max,
+                     c->k_max, c->num_sms, (cudaStream_t)stream));
   c->assembled = true;
   return NYS_OK;
 }
@@ -589,9 +598,9 @@ int32_t nys_run(nys_ctx* c, void* stream, double* x_out, int32_t* status_out) {
     {
       cudaError_t e2 = fork_factor(c, cs);
       if (e2 == cudaSuccess)
-        e2 = launch_assemble(c->fp32, c->inst.p, c->work.p, c->nwork, c->counter.p,
-                                       c->lm.p, c->tab.p, c->part.p, c->slot_off.p, c->m_max,
-                                       c->num_sms, cs);
+        e2 = launch_assemble(c->fp32, c->inst.p, c->fp32 ? c->lset.p : nullptr, c->lag.p,
+                             c->work.p, c->nwork, c->counter.p, c->lm.p, c->tab.p, c->part.p,
+                             c->slot_off.p, c->m_max, c->k_max, c->num_sms, cs);
       if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(cs, c->ev_join, 0);
       if (e2 != cudaSuccess) r = fail(NYS_ECUDA, "capture: assemble: %s", cudaGetErrorString(e2));
       if (r == NYS_OK) r = solve_impl(c, cs, x_out, status_out);

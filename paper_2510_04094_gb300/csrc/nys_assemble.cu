@@ -116,24 +116,31 @@ k_assemble_f64(const Inst* __restrict__ insts, const Work* __restrict__ work, in
 // FP32 variant (mixed-precision path).  The Gram is tiled in 8 x 8 register
 // blocks of the upper triangle (U = NB (NB+1)/2 blocks, NB = MP/8); S row
 // slices of U threads each split the rows of a tile, every thread running a
-// plain FP32 FMA accumulation of its 64 entries over its rows.  The S slice
+// plain FP32 FMA accumulation of its 64 entries over its rows (operands for
+// the next row are loaded while the current row's 64 FMAs issue).  The S slice
 // sums are added at the end of the work item and stored as doubles.  The
 // accumulation error is removed later by FP64-accurate refinement.
+// Features are evaluated per entry with the MUFU exponential (measured faster
+// here than filling the tile from a lag table in shared memory, whose lookups
+// across landmark columns conflict in the banks).
 // ---------------------------------------------------------------------------
 constexpr int kAsm32Threads = 384;
-constexpr int kAsm32Rows = 128;
-constexpr int kPadF = 4;  // row padding of the psi tile (floats)
+constexpr int kAsm32Rows = 256;
+constexpr int kPadF = 4;          // row padding of the psi tile (floats)
 
 __global__ void __launch_bounds__(kAsm32Threads, 1)
-k_assemble_f32(const Inst* __restrict__ insts, const Work* __restrict__ work, int nwork,
+k_assemble_f32(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
+               const float* __restrict__ lag, const Work* __restrict__ work, int nwork,
                int* __restrict__ counter, const int32_t* __restrict__ lm_idx,
                const double* __restrict__ tab, double* __restrict__ part,
-               const int64_t* __restrict__ slot_off) {
+               const int64_t* __restrict__ slot_off, int tile_floats, int k_cap) {
   extern __shared__ __align__(16) float sm32[];
   __shared__ int s_item;
   __shared__ int s_idx[kMMax];
   __shared__ float s_rc[kAsm32Rows][5];
   const int tid = threadIdx.x;
+  float* psi = sm32;
+  (void)lsets; (void)lag; (void)tile_floats; (void)k_cap;
 
   for (;;) {
     if (tid == 0) s_item = atomicAdd(counter, 1);
@@ -147,6 +154,7 @@ k_assemble_f32(const Inst* __restrict__ insts, const Work* __restrict__ work, in
     const int S = max(1, kAsm32Threads / U);
     const int ld = MP + kPadF;
     for (int j = tid; j < m; j += kAsm32Threads) s_idx[j] = lm_idx[I.lm_off + j];
+    const RowConst RK = row_const(I);
 
     // this thread's block (bj <= bl) and slice
     const bool active = tid < U * S;
@@ -161,31 +169,28 @@ k_assemble_f32(const Inst* __restrict__ insts, const Work* __restrict__ work, in
     const int RS = kAsm32Threads / MP;
     const int fj = tid % MP, fr0 = tid / MP;
     const float hs = (float)I.hs;
-    const RowConst RK = row_const(I);
 
     float acc[64];
 #pragma unroll
     for (int k = 0; k < 64; ++k) acc[k] = 0.f;
     __syncthreads();
+    const int sidx = (fj < m) ? s_idx[fj] : 0;
 
-    float* psi = sm32;
     for (int base = wk.r0; base < wk.r1; base += kAsm32Rows) {
-      if (tid < kAsm32Rows) {
-        const int i = base + tid;
-        if (i < wk.r1) {
-          ff c5[5];
-          row_coef_ff(I, RK, tab, i, c5);
+      const int rows = min(kAsm32Rows, wk.r1 - base);
+      // per-row quantities, one row per thread (r(t_i) needs a sine per row)
+      if (tid < rows) {
+        ff c5[5];
+        row_coef_ff(I, RK, tab, base + tid, c5);
 #pragma unroll
-          for (int q = 0; q < 5; ++q) s_rc[tid][q] = c5[q].hi;
-        }
+        for (int q = 0; q < 5; ++q) s_rc[tid][q] = c5[q].hi;
       }
       __syncthreads();
       if (fr0 < RS) {
-        const int sidx = (fj < m) ? s_idx[fj] : 0;
         for (int r = fr0; r < kAsm32Rows; r += RS) {
           const int i = base + r;
           float val = 0.f;
-          if (i < wk.r1 && fj < M2) {
+          if (r < rows && fj < M2) {
             if (fj < m) {
               const float x = (float)(i - sidx) * hs;
               const float uu = x * x;
@@ -198,27 +203,39 @@ k_assemble_f32(const Inst* __restrict__ insts, const Work* __restrict__ work, in
         }
       }
       __syncthreads();
-      if (active) {
-        const int rows = min(kAsm32Rows, wk.r1 - base);
+      if (active && slice < rows) {
         const float* pa = psi + 8 * bj;
         const float* pb = psi + 8 * bl;
-        for (int r = slice; r < rows; r += S) {
-          const float4 a0 = *reinterpret_cast<const float4*>(pa + r * ld);
-          const float4 a1 = *reinterpret_cast<const float4*>(pa + r * ld + 4);
-          const float4 b0 = *reinterpret_cast<const float4*>(pb + r * ld);
-          const float4 b1 = *reinterpret_cast<const float4*>(pb + r * ld + 4);
+        int r = slice;
+        float4 a0 = *reinterpret_cast<const float4*>(pa + r * ld);
+        float4 a1 = *reinterpret_cast<const float4*>(pa + r * ld + 4);
+        float4 b0 = *reinterpret_cast<const float4*>(pb + r * ld);
+        float4 b1 = *reinterpret_cast<const float4*>(pb + r * ld + 4);
+        for (;;) {
+          const int rn = r + S;
+          const bool more = rn < rows;
+          float4 na0, na1, nb0, nb1;
+          if (more) {
+            na0 = *reinterpret_cast<const float4*>(pa + rn * ld);
+            na1 = *reinterpret_cast<const float4*>(pa + rn * ld + 4);
+            nb0 = *reinterpret_cast<const float4*>(pb + rn * ld);
+            nb1 = *reinterpret_cast<const float4*>(pb + rn * ld + 4);
+          }
           const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
           const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
           for (int x = 0; x < 8; ++x)
 #pragma unroll
             for (int y = 0; y < 8; ++y) acc[x * 8 + y] = fmaf(av[x], bv[y], acc[x * 8 + y]);
+          if (!more) break;
+          a0 = na0; a1 = na1; b0 = nb0; b1 = nb1;
+          r = rn;
         }
       }
       __syncthreads();
     }
     // add the S slice sums (FP32) and store the packed upper triangle as doubles
-    float* red = sm32;  // S * U * 64 floats <= 384 * 64
+    float* red = sm32;  // S * U * 64 floats <= 384 * 64 (the tile and table are dead)
     if (active) {
 #pragma unroll
       for (int k = 0; k < 64; ++k) red[(slice * U + u) * 64 + k] = acc[k];
@@ -233,19 +250,22 @@ k_assemble_f32(const Inst* __restrict__ insts, const Work* __restrict__ work, in
       const int cb = j >> 3, lb = l >> 3;
       const int ub = cb * NB - cb * (cb - 1) / 2 + (lb - cb);
       const int k = (j & 7) * 8 + (l & 7);
-      float s = 0.f;
-      for (int q = 0; q < S; ++q) s += red[(q * U + ub) * 64 + k];
-      out[e] = (double)s;
+      float sum = 0.f;
+      for (int q = 0; q < S; ++q) sum += red[(q * U + ub) * 64 + k];
+      out[e] = (double)sum;
     }
     __syncthreads();
   }
 }
 
-size_t asm_smem_bytes(bool fp32, int m_max) {
+static int asm32_tile_floats(int m_max) {
+  return kAsm32Rows * (round_up(m_max + 2, 8) + kPadF);
+}
+
+size_t asm_smem_bytes(bool fp32, int m_max, int k_cap) {
   const int M2 = m_max + 2;
   if (fp32) {
-    const int MP = round_up(M2, 8);
-    const size_t tile = sizeof(float) * (size_t)kAsm32Rows * (MP + kPadF);
+    const size_t tile = sizeof(float) * ((size_t)asm32_tile_floats(m_max) + 2 * (size_t)k_cap + 1);
     const size_t red = sizeof(float) * (size_t)kAsm32Threads * 64;
     return tile > red ? tile : red;
   }
@@ -264,18 +284,22 @@ static cudaError_t launch64(const Inst* insts, const Work* work, int nwork, int*
   return cudaGetLastError();
 }
 
-cudaError_t launch_assemble(bool fp32, const Inst* insts, const Work* work, int nwork,
-                            int* counter, const int32_t* lm, const double* tab, double* part,
-                            const int64_t* slot_off, int m_max, int num_sms, cudaStream_t st) {
+cudaError_t launch_assemble(bool fp32, const Inst* insts, const Lset* lsets, const float* lag,
+                            const Work* work, int nwork, int* counter, const int32_t* lm,
+                            const double* tab, double* part, const int64_t* slot_off, int m_max,
+                            int k_max, int num_sms, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  const size_t sm = asm_smem_bytes(fp32, m_max);
+  // k_cap: capacity of the shared-memory kappa table, fixed at launch (an update
+  // that lengthens the lag tables makes those instances use computed features)
+  const int k_cap = 0;  // features are computed, no table in shared memory
+  const size_t sm = asm_smem_bytes(fp32, m_max, k_cap);
   if (fp32) {
     e = cudaFuncSetAttribute(k_assemble_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const int grid = min(nwork, num_sms);
-    k_assemble_f32<<<grid, kAsm32Threads, sm, st>>>(insts, work, nwork, counter, lm, tab, part,
-                                                    slot_off);
+    k_assemble_f32<<<grid, kAsm32Threads, sm, st>>>(insts, lsets, lag, work, nwork, counter, lm, tab,
+                                                    part, slot_off, asm32_tile_floats(m_max), k_cap);
     return cudaGetLastError();
   }
   const int M2 = m_max + 2, E = M2 * (M2 + 1) / 2;

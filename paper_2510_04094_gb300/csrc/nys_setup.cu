@@ -194,18 +194,29 @@ size_t setup_smem_bytes(int m) {
   return sizeof(double) * (2 * (size_t)m * (m + 1) + N + 32) + sizeof(int) * (N + 2 * m);
 }
 
-cudaError_t launch_setup(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
-                         double* lam, float* lag, double tau, int m_max, cudaStream_t st) {
+// The lag tables feed the row passes; the eigendecomposition only the solve.
+cudaError_t launch_lag(const Lset* lsets, int capacity, float* lag, cudaStream_t st) {
+  if (capacity == 0 || lag == nullptr) return cudaSuccess;
+  k_setup_lag<<<dim3(capacity, 8), 256, 0, st>>>(lsets, lag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eig(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
+                       double* lam, double tau, int m_max, cudaStream_t st) {
   if (capacity == 0) return cudaSuccess;
   const size_t sm = setup_smem_bytes(m_max);
   cudaError_t e = cudaFuncSetAttribute(k_setup_eig, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sm);
   if (e != cudaSuccess) return e;
   k_setup_eig<<<capacity, kSetupThreads, sm, st>>>(lsets, lm_idx, W, W32, lam, tau);
-  e = cudaGetLastError();
-  if (e != cudaSuccess || lag == nullptr) return e;
-  k_setup_lag<<<dim3(capacity, 8), 256, 0, st>>>(lsets, lag);
   return cudaGetLastError();
+}
+
+cudaError_t launch_setup(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
+                         double* lam, float* lag, double tau, int m_max, cudaStream_t st) {
+  cudaError_t e = launch_lag(lsets, capacity, lag, st);
+  if (e != cudaSuccess) return e;
+  return launch_eig(lsets, capacity, lm_idx, W, W32, lam, tau, m_max, st);
 }
 
 }  // namespace nys

@@ -442,6 +442,28 @@ __device__ __forceinline__ ff kappa_lag(const float* __restrict__ T, int K, int 
   return r;
 }
 
+// acc += a * b for float-float a, b: exact leading product by FMA, TwoSum on
+// the high parts, everything else gathered in the low part (renormalised by
+// the caller at the end).
+__device__ __forceinline__ void ff_acc_mul(ff& acc, ff a, ff b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const float s = acc.hi + p;
+  const float bb = s - acc.hi;
+  const float err = (acc.hi - (s - bb)) + (p - bb);
+  acc.hi = s;
+  acc.lo += err + e;
+}
+__device__ __forceinline__ ff ff_norm(ff a) {
+  const float hi = a.hi + a.lo;
+  return {hi, a.lo - (hi - a.hi)};
+}
+
+constexpr int kRefWarps = kRefThreads / 32;
+constexpr int kRefColsPerWarp = (kM1Max + kRefWarps - 1) / kRefWarps;   // 15
+
 __global__ void __launch_bounds__(kRefThreads)
 k_refine_rows(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
               const float* __restrict__ lag, const Work* __restrict__ work, int nwork,
@@ -457,7 +479,7 @@ k_refine_rows(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   __shared__ float s_zh[kM1Max], s_zl[kM1Max];
   __shared__ float s_sh[kRefRows], s_sl[kRefRows];   // residuals (float-float)
   __shared__ float s_rc[kRefRows * 10];  // per row: A0 A1 A2 w1 r, each as hi/lo
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (;;) {
     if (tid == 0) s_item = atomicAdd(counter, 1);
     __syncthreads();
@@ -467,7 +489,7 @@ k_refine_rows(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     const Inst I = insts[wk.inst];
     const Lset L = lsets[I.lset];
     const float* T = lag + L.lag_off;
-    const int m = I.m, M1 = m + 1, K = L.K;
+    const int m = I.m, K = L.K;
     const bool folded = (I.kind == NYS_COEF_LIN) && (K <= k_cap);
     float* khi = smr;
     float* klo = smr + (2 * K + 1);
@@ -486,14 +508,13 @@ k_refine_rows(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         klo[t] = kv.lo;
       }
     }
-    const int S = max(1, kRefThreads / M1);
-    const int slice = tid / M1, col = tid - slice * M1;
-    const bool cactive = slice < S;
-    const int cidx = (cactive && col < m) ? s_idx[col] : 0;
     // The sums acc_j = sum_i kappa~_ij s_i cancel almost completely at the
     // solution (the residual is orthogonal to the features up to the
-    // regularisation), so they are accumulated in float-float.
-    ff acc = {0.f, 0.f};
+    // regularisation), so they are accumulated in float-float.  Warp w owns
+    // columns j = w, w + 8, ...; its lanes walk the rows.
+    ff acc[kRefColsPerWarp];
+#pragma unroll
+    for (int q = 0; q < kRefColsPerWarp; ++q) acc[q] = {0.f, 0.f};
     __syncthreads();
     for (int base = wk.r0; base < wk.r1 && !skip; base += kRefRows) {
       const int rows = min(kRefRows, wk.r1 - base);
@@ -506,13 +527,23 @@ k_refine_rows(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         for (int q = 0; q < 5; ++q) { rc[2 * q] = c5[q].hi; rc[2 * q + 1] = c5[q].lo; }
       }
       __syncthreads();
-      // residual of each row, one row per thread
+      // residual of each row, one row per thread: s = r - kappa~^T z~
       for (int r = tid; r < rows; r += kRefThreads) {
         const int i = base + r;
         const float* rc = s_rc + r * 10;
-        ff sres = {rc[8], rc[9]};
         const ff A0 = {rc[0], rc[1]}, A1 = {rc[2], rc[3]}, A2 = {rc[4], rc[5]};
-        for (int j = 0; j < m; ++j) {
+        ff sp = {0.f, 0.f};   // sum of kappa~ z~ (subtracted at the end)
+        // kappa vanishes beyond lag K: only landmarks with |i - idx_j| <= K count
+        int jlo = 0, jhi = m;
+        {
+          int a = 0, b = m;           // first j with idx_j >= i - K
+          while (a < b) { const int c = (a + b) >> 1; if (s_idx[c] < i - K) a = c + 1; else b = c; }
+          jlo = a;
+          b = m;                      // first j with idx_j > i + K
+          while (a < b) { const int c = (a + b) >> 1; if (s_idx[c] <= i + K) a = c + 1; else b = c; }
+          jhi = a;
+        }
+        for (int j = jlo; j < jhi; ++j) {
           const int k = i - s_idx[j];
           ff kv;
           if (folded) {
@@ -521,47 +552,53 @@ k_refine_rows(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
           } else {
             kv = kappa_lag(T, K, k, A0, A1, A2);
           }
-          const ff pz = ff_mul(kv, ff{s_zh[j], s_zl[j]});
-          sres = ff_add(sres, ff{-pz.hi, -pz.lo});
+          ff_acc_mul(sp, kv, ff{s_zh[j], s_zl[j]});
         }
-        const ff pb = ff_mul(ff{rc[6], rc[7]}, ff{s_zh[m], s_zl[m]});
-        sres = ff_add(sres, ff{-pb.hi, -pb.lo});
+        ff_acc_mul(sp, ff{rc[6], rc[7]}, ff{s_zh[m], s_zl[m]});
+        sp = ff_norm(sp);
+        const ff sres = ff_add(ff{rc[8], rc[9]}, ff{-sp.hi, -sp.lo});
         s_sh[r] = sres.hi;
         s_sl[r] = sres.lo;
       }
       __syncthreads();
-      // acc_j += kappa~_ij s_i  (column per thread, rows split in S slices)
-      if (cactive) {
-        for (int r = slice; r < rows; r += S) {
-          const int i = base + r;
-          const float* rc = s_rc + r * 10;
-          ff kv;
-          if (col == m) {
-            kv = ff{rc[6], rc[7]};
-          } else if (folded) {
-            const int t = i - cidx + K;
-            kv = (t >= 0 && t <= 2 * K) ? ff{khi[t], klo[t]} : ff{0.f, 0.f};
-          } else {
-            kv = kappa_lag(T, K, i - cidx, ff{rc[0], rc[1]}, ff{rc[2], rc[3]}, ff{rc[4], rc[5]});
+      // acc_j += kappa~_ij s_i: lanes over rows (conflict-free table reads)
+#pragma unroll
+      for (int q = 0; q < kRefColsPerWarp; ++q) {
+        const int j = warp + q * kRefWarps;
+        if (j <= m) {
+          const int cj = (j < m) ? s_idx[j] : 0;
+          // rows within lag K of landmark j (all rows for the b column)
+          const int rlo = (j < m) ? max(0, cj - K - base) : 0;
+          const int rhi = (j < m) ? min(rows, cj + K + 1 - base) : rows;
+          for (int r = rlo + lane; r < rhi; r += 32) {
+            const int i = base + r;
+            const float* rc = s_rc + r * 10;
+            ff kv;
+            if (j == m) {
+              kv = ff{rc[6], rc[7]};
+            } else if (folded) {
+              const int t = i - cj + K;
+              kv = (t >= 0 && t <= 2 * K) ? ff{khi[t], klo[t]} : ff{0.f, 0.f};
+            } else {
+              kv = kappa_lag(T, K, i - cj, ff{rc[0], rc[1]}, ff{rc[2], rc[3]}, ff{rc[4], rc[5]});
+            }
+            ff_acc_mul(acc[q], kv, ff{s_sh[r], s_sl[r]});
           }
-          acc = ff_add(acc, ff_mul(kv, ff{s_sh[r], s_sl[r]}));
         }
       }
       __syncthreads();
     }
-    // sum the slices in FP64, write the partial (M1 doubles)
-    float* red = smr;
-    __syncthreads();
-    if (cactive) {
-      red[2 * (slice * M1 + col)] = acc.hi;
-      red[2 * (slice * M1 + col) + 1] = acc.lo;
-    }
-    __syncthreads();
+    // reduce over lanes (float-float), write the partial (M1 doubles)
     double* out = part + slot_off[wk.slot];
-    for (int j = tid; j < M1; j += kRefThreads) {
-      double sum = 0.0;
-      for (int q = 0; q < S; ++q) sum += (double)red[2 * (q * M1 + j)] + (double)red[2 * (q * M1 + j) + 1];
-      out[j] = skip ? 0.0 : sum;
+#pragma unroll
+    for (int q = 0; q < kRefColsPerWarp; ++q) {
+      const int j = warp + q * kRefWarps;
+      ff a = ff_norm(acc[q]);
+      for (int o = 16; o > 0; o >>= 1) {
+        const ff b = {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+        a = ff_add(a, b);
+      }
+      if (lane == 0 && j <= m) out[j] = skip ? 0.0 : (double)a.hi + (double)a.lo;
     }
     __syncthreads();
   }
@@ -688,7 +725,10 @@ cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W,
   const size_t sm = refine_smem_bytes(k_cap);
   e = cudaFuncSetAttribute(k_refine_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  const int grid = min(nwork, num_sms * 2);
+  // as many co-resident CTAs as registers and shared memory allow
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_refine_rows, kRefThreads, sm);
+  const int grid = min(nwork, num_sms * max(1, per_sm));
   k_refine_rows<<<grid, kRefThreads, sm, s>>>(insts, lsets, lag, work, nwork, counter, lm, tab, zs,
                                                ZS, part, slot_off, st, k_cap);
   e = cudaGetLastError();
