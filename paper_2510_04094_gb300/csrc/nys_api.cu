@@ -94,7 +94,7 @@ struct GraphKey {
 };
 
 struct nys_ctx {
-  int batch = 0, m_max = 0, p_max = 0, num_sms = 0, nwork = 0, nlset = 0;
+  int batch = 0, m_max = 0, p_max = 0, num_sms = 0, nwork = 0, nrwork = 0, nlset = 0;
   int XS = 0, ZS = 0, M1S = 0;
   int64_t facs = 0;
   nys_options opt{};
@@ -117,8 +117,8 @@ struct nys_ctx {
   DBuf<Lset> lset;
   DBuf<int32_t> lm;
   DBuf<double> tab;
-  DBuf<Work> work;
-  DBuf<int64_t> slot_off;
+  DBuf<Work> work, rwork;
+  DBuf<int64_t> slot_off;   // assembly slots first, then refinement slots
   DBuf<double> part;
   DBuf<double> W;
   DBuf<float> W32;
@@ -352,7 +352,7 @@ void nys_destroy(nys_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
-  c->inst.release(); c->lset.release(); c->lm.release(); c->tab.release(); c->work.release();
+  c->inst.release(); c->lset.release(); c->lm.release(); c->tab.release(); c->work.release(); c->rwork.release();
   c->slot_off.release(); c->part.release(); c->W.release(); c->W32.release(); c->lam.release();
   c->fac.release(); c->lag.release(); c->xs.release(); c->zs.release(); c->dzs.release(); c->cws.release();
   c->st.release(); c->stinit.release(); c->counter.release(); c->yaux.release(); c->rowstate.release();
@@ -420,14 +420,16 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   for (int b = 0; b < batch; ++b) total_rows += q[b].n - 1;
   c->total_rows = total_rows;
   const int64_t target = std::max<int64_t>(batch, 4LL * c->num_sms);
-  const int64_t rpi = std::max<int64_t>(64, (total_rows + target - 1) / target);
+  int64_t rpi = std::max<int64_t>(64, (total_rows + target - 1) / target);
+  // FP32 row pass: chunks of at most 1024 rows, whose landmark windows are narrow
+  if (c->fp32) rpi = std::min<int64_t>(rpi, 1024);
   int64_t poff = 0;
   int slot = 0;
   for (int b = 0; b < batch; ++b) {
     const int nrows = q[b].n - 1;
     const int chunks = (int)std::max<int64_t>(1, (nrows + rpi - 1) / rpi);
     const int M2 = q[b].m + 2;
-    const int64_t E = (int64_t)M2 * (M2 + 1) / 2;
+    const int64_t E = (int64_t)M2 * (M2 + 1) / 2 + 2;   // + [first landmark, count]
     c->h_inst[b].slot_begin = slot;
     c->h_inst[b].slot_count = chunks;
     for (int k = 0; k < chunks; ++k) {
@@ -441,12 +443,37 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
       poff += E;
     }
   }
-  std::stable_sort(wl.begin(), wl.end(), [&](const Work& a, const Work& b2) {
+  // refinement work list: balance rule only (its per-item setup, a lag table
+  // per instance, favours long chunks); slots of M1 doubles after the others
+  std::vector<Work> rwl;
+  {
+    const int64_t rpr = std::max<int64_t>(64, (total_rows + target - 1) / target);
+    for (int b = 0; b < batch; ++b) {
+      const int nrows = q[b].n - 1;
+      const int chunks = (int)std::max<int64_t>(1, (nrows + rpr - 1) / rpr);
+      c->h_inst[b].rslot_begin = slot;
+      c->h_inst[b].rslot_count = chunks;
+      for (int k = 0; k < chunks; ++k) {
+        Work w;
+        w.inst = b;
+        w.r0 = 1 + (int)((int64_t)nrows * k / chunks);
+        w.r1 = 1 + (int)((int64_t)nrows * (k + 1) / chunks);
+        w.slot = slot++;
+        rwl.push_back(w);
+        soff.push_back(poff);
+        poff += q[b].m + 1;
+      }
+    }
+  }
+  auto by_cost = [&](const Work& a, const Work& b2) {
     const double ca = (double)(a.r1 - a.r0) * (q[a.inst].m + 2) * (q[a.inst].m + 2);
     const double cb = (double)(b2.r1 - b2.r0) * (q[b2.inst].m + 2) * (q[b2.inst].m + 2);
     return ca > cb;
-  });
+  };
+  std::stable_sort(wl.begin(), wl.end(), by_cost);
+  std::stable_sort(rwl.begin(), rwl.end(), by_cost);
   c->nwork = (int)wl.size();
+  c->nrwork = (int)rwl.size();
   c->XS = c->m_max + 3;
   c->ZS = c->m_max + 1;
   c->M1S = c->m_max + 1;
@@ -468,6 +495,7 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   A(c->lm.alloc(c->h_lm.size()));
   A(c->tab.alloc(std::max<size_t>(1, c->h_tab.size())));
   A(c->work.alloc(wl.size()));
+  A(c->rwork.alloc(rwl.size()));
   A(c->slot_off.alloc(soff.size()));
   A(c->part.alloc((size_t)poff));
   A(c->W.alloc((size_t)batch * c->m_max * c->m_max));
@@ -507,6 +535,7 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   // one-time uploads (pageable sources: synchronous with respect to the host)
   A(cudaMemcpyAsync(c->lm.p, c->h_lm.data(), sizeof(int32_t) * c->h_lm.size(), cudaMemcpyHostToDevice, s));
   A(cudaMemcpyAsync(c->work.p, wl.data(), sizeof(Work) * wl.size(), cudaMemcpyHostToDevice, s));
+  A(cudaMemcpyAsync(c->rwork.p, rwl.data(), sizeof(Work) * rwl.size(), cudaMemcpyHostToDevice, s));
   A(cudaMemcpyAsync(c->slot_off.p, soff.data(), sizeof(int64_t) * soff.size(), cudaMemcpyHostToDevice, s));
   if (c->any_nl) A(cudaMemcpyAsync(c->row_off.p, roff.data(), sizeof(int64_t) * batch, cudaMemcpyHostToDevice, s));
   A(cudaStreamSynchronize(s));
@@ -529,6 +558,8 @@ int32_t nys_update(nys_ctx* c, const nys_instance* q, void* stream) {
   for (int b = 0; b < c->batch; ++b) {
     c->h_inst[b].slot_begin = keep[b].slot_begin;
     c->h_inst[b].slot_count = keep[b].slot_count;
+    c->h_inst[b].rslot_begin = keep[b].rslot_begin;
+    c->h_inst[b].rslot_count = keep[b].rslot_count;
     c->h_inst[b].y_off = keep[b].y_off;
   }
   return upload_and_setup(c, (cudaStream_t)stream, false);
@@ -556,7 +587,7 @@ static int32_t solve_impl(nys_ctx* c, cudaStream_t s, double* x_out, int32_t* st
                   c->stinit.p, c->st.p, gscale, c->batch, c->m_max, s));
   if (c->fp32) {
     for (int k = 0; k < c->opt.refine_steps; ++k)
-      CK(launch_refine(c->inst.p, c->lset.p, c->W.p, c->lag.p, c->work.p, c->nwork, c->counter.p,
+      CK(launch_refine(c->inst.p, c->lset.p, c->W.p, c->lag.p, c->rwork.p, c->nrwork, c->counter.p,
                        c->lm.p, c->tab.p, c->part.p, c->slot_off.p, c->fac.p, c->facs, c->xs.p, c->zs.p,
                        c->cws.p, c->XS, c->ZS, c->M1S, c->st.p, gscale, c->batch, c->m_max,
                        c->k_max, c->num_sms, s));

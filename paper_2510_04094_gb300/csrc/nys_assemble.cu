@@ -103,11 +103,13 @@ k_assemble_f64(const Inst* __restrict__ insts, const Work* __restrict__ work, in
       }
       __syncthreads();
     }
+    // slot layout: [first landmark, landmark count, packed upper Gram]
     double* out = part + slot_off[wk.slot];
+    if (tid == 0) { out[0] = 0.0; out[1] = (double)m; }
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
       const int e = tid + k * kAsm64Threads;
-      if (e < E) out[e] = acc[k];
+      if (e < E) out[2 + e] = acc[k];
     }
   }
 }
@@ -123,6 +125,11 @@ k_assemble_f64(const Inst* __restrict__ insts, const Work* __restrict__ work, in
 // Features are evaluated per entry with the MUFU exponential (measured faster
 // here than filling the tile from a lag table in shared memory, whose lookups
 // across landmark columns conflict in the banks).
+// Band structure: kappa_ij vanishes (exp(-u) < 2e-35, u > 80) once |i - idx_j|
+// exceeds the landmark set's lag K, so a work item of consecutive rows only
+// needs the landmarks idx_j in [r0 - K, r1 - 1 + K]: it accumulates the local
+// Gram of that window (plus the -f_p and r columns) and records where the
+// window starts; the solve kernel adds the local Grams into the full one.
 // ---------------------------------------------------------------------------
 constexpr int kAsm32Threads = 384;
 constexpr int kAsm32Rows = 256;
@@ -149,11 +156,24 @@ k_assemble_f32(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     if (w >= nwork) break;
     const Work wk = work[w];
     const Inst I = insts[wk.inst];
-    const int m = I.m, M2 = m + 2;
+    const int m = I.m;
+    for (int j = tid; j < m; j += kAsm32Threads) s_idx[j] = lm_idx[I.lm_off + j];
+    __syncthreads();
+    // landmark window of this row range
+    int jlo = 0, A = m;
+    if (lsets != nullptr) {
+      const int Kl = lsets[I.lset].K;
+      int a = 0, b = m;
+      while (a < b) { const int c = (a + b) >> 1; if (s_idx[c] < wk.r0 - Kl) a = c + 1; else b = c; }
+      jlo = a;
+      b = m;
+      while (a < b) { const int c = (a + b) >> 1; if (s_idx[c] <= wk.r1 - 1 + Kl) a = c + 1; else b = c; }
+      A = a - jlo;
+    }
+    const int M2 = A + 2;
     const int MP = round_up(M2, 8), NB = MP / 8, U = NB * (NB + 1) / 2;
     const int S = max(1, kAsm32Threads / U);
     const int ld = MP + kPadF;
-    for (int j = tid; j < m; j += kAsm32Threads) s_idx[j] = lm_idx[I.lm_off + j];
     const RowConst RK = row_const(I);
 
     // this thread's block (bj <= bl) and slice
@@ -174,7 +194,7 @@ k_assemble_f32(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
 #pragma unroll
     for (int k = 0; k < 64; ++k) acc[k] = 0.f;
     __syncthreads();
-    const int sidx = (fj < m) ? s_idx[fj] : 0;
+    const int sidx = (fj < A) ? s_idx[jlo + fj] : 0;
 
     for (int base = wk.r0; base < wk.r1; base += kAsm32Rows) {
       const int rows = min(kAsm32Rows, wk.r1 - base);
@@ -191,12 +211,12 @@ k_assemble_f32(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
           const int i = base + r;
           float val = 0.f;
           if (r < rows && fj < M2) {
-            if (fj < m) {
+            if (fj < A) {
               const float x = (float)(i - sidx) * hs;
               const float uu = x * x;
               val = exp_neg_fast(uu) * fmaf(s_rc[r][2], uu, fmaf(s_rc[r][1], x, s_rc[r][0]));
             } else {
-              val = s_rc[r][3 + (fj - m)];
+              val = s_rc[r][3 + (fj - A)];
             }
           }
           psi[r * ld + fj] = val;
@@ -241,8 +261,10 @@ k_assemble_f32(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
       for (int k = 0; k < 64; ++k) red[(slice * U + u) * 64 + k] = acc[k];
     }
     __syncthreads();
+    // slot layout: [first landmark, landmark count, packed upper local Gram]
     const int E = M2 * (M2 + 1) / 2;
     double* out = part + slot_off[wk.slot];
+    if (tid == 0) { out[0] = (double)jlo; out[1] = (double)A; }
     for (int e = tid; e < E; e += kAsm32Threads) {
       int j = 0, rem = e;
       while (rem >= M2 - j) { rem -= M2 - j; ++j; }
@@ -252,7 +274,7 @@ k_assemble_f32(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
       const int k = (j & 7) * 8 + (l & 7);
       float sum = 0.f;
       for (int q = 0; q < S; ++q) sum += red[(q * U + ub) * 64 + k];
-      out[e] = (double)sum;
+      out[2 + e] = (double)sum;
     }
     __syncthreads();
   }

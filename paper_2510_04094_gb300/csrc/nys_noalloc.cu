@@ -155,7 +155,7 @@ extern "C" int32_t nys_solve_noalloc(const nys_instance* q, int32_t batch, doubl
     I.lset = nl++;
     const int nrows = s.n - 1;
     const int chunks = nrows < 64 * kChunks ? 1 : kChunks;
-    const int64_t E = (int64_t)(s.m + 2) * (s.m + 3) / 2;
+    const int64_t E = (int64_t)(s.m + 2) * (s.m + 3) / 2 + 2;   // + [first landmark, count]
     I.slot_begin = nwork;
     I.slot_count = chunks;
     for (int k = 0; k < chunks; ++k) {

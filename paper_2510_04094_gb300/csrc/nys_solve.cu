@@ -238,19 +238,30 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   __shared__ T s_beta[2], s_R[4];
   __shared__ double s_c[2][kM1Max];
 
-  // 1. sum the partial Grams (packed upper over M2) -> G (symmetric, full)
-  const int E = M2 * (M2 + 1) / 2;
-  for (int e = threadIdx.x; e < E; e += blockDim.x) {
-    int j = 0, rem = e;
-    while (rem >= M2 - j) { rem -= M2 - j; ++j; }
-    const int l = j + rem;
-    if (j > m) continue;  // the (r, r) entry is not needed
-    double s = 0.0;
-    for (int q = 0; q < I.slot_count; ++q) s += part[slot_off[I.slot_begin + q] + e];
-    Gs[j * ldg + l] = (T)s;
-    if (l <= m) Gs[l * ldg + j] = (T)s;
-  }
+  // 1. add the partial Grams of the row chunks into G (symmetric, full).  A slot
+  //    holds [first landmark jlo, count A, packed upper Gram over the local
+  //    columns (landmarks jlo..jlo+A-1, then -f_p, then r)]; slots are added
+  //    one after the other, so the sum order is fixed.
+  (void)M2;
+  for (int e = threadIdx.x; e < (m + 1) * ldg; e += blockDim.x) Gs[e] = T(0);
   __syncthreads();
+  for (int q = 0; q < I.slot_count; ++q) {
+    const double* P = part + slot_off[I.slot_begin + q];
+    const int jlo = (int)P[0], A = (int)P[1], M2l = A + 2;
+    const int El = M2l * (M2l + 1) / 2;
+    for (int e = threadIdx.x; e < El; e += blockDim.x) {
+      int a = 0, rem = e;
+      while (rem >= M2l - a) { rem -= M2l - a; ++a; }
+      const int bb = a + rem;
+      const int j = (a < A) ? jlo + a : m + (a - A);
+      const int l = (bb < A) ? jlo + bb : m + (bb - A);
+      if (j > m) continue;  // the (r, r) entry is not needed
+      const T v = (T)P[2 + e];
+      Gs[j * ldg + l] += v;
+      if (l <= m && l != j) Gs[l * ldg + j] += v;
+    }
+    __syncthreads();
+  }
   // 2. small pieces: H_wb = W G_kb, g_w = W g_k, H_bb, g_b
   for (int k = threadIdx.x; k < me; k += blockDim.x) {
     T s1 = 0, s2 = 0;
@@ -630,7 +641,7 @@ k_refine_update(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   const double* C1 = C0 + M1S;
   for (int j = threadIdx.x; j <= m; j += blockDim.x) {
     double s = 0.0;
-    for (int q = 0; q < I.slot_count; ++q) s += part[slot_off[I.slot_begin + q] + j];
+    for (int q = 0; q < I.rslot_count; ++q) s += part[slot_off[I.rslot_begin + q] + j];
     acc[j] = s;
   }
   __syncthreads();
