@@ -43,7 +43,9 @@ typedef enum {
   NYS_ENOCONV = -5,     /* per instance: Newton iteration cap reached           */
   NYS_ENONFINITE = -6,  /* per instance: NaN/Inf in inputs or results           */
   NYS_ETIMEOUT = -7,    /* reserved: a bounded device wait gave up              */
-  NYS_EPRECISION = -8,  /* reserved: refinement did not contract                */
+  NYS_EPRECISION = -8,  /* per instance, MIXED: landmark kernel too ill-conditioned
+                           for the FP32 factor (kept lambda_min < 1e-7 lambda_max);
+                           solve that instance with NYS_FP64                   */
   NYS_ESTATE = -9       /* call out of order (e.g. solve before assemble)       */
 } nys_status;
 
@@ -119,11 +121,13 @@ int32_t nys_assemble(nys_ctx* c, void* stream);
 
 /* Solve Lemma 1's system [E + A M, -A f_p, C^T; ...] [omega; b; lambda] =
    [A r; V r; v] for every instance: H = D + gamma B G B^T with B = blkdiag(W, 1),
-   null-space elimination of the initial-condition rows, Cholesky.  MIXED adds
+   null-space elimination of the initial-condition rows, Cholesky.  Landmark
+   sets whose kept eigenvalues span more than 1e7 are assembled in omega
+   coordinates instead (each row projected through W; FP64 only).  MIXED adds
    refine_steps residual passes.  x_out: device, batch x nys_x_stride(c)
    doubles, per instance [omega (m_eff, zero padded to m_max), b, lambda_1,
    lambda_2].  status_out: device, batch int32 (NYS_OK / NYS_ENOTSPD /
-   NYS_ENONFINITE).  Either pointer may be NULL.                              */
+   NYS_ENONFINITE / NYS_EPRECISION).  Either pointer may be NULL.            */
 int32_t nys_solve(nys_ctx* c, void* stream, double* x_out, int32_t* status_out);
 
 /* Nystrom setup + nys_assemble + nys_solve as one CUDA graph (reading the

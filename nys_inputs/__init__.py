@@ -23,7 +23,7 @@ import numpy as np
 SEED = 20251004
 GAMMA = 1e10
 
-_KEYS = {"cfg1": 1, "cfg2": 2, "m0": 10, "cfg3": 3, "cfg4": 4, "cfg5": 5, "small": 99}
+_KEYS = {"cfg1": 1, "cfg2": 2, "m0": 10, "cfg3": 3, "cfg4": 4, "cfg5": 5, "small": 99, "trunc": 98}
 
 
 def rng(name, sub=0):

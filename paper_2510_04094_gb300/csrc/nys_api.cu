@@ -20,9 +20,10 @@ cudaError_t launch_lag(const Lset* lsets, int capacity, float* lag, cudaStream_t
 cudaError_t launch_eig(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
                        double* lam, double tau, int m_max, cudaStream_t st);
 cudaError_t launch_assemble(bool fp32, const Inst* insts, const Lset* lsets, const float* lag,
-                            const Work* work, int nwork, int* counter, const int32_t* lm,
-                            const double* tab, double* part, const int64_t* slot_off, int m_max,
-                            int k_max, int num_sms, cudaStream_t st);
+                            const double* W, const Work* work, int nwork, int* counter,
+                            const int32_t* lm, const double* tab, double* part,
+                            const int64_t* slot_off, int m_max, int k_max, int num_sms,
+                            cudaStream_t st);
 cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const double* W,
                          const float* W32, const double* part, const int64_t* slot_off,
                          const int32_t* lm, void* fac, int64_t facs, double* xs, double* zs,
@@ -40,6 +41,21 @@ cudaError_t launch_eval(const Inst* insts, const double* zs, int ZS, const int32
                         cudaStream_t s);
 
 int64_t fac_elems(int m_max);
+cudaError_t launch_newton_init(const Inst* insts, double* xs, double* zs, double* dzs, double* yaux,
+                               double* nrm, int32_t* iters, int32_t* active, int32_t* st,
+                               const int32_t* st_init, int XS, int ZS, int batch, cudaStream_t s);
+cudaError_t launch_newton_pass(const Inst* insts, const Lset* lsets, const double* W,
+                               const Work* work, int nwork, int* counter, const int32_t* lm,
+                               const double* xs, int XS, const double* zs, const double* dzs, int ZS,
+                               double* yaux, double* rowstate, double* part,
+                               const int64_t* slot_off, const int32_t* active, int mode,
+                               int apply_dy, int m_max, int num_sms, cudaStream_t s);
+cudaError_t launch_newton_step(const Inst* insts, const Lset* lsets, const double* W,
+                               const double* part, const int64_t* slot_off, const int32_t* lm,
+                               double* xs, double* zs, double* dzs, double* cws, int XS, int ZS,
+                               int M1S, int32_t* st, int32_t* active, int32_t* iters, double* nrm,
+                               int max_iter, double tol, int32_t* flags, int mode, int batch,
+                               int m_max, cudaStream_t s);
 }  // namespace nys
 
 using namespace nys;
@@ -429,7 +445,10 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
     const int nrows = q[b].n - 1;
     const int chunks = (int)std::max<int64_t>(1, (nrows + rpi - 1) / rpi);
     const int M2 = q[b].m + 2;
-    const int64_t E = (int64_t)M2 * (M2 + 1) / 2 + 2;   // + [first landmark, count]
+    // linear: [first landmark, count] + packed Gram over m + 2 columns;
+    // Newton: packed Gram over m + 1 columns, two (m+1)-vectors, two scalars
+    const int64_t E = std::max<int64_t>((int64_t)M2 * (M2 + 1) / 2 + 2,
+                                        (int64_t)(M2 - 1) * M2 / 2 + 2 * (M2 - 1) + 2);
     c->h_inst[b].slot_begin = slot;
     c->h_inst[b].slot_count = chunks;
     for (int k = 0; k < chunks; ++k) {
@@ -517,12 +536,12 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
     A(c->nrm.alloc((size_t)batch * 4));
     A(c->active.alloc(batch));
     A(c->iters.alloc(batch));
-    A(c->any_active.alloc(1));
+    A(c->any_active.alloc(2));
   }
   A(cudaMallocHost(reinterpret_cast<void**>(&c->pin_inst), sizeof(Inst) * batch));
   A(cudaMallocHost(reinterpret_cast<void**>(&c->pin_lset), sizeof(Lset) * batch));
   A(cudaMallocHost(reinterpret_cast<void**>(&c->pin_st), sizeof(int32_t) * (batch + 1)));
-  A(cudaMallocHost(reinterpret_cast<void**>(&c->pin_flag), sizeof(int32_t)));
+  A(cudaMallocHost(reinterpret_cast<void**>(&c->pin_flag), 2 * sizeof(int32_t)));
   A(cudaEventCreateWithFlags(&c->staged, cudaEventDisableTiming));
   A(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
   A(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
@@ -573,7 +592,7 @@ int32_t nys_assemble(nys_ctx* c, void* stream) {
     c->factor_stale = false;
     c->join_pending = true;
   }
-  CK(launch_assemble(c->fp32, c->inst.p, c->fp32 ? c->lset.p : nullptr, c->lag.p, c->work.p,
+  CK(launch_assemble(c->fp32, c->inst.p, c->lset.p, c->lag.p, c->W.p, c->work.p,
                      c->nwork, c->counter.p, c->lm.p, c->tab.p, c->part.p, c->slot_off.p, c->m_max,
                      c->k_max, c->num_sms, (cudaStream_t)stream));
   c->assembled = true;
@@ -629,7 +648,7 @@ int32_t nys_run(nys_ctx* c, void* stream, double* x_out, int32_t* status_out) {
     {
       cudaError_t e2 = fork_factor(c, cs);
       if (e2 == cudaSuccess)
-        e2 = launch_assemble(c->fp32, c->inst.p, c->fp32 ? c->lset.p : nullptr, c->lag.p,
+        e2 = launch_assemble(c->fp32, c->inst.p, c->lset.p, c->lag.p, c->W.p,
                              c->work.p, c->nwork, c->counter.p, c->lm.p, c->tab.p, c->part.p,
                              c->slot_off.p, c->m_max, c->k_max, c->num_sms, cs);
       if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(cs, c->ev_join, 0);
@@ -680,9 +699,57 @@ int32_t nys_eval(nys_ctx* c, void* stream, const double* tq, const int64_t* tq_o
 
 int32_t nys_newton(nys_ctx* c, void* stream, int32_t max_iter, double tol, double* x_out,
                    double* y_aux_out, int32_t* iters_out, int32_t* status_out) {
-  (void)c; (void)stream; (void)max_iter; (void)tol; (void)x_out; (void)y_aux_out;
-  (void)iters_out; (void)status_out;
-  return fail(NYS_ESTATE, "nys_newton: not available in this build");
+  if (!c) return fail(NYS_EINVAL, "nys_newton: NULL context");
+  if (!c->any_nl || c->any_lin)
+    return fail(NYS_EINVAL, "nys_newton: every instance must be of kind NYS_COEF_POLY_NL");
+  if (max_iter < 0 || max_iter > 100000) return fail(NYS_EINVAL, "nys_newton: max_iter out of range");
+  if (!(tol > 0)) return fail(NYS_EINVAL, "nys_newton: tol must be > 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (c->factor_stale) {
+    CK(enqueue_factor(c, s));
+    c->factor_stale = false;
+  }
+  if (c->join_pending) {
+    CK(cudaStreamWaitEvent(s, c->ev_join, 0));
+    c->join_pending = false;
+  }
+  CK(launch_newton_init(c->inst.p, c->xs.p, c->zs.p, c->dzs.p, c->yaux.p, c->nrm.p, c->iters.p,
+                        c->active.p, c->st.p, c->stinit.p, c->XS, c->ZS, c->batch, s));
+  int32_t* flags = c->any_active.p;   // [stepped, needs re-pass]
+  for (int k = 0; k <= max_iter; ++k) {
+    CK(cudaMemsetAsync(flags, 0, 2 * sizeof(int32_t), s));
+    CK(launch_newton_pass(c->inst.p, c->lset.p, c->W.p, c->work.p, c->nwork, c->counter.p, c->lm.p,
+                          c->xs.p, c->XS, c->zs.p, c->dzs.p, c->ZS, c->yaux.p, c->rowstate.p, c->part.p, c->slot_off.p, c->active.p,
+                          0, k > 0 ? 1 : 0, c->m_max, c->num_sms, s));
+    CK(launch_newton_step(c->inst.p, c->lset.p, c->W.p, c->part.p, c->slot_off.p, c->lm.p, c->xs.p,
+                          c->zs.p, c->dzs.p, c->cws.p, c->XS, c->ZS, c->M1S, c->st.p, c->active.p,
+                          c->iters.p, c->nrm.p, max_iter, tol, flags, 0, c->batch, c->m_max, s));
+    CK(cudaMemcpyAsync(c->pin_flag, flags, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (c->pin_flag[1]) {  // Gauss-Newton re-pass for the flagged instances
+      CK(launch_newton_pass(c->inst.p, c->lset.p, c->W.p, c->work.p, c->nwork, c->counter.p,
+                            c->lm.p, c->xs.p, c->XS, c->zs.p, c->dzs.p, c->ZS, c->yaux.p, c->rowstate.p, c->part.p, c->slot_off.p,
+                            c->active.p, 1, 0, c->m_max, c->num_sms, s));
+      CK(launch_newton_step(c->inst.p, c->lset.p, c->W.p, c->part.p, c->slot_off.p, c->lm.p,
+                            c->xs.p, c->zs.p, c->dzs.p, c->cws.p, c->XS, c->ZS, c->M1S, c->st.p,
+                            c->active.p, c->iters.p, c->nrm.p, max_iter, tol, flags, 1, c->batch,
+                            c->m_max, s));
+      continue;
+    }
+    if (!c->pin_flag[0]) break;
+  }
+  // the final step's y-update: y_i += dy_i with the last step (a pass in mode 0 that
+  // applies it; instances that stopped took no step after their last pass)
+  if (x_out)
+    CK(cudaMemcpyAsync(x_out, c->xs.p, sizeof(double) * c->batch * c->XS, cudaMemcpyDeviceToDevice, s));
+  if (status_out)
+    CK(cudaMemcpyAsync(status_out, c->st.p, sizeof(int32_t) * c->batch, cudaMemcpyDeviceToDevice, s));
+  if (iters_out)
+    CK(cudaMemcpyAsync(iters_out, c->iters.p, sizeof(int32_t) * c->batch, cudaMemcpyDeviceToDevice, s));
+  if (y_aux_out)
+    CK(cudaMemcpyAsync(y_aux_out, c->yaux.p, sizeof(double) * c->yaux.n, cudaMemcpyDeviceToDevice, s));
+  c->solved = true;
+  return NYS_OK;
 }
 
 int32_t nys_grad(nys_ctx* c, void* stream, const double* obs_t, const int64_t* obs_off,

@@ -22,9 +22,15 @@ namespace nys {
 constexpr int kAsm64Threads = 256;
 constexpr int kAsm64Rows = 32;
 
+// Omega mode (landmark sets flagged ill-conditioned by the setup): the tile of
+// kernel-coordinate rows is projected through W (psi_w = psi_k W^T, one m x m_eff
+// product per row, as the feature map phi = W k of eq32 prescribes) and the
+// Gram is accumulated over (m_eff + 2) omega-coordinate columns; the slot header
+// then reads [-1, m_eff].
 template <int KMAX>
 __global__ void __launch_bounds__(kAsm64Threads)
-k_assemble_f64(const Inst* __restrict__ insts, const Work* __restrict__ work, int nwork,
+k_assemble_f64(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
+               const double* __restrict__ W_all, const Work* __restrict__ work, int nwork,
                int* __restrict__ counter, const int32_t* __restrict__ lm_idx,
                const double* __restrict__ tab, double* __restrict__ part,
                const int64_t* __restrict__ slot_off) {
@@ -43,10 +49,20 @@ k_assemble_f64(const Inst* __restrict__ insts, const Work* __restrict__ work, in
     if (w >= nwork) break;
     const Work wk = work[w];
     const Inst I = insts[wk.inst];
-    const int m = I.m, M2 = m + 2, ld = M2 + 1;
+    const int m = I.m, ld = m + 3;
+    int omode = 0, me = m;
+    if (lsets != nullptr) {
+      const Lset L = lsets[I.lset];
+      omode = L.omode;
+      me = L.m_eff;
+    }
+    const double* W = (lsets != nullptr) ? W_all + lsets[I.lset].w_off : nullptr;
+    const int D = omode ? me : m;          // feature columns of the Gram
+    const int M2 = D + 2;
     const int E = M2 * (M2 + 1) / 2;
     for (int j = tid; j < m; j += kAsm64Threads) s_idx[j] = lm_idx[I.lm_off + j];
     if (M2 != cached_m2) {
+      __syncthreads();
       for (int e = tid; e < E; e += kAsm64Threads) {
         int j = 0, rem = e;
         while (rem >= M2 - j) { rem -= M2 - j; ++j; }
@@ -74,8 +90,8 @@ k_assemble_f64(const Inst* __restrict__ insts, const Work* __restrict__ work, in
         }
       }
       __syncthreads();
-      for (int e = tid; e < kAsm64Rows * M2; e += kAsm64Threads) {
-        const int r = e / M2, j = e - r * M2;
+      for (int e = tid; e < kAsm64Rows * (m + 2); e += kAsm64Threads) {
+        const int r = e / (m + 2), j = e - r * (m + 2);
         const int i = base + r;
         double val = 0.0;
         if (i < wk.r1) {
@@ -90,14 +106,30 @@ k_assemble_f64(const Inst* __restrict__ insts, const Work* __restrict__ work, in
         psi[r * ld + j] = val;
       }
       __syncthreads();
+      if (omode) {  // project the kernel-coordinate rows: psi_w[r][k] = sum_j W[k][j] psi[r][j]
+        double* pw = psi + kAsm64Rows * ld;
+        for (int e = tid; e < kAsm64Rows * M2; e += kAsm64Threads) {
+          const int r = e / M2, k = e - r * M2;
+          double v;
+          if (k < me) {
+            v = 0.0;
+            for (int j = 0; j < m; ++j) v = fma(W[k * m + j], psi[r * ld + j], v);
+          } else {
+            v = psi[r * ld + m + (k - me)];
+          }
+          pw[r * ld + k] = v;
+        }
+        __syncthreads();
+      }
       const int rows = min(kAsm64Rows, wk.r1 - base);
+      const double* pg = omode ? psi + kAsm64Rows * ld : psi;
 #pragma unroll
       for (int k = 0; k < KMAX; ++k) {
         const int e = tid + k * kAsm64Threads;
         if (e < E) {
           const int j = s_pair[2 * e], l = s_pair[2 * e + 1];
           double a = acc[k];
-          for (int r = 0; r < rows; ++r) a = fma(psi[r * ld + j], psi[r * ld + l], a);
+          for (int r = 0; r < rows; ++r) a = fma(pg[r * ld + j], pg[r * ld + l], a);
           acc[k] = a;
         }
       }
@@ -105,7 +137,7 @@ k_assemble_f64(const Inst* __restrict__ insts, const Work* __restrict__ work, in
     }
     // slot layout: [first landmark, landmark count, packed upper Gram]
     double* out = part + slot_off[wk.slot];
-    if (tid == 0) { out[0] = 0.0; out[1] = (double)m; }
+    if (tid == 0) { out[0] = omode ? -1.0 : 0.0; out[1] = (double)D; }
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
       const int e = tid + k * kAsm64Threads;
@@ -291,25 +323,27 @@ size_t asm_smem_bytes(bool fp32, int m_max, int k_cap) {
     const size_t red = sizeof(float) * (size_t)kAsm32Threads * 64;
     return tile > red ? tile : red;
   }
-  return sizeof(double) * (size_t)kAsm64Rows * (M2 + 1);
+  return sizeof(double) * 2 * (size_t)kAsm64Rows * (M2 + 1);
 }
 
 template <int K>
-static cudaError_t launch64(const Inst* insts, const Work* work, int nwork, int* counter,
-                            const int32_t* lm, const double* tab, double* part,
-                            const int64_t* slot_off, size_t sm, int grid, cudaStream_t st) {
+static cudaError_t launch64(const Inst* insts, const Lset* lsets, const double* W,
+                            const Work* work, int nwork, int* counter, const int32_t* lm,
+                            const double* tab, double* part, const int64_t* slot_off, size_t sm,
+                            int grid, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k_assemble_f64<K>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_assemble_f64<K><<<grid, kAsm64Threads, sm, st>>>(insts, work, nwork, counter, lm, tab, part,
-                                                     slot_off);
+  k_assemble_f64<K><<<grid, kAsm64Threads, sm, st>>>(insts, lsets, W, work, nwork, counter, lm,
+                                                     tab, part, slot_off);
   return cudaGetLastError();
 }
 
 cudaError_t launch_assemble(bool fp32, const Inst* insts, const Lset* lsets, const float* lag,
-                            const Work* work, int nwork, int* counter, const int32_t* lm,
-                            const double* tab, double* part, const int64_t* slot_off, int m_max,
-                            int k_max, int num_sms, cudaStream_t st) {
+                            const double* W, const Work* work, int nwork, int* counter,
+                            const int32_t* lm, const double* tab, double* part,
+                            const int64_t* slot_off, int m_max, int k_max, int num_sms,
+                            cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   // k_cap: capacity of the shared-memory kappa table, fixed at launch (an update
@@ -327,11 +361,13 @@ cudaError_t launch_assemble(bool fp32, const Inst* insts, const Lset* lsets, con
   const int M2 = m_max + 2, E = M2 * (M2 + 1) / 2;
   const int kneed = (E + kAsm64Threads - 1) / kAsm64Threads;
   const int grid = min(nwork, num_sms * 2);
-  if (kneed <= 4) return launch64<4>(insts, work, nwork, counter, lm, tab, part, slot_off, sm, grid, st);
-  if (kneed <= 8) return launch64<8>(insts, work, nwork, counter, lm, tab, part, slot_off, sm, grid, st);
-  if (kneed <= 14) return launch64<14>(insts, work, nwork, counter, lm, tab, part, slot_off, sm, grid, st);
-  if (kneed <= 20) return launch64<20>(insts, work, nwork, counter, lm, tab, part, slot_off, sm, grid, st);
-  return launch64<26>(insts, work, nwork, counter, lm, tab, part, slot_off, sm, grid, st);
+#define A64 insts, lsets, W, work, nwork, counter, lm, tab, part, slot_off, sm, grid, st
+  if (kneed <= 4) return launch64<4>(A64);
+  if (kneed <= 8) return launch64<8>(A64);
+  if (kneed <= 14) return launch64<14>(A64);
+  if (kneed <= 20) return launch64<20>(A64);
+  return launch64<26>(A64);
+#undef A64
 }
 
 }  // namespace nys

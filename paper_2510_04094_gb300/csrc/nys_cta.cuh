@@ -1,0 +1,184 @@
+// Block-level (one CTA) dense linear algebra used by the per-instance solve
+// kernels: reductions, Householder reflectors, Cholesky, triangular solves and
+// the null-space KKT solve with a stored factor.
+#pragma once
+#include "nys_internal.cuh"
+
+namespace nys {
+
+template <typename T>
+struct FacView {  // factor storage of one instance in the T arena
+  T* V;    // 2 x M1 Householder vectors
+  T* beta; // 2
+  T* R;    // 4: R00, R01, R11
+  T* H1;   // 2 x M1: first p rows of Q^T H Q
+  T* L;    // N2 x N2 lower Cholesky factor (row-major, ld N2)
+};
+template <typename T>
+__device__ __forceinline__ FacView<T> fac_view(T* base, int M1) {
+  FacView<T> f;
+  f.V = base;
+  f.beta = base + 2 * M1;
+  f.R = f.beta + 2;
+  f.H1 = f.R + 4;
+  f.L = f.H1 + 2 * M1;
+  return f;
+}
+inline int64_t fac_elems_inline(int m_max) {
+  const int M1 = m_max + 1;
+  return 2 * M1 + 2 + 4 + 2 * M1 + (int64_t)M1 * M1;
+}
+
+// ---- CTA helpers -----------------------------------------------------------
+template <typename T>
+__device__ T cta_dot(const T* a, const T* b, int n, T* red) {
+  T s = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += a[i] * b[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    red[32] = t;
+  }
+  __syncthreads();
+  const T r = red[32];
+  __syncthreads();
+  return r;
+}
+
+// Householder vector of x[0..n): v with v[0] = x0 + sign(x0)|x|, beta = 2/(v^T v),
+// (I - beta v v^T) x = -sign(x0)|x| e_0.  Returns the diagonal value.
+template <typename T>
+__device__ T house(const T* x, T* v, int n, T* beta, T* red) {
+  const T nrm2 = cta_dot(x, x, n, red);
+  const T nrm = sqrt(nrm2);
+  const T x0 = x[0];
+  const T sg = (x0 >= T(0)) ? T(1) : T(-1);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = (i == 0) ? x0 + sg * nrm : x[i];
+  __syncthreads();
+  const T vv = nrm2 + T(2) * sg * nrm * x0 + nrm2;  // |v|^2 = 2|x|^2 + 2|x0||x|
+  if (threadIdx.x == 0) *beta = (vv > T(0)) ? T(2) / vv : T(0);
+  __syncthreads();
+  return -sg * nrm;
+}
+
+// A <- (I - b v v^T) A (I - b v v^T) for symmetric A (n x n, ld), w scratch n.
+template <typename T>
+__device__ void apply_house_sym(T* A, int ld, int n, const T* v, T b, T* w, T* red) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    T s = 0;
+    for (int j = 0; j < n; ++j) s += A[i * ld + j] * v[j];
+    w[i] = b * s;
+  }
+  __syncthreads();
+  const T k = T(0.5) * b * cta_dot(v, w, n, red);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) w[i] -= k * v[i];
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e - (e / n) * n;
+    A[i * ld + j] -= v[i] * w[j] + w[i] * v[j];
+  }
+  __syncthreads();
+}
+
+// x <- (I - b v v^T) x
+template <typename T>
+__device__ void apply_house_vec(T* x, int n, const T* v, T b, T* red) {
+  const T s = b * cta_dot(v, x, n, red);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] -= s * v[i];
+  __syncthreads();
+}
+
+// In-place lower Cholesky of A (n x n, ld).  Returns false on a non-positive pivot.
+template <typename T>
+__device__ bool cta_cholesky(T* A, int ld, int n, int* flag) {
+  if (threadIdx.x == 0) *flag = 0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      const T d = A[k * ld + k];
+      if (!(d > T(0))) { *flag = 1; A[k * ld + k] = T(1); }
+      else A[k * ld + k] = sqrt(d);
+    }
+    __syncthreads();
+    const T lkk = A[k * ld + k];
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[i * ld + k] /= lkk;
+    __syncthreads();
+    const int R = n - k - 1;
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+      const int i = k + 1 + e / R, j = k + 1 + e % R;
+      if (j <= i) A[i * ld + j] -= A[i * ld + k] * A[j * ld + k];
+    }
+    __syncthreads();
+  }
+  return *flag == 0;
+}
+
+// Solve L L^T y = b in place (b overwritten), L lower (n x n, ld).
+template <typename T>
+__device__ void cta_chol_solve(const T* L, int ld, int n, T* b) {
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) b[k] /= L[k * ld + k];
+    __syncthreads();
+    const T yk = b[k];
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) b[i] -= L[i * ld + k] * yk;
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    if (threadIdx.x == 0) b[k] /= L[k * ld + k];
+    __syncthreads();
+    const T yk = b[k];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) b[i] -= L[k * ld + i] * yk;
+    __syncthreads();
+  }
+}
+
+// Apply the stored factor: given residuals (h: M1, cr: p) return the KKT
+// solution (dx: M1, dl: p) of [H C^T; C 0][dx; dl] = [h; cr].  All arrays in
+// shared memory; h is overwritten.
+template <typename T>
+__device__ void kkt_apply(const FacView<T>& F, int M1, int p, T* h, const T* cr, T* dx, T* dl,
+                          T* red) {
+  // h' = Q^T h = H_p .. H_1 h
+  for (int k = 0; k < p; ++k) apply_house_vec(h, M1, F.V + k * M1, F.beta[k], red);
+  // y1 = R^{-T} cr
+  __shared__ T y1s[2];
+  if (threadIdx.x == 0) {
+    y1s[0] = cr[0] / F.R[0];
+    if (p == 2) y1s[1] = (cr[1] - F.R[1] * y1s[0]) / F.R[2];
+  }
+  __syncthreads();
+  const int N2 = M1 - p;
+  // rhs2 = h'[p:] - H'[p:, :p] y1   (H'[p:, :p] = H1[:, p:]^T)
+  for (int i = threadIdx.x; i < N2; i += blockDim.x) {
+    T s = h[p + i];
+    for (int k = 0; k < p; ++k) s -= F.H1[k * M1 + p + i] * y1s[k];
+    dx[p + i] = s;
+  }
+  __syncthreads();
+  cta_chol_solve(F.L, N2, N2, dx + p);
+  // lambda: R lam = h'[:p] - H'[:p, :] y
+  if (threadIdx.x < 2 && threadIdx.x < p) dx[threadIdx.x] = y1s[threadIdx.x];
+  __syncthreads();
+  T r0 = cta_dot(F.H1, dx, M1, red);
+  T r1 = (p == 2) ? cta_dot(F.H1 + M1, dx, M1, red) : T(0);
+  if (threadIdx.x == 0) {
+    r0 = h[0] - r0;
+    r1 = (p == 2) ? h[1] - r1 : T(0);
+    if (p == 2) {
+      dl[1] = r1 / F.R[2];
+      dl[0] = (r0 - F.R[1] * dl[1]) / F.R[0];
+    } else {
+      dl[0] = r0 / F.R[0];
+    }
+  }
+  __syncthreads();
+  // dx = Q y = H_1 .. H_p y
+  for (int k = p - 1; k >= 0; --k) apply_house_vec(dx, M1, F.V + k * M1, F.beta[k], red);
+}
+
+}  // namespace nys

@@ -39,7 +39,11 @@ struct Inst {
 struct Lset {
   int32_t m, m_eff;    // m_eff written by the setup kernel
   int32_t n, K;        // K: largest tabulated lag, exp(-(K h/sigma)^2) < 1e-34
-  int32_t active, pad;
+  int32_t active;
+  int32_t omode;       // 1: ill-conditioned landmark kernel (smallest kept eigenvalue
+                       // < kOmegaCond * largest): row passes project every row
+                       // through W (omega coordinates) instead of accumulating in
+                       // kernel coordinates, which would lose precision there
   int64_t lm_off;
   int64_t w_off;       // W: m x m doubles (rows k < m_eff used), row-major
   int64_t lag_off;     // lag tables (floats): 6 per lag k = 0..K, see k_setup_lag
@@ -47,6 +51,7 @@ struct Lset {
 };
 // Largest lag whose kernel value is kept: (K hs)^2 <= kLagU.
 constexpr double kLagU = 80.0;
+constexpr double kOmegaCond = 1e-7;
 
 // One unit of a row pass: rows i in [r0, r1) (0-based grid index, 1 <= i <= n-1).
 struct Work {

@@ -25,9 +25,10 @@ namespace nys {
 cudaError_t launch_setup(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
                          double* lam, float* lag, double tau, int m_max, cudaStream_t st);
 cudaError_t launch_assemble(bool fp32, const Inst* insts, const Lset* lsets, const float* lag,
-                            const Work* work, int nwork, int* counter, const int32_t* lm,
-                            const double* tab, double* part, const int64_t* slot_off, int m_max,
-                            int k_max, int num_sms, cudaStream_t st);
+                            const double* W, const Work* work, int nwork, int* counter,
+                            const int32_t* lm, const double* tab, double* part,
+                            const int64_t* slot_off, int m_max, int k_max, int num_sms,
+                            cudaStream_t st);
 cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const double* W,
                          const float* W32, const double* part, const int64_t* slot_off,
                          const int32_t* lm, void* fac, int64_t facs, double* xs, double* zs,
@@ -214,7 +215,8 @@ extern "C" int32_t nys_solve_noalloc(const nys_instance* q, int32_t batch, doubl
                      reinterpret_cast<float*>(B + o_W32), reinterpret_cast<double*>(B + o_lam),
                      nullptr, 1e-12, m_max, st));
   // the work counter is cleared inside launch_assemble before the kernel
-  NA_CK(launch_assemble(false, d_inst, nullptr, nullptr, reinterpret_cast<const Work*>(B + o_work),
+  NA_CK(launch_assemble(false, d_inst, d_lset, nullptr, reinterpret_cast<const double*>(B + o_W),
+                        reinterpret_cast<const Work*>(B + o_work),
                         nwork, reinterpret_cast<int*>(B + o_cnt), d_lm, nullptr,
                         reinterpret_cast<double*>(B + o_part),
                         reinterpret_cast<const int64_t*>(B + o_soff), m_max, 0, sms, st));

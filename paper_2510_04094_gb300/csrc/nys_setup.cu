@@ -146,6 +146,7 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict_
     int me = 0;
     while (me < m && A[perm[me] * ld + perm[me]] > tau * lmax) ++me;
     lsets[L].m_eff = me;
+    lsets[L].omode = (A[perm[me - 1] * ld + perm[me - 1]] < kOmegaCond * lmax) ? 1 : 0;
     red[0] = (double)me;
   }
   __syncthreads();

@@ -15,186 +15,13 @@
 // T = double: the plain FP64 path.  T = float: the factor of the mixed path;
 // its error is removed by refinement passes whose residuals are computed
 // from the definition of the problem with FP64-accurate features.
-#include "nys_internal.cuh"
+#include "nys_cta.cuh"
 
 namespace nys {
 
 constexpr int kSolveThreads = 256;
 
-template <typename T>
-struct FacView {  // factor storage of one instance in the T arena
-  T* V;    // 2 x M1 Householder vectors
-  T* beta; // 2
-  T* R;    // 4: R00, R01, R11
-  T* H1;   // 2 x M1: first p rows of Q^T H Q
-  T* L;    // N2 x N2 lower Cholesky factor (row-major, ld N2)
-};
-template <typename T>
-__device__ __forceinline__ FacView<T> fac_view(T* base, int M1) {
-  FacView<T> f;
-  f.V = base;
-  f.beta = base + 2 * M1;
-  f.R = f.beta + 2;
-  f.H1 = f.R + 4;
-  f.L = f.H1 + 2 * M1;
-  return f;
-}
-int64_t fac_elems(int m_max) {
-  const int M1 = m_max + 1;
-  return 2 * M1 + 2 + 4 + 2 * M1 + (int64_t)M1 * M1;
-}
-
-// ---- CTA helpers -----------------------------------------------------------
-template <typename T>
-__device__ T cta_dot(const T* a, const T* b, int n, T* red) {
-  T s = 0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += a[i] * b[i];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) red[w] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    T t = 0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
-    red[32] = t;
-  }
-  __syncthreads();
-  const T r = red[32];
-  __syncthreads();
-  return r;
-}
-
-// Householder vector of x[0..n): v with v[0] = x0 + sign(x0)|x|, beta = 2/(v^T v),
-// (I - beta v v^T) x = -sign(x0)|x| e_0.  Returns the diagonal value.
-template <typename T>
-__device__ T house(const T* x, T* v, int n, T* beta, T* red) {
-  const T nrm2 = cta_dot(x, x, n, red);
-  const T nrm = sqrt(nrm2);
-  const T x0 = x[0];
-  const T sg = (x0 >= T(0)) ? T(1) : T(-1);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = (i == 0) ? x0 + sg * nrm : x[i];
-  __syncthreads();
-  const T vv = nrm2 + T(2) * sg * nrm * x0 + nrm2;  // |v|^2 = 2|x|^2 + 2|x0||x|
-  if (threadIdx.x == 0) *beta = (vv > T(0)) ? T(2) / vv : T(0);
-  __syncthreads();
-  return -sg * nrm;
-}
-
-// A <- (I - b v v^T) A (I - b v v^T) for symmetric A (n x n, ld), w scratch n.
-template <typename T>
-__device__ void apply_house_sym(T* A, int ld, int n, const T* v, T b, T* w, T* red) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    T s = 0;
-    for (int j = 0; j < n; ++j) s += A[i * ld + j] * v[j];
-    w[i] = b * s;
-  }
-  __syncthreads();
-  const T k = T(0.5) * b * cta_dot(v, w, n, red);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) w[i] -= k * v[i];
-  __syncthreads();
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int i = e / n, j = e - (e / n) * n;
-    A[i * ld + j] -= v[i] * w[j] + w[i] * v[j];
-  }
-  __syncthreads();
-}
-
-// x <- (I - b v v^T) x
-template <typename T>
-__device__ void apply_house_vec(T* x, int n, const T* v, T b, T* red) {
-  const T s = b * cta_dot(v, x, n, red);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] -= s * v[i];
-  __syncthreads();
-}
-
-// In-place lower Cholesky of A (n x n, ld).  Returns false on a non-positive pivot.
-template <typename T>
-__device__ bool cta_cholesky(T* A, int ld, int n, int* flag) {
-  if (threadIdx.x == 0) *flag = 0;
-  __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    if (threadIdx.x == 0) {
-      const T d = A[k * ld + k];
-      if (!(d > T(0))) { *flag = 1; A[k * ld + k] = T(1); }
-      else A[k * ld + k] = sqrt(d);
-    }
-    __syncthreads();
-    const T lkk = A[k * ld + k];
-    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[i * ld + k] /= lkk;
-    __syncthreads();
-    const int R = n - k - 1;
-    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
-      const int i = k + 1 + e / R, j = k + 1 + e % R;
-      if (j <= i) A[i * ld + j] -= A[i * ld + k] * A[j * ld + k];
-    }
-    __syncthreads();
-  }
-  return *flag == 0;
-}
-
-// Solve L L^T y = b in place (b overwritten), L lower (n x n, ld).
-template <typename T>
-__device__ void cta_chol_solve(const T* L, int ld, int n, T* b) {
-  for (int k = 0; k < n; ++k) {
-    if (threadIdx.x == 0) b[k] /= L[k * ld + k];
-    __syncthreads();
-    const T yk = b[k];
-    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) b[i] -= L[i * ld + k] * yk;
-    __syncthreads();
-  }
-  for (int k = n - 1; k >= 0; --k) {
-    if (threadIdx.x == 0) b[k] /= L[k * ld + k];
-    __syncthreads();
-    const T yk = b[k];
-    for (int i = threadIdx.x; i < k; i += blockDim.x) b[i] -= L[k * ld + i] * yk;
-    __syncthreads();
-  }
-}
-
-// Apply the stored factor: given residuals (h: M1, cr: p) return the KKT
-// solution (dx: M1, dl: p) of [H C^T; C 0][dx; dl] = [h; cr].  All arrays in
-// shared memory; h is overwritten.
-template <typename T>
-__device__ void kkt_apply(const FacView<T>& F, int M1, int p, T* h, const T* cr, T* dx, T* dl,
-                          T* red) {
-  // h' = Q^T h = H_p .. H_1 h
-  for (int k = 0; k < p; ++k) apply_house_vec(h, M1, F.V + k * M1, F.beta[k], red);
-  // y1 = R^{-T} cr
-  __shared__ T y1s[2];
-  if (threadIdx.x == 0) {
-    y1s[0] = cr[0] / F.R[0];
-    if (p == 2) y1s[1] = (cr[1] - F.R[1] * y1s[0]) / F.R[2];
-  }
-  __syncthreads();
-  const int N2 = M1 - p;
-  // rhs2 = h'[p:] - H'[p:, :p] y1   (H'[p:, :p] = H1[:, p:]^T)
-  for (int i = threadIdx.x; i < N2; i += blockDim.x) {
-    T s = h[p + i];
-    for (int k = 0; k < p; ++k) s -= F.H1[k * M1 + p + i] * y1s[k];
-    dx[p + i] = s;
-  }
-  __syncthreads();
-  cta_chol_solve(F.L, N2, N2, dx + p);
-  // lambda: R lam = h'[:p] - H'[:p, :] y
-  if (threadIdx.x < 2 && threadIdx.x < p) dx[threadIdx.x] = y1s[threadIdx.x];
-  __syncthreads();
-  T r0 = cta_dot(F.H1, dx, M1, red);
-  T r1 = (p == 2) ? cta_dot(F.H1 + M1, dx, M1, red) : T(0);
-  if (threadIdx.x == 0) {
-    r0 = h[0] - r0;
-    r1 = (p == 2) ? h[1] - r1 : T(0);
-    if (p == 2) {
-      dl[1] = r1 / F.R[2];
-      dl[0] = (r0 - F.R[1] * dl[1]) / F.R[0];
-    } else {
-      dl[0] = r0 / F.R[0];
-    }
-  }
-  __syncthreads();
-  // dx = Q y = H_1 .. H_p y
-  for (int k = p - 1; k >= 0; --k) apply_house_vec(dx, M1, F.V + k * M1, F.beta[k], red);
-}
+int64_t fac_elems(int m_max) { return fac_elems_inline(m_max); }
 
 // ---------------------------------------------------------------------------
 // K3: form H, g, C; factor; solve.  One CTA per instance.
@@ -210,21 +37,30 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         double* __restrict__ cws, int XS, int ZS, int M1S, const int32_t* __restrict__ st_init,
         int32_t* __restrict__ st_all, double gamma_scale) {
   const int b = blockIdx.x;
-  if (st_init[b] != NYS_OK) {
-    if (threadIdx.x == 0) st_all[b] = st_init[b];
-    return;
-  }
   const Inst I = insts[b];
   const Lset LS = lsets[I.lset];
+  // omega mode (ill-conditioned landmark kernel): the row pass projected each
+  // row through W, so the slots hold the Gram in omega coordinates.  The FP32
+  // factor is too coarse there; the mixed path reports NYS_EPRECISION.
+  const bool om = (LS.omode != 0);
+  const int st0 = (st_init[b] != NYS_OK) ? st_init[b]
+                  : (om && sizeof(T) == sizeof(float)) ? NYS_EPRECISION : NYS_OK;
+  if (st0 != NYS_OK) {  // no solution: zero x and z, report the status
+    for (int k = threadIdx.x; k < XS; k += blockDim.x) xs[(int64_t)b * XS + k] = 0.0;
+    for (int k = threadIdx.x; k < ZS; k += blockDim.x) zs[(int64_t)b * ZS + k] = 0.0;
+    if (threadIdx.x == 0) st_all[b] = st0;
+    return;
+  }
   const int m = I.m, p = I.p, me = LS.m_eff;
-  const int M1 = me + 1, M2 = m + 2, N2 = M1 - p;
-  const int ldg = m + 2, ldh = M1;
+  const int M1 = me + 1, N2 = M1 - p;
+  const int Dg = om ? me : m;          // feature columns of the accumulated Gram
+  const int ldg = Dg + 2, ldh = M1;
   const double* W = W_all + LS.w_off;  // m x m, rows < me
   const T* Wt = Wt_all + LS.w_off;     // same in T
   const double gamma = I.gamma * gamma_scale;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* Gs = reinterpret_cast<T*>(smraw);             // (m+1) x (m+2)
-  T* Hs = Gs + (m + 1) * ldg;                        // M1 x M1
+  T* Gs = reinterpret_cast<T*>(smraw);             // (Dg+1) x (Dg+2), room for (m+1) x (m+2)
+  T* Hs = Gs + (m + 1) * (m + 2);                    // M1 x M1
   T* Yb = Hs + M1 * ldh;                             // 8 x m
   T* vec = Yb + 8 * m;                               // misc vectors
   T* g = vec;                                        // M1
@@ -239,65 +75,75 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   __shared__ double s_c[2][kM1Max];
 
   // 1. add the partial Grams of the row chunks into G (symmetric, full).  A slot
-  //    holds [first landmark jlo, count A, packed upper Gram over the local
-  //    columns (landmarks jlo..jlo+A-1, then -f_p, then r)]; slots are added
-  //    one after the other, so the sum order is fixed.
-  (void)M2;
-  for (int e = threadIdx.x; e < (m + 1) * ldg; e += blockDim.x) Gs[e] = T(0);
+  //    holds [first column jlo (-1: omega coordinates, all me columns), count A,
+  //    packed upper Gram over the local columns (features jlo..jlo+A-1, then
+  //    -f_p, then r)]; slots are added one after the other, so the sum order is
+  //    fixed.
+  for (int e = threadIdx.x; e < (Dg + 1) * ldg; e += blockDim.x) Gs[e] = T(0);
   __syncthreads();
   for (int q = 0; q < I.slot_count; ++q) {
     const double* P = part + slot_off[I.slot_begin + q];
-    const int jlo = (int)P[0], A = (int)P[1], M2l = A + 2;
+    const int jlo = (int)P[0] < 0 ? 0 : (int)P[0], A = (int)P[1], M2l = A + 2;
     const int El = M2l * (M2l + 1) / 2;
     for (int e = threadIdx.x; e < El; e += blockDim.x) {
       int a = 0, rem = e;
       while (rem >= M2l - a) { rem -= M2l - a; ++a; }
       const int bb = a + rem;
-      const int j = (a < A) ? jlo + a : m + (a - A);
-      const int l = (bb < A) ? jlo + bb : m + (bb - A);
-      if (j > m) continue;  // the (r, r) entry is not needed
+      const int j = (a < A) ? jlo + a : Dg + (a - A);
+      const int l = (bb < A) ? jlo + bb : Dg + (bb - A);
+      if (j > Dg) continue;  // the (r, r) entry is not needed
       const T v = (T)P[2 + e];
       Gs[j * ldg + l] += v;
-      if (l <= m && l != j) Gs[l * ldg + j] += v;
+      if (l <= Dg && l != j) Gs[l * ldg + j] += v;
     }
     __syncthreads();
   }
-  // 2. small pieces: H_wb = W G_kb, g_w = W g_k, H_bb, g_b
-  for (int k = threadIdx.x; k < me; k += blockDim.x) {
-    T s1 = 0, s2 = 0;
-    for (int j = 0; j < m; ++j) {
-      const T wkj = Wt[k * m + j];
-      s1 += wkj * Gs[j * ldg + m];
-      s2 += wkj * Gs[j * ldg + m + 1];
+  if (om) {
+    // 2-3 in omega coordinates: H = D + gamma G, g = gamma G[:, r]
+    for (int e = threadIdx.x; e < M1 * M1; e += blockDim.x) {
+      const int k = e / M1, l = e - k * M1;
+      Hs[k * ldh + l] = (T)gamma * Gs[k * ldg + l] + ((k == l && k < me) ? T(1) : T(0));
     }
-    hb[k] = s1;
-    g[k] = (T)gamma * s2;
-  }
-  if (threadIdx.x == 0) g[me] = (T)gamma * Gs[m * ldg + m + 1];
-  __syncthreads();
-  // 3. H_ww = gamma W G_kk W^T + I, in blocks of 8 rows of Y = W G_kk
-  for (int k0 = 0; k0 < me; k0 += 8) {
-    const int kb = min(8, me - k0);
-    for (int e = threadIdx.x; e < kb * m; e += blockDim.x) {
-      const int kk = e / m, l = e - kk * m;
-      T s = 0;
-      for (int j = 0; j < m; ++j) s += Wt[(k0 + kk) * m + j] * Gs[j * ldg + l];
-      Yb[kk * m + l] = s;
-    }
+    for (int k = threadIdx.x; k < M1; k += blockDim.x) g[k] = (T)gamma * Gs[k * ldg + me + 1];
     __syncthreads();
-    for (int e = threadIdx.x; e < kb * me; e += blockDim.x) {
-      const int kk = e / me, l = e - kk * me;
-      T s = 0;
-      for (int j = 0; j < m; ++j) s += Yb[kk * m + j] * Wt[l * m + j];
-      Hs[(k0 + kk) * ldh + l] = (T)gamma * s + ((k0 + kk) == l ? T(1) : T(0));
+  } else {
+    // 2. small pieces: H_wb = W G_kb, g_w = W g_k, H_bb, g_b
+    for (int k = threadIdx.x; k < me; k += blockDim.x) {
+      T s1 = 0, s2 = 0;
+      for (int j = 0; j < m; ++j) {
+        const T wkj = Wt[k * m + j];
+        s1 += wkj * Gs[j * ldg + m];
+        s2 += wkj * Gs[j * ldg + m + 1];
+      }
+      hb[k] = s1;
+      g[k] = (T)gamma * s2;
     }
+    if (threadIdx.x == 0) g[me] = (T)gamma * Gs[m * ldg + m + 1];
     __syncthreads();
+    // 3. H_ww = gamma W G_kk W^T + I, in blocks of 8 rows of Y = W G_kk
+    for (int k0 = 0; k0 < me; k0 += 8) {
+      const int kb = min(8, me - k0);
+      for (int e = threadIdx.x; e < kb * m; e += blockDim.x) {
+        const int kk = e / m, l = e - kk * m;
+        T s = 0;
+        for (int j = 0; j < m; ++j) s += Wt[(k0 + kk) * m + j] * Gs[j * ldg + l];
+        Yb[kk * m + l] = s;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < kb * me; e += blockDim.x) {
+        const int kk = e / me, l = e - kk * me;
+        T s = 0;
+        for (int j = 0; j < m; ++j) s += Yb[kk * m + j] * Wt[l * m + j];
+        Hs[(k0 + kk) * ldh + l] = (T)gamma * s + ((k0 + kk) == l ? T(1) : T(0));
+      }
+      __syncthreads();
+    }
+    for (int k = threadIdx.x; k < me; k += blockDim.x) {
+      Hs[k * ldh + me] = (T)gamma * hb[k];
+      Hs[me * ldh + k] = (T)gamma * hb[k];
+    }
+    if (threadIdx.x == 0) Hs[me * ldh + me] = (T)gamma * Gs[m * ldg + m];
   }
-  for (int k = threadIdx.x; k < me; k += blockDim.x) {
-    Hs[k * ldh + me] = (T)gamma * hb[k];
-    Hs[me * ldh + k] = (T)gamma * hb[k];
-  }
-  if (threadIdx.x == 0) Hs[me * ldh + me] = (T)gamma * Gs[m * ldg + m];
   // 4. constraint rows in omega coordinates (FP64): c_1 = [W k(t_1); 1], c_2 = [W k'(t_1); 0]
   for (int k = threadIdx.x; k < M1; k += blockDim.x) {
     double s0 = 0.0, s1 = 0.0;
@@ -691,6 +537,309 @@ k_refine_update(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   if (threadIdx.x == 0) {
     if (!isfinite(xb[XS - 3]) || !isfinite(xb[XS - 2])) st_all[b] = NYS_ENONFINITE;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Newton step for Lemma 2 (Eq. 3.2.1), one CTA per instance, FP64.  Reads the
+// partials of k_newton_pass (reduced Gram G and vectors v, u in kernel
+// coordinates, sum Fy^2, small-pivot count) and
+//   grad_x L = D x + C^T lambda + B u,   |F|^2 = |grad_x L|^2 + sum Fy^2 + |C x - v|^2,
+// applies the stopping rule (|dx_prev| <= tol (1 + |x|) and |F| <= tol max(1, |F0|),
+// x = (omega, b)) and the iteration cap, falls back to Gauss-Newton (re-pass,
+// mode 1) when a pivot d_i <= 1e-12 gamma or the projected reduced Hessian is
+// not positive definite, and otherwise solves
+//   [D + B G B^T, C^T; C, 0] [dx; dlambda] = [-(D x + C^T lambda + B v); v - C x]
+// by the null-space Cholesky method and updates x, lambda, z = B^T x, dz = B^T dx.
+// flags[0]: some instance took a step; flags[1]: some instance needs a re-pass.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSolveThreads)
+k_newton_step(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
+              const double* __restrict__ W_all, const double* __restrict__ part,
+              const int64_t* __restrict__ slot_off, const int32_t* __restrict__ lm_idx,
+              double* __restrict__ xs, double* __restrict__ zs, double* __restrict__ dzs,
+              double* __restrict__ cws, int XS, int ZS, int M1S, int32_t* __restrict__ st_all,
+              int32_t* __restrict__ active, int32_t* __restrict__ iters, double* __restrict__ nrm,
+              int max_iter, double tol, int32_t* __restrict__ flags, int mode) {
+  const int b = blockIdx.x;
+  const int act = active[b];
+  if (act == 0 || (mode == 1 && act != 2)) return;
+  const Inst I = insts[b];
+  const Lset LS = lsets[I.lset];
+  const int m = I.m, p = I.p, me = LS.m_eff;
+  // omega mode: the row pass accumulated G, v, u in omega coordinates (D = me)
+  const bool om = (LS.omode != 0);
+  const int D = om ? me : m;
+  const int M1 = me + 1, M1k = D + 1, N2 = M1 - p;
+  const int ldg = D + 2, ldh = M1;
+  const int E1 = M1k * (M1k + 1) / 2;
+  const double* W = W_all + LS.w_off;
+  extern __shared__ __align__(16) unsigned char smraw_nt[];
+  double* Gs = reinterpret_cast<double*>(smraw_nt);   // (D+1) x (D+2): G | v
+  double* Hs = Gs + (m + 1) * (m + 2);                 // M1 x M1
+  double* Yb = Hs + M1 * ldh;                          // 8 x m
+  double* g = Yb + 8 * m;                              // M1
+  double* hb = g + M1;
+  double* Vh = hb + M1;                                // 2 x M1
+  double* c2 = Vh + 2 * M1;
+  double* w = c2 + M1;
+  double* y = w + M1;
+  double* red = y + M1;                                // 40
+  __shared__ double s_u[kM1Max], s_gx[kM1Max + 1];
+  __shared__ double s_c[2][kM1Max];
+  __shared__ double s_sc[4];   // sum Fy^2, small count, |h|^2, |x|^2
+  __shared__ double s_beta[2], s_R[4];
+  __shared__ int s_flag;
+  double* xb = xs + (int64_t)b * XS;
+
+  // 1. partial sums in slot order
+  for (int e = threadIdx.x; e < (D + 1) * ldg; e += blockDim.x) Gs[e] = 0.0;
+  if (threadIdx.x < 4) s_sc[threadIdx.x] = 0.0;
+  __syncthreads();
+  for (int q = 0; q < I.slot_count; ++q) {
+    const double* P = part + slot_off[I.slot_begin + q];
+    for (int e = threadIdx.x; e < E1; e += blockDim.x) {
+      int j = 0, rem = e;
+      while (rem >= M1k - j) { rem -= M1k - j; ++j; }
+      const int l = j + rem;
+      Gs[j * ldg + l] += P[e];
+      if (l != j) Gs[l * ldg + j] += P[e];
+    }
+    for (int j = threadIdx.x; j <= D; j += blockDim.x) {
+      Gs[j * ldg + D + 1] += P[E1 + j];
+      s_u[j] = (q == 0 ? 0.0 : s_u[j]) + P[E1 + M1k + j];
+    }
+    if (threadIdx.x == 0) {
+      s_sc[0] += P[E1 + 2 * M1k];
+      s_sc[1] += P[E1 + 2 * M1k + 1];
+    }
+    __syncthreads();
+  }
+  // 2. constraint rows in omega coordinates, grad_x L, |F|
+  for (int k = threadIdx.x; k < M1; k += blockDim.x) {
+    double s0 = 0.0, s1 = 0.0;
+    if (k < me) {
+      for (int j = 0; j < m; ++j) {
+        const double x = (double)(0 - lm_idx[I.lm_off + j]) * I.hs;
+        const double e = exp(-x * x);
+        s0 += W[k * m + j] * e;
+        s1 += W[k * m + j] * (-2.0 * x / I.sigma) * e;
+      }
+    } else {
+      s0 = 1.0;
+    }
+    s_c[0][k] = s0;
+    s_c[1][k] = s1;
+    cws[(int64_t)b * 2 * M1S + k] = s0;
+    cws[(int64_t)b * 2 * M1S + M1S + k] = s1;
+  }
+  __syncthreads();
+  const double lam0 = xb[XS - 2], lam1 = (p == 2) ? xb[XS - 1] : 0.0;
+  for (int k = threadIdx.x; k < M1; k += blockDim.x) {
+    double s;
+    if (k < me) {
+      s = xb[k];
+      if (om) s += s_u[k];
+      else
+        for (int j = 0; j < m; ++j) s += W[k * m + j] * s_u[j];
+    } else {
+      s = s_u[D];
+    }
+    s += s_c[0][k] * lam0 + s_c[1][k] * lam1;
+    s_gx[k] = s;
+  }
+  if (threadIdx.x < 2 && threadIdx.x < p) {
+    const int kk = threadIdx.x;
+    double h = -I.v[kk];
+    for (int k = 0; k < me; ++k) h += s_c[kk][k] * xb[k];
+    h += s_c[kk][me] * xb[XS - 3];
+    atomicAdd(&s_sc[2], h * h);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double gx2 = 0.0, x2 = 0.0;
+    for (int k = 0; k < M1; ++k) gx2 += s_gx[k] * s_gx[k];
+    for (int k = 0; k < me; ++k) x2 += xb[k] * xb[k];
+    x2 += xb[XS - 3] * xb[XS - 3];
+    s_sc[3] = x2;
+    s_gx[M1] = sqrt(gx2 + s_sc[0] + s_sc[2]);   // |F|
+  }
+  __syncthreads();
+  if (mode == 0) {
+    const int it = iters[b];
+    const double nF = s_gx[M1];
+    if (threadIdx.x == 0) {
+      int decision = 0;   // 0: step, 1: converged, 2: cap, 3: re-pass
+      if (it == 0) nrm[(int64_t)b * 4] = nF;
+      const double F0 = nrm[(int64_t)b * 4];
+      if (it > 0 && nrm[(int64_t)b * 4 + 1] <= tol * (1.0 + sqrt(s_sc[3])) && nF <= tol * fmax(1.0, F0))
+        decision = 1;
+      else if (it >= max_iter)
+        decision = 2;
+      else if (s_sc[1] > 0.0)
+        decision = 3;
+      if (decision == 1) { active[b] = 0; st_all[b] = NYS_OK; }
+      if (decision == 2) { active[b] = 0; st_all[b] = NYS_ENOCONV; }
+      if (decision == 3) { active[b] = 2; atomicOr(&flags[1], 1); }
+      s_flag = decision;
+    }
+    __syncthreads();
+    if (s_flag != 0) return;
+  }
+  // 3. H = D + B G B^T, rhs = -(D x + C^T lambda + B v)  (B = I in omega mode)
+  if (om) {
+    for (int e = threadIdx.x; e < M1 * M1; e += blockDim.x) {
+      const int k = e / M1, l = e - k * M1;
+      Hs[k * ldh + l] = Gs[k * ldg + l] + ((k == l && k < me) ? 1.0 : 0.0);
+    }
+    for (int k = threadIdx.x; k < me; k += blockDim.x)
+      g[k] = -(xb[k] + Gs[k * ldg + D + 1] + s_c[0][k] * lam0 + s_c[1][k] * lam1);
+    if (threadIdx.x == 0) g[me] = -(Gs[D * ldg + D + 1] + lam0);
+    __syncthreads();
+  } else {
+    for (int k = threadIdx.x; k < me; k += blockDim.x) {
+      double s1 = 0.0, s2 = 0.0;
+      for (int j = 0; j < m; ++j) {
+        s1 += W[k * m + j] * Gs[j * ldg + m];
+        s2 += W[k * m + j] * Gs[j * ldg + m + 1];
+      }
+      hb[k] = s1;
+      g[k] = -(xb[k] + s2 + s_c[0][k] * lam0 + s_c[1][k] * lam1);
+    }
+    if (threadIdx.x == 0) g[me] = -(Gs[m * ldg + m + 1] + lam0);
+    __syncthreads();
+    for (int k0 = 0; k0 < me; k0 += 8) {
+      const int kb = min(8, me - k0);
+      for (int e = threadIdx.x; e < kb * m; e += blockDim.x) {
+        const int kk = e / m, l = e - kk * m;
+        double s = 0.0;
+        for (int j = 0; j < m; ++j) s += W[(k0 + kk) * m + j] * Gs[j * ldg + l];
+        Yb[kk * m + l] = s;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < kb * me; e += blockDim.x) {
+        const int kk = e / me, l = e - kk * me;
+        double s = 0.0;
+        for (int j = 0; j < m; ++j) s += Yb[kk * m + j] * W[l * m + j];
+        Hs[(k0 + kk) * ldh + l] = s + ((k0 + kk) == l ? 1.0 : 0.0);
+      }
+      __syncthreads();
+    }
+    for (int k = threadIdx.x; k < me; k += blockDim.x) {
+      Hs[k * ldh + me] = hb[k];
+      Hs[me * ldh + k] = hb[k];
+    }
+    if (threadIdx.x == 0) Hs[me * ldh + me] = Gs[m * ldg + m];
+  }
+  // Householder reflectors of C^T
+  for (int k = threadIdx.x; k < M1; k += blockDim.x) {
+    w[k] = s_c[0][k];
+    c2[k] = s_c[1][k];
+  }
+  __syncthreads();
+  {
+    const double r00 = house(w, Vh, M1, &s_beta[0], red);
+    if (threadIdx.x == 0) s_R[0] = r00;
+    __syncthreads();
+    if (p == 2) {
+      apply_house_vec(c2, M1, Vh, s_beta[0], red);
+      if (threadIdx.x == 0) s_R[1] = c2[0];
+      for (int k = threadIdx.x; k < M1; k += blockDim.x) Vh[M1 + k] = 0.0;
+      __syncthreads();
+      const double r11 = house(c2 + 1, Vh + M1 + 1, M1 - 1, &s_beta[1], red);
+      if (threadIdx.x == 0) s_R[2] = r11;
+      __syncthreads();
+    }
+  }
+  for (int k = 0; k < p; ++k) {
+    apply_house_sym(Hs, ldh, M1, Vh + k * M1, s_beta[k], w, red);
+    apply_house_vec(g, M1, Vh + k * M1, s_beta[k], red);
+  }
+  // y1 = R^{-T} (v - C x)
+  if (threadIdx.x == 0) {
+    double h0 = I.v[0], h1 = (p == 2) ? I.v[1] : 0.0;
+    for (int k = 0; k < me; ++k) { h0 -= s_c[0][k] * xb[k]; h1 -= s_c[1][k] * xb[k]; }
+    h0 -= s_c[0][me] * xb[XS - 3];
+    h1 -= s_c[1][me] * xb[XS - 3];
+    y[0] = h0 / s_R[0];
+    if (p == 2) y[1] = (h1 - s_R[1] * y[0]) / s_R[2];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < N2; i += blockDim.x) {
+    double sv = g[p + i];
+    for (int k = 0; k < p; ++k) sv -= Hs[(p + i) * ldh + k] * y[k];
+    y[p + i] = sv;
+  }
+  __syncthreads();
+  // keep the first p rows of H' for lambda before the factorisation
+  for (int e = threadIdx.x; e < p * M1; e += blockDim.x) Yb[e] = Hs[(e / M1) * ldh + (e % M1)];
+  double* A22 = Hs + p * ldh + p;
+  const bool ok = cta_cholesky(A22, ldh, N2, &s_flag);
+  if (!ok) {
+    if (threadIdx.x == 0) {
+      if (mode == 0) { active[b] = 2; atomicOr(&flags[1], 1); }
+      else { active[b] = 0; st_all[b] = NYS_ENOTSPD; }
+    }
+    return;
+  }
+  cta_chol_solve(A22, ldh, N2, y + p);
+  const double q0 = cta_dot(Yb, y, M1, red);
+  const double q1 = (p == 2) ? cta_dot(Yb + M1, y, M1, red) : 0.0;
+  double dl0 = 0.0, dl1 = 0.0;
+  if (p == 2) {
+    dl1 = (g[1] - q1) / s_R[2];
+    dl0 = (g[0] - q0 - s_R[1] * dl1) / s_R[0];
+  } else {
+    dl0 = (g[0] - q0) / s_R[0];
+  }
+  for (int k = p - 1; k >= 0; --k) apply_house_vec(y, M1, Vh + k * M1, s_beta[k], red);
+  // 4. update x, lambda; dz = B^T dx, z = B^T x
+  for (int k = threadIdx.x; k < M1; k += blockDim.x) {
+    const int slot = (k < me) ? k : XS - 3;
+    xb[slot] += y[k];
+  }
+  if (threadIdx.x == 0) {
+    xb[XS - 2] += dl0;
+    if (p == 2) xb[XS - 1] += dl1;
+    double d2 = 0.0;
+    for (int k = 0; k < M1; ++k) d2 += y[k] * y[k];
+    nrm[(int64_t)b * 4 + 1] = sqrt(d2);
+    iters[b] += 1;
+    active[b] = 1;
+    atomicOr(&flags[0], 1);
+  }
+  __syncthreads();
+  double* zb = zs + (int64_t)b * ZS;
+  double* dzb = dzs + (int64_t)b * ZS;
+  for (int j = threadIdx.x; j <= m; j += blockDim.x) {
+    double s = 0.0, ds = 0.0;
+    if (j < m) {
+      for (int k = 0; k < me; ++k) { s += W[k * m + j] * xb[k]; ds += W[k * m + j] * y[k]; }
+    } else {
+      s = xb[XS - 3];
+      ds = y[me];
+    }
+    zb[j] = s;
+    if (!om) dzb[j] = ds;
+  }
+  // omega mode: the row pass reads the step in omega coordinates, b last
+  if (om)
+    for (int k = threadIdx.x; k < M1; k += blockDim.x) dzb[k] = y[k];
+}
+
+cudaError_t launch_newton_step(const Inst* insts, const Lset* lsets, const double* W,
+                               const double* part, const int64_t* slot_off, const int32_t* lm,
+                               double* xs, double* zs, double* dzs, double* cws, int XS, int ZS,
+                               int M1S, int32_t* st, int32_t* active, int32_t* iters, double* nrm,
+                               int max_iter, double tol, int32_t* flags, int mode, int batch,
+                               int m_max, cudaStream_t s) {
+  const size_t sm = solve_smem_bytes(false, m_max);
+  cudaError_t e = cudaFuncSetAttribute(k_newton_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
+  if (e != cudaSuccess) return e;
+  k_newton_step<<<batch, kSolveThreads, sm, s>>>(insts, lsets, W, part, slot_off, lm, xs, zs, dzs,
+                                                  cws, XS, ZS, M1S, st, active, iters, nrm,
+                                                  max_iter, tol, flags, mode);
+  return cudaGetLastError();
 }
 
 size_t refine_smem_bytes(int k_max) {

@@ -187,3 +187,70 @@ def test_eval_subset_of_instances(api):
     ref = core.solve_linear(probs[0])["y"]
     assert np.abs(y.cpu().numpy() - ref).max() <= 1e-10 * np.abs(ref).max()
     bt.close()
+
+
+def _truncated_set():
+    """Landmark kernels with dropped eigenpairs (lambda <= 1e-12 lambda_max): landmark
+    spacing well below sigma.  The first is Table A.8's P8 setting (m = 50 on [0, 2]
+    with sigma = 1)."""
+    p8 = dict(p=2, n=1000, m=50, t0=0.0, t1=2.0, sigma=1.0, gamma=1e7, v=[-0.5, 1.0], kind="lin",
+              a=[0.0, 36.0], c=0.0, omega=0.0, phi0=np.pi / 2)
+    return [p8, dict(p8, t1=5.0),
+            dict(p=1, n=640, m=50, t0=0.0, t1=5.0, sigma=0.5, gamma=1e10, v=[0.0], kind="lin",
+                 a=[0.3], c=1.0, omega=1.0, phi0=0.0)] + ni.linear_family(2, n=3000, T=5.0, name="trunc")
+
+
+def test_truncated_landmark_kernel_fp64(api):
+    """Ill-conditioned landmark kernels go through omega coordinates (rows projected
+    through W before the Gram): m_eff matches the oracle and so does the fit.
+
+    These systems are themselves sensitive in FP64: the oracle's two exact routes
+    (dense LU of Lemma 1's matrix and the null-space method) already differ by up to
+    ~2e-8 on P8.  The bound per instance is 10x that spread, at least 1e-10."""
+    import torch
+    probs = _truncated_set()
+    bt = api.Batch(probs, precision="fp64")
+    bt.assemble()
+    x, st = bt.solve()
+    grids = [core.grid(q) for q in probs]
+    y, _ = bt.eval(grids)
+    torch.cuda.synchronize()
+    assert (st.cpu().numpy() == 0).all()
+    meff = bt.m_eff()
+    yc = y.cpu().numpy()
+    off = 0
+    for k, (q, g) in enumerate(zip(probs, grids)):
+        ref = core.solve_linear(q)
+        alt = core.solve_linear_nullspace(q)
+        assert ref["m_eff"] < q["m"] and meff[k] == ref["m_eff"]
+        spread = np.abs(alt["y"] - ref["y"]).max() / np.abs(ref["y"]).max()
+        err = np.abs(yc[off:off + len(g)] - ref["y"]).max() / np.abs(ref["y"]).max()
+        assert err <= max(1e-10, 10 * spread), (k, err, spread)
+        off += len(g)
+    bt.close()
+
+
+def test_truncated_landmark_kernel_mixed_reports_eprecision(api):
+    """The mixed path refuses (NYS_EPRECISION) the instances whose landmark kernel is
+    too ill-conditioned for its FP32 factor, and solves the others as usual."""
+    import torch
+    good = ni.small_linear(B=3, sub=7)
+    bad = _truncated_set()[:2]
+    probs = [good[0], bad[0], good[1], bad[1], good[2]]
+    bt = api.Batch(probs, precision="mixed")
+    bt.assemble()
+    x, st = bt.solve()
+    grids = [core.grid(q) for q in probs]
+    y, _ = bt.eval(grids)
+    torch.cuda.synchronize()
+    st = st.cpu().numpy()
+    assert list(st) == [0, -8, 0, -8, 0], st
+    yc = y.cpu().numpy()
+    off = 0
+    for k, (q, g) in enumerate(zip(probs, grids)):
+        if st[k] == 0:
+            ref = core.solve_linear(q)
+            err = np.abs(yc[off:off + len(g)] - ref["y"]).max() / np.abs(ref["y"]).max()
+            assert err <= TOL["mixed"], (k, err)
+        off += len(g)
+    bt.close()
