@@ -165,12 +165,19 @@ int32_t nys_newton(nys_ctx* c, void* stream, int32_t max_iter, double tol,
                    double* x_out, double* y_aux_out, int32_t* iters_out,
                    int32_t* status_out);
 
-/* Adjoint gradient (NYS_COEF_LIN, p = 2) of a loss on y^(tau) with respect to
-   theta = (a_1, a_2, c, omega, y0, y0', sigma) of the last nys_solve:
-   one adjoint solve with the stored factor and one fused row pass.
-   obs_t: device observation times, obs_off: device int64[batch + 1],
-   dl_dy: device dloss/dy^(obs_t) (same length as obs_t),
-   grad_out: device, batch x 7 doubles.                                        */
+/* Adjoint gradient (parameter estimation; the paper cites the use and prints no
+   formula) of a loss on the fitted model of the last nys_solve, for NYS_COEF_LIN
+   instances: theta = (a_1, a_2, c, omega, y0, y0', sigma) of
+   y^(p) + a_1 y^(p-1) [+ a_2 y] = c sin(omega t + phi0).  The implicit-function
+   derivative of Lemma 1's system: one adjoint solve with the stored FP64 factor
+   and one fused row pass.  Needs a NYS_FP64 context.
+   obs_t: device observation times, obs_off: device int64[batch + 1] offsets,
+   dl_dy: device d loss / d y^(obs_t) (same length as obs_t),
+   grad_out: device, batch x 7 doubles (a_2 and y0' entries 0 when p = 1).
+   Instances whose solve failed get NaN; the sigma entry is NaN when the
+   landmark kernel was truncated (m_eff < m), where sigma also moves the
+   discarded eigenvectors.  Errors: NYS_EINVAL (NULL pointer, nonlinear batch),
+   NYS_ESTATE (MIXED context, or no solve yet), NYS_ECUDA.                   */
 int32_t nys_grad(nys_ctx* c, void* stream, const double* obs_t, const int64_t* obs_off,
                  const double* dl_dy, double* grad_out);
 

@@ -14,6 +14,9 @@ from . import _abi as A
 
 _KIND = {"table": A.NYS_COEF_TABLE, "lin": A.NYS_COEF_LIN, "nl": A.NYS_COEF_POLY_NL}
 
+# order of the gradient entries of nys_grad (kind "lin")
+THETA = ("a", "b", "c", "omega", "y0", "y0p", "sigma")
+
 
 def _stream_handle(stream=None):
     s = torch.cuda.current_stream() if stream is None else stream
@@ -79,6 +82,7 @@ class Batch:
         dev = torch.device("cuda", torch.cuda.current_device())
         self.x = torch.zeros(self.B, self.XS, dtype=torch.float64, device=dev)
         self.status = torch.zeros(self.B, dtype=torch.int32, device=dev)
+        self.version = 0   # bumped by every solve; nys_grad differentiates the latest
 
     def close(self):
         if getattr(self, "ctx", None) is not None:
@@ -101,10 +105,12 @@ class Batch:
 
     def solve(self):
         A.nys_solve(self.ctx, _stream_handle(self.stream), _ptr(self.x), _ptr(self.status))
+        self.version += 1
         return self.x, self.status
 
     def run(self):
         A.nys_run(self.ctx, _stream_handle(self.stream), _ptr(self.x), _ptr(self.status))
+        self.version += 1
         return self.x, self.status
 
     def m_eff(self):
@@ -115,6 +121,12 @@ class Batch:
     def eval(self, tq, tq_off=None, deriv=0):
         """tq: list of per-instance query arrays (instances 0..len(tq)-1; the rest get
         none), or a flat CUDA tensor with int64 offsets of length batch + 1."""
+        tq, tq_off = self._queries(tq, tq_off)
+        y = torch.empty_like(tq)
+        A.nys_eval(self.ctx, _stream_handle(self.stream), _ptr(tq), _ptr(tq_off), int(deriv), _ptr(y))
+        return y, tq_off
+
+    def _queries(self, tq, tq_off):
         dev = self.x.device
         if tq_off is None:
             if len(tq) > self.B:
@@ -125,9 +137,7 @@ class Batch:
                               dtype=torch.float64, device=dev)
         if tq_off.numel() != self.B + 1:
             raise ValueError("tq_off must have batch + 1 entries")
-        y = torch.empty_like(tq)
-        A.nys_eval(self.ctx, _stream_handle(self.stream), _ptr(tq), _ptr(tq_off), int(deriv), _ptr(y))
-        return y, tq_off
+        return tq, tq_off
 
     def newton(self, max_iter=50, tol=1e-10, want_y=False):
         dev = self.x.device
@@ -140,6 +150,12 @@ class Batch:
         return self.x, self.status, iters, yaux
 
     def grad(self, obs_t, obs_off, dl_dy):
+        """d loss / d theta (batch x 7, order THETA) of the last solve, given the
+        upstream d loss / d y^(obs_t) (flat CUDA float64 tensors as for eval)."""
+        obs_t, obs_off = self._queries(obs_t, obs_off)
+        dl_dy = torch.as_tensor(dl_dy, dtype=torch.float64, device=self.x.device).contiguous()
+        if dl_dy.numel() != obs_t.numel():
+            raise ValueError("dl_dy must have one entry per observation time")
         g = torch.empty(self.B, 7, dtype=torch.float64, device=self.x.device)
         A.nys_grad(self.ctx, _stream_handle(self.stream), _ptr(obs_t), _ptr(obs_off), _ptr(dl_dy), _ptr(g))
         return g
@@ -151,3 +167,60 @@ class Batch:
         for b in range(self.B):
             out.append(dict(omega=x[b, :self.XS - 3], b=x[b, self.XS - 3], lam=x[b, self.XS - 2:]))
         return out
+
+
+def problems_with_theta(problems, theta):
+    """Copies of the "lin" problem dicts with (a_1, a_2, c, omega, y0, y0', sigma)
+    taken from the rows of theta (batch x 7)."""
+    th = np.asarray(theta, dtype=np.float64).reshape(len(problems), 7)
+    out = []
+    for q, t in zip(problems, th):
+        if q["kind"] != "lin":
+            raise ValueError("theta applies to kind 'lin' problems only")
+        p = int(q["p"])
+        r = dict(q)
+        r["a"] = [float(t[0]), float(t[1])][:p]
+        r["c"], r["omega"] = float(t[2]), float(t[3])
+        r["v"] = [float(t[4]), float(t[5])][:p]
+        r["sigma"] = float(t[6])
+        out.append(r)
+    return out
+
+
+def theta_of(problems):
+    """The batch x 7 parameter array (order THETA) of "lin" problem dicts."""
+    th = np.zeros((len(problems), 7))
+    for k, q in enumerate(problems):
+        a = list(q["a"]) + [0.0] * (2 - len(q["a"]))
+        v = list(q["v"]) + [0.0] * (2 - len(q["v"]))
+        th[k] = [a[0], a[1], q["c"], q["omega"], v[0], v[1], q["sigma"]]
+    return th
+
+
+class NysSolve(torch.autograd.Function):
+    """Fitted values y^(tau) of the FP64 linear solve as a differentiable function of
+    theta (batch x 7 float64, order THETA).
+
+    forward: nys_update with theta, nys_assemble, nys_solve, nys_eval at tau.
+    backward: nys_grad with the upstream gradient (one adjoint solve + one row pass).
+    The Batch must be FP64; backward refers to the Batch's latest solve, so only
+    one forward per Batch may be awaiting its backward.
+    """
+
+    @staticmethod
+    def forward(ctx, theta, batch, tq, tq_off):
+        batch.update(problems_with_theta(batch.problems, theta.detach().cpu().numpy()))
+        batch.assemble()
+        batch.solve()
+        y, _ = batch.eval(tq, tq_off)
+        ctx.batch, ctx.version, ctx.theta_device = batch, batch.version, theta.device
+        ctx.save_for_backward(tq, tq_off)
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        if ctx.batch.version != ctx.version:
+            raise RuntimeError("NysSolve: the Batch was solved again after this forward")
+        tq, tq_off = ctx.saved_tensors
+        g = ctx.batch.grad(tq, tq_off, gy.to(torch.float64).contiguous())
+        return g.to(ctx.theta_device), None, None, None

@@ -41,6 +41,13 @@ cudaError_t launch_eval(const Inst* insts, const double* zs, int ZS, const int32
                         cudaStream_t s);
 
 int64_t fac_elems(int m_max);
+size_t grad_adj_stride(int ZS);
+cudaError_t launch_grad(const Inst* insts, const Lset* lsets, const double* W, const double* fac,
+                        int64_t facs, const double* xs, const double* zs, const int32_t* lm, int XS,
+                        int ZS, const int32_t* st, const double* obs_t, const int64_t* obs_off,
+                        const double* dl_dy, double* adj, const Work* rwork, int nrwork,
+                        int* counter, double* part, const int64_t* slot_off, double* grad_out,
+                        double gamma_scale, int batch, int num_sms, cudaStream_t s);
 cudaError_t launch_newton_init(const Inst* insts, double* xs, double* zs, double* dzs, double* yaux,
                                double* nrm, int32_t* iters, int32_t* active, int32_t* st,
                                const int32_t* st_init, int XS, int ZS, int batch, cudaStream_t s);
@@ -480,7 +487,7 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
         w.slot = slot++;
         rwl.push_back(w);
         soff.push_back(poff);
-        poff += q[b].m + 1;
+        poff += std::max(q[b].m + 1, 8);   // refinement: m + 1; gradient: 5
       }
     }
   }
@@ -526,6 +533,7 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   A(c->zs.alloc((size_t)batch * c->ZS));
   A(c->dzs.alloc((size_t)batch * c->ZS));
   A(c->cws.alloc((size_t)batch * 2 * c->M1S));
+  if (c->any_lin && !c->fp32) A(c->adj.alloc((size_t)batch * grad_adj_stride(c->ZS)));
   A(c->st.alloc(batch));
   A(c->stinit.alloc(batch));
   A(c->counter.alloc(1));
@@ -754,8 +762,15 @@ int32_t nys_newton(nys_ctx* c, void* stream, int32_t max_iter, double tol, doubl
 
 int32_t nys_grad(nys_ctx* c, void* stream, const double* obs_t, const int64_t* obs_off,
                  const double* dl_dy, double* grad_out) {
-  (void)c; (void)stream; (void)obs_t; (void)obs_off; (void)dl_dy; (void)grad_out;
-  return fail(NYS_ESTATE, "nys_grad: not available in this build");
+  if (!c || !obs_t || !obs_off || !dl_dy || !grad_out) return fail(NYS_EINVAL, "nys_grad: NULL argument");
+  if (c->any_nl) return fail(NYS_EINVAL, "nys_grad: defined for linear (NYS_COEF_LIN) batches");
+  if (c->fp32) return fail(NYS_ESTATE, "nys_grad: needs a context created with precision NYS_FP64");
+  if (!c->solved) return fail(NYS_ESTATE, "nys_grad: no solution yet");
+  CK(launch_grad(c->inst.p, c->lset.p, c->W.p, (const double*)c->fac.p, c->facs, c->xs.p, c->zs.p,
+                 c->lm.p, c->XS, c->ZS, c->st.p, obs_t, obs_off, dl_dy, c->adj.p, c->rwork.p,
+                 c->nrwork, c->counter.p, c->part.p, c->slot_off.p, grad_out, 1.0, c->batch,
+                 c->num_sms, (cudaStream_t)stream));
+  return NYS_OK;
 }
 
 }  // extern "C"

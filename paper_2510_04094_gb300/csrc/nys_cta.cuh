@@ -50,6 +50,25 @@ __device__ T cta_dot(const T* a, const T* b, int n, T* red) {
   return r;
 }
 
+// Sum over the block of one value per thread (every thread gets the sum).
+template <typename T>
+__device__ T cta_sum(T s, T* red) {
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    red[32] = t;
+  }
+  __syncthreads();
+  const T r = red[32];
+  __syncthreads();
+  return r;
+}
+
 // Householder vector of x[0..n): v with v[0] = x0 + sign(x0)|x|, beta = 2/(v^T v),
 // (I - beta v v^T) x = -sign(x0)|x| e_0.  Returns the diagonal value.
 template <typename T>
