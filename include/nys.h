@@ -4,7 +4,7 @@
  * Method (arXiv 2510.04094): an ODE y^(p) = f(t, y, ..) on a grid t_1..t_n is
  * fitted by y^(t) = omega^T phi(t) + b, where phi(t) = Lambda^{-1/2} U^T k(t)
  * is the explicit Nystrom feature map built from the eigendecomposition
- * Omega_mm = U Lambda U^T of the m x m landmark kernel (Appendix A.2, eq32),
+ * Omega_mm = U Lambda U^T of the m x m landmark kernel (Appendix A.3, eq32),
  * k_j(t) = K(t, s_j) = exp(-(t - s_j)^2 / sigma^2) (Section 3, RBF kernel).
  * Linear ODEs: the primal system of Lemma 1 (Section 3.1).  Nonlinear ODEs:
  * Lemma 2 (Section 3.2, Eq. 2.2) solved by Newton's method (Eq. 3.2.1).
@@ -100,7 +100,7 @@ typedef struct nys_ctx nys_ctx;
 /* Create a context for `batch` instances (host array `inst`), allocate all
    device workspaces, upload the descriptors and enqueue the Nystrom setup
    (landmark kernel, FP64 eigendecomposition, W = Lambda^{-1/2} U^T;
-   Appendix A.2, Eq. 10 and eq32).  Instances with identical landmark sets
+   Appendix A.3 and the feature map eq32).  Instances with identical landmark sets
    (same m, grid spacing/sigma and indices) share one factor.
    Errors: NYS_EINVAL (bad instance: message names it), NYS_ENOMEM, NYS_ECUDA. */
 int32_t nys_setup(nys_ctx** out, const nys_instance* inst, int32_t batch,

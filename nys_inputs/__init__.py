@@ -12,7 +12,7 @@ Problem dict fields (see oracle/core.py for their meaning):
       nl  : P = [c0, c1, c2, c3], delta, g, omega y^(p) = P(y) - delta y^(p-1) + g cos(omega t)
       table: f (p x n), r (n)                    y^(p) - sum f_k y^(p-k) = r
 
-The workloads mirror the paper's scales (Appendix A.7: n up to 1e4-5e4,
+The workloads mirror the paper's scales (Appendix B.5: n up to 1e4-5e4,
 m = 20..200) on synthetic coefficient draws, since the paper's sixteen textbook
 problems are not a dataset.
 """

@@ -8,10 +8,10 @@ baseline leg of ``bench.py`` use it.  It shares no code with the CUDA path
 Modules
 -------
 ``core``     RBF kernel and its t-derivatives (Section 3, Eq. 9 and the two
-             derivative formulas after it), the Nystrom factor (Appendix A.2),
+             derivative formulas after it), the Nystrom factor (Appendix A.3),
              explicit features (eq32), the linear primal system of Lemma 1
-             (Section 3.1, proof in Appendix A.3 "Proof 1") and its solve.
-``newton``   Lemma 2 (Section 3.2, Eq. 2.2, proof in Appendix A.4 "Proof 2"):
+             (Section 3.1, proof in Appendix A.4) and its solve.
+``newton``   Lemma 2 (Section 3.2, Eq. 2.2, proof in Appendix A.5):
              the nonlinear KKT system F = grad L = 0 solved by Newton's method
              (Eq. 3.2.1), dense (m+n+p) Jacobian for small n and the exactly
              equivalent reduced (y-eliminated) form for large n.
@@ -26,7 +26,7 @@ Every function states the passage it follows.  Where the paper is silent or
 garbled, the reading taken is stated in the docstring.
 
 Parity status: all functions here are pinned by ``tests/test_oracle_*.py``
-(closed forms, the paper's Table A.8 accuracy figures, exact identities,
+(closed forms, the accuracy figures of the paper's table in Appendix B.7, exact identities,
 finite differences, brute-force minimisation); none is "parity unpinned"
 except the Duffing accuracy against the true solution, which has no closed form
 (the oracle's Duffing Newton iterate is pinned only through its KKT conditions).

@@ -80,10 +80,10 @@ def rbf_du(u, v, sigma, ell):
 
 
 # --------------------------------------------------------------------------
-# Nystrom factor and features (Appendix A.2, eq32)
+# Nystrom factor and features (Appendix A.3, eq32)
 # --------------------------------------------------------------------------
 def nystrom_factor(s, sigma, tau=TAU_DEFAULT):
-    """Eigen-decompose the landmark kernel Omega_(m,m) (Appendix A.2, Eq. 10).
+    """Eigen-decompose the landmark kernel Omega_(m,m) (Appendix A.3).
 
     Returns (W, lam, U) with lam descending, eigenpairs below tau*lam_max
     dropped, and W = diag(lam)^{-1/2} U^T  (m_eff x m), so that the explicit
@@ -138,7 +138,7 @@ def linear_coefficients(prob, t):
 # Lemma 1: the primal linear system
 # --------------------------------------------------------------------------
 def setup(prob, tau=TAU_DEFAULT):
-    """Grid, landmarks and Nystrom factor for one problem (Appendix A.2)."""
+    """Grid, landmarks and Nystrom factor for one problem (Appendix A.3)."""
     t = grid(prob)
     idx = landmark_indices(prob)
     s = t[idx]

@@ -7,7 +7,7 @@ Problem family ('nl' in ``core``):  y^(p) = f(t, y, y^(p-1)) with
     P(y) = c0 + c1 y + c2 y^2 + c3 y^3.
 This covers y' = 1 - y^2 (tanh), the logistic equation and the Duffing equation.
 
-Eq. 2.2 / Appendix A.4 "Proof 2": unknowns (omega, b, lambda_1..lambda_p, y_2..y_n),
+Eq. 2.2 / Appendix A.5: unknowns (omega, b, lambda_1..lambda_p, y_2..y_n),
     L = 1/2 |omega|^2 + gamma/2 sum e_i^2 + gamma/2 sum xi_i^2 + sum_k lambda_k h_k
     e_i  = omega^T phi^(p)(t_i) - f(t_i, y_i, omega^T phi^(p-1)(t_i))
     xi_i = y_i - omega^T phi(t_i) - b
@@ -16,7 +16,7 @@ The system F = grad L = 0 (Y_1..Y_{p+3} of Lemma 2) is solved by Newton's method
 
 Readings (also in DESIGN.md):
  * Only y_i is an auxiliary unknown; the derivative y^(p-1) inside f is
-   omega^T phi^(p-1)(t_i) (as in the worked Problem 15 of Appendix A.6).
+   omega^T phi^(p-1)(t_i) (as in the worked Problem 15 of Appendix B.2).
  * Start: omega = 0, b = v_1, lambda = 0, y_i = v_1.  Undamped steps.
  * Full Newton; an iteration falls back to the Gauss-Newton Hessian (the
    e_i * P''(y_i) term dropped) when some diagonal entry
@@ -90,7 +90,7 @@ class Pieces:
         return e, xi, h, P, dP, d2P
 
     def lagrangian(self, x):
-        """Scalar L of Appendix A.4 evaluated from its definition."""
+        """Scalar L of Appendix A.5 evaluated from its definition."""
         om, b, lam, y = self.split(x)
         e, xi, h, *_ = self.residuals(x)
         g = self.gamma

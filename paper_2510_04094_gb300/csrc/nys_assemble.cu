@@ -287,10 +287,13 @@ k_assemble_f32(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
       __syncthreads();
     }
     // add the S slice sums (FP32) and store the packed upper triangle as doubles
-    float* red = sm32;  // S * U * 64 floats <= 384 * 64 (the tile and table are dead)
+    // entry k of every thread's block at red[k * SU + thread]: consecutive threads
+    // store to consecutive words (no bank conflicts)
+    float* red = sm32;  // 64 * S * U floats <= 64 * 384 (the tile and table are dead)
+    const int SU = S * U;
     if (active) {
 #pragma unroll
-      for (int k = 0; k < 64; ++k) red[(slice * U + u) * 64 + k] = acc[k];
+      for (int k = 0; k < 64; ++k) red[k * SU + slice * U + u] = acc[k];
     }
     __syncthreads();
     // slot layout: [first landmark, landmark count, packed upper local Gram]
@@ -305,7 +308,7 @@ k_assemble_f32(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
       const int ub = cb * NB - cb * (cb - 1) / 2 + (lb - cb);
       const int k = (j & 7) * 8 + (l & 7);
       float sum = 0.f;
-      for (int q = 0; q < S; ++q) sum += red[(q * U + ub) * 64 + k];
+      for (int q = 0; q < S; ++q) sum += red[k * SU + q * U + ub];
       out[2 + e] = (double)sum;
     }
     __syncthreads();

@@ -1,7 +1,7 @@
 // Newton's method for nonlinear ODEs (Lemma 2, Section 3.2; Eq. 2.2; Eq. 3.2.1).
 //
 // Family: y^(p) = f(t, y, y^(p-1)),  f = P(y) - delta y^(p-1) [p = 2] + g cos(omega t),
-// P(y) = c0 + c1 y + c2 y^2 + c3 y^3.  Lagrangian (Appendix A.4):
+// P(y) = c0 + c1 y + c2 y^2 + c3 y^3.  Lagrangian (Appendix A.5):
 //   L = 1/2 |omega|^2 + gamma/2 sum e_i^2 + gamma/2 sum xi_i^2 + sum_k lambda_k h_k,
 //   e_i = omega^T q_i - P(y_i) - rho_i,   q_i = phi^(p)(t_i) + delta phi^(p-1)(t_i),
 //   xi_i = y_i - omega^T phi(t_i) - b,    rho_i = g cos(omega t_i).

@@ -1,4 +1,4 @@
-// Nystrom setup (Appendix A.2, Eq. 10 and eq32): landmark kernel Omega_mm,
+// Nystrom setup (Appendix A.3 and the feature map eq32): landmark kernel Omega_mm,
 // symmetric eigendecomposition in FP64, feature factor W = Lambda^{-1/2} U^T
 // with eigenpairs below tau * lambda_max dropped.
 //

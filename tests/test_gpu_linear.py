@@ -191,7 +191,7 @@ def test_eval_subset_of_instances(api):
 
 def _truncated_set():
     """Landmark kernels with dropped eigenpairs (lambda <= 1e-12 lambda_max): landmark
-    spacing well below sigma.  The first is Table A.8's P8 setting (m = 50 on [0, 2]
+    spacing well below sigma.  The first is the P8 setting of the table in Appendix B.7 (m = 50 on [0, 2]
     with sigma = 1)."""
     p8 = dict(p=2, n=1000, m=50, t0=0.0, t1=2.0, sigma=1.0, gamma=1e7, v=[-0.5, 1.0], kind="lin",
               a=[0.0, 36.0], c=0.0, omega=0.0, phi0=np.pi / 2)

@@ -1,7 +1,7 @@
 """Pins of the oracle's linear path against things other than itself.
 
 Kernel derivatives vs finite differences and Hermite polynomials, exact Nystrom
-identities, the printed accuracy of the paper (Table A.8), closed-form ODE
+identities, the printed accuracy of the paper (table in Appendix B.7), closed-form ODE
 solutions, brute-force optimality of the primal problem, invariances.
 """
 import math
@@ -14,7 +14,7 @@ from numpy.polynomial import hermite as H
 import nys_inputs as ni
 from oracle import core, dual
 
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_table_A8.txt")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_table_B7.txt")
 
 
 # ---------------------------------------------------------------- kernel ----
@@ -231,7 +231,7 @@ def _exact(name, t):
 
 
 @pytest.mark.parametrize("row", _golden_rows(), ids=lambda r: r[0])
-def test_paper_table_A8_accuracy(row):
+def test_paper_table_B7_accuracy(row):
     """The paper's printed NLS-SVM errors are matched to within the freedom the paper
     leaves open (landmark positions, handling of the numerically singular landmark
     kernel): ours is at most 2x each printed figure and, for P7 and P9, at least 1/10
