@@ -42,7 +42,8 @@ typedef enum {
   NYS_ENOTSPD = -4,     /* per instance: projected Hessian not positive definite */
   NYS_ENOCONV = -5,     /* per instance: Newton iteration cap reached           */
   NYS_ENONFINITE = -6,  /* per instance: NaN/Inf in inputs or results           */
-  NYS_ETIMEOUT = -7,    /* reserved: a bounded device wait gave up              */
+  NYS_ETIMEOUT = -7,    /* per instance: a bounded device wait gave up (the
+                           tensor-core assembly); the GPU context stays usable */
   NYS_EPRECISION = -8,  /* per instance, MIXED: landmark kernel too ill-conditioned
                            for the FP32 factor (kept lambda_min < 1e-7 lambda_max);
                            solve that instance with NYS_FP64                   */
@@ -88,12 +89,18 @@ typedef struct {
   int32_t precision;     /* nys_precision.  MIXED: FP32 assembly and FP32 factor,
                             refined against FP64-accurate residuals.             */
   int32_t refine_steps;  /* MIXED: residual passes after the first solve (0..8;
-                            default 2 when negative)                             */
+                            default 1 when negative: one pass brings every
+                            parity workload to <= 2e-7 of the FP64 solution)   */
   double eig_tau;        /* drop eigenpairs with lambda <= tau * lambda_max
                             (default 1e-12 when <= 0)                            */
   int32_t scale_sqrt_m;  /* 1: eq32's sqrt(m) feature scale (== gamma * m)      */
-  int32_t reserved;
+  int32_t assembly;      /* MIXED only, nys_assembly: NYS_ASM_AUTO (0) runs the
+                            Gram on the tensor cores (tcgen05, TF32 hi/lo split,
+                            FP32 accumulation in tensor memory); NYS_ASM_SIMT (1)
+                            on the CUDA cores (FP32 FMA, 8x8 register blocks)  */
 } nys_options;
+
+typedef enum { NYS_ASM_AUTO = 0, NYS_ASM_SIMT = 1 } nys_assembly;
 
 typedef struct nys_ctx nys_ctx;
 

@@ -13,6 +13,7 @@ NYS_OK, NYS_EINVAL, NYS_ENOMEM, NYS_ECUDA = 0, -1, -2, -3
 NYS_ENOTSPD, NYS_ENOCONV, NYS_ENONFINITE, NYS_ETIMEOUT = -4, -5, -6, -7
 NYS_EPRECISION, NYS_ESTATE = -8, -9
 NYS_FP64, NYS_MIXED = 0, 1
+NYS_ASM_AUTO, NYS_ASM_SIMT = 0, 1
 NYS_COEF_TABLE, NYS_COEF_LIN, NYS_COEF_POLY_NL = 0, 1, 2
 NYS_M_MAX = 112
 
@@ -26,7 +27,7 @@ class nys_instance(C.Structure):
 
 class nys_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("refine_steps", C.c_int32), ("eig_tau", C.c_double),
-                ("scale_sqrt_m", C.c_int32), ("reserved", C.c_int32)]
+                ("scale_sqrt_m", C.c_int32), ("assembly", C.c_int32)]
 
 
 class NysError(RuntimeError):

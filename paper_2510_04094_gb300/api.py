@@ -67,7 +67,7 @@ class Batch:
     """A batch of ODE instances bound to one nys_ctx on the current CUDA device."""
 
     def __init__(self, problems, precision="fp64", refine_steps=-1, eig_tau=0.0,
-                 scale_sqrt_m=False, stream=None):
+                 scale_sqrt_m=False, stream=None, assembly="auto"):
         self.problems = list(problems)
         self.B = len(self.problems)
         self.stream = stream
@@ -76,6 +76,7 @@ class Batch:
         opt.refine_steps = int(refine_steps)
         opt.eig_tau = float(eig_tau)
         opt.scale_sqrt_m = 1 if scale_sqrt_m else 0
+        opt.assembly = {"auto": A.NYS_ASM_AUTO, "simt": A.NYS_ASM_SIMT}[assembly]
         arr, keep = pack_instances(self.problems)
         self.ctx = A.nys_setup(arr, self.B, opt, _stream_handle(stream))
         self.XS = A.nys_x_stride(self.ctx)

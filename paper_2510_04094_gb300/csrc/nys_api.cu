@@ -23,12 +23,13 @@ cudaError_t launch_assemble(bool fp32, const Inst* insts, const Lset* lsets, con
                             const double* W, const Work* work, int nwork, int* counter,
                             const int32_t* lm, const double* tab, double* part,
                             const int64_t* slot_off, int m_max, int k_max, int num_sms,
-                            cudaStream_t st);
+                            cudaStream_t st, int asm_kind, int32_t* err);
 cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const double* W,
                          const float* W32, const double* part, const int64_t* slot_off,
                          const int32_t* lm, void* fac, int64_t facs, double* xs, double* zs,
                          double* cws, int XS, int ZS, int M1S, const int32_t* st_init,
-                         int32_t* st, double gamma_scale, int batch, int m_max, cudaStream_t s);
+                         int32_t* st, double gamma_scale, int batch, int m_max, cudaStream_t s,
+                         const int32_t* asm_err);
 cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W, const float* lag,
                           const Work* work, int nwork, int* counter, const int32_t* lm,
                           const double* tab,
@@ -149,7 +150,7 @@ struct nys_ctx {
   DBuf<double> lam;
   DBuf<unsigned char> fac;
   DBuf<double> xs, zs, dzs, cws;
-  DBuf<int32_t> st, stinit, counter;
+  DBuf<int32_t> st, stinit, counter, err;
   // Newton state
   DBuf<double> yaux, rowstate, nrm;
   DBuf<int64_t> row_off;
@@ -264,6 +265,7 @@ static int32_t pack(nys_ctx* c, const nys_instance* q, bool first) {
     I.hs = I.h / s.sigma;
     I.th0 = mod2pi(s.c[3] * s.t0 + s.c[4]);
     I.dth = mod2pi(s.c[3] * I.h);
+    I.rk = row_const(I);
     I.tab_off = -1;
     if (s.kind == NYS_COEF_TABLE) {
       I.tab_off = (int64_t)c->h_tab.size();
@@ -405,7 +407,12 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
     delete c;
     return fail(NYS_EINVAL, "nys_setup: unknown precision %d", c->opt.precision);
   }
-  if (c->opt.refine_steps < 0) c->opt.refine_steps = 2;
+  if (c->opt.assembly != NYS_ASM_AUTO && c->opt.assembly != NYS_ASM_SIMT) {
+    const int a = c->opt.assembly;
+    delete c;
+    return fail(NYS_EINVAL, "nys_setup: unknown assembly kernel %d", a);
+  }
+  if (c->opt.refine_steps < 0) c->opt.refine_steps = 1;
   if (c->opt.refine_steps > 8) { delete c; return fail(NYS_EINVAL, "nys_setup: refine_steps > 8"); }
   c->fp32 = (c->opt.precision == NYS_MIXED);
   for (int b = 0; b < batch; ++b) {
@@ -537,6 +544,7 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   A(c->st.alloc(batch));
   A(c->stinit.alloc(batch));
   A(c->counter.alloc(1));
+  A(c->err.alloc(1));
   if (c->any_nl) {
     A(c->yaux.alloc((size_t)ytot));
     A(c->rowstate.alloc((size_t)ytot * 4));
@@ -602,7 +610,7 @@ int32_t nys_assemble(nys_ctx* c, void* stream) {
   }
   CK(launch_assemble(c->fp32, c->inst.p, c->lset.p, c->lag.p, c->W.p, c->work.p,
                      c->nwork, c->counter.p, c->lm.p, c->tab.p, c->part.p, c->slot_off.p, c->m_max,
-                     c->k_max, c->num_sms, (cudaStream_t)stream));
+                     c->k_max, c->num_sms, (cudaStream_t)stream, c->opt.assembly, c->err.p));
   c->assembled = true;
   return NYS_OK;
 }
@@ -611,7 +619,8 @@ static int32_t solve_impl(nys_ctx* c, cudaStream_t s, double* x_out, int32_t* st
   const double gscale = 1.0;
   CK(launch_solve(c->fp32, c->inst.p, c->lset.p, c->W.p, c->W32.p, c->part.p, c->slot_off.p,
                   c->lm.p, c->fac.p, c->facs, c->xs.p, c->zs.p, c->cws.p, c->XS, c->ZS, c->M1S,
-                  c->stinit.p, c->st.p, gscale, c->batch, c->m_max, s));
+                  c->stinit.p, c->st.p, gscale, c->batch, c->m_max, s,
+                  c->fp32 ? c->err.p : nullptr));
   if (c->fp32) {
     for (int k = 0; k < c->opt.refine_steps; ++k)
       CK(launch_refine(c->inst.p, c->lset.p, c->W.p, c->lag.p, c->rwork.p, c->nrwork, c->counter.p,
@@ -658,7 +667,8 @@ int32_t nys_run(nys_ctx* c, void* stream, double* x_out, int32_t* status_out) {
       if (e2 == cudaSuccess)
         e2 = launch_assemble(c->fp32, c->inst.p, c->lset.p, c->lag.p, c->W.p,
                              c->work.p, c->nwork, c->counter.p, c->lm.p, c->tab.p, c->part.p,
-                             c->slot_off.p, c->m_max, c->k_max, c->num_sms, cs);
+                             c->slot_off.p, c->m_max, c->k_max, c->num_sms, cs, c->opt.assembly,
+                             c->err.p);
       if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(cs, c->ev_join, 0);
       if (e2 != cudaSuccess) r = fail(NYS_ECUDA, "capture: assemble: %s", cudaGetErrorString(e2));
       if (r == NYS_OK) r = solve_impl(c, cs, x_out, status_out);

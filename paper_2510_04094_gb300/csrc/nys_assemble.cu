@@ -206,7 +206,7 @@ k_assemble_f32(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     const int MP = round_up(M2, 8), NB = MP / 8, U = NB * (NB + 1) / 2;
     const int S = max(1, kAsm32Threads / U);
     const int ld = MP + kPadF;
-    const RowConst RK = row_const(I);
+    const RowConst RK = I.rk;
 
     // this thread's block (bj <= bl) and slice
     const bool active = tid < U * S;
@@ -329,6 +329,11 @@ size_t asm_smem_bytes(bool fp32, int m_max, int k_cap) {
   return sizeof(double) * 2 * (size_t)kAsm64Rows * (M2 + 1);
 }
 
+cudaError_t launch_assemble_tc(const Inst* insts, const Lset* lsets, const Work* work, int nwork,
+                               int* counter, const int32_t* lm, const double* tab, double* part,
+                               const int64_t* slot_off, int32_t* err, int num_sms,
+                               cudaStream_t st);
+
 template <int K>
 static cudaError_t launch64(const Inst* insts, const Lset* lsets, const double* W,
                             const Work* work, int nwork, int* counter, const int32_t* lm,
@@ -346,9 +351,17 @@ cudaError_t launch_assemble(bool fp32, const Inst* insts, const Lset* lsets, con
                             const double* W, const Work* work, int nwork, int* counter,
                             const int32_t* lm, const double* tab, double* part,
                             const int64_t* slot_off, int m_max, int k_max, int num_sms,
-                            cudaStream_t st) {
+                            cudaStream_t st, int asm_kind, int32_t* err) {
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
+  if (err != nullptr) {  // error word read by the solve (NYS_ETIMEOUT)
+    e = cudaMemsetAsync(err, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+  }
+  if (fp32 && asm_kind == NYS_ASM_AUTO && err != nullptr) {  // tensor-core Gram
+    return launch_assemble_tc(insts, lsets, work, nwork, counter, lm, tab, part, slot_off, err,
+                              num_sms, st);
+  }
   // k_cap: capacity of the shared-memory kappa table, fixed at launch (an update
   // that lengthens the lag tables makes those instances use computed features)
   const int k_cap = 0;  // features are computed, no table in shared memory

@@ -13,6 +13,17 @@ constexpr int kM1Max = kMMax + 1;         // (omega, b)
 constexpr int kM2Max = kMMax + 2;         // augmented row [kappa; -f_p; r]
 constexpr int kMPMax = 120;               // kM2Max rounded up to a multiple of 8
 
+struct ff { float hi, lo; };
+
+// Constants of an instance in float-float (computed once on the host), so that
+// the per-row work of the FP32 kernels needs no FP64 arithmetic or conversion.
+struct RowConst {
+  ff A0, A1, A2, w1;   // constant-coefficient operator (kind LIN)
+  ff is, is2;          // 1/sigma, 1/sigma^2
+  ff th0, dth;         // r(t_i) = c sin(th0 + i dth)
+  float c;
+};
+
 // Device descriptor of one ODE instance (built on the host by nys_setup).
 struct Inst {
   int32_t p, n, m, kind;
@@ -31,6 +42,7 @@ struct Inst {
   // derived constants (host-computed in FP64)
   double hs;           // h / sigma
   double th0, dth;     // LIN: omega*t0 + phi0 and omega*h, both reduced mod 2 pi
+  RowConst rk;         // float-float operator constants (row_const, set by the host)
 };
 
 // A landmark set: m indices on a grid of n points with spacing h, kernel width
@@ -69,7 +81,6 @@ struct SolveSlots {
 // ---------------------------------------------------------------------------
 // float-float helpers (Dekker / Knuth two-sum and FMA-based two-product)
 // ---------------------------------------------------------------------------
-struct ff { float hi, lo; };
 
 __device__ __forceinline__ ff ff_two_sum(float a, float b) {
   float s = a + b;
@@ -101,7 +112,7 @@ __device__ __forceinline__ ff ff_mul_ff(ff a, ff b) {
   const float hi = p + e;
   return {hi, e - (hi - p)};
 }
-__device__ __forceinline__ ff ff_from_double(double x) {
+__host__ __device__ __forceinline__ ff ff_from_double(double x) {
   float hi = (float)x;
   return {hi, (float)(x - (double)hi)};
 }
@@ -171,7 +182,7 @@ __device__ __forceinline__ void coef_f(const Inst& I, const double* tab, int i, 
   }
 }
 
-__device__ __forceinline__ RowCoef row_coef_from_f(const Inst& I, double f1, double f2, double rr) {
+__host__ __device__ __forceinline__ RowCoef row_coef_from_f(const Inst& I, double f1, double f2, double rr) {
   RowCoef R;
   const double is = 1.0 / I.sigma, is2 = is * is;
   if (I.p == 2) {
@@ -195,16 +206,7 @@ __device__ __forceinline__ double lin_rhs_f64(const Inst& I, int i) {
   return I.c[2] * sin(I.c[3] * t + I.c[4]);
 }
 
-// Per-work-item constants of an instance in float-float, so that the per-row
-// work of the FP32 kernels needs no FP64 arithmetic or conversion.
-struct RowConst {
-  ff A0, A1, A2, w1;   // constant-coefficient operator (kind LIN)
-  ff is, is2;          // 1/sigma, 1/sigma^2
-  ff th0, dth;         // r(t_i) = c sin(th0 + i dth)
-  float c;
-};
-
-__device__ __forceinline__ RowConst row_const(const Inst& I) {
+__host__ __device__ __forceinline__ RowConst row_const(const Inst& I) {
   RowConst K;
   double f1 = -I.c[0], f2 = (I.p == 2) ? -I.c[1] : 0.0, rr = 0.0;
   const RowCoef R = row_coef_from_f(I, f1, f2, rr);

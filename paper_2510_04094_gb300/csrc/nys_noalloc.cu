@@ -28,12 +28,13 @@ cudaError_t launch_assemble(bool fp32, const Inst* insts, const Lset* lsets, con
                             const double* W, const Work* work, int nwork, int* counter,
                             const int32_t* lm, const double* tab, double* part,
                             const int64_t* slot_off, int m_max, int k_max, int num_sms,
-                            cudaStream_t st);
+                            cudaStream_t st, int asm_kind, int32_t* err);
 cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const double* W,
                          const float* W32, const double* part, const int64_t* slot_off,
                          const int32_t* lm, void* fac, int64_t facs, double* xs, double* zs,
                          double* cws, int XS, int ZS, int M1S, const int32_t* st_init,
-                         int32_t* st, double gamma_scale, int batch, int m_max, cudaStream_t s);
+                         int32_t* st, double gamma_scale, int batch, int m_max, cudaStream_t s,
+                         const int32_t* asm_err);
 int64_t fac_elems(int m_max);
 int32_t set_last_error(int32_t code, const char* msg);  // nys_api.cu: feeds nys_last_error()
 }  // namespace nys
@@ -219,13 +220,14 @@ extern "C" int32_t nys_solve_noalloc(const nys_instance* q, int32_t batch, doubl
                         reinterpret_cast<const Work*>(B + o_work),
                         nwork, reinterpret_cast<int*>(B + o_cnt), d_lm, nullptr,
                         reinterpret_cast<double*>(B + o_part),
-                        reinterpret_cast<const int64_t*>(B + o_soff), m_max, 0, sms, st));
+                        reinterpret_cast<const int64_t*>(B + o_soff), m_max, 0, sms, st, 1,
+                        nullptr));
   NA_CK(launch_solve(false, d_inst, d_lset, reinterpret_cast<const double*>(B + o_W),
                      reinterpret_cast<const float*>(B + o_W32),
                      reinterpret_cast<const double*>(B + o_part),
                      reinterpret_cast<const int64_t*>(B + o_soff), d_lm, B + o_fac, facs, x_out,
                      reinterpret_cast<double*>(B + o_zs), reinterpret_cast<double*>(B + o_cws), XS,
-                     ZS, M1S, d_stinit, status_out, 1.0, batch, m_max, st));
+                     ZS, M1S, d_stinit, status_out, 1.0, batch, m_max, st, nullptr));
 #undef NA_CK
   return NYS_OK;
 }

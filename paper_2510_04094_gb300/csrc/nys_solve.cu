@@ -35,7 +35,7 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         const int64_t* __restrict__ slot_off, const int32_t* __restrict__ lm_idx,
         T* __restrict__ fac_all, int64_t facs, double* __restrict__ xs, double* __restrict__ zs,
         double* __restrict__ cws, int XS, int ZS, int M1S, const int32_t* __restrict__ st_init,
-        int32_t* __restrict__ st_all, double gamma_scale) {
+        int32_t* __restrict__ st_all, double gamma_scale, const int32_t* __restrict__ asm_err) {
   const int b = blockIdx.x;
   const Inst I = insts[b];
   const Lset LS = lsets[I.lset];
@@ -44,7 +44,8 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   // factor is too coarse there; the mixed path reports NYS_EPRECISION.
   const bool om = (LS.omode != 0);
   const int st0 = (st_init[b] != NYS_OK) ? st_init[b]
-                  : (om && sizeof(T) == sizeof(float)) ? NYS_EPRECISION : NYS_OK;
+                  : (om && sizeof(T) == sizeof(float)) ? NYS_EPRECISION
+                  : (asm_err != nullptr && *asm_err != 0) ? NYS_ETIMEOUT : NYS_OK;
   if (st0 != NYS_OK) {  // no solution: zero x and z, report the status
     for (int k = threadIdx.x; k < XS; k += blockDim.x) xs[(int64_t)b * XS + k] = 0.0;
     for (int k = threadIdx.x; k < ZS; k += blockDim.x) zs[(int64_t)b * ZS + k] = 0.0;
@@ -357,7 +358,7 @@ k_refine_rows(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
       s_zl[j] = z.lo;
     }
     const bool skip = (st_all[wk.inst] != NYS_OK);
-    const RowConst RK = row_const(I);
+    const RowConst RK = I.rk;
     if (folded && !skip) {  // constant operator: kappa(k) for k = -K..K
       for (int t = tid; t <= 2 * K; t += kRefThreads) {
         const ff kv = kappa_lag(T, K, t - K, RK.A0, RK.A1, RK.A2);
@@ -854,7 +855,7 @@ cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const 
                          const float* W32, const double* part, const int64_t* slot_off, const int32_t* lm,
                          void* fac, int64_t facs, double* xs, double* zs, double* cws, int XS,
                          int ZS, int M1S, const int32_t* st_init, int32_t* st, double gamma_scale,
-                         int batch, int m_max, cudaStream_t s) {
+                         int batch, int m_max, cudaStream_t s, const int32_t* asm_err) {
   const size_t sm = solve_smem_bytes(fp32, m_max);
   cudaError_t e;
   if (fp32) {
@@ -862,13 +863,13 @@ cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const 
     if (e != cudaSuccess) return e;
     k_solve<float><<<batch, kSolveThreads, sm, s>>>(insts, lsets, W, W32, part, slot_off, lm,
                                                      (float*)fac, facs, xs, zs, cws, XS, ZS, M1S,
-                                                     st_init, st, gamma_scale);
+                                                     st_init, st, gamma_scale, asm_err);
   } else {
     e = cudaFuncSetAttribute(k_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     k_solve<double><<<batch, kSolveThreads, sm, s>>>(insts, lsets, W, W, part, slot_off, lm,
                                                       (double*)fac, facs, xs, zs, cws, XS, ZS,
-                                                      M1S, st_init, st, gamma_scale);
+                                                      M1S, st_init, st, gamma_scale, asm_err);
   }
   return cudaGetLastError();
 }

@@ -25,9 +25,12 @@ def api():
 
 
 def _check(api, probs, precision, tol=None, refine=-1):
+    """precision: "fp64", "mixed" (tensor-core Gram) or "mixed-simt" (CUDA-core Gram)."""
     import torch
+    assembly = "simt" if precision.endswith("-simt") else "auto"
+    precision = precision.split("-")[0]
     tol = TOL[precision] if tol is None else tol
-    bt = api.Batch(probs, precision=precision, refine_steps=refine)
+    bt = api.Batch(probs, precision=precision, refine_steps=refine, assembly=assembly)
     bt.assemble()
     x, st = bt.solve()
     grids = [core.grid(q) for q in probs]
@@ -58,29 +61,29 @@ def _check(api, probs, precision, tol=None, refine=-1):
     return worst
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed-simt"])
 def test_cfg1_single_instance(api, precision):
     _check(api, [ni.cfg1()], precision)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed-simt"])
 def test_small_ragged_batch(api, precision):
     """Mixed p, n, m: several row tiles plus ragged tails, tiny m."""
     _check(api, ni.small_linear(12), precision)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed-simt"])
 def test_metric_family_full_size_sample(api, precision):
     """The n = 1e4, m = 50 family of the throughput workload (a few instances)."""
     _check(api, ni.m0(4), precision)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed-simt"])
 def test_cfg2_linear_full_size(api, precision):
     _check(api, [ni.cfg2_linear()], precision)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed-simt"])
 def test_ragged_batch_all_m_values(api, precision):
     """The ragged family (m in {20, 32, 50, 64, 100}, sigma = T/m), n capped for the oracle."""
     probs = [q for q in ni.cfg3(40, n_hi=4000)]
@@ -94,6 +97,7 @@ def test_table_coefficients_match_parametric(api):
               r=q["c"] * np.sin(q["omega"] * t + q["phi0"]))
     _check(api, [tq], "fp64")
     _check(api, [tq], "mixed")
+    _check(api, [tq], "mixed-simt")
 
 
 def test_nonfinite_instance_is_isolated(api):
