@@ -146,14 +146,21 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     if (threadIdx.x == 0) Hs[me * ldh + me] = (T)gamma * Gs[m * ldg + m];
   }
   // 4. constraint rows in omega coordinates (FP64): c_1 = [W k(t_1); 1], c_2 = [W k'(t_1); 0]
+  //    with k_j(t_1) = exp(-x_j^2), k'_j(t_1) = -2 x_j / sigma exp(-x_j^2), x_j = (t_1 - s_j) / sigma
+  __shared__ double s_e[2][kMMax];
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    const double x = (double)(0 - lm_idx[I.lm_off + j]) * I.hs;
+    const double e = exp(-x * x);
+    s_e[0][j] = e;
+    s_e[1][j] = (-2.0 * x / I.sigma) * e;
+  }
+  __syncthreads();
   for (int k = threadIdx.x; k < M1; k += blockDim.x) {
     double s0 = 0.0, s1 = 0.0;
     if (k < me) {
       for (int j = 0; j < m; ++j) {
-        const double x = (double)(0 - lm_idx[I.lm_off + j]) * I.hs;
-        const double e = exp(-x * x);
-        s0 += W[k * m + j] * e;
-        s1 += W[k * m + j] * (-2.0 * x / I.sigma) * e;
+        s0 += W[k * m + j] * s_e[0][j];
+        s1 += W[k * m + j] * s_e[1][j];
       }
     } else {
       s0 = 1.0;
@@ -616,14 +623,20 @@ k_newton_step(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     __syncthreads();
   }
   // 2. constraint rows in omega coordinates, grad_x L, |F|
+  __shared__ double s_e[2][kMMax];
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    const double x = (double)(0 - lm_idx[I.lm_off + j]) * I.hs;
+    const double e = exp(-x * x);
+    s_e[0][j] = e;
+    s_e[1][j] = (-2.0 * x / I.sigma) * e;
+  }
+  __syncthreads();
   for (int k = threadIdx.x; k < M1; k += blockDim.x) {
     double s0 = 0.0, s1 = 0.0;
     if (k < me) {
       for (int j = 0; j < m; ++j) {
-        const double x = (double)(0 - lm_idx[I.lm_off + j]) * I.hs;
-        const double e = exp(-x * x);
-        s0 += W[k * m + j] * e;
-        s1 += W[k * m + j] * (-2.0 * x / I.sigma) * e;
+        s0 += W[k * m + j] * s_e[0][j];
+        s1 += W[k * m + j] * s_e[1][j];
       }
     } else {
       s0 = 1.0;
@@ -851,6 +864,7 @@ size_t refine_smem_bytes(int k_max) {
 }
 
 // ---- launchers --------------------------------------------------------------
+
 cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const double* W,
                          const float* W32, const double* part, const int64_t* slot_off, const int32_t* lm,
                          void* fac, int64_t facs, double* xs, double* zs, double* cws, int XS,
