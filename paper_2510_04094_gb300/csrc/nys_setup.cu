@@ -57,6 +57,76 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict_
   for (int j = tid; j < m; j += nt) idx[j] = lm_idx[S.lm_off + j];
   for (int k = tid; k < N; k += nt) pos[k] = k;
   __syncthreads();
+  double* Wl = W_all + S.w_off;
+  float* W32l = W32_all + S.w_off;
+
+  // Cholesky route.  Any W with W^T W = Omega^-1 gives the same features up to
+  // an orthogonal map of omega-space, hence the same fit (Appendix A.3's factor
+  // Lambda^-1/2 U^T is one such W).  With Omega = L L^T, W = L^-1 costs m^3/3
+  // + m^3/3 FP64 flops instead of a Jacobi eigendecomposition's ~10 sweeps.
+  // It is used when cond(Omega) <= m |W|_F^2 <= 1e6: nothing would be
+  // truncated and the kernel-coordinate Gram keeps its precision.
+  for (int e = tid; e < m * m; e += nt) {
+    const int j = e / m, l = e % m;
+    const double d = (double)(idx[j] - idx[l]) * S.hs;
+    V[j * ld + l] = exp(-d * d);
+  }
+  __shared__ int s_bad;
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  for (int k = 0; k < m; ++k) {   // lower Cholesky of Omega in V
+    if (tid == 0) {
+      const double d = V[k * ld + k];
+      if (!(d > 0.0)) { s_bad = 1; V[k * ld + k] = 1.0; }
+      else V[k * ld + k] = sqrt(d);
+    }
+    __syncthreads();
+    const double lkk = V[k * ld + k];
+    for (int i = k + 1 + tid; i < m; i += nt) V[i * ld + k] /= lkk;
+    __syncthreads();
+    const int R = m - k - 1;
+    for (int e = tid; e < R * R; e += nt) {
+      const int i = k + 1 + e / R, j = k + 1 + e % R;
+      if (j <= i) V[i * ld + j] -= V[i * ld + k] * V[j * ld + k];
+    }
+    __syncthreads();
+  }
+  // W = L^-1 into A (lower triangular), one column per thread: L w = e_c
+  for (int c = tid; c < m; c += nt) {
+    for (int i = 0; i < c; ++i) A[i * ld + c] = 0.0;
+    for (int i = c; i < m; ++i) {
+      double sv = (i == c) ? 1.0 : 0.0;
+      for (int k2 = c; k2 < i; ++k2) sv -= V[i * ld + k2] * A[k2 * ld + c];
+      A[i * ld + c] = sv / V[i * ld + i];
+    }
+  }
+  __syncthreads();
+  {
+    double f2 = 0.0;
+    for (int e = tid; e < m * m; e += nt) {
+      const double w = A[(e / m) * ld + (e % m)];
+      f2 += w * w;
+    }
+    f2 = block_sum(f2, red);
+    const bool chol_ok = (s_bad == 0) && isfinite(f2) && ((double)m * f2 <= 1e6);
+    if (chol_ok) {
+      for (int e = tid; e < m * m; e += nt) {
+        const double w = A[(e / m) * ld + (e % m)];
+        Wl[e] = w;
+        W32l[e] = (float)w;
+      }
+      for (int k = tid; k < m; k += nt) {
+        const double l = V[k * ld + k];
+        lam_all[(int64_t)L * kMMax + k] = l * l;   // Cholesky pivots (informational)
+      }
+      if (tid == 0) {
+        lsets[L].m_eff = m;
+        lsets[L].omode = 0;
+      }
+      return;
+    }
+  }
+  // Jacobi route: the landmark kernel again, V = I
   for (int e = tid; e < m * m; e += nt) {
     const int j = e / m, l = e % m;
     const double d = (double)(idx[j] - idx[l]) * S.hs;
@@ -151,8 +221,6 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict_
   }
   __syncthreads();
   const int me = (int)red[0];
-  double* Wl = W_all + S.w_off;
-  float* W32l = W32_all + S.w_off;
   for (int e = tid; e < m * m; e += nt) {
     const int k = e / m, j = e % m;
     double w = 0.0;

@@ -169,6 +169,23 @@ def test_rotation_of_features_leaves_fit_unchanged():
     assert np.abs(a["y"] - b["y"]).max() <= 1e-10 * np.abs(a["y"]).max()
 
 
+def test_cholesky_whitening_gives_the_same_fit():
+    """Any W with W^T W = Omega^-1 spans the same features up to an orthogonal map,
+    so W = L^-1 (Omega = L L^T) fits exactly like Appendix A.3's Lambda^-1/2 U^T when
+    nothing is truncated (the GPU setup uses it when cond(Omega) is small)."""
+    for prob in (ni.cfg2_linear(n=2000), ni.cfg1(), ni.m0(1, n=3000)[0]):
+        st = core.setup(prob)
+        assert st["W"].shape[0] == prob["m"]
+        t = core.grid(prob)
+        s = t[core.landmark_indices(prob)]
+        L = np.linalg.cholesky(core.rbf(s[:, None], s[None, :], prob["sigma"]))
+        Wc = np.linalg.solve(L, np.eye(len(s)))
+        a = core.solve_linear(prob, st=st)
+        b = core.solve_linear(prob, st=dict(st, W=Wc))
+        assert np.abs(a["y"] - b["y"]).max() <= 1e-10 * np.abs(a["y"]).max()
+        assert abs(a["b"] - b["b"]) <= 1e-10 * max(1.0, np.abs(a["y"]).max())
+
+
 def test_sqrt_m_feature_scaling_equals_gamma_times_m():
     prob = ni.cfg1()
     st = core.setup(prob)
