@@ -107,7 +107,7 @@ typedef struct nys_ctx nys_ctx;
 /* Create a context for `batch` instances (host array `inst`), allocate all
    device workspaces, upload the descriptors and enqueue the Nystrom setup
    (landmark kernel Omega in FP64; W with W^T W = Omega^{-1}: W = L^{-1} from
-   Omega = L L^T when m |W|_F^2 <= 1e6 certifies cond(Omega) <= 1e6, else the
+   Omega = L L^T for NYS_FP64 when m |W|_F^2 <= 1e6 certifies cond(Omega) <= 1e6, else the
    Jacobi eigendecomposition W = Lambda^{-1/2} U^T with truncation; the fit
    does not depend on which; Appendix A.3 and the feature map eq32).  Instances with identical landmark sets
    (same m, grid spacing/sigma and indices) share one factor.

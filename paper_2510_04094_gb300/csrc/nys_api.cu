@@ -15,10 +15,11 @@
 namespace nys {
 // kernel launchers (defined in the other translation units)
 cudaError_t launch_setup(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
-                         double* lam, float* lag, double tau, int m_max, cudaStream_t st);
+                         double* lam, float* lag, double tau, int m_max, cudaStream_t st,
+                         int allow_chol);
 cudaError_t launch_lag(const Lset* lsets, int capacity, float* lag, cudaStream_t st);
 cudaError_t launch_eig(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
-                       double* lam, double tau, int m_max, cudaStream_t st);
+                       double* lam, double tau, int m_max, cudaStream_t st, int allow_chol);
 cudaError_t launch_assemble(bool fp32, const Inst* insts, const Lset* lsets, const float* lag,
                             const double* W, const Work* work, int nwork, int* counter,
                             const int32_t* lm, const double* tab, double* part,
@@ -307,7 +308,7 @@ static int32_t pack(nys_ctx* c, const nys_instance* q, bool first) {
 
 static cudaError_t enqueue_factor(nys_ctx* c, cudaStream_t s) {
   return launch_setup(c->lset.p, c->batch, c->lm.p, c->W.p, c->W32.p, c->lam.p, c->lag.p,
-                      c->opt.eig_tau > 0 ? c->opt.eig_tau : 1e-12, c->m_max, s);
+                      c->opt.eig_tau > 0 ? c->opt.eig_tau : 1e-12, c->m_max, s, c->fp32 ? 0 : 1);
 }
 
 // The lag tables (read by the row passes) go on the caller's stream; the
@@ -319,7 +320,8 @@ static cudaError_t fork_factor(nys_ctx* c, cudaStream_t s) {
   if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
   if (e == cudaSuccess)
     e = launch_eig(c->lset.p, c->batch, c->lm.p, c->W.p, c->W32.p, c->lam.p,
-                   c->opt.eig_tau > 0 ? c->opt.eig_tau : 1e-12, c->m_max, c->side);
+                   c->opt.eig_tau > 0 ? c->opt.eig_tau : 1e-12, c->m_max, c->side,
+                   c->fp32 ? 0 : 1);
   if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
   return e;
 }

@@ -195,24 +195,37 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
             unsigned char* lrow = hrow + kTcTileBytes;
             // the 8 K chunks of this lane are independent: evaluate all, then store
             float vv[8];
+            if (kind == 0) {
+              // x_q = (t_i - s_j) / sigma at the rows t0 + 4q: one FMA per chunk
+              const float x0 = (float)(wk.r0 + t0 - idxj) * hs;
+              const float dx = 4.f * hs;
+              float A0 = RK.A0.hi, A1 = RK.A1.hi, A2 = RK.A2.hi;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const int t = t0 + 4 * q;
-              const float x = (float)(wk.r0 + t - idxj) * hs;
-              const float u = x * x;
-              const int tc = min(t, tmax);
-              float A0 = RK.A0.hi, A1 = RK.A1.hi, A2 = RK.A2.hi, w1 = RK.w1.hi;
-              if (!lin) {
-                const float4 co = s_co[tc];
-                A0 = co.x; A1 = co.y; A2 = co.z; w1 = co.w;
+              for (int q = 0; q < 8; ++q) {
+                if (!lin) {
+                  const float4 co = s_co[min(t0 + 4 * q, tmax)];
+                  A0 = co.x; A1 = co.y; A2 = co.z;
+                }
+                const float x = fmaf((float)q, dx, x0);
+                const float u = x * x;
+                vv[q] = ex2_approx(-1.44269504088896341f * u) * fmaf(A2, u, fmaf(A1, x, A0));
               }
-              float v = exp_neg_fast(u) * fmaf(A2, u, fmaf(A1, x, A0));
-              if (kind != 0) v = (kind == 1) ? w1 : (kind == 2 ? s_r[tc] : 0.f);
-              vv[q] = (t < nrows) ? v : 0.f;
+            } else {
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                const int tc = min(t0 + 4 * q, tmax);
+                vv[q] = (kind == 1) ? (lin ? RK.w1.hi : s_co[tc].w) : (kind == 2 ? s_r[tc] : 0.f);
+              }
+            }
+            if (t0 + 28 >= nrows) {                    // rows past the end of the item
+#pragma unroll
+              for (int q = 0; q < 8; ++q)
+                if (t0 + 4 * q >= nrows) vv[q] = 0.f;
             }
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-              const float h = to_tf32(vv[q]);
+              // TF32 part by truncation (the low part v - hi is exact either way)
+              const float h = __uint_as_float(__float_as_uint(vv[q]) & 0xFFFFE000u);
               const int ch = ((q ^ j8) & 7) << 4;      // 128-byte swizzle
               *reinterpret_cast<float*>(hrow + ch) = h;
               *reinterpret_cast<float*>(lrow + ch) = vv[q] - h;

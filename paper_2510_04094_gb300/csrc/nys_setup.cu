@@ -34,7 +34,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 
 __global__ void __launch_bounds__(kSetupThreads)
 k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict__ W_all,
-            float* __restrict__ W32_all, double* __restrict__ lam_all, double tau) {
+            float* __restrict__ W32_all, double* __restrict__ lam_all, double tau, int allow_chol) {
   // the grid covers every slot; inactive slots (instances that share another
   // instance's set) return at once, so a captured graph stays valid when an
   // update changes which instances share
@@ -65,7 +65,10 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict_
   // Lambda^-1/2 U^T is one such W).  With Omega = L L^T, W = L^-1 costs m^3/3
   // + m^3/3 FP64 flops instead of a Jacobi eigendecomposition's ~10 sweeps.
   // It is used when cond(Omega) <= m |W|_F^2 <= 1e6: nothing would be
-  // truncated and the kernel-coordinate Gram keeps its precision.
+  // truncated and the kernel-coordinate Gram keeps its precision.  Only for
+  // FP64 solves (allow_chol): L^-1 has large alternating entries, and the FP32
+  // factor of the mixed path built from it refines about ten times slower
+  // than one built from the nearly orthogonal rows of Lambda^-1/2 U^T.
   for (int e = tid; e < m * m; e += nt) {
     const int j = e / m, l = e % m;
     const double d = (double)(idx[j] - idx[l]) * S.hs;
@@ -108,7 +111,7 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict_
       f2 += w * w;
     }
     f2 = block_sum(f2, red);
-    const bool chol_ok = (s_bad == 0) && isfinite(f2) && ((double)m * f2 <= 1e6);
+    const bool chol_ok = allow_chol && (s_bad == 0) && isfinite(f2) && ((double)m * f2 <= 1e6);
     if (chol_ok) {
       for (int e = tid; e < m * m; e += nt) {
         const double w = A[(e / m) * ld + (e % m)];
@@ -271,21 +274,22 @@ cudaError_t launch_lag(const Lset* lsets, int capacity, float* lag, cudaStream_t
 }
 
 cudaError_t launch_eig(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
-                       double* lam, double tau, int m_max, cudaStream_t st) {
+                       double* lam, double tau, int m_max, cudaStream_t st, int allow_chol) {
   if (capacity == 0) return cudaSuccess;
   const size_t sm = setup_smem_bytes(m_max);
   cudaError_t e = cudaFuncSetAttribute(k_setup_eig, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sm);
   if (e != cudaSuccess) return e;
-  k_setup_eig<<<capacity, kSetupThreads, sm, st>>>(lsets, lm_idx, W, W32, lam, tau);
+  k_setup_eig<<<capacity, kSetupThreads, sm, st>>>(lsets, lm_idx, W, W32, lam, tau, allow_chol);
   return cudaGetLastError();
 }
 
 cudaError_t launch_setup(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
-                         double* lam, float* lag, double tau, int m_max, cudaStream_t st) {
+                         double* lam, float* lag, double tau, int m_max, cudaStream_t st,
+                         int allow_chol) {
   cudaError_t e = launch_lag(lsets, capacity, lag, st);
   if (e != cudaSuccess) return e;
-  return launch_eig(lsets, capacity, lm_idx, W, W32, lam, tau, m_max, st);
+  return launch_eig(lsets, capacity, lm_idx, W, W32, lam, tau, m_max, st, allow_chol);
 }
 
 }  // namespace nys

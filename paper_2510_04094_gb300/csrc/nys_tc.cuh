@@ -132,6 +132,14 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// 2^x by the MUFU unit (flush-to-zero; the features are multiplied by it, and
+// arguments below -126 only occur beyond the kernel's band where the value is 0)
+__device__ __forceinline__ float ex2_approx(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // round to the nearest TF32 value (low 13 mantissa bits cleared)
 __device__ __forceinline__ float to_tf32(float x) {
   uint32_t r;

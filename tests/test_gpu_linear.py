@@ -90,6 +90,13 @@ def test_ragged_batch_all_m_values(api, precision):
     _check(api, probs, precision)
 
 
+@pytest.mark.parametrize("precision", ["mixed", "mixed-simt"])
+def test_ragged_family_default_refinement(api, precision):
+    """The ragged batched family (n log-uniform in [500, 2e4], m in {20..100},
+    sigma = T/m) meets the mixed-path bar with the default single refinement pass."""
+    _check(api, ni.cfg3(8), precision)
+
+
 def test_table_coefficients_match_parametric(api):
     q = ni.m0(1, n=3000)[0]
     t = core.grid(q)
