@@ -28,6 +28,10 @@ sys.path.insert(0, ROOT)
 METRIC = "batched ODE solves/s at n=1e4, m=50"
 UNIT = "solves/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2070 MHz
+# DRAM bytes (read + write) of one k_assemble_tc launch per instance, from the ncu
+# capture summarised in profiles/k_assemble_tc_m0_304.md (428.8 KB + 0.3 KB for 304
+# instances); the kernel keeps its operands on chip, HBM traffic is descriptors only
+TC_DRAM_BYTES_PER_INSTANCE = (428.8e3 + 0.256e3) / 304
 
 
 def parse():
@@ -368,7 +372,9 @@ def main():
                     "d2h_bytes_per_step": d2h},
             "roofline": {"bound": "alu", "kernel": "k_assemble_tc" if args.precision == "mixed"
                          else "k_assemble_f64", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                         "traffic": (TC_DRAM_BYTES_PER_INSTANCE * B if args.precision == "mixed"
+                                     and args.n == 10_000 and args.m == 50 else None),
                          "flops_per_launch": fl, "ms_per_launch": asm_ms},
             "cpu_baseline": cpu_base,
             "clocks": clk,

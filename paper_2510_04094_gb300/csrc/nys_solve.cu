@@ -19,7 +19,7 @@
 
 namespace nys {
 
-constexpr int kSolveThreads = 256;
+constexpr int kSolveThreads = 128;
 
 int64_t fac_elems(int m_max) { return fac_elems_inline(m_max); }
 
