@@ -62,6 +62,24 @@ def dist_init():
     return rank, ws, local
 
 
+def rank_problems(rank, B, n, m):
+    """The batch of one rank (weak scaling: every rank solves its own B instances of
+    the family, rank 0 the metric batch itself, rank r > 0 the family under spawn key r)."""
+    import nys_inputs as ni
+    return ni.linear_family(B, n=n, m=m, name="m0", sub=rank) if rank else ni.m0(B, n=n, m=m)
+
+
+def job_rate(ms_local, B, ws, device=None):
+    """Whole-job solves/s: every rank's B instances over the slowest rank's step time
+    (one MAX all-reduce; the only collective of the job)."""
+    import torch
+    ms_t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if ws > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    return ws * B / (ms / 1000.0), ms
+
+
 class Clocks:
     """nvidia-smi sampler (SM clock, max clock, throttle reasons) during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -213,8 +231,7 @@ def main():
     from paper_2510_04094_gb300.api import Batch, pack_instances
 
     B = args.batch
-    probs = ni.linear_family(B, n=args.n, m=args.m, name="m0", sub=rank) if rank else \
-        ni.m0(B, n=args.n, m=args.m)
+    probs = rank_problems(rank, B, args.n, args.m)
     bt = Batch(probs, precision=args.precision)
     refine = 1 if args.precision == "mixed" else 0   # default refinement passes
     # setup (lag tables [mixed] + eigendecomposition), assembly, solve, 2 per refinement pass
@@ -245,11 +262,7 @@ def main():
         torch.distributed.barrier()
     clk = clocks.stop()
     ms = sum(a.elapsed_time(b) for a, b in times) / args.steps
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms = float(ms_t.item())
-    value = ws * B / (ms / 1000.0)
+    value, ms = job_rate(ms, B, ws, device="cuda")
 
     # dominant-kernel timing (fused assembly) on the launching stream
     asm_ms = []
