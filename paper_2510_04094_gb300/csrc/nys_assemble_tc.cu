@@ -107,9 +107,14 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     uint32_t ph_empty[kTcStages] = {0, 0, 0, 0}, ph_mfree[2] = {0, 0};
     bool used[kTcStages] = {false, false, false, false};
     int gs = 0;                                        // stages produced so far
+    // the lead producer fetches the next item while the current one is produced
+    int next_w = (tid == 0) ? atomicAdd(counter, 1) : 0;
     for (int it = 0;; ++it) {
       const int rs = it & 1;
-      if (tid == 0) s_w = s_abort ? nwork : atomicAdd(counter, 1);
+      if (tid == 0) {
+        s_w = s_abort ? nwork : next_w;
+        if (next_w < nwork) next_w = atomicAdd(counter, 1);
+      }
       bar_named(1, 32 * kTcProducers);
       const int w = s_w;                               // one value for every producer
       if (w >= nwork) {
@@ -196,19 +201,22 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
             // the 8 K chunks of this lane are independent: evaluate all, then store
             float vv[8];
             if (kind == 0) {
-              // x_q = (t_i - s_j) / sigma at the rows t0 + 4q: one FMA per chunk
-              const float x0 = (float)(wk.r0 + t0 - idxj) * hs;
-              const float dx = 4.f * hs;
-              float A0 = RK.A0.hi, A1 = RK.A1.hi, A2 = RK.A2.hi;
+              // y = x sqrt(log2 e), x = (t_i - s_j) / sigma at the rows t0 + 4q (one FMA
+              // per chunk); exp(-x^2) = 2^(-y^2) and A0 + A1 x + A2 x^2 =
+              // A0 + (A1 / c) y + (A2 / c^2) y^2 with c = sqrt(log2 e)
+              const float c1 = 1.20112240878645f, ic1 = 0.832554611157698f, ic2 = 0.693147180559945f;
+              const float y0 = (float)(wk.r0 + t0 - idxj) * (hs * c1);
+              const float dy = 4.f * hs * c1;
+              float A0 = RK.A0.hi, B1 = RK.A1.hi * ic1, B2 = -RK.A2.hi * ic2;
 #pragma unroll
               for (int q = 0; q < 8; ++q) {
                 if (!lin) {
                   const float4 co = s_co[min(t0 + 4 * q, tmax)];
-                  A0 = co.x; A1 = co.y; A2 = co.z;
+                  A0 = co.x; B1 = co.y * ic1; B2 = -co.z * ic2;
                 }
-                const float x = fmaf((float)q, dx, x0);
-                const float u = x * x;
-                vv[q] = ex2_approx(-1.44269504088896341f * u) * fmaf(A2, u, fmaf(A1, x, A0));
+                const float y = fmaf((float)q, dy, y0);
+                const float nu = -y * y;                 // -y^2
+                vv[q] = ex2_approx(nu) * fmaf(B2, nu, fmaf(B1, y, A0));
               }
             } else {
 #pragma unroll

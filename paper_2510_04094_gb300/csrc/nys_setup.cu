@@ -32,6 +32,100 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
+__device__ __forceinline__ double block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+    if (threadIdx.x == 0) red[0] = s;
+  }
+  __syncthreads();
+  s = red[0];
+  __syncthreads();
+  return s;
+}
+
+// Parallel cyclic Jacobi sweeps on the symmetric m x m matrix A (ld), rotations
+// accumulated in V; round-robin pairing in pos (N = m rounded up to even; index
+// m, if present, sits out).  Stops when off(A)^2 <= tol tot(A)^2.
+template <typename T>
+__device__ void jacobi_sweeps(T* A, T* V, int ld, int m, int N, int* pos, T* cs, double* red,
+                              double tol, int max_sweeps) {
+  const int tid = threadIdx.x, nt = blockDim.x, half = N / 2;
+  for (int k = tid; k < N; k += nt) pos[k] = k;
+  __syncthreads();
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int e = tid; e < m * m; e += nt) {
+      const int j = e / m, l = e % m;
+      const double a = (double)A[j * ld + l];
+      tot += a * a;
+      if (j != l) off += a * a;
+    }
+    off = block_sum(off, red);
+    tot = block_sum(tot, red);
+    if (off <= tol * tot) break;
+    for (int round = 0; round < N - 1; ++round) {
+      // rotation angles of the m/2 disjoint pairs (symmetric Schur decomposition)
+      for (int k = tid; k < half; k += nt) {
+        int p = pos[k], q = pos[N - 1 - k];
+        if (p > q) { int t = p; p = q; q = t; }
+        T c = T(1), sn = T(0);
+        if (q < m) {
+          const T apq = A[p * ld + q];
+          if (fabs(apq) > T(1e-30)) {
+            const T tau_ = (A[q * ld + q] - A[p * ld + p]) / (T(2) * apq);
+            const T t = (tau_ >= T(0) ? T(1) : T(-1)) / (fabs(tau_) + sqrt(T(1) + tau_ * tau_));
+            c = T(1) / sqrt(T(1) + t * t);
+            sn = t * c;
+          }
+        }
+        cs[k] = c;
+        cs[half + k] = sn;
+      }
+      __syncthreads();
+      // A <- A J and V <- V J : columns p, q of every row
+      for (int e = tid; e < half * m; e += nt) {
+        const int k = e / m, i = e % m;
+        int p = pos[k], q = pos[N - 1 - k];
+        if (p > q) { int t = p; p = q; q = t; }
+        if (q >= m) continue;
+        const T c = cs[k], sn = cs[half + k];
+        const T aip = A[i * ld + p], aiq = A[i * ld + q];
+        A[i * ld + p] = c * aip - sn * aiq;
+        A[i * ld + q] = sn * aip + c * aiq;
+        const T vip = V[i * ld + p], viq = V[i * ld + q];
+        V[i * ld + p] = c * vip - sn * viq;
+        V[i * ld + q] = sn * vip + c * viq;
+      }
+      __syncthreads();
+      // A <- J^T A : rows p, q
+      for (int e = tid; e < half * m; e += nt) {
+        const int k = e / m, j = e % m;
+        int p = pos[k], q = pos[N - 1 - k];
+        if (p > q) { int t = p; p = q; q = t; }
+        if (q >= m) continue;
+        const T c = cs[k], sn = cs[half + k];
+        const T apj = A[p * ld + j], aqj = A[q * ld + j];
+        A[p * ld + j] = c * apj - sn * aqj;
+        A[q * ld + j] = sn * apj + c * aqj;
+      }
+      __syncthreads();
+      if (tid == 0) {  // round-robin: keep pos[0], rotate the rest
+        const int last = pos[N - 1];
+        for (int k = N - 1; k > 1; --k) pos[k] = pos[k - 1];
+        pos[1] = last;
+      }
+      __syncthreads();
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kSetupThreads)
 k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict__ W_all,
             float* __restrict__ W32_all, double* __restrict__ lam_all, double tau, int allow_chol) {
@@ -129,7 +223,92 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict_
       return;
     }
   }
-  // Jacobi route: the landmark kernel again, V = I
+  // FP32 route (mixed contexts): Jacobi sweeps in FP32 (64x the FP64 rate), then
+  // one FP64 correction that makes W an exact whitening again: with W0 from the
+  // FP32 eigenpairs, M = W0 Omega W0^T = I + E and W = (I - E/2) W0 satisfies
+  // W^T W = Omega^-1 up to O(E^2); its rows stay nearly orthogonal, which the
+  // FP32 factor of the mixed path needs.  Used when lambda_min > 1e-5 lambda_max
+  // (nothing truncated) and |E| <= 1e-5; otherwise the FP64 Jacobi below.
+  if (!allow_chol) {
+    for (int e = tid; e < m * m; e += nt) {
+      const int j = e / m, l = e % m;
+      const double d = (double)(idx[j] - idx[l]) * S.hs;
+      A[j * ld + l] = exp(-d * d);
+    }
+    float* Af = reinterpret_cast<float*>(V);   // two m x ld float matrices in V's space
+    float* Vf = Af + m * ld;
+    __syncthreads();
+    for (int e = tid; e < m * m; e += nt) {
+      const int j = e / m, l = e % m;
+      Af[j * ld + l] = (float)A[j * ld + l];
+      Vf[j * ld + l] = (j == l) ? 1.f : 0.f;
+    }
+    __syncthreads();
+    // FP32 sweeps reach off(A)^2 ~ 1e-13 tot(A)^2; the correction below absorbs the rest
+    jacobi_sweeps<float>(Af, Vf, ld, m, N, pos, reinterpret_cast<float*>(cs), red, 1e-13, kMaxSweeps);
+    if (tid == 0) {
+      for (int k = 0; k < m; ++k) perm[k] = k;
+      for (int a2 = 0; a2 < m; ++a2) {
+        int best = a2;
+        for (int b2 = a2 + 1; b2 < m; ++b2)
+          if (Af[perm[b2] * ld + perm[b2]] > Af[perm[best] * ld + perm[best]]) best = b2;
+        const int t = perm[a2]; perm[a2] = perm[best]; perm[best] = t;
+      }
+      const double lmax = Af[perm[0] * ld + perm[0]], lmin = Af[perm[m - 1] * ld + perm[m - 1]];
+      red[0] = (lmin > 1e-5 * lmax && lmin > 0.0) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const bool well = red[0] != 0.0;
+    __syncthreads();
+    if (well) {
+      // W0 = Lambda^-1/2 U^T (descending), straight to the output
+      for (int e = tid; e < m * m; e += nt) {
+        const int k = e / m, j = e % m;
+        const int c = perm[k];
+        Wl[e] = (double)Vf[j * ld + c] / sqrt((double)Af[c * ld + c]);
+      }
+      for (int k = tid; k < m; k += nt) lam_all[(int64_t)L * kMMax + k] = (double)Af[perm[k] * ld + perm[k]];
+      __syncthreads();
+      double* Tm = V;                           // T = W0 Omega (the FP32 matrices are done)
+      for (int e = tid; e < m * m; e += nt) {
+        const int k = e / m, j = e % m;
+        double sv = 0.0;
+        for (int i = 0; i < m; ++i) sv += Wl[k * m + i] * A[i * ld + j];
+        Tm[k * ld + j] = sv;
+      }
+      __syncthreads();
+      for (int e = tid; e < m * m; e += nt) {   // E = T W0^T - I, into A
+        const int k = e / m, l = e % m;
+        double sv = 0.0;
+        for (int j = 0; j < m; ++j) sv += Tm[k * ld + j] * Wl[l * m + j];
+        A[k * ld + l] = sv - (k == l ? 1.0 : 0.0);
+      }
+      __syncthreads();
+      double emax = 0.0;
+      for (int e = tid; e < m * m; e += nt) emax = fmax(emax, fabs(A[(e / m) * ld + (e % m)]));
+      emax = block_max(emax, red);
+      if (emax <= 1e-5) {
+        for (int e = tid; e < m * m; e += nt) {   // W = W0 - E W0 / 2, into V
+          const int k = e / m, j = e % m;
+          double sv = 0.0;
+          for (int l = 0; l < m; ++l) sv += A[k * ld + l] * Wl[l * m + j];
+          Tm[k * ld + j] = Wl[k * m + j] - 0.5 * sv;
+        }
+        __syncthreads();
+        for (int e = tid; e < m * m; e += nt) {
+          const double w = Tm[(e / m) * ld + (e % m)];
+          Wl[e] = w;
+          W32l[e] = (float)w;
+        }
+        if (tid == 0) {
+          lsets[L].m_eff = m;
+          lsets[L].omode = 0;
+        }
+        return;
+      }
+    }
+  }
+  // FP64 Jacobi route: the landmark kernel again, V = I
   for (int e = tid; e < m * m; e += nt) {
     const int j = e / m, l = e % m;
     const double d = (double)(idx[j] - idx[l]) * S.hs;
@@ -137,74 +316,7 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict_
     V[j * ld + l] = (j == l) ? 1.0 : 0.0;
   }
   __syncthreads();
-
-  const int half = N / 2;
-  for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int e = tid; e < m * m; e += nt) {
-      const int j = e / m, l = e % m;
-      const double a = A[j * ld + l];
-      tot += a * a;
-      if (j != l) off += a * a;
-    }
-    off = block_sum(off, red);
-    tot = block_sum(tot, red);
-    if (off <= 1e-30 * tot) break;
-
-    for (int round = 0; round < N - 1; ++round) {
-      // rotation angles of the m/2 disjoint pairs (symmetric Schur decomposition)
-      for (int k = tid; k < half; k += nt) {
-        int p = pos[k], q = pos[N - 1 - k];
-        if (p > q) { int t = p; p = q; q = t; }
-        double c = 1.0, s = 0.0;
-        if (q < m) {
-          const double apq = A[p * ld + q];
-          if (fabs(apq) > 1e-300) {
-            const double tau_ = (A[q * ld + q] - A[p * ld + p]) / (2.0 * apq);
-            const double t = (tau_ >= 0.0 ? 1.0 : -1.0) / (fabs(tau_) + sqrt(1.0 + tau_ * tau_));
-            c = 1.0 / sqrt(1.0 + t * t);
-            s = t * c;
-          }
-        }
-        cs[k] = c;
-        cs[half + k] = s;
-      }
-      __syncthreads();
-      // A <- A J and V <- V J : columns p, q of every row
-      for (int e = tid; e < half * m; e += nt) {
-        const int k = e / m, i = e % m;
-        int p = pos[k], q = pos[N - 1 - k];
-        if (p > q) { int t = p; p = q; q = t; }
-        if (q >= m) continue;
-        const double c = cs[k], s = cs[half + k];
-        const double aip = A[i * ld + p], aiq = A[i * ld + q];
-        A[i * ld + p] = c * aip - s * aiq;
-        A[i * ld + q] = s * aip + c * aiq;
-        const double vip = V[i * ld + p], viq = V[i * ld + q];
-        V[i * ld + p] = c * vip - s * viq;
-        V[i * ld + q] = s * vip + c * viq;
-      }
-      __syncthreads();
-      // A <- J^T A : rows p, q
-      for (int e = tid; e < half * m; e += nt) {
-        const int k = e / m, j = e % m;
-        int p = pos[k], q = pos[N - 1 - k];
-        if (p > q) { int t = p; p = q; q = t; }
-        if (q >= m) continue;
-        const double c = cs[k], s = cs[half + k];
-        const double apj = A[p * ld + j], aqj = A[q * ld + j];
-        A[p * ld + j] = c * apj - s * aqj;
-        A[q * ld + j] = s * apj + c * aqj;
-      }
-      __syncthreads();
-      if (tid == 0) {  // round-robin: keep pos[0], rotate the rest
-        const int last = pos[N - 1];
-        for (int k = N - 1; k > 1; --k) pos[k] = pos[k - 1];
-        pos[1] = last;
-      }
-      __syncthreads();
-    }
-  }
+  jacobi_sweeps<double>(A, V, ld, m, N, pos, cs, red, 1e-30, kMaxSweeps);
 
   // sort eigenvalues descending, keep lambda > tau * lambda_max
   if (tid == 0) {
