@@ -15,10 +15,11 @@
 // to its diagonal blocks (the off-diagonal blocks mix rows and are not read).
 //
 // Warp roles (persistent CTA per SM, all hand-offs through mbarriers):
-//   * 16 producer warps fetch work items, evaluate features (FP32, MUFU
+//   * 20 producer warps fetch work items, evaluate features (FP32, MUFU
 //     exponential) straight into the operand layout (one warp store fills one
-//     8-slot x 4-row core matrix, conflict-free) and arrive on the stage's
-//     "full" barrier; four stage buffers;
+//     8-slot x 4-row core matrix, conflict-free; a warp takes half of the K
+//     chunks of one 8-slot group per unit) and arrive on the stage's "full"
+//     barrier; four stage buffers;
 //   * one issuer warp waits for "full", issues the MMAs (two accumulators per
 //     item, alternating) and commits to the stage's "empty" barrier and, after
 //     the item's last stage, to the accumulator barrier;
@@ -35,7 +36,7 @@
 
 namespace nys {
 
-constexpr int kTcProducers = 16;                       // producer warps
+constexpr int kTcProducers = 20;                       // producer warps
 constexpr int kTcIssuerWarp = kTcProducers;            // warp 16
 constexpr int kTcEpiWarp0 = kTcProducers + 1;          // warps 17..20
 constexpr int kTcThreads = 32 * (kTcProducers + 5);
@@ -189,17 +190,18 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         unsigned char* hi = sm + s * kTcStageBytes;
         if (!late) {
           // warp -> (block p, 8-slot group g); lane -> (slot j8, K position w4)
-          for (int pg = warp; pg < P * Gf; pg += kTcProducers) {
+          for (int pu = warp; pu < 2 * P * Gf; pu += kTcProducers) {
+            const int pg = pu >> 1, qh = pu & 1;        // (block, group), half of the K chunks
             const int p = (int)(((float)pg + 0.5f) * invGf);
             const int g = pg - p * Gf;
             const int j = (g << 3) + j8;               // local column of this lane
             const int idxj = s_idx[min(jlo + j, m - 1)];
             const int kind = (j < A) ? 0 : (j == A ? 1 : (j == A + 1 ? 2 : 3));
-            const int t0 = k * SR + 32 * p + w4;        // item row for K chunk 0
+            const int t0 = k * SR + 32 * p + w4 + 16 * qh;   // item row for this lane's first chunk
             unsigned char* hrow = hi + ((((p * Bs) >> 3) + g) << 10) + (j8 << 7) + (w4 << 2);
             unsigned char* lrow = hrow + kTcTileBytes;
             // the 8 K chunks of this lane are independent: evaluate all, then store
-            float vv[8];
+            float vv[4];
             if (kind == 0) {
               // y = x sqrt(log2 e), x = (t_i - s_j) / sigma at the rows t0 + 4q (one FMA
               // per chunk); exp(-x^2) = 2^(-y^2) and A0 + A1 x + A2 x^2 =
@@ -209,7 +211,7 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
               const float dy = 4.f * hs * c1;
               float A0 = RK.A0.hi, B1 = RK.A1.hi * ic1, B2 = -RK.A2.hi * ic2;
 #pragma unroll
-              for (int q = 0; q < 8; ++q) {
+              for (int q = 0; q < 4; ++q) {
                 if (!lin) {
                   const float4 co = s_co[min(t0 + 4 * q, tmax)];
                   A0 = co.x; B1 = co.y * ic1; B2 = -co.z * ic2;
@@ -220,21 +222,21 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
               }
             } else {
 #pragma unroll
-              for (int q = 0; q < 8; ++q) {
+              for (int q = 0; q < 4; ++q) {
                 const int tc = min(t0 + 4 * q, tmax);
                 vv[q] = (kind == 1) ? (lin ? RK.w1.hi : s_co[tc].w) : (kind == 2 ? s_r[tc] : 0.f);
               }
             }
-            if (t0 + 28 >= nrows) {                    // rows past the end of the item
+            if (t0 + 12 >= nrows) {                    // rows past the end of the item
 #pragma unroll
-              for (int q = 0; q < 8; ++q)
+              for (int q = 0; q < 4; ++q)
                 if (t0 + 4 * q >= nrows) vv[q] = 0.f;
             }
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
+            for (int q = 0; q < 4; ++q) {
               // TF32 part by truncation (the low part v - hi is exact either way)
               const float h = __uint_as_float(__float_as_uint(vv[q]) & 0xFFFFE000u);
-              const int ch = ((q ^ j8) & 7) << 4;      // 128-byte swizzle
+              const int ch = (((q + 4 * qh) ^ j8) & 7) << 4;   // 128-byte swizzle
               *reinterpret_cast<float*>(hrow + ch) = h;
               *reinterpret_cast<float*>(lrow + ch) = vv[q] - h;
             }

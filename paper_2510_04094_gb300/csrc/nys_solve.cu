@@ -329,7 +329,9 @@ __device__ __forceinline__ ff ff_norm(ff a) {
 constexpr int kRefWarps = kRefThreads / 32;
 constexpr int kRefColsPerWarp = (kM1Max + kRefWarps - 1) / kRefWarps;   // 15
 
-__global__ void __launch_bounds__(kRefThreads)
+// four CTAs per SM (64 registers): occupancy hides the latency of the
+// float-float chains better than the registers saved would
+__global__ void __launch_bounds__(kRefThreads, 4)
 k_refine_rows(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
               const float* __restrict__ lag, const Work* __restrict__ work, int nwork,
               int* __restrict__ counter, const int32_t* __restrict__ lm_idx,
