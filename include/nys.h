@@ -100,7 +100,11 @@ typedef struct {
                             on the CUDA cores (FP32 FMA, 8x8 register blocks)  */
 } nys_options;
 
-typedef enum { NYS_ASM_AUTO = 0, NYS_ASM_SIMT = 1 } nys_assembly;
+/* NYS_ASM_TUNE (MIXED): before the first assembly, time the tensor-core and the
+   CUDA-core Gram with work items of 512 and 1024 rows on the context's own
+   batch (CUDA events, a few launches each) and keep the fastest; see
+   nys_assembly_config.  Other precisions ignore it.                          */
+typedef enum { NYS_ASM_AUTO = 0, NYS_ASM_SIMT = 1, NYS_ASM_TUNE = 2 } nys_assembly;
 
 typedef struct nys_ctx nys_ctx;
 
@@ -143,6 +147,11 @@ int32_t nys_solve(nys_ctx* c, void* stream, double* x_out, int32_t* status_out);
    descriptors currently on the device), captured on the first call for this
    (x_out, status_out) pair and replayed afterwards.                         */
 int32_t nys_run(nys_ctx* c, void* stream, double* x_out, int32_t* status_out);
+
+/* Assembly configuration in use: kernel (NYS_ASM_AUTO = tensor cores or
+   NYS_ASM_SIMT) and rows per work item.  With NYS_ASM_TUNE this runs the tuner
+   if it has not run yet (synchronises `stream`).                              */
+int32_t nys_assembly_config(nys_ctx* c, void* stream, int32_t* kernel_out, int32_t* rows_out);
 
 /* Stride (doubles) of one instance in x_out: m_max + 3.                     */
 int32_t nys_x_stride(const nys_ctx* c);

@@ -13,7 +13,7 @@ NYS_OK, NYS_EINVAL, NYS_ENOMEM, NYS_ECUDA = 0, -1, -2, -3
 NYS_ENOTSPD, NYS_ENOCONV, NYS_ENONFINITE, NYS_ETIMEOUT = -4, -5, -6, -7
 NYS_EPRECISION, NYS_ESTATE = -8, -9
 NYS_FP64, NYS_MIXED = 0, 1
-NYS_ASM_AUTO, NYS_ASM_SIMT = 0, 1
+NYS_ASM_AUTO, NYS_ASM_SIMT, NYS_ASM_TUNE = 0, 1, 2
 NYS_COEF_TABLE, NYS_COEF_LIN, NYS_COEF_POLY_NL = 0, 1, 2
 NYS_M_MAX = 112
 
@@ -55,6 +55,7 @@ def lib():
         L.nys_solve.argtypes = [vp, vp, vp, vp]
         L.nys_run.argtypes = [vp, vp, vp, vp]
         L.nys_x_stride.argtypes = [vp]
+        L.nys_assembly_config.argtypes = [vp, vp, C.POINTER(i32), C.POINTER(i32)]
         L.nys_upload_bytes.argtypes = [vp]
         L.nys_upload_bytes.restype = C.c_int64
         L.nys_m_eff.argtypes = [vp, vp, C.POINTER(i32)]
@@ -70,7 +71,8 @@ def lib():
         L.nys_last_error.argtypes = []
         L.nys_last_error.restype = C.c_char_p
         for name in ("nys_setup", "nys_update", "nys_assemble", "nys_solve", "nys_run",
-                     "nys_x_stride", "nys_m_eff", "nys_eval", "nys_newton", "nys_grad"):
+                     "nys_x_stride", "nys_m_eff", "nys_eval", "nys_newton", "nys_grad",
+                     "nys_assembly_config"):
             getattr(L, name).restype = i32
         _LIB = L
     return _LIB
@@ -109,6 +111,12 @@ def nys_x_stride(ctx):
     return lib().nys_x_stride(ctx)
 
 
+def nys_assembly_config(ctx, stream):
+    kernel, rows = C.c_int32(), C.c_int32()
+    check(lib().nys_assembly_config(ctx, stream, C.byref(kernel), C.byref(rows)))
+    return kernel.value, rows.value
+
+
 def nys_upload_bytes(ctx):
     return lib().nys_upload_bytes(ctx)
 
@@ -138,7 +146,7 @@ def nys_destroy(ctx):
 
 
 EXPORTS = ("nys_setup", "nys_update", "nys_assemble", "nys_solve", "nys_run", "nys_x_stride",
-           "nys_upload_bytes",
+           "nys_upload_bytes", "nys_assembly_config",
            "nys_m_eff", "nys_eval", "nys_newton", "nys_grad", "nys_solve_noalloc", "nys_destroy",
            "nys_status_str",
            "nys_last_error")

@@ -76,7 +76,7 @@ class Batch:
         opt.refine_steps = int(refine_steps)
         opt.eig_tau = float(eig_tau)
         opt.scale_sqrt_m = 1 if scale_sqrt_m else 0
-        opt.assembly = {"auto": A.NYS_ASM_AUTO, "simt": A.NYS_ASM_SIMT}[assembly]
+        opt.assembly = {"auto": A.NYS_ASM_AUTO, "simt": A.NYS_ASM_SIMT, "tune": A.NYS_ASM_TUNE}[assembly]
         arr, keep = pack_instances(self.problems)
         self.ctx = A.nys_setup(arr, self.B, opt, _stream_handle(stream))
         self.XS = A.nys_x_stride(self.ctx)
@@ -113,6 +113,11 @@ class Batch:
         A.nys_run(self.ctx, _stream_handle(self.stream), _ptr(self.x), _ptr(self.status))
         self.version += 1
         return self.x, self.status
+
+    def assembly_config(self):
+        """(kernel, rows per work item) of the assembly; runs the tuner if pending."""
+        kernel, rows = A.nys_assembly_config(self.ctx, _stream_handle(self.stream))
+        return {A.NYS_ASM_AUTO: "tensor-core", A.NYS_ASM_SIMT: "simt"}[kernel], rows
 
     def m_eff(self):
         out = (C.c_int32 * self.B)()

@@ -136,6 +136,9 @@ struct nys_ctx {
   std::vector<int64_t> h_lagcap;           // lag-table offset of slot b (floats)
   int64_t total_rows = 0;
   int64_t lag_floats = 0;
+  int64_t rpi = 0;                // rows per assembly work item
+  int asm_slots = 0;              // assembly slot region (capacity) in slot_off / part
+  bool tune_pending = false;      // NYS_ASM_TUNE: choose kernel and item size at first use
   int k_max = 0;                  // largest lag-table length of the current sets
   // device
   DBuf<Inst> inst;
@@ -396,6 +399,44 @@ void nys_destroy(nys_ctx* c) {
   delete c;
 }
 
+// Assembly work list: the rows of every instance in chunks of at most rpi rows,
+// sorted by cost (rows x (m+2)^2, longest first, for the persistent grid); slot
+// offsets into `part` from 0.  Sets the instances' assembly slot ranges.
+static int64_t asm_layout(nys_ctx* c, int64_t rpi, std::vector<Work>& wl, std::vector<int64_t>& soff) {
+  wl.clear();
+  soff.clear();
+  int64_t poff = 0;
+  int slot = 0;
+  for (int b = 0; b < c->batch; ++b) {
+    const int nrows = c->shape[b].n - 1;
+    const int chunks = (int)std::max<int64_t>(1, (nrows + rpi - 1) / rpi);
+    const int M2 = c->shape[b].m + 2;
+    // linear: [first landmark, count] + packed Gram over m + 2 columns;
+    // Newton: packed Gram over m + 1 columns, two (m+1)-vectors, two scalars
+    const int64_t E = std::max<int64_t>((int64_t)M2 * (M2 + 1) / 2 + 2,
+                                        (int64_t)(M2 - 1) * M2 / 2 + 2 * (M2 - 1) + 2);
+    c->h_inst[b].slot_begin = slot;
+    c->h_inst[b].slot_count = chunks;
+    for (int k = 0; k < chunks; ++k) {
+      Work w;
+      w.inst = b;
+      w.r0 = 1 + (int)((int64_t)nrows * k / chunks);
+      w.r1 = 1 + (int)((int64_t)nrows * (k + 1) / chunks);
+      w.slot = slot++;
+      wl.push_back(w);
+      soff.push_back(poff);
+      poff += E;
+    }
+  }
+  const std::vector<nys_instance>& q = c->shape;
+  std::stable_sort(wl.begin(), wl.end(), [&](const Work& a, const Work& b2) {
+    const double ca = (double)(a.r1 - a.r0) * (q[a.inst].m + 2) * (q[a.inst].m + 2);
+    const double cb = (double)(b2.r1 - b2.r0) * (q[b2.inst].m + 2) * (q[b2.inst].m + 2);
+    return ca > cb;
+  });
+  return poff;
+}
+
 int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys_options* opt,
                   void* stream) {
   if (!out) return fail(NYS_EINVAL, "nys_setup: out is NULL");
@@ -409,7 +450,8 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
     delete c;
     return fail(NYS_EINVAL, "nys_setup: unknown precision %d", c->opt.precision);
   }
-  if (c->opt.assembly != NYS_ASM_AUTO && c->opt.assembly != NYS_ASM_SIMT) {
+  if (c->opt.assembly != NYS_ASM_AUTO && c->opt.assembly != NYS_ASM_SIMT &&
+      c->opt.assembly != NYS_ASM_TUNE) {
     const int a = c->opt.assembly;
     delete c;
     return fail(NYS_EINVAL, "nys_setup: unknown assembly kernel %d", a);
@@ -446,8 +488,6 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   cudaStream_t s = (cudaStream_t)stream;
 
   // row-pass work list: split instances so that there are >= 4 items per SM
-  std::vector<Work> wl;
-  std::vector<int64_t> soff;
   int64_t total_rows = 0;
   for (int b = 0; b < batch; ++b) total_rows += q[b].n - 1;
   c->total_rows = total_rows;
@@ -455,29 +495,21 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   int64_t rpi = std::max<int64_t>(64, (total_rows + target - 1) / target);
   // FP32 row pass: chunks of at most 1024 rows, whose landmark windows are narrow
   if (c->fp32) rpi = std::min<int64_t>(rpi, 1024);
-  int64_t poff = 0;
-  int slot = 0;
-  for (int b = 0; b < batch; ++b) {
-    const int nrows = q[b].n - 1;
-    const int chunks = (int)std::max<int64_t>(1, (nrows + rpi - 1) / rpi);
-    const int M2 = q[b].m + 2;
-    // linear: [first landmark, count] + packed Gram over m + 2 columns;
-    // Newton: packed Gram over m + 1 columns, two (m+1)-vectors, two scalars
-    const int64_t E = std::max<int64_t>((int64_t)M2 * (M2 + 1) / 2 + 2,
-                                        (int64_t)(M2 - 1) * M2 / 2 + 2 * (M2 - 1) + 2);
-    c->h_inst[b].slot_begin = slot;
-    c->h_inst[b].slot_count = chunks;
-    for (int k = 0; k < chunks; ++k) {
-      Work w;
-      w.inst = b;
-      w.r0 = 1 + (int)((int64_t)nrows * k / chunks);
-      w.r1 = 1 + (int)((int64_t)nrows * (k + 1) / chunks);
-      w.slot = slot++;
-      wl.push_back(w);
-      soff.push_back(poff);
-      poff += E;
-    }
+  c->rpi = rpi;
+  c->tune_pending = c->fp32 && c->opt.assembly == NYS_ASM_TUNE;
+  if (c->opt.assembly == NYS_ASM_TUNE && !c->fp32) c->opt.assembly = NYS_ASM_AUTO;
+  // the assembly slot region holds the finest layout the tuner may pick
+  std::vector<Work> wl;
+  std::vector<int64_t> soff;
+  const int64_t asm_elems = asm_layout(c, c->tune_pending ? std::min<int64_t>(rpi, 512) : rpi, wl, soff);
+  const size_t asm_work_cap = wl.size();
+  c->asm_slots = (int)soff.size();
+  if (c->tune_pending) {
+    asm_layout(c, rpi, wl, soff);
+    soff.resize((size_t)c->asm_slots, 0);
   }
+  int64_t poff = asm_elems;
+  int slot = c->asm_slots;
   // refinement work list: balance rule only (its per-item setup, a lag table
   // per instance, favours long chunks); slots of M1 doubles after the others
   std::vector<Work> rwl;
@@ -505,7 +537,6 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
     const double cb = (double)(b2.r1 - b2.r0) * (q[b2.inst].m + 2) * (q[b2.inst].m + 2);
     return ca > cb;
   };
-  std::stable_sort(wl.begin(), wl.end(), by_cost);
   std::stable_sort(rwl.begin(), rwl.end(), by_cost);
   c->nwork = (int)wl.size();
   c->nrwork = (int)rwl.size();
@@ -529,7 +560,7 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   A(c->lset.alloc(batch));
   A(c->lm.alloc(c->h_lm.size()));
   A(c->tab.alloc(std::max<size_t>(1, c->h_tab.size())));
-  A(c->work.alloc(wl.size()));
+  A(c->work.alloc(std::max(asm_work_cap, wl.size())));
   A(c->rwork.alloc(rwl.size()));
   A(c->slot_off.alloc(soff.size()));
   A(c->part.alloc((size_t)poff));
@@ -602,9 +633,88 @@ int32_t nys_update(nys_ctx* c, const nys_instance* q, void* stream) {
   return upload_and_setup(c, (cudaStream_t)stream, false);
 }
 
+// ---- assembly autotuner ------------------------------------------------------
+// Rebuild the assembly work list for chunks of rpi rows (within the slot region
+// sized at setup) and upload it with the instances' slot ranges.
+static int32_t set_asm_layout(nys_ctx* c, int64_t rpi, cudaStream_t s) {
+  std::vector<Work> wl;
+  std::vector<int64_t> soff;
+  asm_layout(c, rpi, wl, soff);
+  if ((int)soff.size() > c->asm_slots) return fail(NYS_ESTATE, "assembly layout exceeds its slot region");
+  CK(cudaStreamSynchronize(s));
+  CK(cudaMemcpy(c->work.p, wl.data(), sizeof(Work) * wl.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->slot_off.p, soff.data(), sizeof(int64_t) * soff.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->inst.p, c->h_inst.data(), sizeof(Inst) * c->batch, cudaMemcpyHostToDevice));
+  c->nwork = (int)wl.size();
+  c->rpi = rpi;
+  return NYS_OK;
+}
+
+// Time every (kernel, rows per item) candidate on this batch: one warm-up and
+// three timed launches each; keep the fastest.  Runs once, outside any graph.
+static int32_t tune_assembly(nys_ctx* c, cudaStream_t s) {
+  c->tune_pending = false;
+  if (c->factor_stale) {
+    CK(enqueue_factor(c, s));
+    c->factor_stale = false;
+  }
+  if (c->join_pending) {
+    CK(cudaStreamWaitEvent(s, c->ev_join, 0));
+    c->join_pending = false;
+  }
+  const int64_t rpi0 = c->rpi;
+  const int64_t rows[2] = {std::min<int64_t>(rpi0, 512), rpi0};
+  const int kinds[2] = {NYS_ASM_AUTO, NYS_ASM_SIMT};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_kind = NYS_ASM_AUTO;
+  int64_t best_rows = rpi0;
+  for (int kr = 0; kr < 2; ++kr) {
+    if (kr == 0 && rows[0] == rows[1]) continue;
+    int32_t r = set_asm_layout(c, rows[kr], s);
+    if (r != NYS_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return r; }
+    for (int kk = 0; kk < 2; ++kk) {
+      float tot = 0.f;
+      for (int rep = 0; rep < 4; ++rep) {
+        CK(cudaEventRecord(e0, s));
+        CK(launch_assemble(c->fp32, c->inst.p, c->lset.p, c->lag.p, c->W.p, c->work.p, c->nwork,
+                           c->counter.p, c->lm.p, c->tab.p, c->part.p, c->slot_off.p, c->m_max,
+                           c->k_max, c->num_sms, s, kinds[kk], c->err.p));
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) tot += ms;
+      }
+      if (tot < best) { best = tot; best_kind = kinds[kk]; best_rows = rows[kr]; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->opt.assembly = best_kind;
+  return set_asm_layout(c, best_rows, s);
+}
+
+int32_t nys_assembly_config(nys_ctx* c, void* stream, int32_t* kernel_out, int32_t* rows_out) {
+  if (!c) return fail(NYS_EINVAL, "nys_assembly_config: NULL context");
+  if (c->tune_pending) {
+    const int32_t r = tune_assembly(c, (cudaStream_t)stream);
+    if (r != NYS_OK) return r;
+  }
+  if (kernel_out) *kernel_out = c->opt.assembly;
+  if (rows_out) *rows_out = (int32_t)c->rpi;
+  return NYS_OK;
+}
+
 int32_t nys_assemble(nys_ctx* c, void* stream) {
   if (!c) return fail(NYS_EINVAL, "nys_assemble: NULL context");
   if (c->any_nl) return fail(NYS_EINVAL, "nys_assemble: the batch holds nonlinear instances (use nys_newton)");
+  if (c->tune_pending) {
+    const int32_t r = tune_assembly(c, (cudaStream_t)stream);
+    if (r != NYS_OK) return r;
+  }
   if (c->factor_stale) {
     CK(fork_factor(c, (cudaStream_t)stream));
     c->factor_stale = false;
@@ -653,6 +763,10 @@ int32_t nys_run(nys_ctx* c, void* stream, double* x_out, int32_t* status_out) {
   if (!c) return fail(NYS_EINVAL, "nys_run: NULL context");
   if (c->any_nl) return fail(NYS_EINVAL, "nys_run: the batch holds nonlinear instances");
   cudaStream_t s = (cudaStream_t)stream;
+  if (c->tune_pending) {
+    const int32_t r = tune_assembly(c, s);
+    if (r != NYS_OK) return r;
+  }
   cudaGraphExec_t exec = nullptr;
   for (auto& g : c->graphs)
     if (g.x == x_out && g.st == status_out) exec = g.exec;

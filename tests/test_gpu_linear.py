@@ -265,3 +265,28 @@ def test_truncated_landmark_kernel_mixed_reports_eprecision(api):
             assert err <= TOL["mixed"], (k, err)
         off += len(g)
     bt.close()
+
+
+def test_autotuned_assembly_keeps_parity(api):
+    """NYS_ASM_TUNE times the tensor-core and CUDA-core Gram with 512- and 1024-row
+    items on the batch itself and keeps the fastest; the result still matches the
+    oracle, through the graph path too."""
+    import torch
+    probs = ni.m0(64, n=3000, m=30) + ni.small_linear(6)
+    bt = api.Batch(probs, precision="mixed", assembly="tune")
+    kernel, rows = bt.assembly_config()
+    assert kernel in ("tensor-core", "simt") and rows in (512, 1024) or rows >= 64
+    x, st = bt.run()
+    grids = [core.grid(q) for q in probs]
+    y, _ = bt.eval(grids)
+    torch.cuda.synchronize()
+    assert (st.cpu().numpy() == 0).all()
+    yc = y.cpu().numpy()
+    off = 0
+    for q, g in zip(probs, grids):
+        ref = core.solve_linear(q)["y"]
+        err = np.abs(yc[off:off + len(g)] - ref).max() / np.abs(ref).max()
+        assert err <= TOL["mixed"], err
+        off += len(g)
+    assert bt.assembly_config() == (kernel, rows)   # chosen once
+    bt.close()
