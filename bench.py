@@ -367,6 +367,45 @@ def main():
         extra["grad_cfg4"] = {"instances": len(g4), "fp64_solve_ms": e0.elapsed_time(e1),
                               "grad_ms": e1.elapsed_time(e2) / 5}
         bg.close()
+
+        def step_ms(batch, fn, reps=3):
+            fn()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b2 = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b2.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b2) / reps
+
+        # ragged batched family: 4096 instances, n log-uniform in [500, 2e4],
+        # m in {20, 32, 50, 64, 100}, sigma = T/m, one CUDA graph per step
+        r3 = Batch(ni.cfg3(), precision="mixed")
+        ms3 = step_ms(r3, r3.run)
+        extra["ragged_4096"] = {"ms_per_step": ms3, "solves_s": len(r3.problems) / (ms3 / 1000.0),
+                                "rows": int(sum(q["n"] - 1 for q in r3.problems))}
+        r3.close()
+        # single instances at the paper's scale (n = 1e4, m = 50): linear FP64 and
+        # mixed, nonlinear y' = 1 - y^2 by Newton (FP64)
+        single = {}
+        for prec in ("fp64", "mixed"):
+            s1 = Batch([ni.cfg2_linear()], precision=prec)
+            single["linear_" + prec + "_ms"] = step_ms(s1, s1.run)
+            s1.close()
+        sn = Batch([ni.cfg2_tanh()], precision="fp64")
+        single["tanh_newton_ms"] = step_ms(sn, lambda: sn.newton(max_iter=50, tol=1e-10), reps=2)
+        sn.close()
+        extra["single_n1e4"] = single
+        # batched Newton family: 64 logistic / Duffing instances, n in [2000, 1e4], FP64
+        b5 = Batch(ni.cfg5(), precision="fp64")
+        ms5 = step_ms(b5, lambda: b5.newton(max_iter=20, tol=1e-10), reps=2)
+        _, st5, it5, _ = b5.newton(max_iter=20, tol=1e-10)
+        extra["newton_cfg5"] = {"instances": len(b5.problems), "ms": ms5,
+                                "max_iters": int(it5.max().item()),
+                                "converged": int((st5 == 0).sum().item())}
+        b5.close()
         rate, kk, dt = oracle_rate(probs, args.cpu_seconds)
         cpu_base = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                     "sample": "first %d instances of the workload, numpy FP64 oracle, %.1f s" % (kk, dt)}

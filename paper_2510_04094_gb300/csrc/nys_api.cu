@@ -16,10 +16,11 @@ namespace nys {
 // kernel launchers (defined in the other translation units)
 cudaError_t launch_setup(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
                          double* lam, float* lag, double tau, int m_max, cudaStream_t st,
-                         int allow_chol);
+                         int allow_chol, const int* m_bounds, int nclass);
 cudaError_t launch_lag(const Lset* lsets, int capacity, float* lag, cudaStream_t st);
 cudaError_t launch_eig(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
-                       double* lam, double tau, int m_max, cudaStream_t st, int allow_chol);
+                       double* lam, double tau, int m_max, cudaStream_t st, int allow_chol,
+                       const int* m_bounds, int nclass);
 cudaError_t launch_assemble(bool fp32, const Inst* insts, const Lset* lsets, const float* lag,
                             const double* W, const Work* work, int nwork, int* counter,
                             const int32_t* lm, const double* tab, double* part,
@@ -139,6 +140,7 @@ struct nys_ctx {
   int64_t rpi = 0;                // rows per assembly work item
   int asm_slots = 0;              // assembly slot region (capacity) in slot_off / part
   bool tune_pending = false;      // NYS_ASM_TUNE: choose kernel and item size at first use
+  std::vector<int> eig_bounds;    // landmark-count classes of the setup launches
   int k_max = 0;                  // largest lag-table length of the current sets
   // device
   DBuf<Inst> inst;
@@ -311,7 +313,8 @@ static int32_t pack(nys_ctx* c, const nys_instance* q, bool first) {
 
 static cudaError_t enqueue_factor(nys_ctx* c, cudaStream_t s) {
   return launch_setup(c->lset.p, c->batch, c->lm.p, c->W.p, c->W32.p, c->lam.p, c->lag.p,
-                      c->opt.eig_tau > 0 ? c->opt.eig_tau : 1e-12, c->m_max, s, c->fp32 ? 0 : 1);
+                      c->opt.eig_tau > 0 ? c->opt.eig_tau : 1e-12, c->m_max, s, c->fp32 ? 0 : 1,
+                      c->eig_bounds.data(), (int)c->eig_bounds.size());
 }
 
 // The lag tables (read by the row passes) go on the caller's stream; the
@@ -324,7 +327,7 @@ static cudaError_t fork_factor(nys_ctx* c, cudaStream_t s) {
   if (e == cudaSuccess)
     e = launch_eig(c->lset.p, c->batch, c->lm.p, c->W.p, c->W32.p, c->lam.p,
                    c->opt.eig_tau > 0 ? c->opt.eig_tau : 1e-12, c->m_max, c->side,
-                   c->fp32 ? 0 : 1);
+                   c->fp32 ? 0 : 1, c->eig_bounds.data(), (int)c->eig_bounds.size());
   if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
   return e;
 }
@@ -464,6 +467,17 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
     c->p_max = std::max(c->p_max, q[b].p);
   }
   c->m_max = std::min(c->m_max, NYS_M_MAX);
+  {  // setup launch classes: the distinct m values, or 16-wide buckets when many
+    std::vector<int> ms;
+    for (int b = 0; b < batch; ++b) ms.push_back(std::min(std::max(2, q[b].m), NYS_M_MAX));
+    std::sort(ms.begin(), ms.end());
+    ms.erase(std::unique(ms.begin(), ms.end()), ms.end());
+    if (ms.size() > 6) {
+      for (int& v : ms) v = std::min(NYS_M_MAX, (v + 15) / 16 * 16);
+      ms.erase(std::unique(ms.begin(), ms.end()), ms.end());
+    }
+    c->eig_bounds = ms;
+  }
   c->shape.assign(q, q + batch);
   c->h_lagcap.assign(batch, 0);
   {

@@ -24,7 +24,7 @@
 namespace nys {
 cudaError_t launch_setup(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
                          double* lam, float* lag, double tau, int m_max, cudaStream_t st,
-                         int allow_chol);
+                         int allow_chol, const int* m_bounds, int nclass);
 cudaError_t launch_assemble(bool fp32, const Inst* insts, const Lset* lsets, const float* lag,
                             const double* W, const Work* work, int nwork, int* counter,
                             const int32_t* lm, const double* tab, double* part,
@@ -215,7 +215,7 @@ extern "C" int32_t nys_solve_noalloc(const nys_instance* q, int32_t batch, doubl
   const int32_t* d_stinit = reinterpret_cast<const int32_t*>(B + o_st);
   NA_CK(launch_setup(d_lset, nl, d_lm, reinterpret_cast<double*>(B + o_W),
                      reinterpret_cast<float*>(B + o_W32), reinterpret_cast<double*>(B + o_lam),
-                     nullptr, 1e-12, m_max, st, 1));
+                     nullptr, 1e-12, m_max, st, 1, nullptr, 0));
   // the work counter is cleared inside launch_assemble before the kernel
   NA_CK(launch_assemble(false, d_inst, d_lset, nullptr, reinterpret_cast<const double*>(B + o_W),
                         reinterpret_cast<const Work*>(B + o_work),

@@ -13,6 +13,7 @@ namespace nys {
 
 constexpr int kSetupThreads = 256;
 constexpr int kMaxSweeps = 40;
+constexpr int kJW = kSetupThreads / 32;            // warps of the setup CTA
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -51,30 +52,48 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 }
 
 // Parallel cyclic Jacobi sweeps on the symmetric m x m matrix A (ld), rotations
-// accumulated in V; round-robin pairing in pos (N = m rounded up to even; index
-// m, if present, sits out).  Stops when off(A)^2 <= tol tot(A)^2.
+// accumulated in V.  Round-robin ("chess tournament") pairing of N = m rounded
+// up to even players: in round r player 0 stays, the others sit at
+// 1 + ((k - 1 - r) mod (N - 1)); pair k = (slot k, slot N-1-k); index m, if
+// present, sits out (identity rotation).  Each round: one thread per pair
+// computes the pair's rotation (symmetric Schur decomposition) from the
+// round's starting entries; after a barrier the CTA applies A <- J^T A J to
+// whole 2x2 blocks (row pair a, column pair b: the column rotation, then the
+// row rotation, as two sequential one-sided passes would) and V <- V J to row
+// segments, all independent.  Stops when off(A)^2 <=
+// tol tot(A)^2, or (stall > 0) once off(A)^2 <= stall tot(A)^2 and a sweep no
+// longer shrinks it fourfold: the rounding floor of the working precision.
+__device__ __forceinline__ int rr_pos(int k, int r, int N) {
+  if (k == 0) return 0;
+  int t = (k - 1 - r) % (N - 1);
+  if (t < 0) t += N - 1;
+  return 1 + t;
+}
+
 template <typename T>
-__device__ void jacobi_sweeps(T* A, T* V, int ld, int m, int N, int* pos, T* cs, double* red,
-                              double tol, int max_sweeps) {
-  const int tid = threadIdx.x, nt = blockDim.x, half = N / 2;
-  for (int k = tid; k < N; k += nt) pos[k] = k;
-  __syncthreads();
+__device__ void jacobi_sweeps(T* A, T* V, int ld, int m, int N, T* cs, int* pq, double* red,
+                              double tol, int max_sweeps, double stall) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int half = N / 2;
+  constexpr int kJB = sizeof(T) == 4 ? 4 : 2;   // row pairs whose loads are batched
+  double prev = 1e300;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     double off = 0.0, tot = 0.0;
-    for (int e = tid; e < m * m; e += nt) {
-      const int j = e / m, l = e % m;
-      const double a = (double)A[j * ld + l];
-      tot += a * a;
-      if (j != l) off += a * a;
-    }
+    for (int j = warp; j < m; j += nw)
+      for (int l = lane; l < m; l += 32) {
+        const double a = (double)A[j * ld + l];
+        tot += a * a;
+        if (j != l) off += a * a;
+      }
     off = block_sum(off, red);
     tot = block_sum(tot, red);
     if (off <= tol * tot) break;
+    if (stall > 0.0 && off <= stall * tot && off > 0.25 * prev) break;
+    prev = off;
     for (int round = 0; round < N - 1; ++round) {
-      // rotation angles of the m/2 disjoint pairs (symmetric Schur decomposition)
       for (int k = tid; k < half; k += nt) {
-        int p = pos[k], q = pos[N - 1 - k];
-        if (p > q) { int t = p; p = q; q = t; }
+        int p = rr_pos(k, round, N), q = rr_pos(N - 1 - k, round, N);
+        if (p > q) { const int t = p; p = q; q = t; }
         T c = T(1), sn = T(0);
         if (q < m) {
           const T apq = A[p * ld + q];
@@ -87,54 +106,98 @@ __device__ void jacobi_sweeps(T* A, T* V, int ld, int m, int N, int* pos, T* cs,
         }
         cs[k] = c;
         cs[half + k] = sn;
+        pq[k] = p;
+        pq[half + k] = q;
       }
       __syncthreads();
-      // A <- A J and V <- V J : columns p, q of every row
-      for (int e = tid; e < half * m; e += nt) {
-        const int k = e / m, i = e % m;
-        int p = pos[k], q = pos[N - 1 - k];
-        if (p > q) { int t = p; p = q; q = t; }
-        if (q >= m) continue;
-        const T c = cs[k], sn = cs[half + k];
-        const T aip = A[i * ld + p], aiq = A[i * ld + q];
-        A[i * ld + p] = c * aip - sn * aiq;
-        A[i * ld + q] = sn * aip + c * aiq;
-        const T vip = V[i * ld + p], viq = V[i * ld + q];
-        V[i * ld + p] = c * vip - sn * viq;
-        V[i * ld + q] = sn * vip + c * viq;
-      }
-      __syncthreads();
-      // A <- J^T A : rows p, q
-      for (int e = tid; e < half * m; e += nt) {
-        const int k = e / m, j = e % m;
-        int p = pos[k], q = pos[N - 1 - k];
-        if (p > q) { int t = p; p = q; q = t; }
-        if (q >= m) continue;
-        const T c = cs[k], sn = cs[half + k];
-        const T apj = A[p * ld + j], aqj = A[q * ld + j];
-        A[p * ld + j] = c * apj - sn * aqj;
-        A[q * ld + j] = sn * apj + c * aqj;
-      }
-      __syncthreads();
-      if (tid == 0) {  // round-robin: keep pos[0], rotate the rest
-        const int last = pos[N - 1];
-        for (int k = N - 1; k > 1; --k) pos[k] = pos[k - 1];
-        pos[1] = last;
+      // lane <-> column pair b (its rotation read once per round); warp <-> row
+      // pairs a and rows i of V; a thread's loads all precede its stores
+      for (int b = lane; b < half; b += 32) {
+        const int p2 = pq[b], q2 = pq[half + b];
+        const T c2 = cs[b], s2 = cs[half + b];
+        const bool h2 = q2 < m;
+        for (int a0 = warp; a0 < half; a0 += kJB * kJW) {
+        T x[kJB][4];
+#pragma unroll
+        for (int j = 0; j < kJB; ++j) {
+          const int a = a0 + j * kJW;
+          if (a < half) {
+            const int p1 = pq[a], q1 = pq[half + a];
+            const bool h1 = q1 < m;
+            x[j][0] = A[p1 * ld + p2];
+            x[j][1] = h2 ? A[p1 * ld + q2] : T(0);
+            x[j][2] = h1 ? A[q1 * ld + p2] : T(0);
+            x[j][3] = (h1 && h2) ? A[q1 * ld + q2] : T(0);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < kJB; ++j) {
+          const int a = a0 + j * kJW;
+          if (a < half) {
+            const int p1 = pq[a], q1 = pq[half + a];
+            const T c1 = cs[a], s1 = cs[half + a];
+            const bool h1 = q1 < m;
+            const T y00 = c2 * x[j][0] - s2 * x[j][1], y01 = s2 * x[j][0] + c2 * x[j][1];
+            const T y10 = c2 * x[j][2] - s2 * x[j][3], y11 = s2 * x[j][2] + c2 * x[j][3];
+            A[p1 * ld + p2] = c1 * y00 - s1 * y10;
+            if (h2) A[p1 * ld + q2] = c1 * y01 - s1 * y11;
+            if (h1) A[q1 * ld + p2] = s1 * y00 + c1 * y10;
+            if (h1 && h2) A[q1 * ld + q2] = s1 * y01 + c1 * y11;
+          }
+        }
+        }
+        if (h2) {
+          for (int i0 = warp; i0 < m; i0 += 4 * kJW) {
+            T vp[4], vq[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int i = i0 + u * kJW;
+              if (i < m) { vp[u] = V[i * ld + p2]; vq[u] = V[i * ld + q2]; }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int i = i0 + u * kJW;
+              if (i < m) {
+                V[i * ld + p2] = c2 * vp[u] - s2 * vq[u];
+                V[i * ld + q2] = s2 * vp[u] + c2 * vq[u];
+              }
+            }
+          }
+        }
       }
       __syncthreads();
     }
   }
 }
 
-__global__ void __launch_bounds__(kSetupThreads)
+// perm[0..m) = indices of the diagonal entries of A in descending order (ties by
+// index), one rank per thread
+template <typename T>
+__device__ void sort_desc(const T* A, int ld, int m, int* perm) {
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    const T d = A[k * ld + k];
+    int r = 0;
+    for (int j = 0; j < m; ++j) {
+      const T e = A[j * ld + j];
+      r += (e > d) || (e == d && j < k);
+    }
+    perm[r] = k;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kSetupThreads, 4)
 k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict__ W_all,
-            float* __restrict__ W32_all, double* __restrict__ lam_all, double tau, int allow_chol) {
+            float* __restrict__ W32_all, double* __restrict__ lam_all, double tau, int allow_chol,
+            int m_lo, int m_hi) {
   // the grid covers every slot; inactive slots (instances that share another
   // instance's set) return at once, so a captured graph stays valid when an
   // update changes which instances share
   const int L = blockIdx.x;
   const Lset S = lsets[L];
-  if (!S.active) return;
+  // one launch per landmark-count class (m_lo, m_hi], each with shared memory
+  // for its own largest m
+  if (!S.active || S.m <= m_lo || S.m > m_hi) return;
   const int m = S.m;
   const int N = m + (m & 1);  // even player count; index m (if present) is a bye
   const int ld = m + 1;
@@ -143,13 +206,12 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict_
   double* V = A + m * ld;
   double* cs = V + m * ld;                 // N/2 cosines then N/2 sines
   double* red = cs + N;                    // 32
-  int* pos = reinterpret_cast<int*>(red + 32);   // N
+  int* pos = reinterpret_cast<int*>(red + 32);   // N: the round's pairs (p then q)
   int* perm = pos + N;                     // m
   int* idx = perm + m;                     // m
   const int tid = threadIdx.x, nt = blockDim.x;
 
   for (int j = tid; j < m; j += nt) idx[j] = lm_idx[S.lm_off + j];
-  for (int k = tid; k < N; k += nt) pos[k] = k;
   __syncthreads();
   double* Wl = W_all + S.w_off;
   float* W32l = W32_all + S.w_off;
@@ -163,64 +225,66 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict_
   // FP64 solves (allow_chol): L^-1 has large alternating entries, and the FP32
   // factor of the mixed path built from it refines about ten times slower
   // than one built from the nearly orthogonal rows of Lambda^-1/2 U^T.
-  for (int e = tid; e < m * m; e += nt) {
-    const int j = e / m, l = e % m;
-    const double d = (double)(idx[j] - idx[l]) * S.hs;
-    V[j * ld + l] = exp(-d * d);
-  }
-  __shared__ int s_bad;
-  if (tid == 0) s_bad = 0;
-  __syncthreads();
-  for (int k = 0; k < m; ++k) {   // lower Cholesky of Omega in V
-    if (tid == 0) {
-      const double d = V[k * ld + k];
-      if (!(d > 0.0)) { s_bad = 1; V[k * ld + k] = 1.0; }
-      else V[k * ld + k] = sqrt(d);
-    }
-    __syncthreads();
-    const double lkk = V[k * ld + k];
-    for (int i = k + 1 + tid; i < m; i += nt) V[i * ld + k] /= lkk;
-    __syncthreads();
-    const int R = m - k - 1;
-    for (int e = tid; e < R * R; e += nt) {
-      const int i = k + 1 + e / R, j = k + 1 + e % R;
-      if (j <= i) V[i * ld + j] -= V[i * ld + k] * V[j * ld + k];
-    }
-    __syncthreads();
-  }
-  // W = L^-1 into A (lower triangular), one column per thread: L w = e_c
-  for (int c = tid; c < m; c += nt) {
-    for (int i = 0; i < c; ++i) A[i * ld + c] = 0.0;
-    for (int i = c; i < m; ++i) {
-      double sv = (i == c) ? 1.0 : 0.0;
-      for (int k2 = c; k2 < i; ++k2) sv -= V[i * ld + k2] * A[k2 * ld + c];
-      A[i * ld + c] = sv / V[i * ld + i];
-    }
-  }
-  __syncthreads();
-  {
-    double f2 = 0.0;
+  if (allow_chol) {
     for (int e = tid; e < m * m; e += nt) {
-      const double w = A[(e / m) * ld + (e % m)];
-      f2 += w * w;
+      const int j = e / m, l = e % m;
+      const double d = (double)(idx[j] - idx[l]) * S.hs;
+      V[j * ld + l] = exp(-d * d);
     }
-    f2 = block_sum(f2, red);
-    const bool chol_ok = allow_chol && (s_bad == 0) && isfinite(f2) && ((double)m * f2 <= 1e6);
-    if (chol_ok) {
+    __shared__ int s_bad;
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    for (int k = 0; k < m; ++k) {   // lower Cholesky of Omega in V
+      if (tid == 0) {
+        const double d = V[k * ld + k];
+        if (!(d > 0.0)) { s_bad = 1; V[k * ld + k] = 1.0; }
+        else V[k * ld + k] = sqrt(d);
+      }
+      __syncthreads();
+      const double lkk = V[k * ld + k];
+      for (int i = k + 1 + tid; i < m; i += nt) V[i * ld + k] /= lkk;
+      __syncthreads();
+      const int R = m - k - 1;
+      for (int e = tid; e < R * R; e += nt) {
+        const int i = k + 1 + e / R, j = k + 1 + e % R;
+        if (j <= i) V[i * ld + j] -= V[i * ld + k] * V[j * ld + k];
+      }
+      __syncthreads();
+    }
+    // W = L^-1 into A (lower triangular), one column per thread: L w = e_c
+    for (int c = tid; c < m; c += nt) {
+      for (int i = 0; i < c; ++i) A[i * ld + c] = 0.0;
+      for (int i = c; i < m; ++i) {
+        double sv = (i == c) ? 1.0 : 0.0;
+        for (int k2 = c; k2 < i; ++k2) sv -= V[i * ld + k2] * A[k2 * ld + c];
+        A[i * ld + c] = sv / V[i * ld + i];
+      }
+    }
+    __syncthreads();
+    {
+      double f2 = 0.0;
       for (int e = tid; e < m * m; e += nt) {
         const double w = A[(e / m) * ld + (e % m)];
-        Wl[e] = w;
-        W32l[e] = (float)w;
+        f2 += w * w;
       }
-      for (int k = tid; k < m; k += nt) {
-        const double l = V[k * ld + k];
-        lam_all[(int64_t)L * kMMax + k] = l * l;   // Cholesky pivots (informational)
+      f2 = block_sum(f2, red);
+      const bool chol_ok = allow_chol && (s_bad == 0) && isfinite(f2) && ((double)m * f2 <= 1e6);
+      if (chol_ok) {
+        for (int e = tid; e < m * m; e += nt) {
+          const double w = A[(e / m) * ld + (e % m)];
+          Wl[e] = w;
+          W32l[e] = (float)w;
+        }
+        for (int k = tid; k < m; k += nt) {
+          const double l = V[k * ld + k];
+          lam_all[(int64_t)L * kMMax + k] = l * l;   // Cholesky pivots (informational)
+        }
+        if (tid == 0) {
+          lsets[L].m_eff = m;
+          lsets[L].omode = 0;
+        }
+        return;
       }
-      if (tid == 0) {
-        lsets[L].m_eff = m;
-        lsets[L].omode = 0;
-      }
-      return;
     }
   }
   // FP32 route (mixed contexts): Jacobi sweeps in FP32 (64x the FP64 rate), then
@@ -245,15 +309,9 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict_
     }
     __syncthreads();
     // FP32 sweeps reach off(A)^2 ~ 1e-13 tot(A)^2; the correction below absorbs the rest
-    jacobi_sweeps<float>(Af, Vf, ld, m, N, pos, reinterpret_cast<float*>(cs), red, 1e-13, kMaxSweeps);
+    jacobi_sweeps<float>(Af, Vf, ld, m, N, reinterpret_cast<float*>(cs), pos, red, 1e-13, kMaxSweeps, 1e-9);
+    sort_desc(Af, ld, m, perm);
     if (tid == 0) {
-      for (int k = 0; k < m; ++k) perm[k] = k;
-      for (int a2 = 0; a2 < m; ++a2) {
-        int best = a2;
-        for (int b2 = a2 + 1; b2 < m; ++b2)
-          if (Af[perm[b2] * ld + perm[b2]] > Af[perm[best] * ld + perm[best]]) best = b2;
-        const int t = perm[a2]; perm[a2] = perm[best]; perm[best] = t;
-      }
       const double lmax = Af[perm[0] * ld + perm[0]], lmin = Af[perm[m - 1] * ld + perm[m - 1]];
       red[0] = (lmin > 1e-5 * lmax && lmin > 0.0) ? 1.0 : 0.0;
     }
@@ -316,17 +374,11 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict_
     V[j * ld + l] = (j == l) ? 1.0 : 0.0;
   }
   __syncthreads();
-  jacobi_sweeps<double>(A, V, ld, m, N, pos, cs, red, 1e-30, kMaxSweeps);
+  jacobi_sweeps<double>(A, V, ld, m, N, cs, pos, red, 1e-30, kMaxSweeps, 0.0);
 
   // sort eigenvalues descending, keep lambda > tau * lambda_max
+  sort_desc(A, ld, m, perm);
   if (tid == 0) {
-    for (int k = 0; k < m; ++k) perm[k] = k;
-    for (int a = 0; a < m; ++a) {
-      int best = a;
-      for (int b = a + 1; b < m; ++b)
-        if (A[perm[b] * ld + perm[b]] > A[perm[best] * ld + perm[best]]) best = b;
-      const int t = perm[a]; perm[a] = perm[best]; perm[best] = t;
-    }
     const double lmax = A[perm[0] * ld + perm[0]];
     int me = 0;
     while (me < m && A[perm[me] * ld + perm[me]] > tau * lmax) ++me;
@@ -385,23 +437,35 @@ cudaError_t launch_lag(const Lset* lsets, int capacity, float* lag, cudaStream_t
   return cudaGetLastError();
 }
 
+// m_bounds: increasing class bounds of the landmark counts present (nclass of
+// them, the last >= every m); nclass == 0: one class up to m_max.
 cudaError_t launch_eig(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
-                       double* lam, double tau, int m_max, cudaStream_t st, int allow_chol) {
+                       double* lam, double tau, int m_max, cudaStream_t st, int allow_chol,
+                       const int* m_bounds, int nclass) {
   if (capacity == 0) return cudaSuccess;
-  const size_t sm = setup_smem_bytes(m_max);
+  const size_t smax = setup_smem_bytes(m_max);
   cudaError_t e = cudaFuncSetAttribute(k_setup_eig, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sm);
+                                       (int)smax);
   if (e != cudaSuccess) return e;
-  k_setup_eig<<<capacity, kSetupThreads, sm, st>>>(lsets, lm_idx, W, W32, lam, tau, allow_chol);
-  return cudaGetLastError();
+  int lo = 0;
+  for (int k = 0; k < (nclass > 0 ? nclass : 1); ++k) {
+    const int hi = (nclass > 0) ? m_bounds[k] : m_max;
+    k_setup_eig<<<capacity, kSetupThreads, setup_smem_bytes(hi), st>>>(lsets, lm_idx, W, W32, lam,
+                                                                         tau, allow_chol, lo, hi);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    lo = hi;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_setup(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
                          double* lam, float* lag, double tau, int m_max, cudaStream_t st,
-                         int allow_chol) {
+                         int allow_chol, const int* m_bounds, int nclass) {
   cudaError_t e = launch_lag(lsets, capacity, lag, st);
   if (e != cudaSuccess) return e;
-  return launch_eig(lsets, capacity, lm_idx, W, W32, lam, tau, m_max, st, allow_chol);
+  return launch_eig(lsets, capacity, lm_idx, W, W32, lam, tau, m_max, st, allow_chol, m_bounds,
+                    nclass);
 }
 
 }  // namespace nys
