@@ -340,11 +340,11 @@ k_refine_rows(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
               const int32_t* __restrict__ st_all, int k_cap) {
   // k_cap: capacity of the shared-memory kappa table (fixed at launch, so a
   // graph captured earlier stays safe when an update lengthens the tables)
-  extern __shared__ __align__(16) float smr[];
+  extern __shared__ __align__(16) float2 smr[];
   __shared__ int s_item;
   __shared__ int s_idx[kMMax];
-  __shared__ float s_zh[kM1Max], s_zl[kM1Max];
-  __shared__ float s_sh[kRefRows], s_sl[kRefRows];   // residuals (float-float)
+  __shared__ float4 s_zj[kM1Max];   // per column: z~ hi, lo, landmark index (bits), -
+  __shared__ float2 s_s[kRefRows];  // residuals (float-float)
   __shared__ float s_rc[kRefRows * 10];  // per row: A0 A1 A2 w1 r, each as hi/lo
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (;;) {
@@ -358,21 +358,18 @@ k_refine_rows(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     const float* T = lag + L.lag_off;
     const int m = I.m, K = L.K;
     const bool folded = (I.kind == NYS_COEF_LIN) && (K <= k_cap);
-    float* khi = smr;
-    float* klo = smr + (2 * K + 1);
+    float2* kk = smr;   // kappa(t - K), t = 0..2K, float-float
     for (int j = tid; j < m; j += kRefThreads) s_idx[j] = lm_idx[I.lm_off + j];
     for (int j = tid; j <= m; j += kRefThreads) {
       const ff z = ff_from_double(zs[(int64_t)wk.inst * ZS + j]);
-      s_zh[j] = z.hi;
-      s_zl[j] = z.lo;
+      s_zj[j] = make_float4(z.hi, z.lo, __int_as_float(j < m ? lm_idx[I.lm_off + j] : 0), 0.f);
     }
     const bool skip = (st_all[wk.inst] != NYS_OK);
     const RowConst RK = I.rk;
     if (folded && !skip) {  // constant operator: kappa(k) for k = -K..K
       for (int t = tid; t <= 2 * K; t += kRefThreads) {
         const ff kv = kappa_lag(T, K, t - K, RK.A0, RK.A1, RK.A2);
-        khi[t] = kv.hi;
-        klo[t] = kv.lo;
+        kk[t] = make_float2(kv.hi, kv.lo);
       }
     }
     // The sums acc_j = sum_i kappa~_ij s_i cancel almost completely at the
@@ -398,9 +395,9 @@ k_refine_rows(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
       for (int r = tid; r < rows; r += kRefThreads) {
         const int i = base + r;
         const float* rc = s_rc + r * 10;
-        const ff A0 = {rc[0], rc[1]}, A1 = {rc[2], rc[3]}, A2 = {rc[4], rc[5]};
         ff sp = {0.f, 0.f};   // sum of kappa~ z~ (subtracted at the end)
-        // kappa vanishes beyond lag K: only landmarks with |i - idx_j| <= K count
+        // kappa vanishes beyond lag K: only landmarks with |i - idx_j| <= K
+        // count, so every table index below lies in 0..2K
         int jlo = 0, jhi = m;
         {
           int a = 0, b = m;           // first j with idx_j >= i - K
@@ -410,46 +407,55 @@ k_refine_rows(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
           while (a < b) { const int c = (a + b) >> 1; if (s_idx[c] <= i + K) a = c + 1; else b = c; }
           jhi = a;
         }
-        for (int j = jlo; j < jhi; ++j) {
-          const int k = i - s_idx[j];
-          ff kv;
-          if (folded) {
-            const int t = k + K;
-            kv = (t >= 0 && t <= 2 * K) ? ff{khi[t], klo[t]} : ff{0.f, 0.f};
-          } else {
-            kv = kappa_lag(T, K, k, A0, A1, A2);
+        if (folded) {
+          const int iK = i + K;
+          for (int j = jlo; j < jhi; ++j) {
+            const float4 zj = s_zj[j];
+            const float2 kv = kk[iK - __float_as_int(zj.z)];
+            ff_acc_mul(sp, ff{kv.x, kv.y}, ff{zj.x, zj.y});
           }
-          ff_acc_mul(sp, kv, ff{s_zh[j], s_zl[j]});
+        } else {
+          const ff A0 = {rc[0], rc[1]}, A1 = {rc[2], rc[3]}, A2 = {rc[4], rc[5]};
+          for (int j = jlo; j < jhi; ++j) {
+            const float4 zj = s_zj[j];
+            ff_acc_mul(sp, kappa_lag(T, K, i - __float_as_int(zj.z), A0, A1, A2), ff{zj.x, zj.y});
+          }
         }
-        ff_acc_mul(sp, ff{rc[6], rc[7]}, ff{s_zh[m], s_zl[m]});
+        const float4 zb = s_zj[m];
+        ff_acc_mul(sp, ff{rc[6], rc[7]}, ff{zb.x, zb.y});
         sp = ff_norm(sp);
         const ff sres = ff_add(ff{rc[8], rc[9]}, ff{-sp.hi, -sp.lo});
-        s_sh[r] = sres.hi;
-        s_sl[r] = sres.lo;
+        s_s[r] = make_float2(sres.hi, sres.lo);
       }
       __syncthreads();
       // acc_j += kappa~_ij s_i: lanes over rows (conflict-free table reads)
 #pragma unroll
       for (int q = 0; q < kRefColsPerWarp; ++q) {
         const int j = warp + q * kRefWarps;
-        if (j <= m) {
-          const int cj = (j < m) ? s_idx[j] : 0;
-          // rows within lag K of landmark j (all rows for the b column)
-          const int rlo = (j < m) ? max(0, cj - K - base) : 0;
-          const int rhi = (j < m) ? min(rows, cj + K + 1 - base) : rows;
-          for (int r = rlo + lane; r < rhi; r += 32) {
-            const int i = base + r;
-            const float* rc = s_rc + r * 10;
-            ff kv;
-            if (j == m) {
-              kv = ff{rc[6], rc[7]};
-            } else if (folded) {
-              const int t = i - cj + K;
-              kv = (t >= 0 && t <= 2 * K) ? ff{khi[t], klo[t]} : ff{0.f, 0.f};
-            } else {
-              kv = kappa_lag(T, K, i - cj, ff{rc[0], rc[1]}, ff{rc[2], rc[3]}, ff{rc[4], rc[5]});
+        if (j < m) {
+          // rows within lag K of landmark j: table index r + toff in 0..2K
+          const int cj = s_idx[j];
+          const int rlo = max(0, cj - K - base), rhi = min(rows, cj + K + 1 - base);
+          if (folded) {
+            const int toff = base - cj + K;
+            for (int r = rlo + lane; r < rhi; r += 32) {
+              const float2 kv = kk[r + toff], sv = s_s[r];
+              ff_acc_mul(acc[q], ff{kv.x, kv.y}, ff{sv.x, sv.y});
             }
-            ff_acc_mul(acc[q], kv, ff{s_sh[r], s_sl[r]});
+          } else {
+            for (int r = rlo + lane; r < rhi; r += 32) {
+              const float* rc = s_rc + r * 10;
+              const ff kv = kappa_lag(T, K, base + r - cj, ff{rc[0], rc[1]}, ff{rc[2], rc[3]},
+                                      ff{rc[4], rc[5]});
+              const float2 sv = s_s[r];
+              ff_acc_mul(acc[q], kv, ff{sv.x, sv.y});
+            }
+          }
+        } else if (j == m) {   // the b column: every row
+          for (int r = lane; r < rows; r += 32) {
+            const float* rc = s_rc + r * 10;
+            const float2 sv = s_s[r];
+            ff_acc_mul(acc[q], ff{rc[6], rc[7]}, ff{sv.x, sv.y});
           }
         }
       }
