@@ -290,6 +290,8 @@ size_t solve_smem_bytes(bool fp32, int m_max) {
 constexpr int kRefThreads = 256;
 constexpr int kRefRows = 256;
 constexpr int kRefLagMax = 10000;   // largest K of the shared-memory kappa table
+constexpr int kRefPad = 32;         // zero entries on each side of the kappa table
+static_assert(kRefRows == kRefThreads, "the residual pass maps one row to each thread");
 
 __device__ __forceinline__ ff ff_mul(ff a, ff b) { return ff_mul_ff(a, b); }
 
@@ -358,7 +360,7 @@ k_refine_rows(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     const float* T = lag + L.lag_off;
     const int m = I.m, K = L.K;
     const bool folded = (I.kind == NYS_COEF_LIN) && (K <= k_cap);
-    float2* kk = smr;   // kappa(t - K), t = 0..2K, float-float
+    float2* kk = smr;   // kappa(t - K - kRefPad), t = 0..2K + 2 kRefPad, float-float
     for (int j = tid; j < m; j += kRefThreads) s_idx[j] = lm_idx[I.lm_off + j];
     for (int j = tid; j <= m; j += kRefThreads) {
       const ff z = ff_from_double(zs[(int64_t)wk.inst * ZS + j]);
@@ -367,8 +369,9 @@ k_refine_rows(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     const bool skip = (st_all[wk.inst] != NYS_OK);
     const RowConst RK = I.rk;
     if (folded && !skip) {  // constant operator: kappa(k) for k = -K..K
-      for (int t = tid; t <= 2 * K; t += kRefThreads) {
-        const ff kv = kappa_lag(T, K, t - K, RK.A0, RK.A1, RK.A2);
+      // (zero beyond lag K, so the padding holds zeros)
+      for (int t = tid; t <= 2 * (K + kRefPad); t += kRefThreads) {
+        const ff kv = kappa_lag(T, K, t - K - kRefPad, RK.A0, RK.A1, RK.A2);
         kk[t] = make_float2(kv.hi, kv.lo);
       }
     }
@@ -391,41 +394,43 @@ k_refine_rows(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         for (int q = 0; q < 5; ++q) { rc[2 * q] = c5[q].hi; rc[2 * q + 1] = c5[q].lo; }
       }
       __syncthreads();
-      // residual of each row, one row per thread: s = r - kappa~^T z~
-      for (int r = tid; r < rows; r += kRefThreads) {
-        const int i = base + r;
-        const float* rc = s_rc + r * 10;
-        ff sp = {0.f, 0.f};   // sum of kappa~ z~ (subtracted at the end)
-        // kappa vanishes beyond lag K: only landmarks with |i - idx_j| <= K
-        // count, so every table index below lies in 0..2K
-        int jlo = 0, jhi = m;
-        {
-          int a = 0, b = m;           // first j with idx_j >= i - K
-          while (a < b) { const int c = (a + b) >> 1; if (s_idx[c] < i - K) a = c + 1; else b = c; }
-          jlo = a;
-          b = m;                      // first j with idx_j > i + K
-          while (a < b) { const int c = (a + b) >> 1; if (s_idx[c] <= i + K) a = c + 1; else b = c; }
-          jhi = a;
-        }
-        if (folded) {
-          const int iK = i + K;
-          for (int j = jlo; j < jhi; ++j) {
-            const float4 zj = s_zj[j];
-            const float2 kv = kk[iK - __float_as_int(zj.z)];
-            ff_acc_mul(sp, ff{kv.x, kv.y}, ff{zj.x, zj.y});
+      // residual of each row, one row per thread: s = r - kappa~^T z~.  kappa
+      // vanishes beyond lag K; a warp walks the landmarks within lag K of any
+      // of its 32 rows (one range for all lanes), so a lane's lag stays within
+      // K + 31 and its table index inside the zero padding.
+      if (warp * 32 < rows) {
+        const int ia = base + warp * 32, ib = base + min(rows, warp * 32 + 32) - 1;
+        int a = 0, b = m;             // first j with idx_j >= ia - K
+        while (a < b) { const int c = (a + b) >> 1; if (s_idx[c] < ia - K) a = c + 1; else b = c; }
+        const int jlo = a;
+        b = m;                        // first j with idx_j > ib + K
+        while (a < b) { const int c = (a + b) >> 1; if (s_idx[c] <= ib + K) a = c + 1; else b = c; }
+        const int jhi = a;
+        const int r = tid;
+        if (r < rows) {
+          const int i = base + r;
+          const float* rc = s_rc + r * 10;
+          ff sp = {0.f, 0.f};   // sum of kappa~ z~ (subtracted at the end)
+          if (folded) {
+            const int iK = i + K + kRefPad;
+            for (int j = jlo; j < jhi; ++j) {
+              const float4 zj = s_zj[j];
+              const float2 kv = kk[iK - __float_as_int(zj.z)];
+              ff_acc_mul(sp, ff{kv.x, kv.y}, ff{zj.x, zj.y});
+            }
+          } else {
+            const ff A0 = {rc[0], rc[1]}, A1 = {rc[2], rc[3]}, A2 = {rc[4], rc[5]};
+            for (int j = jlo; j < jhi; ++j) {
+              const float4 zj = s_zj[j];
+              ff_acc_mul(sp, kappa_lag(T, K, i - __float_as_int(zj.z), A0, A1, A2), ff{zj.x, zj.y});
+            }
           }
-        } else {
-          const ff A0 = {rc[0], rc[1]}, A1 = {rc[2], rc[3]}, A2 = {rc[4], rc[5]};
-          for (int j = jlo; j < jhi; ++j) {
-            const float4 zj = s_zj[j];
-            ff_acc_mul(sp, kappa_lag(T, K, i - __float_as_int(zj.z), A0, A1, A2), ff{zj.x, zj.y});
-          }
+          const float4 zb = s_zj[m];
+          ff_acc_mul(sp, ff{rc[6], rc[7]}, ff{zb.x, zb.y});
+          sp = ff_norm(sp);
+          const ff sres = ff_add(ff{rc[8], rc[9]}, ff{-sp.hi, -sp.lo});
+          s_s[r] = make_float2(sres.hi, sres.lo);
         }
-        const float4 zb = s_zj[m];
-        ff_acc_mul(sp, ff{rc[6], rc[7]}, ff{zb.x, zb.y});
-        sp = ff_norm(sp);
-        const ff sres = ff_add(ff{rc[8], rc[9]}, ff{-sp.hi, -sp.lo});
-        s_s[r] = make_float2(sres.hi, sres.lo);
       }
       __syncthreads();
       // acc_j += kappa~_ij s_i: lanes over rows (conflict-free table reads)
@@ -433,11 +438,11 @@ k_refine_rows(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
       for (int q = 0; q < kRefColsPerWarp; ++q) {
         const int j = warp + q * kRefWarps;
         if (j < m) {
-          // rows within lag K of landmark j: table index r + toff in 0..2K
+          // rows within lag K of landmark j: table index r + toff in the table
           const int cj = s_idx[j];
           const int rlo = max(0, cj - K - base), rhi = min(rows, cj + K + 1 - base);
           if (folded) {
-            const int toff = base - cj + K;
+            const int toff = base - cj + K + kRefPad;
             for (int r = rlo + lane; r < rhi; r += 32) {
               const float2 kv = kk[r + toff], sv = s_s[r];
               ff_acc_mul(acc[q], ff{kv.x, kv.y}, ff{sv.x, sv.y});
@@ -866,7 +871,7 @@ cudaError_t launch_newton_step(const Inst* insts, const Lset* lsets, const doubl
 
 size_t refine_smem_bytes(int k_max) {
   const int K = k_max < kRefLagMax ? k_max : kRefLagMax;
-  const size_t table = sizeof(float) * 2 * (size_t)(2 * K + 1);
+  const size_t table = sizeof(float) * 2 * (size_t)(2 * (K + kRefPad) + 1);
   const size_t red = sizeof(float) * (size_t)kRefThreads * 2 + 64;
   return table > red ? table : red;
 }
