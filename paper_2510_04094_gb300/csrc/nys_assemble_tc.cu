@@ -175,10 +175,41 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         M.nst = ok ? nst : 0;
         mbar_arrive(smem_u32(&s_mfull[rs]));
       }
+      // This warp's units (block p, 8-slot group g, K half qh) are the same in
+      // every stage of the item: at most two, since 2 P Gf <= 32 < 2 x 20.
+      // lane -> (slot j8, K position w4)
+      static_assert(2 * kTcProducers >= 32, "two units per producer warp cover a stage");
       const float invGf = 1.0f / (float)Gf;
-      const float hs = (float)I.hs;
+      const float hsc = (float)I.hs * 1.20112240878645f;   // h / sigma * sqrt(log2 e)
       const int tmax = min(nrows, kTcMaxRows) - 1;
       const int j8 = lane >> 2, w4 = lane & 3;
+      int u_kind[2], u_t0[2], u_lag[2], u_off[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int pu = warp + u * kTcProducers;
+        u_kind[u] = -1;
+        u_t0[u] = u_lag[u] = u_off[u] = 0;
+        if (pu < 2 * P * Gf) {
+          const int pg = pu >> 1, qh = pu & 1;        // (block, group), half of the K chunks
+          const int pb = (int)(((float)pg + 0.5f) * invGf);
+          const int g = pg - pb * Gf;
+          const int j = (g << 3) + j8;               // local column of this lane
+          const int idxj = s_idx[min(jlo + j, m - 1)];
+          u_kind[u] = (j < A) ? 0 : (j == A ? 1 : (j == A + 1 ? 2 : 3));
+          u_t0[u] = 32 * pb + w4 + 16 * qh;            // item row of the first chunk (stage 0)
+          u_lag[u] = wk.r0 + u_t0[u] - idxj;           // its lag t_i - s_j in grid steps
+          // operand row of (pb, g, j8), K word w4, and the K-half's swizzle bit
+          u_off[u] = ((((pb * Bs) >> 3) + g) << 10) + (j8 << 7) + (w4 << 2) +
+                     (((qh ^ (j8 >> 2)) & 1) << 6);
+        }
+      }
+      int xq[4];   // 128-byte swizzle of K chunk q + 4 qh: ((q + 4 qh) ^ j8) & 7
+#pragma unroll
+      for (int q = 0; q < 4; ++q) xq[q] = (q ^ (j8 & 3)) << 4;
+      // A0 + A1 x + A2 x^2 = A0 + (A1 / c) y + (A2 / c^2) y^2, y = c x, c = sqrt(log2 e)
+      const float ic1 = 0.832554611157698f, ic2 = 0.693147180559945f;
+      const float LA0 = RK.A0.hi, LB1 = RK.A1.hi * ic1, LB2 = -RK.A2.hi * ic2;
+      const float w1 = RK.w1.hi;
       bool late = false;
       for (int k = 0; k < nst; ++k, ++gs) {
         const int s = gs & (kTcStages - 1);
@@ -189,27 +220,19 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         used[s] = true;
         unsigned char* hi = sm + s * kTcStageBytes;
         if (!late) {
-          // warp -> (block p, 8-slot group g); lane -> (slot j8, K position w4)
-          for (int pu = warp; pu < 2 * P * Gf; pu += kTcProducers) {
-            const int pg = pu >> 1, qh = pu & 1;        // (block, group), half of the K chunks
-            const int p = (int)(((float)pg + 0.5f) * invGf);
-            const int g = pg - p * Gf;
-            const int j = (g << 3) + j8;               // local column of this lane
-            const int idxj = s_idx[min(jlo + j, m - 1)];
-            const int kind = (j < A) ? 0 : (j == A ? 1 : (j == A + 1 ? 2 : 3));
-            const int t0 = k * SR + 32 * p + w4 + 16 * qh;   // item row for this lane's first chunk
-            unsigned char* hrow = hi + ((((p * Bs) >> 3) + g) << 10) + (j8 << 7) + (w4 << 2);
-            unsigned char* lrow = hrow + kTcTileBytes;
-            // the 8 K chunks of this lane are independent: evaluate all, then store
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int kind = u_kind[u];
+            if (kind < 0) continue;                    // warp-uniform
+            const int t0 = k * SR + u_t0[u];           // item row of this lane's first chunk
+            // the 4 K chunks of this lane are independent: evaluate all, then store
             float vv[4];
             if (kind == 0) {
-              // y = x sqrt(log2 e), x = (t_i - s_j) / sigma at the rows t0 + 4q (one FMA
-              // per chunk); exp(-x^2) = 2^(-y^2) and A0 + A1 x + A2 x^2 =
-              // A0 + (A1 / c) y + (A2 / c^2) y^2 with c = sqrt(log2 e)
-              const float c1 = 1.20112240878645f, ic1 = 0.832554611157698f, ic2 = 0.693147180559945f;
-              const float y0 = (float)(wk.r0 + t0 - idxj) * (hs * c1);
-              const float dy = 4.f * hs * c1;
-              float A0 = RK.A0.hi, B1 = RK.A1.hi * ic1, B2 = -RK.A2.hi * ic2;
+              // y = x sqrt(log2 e), x = (t_i - s_j) / sigma at the rows t0 + 4q (one
+              // FMA per chunk); exp(-x^2) = 2^(-y^2)
+              const float y0 = (float)(u_lag[u] + k * SR) * hsc;
+              const float dy = 4.f * hsc;
+              float A0 = LA0, B1 = LB1, B2 = LB2;
 #pragma unroll
               for (int q = 0; q < 4; ++q) {
                 if (!lin) {
@@ -224,7 +247,7 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
 #pragma unroll
               for (int q = 0; q < 4; ++q) {
                 const int tc = min(t0 + 4 * q, tmax);
-                vv[q] = (kind == 1) ? (lin ? RK.w1.hi : s_co[tc].w) : (kind == 2 ? s_r[tc] : 0.f);
+                vv[q] = (kind == 1) ? (lin ? w1 : s_co[tc].w) : (kind == 2 ? s_r[tc] : 0.f);
               }
             }
             if (t0 + 12 >= nrows) {                    // rows past the end of the item
@@ -232,13 +255,14 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
               for (int q = 0; q < 4; ++q)
                 if (t0 + 4 * q >= nrows) vv[q] = 0.f;
             }
+            unsigned char* hrow = hi + u_off[u];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               // TF32 part by truncation (the low part v - hi is exact either way)
               const float h = __uint_as_float(__float_as_uint(vv[q]) & 0xFFFFE000u);
-              const int ch = (((q + 4 * qh) ^ j8) & 7) << 4;   // 128-byte swizzle
-              *reinterpret_cast<float*>(hrow + ch) = h;
-              *reinterpret_cast<float*>(lrow + ch) = vv[q] - h;
+              float* dst = reinterpret_cast<float*>(hrow + xq[q]);
+              dst[0] = h;
+              dst[kTcTileBytes / 4] = vv[q] - h;
             }
           }
         }
