@@ -15,11 +15,14 @@
 // to its diagonal blocks (the off-diagonal blocks mix rows and are not read).
 //
 // Warp roles (persistent CTA per SM, all hand-offs through mbarriers):
-//   * 20 producer warps fetch work items, evaluate features (FP32, MUFU
-//     exponential) straight into the operand layout (one warp store fills one
-//     8-slot x 4-row core matrix, conflict-free; a warp takes half of the K
-//     chunks of one 8-slot group per unit) and arrive on the stage's "full"
-//     barrier; four stage buffers;
+//   * two setup warps prepare the next work item while the current one is
+//     produced: fetch it, load its landmarks, evaluate r(t_i) of its rows,
+//     find its landmark window; item data double-buffered;
+//   * 20 producer warps evaluate features (FP32, MUFU exponential) straight
+//     into the operand layout (one warp store fills one 8-slot x 4-row core
+//     matrix, conflict-free; a warp takes half of the K chunks of one 8-slot
+//     group per unit) and arrive on the stage's "full" barrier; four stage
+//     buffers;
 //   * one issuer warp waits for "full", issues the MMAs (two accumulators per
 //     item, alternating) and commits to the stage's "empty" barrier and, after
 //     the item's last stage, to the accumulator barrier;
@@ -36,10 +39,12 @@
 
 namespace nys {
 
-constexpr int kTcProducers = 20;                       // producer warps
-constexpr int kTcIssuerWarp = kTcProducers;            // warp 16
-constexpr int kTcEpiWarp0 = kTcProducers + 1;          // warps 17..20
-constexpr int kTcThreads = 32 * (kTcProducers + 5);
+constexpr int kTcProducers = 20;                       // producer warps 0..19
+constexpr int kTcIssuerWarp = kTcProducers;            // warp 20
+constexpr int kTcEpiWarp0 = kTcProducers + 1;          // warps 21..24
+constexpr int kTcSetupWarp0 = kTcProducers + 5;        // warps 25, 26
+constexpr int kTcSetupThreads = 64;
+constexpr int kTcThreads = 32 * (kTcProducers + 5) + kTcSetupThreads;
 constexpr int kTcStages = 4;
 constexpr int kTcTileBytes = 16384;      // 128 operand rows x 32 K positions (TF32)
 constexpr int kTcStageBytes = 2 * kTcTileBytes;   // hi + lo
@@ -54,8 +59,13 @@ constexpr uint32_t kTcCols = 2 * kTcSetCols;   // two sets: the whole tensor mem
 
 size_t asm_tc_smem_bytes() { return (size_t)kTcStageArea + kTcSBytes + 1024; }
 
-struct TcItem {          // metadata of a work item, handed from producers to the other roles
+struct TcItem {          // metadata of a work item for the issuer and the epilogue
   int w, slot, jlo, A, M2, P, Bs, N, nst;
+};
+
+struct TcProd {          // what the producers need of a work item (nst < 0: no more items)
+  int r0, nrows, m, jlo, A, P, Bs, SR, Gf, nst, lin;
+  float hsc, LA0, LB1, LB2, w1;
 };
 
 __device__ __forceinline__ void bar_named(int id, int count) {
@@ -74,12 +84,14 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   float* S = reinterpret_cast<float*>(sm + kTcStageArea);
   __shared__ __align__(8) uint64_t s_full[kTcStages], s_empty[kTcStages];
   __shared__ __align__(8) uint64_t s_mfull[2], s_mfree[2], s_accf[2], s_afree[2], s_drain;
+  __shared__ __align__(8) uint64_t s_sfull[2], s_sempty[2];
   __shared__ TcItem s_meta[2];
+  __shared__ TcProd s_pm[2];
   __shared__ uint32_t s_tmem;
-  __shared__ int s_w, s_abort, s_eok;
-  __shared__ int s_idx[kMMax];
-  __shared__ float s_r[kTcMaxRows];   // r(t_i) of the rows of the item (producers)
-  __shared__ float4 s_co[kTcMaxRows]; // kind TABLE: (A0, A1, A2, w1) of every row
+  __shared__ int s_w, s_abort, s_eok, s_sok;
+  __shared__ int s_idx[2][kMMax];
+  __shared__ float s_r[2][kTcMaxRows];   // r(t_i) of the rows of the item
+  __shared__ float4 s_co[kTcMaxRows];    // kind TABLE: (A0, A1, A2, w1) of every row
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == 0) tmem_alloc(smem_u32(&s_tmem), kTcCols);
@@ -95,6 +107,10 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
       mbar_init(smem_u32(&s_afree[s]), 1);
     }
     mbar_init(smem_u32(&s_drain), 1);
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(smem_u32(&s_sfull[s]), kTcSetupThreads);
+      mbar_init(smem_u32(&s_sempty[s]), kTcProducers);
+    }
     mbar_fence_init();
     s_abort = 0;
   }
@@ -105,82 +121,30 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
 
   if (warp < kTcProducers) {
     // =========================== producers ===========================
-    uint32_t ph_empty[kTcStages] = {0, 0, 0, 0}, ph_mfree[2] = {0, 0};
+    uint32_t ph_empty[kTcStages] = {0, 0, 0, 0}, ph_sfull[2] = {0, 0};
     bool used[kTcStages] = {false, false, false, false};
     int gs = 0;                                        // stages produced so far
-    // the lead producer fetches the next item while the current one is produced
-    int next_w = (tid == 0) ? atomicAdd(counter, 1) : 0;
     for (int it = 0;; ++it) {
       const int rs = it & 1;
-      if (tid == 0) {
-        s_w = s_abort ? nwork : next_w;
-        if (next_w < nwork) next_w = atomicAdd(counter, 1);
-      }
-      bar_named(1, 32 * kTcProducers);
-      const int w = s_w;                               // one value for every producer
-      if (w >= nwork) {
-        if (tid == 0) {   // sentinel for the issuer and the epilogue
-          bool ok = true;
-          if (it >= 2) ok = mbar_wait_bounded(smem_u32(&s_mfree[rs]), ph_mfree[rs], kTcWaitIter);
-          if (!ok) atomicExch(&s_abort, 1);
-          s_meta[rs].nst = -1;
-          mbar_arrive(smem_u32(&s_mfull[rs]));
-        }
+      // the setup warps have prepared this item in buffer rs
+      if (!mbar_wait_bounded(smem_u32(&s_sfull[rs]), ph_sfull[rs], kTcWaitIter)) {
+        atomicExch(&s_abort, 1);
         break;
       }
-      const Work wk = work[w];
-      const Inst I = insts[wk.inst];
-      const int m = I.m;
-      const int nrows = wk.r1 - wk.r0;
-      const bool lin = (I.kind == NYS_COEF_LIN);
-      const RowConst RK = I.rk;
-      for (int j = tid; j < m; j += 32 * kTcProducers) s_idx[j] = lm_idx[I.lm_off + j];
-      for (int t = tid; t < nrows && t < kTcMaxRows; t += 32 * kTcProducers) {
-        const int i = wk.r0 + t;
-        if (lin) {
-          s_r[t] = lin_rhs_ff(RK, i);
-        } else {
-          ff c5[5];
-          row_coef_ff(I, RK, tab, i, c5);
-          s_r[t] = c5[4].hi;
-          s_co[t] = make_float4(c5[0].hi, c5[1].hi, c5[2].hi, c5[3].hi);
-        }
-      }
-      bar_named(1, 32 * kTcProducers);
-      // landmark window of the chunk: |i - idx_j| <= K for some row i in [r0, r1)
-      const int Kl = lsets[I.lset].K;
-      int jlo, A;
-      {
-        int a = 0, b = m;
-        while (a < b) { const int c = (a + b) >> 1; if (s_idx[c] < wk.r0 - Kl) a = c + 1; else b = c; }
-        jlo = a;
-        b = m;
-        while (a < b) { const int c = (a + b) >> 1; if (s_idx[c] <= wk.r1 - 1 + Kl) a = c + 1; else b = c; }
-        A = a - jlo;
-      }
-      const int M2 = A + 2;
-      const int P = (M2 <= 32) ? 4 : (M2 <= 64 ? 2 : 1);
-      const int Bs = 128 / P;
-      const int SR = 32 * P;                          // rows per stage
-      const int Gf = (M2 + 7) >> 3;                   // 8-slot groups written per block
-      const int nst = (nrows <= kTcMaxRows) ? (nrows + SR - 1) / SR : 0;
-      if (tid == 0) {
-        bool ok = true;
-        if (it >= 2) ok = mbar_wait_bounded(smem_u32(&s_mfree[rs]), ph_mfree[rs], kTcWaitIter);
-        if (it >= 2) ph_mfree[rs] ^= 1u;
-        if (!ok || nrows > kTcMaxRows) atomicExch(&s_abort, 1);
-        TcItem& M = s_meta[rs];
-        M.w = w; M.slot = wk.slot; M.jlo = jlo; M.A = A; M.M2 = M2; M.P = P; M.Bs = Bs;
-        M.N = (P > 1) ? 128 : round_up(M2, 16);
-        M.nst = ok ? nst : 0;
-        mbar_arrive(smem_u32(&s_mfull[rs]));
-      }
+      ph_sfull[rs] ^= 1u;
+      const TcProd Pm = s_pm[rs];
+      if (Pm.nst < 0) break;
+      const int* idx = s_idx[rs];
+      const float* rr = s_r[rs];
+      const int m = Pm.m, nrows = Pm.nrows, jlo = Pm.jlo, A = Pm.A, P = Pm.P, Bs = Pm.Bs;
+      const int SR = Pm.SR, Gf = Pm.Gf, nst = Pm.nst;
+      const bool lin = Pm.lin != 0;
       // This warp's units (block p, 8-slot group g, K half qh) are the same in
       // every stage of the item: at most two, since 2 P Gf <= 32 < 2 x 20.
       // lane -> (slot j8, K position w4)
       static_assert(2 * kTcProducers >= 32, "two units per producer warp cover a stage");
       const float invGf = 1.0f / (float)Gf;
-      const float hsc = (float)I.hs * 1.20112240878645f;   // h / sigma * sqrt(log2 e)
+      const float hsc = Pm.hsc;                        // h / sigma * sqrt(log2 e)
       const int tmax = min(nrows, kTcMaxRows) - 1;
       const int j8 = lane >> 2, w4 = lane & 3;
       int u_kind[2], u_t0[2], u_lag[2], u_off[2];
@@ -194,10 +158,10 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
           const int pb = (int)(((float)pg + 0.5f) * invGf);
           const int g = pg - pb * Gf;
           const int j = (g << 3) + j8;               // local column of this lane
-          const int idxj = s_idx[min(jlo + j, m - 1)];
+          const int idxj = idx[min(jlo + j, m - 1)];
           u_kind[u] = (j < A) ? 0 : (j == A ? 1 : (j == A + 1 ? 2 : 3));
           u_t0[u] = 32 * pb + w4 + 16 * qh;            // item row of the first chunk (stage 0)
-          u_lag[u] = wk.r0 + u_t0[u] - idxj;           // its lag t_i - s_j in grid steps
+          u_lag[u] = Pm.r0 + u_t0[u] - idxj;           // its lag t_i - s_j in grid steps
           // operand row of (pb, g, j8), K word w4, and the K-half's swizzle bit
           u_off[u] = ((((pb * Bs) >> 3) + g) << 10) + (j8 << 7) + (w4 << 2) +
                      (((qh ^ (j8 >> 2)) & 1) << 6);
@@ -208,8 +172,7 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
       for (int q = 0; q < 4; ++q) xq[q] = (q ^ (j8 & 3)) << 4;
       // A0 + A1 x + A2 x^2 = A0 + (A1 / c) y + (A2 / c^2) y^2, y = c x, c = sqrt(log2 e)
       const float ic1 = 0.832554611157698f, ic2 = 0.693147180559945f;
-      const float LA0 = RK.A0.hi, LB1 = RK.A1.hi * ic1, LB2 = -RK.A2.hi * ic2;
-      const float w1 = RK.w1.hi;
+      const float LA0 = Pm.LA0, LB1 = Pm.LB1, LB2 = Pm.LB2, w1 = Pm.w1;
       bool late = false;
       for (int k = 0; k < nst; ++k, ++gs) {
         const int s = gs & (kTcStages - 1);
@@ -247,7 +210,7 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
 #pragma unroll
               for (int q = 0; q < 4; ++q) {
                 const int tc = min(t0 + 4 * q, tmax);
-                vv[q] = (kind == 1) ? (lin ? w1 : s_co[tc].w) : (kind == 2 ? s_r[tc] : 0.f);
+                vv[q] = (kind == 1) ? (lin ? w1 : s_co[tc].w) : (kind == 2 ? rr[tc] : 0.f);
               }
             }
             if (t0 + 12 >= nrows) {                    // rows past the end of the item
@@ -271,6 +234,108 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         if (lane == 0) mbar_arrive(smem_u32(&s_full[s]));
       }
       if (late && lane == 0) atomicExch(&s_abort, 1);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&s_sempty[rs]));   // buffer rs may be refilled
+    }
+  } else if (warp >= kTcSetupWarp0) {
+    // ============================== setup ==============================
+    // Prepares item it + 1 while the producers fill the stages of item it:
+    // fetches the work item, loads its landmarks, evaluates r(t_i) (and the
+    // row coefficients of kind TABLE), finds the landmark window and publishes
+    // the metadata to the producers (buffer it % 2) and to the issuer and the
+    // epilogue (slot it % 2).
+    const int st = tid - 32 * kTcSetupWarp0;           // 0..63
+    uint32_t ph_sempty[2] = {0, 0}, ph_mfree[2] = {0, 0};
+    bool waited[2] = {false, false};
+    for (int it = 0;; ++it) {
+      const int rs = it & 1;
+      // buffer rs held item it - 2: the producers must be done with it
+      if (it >= 2 && !waited[rs]) {
+        if (st == 0) s_sok = mbar_wait_bounded(smem_u32(&s_sempty[rs]), ph_sempty[rs], kTcWaitIter) ? 1 : 0;
+        ph_sempty[rs] ^= 1u;
+        bar_named(3, kTcSetupThreads);
+        if (!s_sok) atomicExch(&s_abort, 1);
+      }
+      waited[rs] = false;
+      if (st == 0) s_w = s_abort ? nwork : atomicAdd(counter, 1);
+      bar_named(3, kTcSetupThreads);
+      const int w = s_w;
+      bar_named(3, kTcSetupThreads);                   // every thread has read s_w
+      if (w >= nwork) {   // sentinels for the producers, the issuer and the epilogue
+        if (st == 0) {
+          s_pm[rs].nst = -1;
+          bool ok = true;
+          if (it >= 2) ok = mbar_wait_bounded(smem_u32(&s_mfree[rs]), ph_mfree[rs], kTcWaitIter);
+          if (!ok) atomicExch(&s_abort, 1);
+          s_meta[rs].nst = -1;
+          mbar_arrive(smem_u32(&s_mfull[rs]));
+        }
+        mbar_arrive(smem_u32(&s_sfull[rs]));
+        break;
+      }
+      const Work wk = work[w];
+      const Inst& I = insts[wk.inst];
+      const int m = I.m;
+      const int nrows = wk.r1 - wk.r0;
+      const bool lin = (I.kind == NYS_COEF_LIN);
+      const RowConst RK = I.rk;
+      for (int j = st; j < m; j += kTcSetupThreads) s_idx[rs][j] = lm_idx[I.lm_off + j];
+      if (!lin && it >= 1) {
+        // s_co has one buffer: the producers must be done with item it - 1
+        if (st == 0) s_sok = mbar_wait_bounded(smem_u32(&s_sempty[rs ^ 1]), ph_sempty[rs ^ 1], kTcWaitIter) ? 1 : 0;
+        ph_sempty[rs ^ 1] ^= 1u;
+        waited[rs ^ 1] = true;
+        bar_named(3, kTcSetupThreads);
+        if (!s_sok) atomicExch(&s_abort, 1);
+      }
+      for (int t = st; t < nrows && t < kTcMaxRows; t += kTcSetupThreads) {
+        const int i = wk.r0 + t;
+        if (lin) {
+          s_r[rs][t] = lin_rhs_ff(RK, i);
+        } else {
+          ff c5[5];
+          row_coef_ff(I, RK, tab, i, c5);
+          s_r[rs][t] = c5[4].hi;
+          s_co[t] = make_float4(c5[0].hi, c5[1].hi, c5[2].hi, c5[3].hi);
+        }
+      }
+      bar_named(3, kTcSetupThreads);                   // s_idx of this item complete
+      if (st == 0) {
+        // landmark window of the chunk: |i - idx_j| <= K for some row i in [r0, r1)
+        const int* idx = s_idx[rs];
+        const int Kl = lsets[I.lset].K;
+        int a = 0, b = m;
+        while (a < b) { const int c = (a + b) >> 1; if (idx[c] < wk.r0 - Kl) a = c + 1; else b = c; }
+        const int jlo = a;
+        b = m;
+        while (a < b) { const int c = (a + b) >> 1; if (idx[c] <= wk.r1 - 1 + Kl) a = c + 1; else b = c; }
+        const int A = a - jlo;
+        const int M2 = A + 2;
+        const int P = (M2 <= 32) ? 4 : (M2 <= 64 ? 2 : 1);
+        const int Bs = 128 / P;
+        const int SR = 32 * P;                          // rows per stage
+        const int nst = (nrows <= kTcMaxRows) ? (nrows + SR - 1) / SR : 0;
+        bool ok = true;
+        if (it >= 2) ok = mbar_wait_bounded(smem_u32(&s_mfree[rs]), ph_mfree[rs], kTcWaitIter);
+        if (it >= 2) ph_mfree[rs] ^= 1u;
+        if (!ok || nrows > kTcMaxRows) atomicExch(&s_abort, 1);
+        TcItem& M = s_meta[rs];
+        M.w = w; M.slot = wk.slot; M.jlo = jlo; M.A = A; M.M2 = M2; M.P = P; M.Bs = Bs;
+        M.N = (P > 1) ? 128 : round_up(M2, 16);
+        M.nst = ok ? nst : 0;
+        mbar_arrive(smem_u32(&s_mfull[rs]));
+        TcProd& Q = s_pm[rs];
+        Q.r0 = wk.r0; Q.nrows = nrows; Q.m = m; Q.jlo = jlo; Q.A = A; Q.P = P; Q.Bs = Bs;
+        Q.SR = SR; Q.Gf = (M2 + 7) >> 3;               // 8-slot groups written per block
+        Q.nst = ok ? nst : 0;
+        Q.lin = lin ? 1 : 0;
+        Q.hsc = (float)I.hs * 1.20112240878645f;
+        Q.LA0 = RK.A0.hi;
+        Q.LB1 = RK.A1.hi * 0.832554611157698f;
+        Q.LB2 = -RK.A2.hi * 0.693147180559945f;
+        Q.w1 = RK.w1.hi;
+      }
+      mbar_arrive(smem_u32(&s_sfull[rs]));             // each thread: its writes are done
     }
   } else if (warp == kTcIssuerWarp) {
     // ============================= issuer =============================
@@ -331,7 +396,7 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
       (void)ncommit_acc;
     }
   } else {
-    // ============================ epilogue ============================
+    // ============================ epilogue (warps 21..24) ============================
     const int et = tid - 32 * kTcEpiWarp0;             // 0..127
     const int quad = warp & 3;                         // tensor-memory lane quarter
     uint32_t ph_mfull[2] = {0, 0}, ph_accf[2] = {0, 0};
