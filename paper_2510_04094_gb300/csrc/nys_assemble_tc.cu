@@ -51,7 +51,7 @@ constexpr int kTcStageBytes = 2 * kTcTileBytes;   // hi + lo
 constexpr int kTcStageArea = kTcStages * kTcStageBytes;
 constexpr int kTcSBytes = 128 * 129 * 4; // epilogue staging: P blocks of Bs x (Bs + 1)
 constexpr int kTcMaxRows = 1024;         // rows of a work item (the host keeps items this size)
-constexpr int kTcWaitIter = 1 << 22;     // try_wait polls before giving up (seconds)
+constexpr int kTcWaitIter = 1 << 22;     // try_wait polls (<= 1 us each) before giving up
 constexpr int kTcAcc = 2;                // accumulators per item (alternating MMAs)
 constexpr uint32_t kTcAccCols = 128;     // columns per accumulator (N <= 128)
 constexpr uint32_t kTcSetCols = kTcAcc * kTcAccCols;
@@ -121,17 +121,18 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
 
   if (warp < kTcProducers) {
     // =========================== producers ===========================
-    uint32_t ph_empty[kTcStages] = {0, 0, 0, 0}, ph_sfull[2] = {0, 0};
-    bool used[kTcStages] = {false, false, false, false};
+    // mbarrier phase parities and buffer states as bit masks (bit = buffer),
+    // kept in registers
+    uint32_t ph_empty = 0, ph_sfull = 0, used = 0;
     int gs = 0;                                        // stages produced so far
     for (int it = 0;; ++it) {
       const int rs = it & 1;
       // the setup warps have prepared this item in buffer rs
-      if (!mbar_wait_bounded(smem_u32(&s_sfull[rs]), ph_sfull[rs], kTcWaitIter)) {
+      if (!mbar_wait_bounded(smem_u32(&s_sfull[rs]), (ph_sfull >> rs) & 1u, kTcWaitIter)) {
         atomicExch(&s_abort, 1);
         break;
       }
-      ph_sfull[rs] ^= 1u;
+      ph_sfull ^= 1u << rs;
       const TcProd Pm = s_pm[rs];
       if (Pm.nst < 0) break;
       const int* idx = s_idx[rs];
@@ -176,11 +177,11 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
       bool late = false;
       for (int k = 0; k < nst; ++k, ++gs) {
         const int s = gs & (kTcStages - 1);
-        if (used[s]) {  // the MMAs that read this buffer must be done
-          late = late || !mbar_wait_bounded(smem_u32(&s_empty[s]), ph_empty[s], kTcWaitIter);
-          ph_empty[s] ^= 1u;
+        if ((used >> s) & 1u) {  // the MMAs that read this buffer must be done
+          late = late || !mbar_wait_bounded(smem_u32(&s_empty[s]), (ph_empty >> s) & 1u, kTcWaitIter);
+          ph_empty ^= 1u << s;
         }
-        used[s] = true;
+        used |= 1u << s;
         unsigned char* hi = sm + s * kTcStageBytes;
         if (!late) {
 #pragma unroll
@@ -245,18 +246,17 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     // the metadata to the producers (buffer it % 2) and to the issuer and the
     // epilogue (slot it % 2).
     const int st = tid - 32 * kTcSetupWarp0;           // 0..63
-    uint32_t ph_sempty[2] = {0, 0}, ph_mfree[2] = {0, 0};
-    bool waited[2] = {false, false};
+    uint32_t ph_sempty = 0, ph_mfree = 0, waited = 0;   // bit masks (bit = buffer)
     for (int it = 0;; ++it) {
       const int rs = it & 1;
       // buffer rs held item it - 2: the producers must be done with it
-      if (it >= 2 && !waited[rs]) {
-        if (st == 0) s_sok = mbar_wait_bounded(smem_u32(&s_sempty[rs]), ph_sempty[rs], kTcWaitIter) ? 1 : 0;
-        ph_sempty[rs] ^= 1u;
+      if (it >= 2 && !((waited >> rs) & 1u)) {
+        if (st == 0) s_sok = mbar_wait_bounded(smem_u32(&s_sempty[rs]), (ph_sempty >> rs) & 1u, kTcWaitIter) ? 1 : 0;
+        ph_sempty ^= 1u << rs;
         bar_named(3, kTcSetupThreads);
         if (!s_sok) atomicExch(&s_abort, 1);
       }
-      waited[rs] = false;
+      waited &= ~(1u << rs);
       if (st == 0) s_w = s_abort ? nwork : atomicAdd(counter, 1);
       bar_named(3, kTcSetupThreads);
       const int w = s_w;
@@ -265,7 +265,7 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         if (st == 0) {
           s_pm[rs].nst = -1;
           bool ok = true;
-          if (it >= 2) ok = mbar_wait_bounded(smem_u32(&s_mfree[rs]), ph_mfree[rs], kTcWaitIter);
+          if (it >= 2) ok = mbar_wait_bounded(smem_u32(&s_mfree[rs]), (ph_mfree >> rs) & 1u, kTcWaitIter);
           if (!ok) atomicExch(&s_abort, 1);
           s_meta[rs].nst = -1;
           mbar_arrive(smem_u32(&s_mfull[rs]));
@@ -282,9 +282,9 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
       for (int j = st; j < m; j += kTcSetupThreads) s_idx[rs][j] = lm_idx[I.lm_off + j];
       if (!lin && it >= 1) {
         // s_co has one buffer: the producers must be done with item it - 1
-        if (st == 0) s_sok = mbar_wait_bounded(smem_u32(&s_sempty[rs ^ 1]), ph_sempty[rs ^ 1], kTcWaitIter) ? 1 : 0;
-        ph_sempty[rs ^ 1] ^= 1u;
-        waited[rs ^ 1] = true;
+        if (st == 0) s_sok = mbar_wait_bounded(smem_u32(&s_sempty[rs ^ 1]), ((ph_sempty >> (rs ^ 1)) & 1u), kTcWaitIter) ? 1 : 0;
+        ph_sempty ^= 1u << (rs ^ 1);
+        waited |= 1u << (rs ^ 1);
         bar_named(3, kTcSetupThreads);
         if (!s_sok) atomicExch(&s_abort, 1);
       }
@@ -316,8 +316,8 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         const int SR = 32 * P;                          // rows per stage
         const int nst = (nrows <= kTcMaxRows) ? (nrows + SR - 1) / SR : 0;
         bool ok = true;
-        if (it >= 2) ok = mbar_wait_bounded(smem_u32(&s_mfree[rs]), ph_mfree[rs], kTcWaitIter);
-        if (it >= 2) ph_mfree[rs] ^= 1u;
+        if (it >= 2) ok = mbar_wait_bounded(smem_u32(&s_mfree[rs]), (ph_mfree >> rs) & 1u, kTcWaitIter);
+        if (it >= 2) ph_mfree ^= 1u << rs;
         if (!ok || nrows > kTcMaxRows) atomicExch(&s_abort, 1);
         TcItem& M = s_meta[rs];
         M.w = w; M.slot = wk.slot; M.jlo = jlo; M.A = A; M.M2 = M2; M.P = P; M.Bs = Bs;
@@ -340,23 +340,23 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   } else if (warp == kTcIssuerWarp) {
     // ============================= issuer =============================
     if (lane == 0) {
-      uint32_t ph_full[kTcStages] = {0, 0, 0, 0}, ph_mfull[2] = {0, 0}, ph_afree[2] = {0, 0};
+      uint32_t ph_full = 0, ph_mfull = 0, ph_afree = 0;   // bit masks (bit = buffer)
       int gs = 0;
       uint32_t ncommit_acc = 0;   // commits to the accumulator barriers
       for (int it = 0;; ++it) {
         const int rs = it & 1;
-        if (!mbar_wait_bounded(smem_u32(&s_mfull[rs]), ph_mfull[rs], kTcWaitIter)) {
+        if (!mbar_wait_bounded(smem_u32(&s_mfull[rs]), (ph_mfull >> rs) & 1u, kTcWaitIter)) {
           atomicExch(&s_abort, 1);
           break;
         }
-        ph_mfull[rs] ^= 1u;
+        ph_mfull ^= 1u << rs;
         const TcItem M = s_meta[rs];
         mbar_arrive(smem_u32(&s_mfree[rs]));
         if (M.nst < 0) break;
         if (M.nst == 0) { atomicExch(&s_abort, 1); break; }   // producers gave up
         if (it >= 2) {   // the epilogue of item it - 2 has read this accumulator set
-          const bool ok = mbar_wait_bounded(smem_u32(&s_afree[rs]), ph_afree[rs], kTcWaitIter);
-          ph_afree[rs] ^= 1u;
+          const bool ok = mbar_wait_bounded(smem_u32(&s_afree[rs]), (ph_afree >> rs) & 1u, kTcWaitIter);
+          ph_afree ^= 1u << rs;
           if (!ok) { atomicExch(&s_abort, 1); break; }
         }
         tc_fence_after();
@@ -367,8 +367,8 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         int rot = 0;
         for (int k = 0; k < M.nst; ++k, ++gs) {
           const int s = gs & (kTcStages - 1);
-          if (!mbar_wait_bounded(smem_u32(&s_full[s]), ph_full[s], kTcWaitIter)) { late = true; break; }
-          ph_full[s] ^= 1u;
+          if (!mbar_wait_bounded(smem_u32(&s_full[s]), (ph_full >> s) & 1u, kTcWaitIter)) { late = true; break; }
+          ph_full ^= 1u << s;
           tc_fence_after();
           const uint32_t ha = smem_u32(sm + s * kTcStageBytes);
           const uint32_t la = ha + (uint32_t)kTcTileBytes;
@@ -399,13 +399,13 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     // ============================ epilogue (warps 21..24) ============================
     const int et = tid - 32 * kTcEpiWarp0;             // 0..127
     const int quad = warp & 3;                         // tensor-memory lane quarter
-    uint32_t ph_mfull[2] = {0, 0}, ph_accf[2] = {0, 0};
+    uint32_t ph_mfull = 0, ph_accf = 0;   // bit masks (bit = buffer)
     for (int it = 0;; ++it) {
       const int rs = it & 1;
       // one thread waits (bounded) and publishes the outcome, so that the four
       // warps take the same path through their named barriers
-      if (et == 0) s_eok = mbar_wait_bounded(smem_u32(&s_mfull[rs]), ph_mfull[rs], kTcWaitIter) ? 1 : 0;
-      ph_mfull[rs] ^= 1u;
+      if (et == 0) s_eok = mbar_wait_bounded(smem_u32(&s_mfull[rs]), (ph_mfull >> rs) & 1u, kTcWaitIter) ? 1 : 0;
+      ph_mfull ^= 1u << rs;
       bar_named(2, 128);
       const bool okm = s_eok != 0;
       const TcItem M = s_meta[rs];
@@ -417,8 +417,8 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         if (et == 0) { atomicExch(&s_abort, 1); mbar_arrive(smem_u32(&s_afree[rs])); }
         continue;
       }
-      if (et == 0) s_eok = mbar_wait_bounded(smem_u32(&s_accf[rs]), ph_accf[rs], kTcWaitIter) ? 1 : 0;
-      ph_accf[rs] ^= 1u;
+      if (et == 0) s_eok = mbar_wait_bounded(smem_u32(&s_accf[rs]), (ph_accf >> rs) & 1u, kTcWaitIter) ? 1 : 0;
+      ph_accf ^= 1u << rs;
       bar_named(2, 128);
       const bool oka = s_eok != 0;
       tc_fence_after();

@@ -89,10 +89,21 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint32_t mbar, uint32_t parity
       : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
   return ok;
 }
-// Bounded wait for the phase of the given parity; returns false when it gave up.
+// Same, letting the thread sleep up to 1 us (it wakes early when the phase
+// completes): a waiting warp then takes no issue slots from the working ones.
+__device__ __forceinline__ uint32_t mbar_try_wait_sleep(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok) : "r"(mbar), "r"(parity), "r"(1000u) : "memory");
+  return ok;
+}
+// Bounded wait for the phase of the given parity (at most max_iter polls of
+// at most 1 us each); returns false when it gave up.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, int max_iter) {
   for (int it = 0; it < max_iter; ++it)
-    if (mbar_try_wait(mbar, parity)) return true;
+    if (mbar_try_wait_sleep(mbar, parity)) return true;
   return false;
 }
 
