@@ -112,48 +112,56 @@ __device__ void apply_house_vec(T* x, int n, const T* v, T b, T* red) {
   __syncthreads();
 }
 
-// In-place lower Cholesky of A (n x n, ld).  Returns false on a non-positive pivot.
+// In-place lower Cholesky of A (n x n, ld).  Returns false on a non-positive
+// pivot (which is replaced by 1).  One barrier per column: every thread takes
+// the pivot of column k, the trailing update (a warp per row) scales the
+// column entries it reads on the fly, and column k itself is scaled after the
+// barrier, while the next update no longer reads it.
 template <typename T>
 __device__ bool cta_cholesky(T* A, int ld, int n, int* flag) {
-  if (threadIdx.x == 0) *flag = 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  bool bad = false;
   __syncthreads();
   for (int k = 0; k < n; ++k) {
-    if (threadIdx.x == 0) {
-      const T d = A[k * ld + k];
-      if (!(d > T(0))) { *flag = 1; A[k * ld + k] = T(1); }
-      else A[k * ld + k] = sqrt(d);
+    T d = A[k * ld + k];
+    if (!(d > T(0))) { bad = true; d = T(1); }
+    const T lkk = sqrt(d), inv = T(1) / lkk;
+    for (int i = k + 1 + warp; i < n; i += nw) {
+      const T lik = A[i * ld + k] * inv;
+      for (int j = k + 1 + lane; j <= i; j += 32) A[i * ld + j] -= lik * (A[j * ld + k] * inv);
     }
     __syncthreads();
-    const T lkk = A[k * ld + k];
-    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[i * ld + k] /= lkk;
-    __syncthreads();
-    const int R = n - k - 1;
-    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
-      const int i = k + 1 + e / R, j = k + 1 + e % R;
-      if (j <= i) A[i * ld + j] -= A[i * ld + k] * A[j * ld + k];
-    }
-    __syncthreads();
+    if (threadIdx.x == 0) A[k * ld + k] = lkk;
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[i * ld + k] *= inv;
   }
-  return *flag == 0;
+  __syncthreads();
+  if (threadIdx.x == 0) *flag = bad ? 1 : 0;
+  return !bad;
 }
 
-// Solve L L^T y = b in place (b overwritten), L lower (n x n, ld).
+// Solve L L^T y = b in place (b overwritten), L lower (n x n, ld).  One warp
+// runs both substitutions (warp barriers only); the block waits for it.
 template <typename T>
 __device__ void cta_chol_solve(const T* L, int ld, int n, T* b) {
-  for (int k = 0; k < n; ++k) {
-    if (threadIdx.x == 0) b[k] /= L[k * ld + k];
-    __syncthreads();
-    const T yk = b[k];
-    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) b[i] -= L[i * ld + k] * yk;
-    __syncthreads();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int k = 0; k < n; ++k) {
+      const T yk = b[k] / L[k * ld + k];
+      __syncwarp();
+      for (int i = k + 1 + lane; i < n; i += 32) b[i] -= L[i * ld + k] * yk;
+      if (lane == 0) b[k] = yk;
+      __syncwarp();
+    }
+    for (int k = n - 1; k >= 0; --k) {
+      const T yk = b[k] / L[k * ld + k];
+      __syncwarp();
+      for (int i = lane; i < k; i += 32) b[i] -= L[k * ld + i] * yk;
+      if (lane == 0) b[k] = yk;
+      __syncwarp();
+    }
   }
-  for (int k = n - 1; k >= 0; --k) {
-    if (threadIdx.x == 0) b[k] /= L[k * ld + k];
-    __syncthreads();
-    const T yk = b[k];
-    for (int i = threadIdx.x; i < k; i += blockDim.x) b[i] -= L[k * ld + i] * yk;
-    __syncthreads();
-  }
+  __syncthreads();
 }
 
 // Apply the stored factor: given residuals (h: M1, cr: p) return the KKT

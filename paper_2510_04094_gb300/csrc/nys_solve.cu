@@ -82,20 +82,21 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   //    fixed.
   for (int e = threadIdx.x; e < (Dg + 1) * ldg; e += blockDim.x) Gs[e] = T(0);
   __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int q = 0; q < I.slot_count; ++q) {
     const double* P = part + slot_off[I.slot_begin + q];
     const int jlo = (int)P[0] < 0 ? 0 : (int)P[0], A = (int)P[1], M2l = A + 2;
-    const int El = M2l * (M2l + 1) / 2;
-    for (int e = threadIdx.x; e < El; e += blockDim.x) {
-      int a = 0, rem = e;
-      while (rem >= M2l - a) { rem -= M2l - a; ++a; }
-      const int bb = a + rem;
-      const int j = (a < A) ? jlo + a : Dg + (a - A);
-      const int l = (bb < A) ? jlo + bb : Dg + (bb - A);
-      if (j > Dg) continue;  // the (r, r) entry is not needed
-      const T v = (T)P[2 + e];
-      Gs[j * ldg + l] += v;
-      if (l <= Dg && l != j) Gs[l * ldg + j] += v;
+    // a warp per packed row a (local columns bb >= a start at a M2l - a (a-1) / 2);
+    // row A + 1 holds only the (r, r) entry, which is not needed
+    for (int a = warp; a <= A; a += nw) {
+      const int j = (a < A) ? jlo + a : Dg;
+      const double* Pa = P + 2 + a * M2l - a * (a - 1) / 2 - a;
+      for (int bb = a + lane; bb < M2l; bb += 32) {
+        const int l = (bb < A) ? jlo + bb : Dg + (bb - A);
+        const T v = (T)Pa[bb];
+        Gs[j * ldg + l] += v;
+        if (l <= Dg && l != j) Gs[l * ldg + j] += v;
+      }
     }
     __syncthreads();
   }
@@ -121,29 +122,57 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     }
     if (threadIdx.x == 0) g[me] = (T)gamma * Gs[m * ldg + m + 1];
     __syncthreads();
-    // 3. H_ww = gamma W G_kk W^T + I, in blocks of 8 rows of Y = W G_kk
-    for (int k0 = 0; k0 < me; k0 += 8) {
-      const int kb = min(8, me - k0);
-      for (int e = threadIdx.x; e < kb * m; e += blockDim.x) {
-        const int kk = e / m, l = e - kk * m;
+    // 3. H_ww = gamma W G_kk W^T + I.  Y = W G_kk (odd row stride ldy) goes to
+    //    the H area and the 8-row block after it when it fits; as G is
+    //    symmetric, H_kl = sum_j W_kj Y_lj, so both products read a row of W
+    //    that is the same for the whole warp (broadcast) and G or Y with unit
+    //    or odd stride.  H is then written over G, which is no longer needed.
+    //    Otherwise (many eigenpairs dropped) in blocks of 8 rows of Y.
+    const T gbb = Gs[m * ldg + m];
+    const int ldy = (m + 1) | 1;
+    if (me * ldy <= M1 * ldh + 8 * m) {
+      T* Ys = Hs;
+      for (int e = threadIdx.x; e < me * m; e += blockDim.x) {
+        const int k = e / m, l = e - k * m;
+        const T* wk = Wt + k * m;
         T s = 0;
-        for (int j = 0; j < m; ++j) s += Wt[(k0 + kk) * m + j] * Gs[j * ldg + l];
-        Yb[kk * m + l] = s;
+        for (int j = 0; j < m; ++j) s += wk[j] * Gs[j * ldg + l];
+        Ys[k * ldy + l] = s;
       }
       __syncthreads();
-      for (int e = threadIdx.x; e < kb * me; e += blockDim.x) {
-        const int kk = e / me, l = e - kk * me;
+      Hs = Gs;
+      for (int e = threadIdx.x; e < me * me; e += blockDim.x) {
+        const int k = e / me, l = e - k * me;
+        const T* wk = Wt + k * m;
+        const T* yl = Ys + l * ldy;
         T s = 0;
-        for (int j = 0; j < m; ++j) s += Yb[kk * m + j] * Wt[l * m + j];
-        Hs[(k0 + kk) * ldh + l] = (T)gamma * s + ((k0 + kk) == l ? T(1) : T(0));
+        for (int j = 0; j < m; ++j) s += wk[j] * yl[j];
+        Hs[k * ldh + l] = (T)gamma * s + (k == l ? T(1) : T(0));
       }
-      __syncthreads();
+    } else {
+      for (int k0 = 0; k0 < me; k0 += 8) {
+        const int kb = min(8, me - k0);
+        for (int e = threadIdx.x; e < kb * m; e += blockDim.x) {
+          const int kk = e / m, l = e - kk * m;
+          T s = 0;
+          for (int j = 0; j < m; ++j) s += Wt[(k0 + kk) * m + j] * Gs[j * ldg + l];
+          Yb[kk * m + l] = s;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < kb * me; e += blockDim.x) {
+          const int kk = e / me, l = e - kk * me;
+          T s = 0;
+          for (int j = 0; j < m; ++j) s += Yb[kk * m + j] * Wt[l * m + j];
+          Hs[(k0 + kk) * ldh + l] = (T)gamma * s + ((k0 + kk) == l ? T(1) : T(0));
+        }
+        __syncthreads();
+      }
     }
     for (int k = threadIdx.x; k < me; k += blockDim.x) {
       Hs[k * ldh + me] = (T)gamma * hb[k];
       Hs[me * ldh + k] = (T)gamma * hb[k];
     }
-    if (threadIdx.x == 0) Hs[me * ldh + me] = (T)gamma * Gs[m * ldg + m];
+    if (threadIdx.x == 0) Hs[me * ldh + me] = (T)gamma * gbb;
   }
   // 4. constraint rows in omega coordinates (FP64): c_1 = [W k(t_1); 1], c_2 = [W k'(t_1); 0]
   //    with k_j(t_1) = exp(-x_j^2), k'_j(t_1) = -2 x_j / sigma exp(-x_j^2), x_j = (t_1 - s_j) / sigma
@@ -155,21 +184,27 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     s_e[1][j] = (-2.0 * x / I.sigma) * e;
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < M1; k += blockDim.x) {
+  for (int k = warp; k < M1; k += nw) {   // a warp per row of W (coalesced)
     double s0 = 0.0, s1 = 0.0;
     if (k < me) {
-      for (int j = 0; j < m; ++j) {
+      for (int j = lane; j < m; j += 32) {
         s0 += W[k * m + j] * s_e[0][j];
         s1 += W[k * m + j] * s_e[1][j];
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
       }
     } else {
       s0 = 1.0;
       s1 = 0.0;
     }
-    s_c[0][k] = s0;
-    s_c[1][k] = s1;
-    cws[(int64_t)b * 2 * M1S + k] = s0;
-    cws[(int64_t)b * 2 * M1S + M1S + k] = s1;
+    if (lane == 0) {
+      s_c[0][k] = s0;
+      s_c[1][k] = s1;
+      cws[(int64_t)b * 2 * M1S + k] = s0;
+      cws[(int64_t)b * 2 * M1S + M1S + k] = s1;
+    }
   }
   __syncthreads();
   // 5. Householder reflectors of C^T (M1 x p)
