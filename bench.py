@@ -28,10 +28,11 @@ sys.path.insert(0, ROOT)
 METRIC = "batched ODE solves/s at n=1e4, m=50"
 UNIT = "solves/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2070 MHz
-# DRAM bytes (read + write) of one k_assemble_tc launch per instance, from the ncu
-# capture summarised in profiles/k_assemble_tc_m0_304.md (428.8 KB + 0.3 KB for 304
-# instances); the kernel keeps its operands on chip, HBM traffic is descriptors only
-TC_DRAM_BYTES_PER_INSTANCE = (428.8e3 + 0.256e3) / 304
+# DRAM bytes (read + write) of one k_assemble_tc launch per instance, from an ncu
+# capture of 304 instances of this workload (dram__bytes_read.sum 297.2 KB +
+# dram__bytes_write.sum 0.5 KB); the kernel keeps its operands on chip, its HBM
+# traffic is work descriptors and landmark indices only
+TC_DRAM_BYTES_PER_INSTANCE = (297.216e3 + 0.512e3) / 304
 
 
 def parse():

@@ -16,7 +16,7 @@ A problem is a plain dict (built by ``nys_inputs``):
                        P(y) = c0 + c1 y + c2 y^2 + c3 y^3   (Newton, see newton.py)
     landmarks (optional) increasing indices into the grid
 
-Readings of the paper taken here (each also listed in the design doc):
+Readings of the paper taken here:
  * eq32 writes sqrt(m)/sqrt(eig) and a sum over a garbled index; the feature map
    used is phi(t) = Lambda^{-1/2} U^T k(t), k_j(t) = K(t, s_j), which satisfies
    phi(s_j)^T phi(s_l) = K(s_j, s_l) exactly.  The sqrt(m) variant equals the

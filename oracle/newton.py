@@ -14,7 +14,7 @@ Eq. 2.2 / Appendix A.5: unknowns (omega, b, lambda_1..lambda_p, y_2..y_n),
     h_1  = omega^T phi(t_1) + b - v_1,  h_2 = omega^T phi'(t_1) - v_2.
 The system F = grad L = 0 (Y_1..Y_{p+3} of Lemma 2) is solved by Newton's method.
 
-Readings (also in DESIGN.md):
+Readings of the paper taken here:
  * Only y_i is an auxiliary unknown; the derivative y^(p-1) inside f is
    omega^T phi^(p-1)(t_i) (as in the worked Problem 15 of Appendix B.2).
  * Start: omega = 0, b = v_1, lambda = 0, y_i = v_1.  Undamped steps.
