@@ -9,7 +9,11 @@ A problem is a plain dict (built by ``nys_inputs``):
     t0, t1   interval
     sigma    RBF width: K(u, v) = exp(-(u - v)^2 / sigma^2)   (Section 3, RBF)
     gamma    regularisation constant
-    v        initial values v_1 = y(t_1), v_2 = y'(t_1)
+    v        initial values v_1 = y(t_1), v_2 = y'(t_1); for bc = 'bvp' the boundary
+             values q_1 = y(t_1), q_n = y(t_n)
+    bc       'ivp' (default): conditions y^(k-1)(t_1) = v_k, collocation rows 2..n
+             'bvp' (p = 2): y(t_1) = q_1, y(t_n) = q_n, collocation rows 2..n-1
+             (Appendix A.4, BVP case)
     kind     'lin'   : y^(p) + sum_k a_k y^(p-k) = c sin(omega t + phi0)
              'table' : y^(p) - sum_k f_k(t) y^(p-k) = r(t), f and r given on the grid
              'nl'    : y^(p) = P(y) - delta y^(p-1) [p = 2] + g cos(omega t),
@@ -24,7 +28,10 @@ Readings of the paper taken here:
  * Derivatives of the features are taken with respect to the evaluation point t
    (the first kernel argument u of the derivative formulas after Eq. 9).
  * Collocation rows are i = 2..n (the Psi matrices of Lemma 1 start at t_2);
-   t_1 enters only through the initial conditions.
+   t_1 enters only through the initial conditions.  For the boundary value case
+   of Appendix A.4 the rows are i = 2..n-1 (its Psi matrices run over
+   t_2..t_{n-1}; the printed r vector ending at r(t_n) is read as ending at
+   r(t_{n-1}), the same rows), and t_1, t_n enter through the two conditions.
  * Eigenpairs with eigenvalue <= tau * max eigenvalue are dropped (tau = 1e-12);
    the paper divides by sqrt(eigenvalue) and says only that they are >= 0.
  * Landmarks "evenly spaced" among the grid points (Section 4.1): index
@@ -135,6 +142,45 @@ def linear_coefficients(prob, t):
 
 
 # --------------------------------------------------------------------------
+# Collocation rows and condition rows (Section 2; Lemma 1; Appendix A.4)
+# --------------------------------------------------------------------------
+def is_bvp(prob):
+    bc = prob.get("bc", "ivp")
+    if bc not in ("ivp", "bvp"):
+        raise ValueError("bc must be 'ivp' or 'bvp'")
+    if bc == "bvp" and prob["p"] != 2:
+        raise ValueError("the boundary value case is second order (Appendix A.4)")
+    return bc == "bvp"
+
+
+def collocation_points(prob, t):
+    """Points of the collocation constraints: t_2..t_n (IVP), t_2..t_{n-1} (BVP)."""
+    return t[1:-1] if is_bvp(prob) else t[1:]
+
+
+def condition_rows(prob, st):
+    """Rows c_k of the conditions C x = v on x = (omega, b), and v.
+
+    IVP (Lemma 1): c_k = [phi^(k-1)(t_1), [k == 1]], v_k = y^(k-1)(t_1).
+    BVP (Appendix A.4): c_1 = [phi(t_1), 1], c_2 = [phi(t_n), 1], v = (q_1, q_n).
+    """
+    p = prob["p"]
+    t, s, W = st["t"], st["s"], st["W"]
+    sigma = prob["sigma"]
+    me = W.shape[0]
+    C = np.zeros((p, me + 1))
+    if is_bvp(prob):
+        C[0, :me] = features(t[:1], s, sigma, W, 0)[0]
+        C[1, :me] = features(t[-1:], s, sigma, W, 0)[0]
+        C[:, me] = 1.0
+    else:
+        for k in range(p):
+            C[k, :me] = features(t[:1], s, sigma, W, k)[0]
+        C[0, me] = 1.0
+    return C, np.asarray(prob["v"][:p], dtype=np.float64)
+
+
+# --------------------------------------------------------------------------
 # Lemma 1: the primal linear system
 # --------------------------------------------------------------------------
 def setup(prob, tau=TAU_DEFAULT):
@@ -149,7 +195,9 @@ def setup(prob, tau=TAU_DEFAULT):
 def lemma1_system(prob, st, gamma=None):
     """Build the (m_eff + 1 + p) square system of Lemma 1 exactly as printed.
 
-    Psi^(l) are the feature matrices on t_2..t_n, the operator matrix is
+    Psi^(l) are the feature matrices on the collocation points (t_2..t_n; for
+    the BVP of Appendix A.4 t_2..t_{n-1}, whose system has the condition
+    columns phi(t_1)^T, phi(t_n)^T and ones in the b row), the operator matrix is
     M = Psi^(p) - f_1 Psi^(p-1) - ... - f_p Psi (rows scaled by f_k(t_i)),
     A = gamma M^T, V = gamma (-f_p)^T, and
 
@@ -162,7 +210,7 @@ def lemma1_system(prob, st, gamma=None):
     gamma = prob["gamma"] if gamma is None else gamma
     t, s, W = st["t"], st["s"], st["W"]
     sigma = prob["sigma"]
-    ti = t[1:]
+    ti = collocation_points(prob, t)
     Psi = [features(ti, s, sigma, W, ell) for ell in range(p + 1)]
     f, r = linear_coefficients(prob, ti)
     M = Psi[p].copy()
@@ -179,15 +227,12 @@ def lemma1_system(prob, st, gamma=None):
     K[:me, me] = -(A @ fp)
     K[me, :me] = (V @ M)[0]
     K[me, me] = -(V @ fp)[0]
-    phi1 = [features(t[:1], s, sigma, W, ell)[0] for ell in range(p)]
-    for k in range(p):
-        K[:me, me + 1 + k] = phi1[k]
-        K[me + 1 + k, :me] = phi1[k]
-    K[me, me + 1] = 1.0
-    K[me + 1, me] = 1.0
+    C, v = condition_rows(prob, st)
+    K[:me + 1, me + 1:] = C.T
+    K[me + 1:, :me + 1] = C
     rhs[:me] = A @ r
     rhs[me] = (V @ r)[0]
-    rhs[me + 1:] = np.asarray(prob["v"][:p], dtype=np.float64)
+    rhs[me + 1:] = v
     return K, rhs
 
 
@@ -238,7 +283,7 @@ def solve_linear_nullspace(prob, tau=TAU_DEFAULT, st=None):
     gamma = prob["gamma"] * (prob["m"] if prob.get("scale_sqrt_m") else 1.0)
     t, s, W = st["t"], st["s"], st["W"]
     sigma = prob["sigma"]
-    ti = t[1:]
+    ti = collocation_points(prob, t)
     f, r = linear_coefficients(prob, ti)
     # row vectors a~_i = [phi^(p) - sum f_k phi^(p-k); -f_p]
     Phi = [features(ti, s, sigma, W, ell) for ell in range(p + 1)]
@@ -250,11 +295,7 @@ def solve_linear_nullspace(prob, tau=TAU_DEFAULT, st=None):
     H = gamma * At.T @ At
     H[:me, :me] += np.eye(me)
     g = gamma * At.T @ r
-    C = np.zeros((p, me + 1))
-    for k in range(p):
-        C[k, :me] = features(t[:1], s, sigma, W, k)[0]
-    C[0, me] = 1.0
-    v = np.asarray(prob["v"][:p], dtype=np.float64)
+    C, v = condition_rows(prob, st)
     Q, R = np.linalg.qr(C.T, mode="complete")
     Y, Z = Q[:, :p], Q[:, p:]
     xp = Y @ np.linalg.solve(R[:p, :p].T, v)
@@ -277,14 +318,15 @@ def evaluate(prob, sol, tq, deriv=0):
 
 
 def objective(prob, sol_like, omega, b):
-    """Primal objective of Eq. 3.1.9: 1/2 |omega|^2 + gamma/2 sum_{i>=2} e_i^2.
+    """Primal objective of Eq. 3.1.9: 1/2 |omega|^2 + gamma/2 sum_i e_i^2 over the
+    collocation rows (i >= 2; i <= n-1 for the BVP).
 
     e_i is the residual of the collocation constraint of Section 3.1 written out
     from its definition (omega^T phi^(p) - omega^T sum f_k phi^(p-k) - f_p b - r).
     """
     p = prob["p"]
     t, s, W = sol_like["t"], sol_like["s"], sol_like["W"]
-    ti = t[1:]
+    ti = collocation_points(prob, t)
     f, r = linear_coefficients(prob, ti)
     sigma = prob["sigma"]
     lhs = features(ti, s, sigma, W, p) @ omega
@@ -297,13 +339,7 @@ def objective(prob, sol_like, omega, b):
 
 
 def constraints(prob, sol_like, omega, b):
-    """Initial-condition residuals h_k = y^(k-1)(t_1) - v_k (Section 3.1)."""
-    p = prob["p"]
-    t, s, W = sol_like["t"], sol_like["s"], sol_like["W"]
-    out = []
-    for k in range(p):
-        val = features(t[:1], s, prob["sigma"], W, k)[0] @ omega
-        if k == 0:
-            val += b
-        out.append(val - prob["v"][k])
-    return np.array(out)
+    """Condition residuals: y^(k-1)(t_1) - v_k (Section 3.1), or for the BVP
+    y(t_1) - q_1 and y(t_n) - q_n (Appendix A.4)."""
+    C, v = condition_rows(prob, sol_like)
+    return C @ np.concatenate([omega, [b]]) - v

@@ -1,0 +1,121 @@
+"""Pins of the oracle's boundary value case (Appendix A.4, BVP: y(t_1) = q_1,
+y(t_n) = q_n, collocation rows 2..n-1)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import core
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_bvp_B7.txt")
+
+
+def _problem(name, q1, qn, n, m, s2, gam):
+    """Problems 11-13 of Appendix B.1 written as y'' = f1 y' + f2 y + r (tabulated).
+
+    The coefficients are singular at t = 0 = t_1, which is not a collocation point;
+    the table holds 0 there."""
+    t = np.linspace(0.0, 1.0, n)
+    ts = np.where(t == 0, 1.0, t)
+    z = t == 0
+    if name == "P11":     # y'' + y'/t + cos t + sin(t)/t = 0, y = cos t
+        f1, f2, r = np.where(z, 0, -1 / ts), np.zeros(n), np.where(z, 0, -np.cos(t) - np.sin(t) / ts)
+        exact = np.cos(t)
+    elif name == "P12":   # y'' + y = 2
+        f1, f2, r = np.zeros(n), -np.ones(n), 2.0 * np.ones(n)
+        exact = 2 - np.cos(t) + (math.cos(1) - 2) / math.sin(1) * np.sin(t)
+    else:                 # y'' + (1-2t)/t y' + (t-1)/t y = 0, y = e^t
+        f1, f2, r = np.where(z, 0, -(1 - 2 * t) / ts), np.where(z, 0, -(t - 1) / ts), np.zeros(n)
+        exact = np.exp(t)
+    prob = dict(p=2, n=n, m=m, t0=0.0, t1=1.0, sigma=math.sqrt(s2), gamma=gam, v=[q1, qn],
+                kind="table", f=[f1, f2], r=r, bc="bvp")
+    return prob, exact
+
+
+def _golden_rows():
+    rows = []
+    for line in open(GOLDEN):
+        if line.startswith("#") or not line.strip():
+            continue
+        f = line.split()
+        rows.append((f[0],) + tuple(float(x) for x in f[1:]))
+    return rows
+
+
+@pytest.mark.parametrize("row", _golden_rows(), ids=lambda r: r[0])
+def test_paper_bvp_table_accuracy(row):
+    """The printed NLS-SVM errors of Problems 11-13 are met.  The paper does not
+    state how it treats the numerically singular landmark kernel (20 landmarks,
+    sigma = 1 on [0, 1]); keeping eigenpairs down to 1e-16 lambda_max (11 of 20)
+    reproduces its figures for P11 and P12 (ours within [1/10, 2] x printed); for
+    P13 ours is ~17x more accurate than printed, so only the upper bound applies."""
+    name, q1, qn, n, m, s2, gam, mae, rmse, linf = row
+    prob, exact = _problem(name, q1, qn, int(n), int(m), s2, gam)
+    sol = core.solve_linear(prob, tau=1e-16)
+    e = np.abs(sol["y"] - exact)
+    for ours, paper in ((e.mean(), mae), (np.sqrt((e ** 2).mean()), rmse), (e.max(), linf)):
+        assert ours <= 2 * paper, (name, ours, paper)
+        if name != "P13":
+            assert ours >= paper / 10, (name, ours, paper)
+
+
+@pytest.mark.parametrize("name", ["P11", "P12", "P13"])
+def test_bvp_conditions_met_and_exact_routes_agree(name):
+    _, q1, qn, n, m, s2, gam = [r for r in _golden_rows() if r[0] == name][0][:7]
+    prob, _ = _problem(name, q1, qn, int(n), int(m), s2, gam)
+    a = core.solve_linear(prob)
+    b = core.solve_linear_nullspace(prob)
+    # y(t_1) = q_1 and y(t_n) = q_n hold to rounding (the grid evaluation sums
+    # large feature weights, so it is looser)
+    assert np.max(np.abs(core.constraints(prob, a, a["omega"], a["b"]))) <= 1e-12
+    y = a["y"]
+    assert abs(y[0] - prob["v"][0]) <= 1e-10 and abs(y[-1] - prob["v"][1]) <= 1e-10
+    assert np.max(np.abs(a["y"] - b["y"])) <= 1e-9 * np.max(np.abs(a["y"]))
+    # the multipliers carry the conditioning of the KKT matrix (~gamma n): two exact
+    # FP64 routes agree to ~1e-4 relative here
+    np.testing.assert_allclose(a["lam"], b["lam"], rtol=1e-3)
+
+
+def _rbf_rows(t, s, sigma):
+    """k, k', k'' of exp(-(t - s)^2 / sigma^2) in t, written out for this test."""
+    d = t[:, None] - s[None, :]
+    k = np.exp(-(d / sigma) ** 2)
+    return k, -2 * d / sigma ** 2 * k, (4 * d ** 2 / sigma ** 4 - 2 / sigma ** 2) * k
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_bvp_solution_is_stationary_on_interior_rows_only(seed):
+    """First-order optimality of Appendix A.4's problem rebuilt from its statement:
+    the gradient of 1/2|w|^2 + gamma/2 sum_{i=2}^{n-1} e_i^2 lies in the span of the
+    two condition rows.  Including row n (or row 1) in the sum breaks it."""
+    g = np.random.default_rng(seed)
+    n, m = 60, 12
+    t = np.linspace(0.0, 2.0, n)
+    f1, f2 = g.uniform(-1, 1, n), g.uniform(-2, 0, n)
+    r = np.sin(3 * t) + g.uniform(-0.1, 0.1, n)
+    prob = dict(p=2, n=n, m=m, t0=0.0, t1=2.0, sigma=0.4, gamma=1e4, v=[0.3, -0.7],
+                kind="table", f=[f1, f2], r=r, bc="bvp")
+    sol = core.solve_linear(prob)
+    W, s, me = sol["W"], sol["s"], sol["m_eff"]
+    k0, k1, k2 = _rbf_rows(t, s, prob["sigma"])
+    P0, P1, P2 = k0 @ W.T, k1 @ W.T, k2 @ W.T
+    x = np.concatenate([sol["omega"], [sol["b"]]])
+
+    def grad(rows):
+        gr = np.zeros(me + 1)
+        gr[:me] = sol["omega"]
+        for i in rows:
+            a = np.concatenate([P2[i] - f1[i] * P1[i] - f2[i] * P0[i], [-f2[i]]])
+            e = a @ x - r[i]
+            gr += prob["gamma"] * e * a
+        return gr
+
+    C = np.vstack([np.concatenate([P0[0], [1.0]]), np.concatenate([P0[-1], [1.0]])])
+    Q, _ = np.linalg.qr(C.T, mode="complete")
+    Z = Q[:, 2:]
+    good = Z.T @ grad(range(1, n - 1))
+    scale = np.abs(prob["gamma"] * P2).max() * 1e-8 + 1e-8
+    assert np.max(np.abs(good)) <= scale
+    for bad_rows in (range(1, n), range(0, n - 1)):
+        assert np.max(np.abs(Z.T @ grad(bad_rows))) > 100 * scale
