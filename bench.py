@@ -388,6 +388,24 @@ def main():
         extra["ragged_4096"] = {"ms_per_step": ms3, "solves_s": len(r3.problems) / (ms3 / 1000.0),
                                 "rows": int(sum(q["n"] - 1 for q in r3.problems))}
         r3.close()
+        # boundary value family (Appendix A.4): 4096 x (n = 1e4, m = 50), mixed, the
+        # library's default refinement for boundary values (two passes); error of a
+        # few instances against the FP64 oracle
+        rb = Batch(ni.bvp_family(4096), precision="mixed")
+        msb = step_ms(rb, rb.run)
+        kb = 3
+        gb = [core.grid(q) for q in rb.problems[:kb]]
+        yb, _ = rb.eval(gb)
+        ybc = yb.cpu().numpy()
+        off, errs_b = 0, []
+        for q, g in zip(rb.problems[:kb], gb):
+            ref = core.solve_linear(q)["y"]
+            errs_b.append(float(np.abs(ybc[off:off + len(g)] - ref).max() / np.abs(ref).max()))
+            off += len(g)
+        extra["bvp_4096"] = {"ms_per_step": msb, "solves_s": 4096 / (msb / 1000.0),
+                             "refine_passes": 2, "rel_err_vs_oracle_max": max(errs_b),
+                             "status_ok": bool((rb.status.cpu().numpy() == 0).all())}
+        rb.close()
         # single instances at the paper's scale (n = 1e4, m = 50): linear FP64 and
         # mixed, nonlinear y' = 1 - y^2 by Newton (FP64)
         single = {}

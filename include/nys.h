@@ -66,8 +66,20 @@ typedef enum {
   NYS_COEF_POLY_NL = 2
 } nys_coef_kind;
 
+/* Conditions of an instance (Section 2: initial or boundary conditions).   */
+typedef enum {
+  /* initial values (Lemma 1): y(t_1) = v[0], y'(t_1) = v[1] (p = 2);
+     collocation rows i = 2..n                                              */
+  NYS_BC_IVP = 0,
+  /* boundary values of a second-order linear ODE (Appendix A.4, BVP case):
+     y(t_1) = v[0], y(t_n) = v[1]; collocation rows i = 2..n-1.  Needs p = 2
+     and a linear kind (TABLE or LIN); nys_grad refuses such contexts.      */
+  NYS_BC_BVP = 1
+} nys_conditions;
+
 /* One ODE instance (host struct).  Grid: t_i = t0 + (i-1)(t1-t0)/(n-1),
-   i = 1..n.  Constraints at t_1: y(t_1) = v[0], y'(t_1) = v[1] (p = 2).     */
+   i = 1..n.  Conditions per bc: by default at t_1, y(t_1) = v[0],
+   y'(t_1) = v[1] (p = 2).                                                   */
 typedef struct {
   int32_t p;                 /* ODE order, 1 or 2                                  */
   int32_t n;                 /* collocation points, 3 <= n <= 2^24                 */
@@ -76,11 +88,13 @@ typedef struct {
   double t0, t1;             /* interval, t1 > t0                                  */
   double sigma;              /* RBF width in exp(-(u-v)^2/sigma^2), > 0            */
   double gamma;              /* regularisation constant, > 0                       */
-  double v[2];               /* initial values                                     */
+  double v[2];               /* initial (or boundary) values, see bc               */
   double c[8];               /* coefficients, layout per kind above                */
   const int32_t* landmarks;  /* host, optional: m increasing 0-based grid indices;
                                 NULL = evenly spaced, index round(j(n-1)/(m-1))    */
   const double* coef_table;  /* host, kind TABLE only: (p+1) x n                   */
+  int32_t bc;                /* nys_conditions (0 = NYS_BC_IVP)                    */
+  int32_t reserved;          /* must be 0                                          */
 } nys_instance;
 
 #define NYS_M_MAX 112
@@ -89,8 +103,9 @@ typedef struct {
   int32_t precision;     /* nys_precision.  MIXED: FP32 assembly and FP32 factor,
                             refined against FP64-accurate residuals.             */
   int32_t refine_steps;  /* MIXED: residual passes after the first solve (0..8;
-                            default 1 when negative: one pass brings every
-                            parity workload to <= 2e-7 of the FP64 solution)   */
+                            default when negative: 1, which brings every initial
+                            value workload to <= 2e-7 of the FP64 solution; 2 if
+                            any instance has boundary values (NYS_BC_BVP))     */
   double eig_tau;        /* drop eigenpairs with lambda <= tau * lambda_max
                             (default 1e-12 when <= 0)                            */
   int32_t scale_sqrt_m;  /* 1: eq32's sqrt(m) feature scale (== gamma * m)      */

@@ -11,6 +11,7 @@ Problem dict fields (see oracle/core.py for their meaning):
       lin : a = [a_1, .., a_p], c, omega, phi0   y^(p) + sum a_k y^(p-k) = c sin(omega t + phi0)
       nl  : P = [c0, c1, c2, c3], delta, g, omega y^(p) = P(y) - delta y^(p-1) + g cos(omega t)
       table: f (p x n), r (n)                    y^(p) - sum f_k y^(p-k) = r
+    bc (optional): 'ivp' (default) or 'bvp' (p = 2: v = [y(t_1), y(t_n)])
 
 The workloads mirror the paper's scales (Appendix B.5: n up to 1e4-5e4,
 m = 20..200) on synthetic coefficient draws, since the paper's sixteen textbook
@@ -23,7 +24,8 @@ import numpy as np
 SEED = 20251004
 GAMMA = 1e10
 
-_KEYS = {"cfg1": 1, "cfg2": 2, "m0": 10, "cfg3": 3, "cfg4": 4, "cfg5": 5, "small": 99, "trunc": 98}
+_KEYS = {"cfg1": 1, "cfg2": 2, "m0": 10, "cfg3": 3, "cfg4": 4, "cfg5": 5, "small": 99, "trunc": 98,
+         "bvp": 11, "small_bvp": 97}
 
 
 def rng(name, sub=0):
@@ -135,6 +137,44 @@ def cfg5(B=64, n_lo=2000, n_hi=10_000, m=50):
             y0, y1 = (float(x) for x in g.standard_normal(2))
             out.append(dict(p=2, n=n, m=m, t0=0.0, t1=T, sigma=T / m, gamma=GAMMA, v=[y0, y1],
                             kind="nl", P=[0.0, -al, 0.0, -be], delta=de, g=ga, omega=om))
+    return out
+
+
+def bvp_family(B, n=10_000, m=50, T=2.0, sigma=0.05, name="bvp", sub=0):
+    """B boundary value problems y'' + a y' + b y = c sin(omega t), y(0) = q_1,
+    y(T) = q_n (Appendix A.4 form), n, m, sigma fixed.
+
+    a ~ U[0,1], b ~ U[-4,-1] (real characteristic roots of opposite sign: every
+    instance is uniquely solvable), c ~ U[-1,1], omega ~ U[0.5,5], q ~ N(0,1).
+    The metric batch rescaled to [0, 2]: the same sigma / landmark spacing and the
+    same kernel band in rows.
+    """
+    g = rng(name, sub)
+    a = g.uniform(0, 1, B)
+    b = g.uniform(-4, -1, B)
+    c = g.uniform(-1, 1, B)
+    w = g.uniform(0.5, 5, B)
+    q = g.standard_normal((B, 2))
+    return [dict(p=2, n=n, m=m, t0=0.0, t1=T, sigma=sigma, gamma=GAMMA, bc="bvp",
+                 v=[float(q[i, 0]), float(q[i, 1])], kind="lin", a=[float(a[i]), float(b[i])],
+                 c=float(c[i]), omega=float(w[i]), phi0=0.0) for i in range(B)]
+
+
+def small_bvp(B=8, sub=0, n_choices=(3, 5, 37, 64, 129, 300), m_choices=(2, 3, 5, 8, 13, 20)):
+    """Small ragged boundary value problems (down to n = 3: one collocation row)."""
+    g = rng("small_bvp", sub)
+    out = []
+    for i in range(B):
+        n = int(g.choice(np.asarray(n_choices)))
+        m = int(min(g.choice(np.asarray(m_choices)), n))
+        T = float(g.uniform(0.5, 3))
+        t0 = float(g.uniform(-1, 1))
+        out.append(dict(p=2, n=n, m=m, t0=t0, t1=t0 + T, sigma=T / m * 1.5,
+                        gamma=float(10 ** g.uniform(4, 10)), bc="bvp",
+                        v=[float(x) for x in g.standard_normal(2)], kind="lin",
+                        a=[float(g.uniform(0, 1)), float(g.uniform(-4, -1))],
+                        c=float(g.uniform(-1, 1)), omega=float(g.uniform(0.5, 5)),
+                        phi0=float(g.uniform(0, 3))))
     return out
 
 

@@ -15,6 +15,7 @@ NYS_EPRECISION, NYS_ESTATE = -8, -9
 NYS_FP64, NYS_MIXED = 0, 1
 NYS_ASM_AUTO, NYS_ASM_SIMT, NYS_ASM_TUNE = 0, 1, 2
 NYS_COEF_TABLE, NYS_COEF_LIN, NYS_COEF_POLY_NL = 0, 1, 2
+NYS_BC_IVP, NYS_BC_BVP = 0, 1
 NYS_M_MAX = 112
 
 
@@ -22,7 +23,8 @@ class nys_instance(C.Structure):
     _fields_ = [("p", C.c_int32), ("n", C.c_int32), ("m", C.c_int32), ("kind", C.c_int32),
                 ("t0", C.c_double), ("t1", C.c_double), ("sigma", C.c_double),
                 ("gamma", C.c_double), ("v", C.c_double * 2), ("c", C.c_double * 8),
-                ("landmarks", C.POINTER(C.c_int32)), ("coef_table", C.POINTER(C.c_double))]
+                ("landmarks", C.POINTER(C.c_int32)), ("coef_table", C.POINTER(C.c_double)),
+                ("bc", C.c_int32), ("reserved", C.c_int32)]
 
 
 class nys_options(C.Structure):

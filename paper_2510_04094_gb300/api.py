@@ -2,8 +2,8 @@
 
 PyTorch provides device memory (torch tensors) and the CUDA stream; every
 computation happens in libnys.so.  Problems are plain dicts (see
-``nys_inputs``): p, n, m, t0, t1, sigma, gamma, v, kind and the
-kind-specific coefficients.
+``nys_inputs``): p, n, m, t0, t1, sigma, gamma, v, kind, the kind-specific
+coefficients and optionally bc ('ivp', the default, or 'bvp').
 """
 import ctypes as C
 
@@ -13,6 +13,7 @@ import torch
 from . import _abi as A
 
 _KIND = {"table": A.NYS_COEF_TABLE, "lin": A.NYS_COEF_LIN, "nl": A.NYS_COEF_POLY_NL}
+_BC = {"ivp": A.NYS_BC_IVP, "bvp": A.NYS_BC_BVP}
 
 # order of the gradient entries of nys_grad (kind "lin")
 THETA = ("a", "b", "c", "omega", "y0", "y0p", "sigma")
@@ -36,6 +37,7 @@ def pack_instances(problems):
         s = arr[b]
         s.p, s.n, s.m = int(q["p"]), int(q["n"]), int(q["m"])
         s.kind = _KIND[q["kind"]]
+        s.bc = _BC[q.get("bc", "ivp")]
         s.t0, s.t1 = float(q["t0"]), float(q["t1"])
         s.sigma, s.gamma = float(q["sigma"]), float(q["gamma"])
         v = list(q["v"]) + [0.0] * (2 - len(q["v"]))

@@ -207,6 +207,11 @@ static int32_t check_instance(const nys_instance& q, int b) {
     return fail(NYS_EINVAL, "instance %d: the delta y' term needs p = 2", b);
   if (q.kind == NYS_COEF_TABLE && q.coef_table == nullptr)
     return fail(NYS_EINVAL, "instance %d: kind TABLE needs coef_table", b);
+  if (q.bc != NYS_BC_IVP && q.bc != NYS_BC_BVP)
+    return fail(NYS_EINVAL, "instance %d: bc must be NYS_BC_IVP or NYS_BC_BVP (got %d)", b, q.bc);
+  if (q.reserved != 0) return fail(NYS_EINVAL, "instance %d: reserved must be 0", b);
+  if (q.bc == NYS_BC_BVP && (q.p != 2 || q.kind == NYS_COEF_POLY_NL))
+    return fail(NYS_EINVAL, "instance %d: boundary values need a second-order linear ODE", b);
   if (q.landmarks) {
     for (int j = 0; j < q.m; ++j) {
       if (q.landmarks[j] < 0 || q.landmarks[j] >= q.n || (j > 0 && q.landmarks[j] <= q.landmarks[j - 1]))
@@ -216,6 +221,12 @@ static int32_t check_instance(const nys_instance& q, int b) {
   bool fin = finite_all(q.v, q.p) && finite_all(q.c, 8);
   if (q.kind == NYS_COEF_TABLE) fin = fin && finite_all(q.coef_table, (q.p + 1) * q.n);
   return fin ? NYS_OK : NYS_ENONFINITE;
+}
+
+// collocation rows of an instance: i = 2..n (initial values) or 2..n-1
+// (boundary values); 0-based row indices 1 .. collocation_rows(q)
+static int collocation_rows(const nys_instance& q) {
+  return q.n - 1 - (q.bc == NYS_BC_BVP ? 1 : 0);
 }
 
 static void default_landmarks(int n, int m, int32_t* out) {
@@ -243,8 +254,8 @@ static int32_t pack(nys_ctx* c, const nys_instance* q, bool first) {
     if (r == NYS_EINVAL) return r;
     if (!first) {
       const nys_instance& o = c->shape[b];
-      if (o.p != s.p || o.n != s.n || o.m != s.m || o.kind != s.kind)
-        return fail(NYS_EINVAL, "nys_update: instance %d changed p, n, m or kind", b);
+      if (o.p != s.p || o.n != s.n || o.m != s.m || o.kind != s.kind || o.bc != s.bc)
+        return fail(NYS_EINVAL, "nys_update: instance %d changed p, n, m, kind or bc", b);
     }
     std::vector<int32_t> lm(s.m);
     if (s.landmarks) std::memcpy(lm.data(), s.landmarks, sizeof(int32_t) * s.m);
@@ -258,6 +269,7 @@ static int32_t pack(nys_ctx* c, const nys_instance* q, bool first) {
     }
     Inst& I = c->h_inst[b];
     I.p = s.p; I.n = s.n; I.m = s.m; I.kind = s.kind;
+    I.bc = s.bc;
     I.lm_off = c->h_lm_off[b];
     I.t0 = s.t0;
     I.h = (s.t1 - s.t0) / (double)(s.n - 1);
@@ -411,7 +423,7 @@ static int64_t asm_layout(nys_ctx* c, int64_t rpi, std::vector<Work>& wl, std::v
   int64_t poff = 0;
   int slot = 0;
   for (int b = 0; b < c->batch; ++b) {
-    const int nrows = c->shape[b].n - 1;
+    const int nrows = collocation_rows(c->shape[b]);
     const int chunks = (int)std::max<int64_t>(1, (nrows + rpi - 1) / rpi);
     const int M2 = c->shape[b].m + 2;
     // linear: [first landmark, count] + packed Gram over m + 2 columns;
@@ -459,7 +471,15 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
     delete c;
     return fail(NYS_EINVAL, "nys_setup: unknown assembly kernel %d", a);
   }
-  if (c->opt.refine_steps < 0) c->opt.refine_steps = 1;
+  // default refinement: one pass (every initial value workload lands at <= 2e-7
+  // of the FP64 solution); two when the batch holds boundary value instances,
+  // whose FP32 factor contracts the error more slowly (one pass leaves up to
+  // ~3e-6 on the boundary value family, two ~1e-8)
+  if (c->opt.refine_steps < 0) {
+    bool any_bvp = false;
+    for (int b = 0; b < batch; ++b) any_bvp = any_bvp || (q[b].bc == NYS_BC_BVP);
+    c->opt.refine_steps = any_bvp ? 2 : 1;
+  }
   if (c->opt.refine_steps > 8) { delete c; return fail(NYS_EINVAL, "nys_setup: refine_steps > 8"); }
   c->fp32 = (c->opt.precision == NYS_MIXED);
   for (int b = 0; b < batch; ++b) {
@@ -503,7 +523,7 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
 
   // row-pass work list: split instances so that there are >= 4 items per SM
   int64_t total_rows = 0;
-  for (int b = 0; b < batch; ++b) total_rows += q[b].n - 1;
+  for (int b = 0; b < batch; ++b) total_rows += collocation_rows(q[b]);
   c->total_rows = total_rows;
   const int64_t target = std::max<int64_t>(batch, 4LL * c->num_sms);
   int64_t rpi = std::max<int64_t>(64, (total_rows + target - 1) / target);
@@ -530,7 +550,7 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   {
     const int64_t rpr = std::max<int64_t>(64, (total_rows + target - 1) / target);
     for (int b = 0; b < batch; ++b) {
-      const int nrows = q[b].n - 1;
+      const int nrows = collocation_rows(q[b]);
       const int chunks = (int)std::max<int64_t>(1, (nrows + rpr - 1) / rpr);
       c->h_inst[b].rslot_begin = slot;
       c->h_inst[b].rslot_count = chunks;
@@ -904,6 +924,8 @@ int32_t nys_grad(nys_ctx* c, void* stream, const double* obs_t, const int64_t* o
                  const double* dl_dy, double* grad_out) {
   if (!c || !obs_t || !obs_off || !dl_dy || !grad_out) return fail(NYS_EINVAL, "nys_grad: NULL argument");
   if (c->any_nl) return fail(NYS_EINVAL, "nys_grad: defined for linear (NYS_COEF_LIN) batches");
+  for (int b = 0; b < c->batch; ++b)
+    if (c->shape[b].bc != NYS_BC_IVP) return fail(NYS_EINVAL, "nys_grad: initial value problems only");
   if (c->fp32) return fail(NYS_ESTATE, "nys_grad: needs a context created with precision NYS_FP64");
   if (!c->solved) return fail(NYS_ESTATE, "nys_grad: no solution yet");
   CK(launch_grad(c->inst.p, c->lset.p, c->W.p, (const double*)c->fac.p, c->facs, c->xs.p, c->zs.p,

@@ -31,7 +31,8 @@ struct Inst {
   int32_t slot_count;  // assembly row-pass partial slots of this instance
   int64_t slot_begin;  // first slot (slots of an instance are contiguous)
   int64_t rslot_begin; // refinement row-pass slots (own work list, larger chunks)
-  int32_t rslot_count, pad0;
+  int32_t rslot_count;
+  int32_t bc;          // nys_conditions: 1 = boundary values y(t_1), y(t_n), rows 2..n-1
   int64_t lm_off;      // landmark grid indices (int32) in lm_idx[]
   int64_t tab_off;     // kind TABLE: (p+1) x n doubles in tab[]; else -1
   int64_t y_off;       // Newton: auxiliary y_i (n-1 doubles) in yaux[]

@@ -97,6 +97,8 @@ extern "C" int32_t nys_solve_noalloc(const nys_instance* q, int32_t batch, doubl
                              "3 <= n <= NYS_NOALLOC_MAX_N");
     if (!(s.t1 > s.t0) || !(s.sigma > 0) || !(s.gamma > 0))
       return err(NYS_EINVAL, "nys_solve_noalloc: need t1 > t0, sigma > 0, gamma > 0");
+    if ((s.bc != NYS_BC_IVP && s.bc != NYS_BC_BVP) || s.reserved != 0 || (s.bc == NYS_BC_BVP && s.p != 2))
+      return err(NYS_EINVAL, "nys_solve_noalloc: bc must be NYS_BC_IVP, or NYS_BC_BVP with p = 2");
     if (s.m > m_max) m_max = s.m;
   }
   void* base = nullptr;
@@ -119,6 +121,7 @@ extern "C" int32_t nys_solve_noalloc(const nys_instance* q, int32_t batch, doubl
     Inst& I = inst[b];
     I = Inst{};
     I.p = s.p; I.n = s.n; I.m = s.m; I.kind = s.kind;
+    I.bc = s.bc;
     I.lm_off = (int64_t)b * NYS_NOALLOC_MAX_M;
     I.tab_off = -1;
     I.t0 = s.t0;
@@ -156,7 +159,7 @@ extern "C" int32_t nys_solve_noalloc(const nys_instance* q, int32_t batch, doubl
     L.w_off = (int64_t)nl * m_max * m_max;
     L.hs = I.hs;
     I.lset = nl++;
-    const int nrows = s.n - 1;
+    const int nrows = s.n - 1 - (s.bc == NYS_BC_BVP ? 1 : 0);   // rows 2..n (2..n-1)
     const int chunks = nrows < 64 * kChunks ? 1 : kChunks;
     const int64_t E = (int64_t)(s.m + 2) * (s.m + 3) / 2 + 2;   // + [first landmark, count]
     I.slot_begin = nwork;

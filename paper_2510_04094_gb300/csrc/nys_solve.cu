@@ -174,14 +174,22 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     }
     if (threadIdx.x == 0) Hs[me * ldh + me] = (T)gamma * gbb;
   }
-  // 4. constraint rows in omega coordinates (FP64): c_1 = [W k(t_1); 1], c_2 = [W k'(t_1); 0]
-  //    with k_j(t_1) = exp(-x_j^2), k'_j(t_1) = -2 x_j / sigma exp(-x_j^2), x_j = (t_1 - s_j) / sigma
+  // 4. condition rows in omega coordinates (FP64): c_1 = [W k(t_1); 1] and
+  //    initial values (Lemma 1): c_2 = [W k'(t_1); 0], k_j(t_1) = exp(-x_j^2),
+  //    k'_j(t_1) = -2 x_j / sigma exp(-x_j^2), x_j = (t_1 - s_j) / sigma;
+  //    boundary values (Appendix A.4): c_2 = [W k(t_n); 1]
   __shared__ double s_e[2][kMMax];
+  const bool bvp = (I.bc == NYS_BC_BVP);
   for (int j = threadIdx.x; j < m; j += blockDim.x) {
     const double x = (double)(0 - lm_idx[I.lm_off + j]) * I.hs;
     const double e = exp(-x * x);
     s_e[0][j] = e;
-    s_e[1][j] = (-2.0 * x / I.sigma) * e;
+    if (bvp) {
+      const double xn = (double)(I.n - 1 - lm_idx[I.lm_off + j]) * I.hs;
+      s_e[1][j] = exp(-xn * xn);
+    } else {
+      s_e[1][j] = (-2.0 * x / I.sigma) * e;
+    }
   }
   __syncthreads();
   for (int k = warp; k < M1; k += nw) {   // a warp per row of W (coalesced)
@@ -197,7 +205,7 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
       }
     } else {
       s0 = 1.0;
-      s1 = 0.0;
+      s1 = bvp ? 1.0 : 0.0;
     }
     if (lane == 0) {
       s_c[0][k] = s0;

@@ -39,9 +39,10 @@ def test_library_exports_every_declared_symbol(abi):
 
 
 def test_struct_layout_matches_header(abi):
-    assert C.sizeof(abi.nys_instance) == 16 + 8 * 4 + 16 + 64 + 16
+    assert C.sizeof(abi.nys_instance) == 16 + 8 * 4 + 16 + 64 + 16 + 8
     assert C.sizeof(abi.nys_options) == 24
     assert abi.nys_instance.t0.offset == 16 and abi.nys_instance.landmarks.offset == 128
+    assert abi.nys_instance.bc.offset == 144 and abi.nys_instance.reserved.offset == 148
 
 
 def _one(**kw):
@@ -53,7 +54,9 @@ def _one(**kw):
 
 @pytest.mark.parametrize("bad", [dict(p=3), dict(n=2), dict(m=1), dict(m=200, n=300),
                                  dict(sigma=0.0), dict(gamma=-1.0), dict(t1=-1.0),
-                                 dict(landmarks=[0, 5, 5] + list(range(6, 23)))])
+                                 dict(landmarks=[0, 5, 5] + list(range(6, 23))),
+                                 dict(bc="bvp", p=1, a=[1.0], v=[0.0]),
+                                 dict(bc="bvp", kind="nl", P=[0.0, 1.0, 0.0, 0.0])])
 def test_invalid_instances_are_rejected_on_the_host(abi, bad):
     from paper_2510_04094_gb300.api import pack_instances
     arr, keep = pack_instances([_one(**bad)])
@@ -61,6 +64,18 @@ def test_invalid_instances_are_rejected_on_the_host(abi, bad):
     ctx = C.c_void_p()
     code = abi.lib().nys_setup(C.byref(ctx), arr, 1, C.byref(opt), None)
     assert code == abi.NYS_EINVAL
+    assert abi.lib().nys_last_error().decode().startswith("instance 0")
+    assert not ctx.value
+
+
+@pytest.mark.parametrize("field,value", [("bc", 2), ("bc", -1), ("reserved", 1)])
+def test_invalid_condition_fields_are_rejected_on_the_host(abi, field, value):
+    from paper_2510_04094_gb300.api import pack_instances
+    arr, keep = pack_instances([_one()])
+    setattr(arr[0], field, value)
+    opt = abi.nys_options()
+    ctx = C.c_void_p()
+    assert abi.lib().nys_setup(C.byref(ctx), arr, 1, C.byref(opt), None) == abi.NYS_EINVAL
     assert abi.lib().nys_last_error().decode().startswith("instance 0")
     assert not ctx.value
 

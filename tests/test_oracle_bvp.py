@@ -1,46 +1,12 @@
 """Pins of the oracle's boundary value case (Appendix A.4, BVP: y(t_1) = q_1,
 y(t_n) = q_n, collocation rows 2..n-1)."""
-import math
-import os
-
 import numpy as np
 import pytest
 
 from oracle import core
 
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_bvp_B7.txt")
-
-
-def _problem(name, q1, qn, n, m, s2, gam):
-    """Problems 11-13 of Appendix B.1 written as y'' = f1 y' + f2 y + r (tabulated).
-
-    The coefficients are singular at t = 0 = t_1, which is not a collocation point;
-    the table holds 0 there."""
-    t = np.linspace(0.0, 1.0, n)
-    ts = np.where(t == 0, 1.0, t)
-    z = t == 0
-    if name == "P11":     # y'' + y'/t + cos t + sin(t)/t = 0, y = cos t
-        f1, f2, r = np.where(z, 0, -1 / ts), np.zeros(n), np.where(z, 0, -np.cos(t) - np.sin(t) / ts)
-        exact = np.cos(t)
-    elif name == "P12":   # y'' + y = 2
-        f1, f2, r = np.zeros(n), -np.ones(n), 2.0 * np.ones(n)
-        exact = 2 - np.cos(t) + (math.cos(1) - 2) / math.sin(1) * np.sin(t)
-    else:                 # y'' + (1-2t)/t y' + (t-1)/t y = 0, y = e^t
-        f1, f2, r = np.where(z, 0, -(1 - 2 * t) / ts), np.where(z, 0, -(t - 1) / ts), np.zeros(n)
-        exact = np.exp(t)
-    prob = dict(p=2, n=n, m=m, t0=0.0, t1=1.0, sigma=math.sqrt(s2), gamma=gam, v=[q1, qn],
-                kind="table", f=[f1, f2], r=r, bc="bvp")
-    return prob, exact
-
-
-def _golden_rows():
-    rows = []
-    for line in open(GOLDEN):
-        if line.startswith("#") or not line.strip():
-            continue
-        f = line.split()
-        rows.append((f[0],) + tuple(float(x) for x in f[1:]))
-    return rows
+from bvp_problems import golden_rows as _golden_rows
+from bvp_problems import problem as _problem
 
 
 @pytest.mark.parametrize("row", _golden_rows(), ids=lambda r: r[0])
@@ -51,7 +17,7 @@ def test_paper_bvp_table_accuracy(row):
     reproduces its figures for P11 and P12 (ours within [1/10, 2] x printed); for
     P13 ours is ~17x more accurate than printed, so only the upper bound applies."""
     name, q1, qn, n, m, s2, gam, mae, rmse, linf = row
-    prob, exact = _problem(name, q1, qn, int(n), int(m), s2, gam)
+    prob, exact = _problem(name, q1, qn, n, m, s2, gam)
     sol = core.solve_linear(prob, tau=1e-16)
     e = np.abs(sol["y"] - exact)
     for ours, paper in ((e.mean(), mae), (np.sqrt((e ** 2).mean()), rmse), (e.max(), linf)):
@@ -62,8 +28,7 @@ def test_paper_bvp_table_accuracy(row):
 
 @pytest.mark.parametrize("name", ["P11", "P12", "P13"])
 def test_bvp_conditions_met_and_exact_routes_agree(name):
-    _, q1, qn, n, m, s2, gam = [r for r in _golden_rows() if r[0] == name][0][:7]
-    prob, _ = _problem(name, q1, qn, int(n), int(m), s2, gam)
+    prob, _ = _problem(*[r for r in _golden_rows() if r[0] == name][0][:7])
     a = core.solve_linear(prob)
     b = core.solve_linear_nullspace(prob)
     # y(t_1) = q_1 and y(t_n) = q_n hold to rounding (the grid evaluation sums

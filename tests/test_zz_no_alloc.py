@@ -25,7 +25,7 @@ def env():
 
 
 def _problems():
-    return ni.m0(6, n=3000, m=50) + ni.small_linear(10) + [ni.cfg1()]
+    return ni.m0(6, n=3000, m=50) + ni.small_linear(10) + [ni.cfg1()] + ni.small_bvp(6, sub=1)
 
 
 def test_noalloc_matches_regular_fp64_path_twice(env):
