@@ -474,7 +474,7 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   // default refinement: one pass (every initial value workload lands at <= 2e-7
   // of the FP64 solution); two when the batch holds boundary value instances,
   // whose FP32 factor contracts the error more slowly (one pass leaves up to
-  // ~3e-6 on the boundary value family, two ~1e-8)
+  // ~3e-6 on the boundary value family, two <= 2e-7)
   if (c->opt.refine_steps < 0) {
     bool any_bvp = false;
     for (int b = 0; b < batch; ++b) any_bvp = any_bvp || (q[b].bc == NYS_BC_BVP);
