@@ -234,8 +234,73 @@ static void default_landmarks(int n, int m, int32_t* out) {
     out[j] = (int32_t)(((int64_t)j * (n - 1) + (m - 1) / 2) / (m - 1));
 }
 
+// Instance fields that an update may change; the landmark-set fields (lset,
+// lm_off) and the work-list fields of h_inst are kept.
+static void fill_inst(nys_ctx* c, const nys_instance& s, Inst& I) {
+  I.t0 = s.t0;
+  I.h = (s.t1 - s.t0) / (double)(s.n - 1);
+  I.sigma = s.sigma;
+  // eq32's sqrt(m) feature scale is the same problem with gamma -> m gamma
+  I.gamma = c->opt.scale_sqrt_m ? s.gamma * s.m : s.gamma;
+  I.v[0] = s.v[0];
+  I.v[1] = (s.p == 2) ? s.v[1] : 0.0;
+  for (int k = 0; k < 8; ++k) I.c[k] = s.c[k];
+  if (s.p == 1 && s.kind == NYS_COEF_LIN) I.c[1] = 0.0;
+  I.hs = I.h / s.sigma;
+  I.th0 = mod2pi(s.c[3] * s.t0 + s.c[4]);
+  I.dth = mod2pi(s.c[3] * I.h);
+  I.rk = row_const(I);
+  I.tab_off = -1;
+  if (s.kind == NYS_COEF_TABLE) {
+    I.tab_off = (int64_t)c->h_tab.size();
+    c->h_tab.insert(c->h_tab.end(), s.coef_table, s.coef_table + (size_t)(s.p + 1) * s.n);
+  }
+}
+
+static int32_t repack_same_sets(nys_ctx* c, const nys_instance* q);
+static int32_t pack_all(nys_ctx* c, const nys_instance* q, bool first);
+
 // Fill h_inst / h_lset / h_stinit / h_tab from the instance array (host only).
-static int32_t pack(nys_ctx* c, const nys_instance* q, bool first) {
+// An update (first = false) keeps p, n, m, kind, bc and the landmarks; when no
+// instance's h / sigma changed either, the landmark sets and their sharing are
+// those of the previous call and are kept as they are (no key map rebuilt).
+static int32_t pack(nys_ctx* c, const nys_instance* q, bool first, bool* same_out = nullptr) {
+  const int B = c->batch;
+  if (same_out) *same_out = false;
+  if (!first) {
+    bool same_sets = ((int)c->h_inst.size() == B);
+    for (int b = 0; b < B && same_sets; ++b) {
+      const nys_instance& s = q[b];
+      const double h = (s.t1 - s.t0) / (double)(s.n - 1);
+      same_sets = (h / s.sigma == c->h_inst[b].hs);
+    }
+    if (same_sets) {
+      if (same_out) *same_out = true;
+      return repack_same_sets(c, q);
+    }
+  }
+  // an update keeps the work-list fields of the descriptors (and all of them
+  // when it fails)
+  std::vector<Inst> keep;
+  if (!first) keep = c->h_inst;
+  int32_t r = pack_all(c, q, first);
+  if (!first) {
+    if (r != NYS_OK) {
+      c->h_inst = keep;
+      return r;
+    }
+    for (int b = 0; b < B; ++b) {
+      c->h_inst[b].slot_begin = keep[b].slot_begin;
+      c->h_inst[b].slot_count = keep[b].slot_count;
+      c->h_inst[b].rslot_begin = keep[b].rslot_begin;
+      c->h_inst[b].rslot_count = keep[b].rslot_count;
+      c->h_inst[b].y_off = keep[b].y_off;
+    }
+  }
+  return r;
+}
+
+static int32_t pack_all(nys_ctx* c, const nys_instance* q, bool first) {
   const int B = c->batch;
   c->h_inst.assign(B, Inst{});
   c->h_stinit.assign(B, NYS_OK);
@@ -271,24 +336,7 @@ static int32_t pack(nys_ctx* c, const nys_instance* q, bool first) {
     I.p = s.p; I.n = s.n; I.m = s.m; I.kind = s.kind;
     I.bc = s.bc;
     I.lm_off = c->h_lm_off[b];
-    I.t0 = s.t0;
-    I.h = (s.t1 - s.t0) / (double)(s.n - 1);
-    I.sigma = s.sigma;
-    // eq32's sqrt(m) feature scale is the same problem with gamma -> m gamma
-    I.gamma = c->opt.scale_sqrt_m ? s.gamma * s.m : s.gamma;
-    I.v[0] = s.v[0];
-    I.v[1] = (s.p == 2) ? s.v[1] : 0.0;
-    for (int k = 0; k < 8; ++k) I.c[k] = s.c[k];
-    if (s.p == 1 && s.kind == NYS_COEF_LIN) I.c[1] = 0.0;
-    I.hs = I.h / s.sigma;
-    I.th0 = mod2pi(s.c[3] * s.t0 + s.c[4]);
-    I.dth = mod2pi(s.c[3] * I.h);
-    I.rk = row_const(I);
-    I.tab_off = -1;
-    if (s.kind == NYS_COEF_TABLE) {
-      I.tab_off = (int64_t)c->h_tab.size();
-      c->h_tab.insert(c->h_tab.end(), s.coef_table, s.coef_table + (size_t)(s.p + 1) * s.n);
-    }
+    fill_inst(c, s, I);
     c->h_stinit[b] = r;
     // landmark-set key: n, m, indices, bits of h/sigma.  Slot b is the set of
     // instance b; only the first instance with a given key is active.
@@ -323,6 +371,37 @@ static int32_t pack(nys_ctx* c, const nys_instance* q, bool first) {
   return NYS_OK;
 }
 
+// nys_update with unchanged landmark sets: validate, refresh the per-instance
+// fields in place.
+static int32_t repack_same_sets(nys_ctx* c, const nys_instance* q) {
+  const int B = c->batch;
+  for (int b = 0; b < B; ++b) {
+    const nys_instance& s = q[b];
+    const nys_instance& o = c->shape[b];
+    if (o.p != s.p || o.n != s.n || o.m != s.m || o.kind != s.kind || o.bc != s.bc)
+      return fail(NYS_EINVAL, "nys_update: instance %d changed p, n, m, kind or bc", b);
+    int32_t dflt[NYS_M_MAX];
+    const int32_t* lm = s.landmarks;
+    if (!lm) {
+      default_landmarks(s.n, s.m, dflt);
+      lm = dflt;
+    }
+    if (std::memcmp(lm, c->h_lm.data() + c->h_lm_off[b], sizeof(int32_t) * s.m) != 0)
+      return fail(NYS_EINVAL, "nys_update: instance %d changed its landmarks", b);
+  }
+  std::vector<int32_t> st(B);
+  for (int b = 0; b < B; ++b) {
+    st[b] = check_instance(q[b], b);
+    if (st[b] == NYS_EINVAL) return st[b];
+  }
+  c->h_tab.clear();
+  for (int b = 0; b < B; ++b) {
+    fill_inst(c, q[b], c->h_inst[b]);
+    c->h_stinit[b] = st[b];
+  }
+  return NYS_OK;
+}
+
 static cudaError_t enqueue_factor(nys_ctx* c, cudaStream_t s) {
   return launch_setup(c->lset.p, c->batch, c->lm.p, c->W.p, c->W32.p, c->lam.p, c->lag.p,
                       c->opt.eig_tau > 0 ? c->opt.eig_tau : 1e-12, c->m_max, s, c->fp32 ? 0 : 1,
@@ -344,15 +423,22 @@ static cudaError_t fork_factor(nys_ctx* c, cudaStream_t s) {
   return e;
 }
 
-static int32_t upload_and_setup(nys_ctx* c, cudaStream_t s, bool factor_now) {
+// upload_lset = false keeps the device landmark-set descriptors, whose m_eff and
+// omode the factor kernel wrote (an update that keeps every landmark set).
+// factor_now runs the factor on the caller's stream before anything else: a row
+// pass needs the final omode of its set (omega-mode sets project each row through
+// W), so descriptors uploaded with the host's initial omode must not meet a row
+// pass that overlaps a forked factor.
+static int32_t upload_and_setup(nys_ctx* c, cudaStream_t s, bool factor_now, bool upload_lset = true) {
   // reuse of the pinned staging buffers: wait for the previous upload
   CK(cudaEventSynchronize(c->staged));
   std::memcpy(c->pin_inst, c->h_inst.data(), sizeof(Inst) * c->batch);
-  std::memcpy(c->pin_lset, c->h_lset.data(), sizeof(Lset) * c->batch);
+  if (upload_lset) std::memcpy(c->pin_lset, c->h_lset.data(), sizeof(Lset) * c->batch);
   std::memcpy(c->pin_st, c->h_stinit.data(), sizeof(int32_t) * c->batch);
 
   CK(cudaMemcpyAsync(c->inst.p, c->pin_inst, sizeof(Inst) * c->batch, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(c->lset.p, c->pin_lset, sizeof(Lset) * c->batch, cudaMemcpyHostToDevice, s));
+  if (upload_lset)
+    CK(cudaMemcpyAsync(c->lset.p, c->pin_lset, sizeof(Lset) * c->batch, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(c->stinit.p, c->pin_st, sizeof(int32_t) * c->batch, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(c->st.p, c->pin_st, sizeof(int32_t) * c->batch, cudaMemcpyHostToDevice, s));
 
@@ -361,7 +447,7 @@ static int32_t upload_and_setup(nys_ctx* c, cudaStream_t s, bool factor_now) {
                        cudaMemcpyHostToDevice, s));
   CK(cudaEventRecord(c->staged, s));
   if (!c->h_tab.empty()) CK(cudaStreamSynchronize(s));  // pageable source
-  c->upload_bytes = (int64_t)(sizeof(Inst) * c->batch + sizeof(Lset) * c->batch +
+  c->upload_bytes = (int64_t)(sizeof(Inst) * c->batch + (upload_lset ? sizeof(Lset) * c->batch : 0) +
                               2 * sizeof(int32_t) * c->batch + sizeof(double) * c->h_tab.size());
   c->factor_stale = true;
   if (factor_now) {
@@ -387,7 +473,7 @@ const char* nys_status_str(int32_t s) {
     case NYS_ENOCONV: return "Newton iteration cap reached";
     case NYS_ENONFINITE: return "non-finite input or result";
     case NYS_ETIMEOUT: return "device wait timed out";
-    case NYS_EPRECISION: return "refinement did not contract";
+    case NYS_EPRECISION: return "landmark kernel too ill-conditioned for the mixed path";
     case NYS_ESTATE: return "call out of order";
     default: return "unknown status";
   }
@@ -653,18 +739,12 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
 
 int32_t nys_update(nys_ctx* c, const nys_instance* q, void* stream) {
   if (!c || !q) return fail(NYS_EINVAL, "nys_update: NULL argument");
-  // keep the work-list fields of the descriptors
-  std::vector<Inst> keep = c->h_inst;
-  int32_t r = pack(c, q, false);
-  if (r != NYS_OK) { c->h_inst = keep; return r; }
-  for (int b = 0; b < c->batch; ++b) {
-    c->h_inst[b].slot_begin = keep[b].slot_begin;
-    c->h_inst[b].slot_count = keep[b].slot_count;
-    c->h_inst[b].rslot_begin = keep[b].rslot_begin;
-    c->h_inst[b].rslot_count = keep[b].rslot_count;
-    c->h_inst[b].y_off = keep[b].y_off;
-  }
-  return upload_and_setup(c, (cudaStream_t)stream, false);
+  bool same_sets = false;
+  int32_t r = pack(c, q, false, &same_sets);
+  if (r != NYS_OK) return r;
+  // same landmark sets: the device descriptors (and the factor's m_eff, omode)
+  // stay valid; otherwise new ones, factored before the next row pass
+  return upload_and_setup(c, (cudaStream_t)stream, !same_sets, !same_sets);
 }
 
 // ---- assembly autotuner ------------------------------------------------------

@@ -153,3 +153,28 @@ def test_update_cannot_switch_conditions(api):
         bt.update(flipped)
     assert e.value.code == A.NYS_EINVAL
     bt.close()
+
+
+def test_update_of_tabulated_coefficients(api):
+    """An update that keeps every landmark set (same grid spacing and sigma) but
+    changes the tabulated right-hand sides and boundary values."""
+    import torch
+    probs = [p for p, _ in paper_problems()]
+    bt = api.Batch(probs, precision="fp64")
+    bt.run()
+    new = [dict(q, r=np.asarray(q["r"]) * 0.5 + 0.25, v=[q["v"][0] - 0.1, q["v"][1] + 0.2]) for q in probs]
+    bt.update(new)
+    bt.run()
+    y, _ = bt.eval([core.grid(q) for q in new])
+    torch.cuda.synchronize()
+    assert (bt.status.cpu().numpy() == 0).all()
+    yc = y.cpu().numpy()
+    off = 0
+    for q in new:
+        ref = core.solve_linear(q)
+        ref2 = core.solve_linear_nullspace(q)
+        scale = np.abs(ref["y"]).max()
+        tol = max(1e-10, 10 * np.abs(ref["y"] - ref2["y"]).max() / scale)
+        assert np.abs(yc[off:off + q["n"]] - ref["y"]).max() <= tol * scale
+        off += q["n"]
+    bt.close()
