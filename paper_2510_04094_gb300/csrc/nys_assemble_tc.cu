@@ -148,16 +148,32 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
       const float hsc = Pm.hsc;                        // h / sigma * sqrt(log2 e)
       const int tmax = min(nrows, kTcMaxRows) - 1;
       const int j8 = lane >> 2, w4 = lane & 3;
+      // Balance: the units of the last 8-slot group of each block (2 P of them;
+      // the group with the -f_p / r columns, whose lanes take several paths) are
+      // the slowest.  Units are listed with those first, and the warps that get a
+      // single unit (when there are more units than warps) take the head of the
+      // list, the others two each from the rest.
+      const int nunits = 2 * P * Gf;
+      const int ndbl = max(0, nunits - kTcProducers);       // warps with two units
+      const int nsgl = kTcProducers - ndbl;
       int u_kind[2], u_t0[2], u_lag[2], u_off[2];
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
-        const int pu = warp + u * kTcProducers;
+        int li = -1;                                     // index in the unit list
+        if (warp < nsgl) li = (u == 0 && warp < nunits) ? warp : -1;
+        else li = nsgl + 2 * (warp - nsgl) + u;
         u_kind[u] = -1;
         u_t0[u] = u_lag[u] = u_off[u] = 0;
-        if (pu < 2 * P * Gf) {
-          const int pg = pu >> 1, qh = pu & 1;        // (block, group), half of the K chunks
-          const int pb = (int)(((float)pg + 0.5f) * invGf);
-          const int g = pg - pb * Gf;
+        if (li >= 0 && li < nunits) {
+          int pb, g, qh;
+          if (li < 2 * P) {                              // last group of block li / 2
+            pb = li >> 1; qh = li & 1; g = Gf - 1;
+          } else {                                       // groups 0 .. Gf - 2
+            const int l2 = li - 2 * P, pg = l2 >> 1;
+            qh = l2 & 1;
+            pb = (int)(((float)pg + 0.5f) / (float)(Gf - 1));
+            g = pg - pb * (Gf - 1);
+          }
           const int j = (g << 3) + j8;               // local column of this lane
           const int idxj = idx[min(jlo + j, m - 1)];
           u_kind[u] = (j < A) ? 0 : (j == A ? 1 : (j == A + 1 ? 2 : 3));
