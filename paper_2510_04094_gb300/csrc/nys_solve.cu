@@ -372,7 +372,6 @@ __device__ __forceinline__ ff ff_norm(ff a) {
 }
 
 constexpr int kRefWarps = kRefThreads / 32;
-constexpr int kRefColsPerWarp = (kM1Max + kRefWarps - 1) / kRefWarps;   // 15
 
 // four CTAs per SM (64 registers): occupancy hides the latency of the
 // float-float chains better than the registers saved would
@@ -390,6 +389,7 @@ k_refine_rows(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   __shared__ int s_idx[kMMax];
   __shared__ float4 s_zj[kM1Max];   // per column: z~ hi, lo, landmark index (bits), -
   __shared__ float2 s_s[kRefRows];  // residuals (float-float)
+  __shared__ float2 s_acc[kM1Max];  // column sums of the item (float-float)
   __shared__ float s_rc[kRefRows * 10];  // per row: A0 A1 A2 w1 r, each as hi/lo
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (;;) {
@@ -421,10 +421,9 @@ k_refine_rows(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     // The sums acc_j = sum_i kappa~_ij s_i cancel almost completely at the
     // solution (the residual is orthogonal to the features up to the
     // regularisation), so they are accumulated in float-float.  Warp w owns
-    // columns j = w, w + 8, ...; its lanes walk the rows.
-    ff acc[kRefColsPerWarp];
-#pragma unroll
-    for (int q = 0; q < kRefColsPerWarp; ++q) acc[q] = {0.f, 0.f};
+    // columns j = w, w + 8, ...; its lanes walk the rows of a chunk, then the
+    // warp adds its lane sums into s_acc[j].
+    for (int j = tid; j <= m; j += kRefThreads) s_acc[j] = make_float2(0.f, 0.f);
     __syncthreads();
     for (int base = wk.r0; base < wk.r1 && !skip; base += kRefRows) {
       const int rows = min(kRefRows, wk.r1 - base);
@@ -455,12 +454,22 @@ k_refine_rows(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
           const float* rc = s_rc + r * 10;
           ff sp = {0.f, 0.f};   // sum of kappa~ z~ (subtracted at the end)
           if (folded) {
+            // two interleaved accumulators: independent dependency chains
             const int iK = i + K + kRefPad;
-            for (int j = jlo; j < jhi; ++j) {
-              const float4 zj = s_zj[j];
-              const float2 kv = kk[iK - __float_as_int(zj.z)];
-              ff_acc_mul(sp, ff{kv.x, kv.y}, ff{zj.x, zj.y});
+            ff sp1 = {0.f, 0.f};
+            int j = jlo;
+            for (; j + 1 < jhi; j += 2) {
+              const float4 z0 = s_zj[j], z1 = s_zj[j + 1];
+              const float2 k0 = kk[iK - __float_as_int(z0.z)], k1 = kk[iK - __float_as_int(z1.z)];
+              ff_acc_mul(sp, ff{k0.x, k0.y}, ff{z0.x, z0.y});
+              ff_acc_mul(sp1, ff{k1.x, k1.y}, ff{z1.x, z1.y});
             }
+            if (j < jhi) {
+              const float4 z0 = s_zj[j];
+              const float2 k0 = kk[iK - __float_as_int(z0.z)];
+              ff_acc_mul(sp, ff{k0.x, k0.y}, ff{z0.x, z0.y});
+            }
+            sp = ff_add(ff_norm(sp), ff_norm(sp1));
           } else {
             const ff A0 = {rc[0], rc[1]}, A1 = {rc[2], rc[3]}, A2 = {rc[4], rc[5]};
             for (int j = jlo; j < jhi; ++j) {
@@ -476,50 +485,58 @@ k_refine_rows(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         }
       }
       __syncthreads();
-      // acc_j += kappa~_ij s_i: lanes over rows (conflict-free table reads)
-#pragma unroll
-      for (int q = 0; q < kRefColsPerWarp; ++q) {
-        const int j = warp + q * kRefWarps;
+      // acc_j += kappa~_ij s_i: lanes over rows (conflict-free table reads), one
+      // column at a time (a compact loop: the column count varies per chunk)
+#pragma unroll 1
+      for (int j = warp; j <= m; j += kRefWarps) {
+        int rlo = 0, rhi = rows, toff = 0, cj = 0;
         if (j < m) {
           // rows within lag K of landmark j: table index r + toff in the table
-          const int cj = s_idx[j];
-          const int rlo = max(0, cj - K - base), rhi = min(rows, cj + K + 1 - base);
-          if (folded) {
-            const int toff = base - cj + K + kRefPad;
-            for (int r = rlo + lane; r < rhi; r += 32) {
-              const float2 kv = kk[r + toff], sv = s_s[r];
-              ff_acc_mul(acc[q], ff{kv.x, kv.y}, ff{sv.x, sv.y});
-            }
-          } else {
-            for (int r = rlo + lane; r < rhi; r += 32) {
-              const float* rc = s_rc + r * 10;
-              const ff kv = kappa_lag(T, K, base + r - cj, ff{rc[0], rc[1]}, ff{rc[2], rc[3]},
-                                      ff{rc[4], rc[5]});
-              const float2 sv = s_s[r];
-              ff_acc_mul(acc[q], kv, ff{sv.x, sv.y});
-            }
-          }
-        } else if (j == m) {   // the b column: every row
+          cj = s_idx[j];
+          rlo = max(0, cj - K - base);
+          rhi = min(rows, cj + K + 1 - base);
+          toff = base - cj + K + kRefPad;
+        }
+        if (rlo >= rhi) continue;                        // warp-uniform
+        ff a = {0.f, 0.f};
+        if (j == m) {          // the b column: every row
           for (int r = lane; r < rows; r += 32) {
             const float* rc = s_rc + r * 10;
             const float2 sv = s_s[r];
-            ff_acc_mul(acc[q], ff{rc[6], rc[7]}, ff{sv.x, sv.y});
+            ff_acc_mul(a, ff{rc[6], rc[7]}, ff{sv.x, sv.y});
           }
+        } else if (folded) {
+          for (int r = rlo + lane; r < rhi; r += 32) {
+            const float2 kv = kk[r + toff], sv = s_s[r];
+            ff_acc_mul(a, ff{kv.x, kv.y}, ff{sv.x, sv.y});
+          }
+        } else {
+          for (int r = rlo + lane; r < rhi; r += 32) {
+            const float* rc = s_rc + r * 10;
+            const ff kv = kappa_lag(T, K, base + r - cj, ff{rc[0], rc[1]}, ff{rc[2], rc[3]},
+                                    ff{rc[4], rc[5]});
+            const float2 sv = s_s[r];
+            ff_acc_mul(a, kv, ff{sv.x, sv.y});
+          }
+        }
+        a = ff_norm(a);
+        for (int o = 16; o > 0; o >>= 1) {
+          const ff bb = {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+          a = ff_add(a, bb);
+        }
+        if (lane == 0) {                                 // column j belongs to this warp
+          const float2 cur = s_acc[j];
+          const ff t = ff_add(ff{cur.x, cur.y}, a);
+          s_acc[j] = make_float2(t.hi, t.lo);
         }
       }
       __syncthreads();
     }
-    // reduce over lanes (float-float), write the partial (M1 doubles)
+    // write the partial (M1 doubles)
     double* out = part + slot_off[wk.slot];
-#pragma unroll
-    for (int q = 0; q < kRefColsPerWarp; ++q) {
-      const int j = warp + q * kRefWarps;
-      ff a = ff_norm(acc[q]);
-      for (int o = 16; o > 0; o >>= 1) {
-        const ff b = {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
-        a = ff_add(a, b);
-      }
-      if (lane == 0 && j <= m) out[j] = skip ? 0.0 : (double)a.hi + (double)a.lo;
+    for (int j = tid; j <= m; j += kRefThreads) {
+      const float2 a = s_acc[j];
+      out[j] = skip ? 0.0 : (double)a.x + (double)a.y;
     }
     __syncthreads();
   }
