@@ -187,6 +187,15 @@ def oracle_rate(problems, seconds):
     return k / dt, k, dt
 
 
+def workload_config(args, ws):
+    """The workload both arms report (the reference arm times the oracle on a
+    bounded sample of this same batch)."""
+    return {"workload": "linear 2nd-order ODE batch y''+ay'+by=c sin(wt), n=%d, m=%d, "
+                        "sigma=0.5, gamma=1e10, %s" % (args.n, args.m, args.precision),
+            "global_batch": ws * args.batch, "seq_len": args.n, "parallelism": "dp%d" % ws,
+            "l2": "flushed between steps (256 MB write)"}
+
+
 def run_reference(args, rank, ws):
     import nys_inputs as ni
     if rank != 0:
@@ -206,9 +215,7 @@ def run_reference(args, rank, ws):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "linear 2nd-order ODE batch, n=%d, m=%d, sigma=0.5, gamma=1e10"
-                       % (args.n, args.m), "global_batch": args.batch, "seq_len": args.n,
-                       "parallelism": "cpu"},
+            "config": workload_config(args, args.gpus),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                              "sample": "%d instances of the workload, %.1f s" % (tot_k, tot_t)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -435,10 +442,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
             "data": "synthetic",
-            "config": {"workload": "linear 2nd-order ODE batch y''+ay'+by=c sin(wt), n=%d, m=%d, "
-                                   "sigma=0.5, gamma=1e10, %s" % (args.n, args.m, args.precision),
-                       "global_batch": ws * B, "seq_len": args.n, "parallelism": "dp%d" % ws,
-                       "l2": "flushed between steps (256 MB write)"},
+            "config": workload_config(args, ws),
             "e2e": {"value": ws * B / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": {"bound": "alu", "kernel": "k_assemble_tc" if args.precision == "mixed"
