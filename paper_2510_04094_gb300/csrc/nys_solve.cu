@@ -131,23 +131,39 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     const T gbb = Gs[m * ldg + m];
     const int ldy = (m + 1) | 1;
     if (me * ldy <= M1 * ldh + 8 * m) {
+      // each thread: rows k, k + 1 of one column (two independent sums per load)
       T* Ys = Hs;
-      for (int e = threadIdx.x; e < me * m; e += blockDim.x) {
-        const int k = e / m, l = e - k * m;
-        const T* wk = Wt + k * m;
-        T s = 0;
-        for (int j = 0; j < m; ++j) s += wk[j] * Gs[j * ldg + l];
-        Ys[k * ldy + l] = s;
+      const int kp = (me + 1) >> 1;
+      for (int e = threadIdx.x; e < kp * m; e += blockDim.x) {
+        const int k = 2 * (e / m), l = e - (e / m) * m;
+        const bool two = k + 1 < me;
+        const T* w0 = Wt + k * m;
+        const T* w1 = two ? w0 + m : w0;
+        T s0 = 0, s1 = 0;
+        for (int j = 0; j < m; ++j) {
+          const T g = Gs[j * ldg + l];
+          s0 += w0[j] * g;
+          s1 += w1[j] * g;
+        }
+        Ys[k * ldy + l] = s0;
+        if (two) Ys[(k + 1) * ldy + l] = s1;
       }
       __syncthreads();
       Hs = Gs;
-      for (int e = threadIdx.x; e < me * me; e += blockDim.x) {
-        const int k = e / me, l = e - k * me;
-        const T* wk = Wt + k * m;
+      for (int e = threadIdx.x; e < kp * me; e += blockDim.x) {
+        const int k = 2 * (e / me), l = e - (e / me) * me;
+        const bool two = k + 1 < me;
+        const T* w0 = Wt + k * m;
+        const T* w1 = two ? w0 + m : w0;
         const T* yl = Ys + l * ldy;
-        T s = 0;
-        for (int j = 0; j < m; ++j) s += wk[j] * yl[j];
-        Hs[k * ldh + l] = (T)gamma * s + (k == l ? T(1) : T(0));
+        T s0 = 0, s1 = 0;
+        for (int j = 0; j < m; ++j) {
+          const T y = yl[j];
+          s0 += w0[j] * y;
+          s1 += w1[j] * y;
+        }
+        Hs[k * ldh + l] = (T)gamma * s0 + (k == l ? T(1) : T(0));
+        if (two) Hs[(k + 1) * ldh + l] = (T)gamma * s1 + (k + 1 == l ? T(1) : T(0));
       }
     } else {
       for (int k0 = 0; k0 < me; k0 += 8) {
