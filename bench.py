@@ -29,10 +29,10 @@ METRIC = "batched ODE solves/s at n=1e4, m=50"
 UNIT = "solves/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2070 MHz
 # DRAM bytes (read + write) of one k_assemble_tc launch per instance, from an ncu
-# capture of 304 instances of this workload (dram__bytes_read.sum 297.2 KB +
-# dram__bytes_write.sum 0.5 KB); the kernel keeps its operands on chip, its HBM
+# capture of 304 instances of this workload (dram__bytes_read.sum 285.4 KB +
+# dram__bytes_write.sum 0.3 KB); the kernel keeps its operands on chip, its HBM
 # traffic is work descriptors and landmark indices only
-TC_DRAM_BYTES_PER_INSTANCE = (297.216e3 + 0.512e3) / 304
+TC_DRAM_BYTES_PER_INSTANCE = (285.44e3 + 0.256e3) / 304
 
 
 def parse():
