@@ -71,9 +71,10 @@ typedef enum {
   /* initial values (Lemma 1): y(t_1) = v[0], y'(t_1) = v[1] (p = 2);
      collocation rows i = 2..n                                              */
   NYS_BC_IVP = 0,
-  /* boundary values of a second-order linear ODE (Appendix A.4, BVP case):
-     y(t_1) = v[0], y(t_n) = v[1]; collocation rows i = 2..n-1.  Needs p = 2
-     and a linear kind (TABLE or LIN); nys_grad refuses such contexts.      */
+  /* boundary values of a second-order ODE (Appendix A.4, BVP case; for the
+     nonlinear kind in the Lagrangian of its Problem 15 example):
+     y(t_1) = v[0], y(t_n) = v[1]; collocation rows i = 2..n-1.  Needs p = 2;
+     nys_grad refuses such contexts.                                         */
   NYS_BC_BVP = 1
 } nys_conditions;
 

@@ -13,6 +13,9 @@ Eq. 2.2 / Appendix A.5: unknowns (omega, b, lambda_1..lambda_p, y_2..y_n),
     xi_i = y_i - omega^T phi(t_i) - b
     h_1  = omega^T phi(t_1) + b - v_1,  h_2 = omega^T phi'(t_1) - v_2.
 The system F = grad L = 0 (Y_1..Y_{p+3} of Lemma 2) is solved by Newton's method.
+Boundary values (bc = 'bvp', p = 2; the conditions of Appendix A.4 in the
+Lagrangian of its Problem 15 example): rows i = 2..n-1 and
+    h_1 = omega^T phi(t_1) + b - q_1,  h_2 = omega^T phi(t_n) + b - q_n.
 
 Readings of the paper taken here:
  * Only y_i is an auxiliary unknown; the derivative y^(p-1) inside f is
@@ -59,17 +62,14 @@ class Pieces:
         st = self.st
         t, s, W = st["t"], st["s"], st["W"]
         sg = prob["sigma"]
-        self.ti = t[1:]
+        self.ti = core.collocation_points(prob, t)
         self.Phi = core.features(self.ti, s, sg, W, 0)
         Pp = core.features(self.ti, s, sg, W, p)
         if p == 2:
             Pp = Pp + prob.get("delta", 0.0) * core.features(self.ti, s, sg, W, 1)
         self.Q = Pp                           # d e_i / d omega
-        self.C = np.zeros((p, W.shape[0] + 1))  # constraint rows on (omega, b)
-        for k in range(p):
-            self.C[k, :W.shape[0]] = core.features(t[:1], s, sg, W, k)[0]
-        self.C[0, W.shape[0]] = 1.0
-        self.v = np.asarray(prob["v"][:p], dtype=np.float64)
+        # condition rows on (omega, b) and their values
+        self.C, self.v = core.condition_rows(prob, st)
         self.rho = forcing(prob, self.ti)
         self.me = W.shape[0]
         self.p = p
@@ -103,7 +103,7 @@ class Pieces:
         g = self.gamma
         me = self.me
         Y1 = om + g * self.Q.T @ e - g * self.Phi.T @ xi + self.C[:, :me].T @ lam
-        Y2 = -g * xi.sum() + lam[0]
+        Y2 = -g * xi.sum() + self.C[:, me] @ lam
         Yy = -g * e * dP + g * xi
         return np.concatenate([Y1, [Y2], h, Yy])
 
@@ -124,10 +124,8 @@ class Pieces:
         Jm[:me, me] = g * self.Phi.sum(axis=0)
         Jm[me, :me] = Jm[:me, me]
         Jm[me, me] = g * n1
-        Jm[:me, me + 1:me + 1 + p] = self.C[:, :me].T
-        Jm[me + 1:me + 1 + p, :me] = self.C[:, :me]
-        Jm[me, me + 1] = 1.0
-        Jm[me + 1, me] = 1.0
+        Jm[:me + 1, me + 1:me + 1 + p] = self.C.T
+        Jm[me + 1:me + 1 + p, :me + 1] = self.C
         oy = me + 1 + p
         Jwy = -g * dP[None, :] * self.Q.T - g * self.Phi.T   # d Y1 / d y
         Jm[:me, oy:] = Jwy

@@ -210,8 +210,8 @@ static int32_t check_instance(const nys_instance& q, int b) {
   if (q.bc != NYS_BC_IVP && q.bc != NYS_BC_BVP)
     return fail(NYS_EINVAL, "instance %d: bc must be NYS_BC_IVP or NYS_BC_BVP (got %d)", b, q.bc);
   if (q.reserved != 0) return fail(NYS_EINVAL, "instance %d: reserved must be 0", b);
-  if (q.bc == NYS_BC_BVP && (q.p != 2 || q.kind == NYS_COEF_POLY_NL))
-    return fail(NYS_EINVAL, "instance %d: boundary values need a second-order linear ODE", b);
+  if (q.bc == NYS_BC_BVP && q.p != 2)
+    return fail(NYS_EINVAL, "instance %d: boundary values need a second-order ODE", b);
   if (q.landmarks) {
     for (int j = 0; j < q.m; ++j) {
       if (q.landmarks[j] < 0 || q.landmarks[j] >= q.n || (j > 0 && q.landmarks[j] <= q.landmarks[j - 1]))

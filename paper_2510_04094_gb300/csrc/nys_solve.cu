@@ -711,13 +711,21 @@ k_newton_step(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     }
     __syncthreads();
   }
-  // 2. constraint rows in omega coordinates, grad_x L, |F|
+  // 2. condition rows in omega coordinates (initial values: [W k(t_1); 1],
+  //    [W k'(t_1); 0]; boundary values, Appendix A.4: [W k(t_1); 1], [W k(t_n); 1]),
+  //    grad_x L, |F|
   __shared__ double s_e[2][kMMax];
+  const bool bvp = (I.bc == NYS_BC_BVP);
   for (int j = threadIdx.x; j < m; j += blockDim.x) {
     const double x = (double)(0 - lm_idx[I.lm_off + j]) * I.hs;
     const double e = exp(-x * x);
     s_e[0][j] = e;
-    s_e[1][j] = (-2.0 * x / I.sigma) * e;
+    if (bvp) {
+      const double xn = (double)(I.n - 1 - lm_idx[I.lm_off + j]) * I.hs;
+      s_e[1][j] = exp(-xn * xn);
+    } else {
+      s_e[1][j] = (-2.0 * x / I.sigma) * e;
+    }
   }
   __syncthreads();
   for (int k = threadIdx.x; k < M1; k += blockDim.x) {
@@ -729,6 +737,7 @@ k_newton_step(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
       }
     } else {
       s0 = 1.0;
+      s1 = bvp ? 1.0 : 0.0;
     }
     s_c[0][k] = s0;
     s_c[1][k] = s1;
@@ -796,7 +805,7 @@ k_newton_step(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     }
     for (int k = threadIdx.x; k < me; k += blockDim.x)
       g[k] = -(xb[k] + Gs[k * ldg + D + 1] + s_c[0][k] * lam0 + s_c[1][k] * lam1);
-    if (threadIdx.x == 0) g[me] = -(Gs[D * ldg + D + 1] + lam0);
+    if (threadIdx.x == 0) g[me] = -(Gs[D * ldg + D + 1] + s_c[0][me] * lam0 + s_c[1][me] * lam1);
     __syncthreads();
   } else {
     for (int k = threadIdx.x; k < me; k += blockDim.x) {
@@ -808,7 +817,7 @@ k_newton_step(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
       hb[k] = s1;
       g[k] = -(xb[k] + s2 + s_c[0][k] * lam0 + s_c[1][k] * lam1);
     }
-    if (threadIdx.x == 0) g[me] = -(Gs[m * ldg + m + 1] + lam0);
+    if (threadIdx.x == 0) g[me] = -(Gs[m * ldg + m + 1] + s_c[0][me] * lam0 + s_c[1][me] * lam1);
     __syncthreads();
     for (int k0 = 0; k0 < me; k0 += 8) {
       const int kb = min(8, me - k0);

@@ -55,8 +55,7 @@ def _one(**kw):
 @pytest.mark.parametrize("bad", [dict(p=3), dict(n=2), dict(m=1), dict(m=200, n=300),
                                  dict(sigma=0.0), dict(gamma=-1.0), dict(t1=-1.0),
                                  dict(landmarks=[0, 5, 5] + list(range(6, 23))),
-                                 dict(bc="bvp", p=1, a=[1.0], v=[0.0]),
-                                 dict(bc="bvp", kind="nl", P=[0.0, 1.0, 0.0, 0.0])])
+                                 dict(bc="bvp", p=1, a=[1.0], v=[0.0])])
 def test_invalid_instances_are_rejected_on_the_host(abi, bad):
     from paper_2510_04094_gb300.api import pack_instances
     arr, keep = pack_instances([_one(**bad)])

@@ -178,3 +178,59 @@ def test_update_of_tabulated_coefficients(api):
         assert np.abs(yc[off:off + q["n"]] - ref["y"]).max() <= tol * scale
         off += q["n"]
     bt.close()
+
+
+# ---- nonlinear boundary value problems (nys_newton) --------------------------
+def _nl_bvp(P, q, n=200, m=20, sigma=0.3, gamma=1e10, T=1.0, delta=0.0, g=0.0, w=0.0):
+    return dict(p=2, n=n, m=m, t0=0.0, t1=T, sigma=sigma, gamma=gamma, v=list(q), kind="nl",
+                P=list(P), delta=delta, g=g, omega=w, bc="bvp")
+
+
+def _newton_compare(api, probs, max_iter=50, tol=1e-10, ytol=1e-10):
+    """Same iteration counts and statuses as the oracle's Newton; fitted values and
+    auxiliary unknowns (rows 2..n-1 for boundary values) to ytol."""
+    import torch
+    from oracle import newton
+    bt = api.Batch(probs, precision="fp64")
+    x, st, iters, yaux = bt.newton(max_iter=max_iter, tol=tol, want_y=True)
+    grids = [core.grid(q) for q in probs]
+    y, _ = bt.eval(grids)
+    torch.cuda.synchronize()
+    st, iters, y, yaux = st.cpu().numpy(), iters.cpu().numpy(), y.cpu().numpy(), yaux.cpu().numpy()
+    bt.close()
+    off = offy = 0
+    for k, q in enumerate(probs):
+        ref = newton.solve(q, tol=tol, max_iter=max_iter)
+        n = q["n"]
+        assert iters[k] == ref["iters"], (k, iters[k], ref["iters"])
+        assert (st[k] == 0) == ref["converged"], (k, st[k])
+        if ref["converged"]:
+            ny = len(ref["y_aux"])
+            err = np.abs(y[off:off + n] - ref["y"]).max() / np.abs(ref["y"]).max()
+            erry = np.abs(yaux[offy:offy + ny] - ref["y_aux"]).max() / np.abs(ref["y_aux"]).max()
+            assert err <= ytol and erry <= 10 * ytol, (k, err, erry)
+        off += n
+        offy += n - 1   # the device keeps n - 1 auxiliary unknowns per instance
+
+
+def test_nonlinear_bvps_with_closed_forms(api):
+    """y'' = 2 y^3 (y = 1/(1+t)) and y'' = y^2 (y = 6/(1+t)^2) on [0, 1]."""
+    probs = [_nl_bvp([0.0, 0.0, 0.0, 2.0], (1.0, 0.5)), _nl_bvp([0.0, 0.0, 1.0, 0.0], (6.0, 1.5)),
+             _nl_bvp([0.0, 0.0, 0.0, 2.0], (1.0, 0.5), n=2000, m=40, sigma=0.05)]
+    _newton_compare(api, probs)
+
+
+def test_nonlinear_bvp_and_ivp_instances_in_one_batch(api):
+    """Duffing-type boundary value problems on [0, 2] beside initial value problems
+    of the same kind (each with its own rows and conditions)."""
+    rng = np.random.default_rng(5)
+    probs = []
+    for k in range(6):
+        a, b = rng.uniform(0.2, 1.0), rng.uniform(0.5, 2.0)
+        q = _nl_bvp([0.0, -a, 0.0, -b], tuple(rng.uniform(-0.5, 0.5, 2)), n=int(rng.integers(80, 400)),
+                    m=int(rng.integers(8, 24)), T=2.0, delta=0.3, g=0.5, w=1.2, gamma=1e8)
+        q["sigma"] = q["t1"] / q["m"] * 1.3
+        if k % 2:
+            q["bc"] = "ivp"
+        probs.append(q)
+    _newton_compare(api, probs)

@@ -84,3 +84,34 @@ def test_bvp_solution_is_stationary_on_interior_rows_only(seed):
     assert np.max(np.abs(good)) <= scale
     for bad_rows in (range(1, n), range(0, n - 1)):
         assert np.max(np.abs(Z.T @ grad(bad_rows))) > 100 * scale
+
+
+# ---- nonlinear boundary value problems (Newton, Lemma 2 with the conditions of
+# Appendix A.4) ----------------------------------------------------------------
+NL_BVP = [
+    # y'' = 2 y^3, y(0) = 1, y(1) = 1/2: y = 1/(1+t)
+    ("cubic", [0.0, 0.0, 0.0, 2.0], (1.0, 0.5), lambda t: 1 / (1 + t), 1e-6),
+    # y'' = y^2, y(0) = 6, y(1) = 3/2: y = 6/(1+t)^2
+    ("square", [0.0, 0.0, 1.0, 0.0], (6.0, 1.5), lambda t: 6 / (1 + t) ** 2, 2e-5),
+]
+
+
+def nl_bvp_problem(P, q, n=200, m=20, sigma=0.3, gamma=1e10):
+    return dict(p=2, n=n, m=m, t0=0.0, t1=1.0, sigma=sigma, gamma=gamma, v=list(q), kind="nl",
+                P=list(P), delta=0.0, g=0.0, omega=0.0, bc="bvp")
+
+
+@pytest.mark.parametrize("case", NL_BVP, ids=lambda c: c[0])
+def test_nonlinear_bvp_matches_closed_form(case):
+    """Newton on Lemma 2's Lagrangian with boundary conditions reaches the closed-form
+    solution of a polynomial nonlinear BVP; dense and y-eliminated steps agree."""
+    from oracle import newton
+    name, P, q, exact, tol = case
+    prob = nl_bvp_problem(P, q)
+    dense = newton.solve(prob, dense=True)
+    red = newton.solve(prob, dense=False)
+    assert dense["converged"] and red["converged"] and dense["iters"] == red["iters"]
+    t = red["t"]
+    assert np.max(np.abs(red["y"] - exact(t))) <= tol * np.max(np.abs(exact(t)))
+    assert np.max(np.abs(dense["y"] - red["y"])) <= 1e-12 * np.max(np.abs(red["y"]))
+    assert abs(red["y"][0] - q[0]) <= 1e-9 and abs(red["y"][-1] - q[1]) <= 1e-9
