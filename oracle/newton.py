@@ -2,10 +2,11 @@
 
 TEST INFRASTRUCTURE ONLY -- see ``oracle/__init__.py``.
 
-Problem family ('nl' in ``core``):  y^(p) = f(t, y, y^(p-1)) with
-    f = P(y) - delta * y^(p-1) [p = 2 only] + g cos(omega t),
+Problem family ('nl' in ``core``):  y^(p) = f(t, y, u), u = y^(p-1), with
+    f = P(y) - delta * u + beta * u^2 / y [p = 2 only for delta, beta] + g cos(omega t),
     P(y) = c0 + c1 y + c2 y^2 + c3 y^3.
-This covers y' = 1 - y^2 (tanh), the logistic equation and the Duffing equation.
+This covers y' = 1 - y^2 (tanh), the logistic equation, the Duffing equation and
+the paper's Problem 15, y'' = -y + 2 (y')^2 / y (Appendix A.6).
 
 Eq. 2.2 / Appendix A.5: unknowns (omega, b, lambda_1..lambda_p, y_2..y_n),
     L = 1/2 |omega|^2 + gamma/2 sum e_i^2 + gamma/2 sum xi_i^2 + sum_k lambda_k h_k
@@ -19,7 +20,10 @@ Lagrangian of its Problem 15 example): rows i = 2..n-1 and
 
 Readings of the paper taken here:
  * Only y_i is an auxiliary unknown; the derivative y^(p-1) inside f is
-   omega^T phi^(p-1)(t_i) (as in the worked Problem 15 of Appendix B.2).
+   omega^T phi^(p-1)(t_i) (as in the worked Problem 15 of Appendix A.6), so
+   d e_i / d omega = phi^(p)(t_i) - f_u phi^(p-1)(t_i) changes with the iterate
+   when f is nonlinear in u, and the Hessian gains - e_i f_uu phi' phi'^T and
+   - e_i f_yu phi' (dropped, like - e_i f_yy, by the Gauss-Newton fallback).
  * Start: omega = 0, b = v_1, lambda = 0, y_i = v_1.  Undamped steps.
  * Full Newton; an iteration falls back to the Gauss-Newton Hessian (the
    e_i * P''(y_i) term dropped) when some diagonal entry
@@ -44,6 +48,24 @@ def poly(prob, y):
     return P, dP, d2P
 
 
+def rhs_f(prob, t, y, u):
+    """f(t, y, u) and its partial derivatives f_y, f_u, f_yy, f_yu, f_uu."""
+    P, dP, d2P = poly(prob, y)
+    delta, beta = prob.get("delta", 0.0), prob.get("beta", 0.0)
+    f = P - delta * u + forcing(prob, t)
+    f_y, f_u, f_yy = dP, -delta + 0 * u, d2P
+    f_yu = np.zeros_like(y)
+    f_uu = np.zeros_like(y)
+    if beta != 0.0:      # beta u^2 / y
+        f = f + beta * u * u / y
+        f_y = f_y - beta * u * u / y ** 2
+        f_u = f_u + 2 * beta * u / y
+        f_yy = f_yy + 2 * beta * u * u / y ** 3
+        f_yu = -2 * beta * u / y ** 2
+        f_uu = 2 * beta / y
+    return f, f_y, f_u, f_yy, f_yu, f_uu
+
+
 def forcing(prob, t):
     return prob.get("g", 0.0) * np.cos(prob.get("omega", 0.0) * t)
 
@@ -55,8 +77,8 @@ class Pieces:
         if prob["kind"] != "nl":
             raise ValueError("newton oracle needs kind 'nl'")
         p = prob["p"]
-        if p == 1 and prob.get("delta", 0.0) != 0.0:
-            raise ValueError("delta term needs p = 2")
+        if p == 1 and (prob.get("delta", 0.0) != 0.0 or prob.get("beta", 0.0) != 0.0):
+            raise ValueError("delta and beta terms need p = 2")
         self.prob = prob
         self.st = core.setup(prob, tau)
         st = self.st
@@ -64,13 +86,10 @@ class Pieces:
         sg = prob["sigma"]
         self.ti = core.collocation_points(prob, t)
         self.Phi = core.features(self.ti, s, sg, W, 0)
-        Pp = core.features(self.ti, s, sg, W, p)
-        if p == 2:
-            Pp = Pp + prob.get("delta", 0.0) * core.features(self.ti, s, sg, W, 1)
-        self.Q = Pp                           # d e_i / d omega
+        self.Pp = core.features(self.ti, s, sg, W, p)        # phi^(p)
+        self.Pu = core.features(self.ti, s, sg, W, p - 1)    # phi^(p-1): u = omega^T phi^(p-1)
         # condition rows on (omega, b) and their values
         self.C, self.v = core.condition_rows(prob, st)
-        self.rho = forcing(prob, self.ti)
         self.me = W.shape[0]
         self.p = p
         self.n1 = len(self.ti)
@@ -82,12 +101,15 @@ class Pieces:
         return x[:me], x[me], x[me + 1:me + 1 + p], x[me + 1 + p:]
 
     def residuals(self, x):
+        """e, xi, h, and per row: q = d e / d omega, f_y, f_yy, f_yu, f_uu."""
         om, b, lam, y = self.split(x)
-        P, dP, d2P = poly(self.prob, y)
-        e = self.Q @ om - P - self.rho
+        u = self.Pu @ om
+        f, f_y, f_u, f_yy, f_yu, f_uu = rhs_f(self.prob, self.ti, y, u)
+        e = self.Pp @ om - f
         xi = y - self.Phi @ om - b
         h = self.C @ np.r_[om, b] - self.v
-        return e, xi, h, P, dP, d2P
+        Q = self.Pp - f_u[:, None] * self.Pu
+        return e, xi, h, Q, f_y, f_yy, f_yu, f_uu
 
     def lagrangian(self, x):
         """Scalar L of Appendix A.5 evaluated from its definition."""
@@ -99,35 +121,38 @@ class Pieces:
     def F(self, x):
         """F = grad L = (Y_1, Y_2, Y_3..Y_{p+2}, Y_{p+3}) of Lemma 2."""
         om, b, lam, y = self.split(x)
-        e, xi, h, P, dP, d2P = self.residuals(x)
+        e, xi, h, Q, f_y, *_ = self.residuals(x)
         g = self.gamma
         me = self.me
-        Y1 = om + g * self.Q.T @ e - g * self.Phi.T @ xi + self.C[:, :me].T @ lam
+        Y1 = om + g * Q.T @ e - g * self.Phi.T @ xi + self.C[:, :me].T @ lam
         Y2 = -g * xi.sum() + self.C[:, me] @ lam
-        Yy = -g * e * dP + g * xi
+        Yy = -g * e * f_y + g * xi
         return np.concatenate([Y1, [Y2], h, Yy])
 
     def diag_yy(self, x, gauss_newton):
-        e, xi, h, P, dP, d2P = self.residuals(x)
-        curv = 0.0 if gauss_newton else e * d2P
-        return self.gamma * (dP ** 2 - curv + 1.0)
+        e, xi, h, Q, f_y, f_yy, f_yu, f_uu = self.residuals(x)
+        curv = 0.0 if gauss_newton else e * f_yy
+        return self.gamma * (f_y ** 2 - curv + 1.0)
 
     def J(self, x, gauss_newton=False):
         """Dense (m+n+p) Jacobian of F (the matrix of Lemma 2)."""
         om, b, lam, y = self.split(x)
-        e, xi, h, P, dP, d2P = self.residuals(x)
+        e, xi, h, Q, f_y, f_yy, f_yu, f_uu = self.residuals(x)
+        cu = 0.0 if gauss_newton else e * f_uu       # - e f_uu phi' phi'^T
+        cyu = 0.0 if gauss_newton else e * f_yu      # - e f_yu phi'
         g = self.gamma
         me, p, n1 = self.me, self.p, self.n1
         N = me + 1 + p + n1
         Jm = np.zeros((N, N))
-        Jm[:me, :me] = np.eye(me) + g * self.Q.T @ self.Q + g * self.Phi.T @ self.Phi
+        Jm[:me, :me] = (np.eye(me) + g * Q.T @ Q - g * (self.Pu * (cu + 0 * e)[:, None]).T @ self.Pu
+                        + g * self.Phi.T @ self.Phi)
         Jm[:me, me] = g * self.Phi.sum(axis=0)
         Jm[me, :me] = Jm[:me, me]
         Jm[me, me] = g * n1
         Jm[:me + 1, me + 1:me + 1 + p] = self.C.T
         Jm[me + 1:me + 1 + p, :me + 1] = self.C
         oy = me + 1 + p
-        Jwy = -g * dP[None, :] * self.Q.T - g * self.Phi.T   # d Y1 / d y
+        Jwy = -g * (f_y[None, :] * Q.T + (cyu + 0 * e)[None, :] * self.Pu.T) - g * self.Phi.T   # d Y1 / d y
         Jm[:me, oy:] = Jwy
         Jm[oy:, :me] = Jwy.T
         Jm[me, oy:] = -g
@@ -144,17 +169,21 @@ class Pieces:
         [rhs_x; -h] and then dy_i = -(Fy_i + w_i^T dx) / d_i.
         """
         om, b, lam, y = self.split(x)
-        e, xi, h, P, dP, d2P = self.residuals(x)
+        e, xi, h, Q, f_y, f_yy, f_yu, f_uu = self.residuals(x)
+        cu = 0.0 * e if gauss_newton else e * f_uu
+        cyu = 0.0 * e if gauss_newton else e * f_yu
         g = self.gamma
         me = self.me
         Fx = self.F(x)
         Fxb = Fx[:me + 1]
         Fy = Fx[me + 1 + self.p:]
         d = self.diag_yy(x, gauss_newton)
-        Qt = np.concatenate([self.Q, np.zeros((self.n1, 1))], axis=1)
+        Qt = np.concatenate([Q, np.zeros((self.n1, 1))], axis=1)
         St = np.concatenate([self.Phi, np.ones((self.n1, 1))], axis=1)
-        Wr = -g * (dP[:, None] * Qt + St)          # rows w_i
-        S = g * Qt.T @ Qt + g * St.T @ St - (Wr / d[:, None]).T @ Wr
+        Ut = np.concatenate([self.Pu, np.zeros((self.n1, 1))], axis=1)
+        Wr = -g * (f_y[:, None] * Qt + cyu[:, None] * Ut + St)          # rows w_i
+        S = (g * Qt.T @ Qt - g * (Ut * cu[:, None]).T @ Ut + g * St.T @ St
+             - (Wr / d[:, None]).T @ Wr)
         S[:me, :me] += np.eye(me)
         rhs_x = -Fxb + Wr.T @ (Fy / d)
         return S, rhs_x, d, Wr, Fy, h

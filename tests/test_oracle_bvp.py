@@ -1,5 +1,7 @@
 """Pins of the oracle's boundary value case (Appendix A.4, BVP: y(t_1) = q_1,
 y(t_n) = q_n, collocation rows 2..n-1)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -115,3 +117,28 @@ def test_nonlinear_bvp_matches_closed_form(case):
     assert np.max(np.abs(red["y"] - exact(t))) <= tol * np.max(np.abs(exact(t)))
     assert np.max(np.abs(dense["y"] - red["y"])) <= 1e-12 * np.max(np.abs(red["y"]))
     assert abs(red["y"][0] - q[0]) <= 1e-9 and abs(red["y"][-1] - q[1]) <= 1e-9
+
+
+P15 = os.path.join(os.path.dirname(__file__), "golden", "paper_p15_B7.txt")
+
+
+def p15_problem():
+    """Appendix A.6's Problem 15 with its printed hyper-parameters, and the row of
+    printed errors."""
+    row = [line.split() for line in open(P15) if line.strip() and not line.startswith("#")][0]
+    q, n, m, s2, gam = float(row[1]), int(row[2]), int(row[3]), float(row[4]), float(row[5])
+    prob = dict(p=2, n=n, m=m, t0=-1.0, t1=1.0, sigma=s2 ** 0.5, gamma=gam, v=[q, q], kind="nl",
+                P=[0.0, -1.0, 0.0, 0.0], delta=0.0, beta=2.0, g=0.0, omega=0.0, bc="bvp")
+    return prob, tuple(float(x) for x in row[6:9])
+
+
+def test_problem_15_printed_accuracy():
+    """Newton on Problem 15 (f nonlinear in y') meets the printed NLS-SVM errors:
+    ours within [1/10, 2] x each printed figure (ours is ~4x more accurate)."""
+    from oracle import newton
+    prob, printed = p15_problem()
+    sol = newton.solve(prob)
+    assert sol["converged"]
+    e = np.abs(sol["y"] - 0.5 / np.cosh(sol["t"]))
+    for ours, paper in zip((e.mean(), np.sqrt((e ** 2).mean()), e.max()), printed):
+        assert paper / 10 <= ours <= 2 * paper, (ours, paper)

@@ -47,10 +47,10 @@ def test_jacobian_is_derivative_of_F(mk):
     assert np.abs(J - fd).max() <= 1e-6 * np.abs(J).max()
     # Gauss-Newton differs only on the y-diagonal, by gamma * e_i * P''(y_i)
     Jg = pc.J(x, gauss_newton=True)
-    e, xi, hh, P, dP, d2P = pc.residuals(x)
+    e, xi, hh, Q, f_y, f_yy, f_yu, f_uu = pc.residuals(x)
     D = J - Jg
     oy = pc.me + 1 + pc.p
-    np.testing.assert_allclose(np.diag(D)[oy:], -pc.gamma * e * d2P, rtol=1e-12, atol=1e-9)
+    np.testing.assert_allclose(np.diag(D)[oy:], -pc.gamma * e * f_yy, rtol=1e-12, atol=1e-9)
     D[oy + np.arange(pc.n1), oy + np.arange(pc.n1)] = 0
     assert np.abs(D).max() == 0
 
@@ -182,3 +182,28 @@ def test_gradient_vanishes_at_exact_fit():
     g = adjoint.complex_step_gradient(prob, tau, yfit)
     g_noisy = adjoint.complex_step_gradient(prob, tau, yobs)
     assert np.abs(g).max() < 1e-10 * np.abs(g_noisy).max()
+
+
+def _problem15(n=60, m=10, gamma=1e4):
+    """Appendix A.6: y'' = -y + 2 (y')^2 / y on [-1, 1], y(-1) = y(1) = 0.324027137."""
+    q = 0.5 / np.cosh(1.0)
+    return dict(p=2, n=n, m=m, t0=-1.0, t1=1.0, sigma=1.0, gamma=gamma, v=[q, q], kind="nl",
+                P=[0.0, -1.0, 0.0, 0.0], delta=0.0, beta=2.0, g=0.0, omega=0.0, bc="bvp")
+
+
+def test_jacobian_is_derivative_of_F_with_nonlinear_derivative_term():
+    """f nonlinear in u = y' (the u^2 / y term of Problem 15): the per-row
+    d e / d omega and the - e f_uu phi' phi'^T and - e f_yu phi' Hessian terms,
+    against central differences of F."""
+    pc = newton.Pieces(_problem15())
+    rng = np.random.default_rng(3)
+    x = newton.x0(pc) + 0.05 * rng.standard_normal(pc.me + 1 + pc.p + pc.n1)
+    x[pc.me + 1 + pc.p:] = np.abs(x[pc.me + 1 + pc.p:]) + 0.2     # y_i away from 0
+    J = pc.J(x)
+    h = 1e-6
+    fd = np.array([(pc.F(x + h * e) - pc.F(x - h * e)) / (2 * h) for e in np.eye(len(x))]).T
+    assert np.abs(J - fd).max() <= 1e-6 * np.abs(J).max()
+    # the reduced (y-eliminated) step equals the dense one
+    a = newton.step_dense(pc, x, False)
+    b = newton.step_reduced(pc, x, False)
+    assert np.abs(a - b).max() <= 1e-8 * max(1.0, np.abs(a).max())
