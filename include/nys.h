@@ -61,8 +61,10 @@ typedef enum {
      c[0] = a_1, c[1] = a_2 (p = 2), c[2] = c, c[3] = omega, c[4] = phi0.   */
   NYS_COEF_LIN = 1,
   /* nonlinear (Lemma 2): y^(p) = c0 + c1 y + c2 y^2 + c3 y^3
-     - delta y^(p-1) [p = 2 only] + g cos(omega t):
-     c[0..3] = c0..c3, c[4] = delta, c[5] = g, c[6] = omega.                */
+     - delta y' + beta y'^2 / y [p = 2 only for delta, beta] + g cos(omega t):
+     c[0..3] = c0..c3, c[4] = delta, c[5] = g, c[6] = omega, c[7] = beta
+     (y'' = -y + 2 y'^2 / y is Problem 15 of Appendix A.6; y must stay
+     nonzero on the collocation points when beta != 0).                      */
   NYS_COEF_POLY_NL = 2
 } nys_coef_kind;
 

@@ -50,6 +50,7 @@ def pack_instances(problems):
         elif q["kind"] == "nl":
             c[0:4] = list(q["P"])
             c[4], c[5], c[6] = q.get("delta", 0.0), q.get("g", 0.0), q.get("omega", 0.0)
+            c[7] = q.get("beta", 0.0)
         elif q["kind"] == "table":
             tabv = np.ascontiguousarray(np.concatenate(
                 [np.asarray(q["f"], dtype=np.float64).reshape(s.p, s.n),

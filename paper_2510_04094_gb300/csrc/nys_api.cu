@@ -59,7 +59,7 @@ cudaError_t launch_newton_pass(const Inst* insts, const Lset* lsets, const doubl
                                const double* xs, int XS, const double* zs, const double* dzs, int ZS,
                                double* yaux, double* rowstate, double* part,
                                const int64_t* slot_off, const int32_t* active, int mode,
-                               int apply_dy, int m_max, int num_sms, cudaStream_t s);
+                               int apply_dy, int m_max, int tiles, int num_sms, cudaStream_t s);
 cudaError_t launch_newton_step(const Inst* insts, const Lset* lsets, const double* W,
                                const double* part, const int64_t* slot_off, const int32_t* lm,
                                double* xs, double* zs, double* dzs, double* cws, int XS, int ZS,
@@ -126,6 +126,7 @@ struct nys_ctx {
   nys_options opt{};
   bool fp32 = false;
   bool any_nl = false, any_lin = false;
+  int nt_tiles = 4;            // shared tiles of the Newton row pass (6 with a beta term)
   bool solved = false, assembled = false;
   std::vector<nys_instance> shape;        // p, n, m, kind per instance (for update checks)
   std::vector<int32_t> h_lm;               // landmark indices (host)
@@ -203,8 +204,8 @@ static int32_t check_instance(const nys_instance& q, int b) {
     return fail(NYS_EINVAL, "instance %d: need finite t0 < t1", b);
   if (!(std::isfinite(q.sigma) && q.sigma > 0)) return fail(NYS_EINVAL, "instance %d: sigma must be > 0", b);
   if (!(std::isfinite(q.gamma) && q.gamma > 0)) return fail(NYS_EINVAL, "instance %d: gamma must be > 0", b);
-  if (q.kind == NYS_COEF_POLY_NL && q.p == 1 && q.c[4] != 0.0)
-    return fail(NYS_EINVAL, "instance %d: the delta y' term needs p = 2", b);
+  if (q.kind == NYS_COEF_POLY_NL && q.p == 1 && (q.c[4] != 0.0 || q.c[7] != 0.0))
+    return fail(NYS_EINVAL, "instance %d: the delta y' and beta y'^2 / y terms need p = 2", b);
   if (q.kind == NYS_COEF_TABLE && q.coef_table == nullptr)
     return fail(NYS_EINVAL, "instance %d: kind TABLE needs coef_table", b);
   if (q.bc != NYS_BC_IVP && q.bc != NYS_BC_BVP)
@@ -600,6 +601,8 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   for (int b = 0; b < batch; ++b) {
     if (q[b].kind == NYS_COEF_POLY_NL) c->any_nl = true;
     else c->any_lin = true;
+    // a beta u^2 / y term needs the Newton row pass's two extra tiles
+    if (q[b].kind == NYS_COEF_POLY_NL && q[b].p == 2 && q[b].c[7] != 0.0) c->nt_tiles = 6;
   }
   int dev = 0;
   cudaError_t ce = cudaGetDevice(&dev);
@@ -700,7 +703,7 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   A(c->err.alloc(1));
   if (c->any_nl) {
     A(c->yaux.alloc((size_t)ytot));
-    A(c->rowstate.alloc((size_t)ytot * 4));
+    A(c->rowstate.alloc((size_t)ytot * kNtRowState));
     A(c->row_off.alloc(batch));
     A(c->nrm.alloc((size_t)batch * 4));
     A(c->active.alloc(batch));
@@ -968,7 +971,7 @@ int32_t nys_newton(nys_ctx* c, void* stream, int32_t max_iter, double tol, doubl
     CK(cudaMemsetAsync(flags, 0, 2 * sizeof(int32_t), s));
     CK(launch_newton_pass(c->inst.p, c->lset.p, c->W.p, c->work.p, c->nwork, c->counter.p, c->lm.p,
                           c->xs.p, c->XS, c->zs.p, c->dzs.p, c->ZS, c->yaux.p, c->rowstate.p, c->part.p, c->slot_off.p, c->active.p,
-                          0, k > 0 ? 1 : 0, c->m_max, c->num_sms, s));
+                          0, k > 0 ? 1 : 0, c->m_max, c->nt_tiles, c->num_sms, s));
     CK(launch_newton_step(c->inst.p, c->lset.p, c->W.p, c->part.p, c->slot_off.p, c->lm.p, c->xs.p,
                           c->zs.p, c->dzs.p, c->cws.p, c->XS, c->ZS, c->M1S, c->st.p, c->active.p,
                           c->iters.p, c->nrm.p, max_iter, tol, flags, 0, c->batch, c->m_max, s));
@@ -977,7 +980,7 @@ int32_t nys_newton(nys_ctx* c, void* stream, int32_t max_iter, double tol, doubl
     if (c->pin_flag[1]) {  // Gauss-Newton re-pass for the flagged instances
       CK(launch_newton_pass(c->inst.p, c->lset.p, c->W.p, c->work.p, c->nwork, c->counter.p,
                             c->lm.p, c->xs.p, c->XS, c->zs.p, c->dzs.p, c->ZS, c->yaux.p, c->rowstate.p, c->part.p, c->slot_off.p,
-                            c->active.p, 1, 0, c->m_max, c->num_sms, s));
+                            c->active.p, 1, 0, c->m_max, c->nt_tiles, c->num_sms, s));
       CK(launch_newton_step(c->inst.p, c->lset.p, c->W.p, c->part.p, c->slot_off.p, c->lm.p,
                             c->xs.p, c->zs.p, c->dzs.p, c->cws.p, c->XS, c->ZS, c->M1S, c->st.p,
                             c->active.p, c->iters.p, c->nrm.p, max_iter, tol, flags, 1, c->batch,

@@ -9,6 +9,7 @@
 namespace nys {
 
 constexpr int kMMax = NYS_M_MAX;          // landmarks per instance
+constexpr int kNtRowState = 5;            // Newton row state: Fy, d, f_y, f_u + delta, e f_yu
 constexpr int kM1Max = kMMax + 1;         // (omega, b)
 constexpr int kM2Max = kMMax + 2;         // augmented row [kappa; -f_p; r]
 constexpr int kMPMax = 120;               // kM2Max rounded up to a multiple of 8

@@ -1,7 +1,9 @@
 // Newton's method for nonlinear ODEs (Lemma 2, Section 3.2; Eq. 2.2; Eq. 3.2.1).
 //
-// Family: y^(p) = f(t, y, y^(p-1)),  f = P(y) - delta y^(p-1) [p = 2] + g cos(omega t),
-// P(y) = c0 + c1 y + c2 y^2 + c3 y^3.  Lagrangian (Appendix A.5):
+// Family: y^(p) = f(t, y, u), u = y^(p-1) = omega^T phi^(p-1)(t_i) (plus b for p = 1),
+//   f = P(y) - delta u + beta u^2 / y [p = 2 for delta, beta] + g cos(omega t),
+// P(y) = c0 + c1 y + c2 y^2 + c3 y^3 (beta: Problem 15 of Appendix A.6).
+// Lagrangian (Appendix A.5):
 //   L = 1/2 |omega|^2 + gamma/2 sum e_i^2 + gamma/2 sum xi_i^2 + sum_k lambda_k h_k,
 //   e_i = omega^T q_i - P(y_i) - rho_i,   q_i = phi^(p)(t_i) + delta phi^(p-1)(t_i),
 //   xi_i = y_i - omega^T phi(t_i) - b,    rho_i = g cos(omega t_i).
@@ -12,6 +14,10 @@
 //   rhs = -grad_x L - sum_i (Fy_i / d_i) gamma (P' qt + st),   Fy_i = dL/dy_i
 //   [S C^T; C 0] [dx; dlambda] = [rhs; -h],   dy_i = -(Fy_i - gamma (P' qt + st)^T dx) / d_i.
 // These are the iterates of the dense (m+n+p) Newton system, at O(n m^2) per step.
+// With beta != 0, f is nonlinear in u: q_i = phi'' + (delta - f_u) phi' follows the
+// iterate (f_u = -delta + 2 beta u / y), and the Hessian gains - e f_uu pt pt^T and
+// - e f_yu pt with pt = [phi'; 0]: each row adds the Gram of [qt st pt] with a
+// symmetric 3 x 3 weight (Gauss-Newton drops the e-terms), two more shared tiles.
 // Omega mode (landmark kernel with lambda_min < 1e-7 lambda_max): the rows are
 // projected through W (qt, st in omega coordinates) before the Gram, since the
 // kernel-coordinate Gram W G W^T loses the digits that cond(W)^2 costs.
@@ -68,13 +74,14 @@ k_newton_pass(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
               const double* __restrict__ zs, const double* __restrict__ dzs, int ZS,
               double* __restrict__ yaux, double* __restrict__ rowstate,
               double* __restrict__ part, const int64_t* __restrict__ slot_off,
-              const int32_t* __restrict__ active, int mode, int apply_dy) {
+              const int32_t* __restrict__ active, int mode, int apply_dy, int tiles) {
   extern __shared__ double smn[];
   __shared__ int s_item;
   __shared__ int s_idx[kMMax];
   __shared__ unsigned char s_pair[2 * kM1Max * (kM1Max + 1) / 2];
   __shared__ double s_z[kM1Max], s_dz[kM1Max];
   __shared__ double s_c[kNtRows][4];   // c_q, c_s, gamma e, -gamma xi
+  __shared__ double s_m[kNtRows][8];   // beta rows: M_qq M_qs M_qp M_ss M_sp M_pp, c_p, f_u + delta
   __shared__ double s_red[kNtThreads / 32][2];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int cached_m1 = -1;
@@ -99,6 +106,8 @@ k_newton_pass(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     const double gam = I.gamma, sig = I.sigma, is = 1.0 / sig, is2 = is * is;
     const double c0 = I.c[0], c1 = I.c[1], c2 = I.c[2], c3 = I.c[3];
     const double delta = (I.p == 2) ? I.c[4] : 0.0, gf = I.c[5], wf = I.c[6];
+    const double beta = (I.p == 2) ? I.c[7] : 0.0;
+    const bool nlu = (beta != 0.0) && (tiles >= 6);   // warp-uniform
     for (int j = tid; j < m; j += kNtThreads) s_idx[j] = lm_idx[I.lm_off + j];
     for (int j = tid; j <= D; j += kNtThreads) {
       // current iterate and last step in the frame of the Gram (dzs holds the
@@ -124,18 +133,23 @@ k_newton_pass(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     double* tk1 = tk0 + kNtRows * ld;
     double* tk2 = tk1 + kNtRows * ld;
     double* tk3 = tk2 + kNtRows * ld;
-    // qt, st: the rows in the frame of the Gram; ta = M11 qt + M12 st, tb = M12 qt + M22 st
+    double* tk4 = tk3 + kNtRows * ld;    // beta rows only (tiles == 6)
+    double* tk5 = tk4 + kNtRows * ld;
+    // qt, st (pt): the rows in the frame of the Gram; ta = M11 qt + M12 st (+ M13 pt),
+    // tb = M12 qt + M22 st (+ M23 pt), tc = M13 qt + M23 st + M33 pt
     double* tq = om ? tk2 : tk0;
     double* ts = om ? tk3 : tk1;
     double* ta = om ? tk0 : tk2;
     double* tb = om ? tk1 : tk3;
+    double* tp = om ? tk5 : tk4;
+    double* tc = om ? tk4 : tk5;
     __syncthreads();
     for (int base = wk.r0; base < wk.r1; base += kNtRows) {
       const int rows = min(kNtRows, wk.r1 - base);
       // features of the tile in kernel coordinates (FP64), into tk0 / tk1
       for (int e = tid; e < kNtRows * (m + 1); e += kNtThreads) {
         const int r = e / (m + 1), j = e - r * (m + 1);
-        double q = 0.0, s = 0.0;
+        double q = 0.0, s = 0.0, pv = 0.0;
         if (r < rows) {
           if (j < m) {
             const double x = (double)(base + r - s_idx[j]) * I.hs;
@@ -145,6 +159,7 @@ k_newton_pass(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
             if (I.p == 2) q = (4.0 * u - 2.0) * is2 * ex + delta * k1;
             else q = k1;
             s = ex;
+            pv = k1;
           } else {
             q = 0.0;
             s = 1.0;
@@ -152,6 +167,7 @@ k_newton_pass(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         }
         tk0[r * ld + j] = q;
         tk1[r * ld + j] = s;
+        if (nlu) tk4[r * ld + j] = pv;
       }
       __syncthreads();
       if (om) {  // omega coordinates: [W kq; 0], [W k; 1]
@@ -167,69 +183,123 @@ k_newton_pass(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
           }
           tq[r * ld + k] = q;
           ts[r * ld + k] = s;
+          if (nlu) {
+            double pv = 0.0;
+            if (k < D)
+              for (int j = 0; j < m; ++j) pv = fma(W[k * m + j], tk4[r * ld + j], pv);
+            tp[r * ld + k] = pv;
+          }
         }
         __syncthreads();
       }
       // per-row scalars: one warp per row, lanes over landmarks
       for (int r = warp; r < rows; r += kNtThreads / 32) {
-        double Q = 0.0, Ph = 0.0, Qd = 0.0, Sd = 0.0;
+        double Q = 0.0, Ph = 0.0, Qd = 0.0, Sd = 0.0, U = 0.0, Pd = 0.0;
         for (int j = lane; j <= D; j += 32) {
           const double qv = tq[r * ld + j], sv = ts[r * ld + j];
           Q = fma(qv, s_z[j], Q);
           Ph = fma(sv, s_z[j], Ph);
           Qd = fma(qv, s_dz[j], Qd);
           Sd = fma(sv, s_dz[j], Sd);
+          if (nlu) {
+            const double pv = tp[r * ld + j];
+            U = fma(pv, s_z[j], U);
+            Pd = fma(pv, s_dz[j], Pd);
+          }
         }
         for (int o = 16; o > 0; o >>= 1) {
           Q += __shfl_xor_sync(0xffffffffu, Q, o);
           Ph += __shfl_xor_sync(0xffffffffu, Ph, o);
           Qd += __shfl_xor_sync(0xffffffffu, Qd, o);
           Sd += __shfl_xor_sync(0xffffffffu, Sd, o);
+          if (nlu) {
+            U += __shfl_xor_sync(0xffffffffu, U, o);
+            Pd += __shfl_xor_sync(0xffffffffu, Pd, o);
+          }
         }
         if (lane == 0) {
           const int i = base + r;
           const int64_t yo = I.y_off + (i - 1);
           double y = yaux[yo];
+          double* rs = rowstate + kNtRowState * yo;
           if (mode == 0 && apply_dy) {   // y-update of the previous step
-            const double* rs = rowstate + 3 * yo;
-            y += -(rs[0] - gam * (rs[2] * Qd + Sd)) / rs[1];
+            // (its q was qt - h_u pt with the previous h_u; e f_yu weights pt)
+            const double Qp = nlu ? Qd - rs[3] * Pd : Qd;
+            const double wd = rs[2] * Qp + Sd + (nlu ? rs[4] * Pd : 0.0);
+            y += -(rs[0] - gam * wd) / rs[1];
             yaux[yo] = y;
           }
           const double P = c0 + y * (c1 + y * (c2 + y * c3));
-          const double dP = c1 + y * (2.0 * c2 + 3.0 * c3 * y);
-          const double d2P = 2.0 * c2 + 6.0 * c3 * y;
           const double rho = gf * cos(wf * (I.t0 + (double)i * I.h));
-          const double e = Q - P - rho;
+          double fy = c1 + y * (2.0 * c2 + 3.0 * c3 * y);   // f_y
+          double fyy = 2.0 * c2 + 6.0 * c3 * y;               // f_yy
+          double e = Q - P - rho;                             // Q = (phi'' + delta phi')^T x
+          double hu = 0.0, cyu = 0.0, cu = 0.0;
+          if (nlu) {   // beta u^2 / y
+            const double iy = 1.0 / y, bu = beta * U * iy;
+            e -= bu * U;
+            fy -= bu * U * iy;
+            fyy += 2.0 * bu * U * iy * iy;
+            hu = 2.0 * bu;                                    // f_u + delta
+            cyu = e * (-2.0 * bu * iy);                       // e f_yu
+            cu = e * (2.0 * beta * iy);                       // e f_uu
+          }
           const double xi = y - Ph;
-          const double Fy = -gam * e * dP + gam * xi;
-          const double dfull = gam * (dP * dP - e * d2P + 1.0);
+          const double Fy = -gam * e * fy + gam * xi;
+          const double dfull = gam * (fy * fy - e * fyy + 1.0);
           if (mode == 0 && !(dfull > 1e-12 * gam)) ++nsmall;
-          const double d = (mode == 0) ? dfull : gam * (dP * dP + 1.0);
-          double* rs = rowstate + 3 * yo;
+          const double d = (mode == 0) ? dfull : gam * (fy * fy + 1.0);
+          if (mode != 0) { cyu = 0.0; cu = 0.0; }             // Gauss-Newton
           rs[0] = Fy;
           rs[1] = d;
-          rs[2] = dP;
+          rs[2] = fy;
+          rs[3] = hu;
+          rs[4] = cyu;
           fy2 = fma(Fy, Fy, fy2);
           const double g2d = gam * gam / d;
-          // M = gamma I - (gamma^2/d) [P' 1][P' 1]^T
-          s_c[r][0] = gam * e + gam * dP * Fy / d;   // c_q
+          // M = diag(gamma, gamma, -gamma e f_uu) - (gamma^2/d) w w^T, w = [f_y 1 e f_yu]
+          s_c[r][0] = gam * e + gam * fy * Fy / d;   // c_q
           s_c[r][1] = -gam * xi + gam * Fy / d;      // c_s
           s_c[r][2] = gam * e;
           s_c[r][3] = -gam * xi;
-          const double M11 = gam - g2d * dP * dP, M12 = -g2d * dP, M22 = gam - g2d;
-          // stash M in the first two slots of the a/b rows (overwritten below)
-          ta[r * ld + M1] = M11;
-          tb[r * ld + M1] = M22;
-          ts[r * ld + M1] = M12;
+          const double M11 = gam - g2d * fy * fy, M12 = -g2d * fy, M22 = gam - g2d;
+          if (nlu) {
+            s_m[r][0] = M11;
+            s_m[r][1] = M12;
+            s_m[r][2] = -g2d * fy * cyu;             // M13
+            s_m[r][3] = M22;
+            s_m[r][4] = -g2d * cyu;                  // M23
+            s_m[r][5] = -gam * cu - g2d * cyu * cyu; // M33
+            s_m[r][6] = gam * cyu * Fy / d;          // c_p
+            s_m[r][7] = hu;
+          } else {
+            // stash M in the first two slots of the a/b rows (overwritten below)
+            ta[r * ld + M1] = M11;
+            tb[r * ld + M1] = M22;
+            ts[r * ld + M1] = M12;
+          }
         }
       }
       __syncthreads();
-      for (int e = tid; e < rows * M1; e += kNtThreads) {
-        const int r = e / M1, j = e - r * M1;
-        const double M11 = ta[r * ld + M1], M22 = tb[r * ld + M1], M12 = ts[r * ld + M1];
-        const double q = tq[r * ld + j], s = ts[r * ld + j];
-        ta[r * ld + j] = M11 * q + M12 * s;
-        tb[r * ld + j] = M12 * q + M22 * s;
+      if (nlu) {
+        // the row's d e / d x: qt - h_u pt, then the three combinations
+        for (int e = tid; e < rows * M1; e += kNtThreads) {
+          const int r = e / M1, j = e - r * M1;
+          const double pv = tp[r * ld + j], sv = ts[r * ld + j];
+          const double qv = tq[r * ld + j] - s_m[r][7] * pv;
+          tq[r * ld + j] = qv;
+          ta[r * ld + j] = s_m[r][0] * qv + s_m[r][1] * sv + s_m[r][2] * pv;
+          tb[r * ld + j] = s_m[r][1] * qv + s_m[r][3] * sv + s_m[r][4] * pv;
+          tc[r * ld + j] = s_m[r][2] * qv + s_m[r][4] * sv + s_m[r][5] * pv;
+        }
+      } else {
+        for (int e = tid; e < rows * M1; e += kNtThreads) {
+          const int r = e / M1, j = e - r * M1;
+          const double M11 = ta[r * ld + M1], M22 = tb[r * ld + M1], M12 = ts[r * ld + M1];
+          const double q = tq[r * ld + j], s = ts[r * ld + j];
+          ta[r * ld + j] = M11 * q + M12 * s;
+          tb[r * ld + j] = M12 * q + M22 * s;
+        }
       }
       __syncthreads();
       // reduced Gram: G_jl += a_j qt_l + b_j st_l
@@ -239,9 +309,17 @@ k_newton_pass(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         if (e < E1) {
           const int j = s_pair[2 * e], l = s_pair[2 * e + 1];
           double a = acc[k];
-          for (int r = 0; r < rows; ++r) {
-            a = fma(ta[r * ld + j], tq[r * ld + l], a);
-            a = fma(tb[r * ld + j], ts[r * ld + l], a);
+          if (nlu) {
+            for (int r = 0; r < rows; ++r) {
+              a = fma(ta[r * ld + j], tq[r * ld + l], a);
+              a = fma(tb[r * ld + j], ts[r * ld + l], a);
+              a = fma(tc[r * ld + j], tp[r * ld + l], a);
+            }
+          } else {
+            for (int r = 0; r < rows; ++r) {
+              a = fma(ta[r * ld + j], tq[r * ld + l], a);
+              a = fma(tb[r * ld + j], ts[r * ld + l], a);
+            }
           }
           acc[k] = a;
         }
@@ -250,6 +328,7 @@ k_newton_pass(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         for (int r = 0; r < rows; ++r) {
           vacc = fma(s_c[r][0], tq[r * ld + tid], fma(s_c[r][1], ts[r * ld + tid], vacc));
           uacc = fma(s_c[r][2], tq[r * ld + tid], fma(s_c[r][3], ts[r * ld + tid], uacc));
+          if (nlu) vacc = fma(s_m[r][6], tp[r * ld + tid], vacc);
         }
       }
       __syncthreads();
@@ -282,7 +361,10 @@ k_newton_pass(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   }
 }
 
-size_t newton_pass_smem(int m_max) { return sizeof(double) * 4 * (size_t)kNtRows * (m_max + 2); }
+// tiles: 4, or 6 when some instance has a beta u^2 / y term
+size_t newton_pass_smem(int m_max, int tiles) {
+  return sizeof(double) * (size_t)tiles * kNtRows * (m_max + 2);
+}
 
 template <int K>
 static cudaError_t launch_pass_k(const Inst* insts, const Lset* lsets, const double* W,
@@ -290,8 +372,8 @@ static cudaError_t launch_pass_k(const Inst* insts, const Lset* lsets, const dou
                                  const double* xs, int XS, const double* zs, const double* dzs, int ZS,
                                  double* yaux, double* rowstate, double* part,
                                  const int64_t* slot_off, const int32_t* active, int mode,
-                                 int apply_dy, int m_max, int num_sms, cudaStream_t s) {
-  const size_t sm = newton_pass_smem(m_max);
+                                 int apply_dy, int m_max, int tiles, int num_sms, cudaStream_t s) {
+  const size_t sm = newton_pass_smem(m_max, tiles);
   cudaError_t e = cudaFuncSetAttribute(k_newton_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sm);
   if (e != cudaSuccess) return e;
@@ -300,7 +382,8 @@ static cudaError_t launch_pass_k(const Inst* insts, const Lset* lsets, const dou
   const int grid = min(nwork, num_sms * max(1, per_sm));
   k_newton_pass<K><<<grid, kNtThreads, sm, s>>>(insts, lsets, W, work, nwork, counter, lm, xs, XS,
                                                   zs, dzs, ZS, yaux,
-                                                  rowstate, part, slot_off, active, mode, apply_dy);
+                                                  rowstate, part, slot_off, active, mode, apply_dy,
+                                                  tiles);
   return cudaGetLastError();
 }
 
@@ -309,13 +392,13 @@ cudaError_t launch_newton_pass(const Inst* insts, const Lset* lsets, const doubl
                                const double* xs, int XS, const double* zs, const double* dzs, int ZS,
                                double* yaux, double* rowstate, double* part,
                                const int64_t* slot_off, const int32_t* active, int mode,
-                               int apply_dy, int m_max, int num_sms, cudaStream_t s) {
+                               int apply_dy, int m_max, int tiles, int num_sms, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   const int M1 = m_max + 1, E1 = M1 * (M1 + 1) / 2;
   const int kneed = (E1 + kNtThreads - 1) / kNtThreads;
 #define NT_ARGS insts, lsets, W, work, nwork, counter, lm, xs, XS, zs, dzs, ZS, yaux, rowstate, part, slot_off, active, \
-                mode, apply_dy, m_max, num_sms, s
+                mode, apply_dy, m_max, tiles, num_sms, s
   if (kneed <= 4) return launch_pass_k<4>(NT_ARGS);
   if (kneed <= 8) return launch_pass_k<8>(NT_ARGS);
   if (kneed <= 14) return launch_pass_k<14>(NT_ARGS);

@@ -234,3 +234,41 @@ def test_nonlinear_bvp_and_ivp_instances_in_one_batch(api):
             q["bc"] = "ivp"
         probs.append(q)
     _newton_compare(api, probs)
+
+
+# ---- right-hand side nonlinear in y' (beta y'^2 / y; Problem 15) ------------
+def _p15(n=300, m=10, sigma=1.0, gamma=1e7, beta=2.0, c1=-1.0, bc="bvp"):
+    """y'' = c1 y + beta (y')^2 / y on [-1, 1]; Appendix A.6 has c1 = -1, beta = 2,
+    y(+-1) = 1 / (2 cosh 1).  The initial value version starts from the closed form."""
+    q = 0.5 / np.cosh(1.0)
+    v = [q, q] if bc == "bvp" else [q, 0.5 * np.sinh(1.0) / np.cosh(1.0) ** 2]
+    return dict(p=2, n=n, m=m, t0=-1.0, t1=1.0, sigma=sigma, gamma=gamma, v=v, kind="nl",
+                P=[0.0, c1, 0.0, 0.0], delta=0.0, beta=beta, g=0.0, omega=0.0, bc=bc)
+
+
+def test_problem_15_on_the_gpu(api):
+    """The paper's Problem 15 with its printed hyper-parameters: the oracle's
+    iteration count and fit, and the printed accuracy against y = 1 / (2 cosh t)."""
+    import torch
+    prob = _p15()
+    _newton_compare(api, [prob])
+    bt = api.Batch([prob], precision="fp64")
+    x, st, iters, _ = bt.newton()
+    y, _ = bt.eval([core.grid(prob)])
+    torch.cuda.synchronize()
+    t = core.grid(prob)
+    e = np.abs(y.cpu().numpy() - 0.5 / np.cosh(t))
+    assert int(st.cpu().numpy()[0]) == 0
+    assert e.mean() <= 2 * 1.68e-7 and e.max() <= 2 * 3.46e-7
+    bt.close()
+
+
+def test_beta_family_batch(api):
+    """Variants of Problem 15 (beta, c1), its initial value form and a finer grid,
+    beside a beta-free instance in one batch (two kinds of Newton rows)."""
+    probs = [_p15(), _p15(beta=1.5, c1=-0.5, n=220, m=14, sigma=0.4, gamma=1e9),
+             _p15(beta=2.5, c1=-1.5, n=180, m=12, sigma=0.5, gamma=1e8),
+             _p15(bc="ivp", n=240, m=16, sigma=0.4, gamma=1e9),
+             _p15(n=2000, m=20, sigma=0.3, gamma=1e10),
+             _nl_bvp([0.0, 0.0, 0.0, 2.0], (1.0, 0.5))]
+    _newton_compare(api, probs)
