@@ -11,9 +11,7 @@
 
 namespace nys {
 
-constexpr int kSetupThreads = 256;
 constexpr int kMaxSweeps = 40;
-constexpr int kJW = kSetupThreads / 32;            // warps of the setup CTA
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -70,7 +68,7 @@ __device__ __forceinline__ int rr_pos(int k, int r, int N) {
   return 1 + t;
 }
 
-template <typename T>
+template <typename T, int kJW>   // kJW: warps of the CTA
 __device__ void jacobi_sweeps(T* A, T* V, int ld, int m, int N, T* cs, int* pq, double* red,
                               double tol, int max_sweeps, double stall) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
@@ -186,7 +184,10 @@ __device__ void sort_desc(const T* A, int ld, int m, int* perm) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kSetupThreads, 4)
+// NT threads per CTA: 256 for the small landmark counts (several CTAs per SM),
+// 512 / 1024 for the large ones, whose shared memory leaves room for 2 / 1 CTAs
+template <int NT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1))
 k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict__ W_all,
             float* __restrict__ W32_all, double* __restrict__ lam_all, double tau, int allow_chol,
             int m_lo, int m_hi) {
@@ -309,7 +310,8 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict_
     }
     __syncthreads();
     // FP32 sweeps reach off(A)^2 ~ 1e-13 tot(A)^2; the correction below absorbs the rest
-    jacobi_sweeps<float>(Af, Vf, ld, m, N, reinterpret_cast<float*>(cs), pos, red, 1e-13, kMaxSweeps, 1e-9);
+    jacobi_sweeps<float, NT / 32>(Af, Vf, ld, m, N, reinterpret_cast<float*>(cs), pos, red, 1e-13,
+                                  kMaxSweeps, 1e-9);
     sort_desc(Af, ld, m, perm);
     if (tid == 0) {
       const double lmax = Af[perm[0] * ld + perm[0]], lmin = Af[perm[m - 1] * ld + perm[m - 1]];
@@ -374,7 +376,7 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict_
     V[j * ld + l] = (j == l) ? 1.0 : 0.0;
   }
   __syncthreads();
-  jacobi_sweeps<double>(A, V, ld, m, N, cs, pos, red, 1e-30, kMaxSweeps, 0.0);
+  jacobi_sweeps<double, NT / 32>(A, V, ld, m, N, cs, pos, red, 1e-30, kMaxSweeps, 0.0);
 
   // sort eigenvalues descending, keep lambda > tau * lambda_max
   sort_desc(A, ld, m, perm);
@@ -439,20 +441,35 @@ cudaError_t launch_lag(const Lset* lsets, int capacity, float* lag, cudaStream_t
 
 // m_bounds: increasing class bounds of the landmark counts present (nclass of
 // them, the last >= every m); nclass == 0: one class up to m_max.
+template <int NT>
+static cudaError_t launch_eig_class(Lset* lsets, int capacity, const int32_t* lm_idx, double* W,
+                                    float* W32, double* lam, double tau, int allow_chol, int lo,
+                                    int hi, cudaStream_t st) {
+  const size_t sm = setup_smem_bytes(hi);
+  cudaError_t e = cudaFuncSetAttribute(k_setup_eig<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
+  if (e != cudaSuccess) return e;
+  k_setup_eig<NT><<<capacity, NT, sm, st>>>(lsets, lm_idx, W, W32, lam, tau, allow_chol, lo, hi);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_eig(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
                        double* lam, double tau, int m_max, cudaStream_t st, int allow_chol,
                        const int* m_bounds, int nclass) {
   if (capacity == 0) return cudaSuccess;
-  const size_t smax = setup_smem_bytes(m_max);
-  cudaError_t e = cudaFuncSetAttribute(k_setup_eig, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smax);
-  if (e != cudaSuccess) return e;
   int lo = 0;
   for (int k = 0; k < (nclass > 0 ? nclass : 1); ++k) {
     const int hi = (nclass > 0) ? m_bounds[k] : m_max;
-    k_setup_eig<<<capacity, kSetupThreads, setup_smem_bytes(hi), st>>>(lsets, lm_idx, W, W32, lam,
-                                                                         tau, allow_chol, lo, hi);
-    e = cudaGetLastError();
+    // threads per CTA from the class's shared memory: one CTA per SM above
+    // ~113 KB, two above ~75 KB (of the SM's 228 KB)
+    const size_t sm = setup_smem_bytes(hi);
+    cudaError_t e;
+    if (sm > 113 * 1024)
+      e = launch_eig_class<1024>(lsets, capacity, lm_idx, W, W32, lam, tau, allow_chol, lo, hi, st);
+    else if (sm > 75 * 1024)
+      e = launch_eig_class<512>(lsets, capacity, lm_idx, W, W32, lam, tau, allow_chol, lo, hi, st);
+    else
+      e = launch_eig_class<256>(lsets, capacity, lm_idx, W, W32, lam, tau, allow_chol, lo, hi, st);
     if (e != cudaSuccess) return e;
     lo = hi;
   }
