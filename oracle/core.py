@@ -4,16 +4,17 @@ TEST INFRASTRUCTURE ONLY -- see ``oracle/__init__.py``.
 
 A problem is a plain dict (built by ``nys_inputs``):
 
-    p        ODE order (1 or 2)
+    p        ODE order (1 or 2; 3 or 4 with tabulated coefficients)
     n, m     collocation points t_1..t_n (uniform on [t0, t1]) and landmarks
     t0, t1   interval
     sigma    RBF width: K(u, v) = exp(-(u - v)^2 / sigma^2)   (Section 3, RBF)
     gamma    regularisation constant
-    v        initial values v_1 = y(t_1), v_2 = y'(t_1); for bc = 'bvp' the boundary
-             values q_1 = y(t_1), q_n = y(t_n)
+    v        initial values v_k = y^(k-1)(t_1), k = 1..p; for bc = 'bvp' the boundary
+             values: y^(k)(t_1) for k < p/2, then y^(k)(t_n) for k < p/2
     bc       'ivp' (default): conditions y^(k-1)(t_1) = v_k, collocation rows 2..n
-             'bvp' (p = 2): y(t_1) = q_1, y(t_n) = q_n, collocation rows 2..n-1
-             (Appendix A.4, BVP case)
+             'bvp' (p = 2 or 4): y(t_1) = q_1, y(t_n) = q_n (Appendix A.4, BVP
+             case), and for p = 4 also y'(t_1), y'(t_n) (the form of Problem 16,
+             Appendix B.1); collocation rows 2..n-1
     kind     'lin'   : y^(p) + sum_k a_k y^(p-k) = c sin(omega t + phi0)
              'table' : y^(p) - sum_k f_k(t) y^(p-k) = r(t), f and r given on the grid
              'nl'    : y^(p) = P(y) - delta y^(p-1) [p = 2] + g cos(omega t),
@@ -70,20 +71,28 @@ def rbf(u, v, sigma):
 
 
 def rbf_du(u, v, sigma, ell):
-    """[nabla_ell^0 K](u, v) = d^ell K / du^ell for ell = 0, 1, 2.
+    """[nabla_ell^0 K](u, v) = d^ell K / du^ell for ell = 0..4.
 
     Section 3: nabla_1^0 K = -2(u - v)/sigma^2 K and
-    nabla_2^0 K = [4(u - v)^2/sigma^4 - 2/sigma^2] K.
+    nabla_2^0 K = [4(u - v)^2/sigma^4 - 2/sigma^2] K; the third and fourth
+    derivatives (higher-order ODEs, Problem 16) continue the same pattern, the
+    physicists' Hermite polynomials: d^ell/du^ell K = (-1/sigma)^ell H_ell(x) K,
+    x = (u - v)/sigma.
     """
     k = rbf(u, v, sigma)
     d = u - v
+    s2 = sigma ** 2
     if ell == 0:
         return k
     if ell == 1:
-        return -2.0 * d / sigma ** 2 * k
+        return -2.0 * d / s2 * k
     if ell == 2:
-        return (4.0 * d ** 2 / sigma ** 4 - 2.0 / sigma ** 2) * k
-    raise ValueError("derivative order > 2 is not part of the hot path")
+        return (4.0 * d ** 2 / s2 ** 2 - 2.0 / s2) * k
+    if ell == 3:
+        return (-8.0 * d ** 3 / s2 ** 3 + 12.0 * d / s2 ** 2) * k
+    if ell == 4:
+        return (16.0 * d ** 4 / s2 ** 4 - 48.0 * d ** 2 / s2 ** 3 + 12.0 / s2 ** 2) * k
+    raise ValueError("derivative order > 4 is not part of the hot path")
 
 
 # --------------------------------------------------------------------------
@@ -148,8 +157,8 @@ def is_bvp(prob):
     bc = prob.get("bc", "ivp")
     if bc not in ("ivp", "bvp"):
         raise ValueError("bc must be 'ivp' or 'bvp'")
-    if bc == "bvp" and prob["p"] != 2:
-        raise ValueError("the boundary value case is second order (Appendix A.4)")
+    if bc == "bvp" and prob["p"] not in (2, 4):
+        raise ValueError("boundary values: p = 2 (Appendix A.4) or p = 4 (Problem 16)")
     return bc == "bvp"
 
 
@@ -162,7 +171,9 @@ def condition_rows(prob, st):
     """Rows c_k of the conditions C x = v on x = (omega, b), and v.
 
     IVP (Lemma 1): c_k = [phi^(k-1)(t_1), [k == 1]], v_k = y^(k-1)(t_1).
-    BVP (Appendix A.4): c_1 = [phi(t_1), 1], c_2 = [phi(t_n), 1], v = (q_1, q_n).
+    BVP (Appendix A.4): c_1 = [phi(t_1), 1], c_2 = [phi(t_n), 1], v = (q_1, q_n);
+    for p = 4 (Problem 16) the rows [phi^(k)(t_1), [k == 0]], k = 0, 1, then
+    [phi^(k)(t_n), [k == 0]], k = 0, 1.
     """
     p = prob["p"]
     t, s, W = st["t"], st["s"], st["W"]
@@ -170,9 +181,11 @@ def condition_rows(prob, st):
     me = W.shape[0]
     C = np.zeros((p, me + 1))
     if is_bvp(prob):
-        C[0, :me] = features(t[:1], s, sigma, W, 0)[0]
-        C[1, :me] = features(t[-1:], s, sigma, W, 0)[0]
-        C[:, me] = 1.0
+        h = p // 2
+        for k in range(h):
+            C[k, :me] = features(t[:1], s, sigma, W, k)[0]
+            C[h + k, :me] = features(t[-1:], s, sigma, W, k)[0]
+        C[0, me] = C[h, me] = 1.0
     else:
         for k in range(p):
             C[k, :me] = features(t[:1], s, sigma, W, k)[0]

@@ -142,3 +142,48 @@ def test_problem_15_printed_accuracy():
     e = np.abs(sol["y"] - 0.5 / np.cosh(sol["t"]))
     for ours, paper in zip((e.mean(), np.sqrt((e ** 2).mean()), e.max()), printed):
         assert paper / 10 <= ours <= 2 * paper, (ours, paper)
+
+
+# ---- higher order (p = 3, 4; tabulated coefficients) -------------------------
+P16 = os.path.join(os.path.dirname(__file__), "golden", "paper_p16_B7.txt")
+
+
+def p16_problem():
+    """Problem 16: y'''' = 120 t on [-1, 1] with y, y' at both ends, as printed."""
+    row = [line.split() for line in open(P16) if line.strip() and not line.startswith("#")][0]
+    n, m, s2, gam = int(row[1]), int(row[2]), float(row[3]), float(row[4])
+    t = np.linspace(-1.0, 1.0, n)
+    prob = dict(p=4, n=n, m=m, t0=-1.0, t1=1.0, sigma=s2 ** 0.5, gamma=gam, v=[1.0, 5.0, 3.0, 5.0],
+                kind="table", f=[np.zeros(n)] * 4, r=120.0 * t, bc="bvp")
+    return prob, t ** 5 + 2, tuple(float(x) for x in row[5:8])
+
+
+def test_problem_16_printed_accuracy():
+    """Fourth order, two conditions at each end.  As for Problems 11-13 the paper
+    leaves the treatment of the numerically singular landmark kernel open; keeping
+    eigenpairs down to 1e-16 lambda_max (15 of 20) gives errors within [1/10, 2] x
+    the printed ones (ours ~5x smaller)."""
+    prob, exact, printed = p16_problem()
+    a = core.solve_linear(prob, tau=1e-16)
+    b = core.solve_linear_nullspace(prob, tau=1e-16)
+    e = np.abs(a["y"] - exact)
+    for ours, paper in zip((e.mean(), np.sqrt((e ** 2).mean()), e.max()), printed):
+        assert paper / 10 <= ours <= 2 * paper, (ours, paper)
+    assert np.max(np.abs(a["y"] - b["y"])) <= 1e-10 * np.max(np.abs(a["y"]))
+    assert np.max(np.abs(core.constraints(prob, a, a["omega"], a["b"]))) <= 1e-10
+
+
+@pytest.mark.parametrize("p,T,sigma,m,n,tol", [(3, 3.0, 1.0, 20, 300, 5e-5), (4, 2.0, 1.0, 16, 200, 1e-3)])
+def test_higher_order_ivp_closed_form(p, T, sigma, m, n, tol):
+    """y''' + y' = 0 and y'''' = y with the initial values of cos t: the fit follows
+    cos t and meets all p initial conditions."""
+    t = np.linspace(0.0, T, n)
+    z = np.zeros(n)
+    f = [z, -np.ones(n), z] if p == 3 else [z, z, z, np.ones(n)]
+    v = [1.0, 0.0, -1.0, 0.0][:p]
+    prob = dict(p=p, n=n, m=m, t0=0.0, t1=T, sigma=sigma, gamma=1e10, v=v, kind="table", f=f, r=z)
+    a = core.solve_linear(prob)
+    assert np.max(np.abs(a["y"] - np.cos(t))) <= tol
+    assert np.max(np.abs(core.constraints(prob, a, a["omega"], a["b"]))) <= 1e-9
+    b = core.solve_linear_nullspace(prob)
+    assert np.max(np.abs(a["y"] - b["y"])) <= 1e-9
