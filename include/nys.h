@@ -39,7 +39,8 @@ typedef enum {
   NYS_EINVAL = -1,      /* invalid argument (detail in nys_last_error)          */
   NYS_ENOMEM = -2,      /* device or pinned host allocation failed              */
   NYS_ECUDA = -3,       /* a CUDA runtime call failed                           */
-  NYS_ENOTSPD = -4,     /* per instance: projected Hessian not positive definite */
+  NYS_ENOTSPD = -4,     /* per instance: projected Hessian not positive definite
+                           (or fewer kept eigenpairs + 1 than conditions)       */
   NYS_ENOCONV = -5,     /* per instance: Newton iteration cap reached           */
   NYS_ENONFINITE = -6,  /* per instance: NaN/Inf in inputs or results           */
   NYS_ETIMEOUT = -7,    /* per instance: a bounded device wait gave up (the
@@ -73,10 +74,11 @@ typedef enum {
   /* initial values (Lemma 1): y(t_1) = v[0], y'(t_1) = v[1] (p = 2);
      collocation rows i = 2..n                                              */
   NYS_BC_IVP = 0,
-  /* boundary values of a second-order ODE (Appendix A.4, BVP case; for the
-     nonlinear kind in the Lagrangian of its Problem 15 example):
-     y(t_1) = v[0], y(t_n) = v[1]; collocation rows i = 2..n-1.  Needs p = 2;
-     nys_grad refuses such contexts.                                         */
+  /* boundary values (Appendix A.4, BVP case; for the nonlinear kind in the
+     Lagrangian of its Problem 15 example): p = 2: y(t_1) = v[0],
+     y(t_n) = v[1]; p = 4 (Problem 16): y(t_1) = v[0], y'(t_1) = v[1],
+     y(t_n) = v[2], y'(t_n) = v[3].  Collocation rows i = 2..n-1.  nys_grad
+     refuses such contexts.                                                   */
   NYS_BC_BVP = 1
 } nys_conditions;
 
@@ -84,14 +86,16 @@ typedef enum {
    i = 1..n.  Conditions per bc: by default at t_1, y(t_1) = v[0],
    y'(t_1) = v[1] (p = 2).                                                   */
 typedef struct {
-  int32_t p;                 /* ODE order, 1 or 2                                  */
+  int32_t p;                 /* ODE order, 1 or 2; 3 or 4 with kind TABLE and
+                                NYS_FP64 (higher-order case of Problem 16)         */
   int32_t n;                 /* collocation points, 3 <= n <= 2^24                 */
   int32_t m;                 /* landmarks, 2 <= m <= min(n, NYS_M_MAX)             */
   int32_t kind;              /* nys_coef_kind                                      */
   double t0, t1;             /* interval, t1 > t0                                  */
   double sigma;              /* RBF width in exp(-(u-v)^2/sigma^2), > 0            */
   double gamma;              /* regularisation constant, > 0                       */
-  double v[2];               /* initial (or boundary) values, see bc               */
+  double v[4];               /* initial values y^(k)(t_1), k < p, or boundary values
+                                (see bc); unused entries ignored                   */
   double c[8];               /* coefficients, layout per kind above                */
   const int32_t* landmarks;  /* host, optional: m increasing 0-based grid indices;
                                 NULL = evenly spaced, index round(j(n-1)/(m-1))    */
@@ -157,7 +161,8 @@ int32_t nys_assemble(nys_ctx* c, void* stream);
    coordinates instead (each row projected through W; FP64 only).  MIXED adds
    refine_steps residual passes.  x_out: device, batch x nys_x_stride(c)
    doubles, per instance [omega (m_eff, zero padded to m_max), b, lambda_1,
-   lambda_2].  status_out: device, batch int32 (NYS_OK / NYS_ENOTSPD /
+   lambda_2] (orders 3 and 4 report the first two of their p multipliers).
+   status_out: device, batch int32 (NYS_OK / NYS_ENOTSPD /
    NYS_ENONFINITE / NYS_EPRECISION).  Either pointer may be NULL.            */
 int32_t nys_solve(nys_ctx* c, void* stream, double* x_out, int32_t* status_out);
 
@@ -212,7 +217,8 @@ int32_t nys_newton(nys_ctx* c, void* stream, int32_t max_iter, double tol,
    grad_out: device, batch x 7 doubles (a_2 and y0' entries 0 when p = 1).
    Instances whose solve failed get NaN; the sigma entry is NaN when the
    landmark kernel was truncated (m_eff < m), where sigma also moves the
-   discarded eigenvectors.  Errors: NYS_EINVAL (NULL pointer, nonlinear batch),
+   discarded eigenvectors.  Errors: NYS_EINVAL (NULL pointer, nonlinear batch,
+   boundary values, order above 2),
    NYS_ESTATE (MIXED context, or no solve yet), NYS_ECUDA.                   */
 int32_t nys_grad(nys_ctx* c, void* stream, const double* obs_t, const int64_t* obs_off,
                  const double* dl_dy, double* grad_out);

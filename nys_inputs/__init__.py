@@ -25,7 +25,7 @@ SEED = 20251004
 GAMMA = 1e10
 
 _KEYS = {"cfg1": 1, "cfg2": 2, "m0": 10, "cfg3": 3, "cfg4": 4, "cfg5": 5, "small": 99, "trunc": 98,
-         "bvp": 11, "small_bvp": 97}
+         "bvp": 11, "small_bvp": 97, "small_higher": 96}
 
 
 def rng(name, sub=0):
@@ -175,6 +175,29 @@ def small_bvp(B=8, sub=0, n_choices=(3, 5, 37, 64, 129, 300), m_choices=(2, 3, 5
                         a=[float(g.uniform(0, 1)), float(g.uniform(-4, -1))],
                         c=float(g.uniform(-1, 1)), omega=float(g.uniform(0.5, 5)),
                         phi0=float(g.uniform(0, 3))))
+    return out
+
+
+def small_higher(B=8, sub=0, n_choices=(9, 37, 64, 129, 300), m_choices=(4, 7, 13, 20)):
+    """Small ragged third- and fourth-order instances with tabulated coefficients
+    f_k(t) = a_k + b_k sin(nu_k t) and forcing r(t) = c cos(omega t + phi0); the
+    fourth-order ones take initial or boundary values (y, y' at both ends)."""
+    g = rng("small_higher", sub)
+    out = []
+    for i in range(B):
+        p = int(g.choice(np.asarray((3, 4))))
+        n = int(g.choice(np.asarray(n_choices)))
+        m = int(min(g.choice(np.asarray(m_choices)), n))
+        T = float(g.uniform(0.5, 3))
+        t0 = float(g.uniform(-1, 1))
+        t = np.linspace(t0, t0 + T, n)
+        f = [g.uniform(-1, 1) + g.uniform(-0.5, 0.5) * np.sin(g.uniform(0.5, 3) * t)
+             for _ in range(p)]
+        r = g.uniform(-1, 1) * np.cos(g.uniform(0.5, 4) * t + g.uniform(0, 3))
+        out.append(dict(p=p, n=n, m=m, t0=t0, t1=t0 + T, sigma=float(T / m * g.uniform(1.5, 3)),
+                        gamma=float(10 ** g.uniform(4, 10)),
+                        bc="bvp" if (p == 4 and g.uniform() < 0.5) else "ivp",
+                        v=[float(x) for x in g.standard_normal(p)], kind="table", f=f, r=r))
     return out
 
 

@@ -22,7 +22,7 @@ NYS_M_MAX = 112
 class nys_instance(C.Structure):
     _fields_ = [("p", C.c_int32), ("n", C.c_int32), ("m", C.c_int32), ("kind", C.c_int32),
                 ("t0", C.c_double), ("t1", C.c_double), ("sigma", C.c_double),
-                ("gamma", C.c_double), ("v", C.c_double * 2), ("c", C.c_double * 8),
+                ("gamma", C.c_double), ("v", C.c_double * 4), ("c", C.c_double * 8),
                 ("landmarks", C.POINTER(C.c_int32)), ("coef_table", C.POINTER(C.c_double)),
                 ("bc", C.c_int32), ("reserved", C.c_int32)]
 

@@ -40,8 +40,9 @@ def pack_instances(problems):
         s.bc = _BC[q.get("bc", "ivp")]
         s.t0, s.t1 = float(q["t0"]), float(q["t1"])
         s.sigma, s.gamma = float(q["sigma"]), float(q["gamma"])
-        v = list(q["v"]) + [0.0] * (2 - len(q["v"]))
-        s.v[0], s.v[1] = float(v[0]), float(v[1])
+        v = list(q["v"]) + [0.0] * (4 - len(q["v"]))
+        for k in range(4):
+            s.v[k] = float(v[k])
         c = [0.0] * 8
         if q["kind"] == "lin":
             a = list(q["a"]) + [0.0] * (2 - len(q["a"]))

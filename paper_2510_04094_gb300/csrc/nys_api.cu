@@ -195,7 +195,9 @@ static double mod2pi(double x) {
 // Validate one instance.  Returns NYS_OK, NYS_EINVAL (message set) or
 // NYS_ENONFINITE (non-finite coefficient data: the instance is skipped).
 static int32_t check_instance(const nys_instance& q, int b) {
-  if (q.p != 1 && q.p != 2) return fail(NYS_EINVAL, "instance %d: p must be 1 or 2 (got %d)", b, q.p);
+  if (q.p < 1 || q.p > 4) return fail(NYS_EINVAL, "instance %d: p must be in 1..4 (got %d)", b, q.p);
+  if (q.p > 2 && q.kind != NYS_COEF_TABLE)
+    return fail(NYS_EINVAL, "instance %d: orders 3 and 4 need kind NYS_COEF_TABLE", b);
   if (q.n < 3 || q.n > (1 << 24)) return fail(NYS_EINVAL, "instance %d: n must be in [3, 2^24] (got %d)", b, q.n);
   if (q.m < 2 || q.m > NYS_M_MAX || q.m > q.n)
     return fail(NYS_EINVAL, "instance %d: m must be in [2, min(n, %d)] (got %d)", b, NYS_M_MAX, q.m);
@@ -211,8 +213,8 @@ static int32_t check_instance(const nys_instance& q, int b) {
   if (q.bc != NYS_BC_IVP && q.bc != NYS_BC_BVP)
     return fail(NYS_EINVAL, "instance %d: bc must be NYS_BC_IVP or NYS_BC_BVP (got %d)", b, q.bc);
   if (q.reserved != 0) return fail(NYS_EINVAL, "instance %d: reserved must be 0", b);
-  if (q.bc == NYS_BC_BVP && q.p != 2)
-    return fail(NYS_EINVAL, "instance %d: boundary values need a second-order ODE", b);
+  if (q.bc == NYS_BC_BVP && q.p != 2 && q.p != 4)
+    return fail(NYS_EINVAL, "instance %d: boundary values need order 2 or 4", b);
   if (q.landmarks) {
     for (int j = 0; j < q.m; ++j) {
       if (q.landmarks[j] < 0 || q.landmarks[j] >= q.n || (j > 0 && q.landmarks[j] <= q.landmarks[j - 1]))
@@ -243,8 +245,7 @@ static void fill_inst(nys_ctx* c, const nys_instance& s, Inst& I) {
   I.sigma = s.sigma;
   // eq32's sqrt(m) feature scale is the same problem with gamma -> m gamma
   I.gamma = c->opt.scale_sqrt_m ? s.gamma * s.m : s.gamma;
-  I.v[0] = s.v[0];
-  I.v[1] = (s.p == 2) ? s.v[1] : 0.0;
+  for (int k = 0; k < 4; ++k) I.v[k] = (k < s.p) ? s.v[k] : 0.0;
   for (int k = 0; k < 8; ++k) I.c[k] = s.c[k];
   if (s.p == 1 && s.kind == NYS_COEF_LIN) I.c[1] = 0.0;
   I.hs = I.h / s.sigma;
@@ -569,6 +570,11 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   }
   if (c->opt.refine_steps > 8) { delete c; return fail(NYS_EINVAL, "nys_setup: refine_steps > 8"); }
   c->fp32 = (c->opt.precision == NYS_MIXED);
+  for (int b = 0; b < batch && c->fp32; ++b)
+    if (q[b].p > 2) {
+      delete c;
+      return fail(NYS_EINVAL, "instance %d: orders 3 and 4 need precision NYS_FP64", b);
+    }
   for (int b = 0; b < batch; ++b) {
     c->m_max = std::max(c->m_max, std::max(2, q[b].m));
     c->p_max = std::max(c->p_max, q[b].p);
@@ -1007,8 +1013,10 @@ int32_t nys_grad(nys_ctx* c, void* stream, const double* obs_t, const int64_t* o
                  const double* dl_dy, double* grad_out) {
   if (!c || !obs_t || !obs_off || !dl_dy || !grad_out) return fail(NYS_EINVAL, "nys_grad: NULL argument");
   if (c->any_nl) return fail(NYS_EINVAL, "nys_grad: defined for linear (NYS_COEF_LIN) batches");
-  for (int b = 0; b < c->batch; ++b)
+  for (int b = 0; b < c->batch; ++b) {
     if (c->shape[b].bc != NYS_BC_IVP) return fail(NYS_EINVAL, "nys_grad: initial value problems only");
+    if (c->shape[b].p > 2) return fail(NYS_EINVAL, "nys_grad: orders 1 and 2 only");
+  }
   if (c->fp32) return fail(NYS_ESTATE, "nys_grad: needs a context created with precision NYS_FP64");
   if (!c->solved) return fail(NYS_ESTATE, "nys_grad: no solution yet");
   CK(launch_grad(c->inst.p, c->lset.p, c->W.p, (const double*)c->fac.p, c->facs, c->xs.p, c->zs.p,

@@ -37,7 +37,7 @@ k_assemble_f64(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   extern __shared__ double sm64[];
   __shared__ int s_item;
   __shared__ int s_idx[kMMax];
-  __shared__ double s_rc[kAsm64Rows][5];
+  __shared__ double s_rc[kAsm64Rows][7];   // A0..A4, w1, r
   __shared__ unsigned char s_pair[2 * kM2Max * (kM2Max + 1) / 2];
   const int tid = threadIdx.x;
   int cached_m2 = -1;
@@ -81,12 +81,11 @@ k_assemble_f64(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
       if (tid < kAsm64Rows) {
         const int i = base + tid;
         if (i < wk.r1) {
-          double f1, f2, rr;
-          coef_f(I, tab, i, f1, f2, rr);
-          if (I.kind == NYS_COEF_LIN) rr = lin_rhs_f64(I, i);
-          const RowCoef R = row_coef_from_f(I, f1, f2, rr);
-          s_rc[tid][0] = R.A0; s_rc[tid][1] = R.A1; s_rc[tid][2] = R.A2;
-          s_rc[tid][3] = R.w1; s_rc[tid][4] = R.rr;
+          const RowCoef4 R = row_coef_f64(I, tab, i);
+#pragma unroll
+          for (int q = 0; q < 5; ++q) s_rc[tid][q] = R.A[q];
+          s_rc[tid][5] = R.w1;
+          s_rc[tid][6] = R.rr;
         }
       }
       __syncthreads();
@@ -97,10 +96,10 @@ k_assemble_f64(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         if (i < wk.r1) {
           if (j < m) {
             const double x = (double)(i - s_idx[j]) * I.hs;
-            const double u = x * x;
-            val = exp(-u) * (s_rc[r][0] + s_rc[r][1] * x + s_rc[r][2] * u);
+            const double* A = s_rc[r];
+            val = exp(-x * x) * fma(x, fma(x, fma(x, fma(x, A[4], A[3]), A[2]), A[1]), A[0]);
           } else {
-            val = s_rc[r][3 + (j - m)];
+            val = s_rc[r][5 + (j - m)];
           }
         }
         psi[r * ld + j] = val;

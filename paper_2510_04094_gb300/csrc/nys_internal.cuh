@@ -39,7 +39,7 @@ struct Inst {
   int64_t y_off;       // Newton: auxiliary y_i (n-1 doubles) in yaux[]
   double t0, h;        // t_i (0-based i) = t0 + i h
   double sigma, gamma;
-  double v[2];
+  double v[4];         // condition values (p of them)
   double c[8];
   // derived constants (host-computed in FP64)
   double hs;           // h / sigma
@@ -206,6 +206,42 @@ __host__ __device__ __forceinline__ RowCoef row_coef_from_f(const Inst& I, doubl
 __device__ __forceinline__ double lin_rhs_f64(const Inst& I, int i) {
   double t = I.t0 + (double)i * I.h;
   return I.c[2] * sin(I.c[3] * t + I.c[4]);
+}
+
+// Operator coefficients of row i for the FP64 row pass, any order p <= 4:
+//   kappa_j(t_i) = exp(-x^2) (A0 + A1 x + A2 x^2 + A3 x^3 + A4 x^4),  x = (t_i - s_j)/sigma,
+// from the kernel's t-derivatives k^(l) = (-1/sigma)^l H_l(x) exp(-x^2) (physicists'
+// Hermite: H1 = 2x, H2 = 4x^2 - 2, H3 = 8x^3 - 12x, H4 = 16x^4 - 48x^2 + 12) and
+// kappa = k^(p) - sum_{k=1..p} f_k k^(p-k) (Section 3.1); w1 = -f_p multiplies b.
+struct RowCoef4 { double A[5], w1, rr; };
+
+__device__ __forceinline__ RowCoef4 row_coef_f64(const Inst& I, const double* tab, int i) {
+  double f[4] = {0.0, 0.0, 0.0, 0.0};
+  RowCoef4 R;
+  const int p = I.p;
+  if (I.kind == NYS_COEF_TABLE) {
+    const double* T = tab + I.tab_off;
+    for (int k = 0; k < p; ++k) f[k] = T[(int64_t)k * I.n + i];
+    R.rr = T[(int64_t)p * I.n + i];
+  } else {  // LIN (p <= 2): f_k = -a_k, r = c sin(omega t + phi0)
+    f[0] = -I.c[0];
+    if (p == 2) f[1] = -I.c[1];
+    R.rr = lin_rhs_f64(I, i);
+  }
+  double g[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // g_l = c_l (-1/sigma)^l, c_p = 1, c_{p-k} = -f_k
+  const double ms = -1.0 / I.sigma;
+  double pw = 1.0;
+  for (int l = 0; l <= p; ++l) {
+    g[l] = ((l == p) ? 1.0 : -f[p - l - 1]) * pw;
+    pw *= ms;
+  }
+  R.A[0] = g[0] - 2.0 * g[2] + 12.0 * g[4];
+  R.A[1] = 2.0 * g[1] - 12.0 * g[3];
+  R.A[2] = 4.0 * g[2] - 48.0 * g[4];
+  R.A[3] = 8.0 * g[3];
+  R.A[4] = 16.0 * g[4];
+  R.w1 = -f[p - 1];
+  return R;
 }
 
 __host__ __device__ __forceinline__ RowConst row_const(const Inst& I) {

@@ -130,6 +130,7 @@ extern "C" int32_t nys_solve_noalloc(const nys_instance* q, int32_t batch, doubl
     I.gamma = s.gamma;
     I.v[0] = s.v[0];
     I.v[1] = (s.p == 2) ? s.v[1] : 0.0;
+    I.v[2] = I.v[3] = 0.0;
     bool fin = std::isfinite(s.v[0]) && std::isfinite(I.v[1]);
     for (int k = 0; k < 8; ++k) {
       I.c[k] = s.c[k];

@@ -43,9 +43,11 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   // row through W, so the slots hold the Gram in omega coordinates.  The FP32
   // factor is too coarse there; the mixed path reports NYS_EPRECISION.
   const bool om = (LS.omode != 0);
+  // more conditions than unknowns (m_eff + 1 < p after truncation): no solution
   const int st0 = (st_init[b] != NYS_OK) ? st_init[b]
                   : (om && sizeof(T) == sizeof(float)) ? NYS_EPRECISION
-                  : (asm_err != nullptr && *asm_err != 0) ? NYS_ETIMEOUT : NYS_OK;
+                  : (asm_err != nullptr && *asm_err != 0) ? NYS_ETIMEOUT
+                  : (LS.m_eff + 1 < I.p) ? NYS_ENOTSPD : NYS_OK;
   if (st0 != NYS_OK) {  // no solution: zero x and z, report the status
     for (int k = threadIdx.x; k < XS; k += blockDim.x) xs[(int64_t)b * XS + k] = 0.0;
     for (int k = threadIdx.x; k < ZS; k += blockDim.x) zs[(int64_t)b * ZS + k] = 0.0;
@@ -66,14 +68,13 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   T* vec = Yb + 8 * m;                               // misc vectors
   T* g = vec;                                        // M1
   T* hb = g + M1;                                    // me
-  T* Vh = hb + M1;                                   // 2 x M1 Householder
-  T* c2 = Vh + 2 * M1;                               // M1 scratch
-  T* w = c2 + M1;                                    // M1 scratch
+  T* Vh = hb + M1;                                   // p x M1 Householder (p <= 4)
+  T* w = Vh + 4 * M1;                                // M1 scratch
   T* y = w + M1;                                     // M1
   T* red = y + M1;                                   // 40
   __shared__ int s_flag;
-  __shared__ T s_beta[2], s_R[4];
-  __shared__ double s_c[2][kM1Max];
+  __shared__ T s_beta[4], s_Rm[4][4];               // reflector scales, R (upper, p x p)
+  __shared__ double s_c[4][kM1Max];                 // condition rows, omega coordinates
 
   // 1. add the partial Grams of the row chunks into G (symmetric, full).  A slot
   //    holds [first column jlo (-1: omega coordinates, all me columns), count A,
@@ -190,68 +191,68 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     }
     if (threadIdx.x == 0) Hs[me * ldh + me] = (T)gamma * gbb;
   }
-  // 4. condition rows in omega coordinates (FP64): c_1 = [W k(t_1); 1] and
-  //    initial values (Lemma 1): c_2 = [W k'(t_1); 0], k_j(t_1) = exp(-x_j^2),
-  //    k'_j(t_1) = -2 x_j / sigma exp(-x_j^2), x_j = (t_1 - s_j) / sigma;
-  //    boundary values (Appendix A.4): c_2 = [W k(t_n); 1]
-  __shared__ double s_e[2][kMMax];
+  // 4. condition rows in omega coordinates (FP64), c_r = [W k^(d_r)(tau_r); [d_r == 0]]:
+  //    initial values (Lemma 1) tau_r = t_1, d_r = r; boundary values (Appendix A.4)
+  //    t_1 then t_n, d_r = 0 for p = 2, and d_r = 0, 1 at each end for p = 4
+  //    (Problem 16).  k^(d)(tau) = (-1/sigma)^d H_d(x) exp(-x^2), x = (tau - s_j)/sigma.
+  __shared__ double s_e[4][kMMax];
   const bool bvp = (I.bc == NYS_BC_BVP);
-  for (int j = threadIdx.x; j < m; j += blockDim.x) {
-    const double x = (double)(0 - lm_idx[I.lm_off + j]) * I.hs;
-    const double e = exp(-x * x);
-    s_e[0][j] = e;
-    if (bvp) {
-      const double xn = (double)(I.n - 1 - lm_idx[I.lm_off + j]) * I.hs;
-      s_e[1][j] = exp(-xn * xn);
-    } else {
-      s_e[1][j] = (-2.0 * x / I.sigma) * e;
-    }
+  const int hp = bvp ? p / 2 : p;                       // conditions at t_1
+  for (int e = threadIdx.x; e < p * m; e += blockDim.x) {
+    const int r = e / m, j = e - r * m;
+    const int at_n = (r >= hp), d = at_n ? r - hp : r;
+    const double x = (double)((at_n ? I.n - 1 : 0) - lm_idx[I.lm_off + j]) * I.hs;
+    const double x2 = x * x;
+    double H;                                           // physicists' Hermite H_d(x)
+    if (d == 0) H = 1.0;
+    else if (d == 1) H = 2.0 * x;
+    else if (d == 2) H = 4.0 * x2 - 2.0;
+    else H = (8.0 * x2 - 12.0) * x;
+    double sc = 1.0;                                    // (-1/sigma)^d
+    for (int q = 0; q < d; ++q) sc *= -1.0 / I.sigma;
+    s_e[r][j] = sc * H * exp(-x2);
   }
   __syncthreads();
   for (int k = warp; k < M1; k += nw) {   // a warp per row of W (coalesced)
-    double s0 = 0.0, s1 = 0.0;
+    double sr[4] = {0.0, 0.0, 0.0, 0.0};
     if (k < me) {
       for (int j = lane; j < m; j += 32) {
-        s0 += W[k * m + j] * s_e[0][j];
-        s1 += W[k * m + j] * s_e[1][j];
+        const double wkj = W[k * m + j];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if (r < p) sr[r] += wkj * s_e[r][j];
       }
-      for (int o = 16; o > 0; o >>= 1) {
-        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        for (int o = 16; o > 0; o >>= 1) sr[r] += __shfl_xor_sync(0xffffffffu, sr[r], o);
     } else {
-      s0 = 1.0;
-      s1 = bvp ? 1.0 : 0.0;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) sr[r] = (r < p && (r == 0 || r == hp)) ? 1.0 : 0.0;
     }
     if (lane == 0) {
-      s_c[0][k] = s0;
-      s_c[1][k] = s1;
-      cws[(int64_t)b * 2 * M1S + k] = s0;
-      cws[(int64_t)b * 2 * M1S + M1S + k] = s1;
+      for (int r = 0; r < p; ++r) s_c[r][k] = sr[r];
+      // rows 0, 1 for the refinement and gradient passes (orders <= 2)
+      cws[(int64_t)b * 2 * M1S + k] = sr[0];
+      cws[(int64_t)b * 2 * M1S + M1S + k] = sr[1];
     }
   }
   __syncthreads();
-  // 5. Householder reflectors of C^T (M1 x p)
-  for (int k = threadIdx.x; k < M1; k += blockDim.x) {
-    w[k] = (T)s_c[0][k];
-    c2[k] = (T)s_c[1][k];
+  // 5. Householder QR of C^T (M1 x p): column k (in the 8-row block buffer, free
+  //    now) takes the reflectors 0..k-1, gives R[0..k-1][k], then its reflector
+  T* cr = Yb;                                           // p x M1
+  for (int e = threadIdx.x; e < p * M1; e += blockDim.x) {
+    const int k = e / M1, i = e - k * M1;
+    cr[e] = (T)s_c[k][i];
+    Vh[e] = T(0);
   }
   __syncthreads();
-  {
-    T bt;
-    const T r00 = house(w, Vh, M1, &s_beta[0], red);
-    bt = s_beta[0];
-    if (threadIdx.x == 0) s_R[0] = r00;
+  for (int k = 0; k < p; ++k) {
+    for (int j = 0; j < k; ++j) apply_house_vec(cr + k * M1, M1, Vh + j * M1, s_beta[j], red);
+    if (threadIdx.x == 0)
+      for (int j = 0; j < k; ++j) s_Rm[j][k] = cr[k * M1 + j];
+    const T rkk = house(cr + k * M1 + k, Vh + k * M1 + k, M1 - k, &s_beta[k], red);
+    if (threadIdx.x == 0) s_Rm[k][k] = rkk;
     __syncthreads();
-    if (p == 2) {
-      apply_house_vec(c2, M1, Vh, bt, red);
-      if (threadIdx.x == 0) s_R[1] = c2[0];
-      for (int k = threadIdx.x; k < M1; k += blockDim.x) Vh[M1 + k] = T(0);
-      __syncthreads();
-      const T r11 = house(c2 + 1, Vh + M1 + 1, M1 - 1, &s_beta[1], red);
-      if (threadIdx.x == 0) s_R[2] = r11;
-      __syncthreads();
-    }
   }
   // 6. H' = Q^T H Q, g' = Q^T g
   // (reflector k has zeros in its first k entries; apply it to the full matrix
@@ -260,20 +261,30 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     apply_house_sym(Hs, ldh, M1, Vh + k * M1, s_beta[k], w, red);
     apply_house_vec(g, M1, Vh + k * M1, s_beta[k], red);
   }
-  // store the first p rows of H' before the Cholesky overwrites the block
+  // the stored factor (orders <= 2: refinement and gradient): the first p rows of
+  // H', the reflectors and R
   T* facb = fac_all + (int64_t)b * facs;
   FacView<T> F = fac_view(facb, M1);
-  for (int e = threadIdx.x; e < p * M1; e += blockDim.x) {
-    const int k = e / M1, j = e - k * M1;
-    F.H1[k * M1 + j] = Hs[k * ldh + j];
-    F.V[k * M1 + j] = Vh[k * M1 + j];
+  if (p <= 2) {
+    for (int e = threadIdx.x; e < p * M1; e += blockDim.x) {
+      const int k = e / M1, j = e - k * M1;
+      F.H1[k * M1 + j] = Hs[k * ldh + j];
+      F.V[k * M1 + j] = Vh[k * M1 + j];
+    }
+    if (threadIdx.x < 2) F.beta[threadIdx.x] = (threadIdx.x < p) ? s_beta[threadIdx.x] : T(0);
+    if (threadIdx.x == 0) {
+      F.R[0] = s_Rm[0][0];
+      F.R[1] = (p == 2) ? s_Rm[0][1] : T(0);
+      F.R[2] = (p == 2) ? s_Rm[1][1] : T(0);
+    }
   }
-  if (threadIdx.x < 2) F.beta[threadIdx.x] = (threadIdx.x < p) ? s_beta[threadIdx.x] : T(0);
-  if (threadIdx.x < 3) F.R[threadIdx.x] = s_R[threadIdx.x];
   // 7. y1 = R^{-T} v ; rhs2 = g'[p:] - H'[p:, :p] y1
   if (threadIdx.x == 0) {
-    y[0] = (T)I.v[0] / s_R[0];
-    if (p == 2) y[1] = ((T)I.v[1] - s_R[1] * y[0]) / s_R[2];
+    for (int k = 0; k < p; ++k) {
+      T sv = (T)I.v[k];
+      for (int j = 0; j < k; ++j) sv -= s_Rm[j][k] * y[j];
+      y[k] = sv / s_Rm[k][k];
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < N2; i += blockDim.x) {
@@ -282,24 +293,26 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     y[p + i] = s;
   }
   __syncthreads();
-  // 8. Cholesky of H'_22 and solve
+  // 8. Cholesky of H'_22 and solve (rows 0..p-1 of H' stay as they are)
   T* A22 = Hs + p * ldh + p;
   const bool ok = cta_cholesky(A22, ldh, N2, &s_flag);
   cta_chol_solve(A22, ldh, N2, y + p);
-  for (int e = threadIdx.x; e < N2 * N2; e += blockDim.x) {
-    const int i = e / N2, j = e - i * N2;
-    F.L[i * N2 + j] = (j <= i) ? A22[i * ldh + j] : T(0);
+  if (p <= 2) {
+    for (int e = threadIdx.x; e < N2 * N2; e += blockDim.x) {
+      const int i = e / N2, j = e - i * N2;
+      F.L[i * N2 + j] = (j <= i) ? A22[i * ldh + j] : T(0);
+    }
   }
   // 9. lambda = R^{-1}(g'[:p] - H'[:p, :] y)
-  const T q0 = cta_dot(F.H1, y, M1, red);
-  const T q1 = (p == 2) ? cta_dot(F.H1 + M1, y, M1, red) : T(0);
-  double lam0 = 0.0, lam1 = 0.0;
-  if (p == 2) {
-    lam1 = (double)((g[1] - q1) / s_R[2]);
-    lam0 = (double)((g[0] - q0 - s_R[1] * (T)lam1) / s_R[0]);
-  } else {
-    lam0 = (double)((g[0] - q0) / s_R[0]);
+  T qk[4];
+  for (int k = 0; k < p; ++k) qk[k] = cta_dot(Hs + k * ldh, y, M1, red);
+  double lam[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k = p - 1; k >= 0; --k) {
+    T sv = g[k] - qk[k];
+    for (int j = k + 1; j < p; ++j) sv -= s_Rm[k][j] * (T)lam[j];
+    lam[k] = (double)(sv / s_Rm[k][k]);
   }
+  const double lam0 = lam[0], lam1 = lam[1];
   // 10. x = Q y
   for (int k = p - 1; k >= 0; --k) apply_house_vec(y, M1, Vh + k * M1, s_beta[k], red);
   double* xb = xs + (int64_t)b * XS;
@@ -307,8 +320,8 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     double val = 0.0;
     if (k < me) val = (double)y[k];
     else if (k == XS - 3) val = (double)y[me];
-    else if (k == XS - 2) val = lam0;
-    else if (k == XS - 1) val = (p == 2) ? lam1 : 0.0;
+    else if (k == XS - 2) val = lam0;                 // the first two multipliers
+    else if (k == XS - 1) val = (p >= 2) ? lam1 : 0.0;
     xb[k] = val;
   }
   __syncthreads();
@@ -325,7 +338,9 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   }
   if (threadIdx.x == 0) {
     int st = ok ? NYS_OK : NYS_ENOTSPD;
-    if (ok && !(isfinite(lam0) && isfinite(lam1) && isfinite((double)y[me]))) st = NYS_ENONFINITE;
+    bool fin = isfinite((double)y[me]);
+    for (int k = 0; k < p; ++k) fin = fin && isfinite(lam[k]);
+    if (ok && !fin) st = NYS_ENONFINITE;
     st_all[b] = st;
   }
 }

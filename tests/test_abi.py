@@ -39,10 +39,11 @@ def test_library_exports_every_declared_symbol(abi):
 
 
 def test_struct_layout_matches_header(abi):
-    assert C.sizeof(abi.nys_instance) == 16 + 8 * 4 + 16 + 64 + 16 + 8
+    assert C.sizeof(abi.nys_instance) == 16 + 8 * 4 + 32 + 64 + 16 + 8
     assert C.sizeof(abi.nys_options) == 24
-    assert abi.nys_instance.t0.offset == 16 and abi.nys_instance.landmarks.offset == 128
-    assert abi.nys_instance.bc.offset == 144 and abi.nys_instance.reserved.offset == 148
+    assert abi.nys_instance.t0.offset == 16 and abi.nys_instance.c.offset == 80
+    assert abi.nys_instance.landmarks.offset == 144
+    assert abi.nys_instance.bc.offset == 160 and abi.nys_instance.reserved.offset == 164
 
 
 def _one(**kw):
