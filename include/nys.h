@@ -89,7 +89,8 @@ typedef struct {
   int32_t p;                 /* ODE order, 1 or 2; 3 or 4 with kind TABLE and
                                 NYS_FP64 (higher-order case of Problem 16)         */
   int32_t n;                 /* collocation points, 3 <= n <= 2^24                 */
-  int32_t m;                 /* landmarks, 2 <= m <= min(n, NYS_M_MAX)             */
+  int32_t m;                 /* landmarks, 2 <= m <= min(n, NYS_M_MAX); above
+                                NYS_M_MAX_MIXED only linear kinds, NYS_FP64     */
   int32_t kind;              /* nys_coef_kind                                      */
   double t0, t1;             /* interval, t1 > t0                                  */
   double sigma;              /* RBF width in exp(-(u-v)^2/sigma^2), > 0            */
@@ -104,7 +105,9 @@ typedef struct {
   int32_t reserved;          /* must be 0                                          */
 } nys_instance;
 
-#define NYS_M_MAX 112
+#define NYS_M_MAX 224        /* landmarks per instance (FP64 linear solves)      */
+#define NYS_M_MAX_MIXED 112  /* landmarks for MIXED, Newton, gradients and
+                                nys_solve_noalloc                                  */
 
 typedef struct {
   int32_t precision;     /* nys_precision.  MIXED: FP32 assembly and FP32 factor,
@@ -218,7 +221,7 @@ int32_t nys_newton(nys_ctx* c, void* stream, int32_t max_iter, double tol,
    Instances whose solve failed get NaN; the sigma entry is NaN when the
    landmark kernel was truncated (m_eff < m), where sigma also moves the
    discarded eigenvectors.  Errors: NYS_EINVAL (NULL pointer, nonlinear batch,
-   boundary values, order above 2),
+   boundary values, order above 2, m above NYS_M_MAX_MIXED),
    NYS_ESTATE (MIXED context, or no solve yet), NYS_ECUDA.                   */
 int32_t nys_grad(nys_ctx* c, void* stream, const double* obs_t, const int64_t* obs_off,
                  const double* dl_dy, double* grad_out);

@@ -25,7 +25,8 @@ SEED = 20251004
 GAMMA = 1e10
 
 _KEYS = {"cfg1": 1, "cfg2": 2, "m0": 10, "cfg3": 3, "cfg4": 4, "cfg5": 5, "small": 99, "trunc": 98,
-         "bvp": 11, "small_bvp": 97, "small_higher": 96}
+         "bvp": 11, "small_bvp": 97, "small_higher": 96,
+         "big_m": 95}
 
 
 def rng(name, sub=0):
@@ -199,6 +200,65 @@ def small_higher(B=8, sub=0, n_choices=(9, 37, 64, 129, 300), m_choices=(4, 7, 1
                         bc="bvp" if (p == 4 and g.uniform() < 0.5) else "ivp",
                         v=[float(x) for x in g.standard_normal(p)], kind="table", f=f, r=r))
     return out
+
+
+def big_m(B=6, sub=0, n_choices=(300, 701, 1500, 3000), m_choices=(113, 128, 150, 200, 224)):
+    """Ragged instances with more landmarks than the shared-memory kernels hold
+    (m > 112): orders 1, 2 and 4, constant or tabulated coefficients, initial or
+    boundary values, kernel widths from well- to ill-conditioned landmark kernels."""
+    g = rng("big_m", sub)
+    out = []
+    for i in range(B):
+        n = int(g.choice(np.asarray(n_choices)))
+        m = int(min(g.choice(np.asarray(m_choices)), n))
+        p = int(g.choice(np.asarray((1, 2, 2, 4))))
+        T = float(g.uniform(2, 20))
+        t0 = float(g.uniform(-1, 1))
+        sigma = float(T / m * g.uniform(1.0, 4.0))
+        bc = "bvp" if (p in (2, 4) and g.uniform() < 0.3) else "ivp"
+        q = dict(p=p, n=n, m=m, t0=t0, t1=t0 + T, sigma=sigma, gamma=float(10 ** g.uniform(5, 9)),
+                 bc=bc, v=[float(x) for x in g.standard_normal(p)])
+        if p == 4 or g.uniform() < 0.3:
+            t = np.linspace(t0, t0 + T, n)
+            q.update(kind="table",
+                     f=[g.uniform(-1, 1) + g.uniform(-0.5, 0.5) * np.sin(g.uniform(0.2, 1) * t)
+                        for _ in range(p)],
+                     r=g.uniform(-1, 1) * np.cos(g.uniform(0.2, 2) * t + g.uniform(0, 3)))
+        else:
+            q.update(kind="lin", a=[float(g.uniform(0, 1)), float(g.uniform(1, 4))][:p],
+                     c=float(g.uniform(-1, 1)), omega=float(g.uniform(0.2, 2)),
+                     phi0=float(g.uniform(0, 3)))
+        out.append(q)
+    return out
+
+
+def long_time(name):
+    """Long-time integration workloads at the sizes of the paper's Table 12 (t up to
+    100, n = 2e4 - 5e4, m = 100 - 200, gamma = 1e7), on Problems 3, 7, 8 and 9 of
+    Appendix A.6, written as constant-coefficient instances:
+      P3: y' + 1000 y = 1000 sin t + cos t, y(0) = 0, sigma^2 = 10, m = 200;
+      P7: y'' + 0.3 y' + y = 1, y(0) = y'(0) = 0, sigma^2 = 1, m = 100;
+      P8: y'' + 36 y = 0, y(0) = -1/2, y'(0) = 1, t in [0, 50], n = 2e4, m = 200;
+      P9: y'' + 4 y' + 4 y = 0, y(0) = y'(0) = 1, sigma^2 = 1, m = 200.
+    Returns the problem dict and its closed-form solution."""
+    if name == "P3":
+        return (dict(p=1, n=50000, m=200, t0=0.0, t1=100.0, sigma=10 ** 0.5, gamma=1e7, v=[0.0],
+                     kind="lin", a=[1000.0], c=float(np.hypot(1000.0, 1.0)), omega=1.0,
+                     phi0=float(np.arctan2(1.0, 1000.0))), lambda t: np.sin(t))
+    if name == "P7":
+        w = np.sqrt(1 - 0.15 ** 2)
+        return (dict(p=2, n=50000, m=100, t0=0.0, t1=100.0, sigma=1.0, gamma=1e7, v=[0.0, 0.0],
+                     kind="lin", a=[0.3, 1.0], c=1.0, omega=0.0, phi0=float(np.pi / 2)),
+                lambda t: 1 - np.exp(-0.15 * t) * (np.cos(w * t) + 0.15 / w * np.sin(w * t)))
+    if name == "P8":
+        return (dict(p=2, n=20000, m=200, t0=0.0, t1=50.0, sigma=1.0, gamma=1e7, v=[-0.5, 1.0],
+                     kind="lin", a=[0.0, 36.0], c=0.0, omega=0.0, phi0=0.0),
+                lambda t: -0.5 * np.cos(6 * t) + np.sin(6 * t) / 6)
+    if name == "P9":
+        return (dict(p=2, n=50000, m=200, t0=0.0, t1=100.0, sigma=1.0, gamma=1e7, v=[1.0, 1.0],
+                     kind="lin", a=[4.0, 4.0], c=0.0, omega=0.0, phi0=0.0),
+                lambda t: (1 + 3 * t) * np.exp(-2 * t))
+    raise KeyError(name)
 
 
 def small_linear(B=8, name="small", sub=0, n_choices=(37, 64, 129, 300), m_choices=(5, 8, 13, 20),

@@ -16,7 +16,8 @@ NYS_FP64, NYS_MIXED = 0, 1
 NYS_ASM_AUTO, NYS_ASM_SIMT, NYS_ASM_TUNE = 0, 1, 2
 NYS_COEF_TABLE, NYS_COEF_LIN, NYS_COEF_POLY_NL = 0, 1, 2
 NYS_BC_IVP, NYS_BC_BVP = 0, 1
-NYS_M_MAX = 112
+NYS_M_MAX = 224
+NYS_M_MAX_MIXED = 112
 
 
 class nys_instance(C.Structure):

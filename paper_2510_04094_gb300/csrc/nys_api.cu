@@ -16,22 +16,24 @@ namespace nys {
 // kernel launchers (defined in the other translation units)
 cudaError_t launch_setup(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
                          double* lam, float* lag, double tau, int m_max, cudaStream_t st,
-                         int allow_chol, const int* m_bounds, int nclass);
+                         int allow_chol, const int* m_bounds, int nclass,
+                         BigSet big = BigSet());
 cudaError_t launch_lag(const Lset* lsets, int capacity, float* lag, cudaStream_t st);
 cudaError_t launch_eig(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
                        double* lam, double tau, int m_max, cudaStream_t st, int allow_chol,
-                       const int* m_bounds, int nclass);
+                       const int* m_bounds, int nclass, BigSet big = BigSet());
 cudaError_t launch_assemble(bool fp32, const Inst* insts, const Lset* lsets, const float* lag,
                             const double* W, const Work* work, int nwork, int* counter,
                             const int32_t* lm, const double* tab, double* part,
                             const int64_t* slot_off, int m_max, int k_max, int num_sms,
-                            cudaStream_t st, int asm_kind, int32_t* err);
+                            cudaStream_t st, int asm_kind, int32_t* err,
+                            BigSet big = BigSet());
 cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const double* W,
                          const float* W32, const double* part, const int64_t* slot_off,
                          const int32_t* lm, void* fac, int64_t facs, double* xs, double* zs,
                          double* cws, int XS, int ZS, int M1S, const int32_t* st_init,
                          int32_t* st, double gamma_scale, int batch, int m_max, cudaStream_t s,
-                         const int32_t* asm_err);
+                         const int32_t* asm_err, BigSet big = BigSet());
 cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W, const float* lag,
                           const Work* work, int nwork, int* counter, const int32_t* lm,
                           const double* tab,
@@ -44,6 +46,8 @@ cudaError_t launch_eval(const Inst* insts, const double* zs, int ZS, const int32
                         cudaStream_t s);
 
 int64_t fac_elems(int m_max);
+size_t setup_ws_doubles();
+size_t solve_ws_doubles();
 size_t grad_adj_stride(int ZS);
 cudaError_t launch_grad(const Inst* insts, const Lset* lsets, const double* W, const double* fac,
                         int64_t facs, const double* xs, const double* zs, const int32_t* lm, int XS,
@@ -156,6 +160,19 @@ struct nys_ctx {
   DBuf<float> lag;
   DBuf<double> lam;
   DBuf<unsigned char> fac;
+  // instances with m > kMMax: ids and their global factor / solve workspace
+  DBuf<int32_t> big_ids;
+  DBuf<double> big_ws;
+  int nbig = 0;
+  int64_t big_stride = 0;
+  BigSet bigset() const {
+    BigSet g;
+    g.ids = big_ids.p;
+    g.n = nbig;
+    g.ws = big_ws.p;
+    g.stride = big_stride;
+    return g;
+  }
   DBuf<double> xs, zs, dzs, cws;
   DBuf<int32_t> st, stinit, counter, err;
   // Newton state
@@ -407,7 +424,7 @@ static int32_t repack_same_sets(nys_ctx* c, const nys_instance* q) {
 static cudaError_t enqueue_factor(nys_ctx* c, cudaStream_t s) {
   return launch_setup(c->lset.p, c->batch, c->lm.p, c->W.p, c->W32.p, c->lam.p, c->lag.p,
                       c->opt.eig_tau > 0 ? c->opt.eig_tau : 1e-12, c->m_max, s, c->fp32 ? 0 : 1,
-                      c->eig_bounds.data(), (int)c->eig_bounds.size());
+                      c->eig_bounds.data(), (int)c->eig_bounds.size(), c->bigset());
 }
 
 // The lag tables (read by the row passes) go on the caller's stream; the
@@ -420,7 +437,7 @@ static cudaError_t fork_factor(nys_ctx* c, cudaStream_t s) {
   if (e == cudaSuccess)
     e = launch_eig(c->lset.p, c->batch, c->lm.p, c->W.p, c->W32.p, c->lam.p,
                    c->opt.eig_tau > 0 ? c->opt.eig_tau : 1e-12, c->m_max, c->side,
-                   c->fp32 ? 0 : 1, c->eig_bounds.data(), (int)c->eig_bounds.size());
+                   c->fp32 ? 0 : 1, c->eig_bounds.data(), (int)c->eig_bounds.size(), c->bigset());
   if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
   return e;
 }
@@ -512,8 +529,15 @@ static int64_t asm_layout(nys_ctx* c, int64_t rpi, std::vector<Work>& wl, std::v
   int slot = 0;
   for (int b = 0; b < c->batch; ++b) {
     const int nrows = collocation_rows(c->shape[b]);
-    const int chunks = (int)std::max<int64_t>(1, (nrows + rpi - 1) / rpi);
     const int M2 = c->shape[b].m + 2;
+    // a Gram of more than kMMax + 2 columns: parts of at most kAsm64Span packed
+    // entries per work item, and chunks of at least 512 rows (the slots of
+    // these instances are summed by a separate pass)
+    const bool bigm = c->shape[b].m > kMMax;
+    const int64_t Elin = (int64_t)M2 * (M2 + 1) / 2;
+    const int parts = bigm ? (int)((Elin + kAsm64Span - 1) / kAsm64Span) : 1;
+    const int64_t rpb = bigm ? std::max<int64_t>(rpi, 512) : rpi;
+    const int chunks = (int)std::max<int64_t>(1, (nrows + rpb - 1) / rpb);
     // linear: [first landmark, count] + packed Gram over m + 2 columns;
     // Newton: packed Gram over m + 1 columns, two (m+1)-vectors, two scalars
     const int64_t E = std::max<int64_t>((int64_t)M2 * (M2 + 1) / 2 + 2,
@@ -521,21 +545,29 @@ static int64_t asm_layout(nys_ctx* c, int64_t rpi, std::vector<Work>& wl, std::v
     c->h_inst[b].slot_begin = slot;
     c->h_inst[b].slot_count = chunks;
     for (int k = 0; k < chunks; ++k) {
-      Work w;
-      w.inst = b;
-      w.r0 = 1 + (int)((int64_t)nrows * k / chunks);
-      w.r1 = 1 + (int)((int64_t)nrows * (k + 1) / chunks);
-      w.slot = slot++;
-      wl.push_back(w);
+      for (int pt = 0; pt < parts; ++pt) {
+        Work w;
+        w.inst = b;
+        w.r0 = 1 + (int)((int64_t)nrows * k / chunks);
+        w.r1 = 1 + (int)((int64_t)nrows * (k + 1) / chunks);
+        w.slot = slot;
+        w.e0 = bigm ? (int)(Elin * pt / parts) : 0;
+        w.e1 = bigm ? (int)(Elin * (pt + 1) / parts) : INT32_MAX;
+        wl.push_back(w);
+      }
+      ++slot;
       soff.push_back(poff);
       poff += E;
     }
   }
   const std::vector<nys_instance>& q = c->shape;
+  auto cost = [&](const Work& a) {
+    const double M2 = q[a.inst].m + 2;
+    const double ent = std::min(M2 * (M2 + 1) / 2, (double)a.e1) - a.e0;
+    return (double)(a.r1 - a.r0) * ent;
+  };
   std::stable_sort(wl.begin(), wl.end(), [&](const Work& a, const Work& b2) {
-    const double ca = (double)(a.r1 - a.r0) * (q[a.inst].m + 2) * (q[a.inst].m + 2);
-    const double cb = (double)(b2.r1 - b2.r0) * (q[b2.inst].m + 2) * (q[b2.inst].m + 2);
-    return ca > cb;
+    return cost(a) > cost(b2);
   });
   return poff;
 }
@@ -575,6 +607,16 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
       delete c;
       return fail(NYS_EINVAL, "instance %d: orders 3 and 4 need precision NYS_FP64", b);
     }
+  for (int b = 0; b < batch; ++b) {
+    if (q[b].m <= NYS_M_MAX_MIXED || q[b].m > NYS_M_MAX) continue;
+    const char* why = c->fp32 ? "precision NYS_FP64"
+                      : (q[b].kind == NYS_COEF_POLY_NL) ? "a linear kind (Newton takes m <= NYS_M_MAX_MIXED)"
+                      : nullptr;
+    if (why) {
+      delete c;
+      return fail(NYS_EINVAL, "instance %d: m > %d needs %s", b, NYS_M_MAX_MIXED, why);
+    }
+  }
   for (int b = 0; b < batch; ++b) {
     c->m_max = std::max(c->m_max, std::max(2, q[b].m));
     c->p_max = std::max(c->p_max, q[b].p);
@@ -655,6 +697,8 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
         w.r0 = 1 + (int)((int64_t)nrows * k / chunks);
         w.r1 = 1 + (int)((int64_t)nrows * (k + 1) / chunks);
         w.slot = slot++;
+        w.e0 = 0;
+        w.e1 = INT32_MAX;
         rwl.push_back(w);
         soff.push_back(poff);
         poff += std::max(q[b].m + 1, 8);   // refinement: m + 1; gradient: 5
@@ -698,6 +742,20 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   if (c->fp32) A(c->lag.alloc((size_t)c->lag_floats));
   A(c->lam.alloc((size_t)batch * NYS_M_MAX));
   A(c->fac.alloc((size_t)batch * c->facs * (c->any_nl ? sizeof(double) : es)));
+  {
+    std::vector<int32_t> ids;
+    for (int b = 0; b < batch; ++b)
+      if (q[b].m > kMMax) ids.push_back(b);
+    c->nbig = (int)ids.size();
+    if (c->nbig > 0) {
+      c->big_stride = (int64_t)std::max(setup_ws_doubles(), solve_ws_doubles());
+      c->big_stride = (c->big_stride + 31) / 32 * 32;
+      A(c->big_ids.alloc(ids.size()));
+      A(c->big_ws.alloc((size_t)c->nbig * c->big_stride));
+      if (e == cudaSuccess)
+        A(cudaMemcpy(c->big_ids.p, ids.data(), sizeof(int32_t) * ids.size(), cudaMemcpyHostToDevice));
+    }
+  }
   A(c->xs.alloc((size_t)batch * c->XS));
   A(c->zs.alloc((size_t)batch * c->ZS));
   A(c->dzs.alloc((size_t)batch * c->ZS));
@@ -804,7 +862,7 @@ static int32_t tune_assembly(nys_ctx* c, cudaStream_t s) {
         CK(cudaEventRecord(e0, s));
         CK(launch_assemble(c->fp32, c->inst.p, c->lset.p, c->lag.p, c->W.p, c->work.p, c->nwork,
                            c->counter.p, c->lm.p, c->tab.p, c->part.p, c->slot_off.p, c->m_max,
-                           c->k_max, c->num_sms, s, kinds[kk], c->err.p));
+                           c->k_max, c->num_sms, s, kinds[kk], c->err.p, c->bigset()));
         CK(cudaEventRecord(e1, s));
         CK(cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -845,7 +903,8 @@ int32_t nys_assemble(nys_ctx* c, void* stream) {
   }
   CK(launch_assemble(c->fp32, c->inst.p, c->lset.p, c->lag.p, c->W.p, c->work.p,
                      c->nwork, c->counter.p, c->lm.p, c->tab.p, c->part.p, c->slot_off.p, c->m_max,
-                     c->k_max, c->num_sms, (cudaStream_t)stream, c->opt.assembly, c->err.p));
+                     c->k_max, c->num_sms, (cudaStream_t)stream, c->opt.assembly, c->err.p,
+                     c->bigset()));
   c->assembled = true;
   return NYS_OK;
 }
@@ -855,7 +914,7 @@ static int32_t solve_impl(nys_ctx* c, cudaStream_t s, double* x_out, int32_t* st
   CK(launch_solve(c->fp32, c->inst.p, c->lset.p, c->W.p, c->W32.p, c->part.p, c->slot_off.p,
                   c->lm.p, c->fac.p, c->facs, c->xs.p, c->zs.p, c->cws.p, c->XS, c->ZS, c->M1S,
                   c->stinit.p, c->st.p, gscale, c->batch, c->m_max, s,
-                  c->fp32 ? c->err.p : nullptr));
+                  c->fp32 ? c->err.p : nullptr, c->bigset()));
   if (c->fp32) {
     for (int k = 0; k < c->opt.refine_steps; ++k)
       CK(launch_refine(c->inst.p, c->lset.p, c->W.p, c->lag.p, c->rwork.p, c->nrwork, c->counter.p,
@@ -907,7 +966,7 @@ int32_t nys_run(nys_ctx* c, void* stream, double* x_out, int32_t* status_out) {
         e2 = launch_assemble(c->fp32, c->inst.p, c->lset.p, c->lag.p, c->W.p,
                              c->work.p, c->nwork, c->counter.p, c->lm.p, c->tab.p, c->part.p,
                              c->slot_off.p, c->m_max, c->k_max, c->num_sms, cs, c->opt.assembly,
-                             c->err.p);
+                             c->err.p, c->bigset());
       if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(cs, c->ev_join, 0);
       if (e2 != cudaSuccess) r = fail(NYS_ECUDA, "capture: assemble: %s", cudaGetErrorString(e2));
       if (r == NYS_OK) r = solve_impl(c, cs, x_out, status_out);
@@ -1018,6 +1077,7 @@ int32_t nys_grad(nys_ctx* c, void* stream, const double* obs_t, const int64_t* o
     if (c->shape[b].p > 2) return fail(NYS_EINVAL, "nys_grad: orders 1 and 2 only");
   }
   if (c->fp32) return fail(NYS_ESTATE, "nys_grad: needs a context created with precision NYS_FP64");
+  if (c->nbig > 0) return fail(NYS_EINVAL, "nys_grad: m <= %d only", NYS_M_MAX_MIXED);
   if (!c->solved) return fail(NYS_ESTATE, "nys_grad: no solution yet");
   CK(launch_grad(c->inst.p, c->lset.p, c->W.p, (const double*)c->fac.p, c->facs, c->xs.p, c->zs.p,
                  c->lm.p, c->XS, c->ZS, c->st.p, obs_t, obs_off, dl_dy, c->adj.p, c->rwork.p,

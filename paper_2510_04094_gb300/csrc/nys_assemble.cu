@@ -11,7 +11,11 @@
 //
 // Work is a list of (instance, row range) items taken from an atomic queue by
 // a persistent grid; each item writes its packed upper-triangular partial Gram
-// (M2 (M2+1)/2 doubles, M2 = m + 2) to its own slot.
+// (M2 (M2+1)/2 doubles, M2 = m + 2) to its own slot.  A Gram of more than
+// kMMax + 2 columns is split into parts (packed entries [e0, e1), at most
+// kAsm64Span each), one work item per part of a row range, all writing their own
+// entries of the range's slot; k_gram_reduce then sums the slots of each such
+// instance over many CTAs.
 #include "nys_internal.cuh"
 
 namespace nys {
@@ -36,11 +40,12 @@ k_assemble_f64(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
                const int64_t* __restrict__ slot_off) {
   extern __shared__ double sm64[];
   __shared__ int s_item;
-  __shared__ int s_idx[kMMax];
+  __shared__ int s_idx[kMLarge];
   __shared__ double s_rc[kAsm64Rows][7];   // A0..A4, w1, r
-  __shared__ unsigned char s_pair[2 * kM2Max * (kM2Max + 1) / 2];
+  __shared__ unsigned char s_pair[2 * KMAX * kAsm64Threads];   // (j, l) of the item's entries
+  static_assert(kMLarge + 2 <= 255, "Gram column index must fit a byte");
   const int tid = threadIdx.x;
-  int cached_m2 = -1;
+  int cached_m2 = -1, cached_e0 = -1;
 
   for (;;) {
     if (tid == 0) s_item = atomicAdd(counter, 1);
@@ -59,17 +64,27 @@ k_assemble_f64(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     const double* W = (lsets != nullptr) ? W_all + lsets[I.lset].w_off : nullptr;
     const int D = omode ? me : m;          // feature columns of the Gram
     const int M2 = D + 2;
-    const int E = M2 * (M2 + 1) / 2;
+    const int Efull = M2 * (M2 + 1) / 2;
+    // this item's packed entries [e0, e0 + E) (the host keeps e1 - e0 <= KMAX x threads)
+    const int e0 = wk.e0;
+    const int E = min(max(0, min(Efull, wk.e1) - e0), KMAX * kAsm64Threads);
     for (int j = tid; j < m; j += kAsm64Threads) s_idx[j] = lm_idx[I.lm_off + j];
-    if (M2 != cached_m2) {
+    if (M2 != cached_m2 || e0 != cached_e0) {
       __syncthreads();
+      // packed row j starts at S(j) = j M2 - j (j - 1) / 2: invert, then correct
       for (int e = tid; e < E; e += kAsm64Threads) {
-        int j = 0, rem = e;
-        while (rem >= M2 - j) { rem -= M2 - j; ++j; }
+        const int g = e0 + e;
+        const double b2 = 2.0 * M2 + 1.0;
+        int j = (int)((b2 - sqrt(b2 * b2 - 8.0 * g)) * 0.5);
+        j = max(0, min(j, M2 - 1));
+        while (j > 0 && j * M2 - j * (j - 1) / 2 > g) --j;
+        while (j + 1 < M2 && (j + 1) * M2 - (j + 1) * j / 2 <= g) ++j;
+        const int rem = g - (j * M2 - j * (j - 1) / 2);
         s_pair[2 * e] = (unsigned char)j;
         s_pair[2 * e + 1] = (unsigned char)(j + rem);
       }
       cached_m2 = M2;
+      cached_e0 = e0;
     }
     double acc[KMAX];
 #pragma unroll
@@ -106,9 +121,11 @@ k_assemble_f64(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
       }
       __syncthreads();
       if (omode) {  // project the kernel-coordinate rows: psi_w[r][k] = sum_j W[k][j] psi[r][j]
+        // (only the columns k >= the item's first Gram row are read)
         double* pw = psi + kAsm64Rows * ld;
-        for (int e = tid; e < kAsm64Rows * M2; e += kAsm64Threads) {
-          const int r = e / M2, k = e - r * M2;
+        const int k0 = (E > 0) ? s_pair[0] : M2, nk = M2 - k0;
+        for (int e = tid; e < kAsm64Rows * nk; e += kAsm64Threads) {
+          const int r = e / nk, k = k0 + (e - r * nk);
           double v;
           if (k < me) {
             v = 0.0;
@@ -136,11 +153,11 @@ k_assemble_f64(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     }
     // slot layout: [first landmark, landmark count, packed upper Gram]
     double* out = part + slot_off[wk.slot];
-    if (tid == 0) { out[0] = omode ? -1.0 : 0.0; out[1] = (double)D; }
+    if (tid == 0 && e0 == 0) { out[0] = omode ? -1.0 : 0.0; out[1] = (double)D; }
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
       const int e = tid + k * kAsm64Threads;
-      if (e < E) out[2 + e] = acc[k];
+      if (e < E) out[2 + e0 + e] = acc[k];
     }
   }
 }
@@ -333,6 +350,25 @@ cudaError_t launch_assemble_tc(const Inst* insts, const Lset* lsets, const Work*
                                const int64_t* slot_off, int32_t* err, int num_sms,
                                cudaStream_t st);
 
+// Sum of the row-chunk partial Grams of each listed instance (Grams of more than
+// kMMax + 2 columns), into its first slot: a thread per packed entry, the slots
+// added in their fixed order, so the result does not depend on the grid.
+__global__ void __launch_bounds__(256)
+k_gram_reduce(const Inst* __restrict__ insts, BigSet big, double* __restrict__ part,
+              const int64_t* __restrict__ slot_off) {
+  for (int bi = blockIdx.y; bi < big.n; bi += gridDim.y) {
+    const Inst I = insts[big.ids[bi]];
+    if (I.slot_count <= 1) continue;
+    double* P0 = part + slot_off[I.slot_begin];
+    const int D = (int)P0[1], M2 = D + 2, E = M2 * (M2 + 1) / 2;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
+      double s = P0[2 + e];
+      for (int q = 1; q < I.slot_count; ++q) s += part[slot_off[I.slot_begin + q] + 2 + e];
+      P0[2 + e] = s;
+    }
+  }
+}
+
 template <int K>
 static cudaError_t launch64(const Inst* insts, const Lset* lsets, const double* W,
                             const Work* work, int nwork, int* counter, const int32_t* lm,
@@ -350,7 +386,7 @@ cudaError_t launch_assemble(bool fp32, const Inst* insts, const Lset* lsets, con
                             const double* W, const Work* work, int nwork, int* counter,
                             const int32_t* lm, const double* tab, double* part,
                             const int64_t* slot_off, int m_max, int k_max, int num_sms,
-                            cudaStream_t st, int asm_kind, int32_t* err) {
+                            cudaStream_t st, int asm_kind, int32_t* err, BigSet big) {
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   if (err != nullptr) {  // error word read by the solve (NYS_ETIMEOUT)
@@ -377,12 +413,19 @@ cudaError_t launch_assemble(bool fp32, const Inst* insts, const Lset* lsets, con
   const int kneed = (E + kAsm64Threads - 1) / kAsm64Threads;
   const int grid = min(nwork, num_sms * 2);
 #define A64 insts, lsets, W, work, nwork, counter, lm, tab, part, slot_off, sm, grid, st
-  if (kneed <= 4) return launch64<4>(A64);
-  if (kneed <= 8) return launch64<8>(A64);
-  if (kneed <= 14) return launch64<14>(A64);
-  if (kneed <= 20) return launch64<20>(A64);
-  return launch64<26>(A64);
+  if (kneed <= 4) e = launch64<4>(A64);
+  else if (kneed <= 8) e = launch64<8>(A64);
+  else if (kneed <= 14) e = launch64<14>(A64);
+  else if (kneed <= 20) e = launch64<20>(A64);
+  else e = launch64<kAsm64BigK>(A64);   // above kMMax the host splits Grams into parts
 #undef A64
+  if (e != cudaSuccess || big.n == 0) return e;
+  // many CTAs per instance: the slots of a single long instance are summed at
+  // HBM speed instead of by its one solve CTA
+  const int EB = (kMLarge + 2) * (kMLarge + 3) / 2;
+  k_gram_reduce<<<dim3(std::max(1, std::min((EB + 255) / 256, 4 * num_sms / std::max(1, big.n))),
+                       std::min(big.n, 65535)), 256, 0, st>>>(insts, big, part, slot_off);
+  return cudaGetLastError();
 }
 
 }  // namespace nys

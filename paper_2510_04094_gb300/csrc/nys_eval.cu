@@ -11,8 +11,8 @@ k_eval(const Inst* __restrict__ insts, const double* __restrict__ zs, int ZS,
   const int b = blockIdx.x;
   const Inst I = insts[b];
   const int m = I.m;
-  __shared__ double s_z[kM1Max];
-  __shared__ double s_s[kMMax];
+  __shared__ double s_z[kMLarge + 1];
+  __shared__ double s_s[kMLarge];
   for (int j = threadIdx.x; j <= m; j += blockDim.x) s_z[j] = zs[(int64_t)b * ZS + j];
   for (int j = threadIdx.x; j < m; j += blockDim.x) s_s[j] = I.t0 + (double)lm_idx[I.lm_off + j] * I.h;
   __syncthreads();

@@ -8,7 +8,8 @@
 
 namespace nys {
 
-constexpr int kMMax = NYS_M_MAX;          // landmarks per instance
+constexpr int kMMax = NYS_M_MAX_MIXED;    // landmarks, shared-memory kernels
+constexpr int kMLarge = NYS_M_MAX;        // landmarks, global-workspace kernels (FP64)
 constexpr int kNtRowState = 5;            // Newton row state: Fy, d, f_y, f_u + delta, e f_yu
 constexpr int kM1Max = kMMax + 1;         // (omega, b)
 constexpr int kM2Max = kMMax + 2;         // augmented row [kappa; -f_p; r]
@@ -70,7 +71,25 @@ constexpr double kOmegaCond = 1e-7;
 // One unit of a row pass: rows i in [r0, r1) (0-based grid index, 1 <= i <= n-1).
 struct Work {
   int32_t inst, r0, r1, slot;
+  int32_t e0, e1;      // FP64 assembly: packed Gram entries [e0, e1) of the rows
+                       // (one part of a Gram too large for one item), else 0, max
 };
+
+// Instances with m > kMMax (FP64, linear): their landmark sets are factored and
+// their KKT systems solved in a global workspace (one area of `stride` doubles per
+// listed instance, shared by the setup and the solve, which run one after the
+// other), their Gram is assembled in entry parts and its row-chunk partials are
+// summed by a separate many-CTA pass.
+struct BigSet {
+  const int32_t* ids = nullptr;   // device: the instances (== their landmark-set slots)
+  int n = 0;
+  double* ws = nullptr;           // device workspace, n x stride doubles
+  int64_t stride = 0;
+};
+// FP64 assembly accumulators per thread for Grams of more than kMMax + 2 columns
+// (the entries of one work item: kAsm64BigK x its 256 threads)
+constexpr int kAsm64BigK = 26;
+constexpr int kAsm64Span = kAsm64BigK * 256;
 
 // Per-instance solve storage offsets (element offsets in the typed arenas).
 struct SolveSlots {

@@ -24,18 +24,20 @@
 namespace nys {
 cudaError_t launch_setup(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
                          double* lam, float* lag, double tau, int m_max, cudaStream_t st,
-                         int allow_chol, const int* m_bounds, int nclass);
+                         int allow_chol, const int* m_bounds, int nclass,
+                         BigSet big = BigSet());
 cudaError_t launch_assemble(bool fp32, const Inst* insts, const Lset* lsets, const float* lag,
                             const double* W, const Work* work, int nwork, int* counter,
                             const int32_t* lm, const double* tab, double* part,
                             const int64_t* slot_off, int m_max, int k_max, int num_sms,
-                            cudaStream_t st, int asm_kind, int32_t* err);
+                            cudaStream_t st, int asm_kind, int32_t* err,
+                            BigSet big = BigSet());
 cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const double* W,
                          const float* W32, const double* part, const int64_t* slot_off,
                          const int32_t* lm, void* fac, int64_t facs, double* xs, double* zs,
                          double* cws, int XS, int ZS, int M1S, const int32_t* st_init,
                          int32_t* st, double gamma_scale, int batch, int m_max, cudaStream_t s,
-                         const int32_t* asm_err);
+                         const int32_t* asm_err, BigSet big = BigSet());
 int64_t fac_elems(int m_max);
 int32_t set_last_error(int32_t code, const char* msg);  // nys_api.cu: feeds nys_last_error()
 }  // namespace nys
@@ -171,6 +173,8 @@ extern "C" int32_t nys_solve_noalloc(const nys_instance* q, int32_t batch, doubl
       w.r0 = 1 + (int)((int64_t)nrows * k / chunks);
       w.r1 = 1 + (int)((int64_t)nrows * (k + 1) / chunks);
       w.slot = nwork;
+      w.e0 = 0;
+      w.e1 = INT32_MAX;
       soff[nwork++] = poff;
       poff += E;
     }

@@ -185,16 +185,18 @@ __device__ void sort_desc(const T* A, int ld, int m, int* perm) {
 }
 
 // NT threads per CTA: 256 for the small landmark counts (several CTAs per SM),
-// 512 / 1024 for the large ones, whose shared memory leaves room for 2 / 1 CTAs
-template <int NT>
+// 512 / 1024 for the large ones, whose shared memory leaves room for 2 / 1 CTAs.
+// kG: landmark counts above kMMax, whose matrices do not fit in shared memory,
+// work in a global (L2-resident) area of their own, one CTA per listed set.
+template <int NT, bool kG>
 __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1))
 k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict__ W_all,
             float* __restrict__ W32_all, double* __restrict__ lam_all, double tau, int allow_chol,
-            int m_lo, int m_hi) {
+            int m_lo, int m_hi, BigSet big) {
   // the grid covers every slot; inactive slots (instances that share another
   // instance's set) return at once, so a captured graph stays valid when an
   // update changes which instances share
-  const int L = blockIdx.x;
+  const int L = kG ? big.ids[blockIdx.x] : blockIdx.x;
   const Lset S = lsets[L];
   // one launch per landmark-count class (m_lo, m_hi], each with shared memory
   // for its own largest m
@@ -202,7 +204,8 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict_
   const int m = S.m;
   const int N = m + (m & 1);  // even player count; index m (if present) is a bye
   const int ld = m + 1;
-  extern __shared__ double sm[];
+  extern __shared__ double smem_eig[];
+  double* sm = kG ? big.ws + (int64_t)blockIdx.x * big.stride : smem_eig;
   double* A = sm;
   double* V = A + m * ld;
   double* cs = V + m * ld;                 // N/2 cosines then N/2 sines
@@ -278,7 +281,7 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict_
         }
         for (int k = tid; k < m; k += nt) {
           const double l = V[k * ld + k];
-          lam_all[(int64_t)L * kMMax + k] = l * l;   // Cholesky pivots (informational)
+          lam_all[(int64_t)L * kMLarge + k] = l * l;   // Cholesky pivots (informational)
         }
         if (tid == 0) {
           lsets[L].m_eff = m;
@@ -327,7 +330,7 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict_
         const int c = perm[k];
         Wl[e] = (double)Vf[j * ld + c] / sqrt((double)Af[c * ld + c]);
       }
-      for (int k = tid; k < m; k += nt) lam_all[(int64_t)L * kMMax + k] = (double)Af[perm[k] * ld + perm[k]];
+      for (int k = tid; k < m; k += nt) lam_all[(int64_t)L * kMLarge + k] = (double)Af[perm[k] * ld + perm[k]];
       __syncthreads();
       double* Tm = V;                           // T = W0 Omega (the FP32 matrices are done)
       for (int e = tid; e < m * m; e += nt) {
@@ -400,7 +403,7 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict_
     Wl[e] = w;
     W32l[e] = (float)w;
   }
-  for (int k = tid; k < m; k += nt) lam_all[(int64_t)L * kMMax + k] = A[perm[k] * ld + perm[k]];
+  for (int k = tid; k < m; k += nt) lam_all[(int64_t)L * kMLarge + k] = A[perm[k] * ld + perm[k]];
 }
 
 // Lag tables of a landmark set on its uniform grid.  Every feature value of
@@ -446,20 +449,24 @@ static cudaError_t launch_eig_class(Lset* lsets, int capacity, const int32_t* lm
                                     float* W32, double* lam, double tau, int allow_chol, int lo,
                                     int hi, cudaStream_t st) {
   const size_t sm = setup_smem_bytes(hi);
-  cudaError_t e = cudaFuncSetAttribute(k_setup_eig<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sm);
+  cudaError_t e = cudaFuncSetAttribute(k_setup_eig<NT, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_setup_eig<NT><<<capacity, NT, sm, st>>>(lsets, lm_idx, W, W32, lam, tau, allow_chol, lo, hi);
+  k_setup_eig<NT, false><<<capacity, NT, sm, st>>>(lsets, lm_idx, W, W32, lam, tau, allow_chol, lo,
+                                                   hi, BigSet());
   return cudaGetLastError();
 }
 
+size_t setup_ws_doubles() { return setup_smem_bytes(kMLarge) / sizeof(double) + 1; }
+
 cudaError_t launch_eig(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
                        double* lam, double tau, int m_max, cudaStream_t st, int allow_chol,
-                       const int* m_bounds, int nclass) {
+                       const int* m_bounds, int nclass, BigSet big) {
   if (capacity == 0) return cudaSuccess;
   int lo = 0;
-  for (int k = 0; k < (nclass > 0 ? nclass : 1); ++k) {
-    const int hi = (nclass > 0) ? m_bounds[k] : m_max;
+  for (int k = 0; k < (nclass > 0 ? nclass : 1) && lo < kMMax; ++k) {
+    const int hi = std::min((nclass > 0) ? m_bounds[k] : m_max, kMMax);
+    if (hi <= lo) continue;
     // threads per CTA from the class's shared memory: one CTA per SM above
     // ~113 KB, two above ~75 KB (of the SM's 228 KB)
     const size_t sm = setup_smem_bytes(hi);
@@ -473,16 +480,22 @@ cudaError_t launch_eig(Lset* lsets, int capacity, const int32_t* lm_idx, double*
     if (e != cudaSuccess) return e;
     lo = hi;
   }
+  if (big.n > 0) {   // landmark counts above kMMax: global workspace
+    k_setup_eig<1024, true><<<big.n, 1024, 0, st>>>(lsets, lm_idx, W, W32, lam, tau, allow_chol,
+                                                     kMMax, kMLarge, big);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   return cudaSuccess;
 }
 
 cudaError_t launch_setup(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
                          double* lam, float* lag, double tau, int m_max, cudaStream_t st,
-                         int allow_chol, const int* m_bounds, int nclass) {
+                         int allow_chol, const int* m_bounds, int nclass, BigSet big) {
   cudaError_t e = launch_lag(lsets, capacity, lag, st);
   if (e != cudaSuccess) return e;
   return launch_eig(lsets, capacity, lm_idx, W, W32, lam, tau, m_max, st, allow_chol, m_bounds,
-                    nclass);
+                    nclass, big);
 }
 
 }  // namespace nys

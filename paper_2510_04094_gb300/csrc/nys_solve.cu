@@ -20,6 +20,7 @@
 namespace nys {
 
 constexpr int kSolveThreads = 128;
+constexpr int kSolveThreadsBig = 512;   // global-workspace solves (m > kMMax)
 
 int64_t fac_elems(int m_max) { return fac_elems_inline(m_max); }
 
@@ -27,17 +28,24 @@ int64_t fac_elems(int m_max) { return fac_elems_inline(m_max); }
 // K3: form H, g, C; factor; solve.  One CTA per instance.
 // Shared memory: G (m+1) x (m+2) [T], H M1 x M1 [T], Y-block 8 x m [T], vectors.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kSolveThreads)
+// MM = kMMax: one CTA per instance, matrices in shared memory; instances with
+// more landmarks are left to MM = kMLarge: one CTA per listed instance, the same
+// steps on its own global (L2-resident) area, whose row chunks k_gram_reduce has
+// already summed into the first slot.
+template <typename T, int MM>
+__global__ void __launch_bounds__(MM > kMMax ? kSolveThreadsBig : kSolveThreads)
 k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         const double* __restrict__ W_all, const T* __restrict__ Wt_all,
         const double* __restrict__ part,
         const int64_t* __restrict__ slot_off, const int32_t* __restrict__ lm_idx,
         T* __restrict__ fac_all, int64_t facs, double* __restrict__ xs, double* __restrict__ zs,
         double* __restrict__ cws, int XS, int ZS, int M1S, const int32_t* __restrict__ st_init,
-        int32_t* __restrict__ st_all, double gamma_scale, const int32_t* __restrict__ asm_err) {
-  const int b = blockIdx.x;
+        int32_t* __restrict__ st_all, double gamma_scale, const int32_t* __restrict__ asm_err,
+        BigSet big) {
+  constexpr bool kBig = MM > kMMax;
+  const int b = kBig ? big.ids[blockIdx.x] : blockIdx.x;
   const Inst I = insts[b];
+  if (!kBig && I.m > kMMax) return;   // solved by the global-workspace variant
   const Lset LS = lsets[I.lset];
   // omega mode (ill-conditioned landmark kernel): the row pass projected each
   // row through W, so the slots hold the Gram in omega coordinates.  The FP32
@@ -62,7 +70,8 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   const T* Wt = Wt_all + LS.w_off;     // same in T
   const double gamma = I.gamma * gamma_scale;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* Gs = reinterpret_cast<T*>(smraw);             // (Dg+1) x (Dg+2), room for (m+1) x (m+2)
+  T* Gs = kBig ? reinterpret_cast<T*>(big.ws + (int64_t)blockIdx.x * big.stride)
+               : reinterpret_cast<T*>(smraw);             // (Dg+1) x (Dg+2), room for (m+1) x (m+2)
   T* Hs = Gs + (m + 1) * (m + 2);                    // M1 x M1
   T* Yb = Hs + M1 * ldh;                             // 8 x m
   T* vec = Yb + 8 * m;                               // misc vectors
@@ -74,7 +83,7 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   T* red = y + M1;                                   // 40
   __shared__ int s_flag;
   __shared__ T s_beta[4], s_Rm[4][4];               // reflector scales, R (upper, p x p)
-  __shared__ double s_c[4][kM1Max];                 // condition rows, omega coordinates
+  __shared__ double s_c[4][MM + 1];                 // condition rows, omega coordinates
 
   // 1. add the partial Grams of the row chunks into G (symmetric, full).  A slot
   //    holds [first column jlo (-1: omega coordinates, all me columns), count A,
@@ -84,7 +93,7 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   for (int e = threadIdx.x; e < (Dg + 1) * ldg; e += blockDim.x) Gs[e] = T(0);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int q = 0; q < I.slot_count; ++q) {
+  for (int q = 0; q < (kBig ? 1 : I.slot_count); ++q) {
     const double* P = part + slot_off[I.slot_begin + q];
     const int jlo = (int)P[0] < 0 ? 0 : (int)P[0], A = (int)P[1], M2l = A + 2;
     // a warp per packed row a (local columns bb >= a start at a M2l - a (a-1) / 2);
@@ -195,7 +204,7 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   //    initial values (Lemma 1) tau_r = t_1, d_r = r; boundary values (Appendix A.4)
   //    t_1 then t_n, d_r = 0 for p = 2, and d_r = 0, 1 at each end for p = 4
   //    (Problem 16).  k^(d)(tau) = (-1/sigma)^d H_d(x) exp(-x^2), x = (tau - s_j)/sigma.
-  __shared__ double s_e[4][kMMax];
+  __shared__ double s_e[4][MM];
   const bool bvp = (I.bc == NYS_BC_BVP);
   const int hp = bvp ? p / 2 : p;                       // conditions at t_1
   for (int e = threadIdx.x; e < p * m; e += blockDim.x) {
@@ -230,7 +239,9 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
       for (int r = 0; r < 4; ++r) sr[r] = (r < p && (r == 0 || r == hp)) ? 1.0 : 0.0;
     }
     if (lane == 0) {
-      for (int r = 0; r < p; ++r) s_c[r][k] = sr[r];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (r < p) s_c[r][k] = sr[r];
       // rows 0, 1 for the refinement and gradient passes (orders <= 2)
       cws[(int64_t)b * 2 * M1S + k] = sr[0];
       cws[(int64_t)b * 2 * M1S + M1S + k] = sr[1];
@@ -280,10 +291,16 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   }
   // 7. y1 = R^{-T} v ; rhs2 = g'[p:] - H'[p:, :p] y1
   if (threadIdx.x == 0) {
-    for (int k = 0; k < p; ++k) {
-      T sv = (T)I.v[k];
-      for (int j = 0; j < k; ++j) sv -= s_Rm[j][k] * y[j];
-      y[k] = sv / s_Rm[k][k];
+    T yk[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (k < p) {
+        T sv = (T)I.v[k];
+#pragma unroll
+        for (int j = 0; j < k; ++j) sv -= s_Rm[j][k] * yk[j];
+        yk[k] = sv / s_Rm[k][k];
+        y[k] = yk[k];
+      }
     }
   }
   __syncthreads();
@@ -304,13 +321,20 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     }
   }
   // 9. lambda = R^{-1}(g'[:p] - H'[:p, :] y)
+  // (loops over the fixed bound 4 keep qk and lam in registers)
   T qk[4];
-  for (int k = 0; k < p; ++k) qk[k] = cta_dot(Hs + k * ldh, y, M1, red);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) qk[k] = (k < p) ? cta_dot(Hs + k * ldh, y, M1, red) : T(0);
   double lam[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int k = p - 1; k >= 0; --k) {
-    T sv = g[k] - qk[k];
-    for (int j = k + 1; j < p; ++j) sv -= s_Rm[k][j] * (T)lam[j];
-    lam[k] = (double)(sv / s_Rm[k][k]);
+#pragma unroll
+  for (int k = 3; k >= 0; --k) {
+    if (k < p) {
+      T sv = g[k] - qk[k];
+#pragma unroll
+      for (int j = k + 1; j < 4; ++j)
+        if (j < p) sv -= s_Rm[k][j] * (T)lam[j];
+      lam[k] = (double)(sv / s_Rm[k][k]);
+    }
   }
   const double lam0 = lam[0], lam1 = lam[1];
   // 10. x = Q y
@@ -339,7 +363,8 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   if (threadIdx.x == 0) {
     int st = ok ? NYS_OK : NYS_ENOTSPD;
     bool fin = isfinite((double)y[me]);
-    for (int k = 0; k < p; ++k) fin = fin && isfinite(lam[k]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) fin = fin && (k >= p || isfinite(lam[k]));
     if (ok && !fin) st = NYS_ENONFINITE;
     st_all[b] = st;
   }
@@ -350,6 +375,8 @@ size_t solve_smem_bytes(bool fp32, int m_max) {
   const size_t es = fp32 ? sizeof(float) : sizeof(double);
   return es * ((size_t)(m + 1) * (m + 2) + (size_t)M1 * M1 + 8 * m + 8 * M1 + 40);
 }
+
+size_t solve_ws_doubles() { return solve_smem_bytes(false, kMLarge) / sizeof(double) + 1; }
 
 // ---------------------------------------------------------------------------
 // K4a: refinement row pass (mixed path).  For each row the residual
@@ -982,22 +1009,32 @@ cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const 
                          const float* W32, const double* part, const int64_t* slot_off, const int32_t* lm,
                          void* fac, int64_t facs, double* xs, double* zs, double* cws, int XS,
                          int ZS, int M1S, const int32_t* st_init, int32_t* st, double gamma_scale,
-                         int batch, int m_max, cudaStream_t s, const int32_t* asm_err) {
-  const size_t sm = solve_smem_bytes(fp32, m_max);
+                         int batch, int m_max, cudaStream_t s, const int32_t* asm_err,
+                         BigSet big) {
+  const size_t sm = solve_smem_bytes(fp32, m_max < kMMax ? m_max : kMMax);
   cudaError_t e;
   if (fp32) {
-    e = cudaFuncSetAttribute(k_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = cudaFuncSetAttribute(k_solve<float, kMMax>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sm);
     if (e != cudaSuccess) return e;
-    k_solve<float><<<batch, kSolveThreads, sm, s>>>(insts, lsets, W, W32, part, slot_off, lm,
-                                                     (float*)fac, facs, xs, zs, cws, XS, ZS, M1S,
-                                                     st_init, st, gamma_scale, asm_err);
+    k_solve<float, kMMax><<<batch, kSolveThreads, sm, s>>>(insts, lsets, W, W32, part, slot_off, lm,
+                                                            (float*)fac, facs, xs, zs, cws, XS, ZS,
+                                                            M1S, st_init, st, gamma_scale, asm_err,
+                                                            BigSet());
   } else {
-    e = cudaFuncSetAttribute(k_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = cudaFuncSetAttribute(k_solve<double, kMMax>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sm);
     if (e != cudaSuccess) return e;
-    k_solve<double><<<batch, kSolveThreads, sm, s>>>(insts, lsets, W, W, part, slot_off, lm,
-                                                      (double*)fac, facs, xs, zs, cws, XS, ZS,
-                                                      M1S, st_init, st, gamma_scale, asm_err);
+    k_solve<double, kMMax><<<batch, kSolveThreads, sm, s>>>(insts, lsets, W, W, part, slot_off, lm,
+                                                             (double*)fac, facs, xs, zs, cws, XS,
+                                                             ZS, M1S, st_init, st, gamma_scale,
+                                                             asm_err, BigSet());
+    if (big.n > 0 && (e = cudaGetLastError()) == cudaSuccess)
+      k_solve<double, kMLarge><<<big.n, kSolveThreadsBig, 0, s>>>(
+          insts, lsets, W, W, part, slot_off, lm, (double*)fac, facs, xs, zs, cws, XS, ZS, M1S,
+          st_init, st, gamma_scale, asm_err, big);
   }
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

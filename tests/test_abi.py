@@ -53,7 +53,7 @@ def _one(**kw):
     return q
 
 
-@pytest.mark.parametrize("bad", [dict(p=3), dict(n=2), dict(m=1), dict(m=200, n=300),
+@pytest.mark.parametrize("bad", [dict(p=3), dict(n=2), dict(m=1), dict(m=230, n=300),
                                  dict(sigma=0.0), dict(gamma=-1.0), dict(t1=-1.0),
                                  dict(landmarks=[0, 5, 5] + list(range(6, 23))),
                                  dict(bc="bvp", p=1, a=[1.0], v=[0.0])])
@@ -65,6 +65,20 @@ def test_invalid_instances_are_rejected_on_the_host(abi, bad):
     code = abi.lib().nys_setup(C.byref(ctx), arr, 1, C.byref(opt), None)
     assert code == abi.NYS_EINVAL
     assert abi.lib().nys_last_error().decode().startswith("instance 0")
+    assert not ctx.value
+
+
+@pytest.mark.parametrize("kw,precision", [(dict(m=150), "mixed"),
+                                          (dict(m=150, kind="nl", P=[0.0, -1.0, 0.0, 0.0]), "fp64")])
+def test_large_landmark_counts_need_fp64_linear(abi, kw, precision):
+    """Above NYS_M_MAX_MIXED landmarks only FP64 solves of the linear kinds run."""
+    from paper_2510_04094_gb300.api import pack_instances
+    arr, keep = pack_instances([_one(**kw)])
+    opt = abi.nys_options()
+    opt.precision = abi.NYS_MIXED if precision == "mixed" else abi.NYS_FP64
+    ctx = C.c_void_p()
+    assert abi.lib().nys_setup(C.byref(ctx), arr, 1, C.byref(opt), None) == abi.NYS_EINVAL
+    assert "m > 112" in abi.lib().nys_last_error().decode()
     assert not ctx.value
 
 

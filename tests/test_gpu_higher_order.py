@@ -11,10 +11,10 @@ import pytest
 import nys_inputs as ni
 from oracle import core
 
+from parity_helpers import check_fp64 as _check
 from test_oracle_bvp import p16_problem
 
 pytestmark = pytest.mark.gpu
-TOL = 1e-10
 
 
 @pytest.fixture(scope="module")
@@ -26,72 +26,6 @@ def api():
     __graft_entry__.build()
     from paper_2510_04094_gb300 import api as A
     return A
-
-
-def _conditions(q):
-    """(t index, derivative, value) of each condition row."""
-    p, n, v = q["p"], q["n"], q["v"]
-    if q.get("bc") == "bvp":
-        h = p // 2
-        return [(0, d, v[d]) for d in range(h)] + [(n - 1, d, v[h + d]) for d in range(h)]
-    return [(0, d, v[d]) for d in range(p)]
-
-
-def _svd_setup(q, tau):
-    """The oracle's setup with the landmark kernel factored by an SVD instead of
-    eigh: an equally exact factor with different rounding."""
-    st = core.setup(q, tau)
-    Om = core.rbf(st["s"][:, None], st["s"][None, :], q["sigma"])
-    U, S, _ = np.linalg.svd(Om)
-    keep = S > tau * S[0]
-    return dict(st, W=(U[:, keep] / np.sqrt(S[keep])).T, lam=S[keep], U=U[:, keep])
-
-
-def _check(api, probs, eig_tau=0.0, tau=core.TAU_DEFAULT):
-    import torch
-    bt = api.Batch(probs, precision="fp64", eig_tau=eig_tau)
-    bt.assemble()
-    x, st = bt.solve()
-    grids = [core.grid(q) for q in probs]
-    ys = [bt.eval(grids, deriv=d)[0] for d in range(3)]
-    torch.cuda.synchronize()
-    st = st.cpu().numpy()
-    assert (st == 0).all(), st
-    meff = bt.m_eff()
-    sols = bt.unpack()
-    yc = [y.cpu().numpy() for y in ys]
-    off = 0
-    out = []
-    for k, (q, g) in enumerate(zip(probs, grids)):
-        ref = core.solve_linear(q, tau=tau)
-        ref2 = core.solve_linear_nullspace(q, tau=tau)
-        scale = np.abs(ref["y"]).max()
-        # the problem's own rounding sensitivity: the oracle's two routes, and the
-        # oracle with an SVD-computed factor (Problem 16 keeps eigenvalues down to
-        # 1e-12 lambda_max or below, where eigh vs SVD alone moves y by 2e-10)
-        ref3 = core.solve_linear(q, st=_svd_setup(q, tau))
-        spread = max(np.abs(ref["y"] - ref2["y"]).max(), np.abs(ref["y"] - ref3["y"]).max())
-        tol = max(TOL, 10 * spread / scale)
-        assert meff[k] == ref["m_eff"]
-        for d in range(3):
-            got = yc[d][off:off + len(g)]
-            want = core.evaluate(q, ref, g, d) if d else ref["y"]
-            err = np.abs(got - want).max() / np.abs(want).max()
-            assert err <= (1 if d == 0 else 50) * tol, (k, q["p"], q.get("bc"), d, err, tol)
-        # the condition rows hold (derivatives up to 2 are evaluated here)
-        for i, d, val in _conditions(q):
-            if d <= 2:
-                assert abs(yc[d][off + i] - val) <= 1e-8 * max(1.0, abs(val), scale), (k, i, d)
-        eb = abs(sols[k]["b"] - ref["b"]) / max(1.0, scale)
-        # b alone can be far less determined than y (with sigma ~ the interval the
-        # kept features nearly span the constants); its own route spread bounds it
-        sb = max(abs(ref["b"] - ref2["b"]), abs(ref["b"] - ref3["b"]))
-        tb = max(10 * tol, 10 * sb / max(1.0, scale))
-        assert eb <= tb, (k, eb, tb)
-        out.append(yc[0][off:off + len(g)])
-        off += len(g)
-    bt.close()
-    return out
 
 
 def test_small_ragged_third_and_fourth_order_batch(api):
