@@ -424,6 +424,15 @@ def main():
         single["tanh_newton_ms"] = step_ms(sn, lambda: sn.newton(max_iter=50, tol=1e-10), reps=2)
         sn.close()
         extra["single_n1e4"] = single
+        # long-time single instances at the sizes of Table 12 (n = 5e4, m = 200, FP64;
+        # factor, assembly and solve per step): Problem 3 (omega coordinates, 111
+        # of 200 eigenpairs kept) and Problem 9 (all 200 kept)
+        lt = {}
+        for nm in ("P3", "P9"):
+            s1 = Batch([ni.long_time(nm)[0]], precision="fp64")
+            lt[nm + "_ms"] = step_ms(s1, s1.run, reps=3)
+            s1.close()
+        extra["long_time_n5e4_m200"] = lt
         # batched Newton family: 64 logistic / Duffing instances, n in [2000, 1e4], FP64
         b5 = Batch(ni.cfg5(), precision="fp64")
         ms5 = step_ms(b5, lambda: b5.newton(max_iter=20, tol=1e-10), reps=2)
