@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-extras", action="store_true", help="skip FP64/oracle side measurements")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--long-time", action="store_true",
+                    help="only time the long-time single instances (n = 5e4, m = 200) by phase")
     return ap.parse_args()
 
 
@@ -223,6 +225,40 @@ def run_reference(args, rank, ws):
     print(json.dumps(line), flush=True)
 
 
+def long_time_breakdown(Batch, ni, torch):
+    """Single long-time instances at the sizes of Table 12 (FP64): ms per nys_run
+    (factor + assembly + solve, one graph; the factor overlaps the assembly on a
+    side stream), per nys_assemble and per nys_solve, each the mean of 3 calls
+    timed with CUDA events on the launching stream."""
+    stream = torch.cuda.current_stream()
+
+    def ev_ms(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    out = {}
+    for nm in ("P3", "P9"):
+        q, _ = ni.long_time(nm)
+        bt = Batch([q], precision="fp64")
+        res = {"n": q["n"], "m": q["m"], "run_ms": ev_ms(bt.run), "assemble_ms": ev_ms(bt.assemble),
+               "solve_ms": ev_ms(bt.solve)}
+        _, st = bt.solve()
+        torch.cuda.synchronize()
+        res["m_eff"] = int(bt.m_eff()[0])
+        res["status_ok"] = bool((st.cpu().numpy() == 0).all())
+        out[nm] = res
+        bt.close()
+    return out
+
+
 def main():
     args = parse()
     rank, ws, local = dist_init()
@@ -237,6 +273,13 @@ def main():
     import nys_inputs as ni
     from paper_2510_04094_gb300 import _abi
     from paper_2510_04094_gb300.api import Batch, pack_instances
+
+    if args.long_time:
+        if rank == 0:
+            print(json.dumps({"workload": "long-time single instances, Table 12 sizes, FP64",
+                              "unit": "ms", "data": "synthetic",
+                              "results": long_time_breakdown(Batch, ni, torch)}))
+        return
 
     B = args.batch
     probs = rank_problems(rank, B, args.n, args.m)
@@ -427,12 +470,7 @@ def main():
         # long-time single instances at the sizes of Table 12 (n = 5e4, m = 200, FP64;
         # factor, assembly and solve per step): Problem 3 (omega coordinates, 111
         # of 200 eigenpairs kept) and Problem 9 (all 200 kept)
-        lt = {}
-        for nm in ("P3", "P9"):
-            s1 = Batch([ni.long_time(nm)[0]], precision="fp64")
-            lt[nm + "_ms"] = step_ms(s1, s1.run, reps=3)
-            s1.close()
-        extra["long_time_n5e4_m200"] = lt
+        extra["long_time_n5e4_m200"] = long_time_breakdown(Batch, ni, torch)
         # batched Newton family: 64 logistic / Duffing instances, n in [2000, 1e4], FP64
         b5 = Batch(ni.cfg5(), precision="fp64")
         ms5 = step_ms(b5, lambda: b5.newton(max_iter=20, tol=1e-10), reps=2)
