@@ -470,7 +470,24 @@ def main():
         # long-time single instances at the sizes of Table 12 (n = 5e4, m = 200, FP64;
         # factor, assembly and solve per step): Problem 3 (omega coordinates, 111
         # of 200 eigenpairs kept) and Problem 9 (all 200 kept)
-        extra["long_time_n5e4_m200"] = long_time_breakdown(Batch, ni, torch)
+        try:
+            extra["long_time_n5e4_m200"] = long_time_breakdown(Batch, ni, torch)
+        except Exception as ex:   # a side measurement must not cost the metric line
+            extra["long_time_n5e4_m200"] = {"error": repr(ex)[:200]}
+        # third- and fourth-order batch (FP64, tabulated coefficients): 1024 instances,
+        # n in {1000, 2000}, m in {20, 32}, half of the fourth-order ones with
+        # Problem 16's boundary values
+        try:
+            hp = ni.small_higher(1024, sub=7, n_choices=(1000, 2000), m_choices=(20, 32))
+            bh = Batch(hp, precision="fp64")
+            msh = step_ms(bh, bh.run)
+            _, sth = bh.run()
+            torch.cuda.synchronize()
+            extra["higher_order_1024"] = {"ms_per_step": msh, "solves_s": len(hp) / (msh / 1000.0),
+                                          "status_ok": bool((sth.cpu().numpy() == 0).all())}
+            bh.close()
+        except Exception as ex:
+            extra["higher_order_1024"] = {"error": repr(ex)[:200]}
         # batched Newton family: 64 logistic / Duffing instances, n in [2000, 1e4], FP64
         b5 = Batch(ni.cfg5(), precision="fp64")
         ms5 = step_ms(b5, lambda: b5.newton(max_iter=20, tol=1e-10), reps=2)
