@@ -139,8 +139,12 @@ typedef struct nys_ctx nys_ctx;
    Omega = L L^T for NYS_FP64 when m |W|_F^2 <= 1e6 certifies cond(Omega) <= 1e6, else the
    Jacobi eigendecomposition W = Lambda^{-1/2} U^T with truncation; the fit
    does not depend on which; Appendix A.3 and the feature map eq32).  Instances with identical landmark sets
-   (same m, grid spacing/sigma and indices) share one factor.
-   Errors: NYS_EINVAL (bad instance: message names it), NYS_ENOMEM, NYS_ECUDA. */
+   (same m, grid spacing/sigma and indices) share one factor.  Instances with
+   m > NYS_M_MAX_MIXED (FP64, linear kinds only) are factored and solved in a
+   device workspace of about 0.85 MB each.
+   Errors: NYS_EINVAL (bad instance: message names it; orders 3-4 or
+   m > NYS_M_MAX_MIXED with NYS_MIXED; m > NYS_M_MAX_MIXED with a nonlinear
+   kind), NYS_ENOMEM, NYS_ECUDA. */
 int32_t nys_setup(nys_ctx** out, const nys_instance* inst, int32_t batch,
                   const nys_options* opt, void* stream);
 
