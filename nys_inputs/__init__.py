@@ -235,7 +235,7 @@ def big_m(B=6, sub=0, n_choices=(300, 701, 1500, 3000), m_choices=(113, 128, 150
 def long_time(name):
     """Long-time integration workloads at the sizes of the paper's Table 12 (t up to
     100, n = 2e4 - 5e4, m = 100 - 200, gamma = 1e7), on Problems 3, 7, 8 and 9 of
-    Appendix A.6, written as constant-coefficient instances:
+    Appendix B.1, written as constant-coefficient instances:
       P3: y' + 1000 y = 1000 sin t + cos t, y(0) = 0, sigma^2 = 10, m = 200;
       P7: y'' + 0.3 y' + y = 1, y(0) = y'(0) = 0, sigma^2 = 1, m = 100;
       P8: y'' + 36 y = 0, y(0) = -1/2, y'(0) = 1, t in [0, 50], n = 2e4, m = 200;
