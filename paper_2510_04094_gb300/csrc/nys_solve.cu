@@ -4,11 +4,12 @@
 // Lemma 1 as a constrained least-squares problem in (omega, b):
 //     [ H  C^T ] [x     ]   [g]     H = D + gamma B G_kk B^T  (D = diag(1_m, 0))
 //     [ C  0   ] [lambda] = [v],    g = gamma B g_k,  B = blkdiag(W, 1)
-// with G_kk, g_k the kernel-coordinate sums of the fused row pass and
-// C = [phi(t_1) 1; phi'(t_1) 0] the initial-condition rows (Lemma 1 sign
-// convention: H x + C^T lambda = g).  Solved by the null-space method:
-// Householder reflectors Q with Q^T C^T = [R; 0], y = Q^T x, y_1 = R^{-T} v,
-// Cholesky of the projected block H'_22 for y_2, lambda from the first p rows.
+// with G_kk, g_k the kernel-coordinate sums of the fused row pass and C the p
+// condition rows, e.g. [phi(t_1) 1; phi'(t_1) 0] for second-order initial
+// values (Lemma 1 sign convention: H x + C^T lambda = g).  Solved by the
+// null-space method: Householder reflectors Q with Q^T C^T = [R; 0] (p <= 4),
+// y = Q^T x, y_1 = R^{-T} v, Cholesky of the projected block H'_22 for y_2,
+// lambda from the first p rows.
 // The KKT matrix itself mixes scales gamma n |kappa|^2 and 1 (cond ~ 1e27);
 // the projected block has the conditioning of the fit (~1e2-1e4 here).
 //
@@ -26,7 +27,8 @@ int64_t fac_elems(int m_max) { return fac_elems_inline(m_max); }
 
 // ---------------------------------------------------------------------------
 // K3: form H, g, C; factor; solve.  One CTA per instance.
-// Shared memory: G (m+1) x (m+2) [T], H M1 x M1 [T], Y-block 8 x m [T], vectors.
+// Shared memory (m <= kMMax) or the instance's global area (m > kMMax):
+// G (m+1) x (m+2) [T], H M1 x M1 [T], Y-block 8 x m [T], vectors.
 // ---------------------------------------------------------------------------
 // MM = kMMax: one CTA per instance, matrices in shared memory; instances with
 // more landmarks are left to MM = kMLarge: one CTA per listed instance, the same
