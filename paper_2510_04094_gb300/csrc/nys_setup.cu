@@ -6,7 +6,8 @@
 // (Golub & Van Loan, Matrix Computations, Sec. 8.5) with the round-robin
 // ("chess tournament") ordering, so the m/2 rotations of a round touch
 // disjoint row/column pairs and run concurrently.  A and the rotation
-// accumulator V live in shared memory (2 m (m+1) doubles, <= 203 KB).
+// accumulator V live in shared memory (2 m (m+1) doubles, <= 203 KB for
+// m <= kMMax); larger landmark sets use a global (L2-resident) area instead.
 #include "nys_internal.cuh"
 
 namespace nys {
