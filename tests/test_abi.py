@@ -97,3 +97,51 @@ def test_invalid_condition_fields_are_rejected_on_the_host(abi, field, value):
 def test_status_strings(abi):
     for code in range(0, -10, -1):
         assert abi.lib().nys_status_str(code)
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <string.h>
+#include "nys.h"
+
+int main(void) {
+  /* every declaration of the header is visible to a plain C99 translation unit */
+  int32_t (*fs)(nys_ctx**, const nys_instance*, int32_t, const nys_options*, void*) = nys_setup;
+  int32_t (*fr)(nys_ctx*, void*, double*, int32_t*) = nys_run;
+  if (!fs || !fr) return 3;
+  nys_instance q;
+  memset(&q, 0, sizeof q);
+  q.p = 9;                       /* invalid order: rejected on the host, no device touched */
+  nys_options opt;
+  memset(&opt, 0, sizeof opt);
+  nys_ctx* ctx = NULL;
+  const int32_t r = nys_setup(&ctx, &q, 1, &opt, NULL);
+  if (r != NYS_EINVAL || ctx != NULL) return 1;
+  printf("%s|%s|%d|%d\n", nys_status_str(NYS_ENOTSPD), nys_last_error(), NYS_M_MAX,
+         NYS_M_MAX_MIXED);
+  return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_links(abi, tmp_path):
+    """include/nys.h compiles as C99 with warnings as errors, a C program links
+    against libnys.so and gets host-side validation from it without a GPU."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_nys.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "use_nys"
+    libdir = os.path.dirname(abi._build.LIB_PATH)
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-o", str(exe), "-L", libdir, "-lnys", "-Wl,-rpath," + libdir],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, (out.returncode, out.stderr)
+    status, err, mmax, mmix = out.stdout.strip().split("|")
+    assert err.startswith("instance 0") and "p must be" in err
+    assert int(mmax) == abi.NYS_M_MAX and int(mmix) == abi.NYS_M_MAX_MIXED
+    assert status
