@@ -71,8 +71,8 @@ typedef enum {
 
 /* Conditions of an instance (Section 2: initial or boundary conditions).   */
 typedef enum {
-  /* initial values (Lemma 1): y(t_1) = v[0], y'(t_1) = v[1] (p = 2);
-     collocation rows i = 2..n                                              */
+  /* initial values (Lemma 1): y^(k)(t_1) = v[k], k < p (y(t_1) = v[0],
+     y'(t_1) = v[1] for p = 2); collocation rows i = 2..n                   */
   NYS_BC_IVP = 0,
   /* boundary values (Appendix A.4, BVP case; for the nonlinear kind in the
      Lagrangian of its Problem 15 example): p = 2: y(t_1) = v[0],

@@ -145,3 +145,27 @@ def test_header_is_plain_c_and_links(abi, tmp_path):
     assert err.startswith("instance 0") and "p must be" in err
     assert int(mmax) == abi.NYS_M_MAX and int(mmix) == abi.NYS_M_MAX_MIXED
     assert status
+
+
+def test_readme_c_example_compiles_and_links(abi, tmp_path):
+    """The C usage example in README.md compiles (C99, -Werror) and links against
+    libnys.so and the CUDA runtime (it needs a GPU to run)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    if gcc is None or not os.path.exists(os.path.join(cuda, "include", "cuda_runtime.h")):
+        pytest.skip("no C compiler or CUDA headers")
+    readme = open(os.path.join(ROOT, "README.md")).read()
+    blocks = re.findall(r"```c\n(.*?)```", readme, flags=re.S)
+    assert len(blocks) == 1
+    src = tmp_path / "example.c"
+    src.write_text(blocks[0])
+    libdir = os.path.dirname(abi._build.LIB_PATH)
+    cudalib = next((d for d in (os.path.join(cuda, "lib64"), os.path.join(cuda, "lib"))
+                    if os.path.isdir(d)), None)
+    cmd = [gcc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+           "-I", os.path.join(cuda, "include"), str(src), "-o", str(tmp_path / "example"),
+           "-L", libdir, "-lnys", "-L", cudalib, "-lcudart", "-Wl,-rpath," + libdir]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
