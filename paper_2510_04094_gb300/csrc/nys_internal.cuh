@@ -56,7 +56,8 @@ struct Lset {
   int32_t n, K;        // K: largest tabulated lag, exp(-(K h/sigma)^2) < 1e-34
   int32_t active;
   int32_t omode;       // 1: ill-conditioned landmark kernel (smallest kept eigenvalue
-                       // < kOmegaCond * largest): row passes project every row
+                       // < kOmegaCond * largest; FP64 contexts: span beyond
+                       // kKernelSpan / sqrt(n)): row passes project every row
                        // through W (omega coordinates) instead of accumulating in
                        // kernel coordinates, which would lose precision there
   int64_t lm_off;
@@ -67,6 +68,12 @@ struct Lset {
 // Largest lag whose kernel value is kept: (K hs)^2 <= kLagU.
 constexpr double kLagU = 80.0;
 constexpr double kOmegaCond = 1e-7;
+// FP64 contexts: the kernel-coordinate Gram W G W^T rounds to about
+// cond u sqrt(n) relative (cond = lambda_max / lambda_min of the kept
+// eigenvalues, u = 2^-53, n rows); a set uses it only while that stays below
+// 1e-11 (cond sqrt(n) <= 1e-11 / u), otherwise omega coordinates, whose
+// per-row projection rounds like the definition's own phi = W k.
+constexpr double kKernelSpan = 1e-11 * 9007199254740992.0;
 
 // One unit of a row pass: rows i in [r0, r1) (0-based grid index, 1 <= i <= n-1).
 struct Work {

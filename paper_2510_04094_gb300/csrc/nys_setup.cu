@@ -225,8 +225,9 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict_
   // an orthogonal map of omega-space, hence the same fit (Appendix A.3's factor
   // Lambda^-1/2 U^T is one such W).  With Omega = L L^T, W = L^-1 costs m^3/3
   // + m^3/3 FP64 flops instead of a Jacobi eigendecomposition's ~10 sweeps.
-  // It is used when cond(Omega) <= m |W|_F^2 <= 1e6: nothing would be
-  // truncated and the kernel-coordinate Gram keeps its precision.  Only for
+  // It is used when the bound cond(Omega) <= |Omega|_inf |W|_F^2 certifies
+  // that nothing would be truncated and that the kernel-coordinate Gram keeps
+  // its precision (cond(Omega) sqrt(n) <= kKernelSpan).  Only for
   // FP64 solves (allow_chol): L^-1 has large alternating entries, and the FP32
   // factor of the mixed path built from it refines about ten times slower
   // than one built from the nearly orthogonal rows of Lambda^-1/2 U^T.
@@ -239,6 +240,14 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict_
     __shared__ int s_bad;
     if (tid == 0) s_bad = 0;
     __syncthreads();
+    // |Omega|_2 <= |Omega|_inf (largest row sum; the entries are positive)
+    double rmax = 0.0;
+    for (int j = tid; j < m; j += nt) {
+      double rs = 0.0;
+      for (int l = 0; l < m; ++l) rs += V[j * ld + l];
+      rmax = fmax(rmax, rs);
+    }
+    rmax = block_max(rmax, red);
     for (int k = 0; k < m; ++k) {   // lower Cholesky of Omega in V
       if (tid == 0) {
         const double d = V[k * ld + k];
@@ -273,7 +282,10 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict_
         f2 += w * w;
       }
       f2 = block_sum(f2, red);
-      const bool chol_ok = allow_chol && (s_bad == 0) && isfinite(f2) && ((double)m * f2 <= 1e6);
+      // cond(Omega) <= |Omega|_inf |Omega^-1|_2 <= rmax |W|_F^2 certifies that the
+      // kernel-coordinate Gram stays within its FP64 budget (kKernelSpan)
+      const bool chol_ok = allow_chol && (s_bad == 0) && isfinite(f2) &&
+                           (rmax * f2 * sqrt((double)S.n) <= kKernelSpan);
       if (chol_ok) {
         for (int e = tid; e < m * m; e += nt) {
           const double w = A[(e / m) * ld + (e % m)];
@@ -389,7 +401,11 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict_
     int me = 0;
     while (me < m && A[perm[me] * ld + perm[me]] > tau * lmax) ++me;
     lsets[L].m_eff = me;
-    lsets[L].omode = (A[perm[me - 1] * ld + perm[me - 1]] < kOmegaCond * lmax) ? 1 : 0;
+    const double lmin = A[perm[me - 1] * ld + perm[me - 1]];
+    // omega coordinates: a span beyond what the FP32 factor or (FP64 contexts,
+    // allow_chol) the FP64 kernel-coordinate Gram can carry, see kKernelSpan
+    lsets[L].omode = (lmin < kOmegaCond * lmax ||
+                      (allow_chol && lmax > lmin * (kKernelSpan / sqrt((double)S.n)))) ? 1 : 0;
     red[0] = (double)me;
   }
   __syncthreads();

@@ -2,11 +2,11 @@
 
 The oracle differentiates the kernel-coordinate form of Lemma 1's problem by
 the complex-step method (exact to rounding for this real-analytic map) and, as a
-second route, by central differences of the eigen-route solver.  Both GPU and
-oracle work in FP64 on a problem whose KKT matrix has condition ~gamma n
-(1e13-1e14 here), so the entries agree to the level that separates the two
-oracle routes (about 1e-6 of the largest entry, measured); the bound is 1e-5 of
-the largest entry of the oracle's gradient.
+second route, by central differences of the eigen-route solver.  Against the
+complex step the bound is 1e-8 of the largest entry of the oracle's gradient
+(measured on the gradient workload's family: at most 1.2e-13).  Central
+differences carry their own truncation error (about 1e-6 here) and are held to
+1e-4.
 """
 import numpy as np
 import pytest
@@ -15,7 +15,7 @@ import nys_inputs as ni
 from oracle import adjoint, core
 
 pytestmark = pytest.mark.gpu
-RTOL = 1e-5
+RTOL = 1e-8
 
 
 @pytest.fixture(scope="module")

@@ -78,6 +78,74 @@ def test_metric_family_full_size_sample(api, precision):
     _check(api, ni.m0(4), precision)
 
 
+def _sampled(api, probs, bt, pick, tol):
+    """Fitted y, y' and b of the instances `pick` (increasing) of a solved batch
+    against the oracle, queried through nys_eval at each instance's own grid."""
+    import torch
+    B = len(probs)
+    grids = [core.grid(probs[k]) for k in pick]
+    lens = np.zeros(B, dtype=np.int64)
+    for k, g in zip(pick, grids):
+        lens[k] = len(g)
+    off = torch.tensor(np.r_[0, np.cumsum(lens)], dtype=torch.int64, device="cuda")
+    tq = torch.tensor(np.concatenate(grids), dtype=torch.float64, device="cuda")
+    y, _ = bt.eval(tq, off)
+    y1, _ = bt.eval(tq, off, deriv=1)
+    yc, y1c = y.cpu().numpy(), y1.cpu().numpy()
+    sols = bt.unpack()
+    pos, worst = 0, 0.0
+    for k, g in zip(pick, grids):
+        ref = core.solve_linear(probs[k])
+        scale = np.abs(ref["y"]).max()
+        err = np.abs(yc[pos:pos + len(g)] - ref["y"]).max() / scale
+        d1 = core.evaluate(probs[k], ref, g, 1)
+        err1 = np.abs(y1c[pos:pos + len(g)] - d1).max() / np.abs(d1).max()
+        eb = abs(sols[k]["b"] - ref["b"]) / max(1.0, scale)
+        pos += len(g)
+        worst = max(worst, err)
+        assert err <= tol, (k, err)
+        assert err1 <= 50 * tol, (k, err1)
+        assert eb <= 10 * tol, (k, eb)
+    return worst
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_metric_batch_full_size_sampled(api, precision):
+    """The throughput workload itself, 4096 instances at n = 1e4, m = 50, in the
+    launch configuration bench.py times (one nys_run graph; mixed: the default
+    single refinement pass), so that every CTA takes many work items and the
+    tensor-core kernel cycles through its accumulator sets; instances sampled
+    across the cost-sorted work list against the oracle."""
+    import torch
+    probs = ni.m0(4096)
+    bt = api.Batch(probs, precision=precision)
+    for _ in range(2):          # the graph is captured once, then replayed
+        x, st = bt.run()
+    torch.cuda.synchronize()
+    assert (st.cpu().numpy() == 0).all()
+    _sampled(api, probs, bt, [0, 1, 777, 2048, 4095], TOL[precision])
+    bt.close()
+
+
+def _cap_m_batch():
+    """Linear instances at the mixed path's landmark cap, sigma = 1.5 landmark
+    spacings: the band of a row spans ~27 landmarks, and grids with few rows per
+    landmark spacing make a work item's window 35-80 landmarks wide, so the
+    tensor-core kernel packs P = 2 (window + 2 <= 64) and P = 1 (> 64) blocks per
+    operand tile besides the usual P = 4."""
+    fam = ni.linear_family(6, n=1000, m=100, T=10.0, name="small", sub=31)
+    shapes = [(140, 112), (130, 112), (700, 101), (400, 105), (3000, 112), (1000, 101)]
+    out = []
+    for q, (n, m) in zip(fam, shapes):
+        out.append(dict(q, n=n, m=m, sigma=1.5 * (q["t1"] - q["t0"]) / (m - 1)))
+    return out
+
+
+@pytest.mark.parametrize("precision", ["mixed", "mixed-simt", "fp64"])
+def test_landmark_cap_wide_windows(api, precision):
+    _check(api, _cap_m_batch(), precision)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed-simt"])
 def test_cfg2_linear_full_size(api, precision):
     _check(api, [ni.cfg2_linear()], precision)
