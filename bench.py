@@ -11,6 +11,13 @@ refinement for the whole batch (nys_run, one CUDA graph), inputs resident.
 
 Prints one JSON line (rank 0).  Under torchrun each rank solves its own batch
 (weak scaling; no collective on the data path, one all-reduce for the timing).
+
+Roofline: the dominant kernel's rate counts the method's own arithmetic, F(m) =
+2m^2 (projection phi = W k) + (m+1)(m+2) (upper-triangle Gram) + 2(m+1) (right-hand
+side) + 10m (operator) FLOPs per collocation row, and divides it by the measured
+peak of the pipe its contraction runs on (include/nys_peak.h probes, run in the
+same process).  The FLOPs the kernel actually issues on that pipe are reported
+beside it.
 """
 import argparse
 import json
@@ -27,12 +34,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "batched ODE solves/s at n=1e4, m=50"
 UNIT = "solves/s"
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2070 MHz
-# DRAM bytes (read + write) of one k_assemble_tc launch per instance, from an ncu
-# capture of 304 instances of this workload (dram__bytes_read.sum 285.4 KB +
-# dram__bytes_write.sum 0.3 KB); the kernel keeps its operands on chip, its HBM
-# traffic is work descriptors and landmark indices only
-TC_DRAM_BYTES_PER_INSTANCE = (285.44e3 + 0.256e3) / 304
+LAG_U = 80.0   # kernel values exp(-u) with u > 80 (< 2e-35) are treated as zero
+# DRAM bytes (read + write) of one k_assemble_tc launch per instance of the
+# metric family, from an ncu capture of the current kernel (None: no capture of
+# the current kernel yet)
+TC_DRAM_BYTES_PER_INSTANCE = None
 
 
 def parse():
@@ -45,8 +51,8 @@ def parse():
     ap.add_argument("--n", type=int, default=10_000)
     ap.add_argument("--m", type=int, default=50)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--no-extras", action="store_true", help="skip FP64/oracle side measurements")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-extras", action="store_true", help="skip the side measurements")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--long-time", action="store_true",
                     help="only time the long-time single instances (n = 5e4, m = 200) by phase")
     return ap.parse_args()
@@ -84,7 +90,7 @@ def job_rate(ms_local, B, ws, device=None):
 
 
 class Clocks:
-    """nvidia-smi sampler (SM clock, max clock, throttle reasons) during the timed region."""
+    """nvidia-smi sampler (SM clock, max clock, throttle reasons) during a timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -103,6 +109,7 @@ class Clocks:
             self.th.start()
         except Exception:
             self.proc = None
+        return self
 
     def _read(self):
         for line in self.proc.stdout:
@@ -116,7 +123,7 @@ class Clocks:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, mx, reasons = [], [], set()
+        sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
@@ -125,6 +132,7 @@ class Clocks:
             try:
                 sm.append(float(f[1]))
                 mx.append(float(f[2]))
+                pw.append(float(f[3]))
             except ValueError:
                 continue
             for nm, val in zip(names, f[5:9]):
@@ -133,65 +141,126 @@ class Clocks:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "power_w_max": max(pw), "samples": len(sm)}
 
 
-LAG_U = 80.0   # kernel values exp(-u) with u > 80 (< 2e-35) are treated as zero
+# ---- FLOP counts ------------------------------------------------------------------
+def F_row(m):
+    """The method's FLOPs per collocation row: 2m^2 (projection) + (m+1)(m+2) (Gram,
+    upper triangle, FMA = 2) + 2(m+1) (right-hand side) + 10m (operator)."""
+    return 2 * m * m + (m + 1) * (m + 2) + 2 * (m + 1) + 10 * m
 
 
-def _band_counts(q):
-    """Per collocation row i = 1..n-1: number of landmarks j with |i - idx_j| <= K,
-    K = min(n - 1, ceil(sqrt(80) sigma / h)) (the band of the RBF features)."""
+def rows_of(q):
+    return q["n"] - 1 - (1 if q.get("bc") == "bvp" else 0)
+
+
+def dense_flops(problems):
+    return float(sum(rows_of(q) * F_row(q["m"]) for q in problems))
+
+
+def _band(q):
     import numpy as np
     n, m = q["n"], q["m"]
     h = (q["t1"] - q["t0"]) / (n - 1)
     K = int(min(n - 1, math.ceil(math.sqrt(LAG_U) / (h / q["sigma"]))))
     j = np.arange(m)
     idx = (j * (n - 1) + (m - 1) // 2) // (m - 1)
-    i = np.arange(1, n)
-    return np.searchsorted(idx, i + K, side="right") - np.searchsorted(idx, i - K, side="left")
+    return idx, K
 
 
-def asm_flops(problems):
-    """Algorithmic FLOPs of one fused assembly pass over the banded features: per
-    row, with a_i landmarks inside the band, (a_i + 2)(a_i + 3) for the upper
-    triangle of the augmented Gram (FMA = 2) + 6 a_i for the feature polynomials
-    (exponentials run on the SFU and are not counted)."""
+def banded_flops(problems):
+    """FLOPs of the Gram over the landmarks inside each row's band (a_i of them):
+    (a_i + 2)(a_i + 3) + 6 a_i per row (exponentials on the SFU, not counted)."""
     import numpy as np
-    cache, tot = {}, 0
+    cache, tot = {}, 0.0
     for q in problems:
         key = (q["n"], q["m"], q["t0"], q["t1"], q["sigma"])
         if key not in cache:
-            a = _band_counts(q).astype(float)
+            idx, K = _band(q)
+            i = np.arange(1, q["n"])
+            a = (np.searchsorted(idx, i + K, side="right") - np.searchsorted(idx, i - K, side="left")).astype(float)
             cache[key] = float(np.sum((a + 2) * (a + 3) + 6 * a))
         tot += cache[key]
     return tot
 
 
-def dense_flops(problems):
-    """The dense minimum form of the method per row, 2m^2 (projection) + (m+1)(m+2)
-    (Gram) + 2(m+1) (right-hand side) + 10m (operator), counted without the band."""
-    return sum((q["n"] - 1) * (2 * q["m"] ** 2 + (q["m"] + 1) * (q["m"] + 2) + 2 * (q["m"] + 1)
-                               + 10 * q["m"]) for q in problems)
+def tc_issued_flops(problems, rpi):
+    """TF32 MMA FLOPs k_assemble_tc issues for the batch: per work item of `rows`
+    rows whose landmark window holds A landmarks (M2 = A + 2 columns), P = 4, 2, 1
+    blocks of 128 / P slots share each 128-row operand tile (M2 <= 32, <= 64, else),
+    a stage covers 32 P rows in 4 K steps of 8, and each K step issues
+    kTcMmaPerStep MMAs of 128 x N x 8 (N = 128 when P > 1, else M2 rounded up to 16)."""
+    cache, tot = {}, 0.0
+    for q in problems:
+        key = (q["n"], q["m"], q["t0"], q["t1"], q["sigma"])
+        if key not in cache:
+            import numpy as np
+            idx, K = _band(q)
+            nrows = rows_of(q)
+            chunks = max(1, -(-nrows // rpi))
+            f = 0.0
+            for k in range(chunks):
+                r0 = 1 + nrows * k // chunks
+                r1 = 1 + nrows * (k + 1) // chunks
+                A = int(np.searchsorted(idx, r1 - 1 + K, side="right") - np.searchsorted(idx, r0 - K, side="left"))
+                M2 = A + 2
+                P = 4 if M2 <= 32 else (2 if M2 <= 64 else 1)
+                N = 128 if P > 1 else -(-M2 // 16) * 16
+                nst = -(-(r1 - r0) // (32 * P))
+                f += nst * 4 * TC_MMA_PER_KSTEP * 2.0 * 128 * N * 8
+            cache[key] = f
+        tot += cache[key]
+    return tot
 
 
-def oracle_rate(problems, seconds):
-    """Oracle solves/s on a bounded sample (the oracle as it stands, numpy FP64)."""
+TC_MMA_PER_KSTEP = 3   # hi hi^T, hi lo^T, lo hi^T
+
+
+# ---- CPU oracle baseline ---------------------------------------------------------------
+def _oracle_worker(job):
+    """Solve problems with the oracle (numpy FP64, one BLAS thread) for about
+    `seconds`; returns (count, elapsed).  Runs in a spawned process."""
+    probs, seconds = job
     from oracle import core
     t0 = time.perf_counter()
     k = 0
-    while k < len(problems):
-        core.solve_linear(problems[k])
+    for q in probs:
+        core.solve_linear(q)
         k += 1
         if time.perf_counter() - t0 > seconds:
             break
-    dt = time.perf_counter() - t0
-    return k / dt, k, dt
+    return k, time.perf_counter() - t0
+
+
+def oracle_baseline(problems, seconds, workers):
+    """Oracle solves/s on `workers` host cores (one single-threaded process per
+    core, spawned), each solving its own slice of the batch for ~`seconds`.
+    Returns (solves/s, solved, wall seconds)."""
+    import multiprocessing as mp
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(workers) as pool:
+            pool.map(_oracle_worker, [(problems[:1], 0.0)] * workers)   # imports, BLAS start-up
+            per = max(1, len(problems) // workers)
+            jobs = [(problems[w * per:(w + 1) * per] or problems[:per], seconds) for w in range(workers)]
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_worker, jobs)
+            wall = time.perf_counter() - t0
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    done = sum(r[0] for r in res)
+    return done / wall, done, wall
 
 
 def workload_config(args, ws):
-    """The workload both arms report (the reference arm times the oracle on a
-    bounded sample of this same batch)."""
     return {"workload": "linear 2nd-order ODE batch y''+ay'+by=c sin(wt), n=%d, m=%d, "
                         "sigma=0.5, gamma=1e10, %s" % (args.n, args.m, args.precision),
             "global_batch": ws * args.batch, "seq_len": args.n, "parallelism": "dp%d" % ws,
@@ -199,30 +268,61 @@ def workload_config(args, ws):
 
 
 def run_reference(args, rank, ws):
+    """The oracle (the paper ships no code) on the host cores, one process per core."""
     import nys_inputs as ni
     if rank != 0:
         return
     probs = ni.m0(args.batch, n=args.n, m=args.m)
+    cores = os.cpu_count() or 1
     per_step = max(0.5, min(4.0, 60.0 / max(1, args.steps + args.warmup)))
-    for _ in range(args.warmup):
-        oracle_rate(probs[:2], per_step / 4)
-    rates, tot_k, tot_t = [], 0, 0.0
+    oracle_baseline(probs[:cores], 0.05, cores)                    # warm-up
+    tot_k, tot_t = 0, 0.0
     for s in range(args.steps):
-        r, k, dt = oracle_rate(probs[s * 3:], per_step)
-        rates.append(r)
+        rate, k, wall = oracle_baseline(probs, per_step, cores)
         tot_k += k
-        tot_t += dt
+        tot_t += wall
     value = tot_k / tot_t
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": workload_config(args, args.gpus),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": "%d instances of the workload, %.1f s" % (tot_k, tot_t)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d instances of the workload, numpy FP64 oracle, %d "
+                                       "single-threaded processes, %.1f s" % (tot_k, cores, tot_t)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
     print(json.dumps(line), flush=True)
+
+
+# ---- GPU side measurements -------------------------------------------------------------
+def ev_ms(fn, reps, stream, flush=None):
+    """Mean ms of fn() over reps launches, CUDA events on `stream` (L2 flushed
+    before each, outside the events)."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        ts.append((a, b))
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ts) / reps
+
+
+def measure_peaks(local):
+    from paper_2510_04094_gb300 import peaks
+    clk = Clocks(local).start()
+    time.sleep(0.3)
+    out = {k: peaks.measure(k) for k in ("tf32_mma", "bf16_mma", "ffma", "dfma")}
+    out["clocks"] = clk.stop()
+    return out
 
 
 def long_time_breakdown(Batch, ni, torch):
@@ -231,25 +331,12 @@ def long_time_breakdown(Batch, ni, torch):
     side stream), per nys_assemble and per nys_solve, each the mean of 3 calls
     timed with CUDA events on the launching stream."""
     stream = torch.cuda.current_stream()
-
-    def ev_ms(fn, reps=3):
-        fn()
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(reps):
-            fn()
-        b.record(stream)
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / reps
-
     out = {}
     for nm in ("P3", "P9"):
         q, _ = ni.long_time(nm)
         bt = Batch([q], precision="fp64")
-        res = {"n": q["n"], "m": q["m"], "run_ms": ev_ms(bt.run), "assemble_ms": ev_ms(bt.assemble),
-               "solve_ms": ev_ms(bt.solve)}
+        res = {"n": q["n"], "m": q["m"], "run_ms": ev_ms(bt.run, 3, stream),
+               "assemble_ms": ev_ms(bt.assemble, 3, stream), "solve_ms": ev_ms(bt.solve, 3, stream)}
         _, st = bt.solve()
         torch.cuda.synchronize()
         res["m_eff"] = int(bt.m_eff()[0])
@@ -259,20 +346,188 @@ def long_time_breakdown(Batch, ni, torch):
     return out
 
 
+def rel_err_sample(bt, probs, ks):
+    """Max relative error of the fitted y of instances ks against the oracle."""
+    import numpy as np
+    import torch
+    from oracle import core
+    grids = [core.grid(probs[k]) for k in ks]
+    lens = np.zeros(len(probs), dtype=np.int64)
+    for k, g in zip(ks, grids):
+        lens[k] = len(g)
+    off = torch.tensor(np.r_[0, np.cumsum(lens)], dtype=torch.int64, device="cuda")
+    tq = torch.tensor(np.concatenate(grids), dtype=torch.float64, device="cuda")
+    y, _ = bt.eval(tq, off)
+    yc = y.cpu().numpy()
+    pos, errs = 0, []
+    for k, g in zip(ks, grids):
+        ref = core.solve_linear(probs[k])["y"]
+        errs.append(float(np.abs(yc[pos:pos + len(g)] - ref).max() / np.abs(ref).max()))
+        pos += len(g)
+    return max(errs)
+
+
+def side_measurements(args, probs, bt, value, ws, local, stream, flush, peaks_out):
+    """Everything beside the metric line's own numbers (rank 0): accuracy, the plain
+    FP64 path on the same batch, per-kernel rooflines, other workloads."""
+    import numpy as np
+    import torch
+    import nys_inputs as ni
+    from paper_2510_04094_gb300.api import Batch
+
+    ex = {}
+    pk = peaks_out
+    dfma, ffma = pk["dfma"]["tflops"], pk["ffma"]["tflops"]
+    B = len(probs)
+    ex["rel_err_vs_oracle_max"] = rel_err_sample(bt, probs, [0, 1, 777, 2048, B - 1] if B > 2048 else [0, B - 1])
+    ex["status_ok"] = bool((bt.status.cpu().numpy() == 0).all())
+
+    # refinement pass: the default solve (k_solve + one refinement pass) minus a
+    # solve without refinement, both after the same assembly
+    b0 = Batch(probs, precision=args.precision, refine_steps=0)
+    b0.assemble()
+    solve0 = ev_ms(b0.solve, 5, stream, flush)
+    b0.close()
+    solve1 = ev_ms(bt.solve, 5, stream, flush)
+    ref_fl = float(sum(rows_of(q) * 4 * q["m"] for q in probs))
+    ex["solve_ms"] = {"k_solve": solve0, "k_solve_plus_one_refinement": solve1}
+    rows = {}
+    if args.precision == "mixed":
+        t = max(1e-6, solve1 - solve0)
+        ach = ref_fl / (t * 1e-3) / 1e12
+        rows["refinement_pass"] = {
+            "kernels": "k_refine_rows + k_refine_update", "ms": t,
+            "flop_count": "4m per row (residual and its projection), FP64-accurate (float-float)",
+            "achieved_tflops": ach, "frac_of_dfma": ach / dfma, "frac_of_ffma": ach / ffma}
+
+    # the plain FP64 path on the same batch: batched (one graph) and per instance
+    b64 = Batch(probs, precision="fp64")
+    ms64 = ev_ms(b64.run, 3, stream, flush)
+    asm64 = ev_ms(b64.assemble, 3, stream, flush)
+    _, st64 = b64.run()
+    torch.cuda.synchronize()
+    fp64_err = rel_err_sample(b64, probs, [0, B - 1])
+    b64.close()
+    fl = dense_flops(probs)
+    exec64 = float(sum(rows_of(q) * ((q["m"] + 2) * (q["m"] + 3) + 12 * q["m"]) for q in probs))
+    rows["k_assemble_f64"] = {
+        "ms": asm64, "achieved_tflops": fl / (asm64 * 1e-3) / 1e12,
+        "peak_tflops": dfma, "frac": fl / (asm64 * 1e-3) / 1e12 / dfma,
+        "issued_tflops": exec64 / (asm64 * 1e-3) / 1e12,
+        "pipe_frac": exec64 / (asm64 * 1e-3) / 1e12 / dfma,
+        "flop_count": "F(m) per row; issued: (m+2)(m+3) Gram + 12m operator per row"}
+    single = Batch(probs[:1], precision="fp64")
+    from paper_2510_04094_gb300 import _abi
+    from paper_2510_04094_gb300.api import pack_instances, _stream_handle
+    packed = [pack_instances([q]) for q in probs]
+    single.run()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for arr, _keep in packed:                   # each instance by its own launch sequence
+        _abi.nys_update(single.ctx, arr, _stream_handle())
+        single.run()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_pi = a.elapsed_time(b)
+    single.close()
+    ex["fp64_path"] = {
+        "instances": B, "timing": "CUDA events on the launching stream",
+        "batched": {"ms_per_step": ms64, "solves_s": B / (ms64 * 1e-3),
+                    "status_ok": bool((st64.cpu().numpy() == 0).all()), "rel_err_vs_oracle_max": fp64_err},
+        "per_instance": {"ms_total": ms_pi, "solves_s": B / (ms_pi * 1e-3),
+                         "how": "one single-instance context; per instance nys_update + nys_run"}}
+    ex["speedup_vs_fp64_batched"] = value / ws / ex["fp64_path"]["batched"]["solves_s"]
+    ex["speedup_vs_fp64_per_instance"] = value / ws / ex["fp64_path"]["per_instance"]["solves_s"]
+
+    # adjoint gradient (nys_grad): 1024 instances, n = 5000, m = 50, 200 observations, FP64
+    g4, tau4, yobs4 = ni.cfg4()
+    bg = Batch(g4, precision="fp64")
+    tq, tq_off = bg._queries(list(tau4), None)
+    bg.run()
+    yq, _ = bg.eval(tq, tq_off)
+    u = 2.0 * (yq - torch.tensor(np.concatenate(yobs4), device=yq.device)) / tau4.shape[1]
+    gms = ev_ms(lambda: bg.grad(tq, tq_off, u), 5, stream, flush)
+    gfl = float(sum(rows_of(q) * 12 * q["m"] for q in g4))
+    rows["nys_grad"] = {"instances": len(g4), "ms": gms,
+                        "flop_count": "12m per row (adjoint row pass)",
+                        "achieved_tflops": gfl / (gms * 1e-3) / 1e12,
+                        "frac_of_dfma": gfl / (gms * 1e-3) / 1e12 / dfma,
+                        "fp64_solve_ms": ev_ms(bg.run, 3, stream, flush)}
+    bg.close()
+
+    # batched Newton family: 64 logistic / Duffing instances, n in [2000, 1e4], FP64, cap 20
+    b5 = Batch(ni.cfg5(), precision="fp64")
+    ms5 = ev_ms(lambda: b5.newton(max_iter=20, tol=1e-10), 2, stream)
+    _, st5, it5, _ = b5.newton(max_iter=20, tol=1e-10)
+    its = it5.cpu().numpy()
+    nfl = float(sum(rows_of(q) * (4 * q["m"] ** 2 + 3 * (q["m"] + 1) ** 2) * (int(k) + 1)
+                    for q, k in zip(b5.problems, its)))
+    rows["nys_newton"] = {"instances": len(b5.problems), "ms": ms5,
+                          "iterations_max": int(its.max()), "converged": int((st5 == 0).sum().item()),
+                          "flop_count": "(4m^2 + 3(m+1)^2) per row and row pass (iterations + 1 passes)",
+                          "achieved_tflops": nfl / (ms5 * 1e-3) / 1e12,
+                          "frac_of_dfma": nfl / (ms5 * 1e-3) / 1e12 / dfma}
+    b5.close()
+    ex["rooflines"] = rows
+
+    # ragged batched family: 4096 instances, n log-uniform in [500, 2e4], m in
+    # {20, 32, 50, 64, 100}, sigma = T/m, one CUDA graph per step
+    r3 = Batch(ni.cfg3(), precision="mixed")
+    ms3 = ev_ms(r3.run, 3, stream, flush)
+    ex["ragged_4096"] = {"ms_per_step": ms3, "solves_s": len(r3.problems) / (ms3 / 1000.0),
+                         "rows": int(sum(q["n"] - 1 for q in r3.problems))}
+    r3.close()
+    # boundary value family (Appendix A.4): 4096 x (n = 1e4, m = 50), mixed, default
+    # refinement for boundary values (two passes)
+    pb = ni.bvp_family(4096)
+    rb = Batch(pb, precision="mixed")
+    msb = ev_ms(rb.run, 3, stream, flush)
+    ex["bvp_4096"] = {"ms_per_step": msb, "solves_s": 4096 / (msb / 1000.0), "refine_passes": 2,
+                      "rel_err_vs_oracle_max": rel_err_sample(rb, pb, [0, 1, 4095]),
+                      "status_ok": bool((rb.status.cpu().numpy() == 0).all())}
+    rb.close()
+    single = {}
+    for prec in ("fp64", "mixed"):
+        s1 = Batch([ni.cfg2_linear()], precision=prec)
+        single["linear_" + prec + "_ms"] = ev_ms(s1.run, 3, stream)
+        s1.close()
+    sn = Batch([ni.cfg2_tanh()], precision="fp64")
+    single["tanh_newton_ms"] = ev_ms(lambda: sn.newton(max_iter=50, tol=1e-10), 2, stream)
+    sn.close()
+    ex["single_n1e4"] = single
+    try:
+        ex["long_time_n5e4_m200"] = long_time_breakdown(Batch, ni, torch)
+    except Exception as e:   # a side measurement must not cost the metric line
+        ex["long_time_n5e4_m200"] = {"error": repr(e)[:200]}
+    try:
+        hp = ni.small_higher(1024, sub=7, n_choices=(1000, 2000), m_choices=(20, 32))
+        bh = Batch(hp, precision="fp64")
+        msh = ev_ms(bh.run, 3, stream, flush)
+        _, sth = bh.run()
+        torch.cuda.synchronize()
+        ex["higher_order_1024"] = {"ms_per_step": msh, "solves_s": len(hp) / (msh / 1000.0),
+                                   "status_ok": bool((sth.cpu().numpy() == 0).all())}
+        bh.close()
+    except Exception as e:
+        ex["higher_order_1024"] = {"error": repr(e)[:200]}
+    return ex
+
+
 def main():
     args = parse()
     rank, ws, local = dist_init()
     if args.impl == "reference":
         run_reference(args, rank, ws)
         return
-    import numpy as np
     import torch
 
     import __graft_entry__
     __graft_entry__.build()
     import nys_inputs as ni
     from paper_2510_04094_gb300 import _abi
-    from paper_2510_04094_gb300.api import Batch, pack_instances
+    from paper_2510_04094_gb300.api import Batch, pack_instances, _stream_handle
 
     if args.long_time:
         if rank == 0:
@@ -293,8 +548,7 @@ def main():
     for _ in range(max(3, args.warmup)):
         bt.run()
     torch.cuda.synchronize()
-    clocks = Clocks(local)
-    clocks.start()
+    clocks = Clocks(local).start()
     time.sleep(0.3)
     if ws > 1:
         torch.distributed.barrier()
@@ -315,22 +569,10 @@ def main():
     ms = sum(a.elapsed_time(b) for a, b in times) / args.steps
     value, ms = job_rate(ms, B, ws, device="cuda")
 
-    # dominant-kernel timing (fused assembly) on the launching stream
-    asm_ms = []
-    for _ in range(max(3, args.steps)):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        bt.assemble()
-        e1.record(stream)
-        asm_ms.append((e0, e1))
-    torch.cuda.synchronize()
-    asm_ms = sum(a.elapsed_time(b) for a, b in asm_ms) / len(asm_ms)
+    # dominant kernel (fused assembly) on the launching stream
+    asm_ms = ev_ms(bt.assemble, max(3, args.steps), stream, flush)
     bt.solve()
     torch.cuda.synchronize()
-    fl = asm_flops(probs)
-    achieved = fl / (asm_ms / 1000.0) / 1e12
 
     # end to end through the public API: host instances -> H2D -> run -> D2H of x
     x_host = torch.empty_like(bt.x, device="cpu").pin_memory()
@@ -341,7 +583,7 @@ def main():
         arr = arr_next if s % 2 == 0 else arr_same
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _abi.nys_update(bt.ctx, arr, C_stream(stream))
+        _abi.nys_update(bt.ctx, arr, _stream_handle())
         bt.run()
         x_host.copy_(bt.x, non_blocking=True)
         torch.cuda.synchronize()
@@ -349,156 +591,43 @@ def main():
     e2e_s = statistics.mean(e2e_t)
     h2d = int(_abi.nys_upload_bytes(bt.ctx))
     d2h = bt.x.numel() * 8
-    _abi.nys_update(bt.ctx, arr_same, C_stream(stream))
+    _abi.nys_update(bt.ctx, arr_same, _stream_handle())
     bt.run()
     torch.cuda.synchronize()
 
-    extra = {}
-    cpu_base = None
-    if rank == 0 and not args.no_extras:
-        from oracle import core
-        # accuracy of the timed configuration against the FP64 oracle (sampled instances)
-        k = 6
-        grids = [core.grid(q) for q in probs[:k]]
-        y, _ = bt.eval(grids)
-        yc = y.cpu().numpy()
-        off, errs = 0, []
-        for q, g in zip(probs[:k], grids):
-            ref = core.solve_linear(q)["y"]
-            errs.append(float(np.abs(yc[off:off + len(g)] - ref).max() / np.abs(ref).max()))
-            off += len(g)
-        extra["rel_err_vs_oracle_max"] = max(errs)
-        extra["status_ok"] = bool((bt.status.cpu().numpy() == 0).all())
-        # plain FP64 path: batched and one instance per launch sequence
-        sub = probs[:256]
-        b64 = Batch(sub, precision="fp64")
-        b64.run()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(2):
-            b64.run()
-        torch.cuda.synchronize()
-        extra["fp64_batched_solves_s"] = 2 * len(sub) / (time.perf_counter() - t0)
-        b64.close()
-        singles = [Batch([q], precision="fp64") for q in probs[:16]]
-        for sb in singles:
-            sb.run()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for sb in singles:
-            sb.run()
-        torch.cuda.synchronize()
-        extra["fp64_per_instance_solves_s"] = len(singles) / (time.perf_counter() - t0)
-        for sb in singles:
-            sb.close()
-        extra["speedup_vs_fp64_per_instance"] = value / ws / extra["fp64_per_instance_solves_s"]
-        extra["asm_ms"] = asm_ms
-        extra["asm_dense_equiv_tflops"] = dense_flops(probs) / (asm_ms / 1000.0) / 1e12
-        # adjoint gradient (nys_grad) on the parameter-estimation workload:
-        # 1024 instances, n = 5000, m = 50, 200 observations each, FP64
-        g4, tau4, yobs4 = ni.cfg4()
-        bg = Batch(g4, precision="fp64")
-        tq, tq_off = bg._queries(list(tau4), None)
-        bg.run()
-        yq, _ = bg.eval(tq, tq_off)
-        u = 2.0 * (yq - torch.tensor(np.concatenate(yobs4), device=yq.device)) / tau4.shape[1]
-        for _ in range(3):
-            bg.grad(tq, tq_off, u)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e2 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        bg.run()
-        e1.record(stream)
-        for _ in range(5):
-            bg.grad(tq, tq_off, u)
-        e2.record(stream)
-        torch.cuda.synchronize()
-        extra["grad_cfg4"] = {"instances": len(g4), "fp64_solve_ms": e0.elapsed_time(e1),
-                              "grad_ms": e1.elapsed_time(e2) / 5}
-        bg.close()
-
-        def step_ms(batch, fn, reps=3):
-            fn()
-            torch.cuda.synchronize()
-            a = torch.cuda.Event(enable_timing=True)
-            b2 = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            for _ in range(reps):
-                fn()
-            b2.record(stream)
-            torch.cuda.synchronize()
-            return a.elapsed_time(b2) / reps
-
-        # ragged batched family: 4096 instances, n log-uniform in [500, 2e4],
-        # m in {20, 32, 50, 64, 100}, sigma = T/m, one CUDA graph per step
-        r3 = Batch(ni.cfg3(), precision="mixed")
-        ms3 = step_ms(r3, r3.run)
-        extra["ragged_4096"] = {"ms_per_step": ms3, "solves_s": len(r3.problems) / (ms3 / 1000.0),
-                                "rows": int(sum(q["n"] - 1 for q in r3.problems))}
-        r3.close()
-        # boundary value family (Appendix A.4): 4096 x (n = 1e4, m = 50), mixed, the
-        # library's default refinement for boundary values (two passes); error of a
-        # few instances against the FP64 oracle
-        rb = Batch(ni.bvp_family(4096), precision="mixed")
-        msb = step_ms(rb, rb.run)
-        kb = 3
-        gb = [core.grid(q) for q in rb.problems[:kb]]
-        yb, _ = rb.eval(gb)
-        ybc = yb.cpu().numpy()
-        off, errs_b = 0, []
-        for q, g in zip(rb.problems[:kb], gb):
-            ref = core.solve_linear(q)["y"]
-            errs_b.append(float(np.abs(ybc[off:off + len(g)] - ref).max() / np.abs(ref).max()))
-            off += len(g)
-        extra["bvp_4096"] = {"ms_per_step": msb, "solves_s": 4096 / (msb / 1000.0),
-                             "refine_passes": 2, "rel_err_vs_oracle_max": max(errs_b),
-                             "status_ok": bool((rb.status.cpu().numpy() == 0).all())}
-        rb.close()
-        # single instances at the paper's scale (n = 1e4, m = 50): linear FP64 and
-        # mixed, nonlinear y' = 1 - y^2 by Newton (FP64)
-        single = {}
-        for prec in ("fp64", "mixed"):
-            s1 = Batch([ni.cfg2_linear()], precision=prec)
-            single["linear_" + prec + "_ms"] = step_ms(s1, s1.run)
-            s1.close()
-        sn = Batch([ni.cfg2_tanh()], precision="fp64")
-        single["tanh_newton_ms"] = step_ms(sn, lambda: sn.newton(max_iter=50, tol=1e-10), reps=2)
-        sn.close()
-        extra["single_n1e4"] = single
-        # long-time single instances at the sizes of Table 12 (n = 5e4, m = 200, FP64;
-        # factor, assembly and solve per step): Problem 3 (omega coordinates, 111
-        # of 200 eigenpairs kept) and Problem 9 (all 200 kept)
-        try:
-            extra["long_time_n5e4_m200"] = long_time_breakdown(Batch, ni, torch)
-        except Exception as ex:   # a side measurement must not cost the metric line
-            extra["long_time_n5e4_m200"] = {"error": repr(ex)[:200]}
-        # third- and fourth-order batch (FP64, tabulated coefficients): 1024 instances,
-        # n in {1000, 2000}, m in {20, 32}, half of the fourth-order ones with
-        # Problem 16's boundary values
-        try:
-            hp = ni.small_higher(1024, sub=7, n_choices=(1000, 2000), m_choices=(20, 32))
-            bh = Batch(hp, precision="fp64")
-            msh = step_ms(bh, bh.run)
-            _, sth = bh.run()
-            torch.cuda.synchronize()
-            extra["higher_order_1024"] = {"ms_per_step": msh, "solves_s": len(hp) / (msh / 1000.0),
-                                          "status_ok": bool((sth.cpu().numpy() == 0).all())}
-            bh.close()
-        except Exception as ex:
-            extra["higher_order_1024"] = {"error": repr(ex)[:200]}
-        # batched Newton family: 64 logistic / Duffing instances, n in [2000, 1e4], FP64
-        b5 = Batch(ni.cfg5(), precision="fp64")
-        ms5 = step_ms(b5, lambda: b5.newton(max_iter=20, tol=1e-10), reps=2)
-        _, st5, it5, _ = b5.newton(max_iter=20, tol=1e-10)
-        extra["newton_cfg5"] = {"instances": len(b5.problems), "ms": ms5,
-                                "max_iters": int(it5.max().item()),
-                                "converged": int((st5 == 0).sum().item())}
-        b5.close()
-        rate, kk, dt = oracle_rate(probs, args.cpu_seconds)
-        cpu_base = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                    "sample": "first %d instances of the workload, numpy FP64 oracle, %.1f s" % (kk, dt)}
+    roof, extra, cpu_base = None, {}, None
+    if rank == 0:
+        pk = measure_peaks(local)
+        fl = dense_flops(probs)
+        achieved = fl / (asm_ms * 1e-3) / 1e12
+        mixed = args.precision == "mixed"
+        peak = pk["tf32_mma"]["tflops"] if mixed else pk["dfma"]["tflops"]
+        roof = {"bound": "tensor" if mixed else "alu",
+                "kernel": "k_assemble_tc" if mixed else "k_assemble_f64",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": ("measured in this run: tcgen05 kind::tf32 probe, burst" if mixed
+                                else "measured in this run: DFMA probe, burst"),
+                "flop_count": "F(m) = 2m^2+(m+1)(m+2)+2(m+1)+10m per collocation row",
+                "flops_per_launch": fl, "ms_per_launch": asm_ms,
+                "traffic": (TC_DRAM_BYTES_PER_INSTANCE * B if mixed and TC_DRAM_BYTES_PER_INSTANCE
+                            and args.n == 10_000 and args.m == 50 else None)}
+        if mixed:
+            iss = tc_issued_flops(probs, 1024)
+            roof["issued_tflops"] = iss / (asm_ms * 1e-3) / 1e12
+            roof["pipe_frac"] = roof["issued_tflops"] / peak
+            roof["banded_useful_tflops"] = banded_flops(probs) / (asm_ms * 1e-3) / 1e12
+        extra["peaks"] = pk
+        if not args.no_extras:
+            extra.update(side_measurements(args, probs, bt, value, ws, local, stream, flush, pk))
+            cores = os.cpu_count() or 1
+            r1, k1, w1 = oracle_baseline(probs, args.cpu_seconds, 1)
+            rN, kN, wN = oracle_baseline(probs, args.cpu_seconds, cores)
+            cpu_base = {"value": rN, "unit": UNIT, "cores": cores, "kind": "oracle",
+                        "sample": "%d instances of the workload on %d single-threaded processes "
+                                  "(one per host core), numpy FP64 oracle, %.1f s" % (kN, cores, wN),
+                        "single_core": {"value": r1, "threads": 1,
+                                        "sample": "%d instances, one process, one BLAS thread, %.1f s"
+                                                  % (k1, w1)}}
 
     if rank == 0:
         line = {
@@ -509,12 +638,7 @@ def main():
             "config": workload_config(args, ws),
             "e2e": {"value": ws * B / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "roofline": {"bound": "alu", "kernel": "k_assemble_tc" if args.precision == "mixed"
-                         else "k_assemble_f64", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                         "traffic": (TC_DRAM_BYTES_PER_INSTANCE * B if args.precision == "mixed"
-                                     and args.n == 10_000 and args.m == 50 else None),
-                         "flops_per_launch": fl, "ms_per_launch": asm_ms},
+            "roofline": roof,
             "cpu_baseline": cpu_base,
             "clocks": clk,
             "gpu_launches": launches_per_step * args.steps,
@@ -524,11 +648,6 @@ def main():
     bt.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
-
-
-def C_stream(stream):
-    import ctypes
-    return ctypes.c_void_p(stream.cuda_stream)
 
 
 if __name__ == "__main__":

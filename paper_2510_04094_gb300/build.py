@@ -1,4 +1,6 @@
-"""Build the C-ABI shared library libnys.so (sm_103a) in-tree.
+"""Build the C-ABI shared libraries (sm_103a) in-tree: libnys.so, the solver
+(include/nys.h), and libnys_peak.so, the arithmetic-peak probes that the
+benchmark divides by (include/nys_peak.h).
 
 Each CUDA translation unit is compiled by its own nvcc process (in parallel),
 then linked with the shared CUDA runtime so that the library shares the
@@ -17,9 +19,11 @@ INC_DIR = os.path.join(ROOT, "include")
 OBJ_DIR = os.path.join(HERE, "_build")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libnys.so")
+PEAK_LIB_PATH = os.path.join(LIB_DIR, "libnys_peak.so")
 SOURCES = ["nys_setup.cu", "nys_assemble.cu", "nys_assemble_tc.cu", "nys_solve.cu", "nys_eval.cu",
            "nys_newton.cu",
            "nys_grad.cu", "nys_noalloc.cu", "nys_api.cu"]
+PEAK_SOURCES = ["nys_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INC_DIR, "-I" + SRC_DIR]
 
@@ -39,19 +43,21 @@ def _stale(obj, deps):
 
 
 def build(force=False, verbose=False):
-    """Compile every .cu in csrc/ for sm_103a and link _lib/libnys.so. Returns the path."""
+    """Compile the .cu sources for sm_103a and link _lib/libnys.so and
+    _lib/libnys_peak.so.  Returns the solver library's path."""
     nvcc = _nvcc()
     os.makedirs(OBJ_DIR, exist_ok=True)
     os.makedirs(LIB_DIR, exist_ok=True)
     headers = [os.path.join(SRC_DIR, f) for f in os.listdir(SRC_DIR) if f.endswith(".cuh")]
-    headers.append(os.path.join(INC_DIR, "nys.h"))
-    srcs = [s for s in SOURCES if os.path.exists(os.path.join(SRC_DIR, s))]
+    headers += [os.path.join(INC_DIR, f) for f in os.listdir(INC_DIR) if f.endswith(".h")]
+    libs = [(LIB_PATH, SOURCES), (PEAK_LIB_PATH, PEAK_SOURCES)]
     jobs = []
-    for s in srcs:
-        src = os.path.join(SRC_DIR, s)
-        obj = os.path.join(OBJ_DIR, s + ".o")
-        if force or _stale(obj, [src] + headers):
-            jobs.append([nvcc] + ARCH + FLAGS + ["-c", src, "-o", obj])
+    for _, sources in libs:
+        for s in sources:
+            src = os.path.join(SRC_DIR, s)
+            obj = os.path.join(OBJ_DIR, s + ".o")
+            if force or _stale(obj, [src] + headers):
+                jobs.append([nvcc] + ARCH + FLAGS + ["-c", src, "-o", obj])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -60,15 +66,18 @@ def build(force=False, verbose=False):
         if verbose and r.stderr.strip():
             sys.stderr.write(r.stderr)
 
-    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
-        list(ex.map(run, jobs))
-    objs = [os.path.join(OBJ_DIR, s + ".o") for s in srcs]
-    if force or jobs or not os.path.exists(LIB_PATH):
-        cudalib = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "lib64")
-        tmp = LIB_PATH + ".tmp"
-        run([nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs
-            + ["-Xlinker", "-rpath=" + cudalib])
-        os.replace(tmp, LIB_PATH)
+    if jobs:
+        with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
+            list(ex.map(run, jobs))
+    cudalib = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "lib64")
+    for path, sources in libs:
+        objs = [os.path.join(OBJ_DIR, s + ".o") for s in sources]
+        if force or not os.path.exists(path) or any(os.path.getmtime(o) > os.path.getmtime(path)
+                                                    for o in objs):
+            tmp = path + ".tmp"
+            run([nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs
+                + ["-Xlinker", "-rpath=" + cudalib])
+            os.replace(tmp, path)
     return LIB_PATH
 
 

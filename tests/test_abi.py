@@ -169,3 +169,32 @@ def test_readme_c_example_compiles_and_links(abi, tmp_path):
            "-L", libdir, "-lnys", "-L", cudalib, "-lcudart", "-Wl,-rpath," + libdir]
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_peak_probe_library_exports_its_header(abi, tmp_path):
+    """include/nys_peak.h (the arithmetic-peak probes of the benchmark's roofline)
+    compiles as C99 and libnys_peak.so exports what it declares; bad arguments are
+    refused on the host."""
+    import shutil
+    import subprocess
+    src = open(os.path.join(ROOT, "include", "nys_peak.h")).read()
+    names = sorted(set(re.findall(r"\b(nys_[a-z_0-9]+)\s*\(", re.sub(r"/\*.*?\*/", "", src, flags=re.S))))
+    assert names == ["nys_peak_launch"]
+    lib = C.CDLL(abi._build.PEAK_LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n)
+    lib.nys_peak_launch.argtypes = [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]
+    fl = C.c_double(-1.0)
+    assert lib.nys_peak_launch(7, 10, None, None, C.byref(fl)) == -1
+    assert lib.nys_peak_launch(0, 0, None, None, C.byref(fl)) == -1
+    assert fl.value == -1.0
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    c = tmp_path / "peak.c"
+    c.write_text('#include "nys_peak.h"\n'
+                 'int main(void) {\n'
+                 '  int32_t (*f)(int32_t, int32_t, void*, int32_t*, double*) = nys_peak_launch;\n'
+                 '  return f ? 0 : 1;\n}\n')
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-c", "-I", os.path.join(ROOT, "include"),
+                    str(c), "-o", str(tmp_path / "peak.o")], check=True, capture_output=True)
