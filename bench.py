@@ -185,36 +185,63 @@ def banded_flops(problems):
     return tot
 
 
-def tc_issued_flops(problems, rpi):
-    """TF32 MMA FLOPs k_assemble_tc issues for the batch: per work item of `rows`
-    rows whose landmark window holds A landmarks (M2 = A + 2 columns), P = 4, 2, 1
-    blocks of 128 / P slots share each 128-row operand tile (M2 <= 32, <= 64, else),
-    a stage covers 32 P rows in 4 K steps of 8, and each K step issues
-    kTcMmaPerStep MMAs of 128 x N x 8 (N = 128 when P > 1, else M2 rounded up to 16)."""
+TC_BAND_U = 24.0      # the tensor-core Gram's sub-chunk windows keep u <= 24
+TC_SUB_ROWS = 256
+TC_MMA_STEPS = 8      # MMA steps per tensor-memory accumulator entry, at most
+
+
+def slot_block(M2):
+    return 16 if M2 <= 16 else (32 if M2 <= 32 else 64)
+
+
+def tc_issued_flops(problems, num_sms=152):
+    """TF32 MMA FLOPs k_assemble_tc issues for the batch.  Work units of
+    max(256, rows / max(B, 4 SMs)) rows per instance are cut into sub-chunks of
+    up to 256 rows; a sub-chunk whose landmark window (rows within u <= 24) has
+    M2 = A + 2 columns uses slot blocks of Bs = 16, 32, 64 (M2 <= Bs) and 4 MMAs
+    of 128 x 128 x 8 per stage of 2048 / Bs rows, or, for M2 > 64, 6 MMAs of
+    128 x N x 8 (N = M2 rounded up to 16) per stage of 16 rows; sub-chunks are
+    cut to 8 * 512 / Bs rows (32 when M2 > 64)."""
+    import numpy as np
+    total = sum(rows_of(q) for q in problems)
+    target = max(len(problems), 4 * num_sms)
+    upr = max(TC_SUB_ROWS, -(-total // target))
     cache, tot = {}, 0.0
     for q in problems:
-        key = (q["n"], q["m"], q["t0"], q["t1"], q["sigma"])
+        key = (q["n"], q["m"], q["t0"], q["t1"], q["sigma"], q.get("bc"))
         if key not in cache:
-            import numpy as np
-            idx, K = _band(q)
+            idx, _ = _band(q)
+            n, m = q["n"], q["m"]
+            hs = (q["t1"] - q["t0"]) / (n - 1) / q["sigma"]
+            Kb = int(min(math.ceil(math.sqrt(TC_BAND_U) / hs), n))
             nrows = rows_of(q)
-            chunks = max(1, -(-nrows // rpi))
+            units = max(1, -(-nrows // upr))
+
+            def window(a, b):
+                return int(np.searchsorted(idx, b - 1 + Kb, side="right")
+                           - np.searchsorted(idx, a - Kb, side="left"))
             f = 0.0
-            for k in range(chunks):
-                r0 = 1 + nrows * k // chunks
-                r1 = 1 + nrows * (k + 1) // chunks
-                A = int(np.searchsorted(idx, r1 - 1 + K, side="right") - np.searchsorted(idx, r0 - K, side="left"))
-                M2 = A + 2
-                P = 4 if M2 <= 32 else (2 if M2 <= 64 else 1)
-                N = 128 if P > 1 else -(-M2 // 16) * 16
-                nst = -(-(r1 - r0) // (32 * P))
-                f += nst * 4 * TC_MMA_PER_KSTEP * 2.0 * 128 * N * 8
+            for u in range(units):
+                r0 = 1 + nrows * u // units
+                r1 = 1 + nrows * (u + 1) // units
+                s0 = r0
+                while s0 < r1:
+                    L = min(TC_SUB_ROWS, r1 - s0)
+                    M2 = window(s0, s0 + L) + 2
+                    cap = TC_MMA_STEPS * 512 // slot_block(M2) if M2 <= 64 else 32
+                    if L > cap:        # at most TC_MMA_STEPS MMAs per accumulator entry
+                        L = cap
+                        M2 = window(s0, s0 + L) + 2
+                    if M2 <= 64:
+                        Bs = slot_block(M2)
+                        f += -(-L // (2048 // Bs)) * 4 * 2.0 * 128 * 128 * 8
+                    else:
+                        N = -(-M2 // 16) * 16
+                        f += -(-L // 16) * 6 * 2.0 * 128 * N * 8
+                    s0 += L
             cache[key] = f
         tot += cache[key]
     return tot
-
-
-TC_MMA_PER_KSTEP = 3   # hi hi^T, hi lo^T, lo hi^T
 
 
 # ---- CPU oracle baseline ---------------------------------------------------------------
@@ -612,7 +639,7 @@ def main():
                 "traffic": (TC_DRAM_BYTES_PER_INSTANCE * B if mixed and TC_DRAM_BYTES_PER_INSTANCE
                             and args.n == 10_000 and args.m == 50 else None)}
         if mixed:
-            iss = tc_issued_flops(probs, 1024)
+            iss = tc_issued_flops(probs)
             roof["issued_tflops"] = iss / (asm_ms * 1e-3) / 1e12
             roof["pipe_frac"] = roof["issued_tflops"] / peak
             roof["banded_useful_tflops"] = banded_flops(probs) / (asm_ms * 1e-3) / 1e12

@@ -125,10 +125,10 @@ typedef struct {
                             on the CUDA cores (FP32 FMA, 8x8 register blocks)  */
 } nys_options;
 
-/* NYS_ASM_TUNE (MIXED): before the first assembly, time the tensor-core and the
-   CUDA-core Gram with work items of 512 and 1024 rows on the context's own
-   batch (CUDA events, a few launches each) and keep the fastest; see
-   nys_assembly_config.  Other precisions ignore it.                          */
+/* NYS_ASM_TUNE (MIXED): before the first assembly, time the tensor-core Gram
+   (on its long work units) and the CUDA-core Gram (work items of 512 and 1024
+   rows) on the context's own batch (CUDA events, a few launches each) and keep
+   the fastest; see nys_assembly_config.  Other precisions ignore it.        */
 typedef enum { NYS_ASM_AUTO = 0, NYS_ASM_SIMT = 1, NYS_ASM_TUNE = 2 } nys_assembly;
 
 typedef struct nys_ctx nys_ctx;
@@ -183,6 +183,16 @@ int32_t nys_run(nys_ctx* c, void* stream, double* x_out, int32_t* status_out);
    if it has not run yet (synchronises `stream`).                              */
 int32_t nys_assembly_config(nys_ctx* c, void* stream, int32_t* kernel_out, int32_t* rows_out);
 
+/* Bounded device waits of the tensor-core assembly (NYS_MIXED with
+   NYS_ASM_AUTO): each mbarrier wait gives up after `polls` polls of at most
+   1 us (default 4,194,304, about 4 s; a negative value restores it).  A wait
+   that gives up makes every instance of the next solve report NYS_ETIMEOUT and
+   leaves the GPU context usable.  0 makes every wait give up at once, which
+   exercises that path without a fault (tests of the failure handling).
+   Synchronises the device and drops the context's captured nys_run graphs,
+   which hold the previous limit.  Errors: NYS_EINVAL (NULL context).        */
+int32_t nys_set_wait_limit(nys_ctx* c, int32_t polls);
+
 /* Stride (doubles) of one instance in x_out: m_max + 3.                     */
 int32_t nys_x_stride(const nys_ctx* c);
 
@@ -203,15 +213,26 @@ int32_t nys_eval(nys_ctx* c, void* stream, const double* tq, const int64_t* tq_o
 /* Newton's method (Eq. 3.2.1) on Lemma 2's KKT system for NYS_COEF_POLY_NL
    instances (FP64).  The diagonal y-block of the Jacobian is eliminated per
    row exactly, so each step costs one fused row pass and an (m+1+p) solve.
-   Start: omega = 0, b = v_1, lambda = 0, y_i = v_1.  Stop when
-   |dx|_2 <= tol (1 + |x|_2) for x = (omega, b) and |F|_2 <= tol max(1, |F0|_2).
+   Start: omega = 0, b = v_1, lambda = 0, y_i = v_1; or the caller's warm
+   start (device, nullable): batch x nys_x_stride doubles in x_out's layout
+   (omega in this context's feature basis, b, lambda_1, lambda_2), followed by
+   sum_b (n_b - 1) doubles in y_aux_out's layout (the auxiliary unknowns y_i,
+   which at a solution differ from the fit y^(t_i)) -- e.g. the outputs of an
+   earlier call on a nearby problem, copied one after the other.
+   Stop when |dx|_2 <= tol (1 + |x|_2) for x = (omega, b) and
+   |F|_2 <= tol max(1, |F0|_2), F0 = F at the default start (also for a warm
+   start, so both stop by the same rule); at most max_iter steps (0..1000).
    x_out as in nys_solve; y_aux_out (device, optional): sum_b (n_b - 1)
    doubles, instance after instance; iters_out, status_out: device int32[batch]
-   (status NYS_OK or NYS_ENOCONV with the last iterate).  Host-synchronising:
-   reads one convergence flag per iteration.                                  */
+   (status NYS_OK or NYS_ENOCONV with the last iterate, NYS_ENOTSPD).
+   The whole iteration runs without host synchronisation: every round is
+   enqueued (converged instances drop out of the row passes; once none runs,
+   the remaining rounds return at once) and captured as one CUDA graph on the
+   first call with these (max_iter, tol, warm, output) arguments, replayed by
+   later calls.                                                                */
 int32_t nys_newton(nys_ctx* c, void* stream, int32_t max_iter, double tol,
-                   double* x_out, double* y_aux_out, int32_t* iters_out,
-                   int32_t* status_out);
+                   const double* warm, double* x_out, double* y_aux_out,
+                   int32_t* iters_out, int32_t* status_out);
 
 /* Adjoint gradient (parameter estimation; the paper cites the use and prints no
    formula) of a loss on the fitted model of the last nys_solve, for NYS_COEF_LIN

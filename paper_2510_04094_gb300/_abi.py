@@ -63,8 +63,10 @@ def lib():
         L.nys_upload_bytes.restype = C.c_int64
         L.nys_m_eff.argtypes = [vp, vp, C.POINTER(i32)]
         L.nys_eval.argtypes = [vp, vp, vp, vp, i32, vp]
-        L.nys_newton.argtypes = [vp, vp, i32, dbl, vp, vp, vp, vp]
+        L.nys_newton.argtypes = [vp, vp, i32, dbl, vp, vp, vp, vp, vp]
         L.nys_grad.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.nys_set_wait_limit.argtypes = [vp, i32]
+        L.nys_set_wait_limit.restype = i32
         L.nys_solve_noalloc.argtypes = [C.POINTER(nys_instance), i32, vp, vp, vp]
         L.nys_solve_noalloc.restype = i32
         L.nys_destroy.argtypes = [vp]
@@ -132,12 +134,16 @@ def nys_eval(ctx, stream, tq, tq_off, deriv, yq_out):
     check(lib().nys_eval(ctx, stream, tq, tq_off, deriv, yq_out))
 
 
-def nys_newton(ctx, stream, max_iter, tol, x_out, y_aux_out, iters_out, status_out):
-    check(lib().nys_newton(ctx, stream, max_iter, tol, x_out, y_aux_out, iters_out, status_out))
+def nys_newton(ctx, stream, max_iter, tol, warm, x_out, y_aux_out, iters_out, status_out):
+    check(lib().nys_newton(ctx, stream, max_iter, tol, warm, x_out, y_aux_out, iters_out, status_out))
 
 
 def nys_grad(ctx, stream, obs_t, obs_off, dl_dy, grad_out):
     check(lib().nys_grad(ctx, stream, obs_t, obs_off, dl_dy, grad_out))
+
+
+def nys_set_wait_limit(ctx, polls):
+    check(lib().nys_set_wait_limit(ctx, polls))
 
 
 def nys_solve_noalloc(inst_array, batch, x_out, status_out, stream):
@@ -151,5 +157,6 @@ def nys_destroy(ctx):
 EXPORTS = ("nys_setup", "nys_update", "nys_assemble", "nys_solve", "nys_run", "nys_x_stride",
            "nys_upload_bytes", "nys_assembly_config",
            "nys_m_eff", "nys_eval", "nys_newton", "nys_grad", "nys_solve_noalloc", "nys_destroy",
+           "nys_set_wait_limit",
            "nys_status_str",
            "nys_last_error")

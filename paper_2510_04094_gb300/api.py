@@ -149,15 +149,32 @@ class Batch:
             raise ValueError("tq_off must have batch + 1 entries")
         return tq, tq_off
 
-    def newton(self, max_iter=50, tol=1e-10, want_y=False):
+    def newton(self, max_iter=50, tol=1e-10, want_y=False, warm=None):
+        """Newton's method (nys_newton).  warm: optional start (x, y_aux): x in
+        x's layout (batch x XS), y_aux the auxiliary unknowns (sum(n - 1)), e.g.
+        copies of an earlier call's outputs."""
         dev = self.x.device
-        iters = torch.zeros(self.B, dtype=torch.int32, device=dev)
-        yaux = None
-        if want_y:
-            yaux = torch.empty(sum(q["n"] - 1 for q in self.problems), dtype=torch.float64, device=dev)
-        A.nys_newton(self.ctx, _stream_handle(self.stream), int(max_iter), float(tol), _ptr(self.x),
-                     _ptr(yaux), _ptr(iters), _ptr(self.status))
-        return self.x, self.status, iters, yaux
+        if not hasattr(self, "_nt_iters"):
+            # output buffers kept per Batch: nys_newton replays its captured graph
+            # for the same pointers
+            self._nt_iters = torch.zeros(self.B, dtype=torch.int32, device=dev)
+            self._nt_y = torch.empty(sum(q["n"] - 1 for q in self.problems), dtype=torch.float64,
+                                     device=dev)
+        if warm is not None:
+            wx = torch.as_tensor(warm[0], dtype=torch.float64, device=dev).reshape(-1)
+            wy = torch.as_tensor(warm[1], dtype=torch.float64, device=dev).reshape(-1)
+            ny = self._nt_y.numel()
+            if wx.numel() != self.B * self.XS or wy.numel() != ny:
+                raise ValueError("warm must be (x: batch x XS, y_aux: sum(n - 1))")
+            if not hasattr(self, "_nt_warm"):
+                self._nt_warm = torch.empty(self.B * self.XS + ny, dtype=torch.float64, device=dev)
+            self._nt_warm[:self.B * self.XS].copy_(wx)
+            self._nt_warm[self.B * self.XS:].copy_(wy)
+            warm = self._nt_warm
+        yaux = self._nt_y if want_y else None
+        A.nys_newton(self.ctx, _stream_handle(self.stream), int(max_iter), float(tol), _ptr(warm),
+                     _ptr(self.x), _ptr(yaux), _ptr(self._nt_iters), _ptr(self.status))
+        return self.x, self.status, self._nt_iters, yaux
 
     def grad(self, obs_t, obs_off, dl_dy):
         """d loss / d theta (batch x 7, order THETA) of the last solve, given the

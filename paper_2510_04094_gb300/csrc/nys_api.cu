@@ -27,7 +27,7 @@ cudaError_t launch_assemble(bool fp32, const Inst* insts, const Lset* lsets, con
                             const int32_t* lm, const double* tab, double* part,
                             const int64_t* slot_off, int m_max, int k_max, int num_sms,
                             cudaStream_t st, int asm_kind, int32_t* err,
-                            BigSet big = BigSet());
+                            BigSet big = BigSet(), int tc_wait = -1);
 cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const double* W,
                          const float* W32, const double* part, const int64_t* slot_off,
                          const int32_t* lm, void* fac, int64_t facs, double* xs, double* zs,
@@ -46,6 +46,7 @@ cudaError_t launch_eval(const Inst* insts, const double* zs, int ZS, const int32
                         cudaStream_t s);
 
 int64_t fac_elems(int m_max);
+int64_t asm_tc_unit_rows(int64_t total_rows, int batch, int num_sms);
 size_t setup_ws_doubles();
 size_t solve_ws_doubles();
 size_t grad_adj_stride(int ZS);
@@ -55,21 +56,24 @@ cudaError_t launch_grad(const Inst* insts, const Lset* lsets, const double* W, c
                         const double* dl_dy, double* adj, const Work* rwork, int nrwork,
                         int* counter, double* part, const int64_t* slot_off, double* grad_out,
                         double gamma_scale, int batch, int num_sms, cudaStream_t s);
-cudaError_t launch_newton_init(const Inst* insts, double* xs, double* zs, double* dzs, double* yaux,
-                               double* nrm, int32_t* iters, int32_t* active, int32_t* st,
-                               const int32_t* st_init, int XS, int ZS, int batch, cudaStream_t s);
+cudaError_t launch_newton_init(const Inst* insts, const Lset* lsets, const double* W,
+                               const int32_t* lm, const double* warm, double* xs, double* zs,
+                               double* dzs, double* yaux, double* nrm, int32_t* iters,
+                               int32_t* active, int32_t* st, const int32_t* st_init, int XS, int ZS,
+                               int batch, int32_t* live, cudaStream_t s);
 cudaError_t launch_newton_pass(const Inst* insts, const Lset* lsets, const double* W,
                                const Work* work, int nwork, int* counter, const int32_t* lm,
                                const double* xs, int XS, const double* zs, const double* dzs, int ZS,
                                double* yaux, double* rowstate, double* part,
                                const int64_t* slot_off, const int32_t* active, int mode,
-                               int apply_dy, int m_max, int tiles, int num_sms, cudaStream_t s);
+                               int apply_dy, int m_max, int tiles, int num_sms, cudaStream_t s,
+                               const int32_t* live);
 cudaError_t launch_newton_step(const Inst* insts, const Lset* lsets, const double* W,
                                const double* part, const int64_t* slot_off, const int32_t* lm,
                                double* xs, double* zs, double* dzs, double* cws, int XS, int ZS,
                                int M1S, int32_t* st, int32_t* active, int32_t* iters, double* nrm,
                                int max_iter, double tol, int32_t* flags, int mode, int batch,
-                               int m_max, cudaStream_t s);
+                               int m_max, cudaStream_t s, int32_t* live);
 }  // namespace nys
 
 using namespace nys;
@@ -123,6 +127,16 @@ struct GraphKey {
   cudaGraphExec_t exec;
 };
 
+// a captured nys_newton: its arguments and the graph
+struct NewtonGraph {
+  int32_t max_iter;
+  double tol;
+  const double* warm;
+  double *x, *y;
+  int32_t *it, *st;
+  cudaGraphExec_t exec;
+};
+
 struct nys_ctx {
   int batch = 0, m_max = 0, p_max = 0, num_sms = 0, nwork = 0, nrwork = 0, nlset = 0;
   int XS = 0, ZS = 0, M1S = 0;
@@ -142,7 +156,10 @@ struct nys_ctx {
   std::vector<int64_t> h_lagcap;           // lag-table offset of slot b (floats)
   int64_t total_rows = 0;
   int64_t lag_floats = 0;
-  int64_t rpi = 0;                // rows per assembly work item
+  int64_t rpi = 0;                // rows per work item of the CUDA-core / FP64 row passes
+  int64_t tc_rpi = 0;             // rows per work unit of the tensor-core assembly
+  int64_t asm_rows = 0;           // rows per item of the assembly work list in use
+  int tc_wait = -1;               // polls per bounded wait of the tensor-core kernel (-1: default)
   int asm_slots = 0;              // assembly slot region (capacity) in slot_off / part
   bool tune_pending = false;      // NYS_ASM_TUNE: choose kernel and item size at first use
   std::vector<int> eig_bounds;    // landmark-count classes of the setup launches
@@ -178,7 +195,7 @@ struct nys_ctx {
   // Newton state
   DBuf<double> yaux, rowstate, nrm;
   DBuf<int64_t> row_off;
-  DBuf<int32_t> active, iters, any_active;
+  DBuf<int32_t> active, iters, any_active, live;
   // gradient scratch
   DBuf<double> adj;
   // pinned staging for descriptor uploads
@@ -188,6 +205,7 @@ struct nys_ctx {
   int32_t* pin_flag = nullptr;
   cudaEvent_t staged = nullptr;
   std::vector<GraphKey> graphs;
+  std::vector<NewtonGraph> ngraphs;
   bool factor_stale = true;
   bool join_pending = false;     // factor running on the side stream
   int64_t upload_bytes = 0;
@@ -502,11 +520,12 @@ void nys_destroy(nys_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  for (auto& g : c->ngraphs) cudaGraphExecDestroy(g.exec);
   c->inst.release(); c->lset.release(); c->lm.release(); c->tab.release(); c->work.release(); c->rwork.release();
   c->slot_off.release(); c->part.release(); c->W.release(); c->W32.release(); c->lam.release();
   c->fac.release(); c->lag.release(); c->xs.release(); c->zs.release(); c->dzs.release(); c->cws.release();
   c->st.release(); c->stinit.release(); c->counter.release(); c->yaux.release(); c->rowstate.release();
-  c->nrm.release(); c->row_off.release(); c->active.release(); c->iters.release();
+  c->nrm.release(); c->row_off.release(); c->active.release(); c->iters.release(); c->live.release();
   c->any_active.release(); c->adj.release();
   if (c->pin_inst) cudaFreeHost(c->pin_inst);
   if (c->pin_lset) cudaFreeHost(c->pin_lset);
@@ -667,17 +686,24 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   // FP32 row pass: chunks of at most 1024 rows, whose landmark windows are narrow
   if (c->fp32) rpi = std::min<int64_t>(rpi, 1024);
   c->rpi = rpi;
+  // tensor-core assembly: long work units (each cut into narrow sub-chunks in the kernel)
+  c->tc_rpi = asm_tc_unit_rows(total_rows, batch, c->num_sms);
   c->tune_pending = c->fp32 && c->opt.assembly == NYS_ASM_TUNE;
   if (c->opt.assembly == NYS_ASM_TUNE && !c->fp32) c->opt.assembly = NYS_ASM_AUTO;
-  // the assembly slot region holds the finest layout the tuner may pick
+  const bool tc0 = c->fp32 && c->opt.assembly == NYS_ASM_AUTO;
+  // the assembly slot region holds the finest layout the tuner may pick (the
+  // CUDA-core kernel's 512-row items; the tensor-core units are never finer)
   std::vector<Work> wl;
   std::vector<int64_t> soff;
-  const int64_t asm_elems = asm_layout(c, c->tune_pending ? std::min<int64_t>(rpi, 512) : rpi, wl, soff);
+  const int64_t first_rows = c->tune_pending ? std::min<int64_t>(rpi, 512) : (tc0 ? c->tc_rpi : rpi);
+  const int64_t asm_elems = asm_layout(c, first_rows, wl, soff);
   const size_t asm_work_cap = wl.size();
   c->asm_slots = (int)soff.size();
+  c->asm_rows = first_rows;
   if (c->tune_pending) {
-    asm_layout(c, rpi, wl, soff);
+    asm_layout(c, c->tc_rpi, wl, soff);
     soff.resize((size_t)c->asm_slots, 0);
+    c->asm_rows = c->tc_rpi;
   }
   int64_t poff = asm_elems;
   int slot = c->asm_slots;
@@ -773,6 +799,7 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
     A(c->active.alloc(batch));
     A(c->iters.alloc(batch));
     A(c->any_active.alloc(2));
+    A(c->live.alloc(1));
   }
   A(cudaMallocHost(reinterpret_cast<void**>(&c->pin_inst), sizeof(Inst) * batch));
   A(cudaMallocHost(reinterpret_cast<void**>(&c->pin_lset), sizeof(Lset) * batch));
@@ -827,12 +854,14 @@ static int32_t set_asm_layout(nys_ctx* c, int64_t rpi, cudaStream_t s) {
   CK(cudaMemcpy(c->slot_off.p, soff.data(), sizeof(int64_t) * soff.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c->inst.p, c->h_inst.data(), sizeof(Inst) * c->batch, cudaMemcpyHostToDevice));
   c->nwork = (int)wl.size();
-  c->rpi = rpi;
+  c->asm_rows = rpi;
   return NYS_OK;
 }
 
-// Time every (kernel, rows per item) candidate on this batch: one warm-up and
-// three timed launches each; keep the fastest.  Runs once, outside any graph.
+// Time every (kernel, rows per item) candidate on this batch -- the tensor-core
+// kernel on its long work units, the CUDA-core kernel with 512- and 1024-row
+// items -- one warm-up and three timed launches each; keep the fastest.  Runs
+// once, outside any graph.
 static int32_t tune_assembly(nys_ctx* c, cudaStream_t s) {
   c->tune_pending = false;
   if (c->factor_stale) {
@@ -843,39 +872,36 @@ static int32_t tune_assembly(nys_ctx* c, cudaStream_t s) {
     CK(cudaStreamWaitEvent(s, c->ev_join, 0));
     c->join_pending = false;
   }
-  const int64_t rpi0 = c->rpi;
-  const int64_t rows[2] = {std::min<int64_t>(rpi0, 512), rpi0};
-  const int kinds[2] = {NYS_ASM_AUTO, NYS_ASM_SIMT};
+  struct Cand { int kind; int64_t rows; };
+  const Cand cand[3] = {{NYS_ASM_AUTO, c->tc_rpi}, {NYS_ASM_SIMT, std::min<int64_t>(c->rpi, 512)},
+                        {NYS_ASM_SIMT, c->rpi}};
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_kind = NYS_ASM_AUTO;
-  int64_t best_rows = rpi0;
-  for (int kr = 0; kr < 2; ++kr) {
-    if (kr == 0 && rows[0] == rows[1]) continue;
-    int32_t r = set_asm_layout(c, rows[kr], s);
+  int best_k = 0;
+  for (int k = 0; k < 3; ++k) {
+    if (k == 2 && cand[2].rows == cand[1].rows) continue;
+    int32_t r = set_asm_layout(c, cand[k].rows, s);
     if (r != NYS_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return r; }
-    for (int kk = 0; kk < 2; ++kk) {
-      float tot = 0.f;
-      for (int rep = 0; rep < 4; ++rep) {
-        CK(cudaEventRecord(e0, s));
-        CK(launch_assemble(c->fp32, c->inst.p, c->lset.p, c->lag.p, c->W.p, c->work.p, c->nwork,
-                           c->counter.p, c->lm.p, c->tab.p, c->part.p, c->slot_off.p, c->m_max,
-                           c->k_max, c->num_sms, s, kinds[kk], c->err.p, c->bigset()));
-        CK(cudaEventRecord(e1, s));
-        CK(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, e0, e1));
-        if (rep > 0) tot += ms;
-      }
-      if (tot < best) { best = tot; best_kind = kinds[kk]; best_rows = rows[kr]; }
+    float tot = 0.f;
+    for (int rep = 0; rep < 4; ++rep) {
+      CK(cudaEventRecord(e0, s));
+      CK(launch_assemble(c->fp32, c->inst.p, c->lset.p, c->lag.p, c->W.p, c->work.p, c->nwork,
+                         c->counter.p, c->lm.p, c->tab.p, c->part.p, c->slot_off.p, c->m_max,
+                         c->k_max, c->num_sms, s, cand[k].kind, c->err.p, c->bigset(), c->tc_wait));
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (rep > 0) tot += ms;
     }
+    if (tot < best) { best = tot; best_k = k; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  c->opt.assembly = best_kind;
-  return set_asm_layout(c, best_rows, s);
+  c->opt.assembly = cand[best_k].kind;
+  return set_asm_layout(c, cand[best_k].rows, s);
 }
 
 int32_t nys_assembly_config(nys_ctx* c, void* stream, int32_t* kernel_out, int32_t* rows_out) {
@@ -885,7 +911,7 @@ int32_t nys_assembly_config(nys_ctx* c, void* stream, int32_t* kernel_out, int32
     if (r != NYS_OK) return r;
   }
   if (kernel_out) *kernel_out = c->opt.assembly;
-  if (rows_out) *rows_out = (int32_t)c->rpi;
+  if (rows_out) *rows_out = (int32_t)c->asm_rows;
   return NYS_OK;
 }
 
@@ -904,7 +930,7 @@ int32_t nys_assemble(nys_ctx* c, void* stream) {
   CK(launch_assemble(c->fp32, c->inst.p, c->lset.p, c->lag.p, c->W.p, c->work.p,
                      c->nwork, c->counter.p, c->lm.p, c->tab.p, c->part.p, c->slot_off.p, c->m_max,
                      c->k_max, c->num_sms, (cudaStream_t)stream, c->opt.assembly, c->err.p,
-                     c->bigset()));
+                     c->bigset(), c->tc_wait));
   c->assembled = true;
   return NYS_OK;
 }
@@ -966,7 +992,7 @@ int32_t nys_run(nys_ctx* c, void* stream, double* x_out, int32_t* status_out) {
         e2 = launch_assemble(c->fp32, c->inst.p, c->lset.p, c->lag.p, c->W.p,
                              c->work.p, c->nwork, c->counter.p, c->lm.p, c->tab.p, c->part.p,
                              c->slot_off.p, c->m_max, c->k_max, c->num_sms, cs, c->opt.assembly,
-                             c->err.p, c->bigset());
+                             c->err.p, c->bigset(), c->tc_wait);
       if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(cs, c->ev_join, 0);
       if (e2 != cudaSuccess) r = fail(NYS_ECUDA, "capture: assemble: %s", cudaGetErrorString(e2));
       if (r == NYS_OK) r = solve_impl(c, cs, x_out, status_out);
@@ -987,6 +1013,16 @@ int32_t nys_run(nys_ctx* c, void* stream, double* x_out, int32_t* status_out) {
   CK(cudaGraphLaunch(exec, s));
   c->assembled = c->solved = true;
   c->factor_stale = false;
+  return NYS_OK;
+}
+
+int32_t nys_set_wait_limit(nys_ctx* c, int32_t polls) {
+  if (!c) return fail(NYS_EINVAL, "nys_set_wait_limit: NULL context");
+  c->tc_wait = polls < 0 ? -1 : polls;
+  // captured graphs hold the old limit among their kernel arguments
+  cudaDeviceSynchronize();
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
   return NYS_OK;
 }
 
@@ -1013,12 +1049,64 @@ int32_t nys_eval(nys_ctx* c, void* stream, const double* tq, const int64_t* tq_o
   return NYS_OK;
 }
 
-int32_t nys_newton(nys_ctx* c, void* stream, int32_t max_iter, double tol, double* x_out,
-                   double* y_aux_out, int32_t* iters_out, int32_t* status_out) {
+// The Newton iteration enqueued as a fixed sequence: for each of max_iter + 1
+// rounds a full-Newton row pass and step, then a Gauss-Newton re-pass and step
+// that only the instances flagged by the first step take.  Instances that stop
+// leave the row passes; once none is running every kernel returns at once
+// (device counter), so no round needs a host decision.
+static int32_t newton_enqueue(nys_ctx* c, cudaStream_t s, int32_t max_iter, double tol,
+                              const double* warm, double* x_out, double* y_aux_out,
+                              int32_t* iters_out, int32_t* status_out) {
+  int32_t* flags = c->any_active.p;   // [stepped, needs re-pass] (informational)
+  CK(launch_newton_init(c->inst.p, c->lset.p, c->W.p, c->lm.p, nullptr, c->xs.p, c->zs.p, c->dzs.p,
+                        c->yaux.p, c->nrm.p, c->iters.p, c->active.p, c->st.p, c->stinit.p, c->XS,
+                        c->ZS, c->batch, c->live.p, s));
+  if (warm) {
+    // the stopping test's scale |F0| is taken at the default start, so that a
+    // warm start stops by the same rule as a cold one; then x, z, y from warm
+    CK(launch_newton_pass(c->inst.p, c->lset.p, c->W.p, c->work.p, c->nwork, c->counter.p, c->lm.p,
+                          c->xs.p, c->XS, c->zs.p, c->dzs.p, c->ZS, c->yaux.p, c->rowstate.p,
+                          c->part.p, c->slot_off.p, c->active.p, 0, 0, c->m_max, c->nt_tiles,
+                          c->num_sms, s, c->live.p));
+    CK(launch_newton_step(c->inst.p, c->lset.p, c->W.p, c->part.p, c->slot_off.p, c->lm.p, c->xs.p,
+                          c->zs.p, c->dzs.p, c->cws.p, c->XS, c->ZS, c->M1S, c->st.p, c->active.p,
+                          c->iters.p, c->nrm.p, max_iter, tol, flags, 2, c->batch, c->m_max, s,
+                          c->live.p));
+    CK(launch_newton_init(c->inst.p, c->lset.p, c->W.p, c->lm.p, warm, c->xs.p, c->zs.p, c->dzs.p,
+                          c->yaux.p, nullptr, c->iters.p, c->active.p, c->st.p, c->stinit.p, c->XS,
+                          c->ZS, c->batch, c->live.p, s));
+  }
+  for (int k = 0; k <= max_iter; ++k) {
+    CK(cudaMemsetAsync(flags, 0, 2 * sizeof(int32_t), s));
+    for (int mode = 0; mode < 2; ++mode) {
+      CK(launch_newton_pass(c->inst.p, c->lset.p, c->W.p, c->work.p, c->nwork, c->counter.p,
+                            c->lm.p, c->xs.p, c->XS, c->zs.p, c->dzs.p, c->ZS, c->yaux.p,
+                            c->rowstate.p, c->part.p, c->slot_off.p, c->active.p, mode,
+                            (mode == 0 && k > 0) ? 1 : 0, c->m_max, c->nt_tiles, c->num_sms, s,
+                            c->live.p));
+      CK(launch_newton_step(c->inst.p, c->lset.p, c->W.p, c->part.p, c->slot_off.p, c->lm.p,
+                            c->xs.p, c->zs.p, c->dzs.p, c->cws.p, c->XS, c->ZS, c->M1S, c->st.p,
+                            c->active.p, c->iters.p, c->nrm.p, max_iter, tol, flags, mode,
+                            c->batch, c->m_max, s, c->live.p));
+    }
+  }
+  if (x_out)
+    CK(cudaMemcpyAsync(x_out, c->xs.p, sizeof(double) * c->batch * c->XS, cudaMemcpyDeviceToDevice, s));
+  if (status_out)
+    CK(cudaMemcpyAsync(status_out, c->st.p, sizeof(int32_t) * c->batch, cudaMemcpyDeviceToDevice, s));
+  if (iters_out)
+    CK(cudaMemcpyAsync(iters_out, c->iters.p, sizeof(int32_t) * c->batch, cudaMemcpyDeviceToDevice, s));
+  if (y_aux_out)
+    CK(cudaMemcpyAsync(y_aux_out, c->yaux.p, sizeof(double) * c->yaux.n, cudaMemcpyDeviceToDevice, s));
+  return NYS_OK;
+}
+
+int32_t nys_newton(nys_ctx* c, void* stream, int32_t max_iter, double tol, const double* warm,
+                   double* x_out, double* y_aux_out, int32_t* iters_out, int32_t* status_out) {
   if (!c) return fail(NYS_EINVAL, "nys_newton: NULL context");
   if (!c->any_nl || c->any_lin)
     return fail(NYS_EINVAL, "nys_newton: every instance must be of kind NYS_COEF_POLY_NL");
-  if (max_iter < 0 || max_iter > 100000) return fail(NYS_EINVAL, "nys_newton: max_iter out of range");
+  if (max_iter < 0 || max_iter > 1000) return fail(NYS_EINVAL, "nys_newton: max_iter must be in [0, 1000]");
   if (!(tol > 0)) return fail(NYS_EINVAL, "nys_newton: tol must be > 0");
   cudaStream_t s = (cudaStream_t)stream;
   if (c->factor_stale) {
@@ -1029,41 +1117,30 @@ int32_t nys_newton(nys_ctx* c, void* stream, int32_t max_iter, double tol, doubl
     CK(cudaStreamWaitEvent(s, c->ev_join, 0));
     c->join_pending = false;
   }
-  CK(launch_newton_init(c->inst.p, c->xs.p, c->zs.p, c->dzs.p, c->yaux.p, c->nrm.p, c->iters.p,
-                        c->active.p, c->st.p, c->stinit.p, c->XS, c->ZS, c->batch, s));
-  int32_t* flags = c->any_active.p;   // [stepped, needs re-pass]
-  for (int k = 0; k <= max_iter; ++k) {
-    CK(cudaMemsetAsync(flags, 0, 2 * sizeof(int32_t), s));
-    CK(launch_newton_pass(c->inst.p, c->lset.p, c->W.p, c->work.p, c->nwork, c->counter.p, c->lm.p,
-                          c->xs.p, c->XS, c->zs.p, c->dzs.p, c->ZS, c->yaux.p, c->rowstate.p, c->part.p, c->slot_off.p, c->active.p,
-                          0, k > 0 ? 1 : 0, c->m_max, c->nt_tiles, c->num_sms, s));
-    CK(launch_newton_step(c->inst.p, c->lset.p, c->W.p, c->part.p, c->slot_off.p, c->lm.p, c->xs.p,
-                          c->zs.p, c->dzs.p, c->cws.p, c->XS, c->ZS, c->M1S, c->st.p, c->active.p,
-                          c->iters.p, c->nrm.p, max_iter, tol, flags, 0, c->batch, c->m_max, s));
-    CK(cudaMemcpyAsync(c->pin_flag, flags, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    if (c->pin_flag[1]) {  // Gauss-Newton re-pass for the flagged instances
-      CK(launch_newton_pass(c->inst.p, c->lset.p, c->W.p, c->work.p, c->nwork, c->counter.p,
-                            c->lm.p, c->xs.p, c->XS, c->zs.p, c->dzs.p, c->ZS, c->yaux.p, c->rowstate.p, c->part.p, c->slot_off.p,
-                            c->active.p, 1, 0, c->m_max, c->nt_tiles, c->num_sms, s));
-      CK(launch_newton_step(c->inst.p, c->lset.p, c->W.p, c->part.p, c->slot_off.p, c->lm.p,
-                            c->xs.p, c->zs.p, c->dzs.p, c->cws.p, c->XS, c->ZS, c->M1S, c->st.p,
-                            c->active.p, c->iters.p, c->nrm.p, max_iter, tol, flags, 1, c->batch,
-                            c->m_max, s));
-      continue;
-    }
-    if (!c->pin_flag[0]) break;
+  cudaGraphExec_t exec = nullptr;
+  for (auto& g : c->ngraphs)
+    if (g.max_iter == max_iter && g.tol == tol && g.warm == warm && g.x == x_out &&
+        g.y == y_aux_out && g.it == iters_out && g.st == status_out)
+      exec = g.exec;
+  if (!exec) {
+    // capture on a private stream so the legacy default stream can be used by callers
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { cudaStreamDestroy(cs); CK(e); }
+    const int32_t r = newton_enqueue(c, cs, max_iter, tol, warm, x_out, y_aux_out, iters_out,
+                                     status_out);
+    e = cudaStreamEndCapture(cs, &graph);
+    cudaStreamDestroy(cs);
+    if (r != NYS_OK) { if (e == cudaSuccess) cudaGraphDestroy(graph); return r; }
+    CK(e);
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(e);
+    c->ngraphs.push_back({max_iter, tol, warm, x_out, y_aux_out, iters_out, status_out, exec});
   }
-  // the final step's y-update: y_i += dy_i with the last step (a pass in mode 0 that
-  // applies it; instances that stopped took no step after their last pass)
-  if (x_out)
-    CK(cudaMemcpyAsync(x_out, c->xs.p, sizeof(double) * c->batch * c->XS, cudaMemcpyDeviceToDevice, s));
-  if (status_out)
-    CK(cudaMemcpyAsync(status_out, c->st.p, sizeof(int32_t) * c->batch, cudaMemcpyDeviceToDevice, s));
-  if (iters_out)
-    CK(cudaMemcpyAsync(iters_out, c->iters.p, sizeof(int32_t) * c->batch, cudaMemcpyDeviceToDevice, s));
-  if (y_aux_out)
-    CK(cudaMemcpyAsync(y_aux_out, c->yaux.p, sizeof(double) * c->yaux.n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaGraphLaunch(exec, s));
   c->solved = true;
   return NYS_OK;
 }

@@ -345,10 +345,10 @@ size_t asm_smem_bytes(bool fp32, int m_max, int k_cap) {
   return sizeof(double) * 2 * (size_t)kAsm64Rows * (M2 + 1);
 }
 
-cudaError_t launch_assemble_tc(const Inst* insts, const Lset* lsets, const Work* work, int nwork,
-                               int* counter, const int32_t* lm, const double* tab, double* part,
-                               const int64_t* slot_off, int32_t* err, int num_sms,
-                               cudaStream_t st);
+cudaError_t launch_assemble_tc(const Inst* insts, const Lset* lsets, const float* lag,
+                               const Work* work, int nwork, int* counter, const int32_t* lm,
+                               const double* tab, double* part, const int64_t* slot_off,
+                               int32_t* err, int num_sms, int wait_iter, cudaStream_t st);
 
 // Sum of the row-chunk partial Grams of each listed instance (Grams of more than
 // kMMax + 2 columns), into its first slot: a thread per packed entry, the slots
@@ -386,7 +386,8 @@ cudaError_t launch_assemble(bool fp32, const Inst* insts, const Lset* lsets, con
                             const double* W, const Work* work, int nwork, int* counter,
                             const int32_t* lm, const double* tab, double* part,
                             const int64_t* slot_off, int m_max, int k_max, int num_sms,
-                            cudaStream_t st, int asm_kind, int32_t* err, BigSet big) {
+                            cudaStream_t st, int asm_kind, int32_t* err, BigSet big,
+                            int tc_wait) {
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   if (err != nullptr) {  // error word read by the solve (NYS_ETIMEOUT)
@@ -394,8 +395,8 @@ cudaError_t launch_assemble(bool fp32, const Inst* insts, const Lset* lsets, con
     if (e != cudaSuccess) return e;
   }
   if (fp32 && asm_kind == NYS_ASM_AUTO && err != nullptr) {  // tensor-core Gram
-    return launch_assemble_tc(insts, lsets, work, nwork, counter, lm, tab, part, slot_off, err,
-                              num_sms, st);
+    return launch_assemble_tc(insts, lsets, lag, work, nwork, counter, lm, tab, part, slot_off, err,
+                              num_sms, tc_wait < 0 ? (1 << 22) : tc_wait, st);
   }
   // k_cap: capacity of the shared-memory kappa table, fixed at launch (an update
   // that lengthens the lag tables makes those instances use computed features)

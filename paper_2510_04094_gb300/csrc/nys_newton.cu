@@ -32,13 +32,15 @@ namespace nys {
 constexpr int kNtThreads = 256;
 constexpr int kNtRows = 32;
 
-// x0: omega = 0, b = v_1, lambda = 0; y_i = v_1.
+// x0: omega = 0, b = v_1, lambda = 0; y_i = v_1.  live counts the running
+// instances (the caller zeroes it first); every later Newton kernel returns at
+// once when it is 0.
 __global__ void k_newton_init(const Inst* __restrict__ insts, double* __restrict__ xs,
                               double* __restrict__ zs, double* __restrict__ dzs,
                               double* __restrict__ yaux, double* __restrict__ nrm,
                               int32_t* __restrict__ iters, int32_t* __restrict__ active,
                               int32_t* __restrict__ st, const int32_t* __restrict__ st_init,
-                              int XS, int ZS) {
+                              int XS, int ZS, int32_t* __restrict__ live) {
   const int b = blockIdx.x;
   const Inst I = insts[b];
   for (int k = threadIdx.x; k < XS; k += blockDim.x) xs[(int64_t)b * XS + k] = (k == XS - 3) ? I.v[0] : 0.0;
@@ -52,7 +54,43 @@ __global__ void k_newton_init(const Inst* __restrict__ insts, double* __restrict
     iters[b] = 0;
     st[b] = st_init[b];
     active[b] = (st_init[b] == NYS_OK) ? 1 : 0;
+    if (st_init[b] == NYS_OK) atomicAdd(live, 1);
   }
+}
+
+// Warm start from the caller's buffer [x (x_out's layout) | y (y_aux_out's
+// layout)]: x = (omega, b, lambda), its kernel coordinates z = (W^T omega, b),
+// and the auxiliary unknowns y_i of Lemma 2 (at a solution they differ from the
+// fit y^(t_i) by xi_i, which need not be small: e_i and xi_i carry the same
+// weight gamma).
+__global__ void k_newton_warm(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
+                              const double* __restrict__ W_all, const double* __restrict__ warm,
+                              double* __restrict__ xs, double* __restrict__ zs,
+                              double* __restrict__ yaux, const int32_t* __restrict__ st_init,
+                              int XS, int ZS, int batch) {
+  const int b = blockIdx.x;
+  if (st_init[b] != NYS_OK) return;
+  const Inst I = insts[b];
+  const Lset L = lsets[I.lset];
+  const int m = I.m, me = L.m_eff;
+  const double* W = W_all + L.w_off;
+  __shared__ double s_x[kMMax + 3];
+  for (int k = threadIdx.x; k < XS; k += blockDim.x) {
+    const double v = warm[(int64_t)b * XS + k];
+    s_x[k] = (k < me || k >= XS - 3) ? v : 0.0;   // omega beyond m_eff is zero
+    xs[(int64_t)b * XS + k] = s_x[k];
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j <= m; j += blockDim.x) {
+    double z = s_x[XS - 3];
+    if (j < m) {
+      z = 0.0;
+      for (int k = 0; k < me; ++k) z += W[k * m + j] * s_x[k];
+    }
+    zs[(int64_t)b * ZS + j] = z;
+  }
+  const double* wy = warm + (int64_t)batch * XS + I.y_off;
+  for (int r = threadIdx.x; r < I.n - 1; r += blockDim.x) yaux[I.y_off + r] = wy[r];
 }
 
 // Partial-slot layout of one work item (doubles):
@@ -74,7 +112,9 @@ k_newton_pass(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
               const double* __restrict__ zs, const double* __restrict__ dzs, int ZS,
               double* __restrict__ yaux, double* __restrict__ rowstate,
               double* __restrict__ part, const int64_t* __restrict__ slot_off,
-              const int32_t* __restrict__ active, int mode, int apply_dy, int tiles) {
+              const int32_t* __restrict__ active, int mode, int apply_dy, int tiles,
+              const int32_t* __restrict__ live) {
+  if (*live == 0) return;   // every instance has stopped (the same value for all threads)
   extern __shared__ double smn[];
   __shared__ int s_item;
   __shared__ int s_idx[kMMax];
@@ -372,7 +412,8 @@ static cudaError_t launch_pass_k(const Inst* insts, const Lset* lsets, const dou
                                  const double* xs, int XS, const double* zs, const double* dzs, int ZS,
                                  double* yaux, double* rowstate, double* part,
                                  const int64_t* slot_off, const int32_t* active, int mode,
-                                 int apply_dy, int m_max, int tiles, int num_sms, cudaStream_t s) {
+                                 int apply_dy, int m_max, int tiles, int num_sms, cudaStream_t s,
+                                 const int32_t* live) {
   const size_t sm = newton_pass_smem(m_max, tiles);
   cudaError_t e = cudaFuncSetAttribute(k_newton_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sm);
@@ -383,7 +424,7 @@ static cudaError_t launch_pass_k(const Inst* insts, const Lset* lsets, const dou
   k_newton_pass<K><<<grid, kNtThreads, sm, s>>>(insts, lsets, W, work, nwork, counter, lm, xs, XS,
                                                   zs, dzs, ZS, yaux,
                                                   rowstate, part, slot_off, active, mode, apply_dy,
-                                                  tiles);
+                                                  tiles, live);
   return cudaGetLastError();
 }
 
@@ -392,13 +433,14 @@ cudaError_t launch_newton_pass(const Inst* insts, const Lset* lsets, const doubl
                                const double* xs, int XS, const double* zs, const double* dzs, int ZS,
                                double* yaux, double* rowstate, double* part,
                                const int64_t* slot_off, const int32_t* active, int mode,
-                               int apply_dy, int m_max, int tiles, int num_sms, cudaStream_t s) {
+                               int apply_dy, int m_max, int tiles, int num_sms, cudaStream_t s,
+                               const int32_t* live) {
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   const int M1 = m_max + 1, E1 = M1 * (M1 + 1) / 2;
   const int kneed = (E1 + kNtThreads - 1) / kNtThreads;
 #define NT_ARGS insts, lsets, W, work, nwork, counter, lm, xs, XS, zs, dzs, ZS, yaux, rowstate, part, slot_off, active, \
-                mode, apply_dy, m_max, tiles, num_sms, s
+                mode, apply_dy, m_max, tiles, num_sms, s, live
   if (kneed <= 4) return launch_pass_k<4>(NT_ARGS);
   if (kneed <= 8) return launch_pass_k<8>(NT_ARGS);
   if (kneed <= 14) return launch_pass_k<14>(NT_ARGS);
@@ -407,11 +449,21 @@ cudaError_t launch_newton_pass(const Inst* insts, const Lset* lsets, const doubl
 #undef NT_ARGS
 }
 
-cudaError_t launch_newton_init(const Inst* insts, double* xs, double* zs, double* dzs, double* yaux,
-                               double* nrm, int32_t* iters, int32_t* active, int32_t* st,
-                               const int32_t* st_init, int XS, int ZS, int batch, cudaStream_t s) {
+// warm == nullptr: the default start (and live counted from 0);
+// warm != nullptr: only x, z, y replaced by the warm start (nrm, iters kept)
+cudaError_t launch_newton_init(const Inst* insts, const Lset* lsets, const double* W,
+                               const int32_t* lm, const double* warm, double* xs, double* zs,
+                               double* dzs, double* yaux, double* nrm, int32_t* iters,
+                               int32_t* active, int32_t* st, const int32_t* st_init, int XS, int ZS,
+                               int batch, int32_t* live, cudaStream_t s) {
+  if (warm != nullptr) {
+    k_newton_warm<<<batch, 256, 0, s>>>(insts, lsets, W, warm, xs, zs, yaux, st_init, XS, ZS, batch);
+    return cudaGetLastError();
+  }
+  cudaError_t e = cudaMemsetAsync(live, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess) return e;
   k_newton_init<<<batch, 256, 0, s>>>(insts, xs, zs, dzs, yaux, nrm, iters, active, st, st_init, XS,
-                                      ZS);
+                                      ZS, live);
   return cudaGetLastError();
 }
 

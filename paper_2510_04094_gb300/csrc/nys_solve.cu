@@ -700,8 +700,10 @@ k_newton_step(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
               double* __restrict__ xs, double* __restrict__ zs, double* __restrict__ dzs,
               double* __restrict__ cws, int XS, int ZS, int M1S, int32_t* __restrict__ st_all,
               int32_t* __restrict__ active, int32_t* __restrict__ iters, double* __restrict__ nrm,
-              int max_iter, double tol, int32_t* __restrict__ flags, int mode) {
+              int max_iter, double tol, int32_t* __restrict__ flags, int mode,
+              int32_t* __restrict__ live) {
   const int b = blockIdx.x;
+  if (*live == 0) return;   // every instance has stopped
   const int act = active[b];
   if (act == 0 || (mode == 1 && act != 2)) return;
   const Inst I = insts[b];
@@ -820,12 +822,19 @@ k_newton_step(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     s_gx[M1] = sqrt(gx2 + s_sc[0] + s_sc[2]);   // |F|
   }
   __syncthreads();
+  if (mode == 2) {   // warm start: |F| at the default start, the stopping test's scale
+    if (threadIdx.x == 0) {
+      nrm[(int64_t)b * 4] = s_gx[M1];
+      nrm[(int64_t)b * 4 + 2] = 1.0;
+    }
+    return;
+  }
   if (mode == 0) {
     const int it = iters[b];
     const double nF = s_gx[M1];
     if (threadIdx.x == 0) {
       int decision = 0;   // 0: step, 1: converged, 2: cap, 3: re-pass
-      if (it == 0) nrm[(int64_t)b * 4] = nF;
+      if (it == 0 && nrm[(int64_t)b * 4 + 2] == 0.0) nrm[(int64_t)b * 4] = nF;
       const double F0 = nrm[(int64_t)b * 4];
       if (it > 0 && nrm[(int64_t)b * 4 + 1] <= tol * (1.0 + sqrt(s_sc[3])) && nF <= tol * fmax(1.0, F0))
         decision = 1;
@@ -833,8 +842,8 @@ k_newton_step(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         decision = 2;
       else if (s_sc[1] > 0.0)
         decision = 3;
-      if (decision == 1) { active[b] = 0; st_all[b] = NYS_OK; }
-      if (decision == 2) { active[b] = 0; st_all[b] = NYS_ENOCONV; }
+      if (decision == 1) { active[b] = 0; st_all[b] = NYS_OK; atomicSub(live, 1); }
+      if (decision == 2) { active[b] = 0; st_all[b] = NYS_ENOCONV; atomicSub(live, 1); }
       if (decision == 3) { active[b] = 2; atomicOr(&flags[1], 1); }
       s_flag = decision;
     }
@@ -933,7 +942,7 @@ k_newton_step(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   if (!ok) {
     if (threadIdx.x == 0) {
       if (mode == 0) { active[b] = 2; atomicOr(&flags[1], 1); }
-      else { active[b] = 0; st_all[b] = NYS_ENOTSPD; }
+      else { active[b] = 0; st_all[b] = NYS_ENOTSPD; atomicSub(live, 1); }
     }
     return;
   }
@@ -987,14 +996,14 @@ cudaError_t launch_newton_step(const Inst* insts, const Lset* lsets, const doubl
                                double* xs, double* zs, double* dzs, double* cws, int XS, int ZS,
                                int M1S, int32_t* st, int32_t* active, int32_t* iters, double* nrm,
                                int max_iter, double tol, int32_t* flags, int mode, int batch,
-                               int m_max, cudaStream_t s) {
+                               int m_max, cudaStream_t s, int32_t* live) {
   const size_t sm = solve_smem_bytes(false, m_max);
   cudaError_t e = cudaFuncSetAttribute(k_newton_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sm);
   if (e != cudaSuccess) return e;
   k_newton_step<<<batch, kSolveThreads, sm, s>>>(insts, lsets, W, part, slot_off, lm, xs, zs, dzs,
                                                   cws, XS, ZS, M1S, st, active, iters, nrm,
-                                                  max_iter, tol, flags, mode);
+                                                  max_iter, tol, flags, mode, live);
   return cudaGetLastError();
 }
 

@@ -21,11 +21,13 @@ def test_method_flop_count_per_row(bench):
 def test_banded_and_issued_counts_are_consistent(bench):
     q = ni.m0(1)[0]
     useful = bench.banded_flops([q])
-    issued = bench.tc_issued_flops([q], 1024)
+    issued = bench.tc_issued_flops([q])
     # every row sees about 22 landmarks of its band; the tensor-core kernel issues
-    # more than the banded count (block packing, hi/lo products) but is finite
+    # more than the banded count (block packing, hi/lo products); on this family
+    # every 256-row sub-chunk fits 16-slot blocks: 32 rows per 128 x 128 x 8 MMA
     assert 9999 * 400 < useful < 9999 * 800
     assert issued > useful
+    assert issued == 40 * 2 * 4 * (2.0 * 128 * 128 * 8)   # 40 sub-chunks x 2 stages x 4 MMAs
     assert bench.dense_flops([q]) > useful
 
 

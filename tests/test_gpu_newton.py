@@ -85,6 +85,95 @@ def test_cfg5_full_size(api):
     _compare(api, probs, max_iter=20)
 
 
+def _chol_basis(q):
+    """This library's feature basis for an FP64 context whose landmark kernel is
+    certified well conditioned (|Omega|_inf |L^-1|_F^2 sqrt(n) <= 9e4): the
+    Cholesky whitening W = L^-1, Omega = L L^T (unique).  None if not certified."""
+    st = core.setup(q)
+    s = st["s"]
+    Om = core.rbf(s[:, None], s[None, :], q["sigma"])
+    L = np.linalg.cholesky(Om)
+    Li = np.linalg.inv(L)
+    if np.abs(Om).sum(axis=1).max() * (Li * Li).sum() * np.sqrt(q["n"]) > 9e4:
+        return None
+    return L
+
+
+def test_warm_start_from_own_solution_takes_one_step(api):
+    """nys_newton started from its own converged (x, y_aux) stops after one step
+    (the stopping test's scale is |F| at the default start, as for a cold start)."""
+    import torch
+    probs = ni.cfg5(B=6, n_lo=800, n_hi=2000)
+    bt = api.Batch(probs, precision="fp64")
+    x, st, it, ya = bt.newton(max_iter=50, want_y=True)
+    grids = [core.grid(q) for q in probs]
+    y0, _ = bt.eval(grids)
+    torch.cuda.synchronize()
+    conv = st.cpu().numpy() == 0
+    assert conv.sum() >= 4
+    x0, ya0, y0 = x.clone(), ya.clone(), y0.cpu().numpy()
+    x1, st1, it1, _ = bt.newton(max_iter=50, warm=(x0, ya0))
+    y1, _ = bt.eval(grids)
+    torch.cuda.synchronize()
+    assert (st1.cpu().numpy()[conv] == 0).all()
+    assert (it1.cpu().numpy()[conv] == 1).all(), it1
+    y1 = y1.cpu().numpy()
+    off = 0
+    for k, g in enumerate(grids):
+        if conv[k]:
+            assert np.abs(y1[off:off + len(g)] - y0[off:off + len(g)]).max() <= 1e-10 * np.abs(y0[off:off + len(g)]).max()
+        off += len(g)
+    bt.close()
+
+
+def test_warm_start_from_the_oracle_takes_one_step(api):
+    """Started from the oracle's converged Newton solution (omega mapped into this
+    context's feature basis: omega = W Omega z = L^T z for the kernel coordinates
+    z = W_o^T omega_o of the oracle's fit; b, lambda and the auxiliary y_i as they
+    are), nys_newton stops after one step with the oracle's fit."""
+    import torch
+    probs = [q for q in ni.cfg5(B=8, n_lo=800, n_hi=2000) if _chol_basis(q) is not None]
+    refs = [newton.solve(q, tol=1e-10, max_iter=50) for q in probs]
+    keep = [k for k, r in enumerate(refs) if r["converged"]]
+    probs, refs = [probs[k] for k in keep], [refs[k] for k in keep]
+    assert len(probs) >= 4
+    bt = api.Batch(probs, precision="fp64")
+    XS = bt.XS
+    warm = np.zeros((len(probs), XS))
+    for k, (q, r) in enumerate(zip(probs, refs)):
+        z = r["W"].T @ r["omega"]
+        warm[k, :q["m"]] = _chol_basis(q).T @ z
+        warm[k, XS - 3] = r["b"]
+        warm[k, XS - 2:XS - 2 + q["p"]] = r["lam"]
+    ya = np.concatenate([r["y_aux"] for r in refs])
+    x, st, it, _ = bt.newton(max_iter=50, warm=(warm, ya))
+    grids = [core.grid(q) for q in probs]
+    y, _ = bt.eval(grids)
+    torch.cuda.synchronize()
+    assert (st.cpu().numpy() == 0).all()
+    assert (it.cpu().numpy() == 1).all(), it
+    y = y.cpu().numpy()
+    off = 0
+    for q, r, g in zip(probs, refs, grids):
+        assert np.abs(y[off:off + len(g)] - r["y"]).max() <= 1e-10 * np.abs(r["y"]).max()
+        off += len(g)
+    bt.close()
+
+
+def test_newton_replays_its_graph(api):
+    """A second nys_newton call with the same arguments replays the captured
+    graph and gives the same result bit for bit."""
+    import torch
+    probs = ni.cfg5(B=4, n_lo=600, n_hi=1200)
+    bt = api.Batch(probs, precision="fp64")
+    a = [t.clone() for t in bt.newton(max_iter=20)[:3]]
+    b = [t.clone() for t in bt.newton(max_iter=20)[:3]]
+    torch.cuda.synchronize()
+    for u, v in zip(a, b):
+        assert torch.equal(u, v)
+    bt.close()
+
+
 def test_linear_rhs_converges_in_one_step(api):
     q = dict(_duffing(200, 12, 1e8), P=[0.3, -1.5, 0.0, 0.0])
     st, iters, y, yaux = _run(api, [q])
