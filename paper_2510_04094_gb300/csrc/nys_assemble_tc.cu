@@ -39,14 +39,19 @@
 // depends on the lag t_i - s_j = (i - idx_j) h only.  For constant
 // coefficients (kind LIN) the producers fold kappa(lag) = A0 b0 + A1 b1 + A2 b2
 // from the landmark set's lag tables (k_setup_lag) once per work unit into a
-// table in shared memory, already split into hi/lo; a feature is then one
-// table read.  Tabulated coefficients (kind TABLE), or a table larger than
-// shared memory allows, evaluate each feature (FP32, MUFU exponential).
+// table in shared memory, already split into hi/lo.  Every lane of a producer
+// unit then reads its value from one shared-memory source per sub-chunk -- the
+// table at its lag, the sub-chunk's split r(t_i), the -f_p cell or a zero cell
+// -- advancing by a fixed stride per stage: one 8-byte load and two stores per
+// operand pair, no branches.  Tabulated coefficients (kind TABLE), or a table
+// larger than shared memory allows, evaluate each feature (FP32, MUFU
+// exponential).
 //
 // Warp roles (persistent CTA per SM, all hand-offs through mbarriers):
-//   * two setup warps take work units from the queue and prepare sub-chunks
-//     into a ring of kTcSub buffers: window, landmark indices, r(t_i) of the
-//     rows (and the row coefficients of kind TABLE);
+//   * four setup warps take work units from the queue and prepare sub-chunks
+//     into a ring of kTcSub buffers: window (advanced along the unit),
+//     landmark indices, the split r(t_i) (and the row coefficients of kind
+//     TABLE);
 //   * kTcProducers producer warps write the operand tiles of a ring of
 //     kTcStages stages: 64 warp-wide units per stage, one value per lane (hi and
 //     lo stores fill 4 K positions x 8 operand rows, conflict-free);
@@ -67,12 +72,12 @@
 
 namespace nys {
 
-constexpr int kTcProducers = 16;                       // producer warps 0..15
+constexpr int kTcProducers = 8;                        // producer warps 0..7
 constexpr int kTcProdThreads = 32 * kTcProducers;
-constexpr int kTcIssuerWarp = kTcProducers;            // warp 16
-constexpr int kTcEpiWarp0 = kTcProducers + 1;          // warps 17..20
-constexpr int kTcSetupWarp0 = kTcProducers + 5;        // warps 21, 22
-constexpr int kTcSetupThreads = 64;
+constexpr int kTcIssuerWarp = kTcProducers;            // warp 8
+constexpr int kTcEpiWarp0 = kTcProducers + 1;          // warps 9..12
+constexpr int kTcSetupWarp0 = kTcProducers + 5;        // warps 13..16
+constexpr int kTcSetupThreads = 128;
 constexpr int kTcThreads = 32 * (kTcProducers + 5) + kTcSetupThreads;
 constexpr int kTcStages = 5;
 constexpr int kTcTileBytes = 16384;      // 128 operand rows x 32 K positions (TF32)
@@ -83,7 +88,7 @@ constexpr int kTcUnitsPerStage = 64;     // warp-wide units of a stage (one valu
 constexpr int kTcUnitsPerWarp = kTcUnitsPerStage / kTcProducers;
 constexpr int kTcSLd = 65;               // epilogue staging stride (Bs <= 64, padded)
 constexpr int kTcSBytes = 128 * kTcSLd * 4;
-constexpr int kTcGuMax = (kMMax + 2) * (kMMax + 3) / 2;   // unit Gram entries (FP64)
+constexpr int kTcGuMax = (kMMax + 2) * (kMMax + 3) / 2;   // unit Gram entries (float2 each)
 constexpr int kTcLmCap = 128;            // landmark indices per sub-chunk buffer
 constexpr int kTcTabCap = 4096;          // kappa(lag) table entries (hi, lo)
 constexpr uint32_t kTcSetCols = 128;
@@ -91,17 +96,20 @@ constexpr uint32_t kTcCols = kTcSub * kTcSetCols;   // the whole tensor memory o
 constexpr double kTcBandU = 24.0;
 constexpr int kTcMmaSteps = 8;           // MMA steps per accumulator entry, at most
 constexpr int kTcDrainIter = 1 << 22;    // final wait for the MMAs in flight
-static_assert(kTcUnitsPerStage % kTcProducers == 0, "units split evenly over producers");
+static_assert(kTcUnitsPerStage % kTcProducers == 0 && kTcProducers == 8,
+              "the unit decoding below assumes 8 producer warps");
 
-// dynamic shared memory layout (offsets from the 1024-aligned base)
-constexpr int kTcOffS = kTcStageArea;
-constexpr int kTcOffTab = kTcOffS + kTcSBytes;                   // float2
-constexpr int kTcOffCo = kTcOffTab + kTcTabCap * 8;              // float4
-constexpr int kTcOffGu = kTcOffCo + kTcSub * kTcSubRows * 16;    // double
-constexpr int kTcOffR = kTcOffGu + kTcGuMax * 8;
-constexpr int kTcOffLm = kTcOffR + kTcSub * kTcSubRows * 4;
-constexpr int kTcSmemUsed = kTcOffLm + kTcSub * kTcLmCap * 4;
-static_assert(kTcOffTab % 8 == 0 && kTcOffCo % 16 == 0 && kTcOffGu % 8 == 0, "alignment");
+// dynamic shared memory layout (byte offsets from the 1024-aligned base)
+constexpr int kTcOffS = kTcStageArea;                            // float  [128][kTcSLd]
+constexpr int kTcOffTab = kTcOffS + kTcSBytes;                   // float2 [kTcTabCap]
+constexpr int kTcOffGu = kTcOffTab + kTcTabCap * 8;              // float2 [kTcGuMax]
+constexpr int kTcOffRs = kTcOffGu + (kTcGuMax * 8 + 15) / 16 * 16;   // float2 [kTcSub][kTcSubRows]
+constexpr int kTcOffCo = kTcOffRs + kTcSub * kTcSubRows * 8;     // float4 [kTcSub][kTcSubRows]
+constexpr int kTcOffLm = kTcOffCo + kTcSub * kTcSubRows * 16;    // int    [kTcSub][kTcLmCap]
+constexpr int kTcOffCell = kTcOffLm + kTcSub * kTcLmCap * 4;     // float2 [kTcSub][2]: -f_p, 0
+constexpr int kTcSmemUsed = kTcOffCell + kTcSub * 16;
+static_assert(kTcOffTab % 8 == 0 && kTcOffGu % 8 == 0 && kTcOffRs % 8 == 0 && kTcOffCo % 16 == 0 &&
+              kTcOffCell % 8 == 0, "alignment");
 static_assert(kTcSmemUsed + 1024 + 2048 <= 227 * 1024, "shared memory of one CTA");
 
 size_t asm_tc_smem_bytes() { return (size_t)kTcSmemUsed + 1024; }
@@ -118,6 +126,7 @@ struct TcSub {
   int mode;        // 0: kappa table (kind LIN); 1: features evaluated, LIN; 2: kind TABLE
   int Kt;          // table: lags -Kt..Kt at entries 0..2Kt
   int Kset;        // lag tables of the landmark set cover lags 0..Kset
+  int unit;        // work unit whose constants (below) the buffer holds
   int64_t slot_off, lag_off;
   float hsc, LA0, LB1, LB2, w1;    // evaluated features: scaled operator constants
   float A0, A1, A2;                // table: operator constants
@@ -131,12 +140,29 @@ __device__ __forceinline__ void bar_named(int id, int count) {
 __device__ __forceinline__ float rn_tf32(float x) {
   return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
+__device__ __forceinline__ float2 split_tf32(float v) {
+  const float h = rn_tf32(v);
+  return make_float2(h, rn_tf32(v - h));
+}
 
-// warp-uniform bounded wait (lane 0 polls)
+// warp-uniform bounded wait: lane 0 polls (acquire), the warp barrier orders the
+// other lanes' later accesses after it
 __device__ __forceinline__ bool warp_wait(uint32_t mbar, uint32_t parity, int iters) {
   int ok = 0;
   if ((threadIdx.x & 31) == 0) ok = mbar_wait_bounded(mbar, parity, iters) ? 1 : 0;
-  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __syncwarp();
+  return ok != 0;
+}
+
+// The producer warps meet (bounded): each warp's accesses so far happen before
+// every producer warp's accesses after it.  ph: this warp's count of meetings.
+__device__ __forceinline__ bool prod_meet(uint64_t* bar, uint32_t& ph, int iters) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive(smem_u32(bar));
+  const bool ok = warp_wait(smem_u32(bar), ph & 1u, iters);
+  ++ph;
+  return ok;
 }
 
 // landmark window of rows [r0, r1): indices j with |i - idx_j| <= K for a row i
@@ -148,6 +174,21 @@ __device__ __forceinline__ void lm_window(const int* idx, int m, int r0, int r1,
   b = m;
   while (a < b) { const int c = (a + b) >> 1; if (idx[c] <= r1 - 1 + K) a = c + 1; else b = c; }
   A = a - jlo;
+}
+
+// g += x in compensated FP32: g.x + g.y carries the running sum, g.y the
+// rounding errors of the additions into g.x (error-free two-sum)
+__device__ __forceinline__ void acc_comp(float2* p, float x) {
+  float2 g = *p;
+  const float s = __fadd_rn(g.x, x);
+  const float z = __fsub_rn(s, g.x);
+  g.y = __fadd_rn(g.y, __fadd_rn(__fsub_rn(g.x, __fsub_rn(s, z)), __fsub_rn(x, z)));
+  g.x = s;
+  *p = g;
+}
+
+__device__ __forceinline__ int slot_block(int M2) {
+  return (M2 <= 16) ? 16 : (M2 <= 32 ? 32 : (M2 <= 64 ? 64 : 128));
 }
 
 // sin and cos of theta_i = th0 + i dth (LIN right-hand side), argument in
@@ -170,102 +211,113 @@ __device__ __forceinline__ void lin_sincos(const RowConst& K, int i, float& s, f
   c = fmaf(-sn, r.lo, cs);
 }
 
-// Producer work of one sub-chunk with slot block BS: per warp, kTcUnitsPerWarp
-// units per stage.  Operand offsets depend on BS only; the feature of a lane is
-// a table read (mode 0) or evaluated (modes 1, 2).
+// Operand offsets of unit k of producer warp `warp`: the row t0 of the stage,
+// the slot j and the byte offsets of the lane's hi and lo words.
 template <int BS>
-__device__ __forceinline__ void produce_sub(const TcSub& M, unsigned char* sm, const float2* tab,
-                                            const float* rr, const float4* co, const int* lmb,
-                                            int& gs, int warp, int lane, int wait_iter,
-                                            uint64_t* s_full, uint64_t* s_empty, bool& late) {
+__device__ __forceinline__ void unit_layout(int warp, int k, int lane, int& t0, int& j,
+                                            uint32_t& oh, uint32_t& ol) {
+  if (BS <= 64) {
+    // u = warp + 8 k: row set r = u / BS, slot j = u % BS (warp-uniform); lane =
+    // K position, so a store fills one whole 128-byte operand row
+    const int u = warp + 8 * k;
+    const int r = u / BS;
+    j = u % BS;
+    t0 = 32 * r + lane;
+    const int rho = 2 * r * BS + j;                    // hi row; lo row rho + BS
+    oh = ((uint32_t)(rho >> 3) << 10) + ((uint32_t)(rho & 7) << 7) +
+         ((uint32_t)(((lane >> 2) ^ rho) & 7) << 4) + ((uint32_t)(lane & 3) << 2);
+    ol = oh + (uint32_t)BS * 128u;                     // same row of its 8-row atom
+  } else {
+    // u = warp + 8 k: slot group g = u >> 2, row quad c = u & 3
+    const int j8 = lane >> 2, w4 = lane & 3;
+    const int u = warp + 8 * k;
+    const int g = u >> 2, c = u & 3;
+    const int qh = 4 * (c >> 1) + (c & 1), ql = qh + 2;
+    t0 = 4 * c + w4;
+    j = 8 * g + j8;
+    oh = ((uint32_t)g << 10) + (j8 << 7) + (((qh ^ j8) & 7) << 4) + (w4 << 2);
+    ol = ((uint32_t)g << 10) + (j8 << 7) + (((ql ^ j8) & 7) << 4) + (w4 << 2);
+  }
+}
+
+// Producer work of one sub-chunk with slot block BS.  Per lane and unit one
+// shared-memory source (kappa table at the lane's lag, split r(t_i), the -f_p
+// cell or the zero cell) and its advance per stage; per stage the eight values
+// are loaded first, then stored (the compiler cannot move loads past stores to
+// the same array).
+template <int BS>
+__device__ __forceinline__ void produce_sub(const TcSub& M, int b, unsigned char* sm, int& gs,
+                                            int warp, int lane, int wait_iter, uint64_t* s_full,
+                                            uint64_t* s_empty, bool& late) {
   constexpr int SR = (BS <= 64) ? 2048 / BS : 16;      // rows per stage
-  constexpr uint32_t kLoOff = (BS <= 64) ? (uint32_t)BS * 128u : 0u;
-  const int j8 = lane >> 2, w4 = lane & 3;
-  const int A = M.A, nrows = M.nrows, mode = M.mode;
-  int u_t0[kTcUnitsPerWarp], u_kind[kTcUnitsPerWarp], u_ti[kTcUnitsPerWarp], u_step[kTcUnitsPerWarp];
-  uint32_t u_oh[kTcUnitsPerWarp], u_ol[kTcUnitsPerWarp];
-  bool u_plain[kTcUnitsPerWarp];
+  const int A = M.A, nrows = M.nrows, nst = M.nst, mode = M.mode;
+  const int* lmb = reinterpret_cast<const int*>(sm + kTcOffLm) + b * kTcLmCap;
+  uint32_t src[kTcUnitsPerWarp], step[kTcUnitsPerWarp], oh[kTcUnitsPerWarp], ol[kTcUnitsPerWarp];
+  int t0s[kTcUnitsPerWarp], js[kTcUnitsPerWarp], dj[kTcUnitsPerWarp];
 #pragma unroll
   for (int k = 0; k < kTcUnitsPerWarp; ++k) {
-    const int u = warp + k * kTcProducers;
-    int t0, j;
-    uint32_t oh, ol;
-    if (BS <= 64) {
-      constexpr int ng = BS >> 3;
-      const int q = u & 7, rg = u >> 3;
-      const int g = rg % ng, r = rg / ng;
-      t0 = 32 * r + 4 * q + w4;
-      j = 8 * g + j8;
-      oh = ((uint32_t)(((2 * r * BS) >> 3) + g) << 10) + (j8 << 7) + (((q ^ j8) & 7) << 4) + (w4 << 2);
-      ol = oh + kLoOff;
-    } else {
-      const int g = u >> 2, c = u & 3;
-      const int qh = 4 * (c >> 1) + (c & 1), ql = qh + 2;
-      t0 = 4 * c + w4;
-      j = 8 * g + j8;
-      oh = ((uint32_t)g << 10) + (j8 << 7) + (((qh ^ j8) & 7) << 4) + (w4 << 2);
-      ol = ((uint32_t)g << 10) + (j8 << 7) + (((ql ^ j8) & 7) << 4) + (w4 << 2);
-    }
-    u_t0[k] = t0;
-    u_oh[k] = oh;
-    u_ol[k] = ol;
-    const int kd = (j < A) ? 0 : (j == A ? 1 : (j == A + 1 ? 2 : 3));
-    u_kind[k] = kd;
-    const int lag0 = M.r0 + t0 - lmb[max(0, min(j, A - 1))];   // t_i - s_j in grid steps
-    // table index of stage 0 and its advance per stage (other slots: the centre)
-    u_ti[k] = (kd == 0) ? lag0 : 0;
-    u_step[k] = (kd == 0) ? SR : 0;
-    // a unit whose 8 slots are all landmarks needs no per-lane selection
-    u_plain[k] = (8 * ((j - j8) >> 3) + 7 < A);
+    unit_layout<BS>(warp, k, lane, t0s[k], js[k], oh[k], ol[k]);
+    dj[k] = lmb[min(js[k], kTcLmCap - 1)];              // landmark index (used when j < A)
   }
-  const bool full = (nrows == M.nst * SR);               // no rows past the end
-  const float w1h = rn_tf32(M.w1), w1l = rn_tf32(M.w1 - w1h);
-  // evaluated features: sqrt(log2 e) scalings of the operator constants
-  const float ic1 = 0.832554611157698f, ic2 = 0.693147180559945f;
-  for (int k = 0; k < M.nst; ++k, ++gs) {
+  const uint32_t cell = kTcOffCell + 16u * b;          // [-f_p hi/lo, zero]
+  const int lag_base = M.Kt + M.r0;
+#pragma unroll
+  for (int k = 0; k < kTcUnitsPerWarp; ++k) {
+    const int j = js[k];
+    if (j < A) {         // landmark: kappa(lag), lag = t_i - s_j in grid steps
+      src[k] = kTcOffTab + 8u * (uint32_t)(lag_base + t0s[k] - dj[k]);
+      step[k] = 8u * SR;
+    } else if (j == A + 1) {                            // r(t_i)
+      src[k] = kTcOffRs + 8u * (uint32_t)(b * kTcSubRows + t0s[k]);
+      step[k] = 8u * SR;
+    } else {                                            // -f_p, or zero padding
+      src[k] = cell + (j == A ? 0u : 8u);
+      step[k] = 0u;
+    }
+  }
+  for (int k = 0; k < nst; ++k, ++gs) {
     const int st = gs % kTcStages;
     if (gs >= kTcStages && !late)   // the MMAs that read this stage must be done
       late = !warp_wait(smem_u32(&s_empty[st]), (uint32_t)(((gs / kTcStages) - 1) & 1), wait_iter);
     if (!late) {
       unsigned char* tile = sm + st * kTcTileBytes;
+      float2 v[kTcUnitsPerWarp];
+      if (mode == 0) {
+#pragma unroll
+        for (int q = 0; q < kTcUnitsPerWarp; ++q)
+          v[q] = *reinterpret_cast<const float2*>(sm + src[q] + (uint32_t)k * step[q]);
+      } else {
+        // evaluated features: exp(-x^2) = 2^(-y^2), y = x sqrt(log2 e)
+        const float4* co = reinterpret_cast<const float4*>(sm + kTcOffCo) + b * kTcSubRows;
+        const float ic1 = 0.832554611157698f, ic2 = 0.693147180559945f;
+#pragma unroll
+        for (int q = 0; q < kTcUnitsPerWarp; ++q) {
+          const int tc = max(0, min(t0s[q] + k * SR, nrows - 1));
+          if (js[q] < A) {
+            float A0 = M.LA0, B1 = M.LB1, B2 = M.LB2;
+            if (mode == 2) {
+              const float4 c4 = co[tc];
+              A0 = c4.x; B1 = c4.y * ic1; B2 = -c4.z * ic2;
+            }
+            const float y = (float)(M.r0 + t0s[q] + k * SR - dj[q]) * M.hsc;
+            const float nu = -y * y;
+            v[q] = split_tf32(ex2_approx(nu) * fmaf(B2, nu, fmaf(B1, y, A0)));
+          } else if (js[q] == A && mode == 2) {
+            v[q] = split_tf32(co[tc].w);
+          } else {
+            v[q] = *reinterpret_cast<const float2*>(sm + src[q] + (uint32_t)k * step[q]);
+          }
+        }
+      }
+      if ((k + 1) * SR > nrows) {                       // rows past the end in this stage
+#pragma unroll
+        for (int q = 0; q < kTcUnitsPerWarp; ++q)
+          if (t0s[q] + k * SR >= nrows) v[q] = make_float2(0.f, 0.f);
+      }
 #pragma unroll
       for (int q = 0; q < kTcUnitsPerWarp; ++q) {
-        const int t = u_t0[q] + k * SR;                  // row of the sub-chunk
-        float hv, lv;
-        if (mode == 0) {
-          const float2 kv = tab[M.Kt + u_ti[q] + k * u_step[q]];
-          hv = kv.x;
-          lv = kv.y;
-        } else {
-          const int tc = max(0, min(t, nrows - 1));
-          float A0 = M.LA0, B1 = M.LB1, B2 = M.LB2;
-          if (mode == 2) {
-            const float4 c4 = co[tc];
-            A0 = c4.x; B1 = c4.y * ic1; B2 = -c4.z * ic2;
-          }
-          // exp(-x^2) = 2^(-y^2), y = x sqrt(log2 e), x = (t_i - s_j) / sigma
-          const float y = (float)(u_ti[q] + k * u_step[q]) * M.hsc;
-          const float nu = -y * y;
-          const float v = ex2_approx(nu) * fmaf(B2, nu, fmaf(B1, y, A0));
-          hv = rn_tf32(v);
-          lv = rn_tf32(v - hv);
-        }
-        if (!u_plain[q]) {                               // warp-uniform
-          const int kd = u_kind[q];
-          if (kd != 0) {
-            const int tc = max(0, min(t, nrows - 1));
-            float sv = 0.f;
-            if (kd == 1) sv = (mode == 2) ? co[tc].w : M.w1;
-            else if (kd == 2) sv = rr[tc];
-            if (kd == 1 && mode != 2) { hv = w1h; lv = w1l; }
-            else { hv = rn_tf32(sv); lv = rn_tf32(sv - hv); }
-          }
-        }
-        if (!full && t >= nrows) { hv = 0.f; lv = 0.f; }
-        unsigned char* p = tile + u_oh[q];
-        *reinterpret_cast<float*>(p) = hv;
-        if (BS <= 64) *reinterpret_cast<float*>(p + kLoOff) = lv;
-        else *reinterpret_cast<float*>(tile + u_ol[q]) = lv;
+        *reinterpret_cast<float*>(tile + oh[q]) = v[q].x;
+        *reinterpret_cast<float*>(tile + ol[q]) = v[q].y;
       }
     }
     fence_proxy_async_smem();
@@ -285,17 +337,18 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
       (reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   float* S = reinterpret_cast<float*>(sm + kTcOffS);
   float2* tab = reinterpret_cast<float2*>(sm + kTcOffTab);
-  double* Gu = reinterpret_cast<double*>(sm + kTcOffGu);
-  float* s_r = reinterpret_cast<float*>(sm + kTcOffR);      // [kTcSub][kTcSubRows]
+  float2* Gu = reinterpret_cast<float2*>(sm + kTcOffGu);   // unit Gram, compensated FP32
+  float2* s_rs = reinterpret_cast<float2*>(sm + kTcOffRs);  // [kTcSub][kTcSubRows]
   float4* s_co = reinterpret_cast<float4*>(sm + kTcOffCo);  // [kTcSub][kTcSubRows]
   int* s_lm = reinterpret_cast<int*>(sm + kTcOffLm);        // [kTcSub][kTcLmCap]
+  float2* s_cell = reinterpret_cast<float2*>(sm + kTcOffCell);   // [kTcSub][2]
   __shared__ __align__(8) uint64_t s_full[kTcStages], s_empty[kTcStages];
   __shared__ __align__(8) uint64_t s_ready[kTcSub], s_used[kTcSub], s_accf[kTcSub], s_afree[kTcSub];
-  __shared__ __align__(8) uint64_t s_drain;
+  __shared__ __align__(8) uint64_t s_drain, s_pbar;
   __shared__ TcSub s_meta[kTcSub];
   __shared__ int s_uidx[kMMax];            // landmark indices of the setup warps' unit
   __shared__ uint32_t s_tmem;
-  __shared__ int s_w, s_abort, s_eok, s_sok, s_pok[kTcSub];
+  __shared__ int s_w, s_abort, s_eok[kTcSub], s_sok[kTcSub];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == 0) tmem_alloc(smem_u32(&s_tmem), kTcCols);
@@ -306,11 +359,13 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     }
     for (int b = 0; b < kTcSub; ++b) {
       mbar_init(smem_u32(&s_ready[b]), kTcSetupThreads);
-      mbar_init(smem_u32(&s_used[b]), kTcProducers + 2);   // producers, issuer, epilogue
+      mbar_init(smem_u32(&s_used[b]), kTcProducers + 1 + 4);   // producers, issuer, epilogue warps
       mbar_init(smem_u32(&s_accf[b]), 1);
       mbar_init(smem_u32(&s_afree[b]), 1);
     }
     mbar_init(smem_u32(&s_drain), 1);
+    mbar_init(smem_u32(&s_pbar), kTcProducers);
+    for (int b = 0; b < kTcSub; ++b) s_meta[b].unit = -1;
     mbar_fence_init();
     s_abort = 0;
   }
@@ -322,22 +377,23 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   if (warp < kTcProducers) {
     // =========================== producers ===========================
     int gs = 0;                                        // stages produced so far
+    uint32_t pph = 0;                                  // meetings at s_pbar
     bool late = false;
     for (int s = 0;; ++s) {
       const int b = s % kTcSub;
-      // one thread waits for the sub-chunk and publishes the outcome (named
-      // barrier 1 holds the whole producer group)
-      if (tid == 0)
-        s_pok[b] = (!*(volatile int*)&s_abort &&
-                    mbar_wait_bounded(smem_u32(&s_ready[b]), (uint32_t)((s / kTcSub) & 1), wait_iter)) ? 1 : 0;
-      bar_named(1, kTcProdThreads);
-      if (!s_pok[b]) { if (tid == 0) atomicExch(&s_abort, 1); break; }
+      // each warp waits for the sub-chunk on its own; they meet only around a
+      // kappa table rebuild (bounded mbarrier waits: a warp that gives up
+      // cannot hold the others)
+      late = !warp_wait(smem_u32(&s_ready[b]), (uint32_t)((s / kTcSub) & 1), wait_iter) ||
+             *(volatile int*)&s_abort;
+      if (late) break;
       const TcSub M = s_meta[b];
       if (M.nst < 0) break;
       if (M.first && M.mode == 0) {
-        // kappa(lag), lag = -Kt..Kt, of this unit: every producer is past the
-        // previous unit's stages (barrier above); A0 b0 + A1 b1 + A2 b2 from the
-        // landmark set's lag tables (zero beyond lag Kset), split into hi/lo
+        // kappa(lag), lag = -Kt..Kt, of this unit, once every producer is past
+        // the previous unit's stages: A0 b0 + A1 b1 + A2 b2 from the landmark
+        // set's lag tables (zero beyond lag Kset), split into hi/lo
+        if (!prod_meet(&s_pbar, pph, wait_iter)) { late = true; break; }
         const float* T = lag + M.lag_off;
         for (int e = tid; e <= 2 * M.Kt; e += kTcProdThreads) {
           const int lg = e - M.Kt, a = lg < 0 ? -lg : lg;
@@ -346,44 +402,38 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
             const float b1 = lg < 0 ? -T[6 * a + 2] : T[6 * a + 2];
             v = fmaf(M.A2, T[6 * a + 4], fmaf(M.A1, b1, M.A0 * T[6 * a]));
           }
-          const float h = rn_tf32(v);
-          tab[e] = make_float2(h, rn_tf32(v - h));
+          tab[e] = split_tf32(v);
         }
-        bar_named(1, kTcProdThreads);
+        if (!prod_meet(&s_pbar, pph, wait_iter)) { late = true; break; }
       }
-      const float* rr = s_r + b * kTcSubRows;
-      const float4* co = s_co + b * kTcSubRows;
-      const int* lmb = s_lm + b * kTcLmCap;
       switch (M.Bs) {
-        case 16: produce_sub<16>(M, sm, tab, rr, co, lmb, gs, warp, lane, wait_iter, s_full, s_empty, late); break;
-        case 32: produce_sub<32>(M, sm, tab, rr, co, lmb, gs, warp, lane, wait_iter, s_full, s_empty, late); break;
-        case 64: produce_sub<64>(M, sm, tab, rr, co, lmb, gs, warp, lane, wait_iter, s_full, s_empty, late); break;
-        default: produce_sub<128>(M, sm, tab, rr, co, lmb, gs, warp, lane, wait_iter, s_full, s_empty, late); break;
+        case 16: produce_sub<16>(M, b, sm, gs, warp, lane, wait_iter, s_full, s_empty, late); break;
+        case 32: produce_sub<32>(M, b, sm, gs, warp, lane, wait_iter, s_full, s_empty, late); break;
+        case 64: produce_sub<64>(M, b, sm, gs, warp, lane, wait_iter, s_full, s_empty, late); break;
+        default: produce_sub<128>(M, b, sm, gs, warp, lane, wait_iter, s_full, s_empty, late); break;
       }
       __syncwarp();
-      if (lane == 0) {
-        if (late) atomicExch(&s_abort, 1);
-        mbar_arrive(smem_u32(&s_used[b]));             // sub-chunk buffer b may be refilled
-      }
+      if (lane == 0 && !late) mbar_arrive(smem_u32(&s_used[b]));   // buffer b may be refilled
+      if (late) break;
     }
+    if (late && lane == 0) atomicExch(&s_abort, 1);
   } else if (warp >= kTcSetupWarp0) {
     // ============================== setup ==============================
-    const int st = tid - 32 * kTcSetupWarp0;           // 0..63
+    const int st = tid - 32 * kTcSetupWarp0;           // 0..127
     int w = -1;                                        // current unit
     int row = 0, ur0 = 0, r1 = 0, m = 0, Kb = 0, jlo_u = 0, Au = 0, mode = 0, Kt = 0;
+    int wlo = 0, whi = 0;                              // window of the last sub-chunk
     int64_t uslot = 0;
-    float cb = 1.f, sb = 0.f;                          // rotation of the sine by 64 rows
+    float cb = 1.f, sb = 0.f;                          // rotation of the sine by 128 rows
     Inst I;
     Lset LS;
     for (int s = 0;; ++s) {
       const int b = s % kTcSub;
       if (s >= kTcSub) {   // every consumer of sub-chunk s - kTcSub is done with buffer b
         if (st == 0)
-          s_sok = mbar_wait_bounded(smem_u32(&s_used[b]), (uint32_t)(((s / kTcSub) - 1) & 1), wait_iter) ? 1 : 0;
+          s_sok[b] = mbar_wait_bounded(smem_u32(&s_used[b]), (uint32_t)(((s / kTcSub) - 1) & 1), wait_iter) ? 1 : 0;
         bar_named(3, kTcSetupThreads);
-        const int ok = s_sok;
-        bar_named(3, kTcSetupThreads);
-        if (!ok) { if (st == 0) atomicExch(&s_abort, 1); break; }
+        if (!s_sok[b]) { if (st == 0) atomicExch(&s_abort, 1); break; }
       }
       if (w < 0 || row >= r1) {                        // next work unit
         if (st == 0) s_w = *(volatile int*)&s_abort ? nwork : atomicAdd(counter, 1);
@@ -407,46 +457,51 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         Kt = Kb + kTcSubRows - 1;
         mode = (I.kind == NYS_COEF_LIN) ? ((2 * Kt + 1 <= kTcTabCap && lag != nullptr) ? 0 : 1) : 2;
         if (I.kind == NYS_COEF_LIN) {
-          // sin and cos of 64 dth (dth reduced mod 2 pi on the host)
-          const double be = remainder(64.0 * I.dth, 6.283185307179586476925286766559);
+          // sin and cos of 128 dth (dth reduced mod 2 pi on the host)
+          const double be = remainder(128.0 * I.dth, 6.283185307179586476925286766559);
           sincosf((float)be, &sb, &cb);
         }
         for (int j = st; j < m; j += kTcSetupThreads) s_uidx[j] = lm_idx[I.lm_off + j];
         bar_named(3, kTcSetupThreads);
         lm_window(s_uidx, m, row, r1, Kb, jlo_u, Au);
+        wlo = whi = jlo_u;
       }
-      // sub-chunk length: at most kTcMmaSteps MMA steps per accumulator entry
+      // window of rows [row, row + n_sub), advanced from the previous one (rows
+      // only move forward inside a unit)
       int n_sub = min(kTcSubRows, r1 - row);
-      int jlo, A;
-      lm_window(s_uidx, m, row, row + n_sub, Kb, jlo, A);
-      int Bs = (A + 2 <= 16) ? 16 : (A + 2 <= 32 ? 32 : (A + 2 <= 64 ? 64 : 128));
+      while (wlo < m && s_uidx[wlo] < row - Kb) ++wlo;
+      if (whi < wlo) whi = wlo;
+      while (whi < m && s_uidx[whi] <= row + n_sub - 1 + Kb) ++whi;
+      int jlo = wlo, A = whi - wlo;
+      int Bs = slot_block(A + 2);
+      // at most kTcMmaSteps MMA steps per accumulator entry
       const int cap = (Bs <= 64) ? kTcMmaSteps * 512 / Bs : 32;
       if (n_sub > cap) {
         n_sub = cap;
         lm_window(s_uidx, m, row, row + n_sub, Kb, jlo, A);
-        Bs = (A + 2 <= 16) ? 16 : (A + 2 <= 32 ? 32 : (A + 2 <= 64 ? 64 : 128));
+        Bs = slot_block(A + 2);
+        // the running window is the exact one of the rows actually taken: the
+        // kappa table covers the lags of window landmarks only
+        wlo = jlo;
+        whi = jlo + A;
       }
       const int M2 = A + 2;
       const int SR = (Bs <= 64) ? 2048 / Bs : 16;
       const RowConst RK = I.rk;
       for (int j = st; j < A; j += kTcSetupThreads) s_lm[b * kTcLmCap + j] = s_uidx[jlo + j];
       if (I.kind == NYS_COEF_LIN) {
-        // r(t_i) = c sin(theta_i): one sine per thread, then rotations by 64 rows
+        // r(t_i) = c sin(theta_i): one sine per thread, then a rotation by 128 rows
         if (st < n_sub) {
           float sn, cs;
           lin_sincos(RK, row + st, sn, cs);
-          for (int t = st; t < n_sub; t += kTcSetupThreads) {
-            s_r[b * kTcSubRows + t] = RK.c * sn;
-            const float s2 = fmaf(sn, cb, cs * sb);
-            cs = fmaf(cs, cb, -sn * sb);
-            sn = s2;
-          }
+          s_rs[b * kTcSubRows + st] = split_tf32(RK.c * sn);
+          if (st + 128 < n_sub) s_rs[b * kTcSubRows + st + 128] = split_tf32(RK.c * fmaf(sn, cb, cs * sb));
         }
       } else {
         for (int t = st; t < n_sub; t += kTcSetupThreads) {
           ff c5[5];
           row_coef_ff(I, RK, ctab, row + t, c5);
-          s_r[b * kTcSubRows + t] = c5[4].hi;
+          s_rs[b * kTcSubRows + t] = split_tf32(c5[4].hi);
           s_co[b * kTcSubRows + t] = make_float4(c5[0].hi, c5[1].hi, c5[2].hi, c5[3].hi);
         }
       }
@@ -460,23 +515,28 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         M.r0 = row;
         M.nrows = n_sub;
         M.joff = jlo - jlo_u;
-        M.Au = Au;
-        M.jlo_u = jlo_u;
         M.first = (row == ur0) ? 1 : 0;
         M.last = (row + n_sub >= r1) ? 1 : 0;
-        M.mode = mode;
-        M.Kt = Kt;
-        M.Kset = LS.K;
-        M.slot_off = uslot;
-        M.lag_off = LS.lag_off;
-        M.hsc = (float)I.hs * 1.20112240878645f;
-        M.LA0 = RK.A0.hi;
-        M.LB1 = RK.A1.hi * 0.832554611157698f;
-        M.LB2 = -RK.A2.hi * 0.693147180559945f;
-        M.w1 = RK.w1.hi;
-        M.A0 = RK.A0.hi;
-        M.A1 = RK.A1.hi;
-        M.A2 = RK.A2.hi;
+        if (M.unit != w) {                             // the unit's constants
+          M.unit = w;
+          M.Au = Au;
+          M.jlo_u = jlo_u;
+          M.mode = mode;
+          M.Kt = Kt;
+          M.Kset = LS.K;
+          M.slot_off = uslot;
+          M.lag_off = LS.lag_off;
+          M.hsc = (float)I.hs * 1.20112240878645f;
+          M.LA0 = RK.A0.hi;
+          M.LB1 = RK.A1.hi * 0.832554611157698f;
+          M.LB2 = -RK.A2.hi * 0.693147180559945f;
+          M.w1 = RK.w1.hi;
+          M.A0 = RK.A0.hi;
+          M.A1 = RK.A1.hi;
+          M.A2 = RK.A2.hi;
+          s_cell[2 * b] = split_tf32(RK.w1.hi);
+          s_cell[2 * b + 1] = make_float2(0.f, 0.f);
+        }
       }
       row += n_sub;
       mbar_arrive(smem_u32(&s_ready[b]));              // each thread: its writes are done
@@ -546,29 +606,30 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     const int rho = 32 * quad + lane;                  // operand row of this thread
     for (int s = 0;; ++s) {
       const int b = s % kTcSub;
-      // one thread waits (bounded) and publishes the outcome, so that the four
-      // warps take the same path through their named barriers
-      if (et == 0) s_eok = mbar_wait_bounded(smem_u32(&s_ready[b]), (uint32_t)((s / kTcSub) & 1), wait_iter) ? 1 : 0;
-      bar_named(2, 128);
-      const bool okm = s_eok != 0;
-      const TcSub M = s_meta[b];
-      bar_named(2, 128);                               // all four warps have read the meta
-      if (et == 0) mbar_arrive(smem_u32(&s_used[b]));
-      if (!okm) { if (et == 0) atomicExch(&s_abort, 1); break; }
-      if (M.nst < 0) break;
-      const int M2u = M.Au + 2, Eu = M2u * (M2u + 1) / 2;
-      if (M.first) {
-        for (int e = et; e < Eu; e += 128) Gu[e] = 0.0;
-        bar_named(2, 128);
+      const uint32_t par = (uint32_t)((s / kTcSub) & 1);
+      // one thread waits for the sub-chunk (its description, then its
+      // accumulator) and publishes the outcome, so that the four warps take the
+      // same path through their named barriers
+      if (et == 0) {
+        int ok = mbar_wait_bounded(smem_u32(&s_ready[b]), par, wait_iter) ? 1 : 0;
+        if (ok && s_meta[b].nst >= 0)
+          ok = mbar_wait_bounded(smem_u32(&s_accf[b]), par, wait_iter) ? 1 : 0;
+        s_eok[b] = ok;
       }
-      if (et == 0) s_eok = mbar_wait_bounded(smem_u32(&s_accf[b]), (uint32_t)((s / kTcSub) & 1), wait_iter) ? 1 : 0;
       bar_named(2, 128);
-      if (s_eok == 0) { if (et == 0) atomicExch(&s_abort, 1); break; }
+      if (!s_eok[b]) { if (et == 0) atomicExch(&s_abort, 1); break; }
+      const int nst = s_meta[b].nst;
+      const int Bs = s_meta[b].Bs, A = s_meta[b].A, M2 = s_meta[b].M2;
+      const int joff = s_meta[b].joff, Au = s_meta[b].Au;
+      const int first = s_meta[b].first, last = s_meta[b].last, jlo_u = s_meta[b].jlo_u;
+      const int64_t so = s_meta[b].slot_off;
+      const int Nc = s_meta[b].N;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&s_used[b]));   // this warp has read the description
+      if (nst < 0) break;
+      const int M2u = Au + 2, Eu = M2u * (M2u + 1) / 2;
       tc_fence_after();
       const uint32_t lanebase = tmem + (uint32_t)b * kTcSetCols + ((uint32_t)(32 * quad) << 16);
-      const int Bs = M.Bs, A = M.A, M2 = M.M2;
-      // sub-chunk column c -> unit column (landmarks shift by joff; -f_p, r last)
-      const int joff = M.joff, Au = M.Au;
       if (Bs <= 64) {
         // lane rho = Bs (2 r + h) + j reads its row set's block: columns
         // 2 Bs r + l (hi) and 2 Bs r + Bs + l (lo), l < Bs
@@ -583,26 +644,31 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
           for (int t = 0; t < 16; ++t)
             S[rho * kTcSLd + l0 + t] = __uint_as_float(vh[t]) + __uint_as_float(vl[t]);
         }
+        if (first)
+          for (int e = et; e < Eu; e += 128) Gu[e] = make_float2(0.f, 0.f);
         tc_fence_before();
-        bar_named(2, 128);                             // accumulator read, S complete
+        bar_named(2, 128);                             // accumulator read, S complete, Gu clear
         if (et == 0) mbar_arrive(smem_u32(&s_afree[b]));
         const int nq = 128 / Bs;                       // operand rows per slot (row sets x hi/lo)
-        const float invM2 = 1.0f / (float)M2;
-        for (int e = et; e < M2 * M2; e += 128) {
-          const int j = (int)(((float)e + 0.5f) * invM2);
-          const int l = e - j * M2;
-          if (l >= j) {
+        const int lb = (Bs == 16) ? 4 : (Bs == 32 ? 5 : 6);
+        for (int e = et; e < Bs * Bs; e += 128) {
+          const int j = e >> lb, l = e & (Bs - 1);
+          if (l >= j && l < M2) {
             float sum = 0.f;
             for (int q = 0; q < nq; ++q) sum += S[(q * Bs + j) * kTcSLd + l];
             const int ju = (j < A) ? j + joff : Au + (j - A);
             const int lu = (l < A) ? l + joff : Au + (l - A);
-            Gu[ju * M2u - ju * (ju - 1) / 2 + (lu - ju)] += (double)sum;
+            acc_comp(&Gu[ju * M2u - ju * (ju - 1) / 2 + (lu - ju)], sum);
           }
         }
       } else {
+        if (first) {
+          for (int e = et; e < Eu; e += 128) Gu[e] = make_float2(0.f, 0.f);
+          bar_named(2, 128);
+        }
         // lane rho = slot j holds row j of the sub-chunk Gram itself
         const int j = rho;
-        for (int l0 = 0; l0 < M.N; l0 += 16) {
+        for (int l0 = 0; l0 < Nc; l0 += 16) {
           uint32_t v[16];
           tmem_ld16_nowait(lanebase + (uint32_t)l0, v);
           tmem_wait_ld();
@@ -613,7 +679,7 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
               const int l = l0 + t;
               if (l >= j && l < M2) {
                 const int lu = (l < A) ? l + joff : Au + (l - A);
-                Gu[ju * M2u - ju * (ju - 1) / 2 + (lu - ju)] += (double)__uint_as_float(v[t]);
+                acc_comp(&Gu[ju * M2u - ju * (ju - 1) / 2 + (lu - ju)], __uint_as_float(v[t]));
               }
             }
           }
@@ -623,11 +689,14 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         if (et == 0) mbar_arrive(smem_u32(&s_afree[b]));
       }
       bar_named(2, 128);                               // Gu updated, S free
-      if (M.last) {
+      if (last) {
         // slot: [first landmark, landmark count, packed upper Gram of the unit]
-        double* out = part + M.slot_off;
-        if (et == 0) { out[0] = (double)M.jlo_u; out[1] = (double)Au; }
-        for (int e = et; e < Eu; e += 128) out[2 + e] = Gu[e];
+        double* out = part + so;
+        if (et == 0) { out[0] = (double)jlo_u; out[1] = (double)Au; }
+        for (int e = et; e < Eu; e += 128) {
+          const float2 g = Gu[e];
+          out[2 + e] = (double)g.x + (double)g.y;
+        }
         bar_named(2, 128);                             // Gu may be cleared for the next unit
       }
     }

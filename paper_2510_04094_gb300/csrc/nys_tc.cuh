@@ -99,9 +99,21 @@ __device__ __forceinline__ uint32_t mbar_try_wait_sleep(uint32_t mbar, uint32_t 
       : "=r"(ok) : "r"(mbar), "r"(parity), "r"(1000u) : "memory");
   return ok;
 }
-// Bounded wait for the phase of the given parity (at most max_iter polls of
-// at most 1 us each); returns false when it gave up.
+// Non-blocking test of the phase of the given parity.
+__device__ __forceinline__ uint32_t mbar_test_wait(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
+  return ok;
+}
+// Bounded wait for the phase of the given parity (a non-blocking test first,
+// then at most max_iter polls of at most 1 us each); returns false when it gave
+// up.  A bound of 0 gives up at once, whatever the phase (the callers use it to
+// exercise their timeout paths).
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, int max_iter) {
+  if (max_iter > 0 && mbar_test_wait(mbar, parity)) return true;
   for (int it = 0; it < max_iter; ++it)
     if (mbar_try_wait_sleep(mbar, parity)) return true;
   return false;
