@@ -12,12 +12,15 @@ refinement for the whole batch (nys_run, one CUDA graph), inputs resident.
 Prints one JSON line (rank 0).  Under torchrun each rank solves its own batch
 (weak scaling; no collective on the data path, one all-reduce for the timing).
 
-Roofline: the dominant kernel's rate counts the method's own arithmetic, F(m) =
-2m^2 (projection phi = W k) + (m+1)(m+2) (upper-triangle Gram) + 2(m+1) (right-hand
-side) + 10m (operator) FLOPs per collocation row, and divides it by the measured
-peak of the pipe its contraction runs on (include/nys_peak.h probes, run in the
-same process).  The FLOPs the kernel actually issues on that pipe are reported
-beside it.
+Roofline (mixed path): the fused assembly of the metric workload runs on the band
+kernel (FP32 FMAs on the CUDA cores); its rate counts the banded Gram each row
+needs -- (a_i + 2)(a_i + 3) + 6 a_i FLOPs with a_i the landmarks within
+u = ((t_i - s_j)/sigma)^2 <= 24 of row i -- and divides it by the measured FP32
+FMA peak (include/nys_peak.h probes, run in the same process).  The method's
+dense count per row, F(m) = 2m^2 (projection phi = W k) + (m+1)(m+2)
+(upper-triangle Gram) + 2(m+1) (right-hand side) + 10m (operator), is reported
+beside it as the method-equivalent rate; the FP64 path divides F(m) by the
+measured DFMA peak.
 """
 import argparse
 import json
@@ -35,10 +38,10 @@ sys.path.insert(0, ROOT)
 METRIC = "batched ODE solves/s at n=1e4, m=50"
 UNIT = "solves/s"
 LAG_U = 80.0   # kernel values exp(-u) with u > 80 (< 2e-35) are treated as zero
-# DRAM bytes (read + write) of one k_assemble_tc launch per instance of the
+# DRAM bytes (read + write) of one k_assemble_band launch per instance of the
 # metric family, from an ncu capture of the current kernel (None: no capture of
 # the current kernel yet)
-TC_DRAM_BYTES_PER_INSTANCE = None
+BAND_DRAM_BYTES_PER_INSTANCE = None
 
 
 def parse():
@@ -159,25 +162,26 @@ def dense_flops(problems):
     return float(sum(rows_of(q) * F_row(q["m"]) for q in problems))
 
 
-def _band(q):
+def _band(q, u=None):
     import numpy as np
     n, m = q["n"], q["m"]
     h = (q["t1"] - q["t0"]) / (n - 1)
-    K = int(min(n - 1, math.ceil(math.sqrt(LAG_U) / (h / q["sigma"]))))
+    K = int(min(n - 1, math.ceil(math.sqrt(LAG_U if u is None else u) / (h / q["sigma"]))))
     j = np.arange(m)
     idx = (j * (n - 1) + (m - 1) // 2) // (m - 1)
     return idx, K
 
 
-def banded_flops(problems):
-    """FLOPs of the Gram over the landmarks inside each row's band (a_i of them):
+def banded_flops(problems, u=None):
+    """FLOPs of the Gram over the landmarks inside each row's band (a_i of them,
+    u = ((t_i - s_j)/sigma)^2 <= u, default the FP64 band LAG_U):
     (a_i + 2)(a_i + 3) + 6 a_i per row (exponentials on the SFU, not counted)."""
     import numpy as np
     cache, tot = {}, 0.0
     for q in problems:
-        key = (q["n"], q["m"], q["t0"], q["t1"], q["sigma"])
+        key = (q["n"], q["m"], q["t0"], q["t1"], q["sigma"], u)
         if key not in cache:
-            idx, K = _band(q)
+            idx, K = _band(q, u)
             i = np.arange(1, q["n"])
             a = (np.searchsorted(idx, i + K, side="right") - np.searchsorted(idx, i - K, side="left")).astype(float)
             cache[key] = float(np.sum((a + 2) * (a + 3) + 6 * a))
@@ -185,7 +189,8 @@ def banded_flops(problems):
     return tot
 
 
-TC_BAND_U = 24.0      # the tensor-core Gram's sub-chunk windows keep u <= 24
+BAND_U = 24.0         # the FP32 assembly Grams keep the landmarks with u <= 24
+TC_BAND_U = BAND_U    # the tensor-core Gram's sub-chunk windows
 TC_SUB_ROWS = 256
 TC_MMA_STEPS = 8      # MMA steps per tensor-memory accumulator entry, at most
 
@@ -241,6 +246,16 @@ def tc_issued_flops(problems, num_sms=152):
                     s0 += L
             cache[key] = f
         tot += cache[key]
+    return tot
+
+
+def band_issued_flops(problems):
+    """FP32 FMA FLOPs k_assemble_band issues: 136 FMAs (16 x 16 window Gram,
+    upper triangle) per row of every window, rows past a unit's end included."""
+    import numpy as np
+    tot = 0.0
+    for q in problems:
+        tot += 2.0 * 136 * rows_of(q)
     return tot
 
 
@@ -626,23 +641,43 @@ def main():
     if rank == 0:
         pk = measure_peaks(local)
         fl = dense_flops(probs)
-        achieved = fl / (asm_ms * 1e-3) / 1e12
+        method_rate = fl / (asm_ms * 1e-3) / 1e12
         mixed = args.precision == "mixed"
-        peak = pk["tf32_mma"]["tflops"] if mixed else pk["dfma"]["tflops"]
-        roof = {"bound": "tensor" if mixed else "alu",
-                "kernel": "k_assemble_tc" if mixed else "k_assemble_f64",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": ("measured in this run: tcgen05 kind::tf32 probe, burst" if mixed
-                                else "measured in this run: DFMA probe, burst"),
-                "flop_count": "F(m) = 2m^2+(m+1)(m+2)+2(m+1)+10m per collocation row",
-                "flops_per_launch": fl, "ms_per_launch": asm_ms,
-                "traffic": (TC_DRAM_BYTES_PER_INSTANCE * B if mixed and TC_DRAM_BYTES_PER_INSTANCE
-                            and args.n == 10_000 and args.m == 50 else None)}
-        if mixed:
-            iss = tc_issued_flops(probs)
-            roof["issued_tflops"] = iss / (asm_ms * 1e-3) / 1e12
-            roof["pipe_frac"] = roof["issued_tflops"] / peak
-            roof["banded_useful_tflops"] = banded_flops(probs) / (asm_ms * 1e-3) / 1e12
+        band_items, other_items = bt.assembly_items() if mixed else (0, 1)
+        if mixed and other_items == 0:
+            # the band kernel: FP32 FMAs on the CUDA cores; its algorithmic work is
+            # the banded Gram of every row (landmarks within u <= 24 of the row)
+            bfl = banded_flops(probs, u=BAND_U)
+            peak = pk["ffma"]["tflops"]
+            roof = {"bound": "alu", "kernel": "k_assemble_band",
+                    "achieved": bfl / (asm_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                    "frac": bfl / (asm_ms * 1e-3) / 1e12 / peak,
+                    "peak_source": "measured in this run: FFMA probe, burst",
+                    "flop_count": "banded Gram per collocation row, (a_i+2)(a_i+3) + 6 a_i with a_i "
+                                  "the landmarks within u = ((t_i - s_j)/sigma)^2 <= 24 of row i",
+                    "flops_per_launch": bfl, "ms_per_launch": asm_ms,
+                    "traffic": (BAND_DRAM_BYTES_PER_INSTANCE * B if BAND_DRAM_BYTES_PER_INSTANCE
+                                and args.n == 10_000 and args.m == 50 else None),
+                    "issued_fma_tflops": band_issued_flops(probs) / (asm_ms * 1e-3) / 1e12,
+                    "method_equivalent": {
+                        "flop_count": "F(m) = 2m^2+(m+1)(m+2)+2(m+1)+10m per collocation row",
+                        "tflops": method_rate,
+                        "vs_tf32_tensor_peak": method_rate / pk["tf32_mma"]["tflops"]}}
+        else:
+            peak = pk["tf32_mma"]["tflops"] if mixed else pk["dfma"]["tflops"]
+            roof = {"bound": "tensor" if mixed else "alu",
+                    "kernel": ("k_assemble_tc" + (" + k_assemble_band" if band_items else "")) if mixed
+                              else "k_assemble_f64",
+                    "achieved": method_rate, "peak": peak, "unit": "TFLOP/s", "frac": method_rate / peak,
+                    "peak_source": ("measured in this run: tcgen05 kind::tf32 probe, burst" if mixed
+                                    else "measured in this run: DFMA probe, burst"),
+                    "flop_count": "F(m) = 2m^2+(m+1)(m+2)+2(m+1)+10m per collocation row",
+                    "flops_per_launch": fl, "ms_per_launch": asm_ms, "traffic": None}
+            if mixed:
+                iss = tc_issued_flops(probs)
+                roof["issued_tflops"] = iss / (asm_ms * 1e-3) / 1e12
+                roof["pipe_frac"] = roof["issued_tflops"] / peak
+                roof["banded_useful_tflops"] = banded_flops(probs) / (asm_ms * 1e-3) / 1e12
         extra["peaks"] = pk
         if not args.no_extras:
             extra.update(side_measurements(args, probs, bt, value, ws, local, stream, flush, pk))

@@ -120,16 +120,29 @@ typedef struct {
                             (default 1e-12 when <= 0)                            */
   int32_t scale_sqrt_m;  /* 1: eq32's sqrt(m) feature scale (== gamma * m)      */
   int32_t assembly;      /* MIXED only, nys_assembly: NYS_ASM_AUTO (0) runs the
-                            Gram on the tensor cores (tcgen05, TF32 hi/lo split,
-                            FP32 accumulation in tensor memory); NYS_ASM_SIMT (1)
-                            on the CUDA cores (FP32 FMA, 8x8 register blocks)  */
+                            Gram of every kind-LIN instance whose landmark
+                            windows are narrow (at most 14 landmarks per window
+                            of 32..256 rows within the band u <= 24) on the CUDA
+                            cores, one warp per work unit (FP32 products, 16 x
+                            16 window Grams, compensated unit sums), and every
+                            other instance on the tensor cores (tcgen05, TF32
+                            hi/lo split, FP32 accumulation in tensor memory);
+                            NYS_ASM_TC (3) puts every instance on the tensor
+                            cores; NYS_ASM_SIMT (1) runs the older CUDA-core
+                            kernel (FP32 FMA, 8x8 register blocks)            */
 } nys_options;
 
-/* NYS_ASM_TUNE (MIXED): before the first assembly, time the tensor-core Gram
-   (on its long work units) and the CUDA-core Gram (work items of 512 and 1024
-   rows) on the context's own batch (CUDA events, a few launches each) and keep
-   the fastest; see nys_assembly_config.  Other precisions ignore it.        */
-typedef enum { NYS_ASM_AUTO = 0, NYS_ASM_SIMT = 1, NYS_ASM_TUNE = 2 } nys_assembly;
+/* NYS_ASM_TUNE (MIXED): before the first assembly, time NYS_ASM_AUTO,
+   NYS_ASM_TC (both on the tensor-core kernel's long work units) and
+   NYS_ASM_SIMT (work items of 512 and 1024 rows) on the context's own batch
+   (CUDA events, a few launches each) and keep the fastest; see
+   nys_assembly_config.  Other precisions ignore it.                         */
+typedef enum {
+  NYS_ASM_AUTO = 0,
+  NYS_ASM_SIMT = 1,
+  NYS_ASM_TUNE = 2,
+  NYS_ASM_TC = 3
+} nys_assembly;
 
 typedef struct nys_ctx nys_ctx;
 
@@ -151,7 +164,9 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* inst, int32_t batch,
 /* Replace the instances of an existing context (same batch size; per
    instance same p, n, m, kind and landmark indices as at setup).  Enqueues
    the host -> device copy of the descriptors; the Nystrom factor is
-   recomputed by the next nys_assemble or nys_run.
+   recomputed by the next nys_assemble or nys_run.  MIXED with NYS_ASM_AUTO:
+   when a new sigma changes an instance's band plan, the assembly work list is
+   rebuilt (synchronises the device, drops captured nys_run graphs).
    Errors: NYS_EINVAL (shape changed), NYS_ECUDA.                            */
 int32_t nys_update(nys_ctx* c, const nys_instance* inst, void* stream);
 
@@ -178,10 +193,17 @@ int32_t nys_solve(nys_ctx* c, void* stream, double* x_out, int32_t* status_out);
    (x_out, status_out) pair and replayed afterwards.                         */
 int32_t nys_run(nys_ctx* c, void* stream, double* x_out, int32_t* status_out);
 
-/* Assembly configuration in use: kernel (NYS_ASM_AUTO = tensor cores or
-   NYS_ASM_SIMT) and rows per work item.  With NYS_ASM_TUNE this runs the tuner
-   if it has not run yet (synchronises `stream`).                              */
+/* Assembly configuration in use: kernel (NYS_ASM_AUTO, NYS_ASM_TC or
+   NYS_ASM_SIMT) and rows per work item (the tensor-core units; band units are
+   planned per instance).  With NYS_ASM_TUNE this runs the tuner if it has not
+   run yet (synchronises `stream`).                                           */
 int32_t nys_assembly_config(nys_ctx* c, void* stream, int32_t* kernel_out, int32_t* rows_out);
+
+/* Work items of the assembly work list in use: band units (NYS_ASM_AUTO's
+   CUDA-core kernel for narrow windows) and the other kernel's items.  Host
+   only, no device call; the tuner's choice shows after it has run.
+   Errors: NYS_EINVAL (NULL context or output).                                */
+int32_t nys_assembly_items(const nys_ctx* c, int32_t* band_items, int32_t* other_items);
 
 /* Bounded device waits of the tensor-core assembly (NYS_MIXED with
    NYS_ASM_AUTO): each mbarrier wait gives up after `polls` polls of at most

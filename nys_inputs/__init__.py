@@ -26,7 +26,7 @@ GAMMA = 1e10
 
 _KEYS = {"cfg1": 1, "cfg2": 2, "m0": 10, "cfg3": 3, "cfg4": 4, "cfg5": 5, "small": 99, "trunc": 98,
          "bvp": 11, "small_bvp": 97, "small_higher": 96,
-         "big_m": 95}
+         "big_m": 95, "band": 94}
 
 
 def rng(name, sub=0):

@@ -13,7 +13,7 @@ NYS_OK, NYS_EINVAL, NYS_ENOMEM, NYS_ECUDA = 0, -1, -2, -3
 NYS_ENOTSPD, NYS_ENOCONV, NYS_ENONFINITE, NYS_ETIMEOUT = -4, -5, -6, -7
 NYS_EPRECISION, NYS_ESTATE = -8, -9
 NYS_FP64, NYS_MIXED = 0, 1
-NYS_ASM_AUTO, NYS_ASM_SIMT, NYS_ASM_TUNE = 0, 1, 2
+NYS_ASM_AUTO, NYS_ASM_SIMT, NYS_ASM_TUNE, NYS_ASM_TC = 0, 1, 2, 3
 NYS_COEF_TABLE, NYS_COEF_LIN, NYS_COEF_POLY_NL = 0, 1, 2
 NYS_BC_IVP, NYS_BC_BVP = 0, 1
 NYS_M_MAX = 224
@@ -59,6 +59,7 @@ def lib():
         L.nys_run.argtypes = [vp, vp, vp, vp]
         L.nys_x_stride.argtypes = [vp]
         L.nys_assembly_config.argtypes = [vp, vp, C.POINTER(i32), C.POINTER(i32)]
+        L.nys_assembly_items.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
         L.nys_upload_bytes.argtypes = [vp]
         L.nys_upload_bytes.restype = C.c_int64
         L.nys_m_eff.argtypes = [vp, vp, C.POINTER(i32)]
@@ -77,7 +78,7 @@ def lib():
         L.nys_last_error.restype = C.c_char_p
         for name in ("nys_setup", "nys_update", "nys_assemble", "nys_solve", "nys_run",
                      "nys_x_stride", "nys_m_eff", "nys_eval", "nys_newton", "nys_grad",
-                     "nys_assembly_config"):
+                     "nys_assembly_config", "nys_assembly_items"):
             getattr(L, name).restype = i32
         _LIB = L
     return _LIB
@@ -122,6 +123,12 @@ def nys_assembly_config(ctx, stream):
     return kernel.value, rows.value
 
 
+def nys_assembly_items(ctx):
+    band, other = C.c_int32(), C.c_int32()
+    check(lib().nys_assembly_items(ctx, C.byref(band), C.byref(other)))
+    return band.value, other.value
+
+
 def nys_upload_bytes(ctx):
     return lib().nys_upload_bytes(ctx)
 
@@ -155,7 +162,7 @@ def nys_destroy(ctx):
 
 
 EXPORTS = ("nys_setup", "nys_update", "nys_assemble", "nys_solve", "nys_run", "nys_x_stride",
-           "nys_upload_bytes", "nys_assembly_config",
+           "nys_upload_bytes", "nys_assembly_config", "nys_assembly_items",
            "nys_m_eff", "nys_eval", "nys_newton", "nys_grad", "nys_solve_noalloc", "nys_destroy",
            "nys_set_wait_limit",
            "nys_status_str",

@@ -72,6 +72,7 @@ class Batch:
 
     def __init__(self, problems, precision="fp64", refine_steps=-1, eig_tau=0.0,
                  scale_sqrt_m=False, stream=None, assembly="auto"):
+        """assembly (mixed precision): "auto", "tc", "simt" or "tune" (nys_assembly)."""
         self.problems = list(problems)
         self.B = len(self.problems)
         self.stream = stream
@@ -80,7 +81,8 @@ class Batch:
         opt.refine_steps = int(refine_steps)
         opt.eig_tau = float(eig_tau)
         opt.scale_sqrt_m = 1 if scale_sqrt_m else 0
-        opt.assembly = {"auto": A.NYS_ASM_AUTO, "simt": A.NYS_ASM_SIMT, "tune": A.NYS_ASM_TUNE}[assembly]
+        opt.assembly = {"auto": A.NYS_ASM_AUTO, "simt": A.NYS_ASM_SIMT, "tune": A.NYS_ASM_TUNE,
+                        "tc": A.NYS_ASM_TC}[assembly]
         arr, keep = pack_instances(self.problems)
         self.ctx = A.nys_setup(arr, self.B, opt, _stream_handle(stream))
         self.XS = A.nys_x_stride(self.ctx)
@@ -119,9 +121,15 @@ class Batch:
         return self.x, self.status
 
     def assembly_config(self):
-        """(kernel, rows per work item) of the assembly; runs the tuner if pending."""
+        """(kernel, rows per work item) of the assembly; runs the tuner if pending.
+        kernel: "auto" (band units on the CUDA cores, the rest on the tensor
+        cores), "tensor-core" or "simt"."""
         kernel, rows = A.nys_assembly_config(self.ctx, _stream_handle(self.stream))
-        return {A.NYS_ASM_AUTO: "tensor-core", A.NYS_ASM_SIMT: "simt"}[kernel], rows
+        return {A.NYS_ASM_AUTO: "auto", A.NYS_ASM_TC: "tensor-core", A.NYS_ASM_SIMT: "simt"}[kernel], rows
+
+    def assembly_items(self):
+        """(band units, other work items) of the assembly work list in use."""
+        return A.nys_assembly_items(self.ctx)
 
     def m_eff(self):
         out = (C.c_int32 * self.B)()

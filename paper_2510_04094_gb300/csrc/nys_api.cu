@@ -27,7 +27,7 @@ cudaError_t launch_assemble(bool fp32, const Inst* insts, const Lset* lsets, con
                             const int32_t* lm, const double* tab, double* part,
                             const int64_t* slot_off, int m_max, int k_max, int num_sms,
                             cudaStream_t st, int asm_kind, int32_t* err,
-                            BigSet big = BigSet(), int tc_wait = -1);
+                            BigSet big = BigSet(), int tc_wait = -1, int nband = 0);
 cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const double* W,
                          const float* W32, const double* part, const int64_t* slot_off,
                          const int32_t* lm, void* fac, int64_t facs, double* xs, double* zs,
@@ -161,6 +161,10 @@ struct nys_ctx {
   int64_t asm_rows = 0;           // rows per item of the assembly work list in use
   int tc_wait = -1;               // polls per bounded wait of the tensor-core kernel (-1: default)
   int asm_slots = 0;              // assembly slot region (capacity) in slot_off / part
+  int64_t asm_elems = 0;          // its doubles in part
+  int nband = 0;                  // leading items of the work list for the band kernel
+  std::vector<int> band_w;        // band plan per instance: window rows (0: tensor cores), unit
+  std::vector<int> band_u;        // rows (the layout uses it unless the slot region is too small)
   bool tune_pending = false;      // NYS_ASM_TUNE: choose kernel and item size at first use
   std::vector<int> eig_bounds;    // landmark-count classes of the setup launches
   int k_max = 0;                  // largest lag-table length of the current sets
@@ -538,14 +542,67 @@ void nys_destroy(nys_ctx* c) {
   delete c;
 }
 
+// Most landmarks (sorted grid indices) within any len consecutive grid points.
+static int lm_span_count(const int32_t* idx, int m, int64_t len) {
+  int best = 0;
+  for (int a = 0, z = 0; a < m; ++a) {
+    if (z < a) z = a;
+    while (z < m && idx[z] <= idx[a] + len - 1) ++z;
+    best = std::max(best, z - a);
+  }
+  return best;
+}
+
+// Band plan of instance b for k_assemble_band (kind LIN): the longest window W
+// (256, 128, 64 or 32 rows) whose rows see at most kBandLm landmarks within the
+// band lag Kb, with its kappa table (2 (Kb + W - 1) + 1 lags and W zeros) in
+// kBandTabCap floats; then unit rows U, a multiple of W of at most
+// max(W, target) rows, whose landmarks + 2 fit kBandUnitCols.  W = 0: the
+// instance goes to the tensor-core kernel.
+static void band_plan(const nys_ctx* c, int b, int64_t target, int& W, int& U) {
+  W = U = 0;
+  const Inst& I = c->h_inst[b];
+  if (I.kind != NYS_COEF_LIN || I.m > kMMax) return;
+  const int32_t* idx = c->h_lm.data() + c->h_lm_off[b];
+  const int Kb = asm_band_lag(I.hs, I.n);
+  for (int w = 256; w >= 32; w /= 2) {
+    if (2LL * (Kb + w - 1) + 1 + w <= kBandTabCap && lm_span_count(idx, I.m, w + 2LL * Kb) <= kBandLm) {
+      W = w;
+      break;
+    }
+  }
+  if (W == 0) return;
+  const int64_t cap = std::max<int64_t>(W, std::min<int64_t>(target, 8192) / W * W);
+  U = W;
+  for (int64_t u = 2LL * W; u <= cap; u += W) {
+    if (lm_span_count(idx, I.m, u + 2LL * Kb) + 2 > kBandUnitCols) break;
+    U = (int)u;
+  }
+}
+
+// Band unit length aimed at: about 4 units per warp of the band kernel's
+// persistent grid (8 warps per SM).
+static int64_t band_target(const nys_ctx* c) {
+  return std::max<int64_t>(256, c->total_rows / (32LL * c->num_sms));
+}
+
 // Assembly work list: the rows of every instance in chunks of at most rpi rows,
 // sorted by cost (rows x (m+2)^2, longest first, for the persistent grid); slot
-// offsets into `part` from 0.  Sets the instances' assembly slot ranges.
-static int64_t asm_layout(nys_ctx* c, int64_t rpi, std::vector<Work>& wl, std::vector<int64_t>& soff) {
+// offsets into `part` from 0.  Sets the instances' assembly slot ranges.  With
+// `band`, instances with a band plan are cut into its units instead (window
+// rows in Work::e0) and listed first; *nband receives their count.
+static int64_t asm_layout(nys_ctx* c, int64_t rpi, std::vector<Work>& wl, std::vector<int64_t>& soff,
+                          bool band = false, int* nband = nullptr) {
   wl.clear();
   soff.clear();
   int64_t poff = 0;
   int slot = 0;
+  std::vector<Work> bl;
+  if (band) {
+    c->band_w.assign(c->batch, 0);
+    c->band_u.assign(c->batch, 0);
+  }
+  const int64_t target = band_target(c);
   for (int b = 0; b < c->batch; ++b) {
     const int nrows = collocation_rows(c->shape[b]);
     const int M2 = c->shape[b].m + 2;
@@ -555,8 +612,16 @@ static int64_t asm_layout(nys_ctx* c, int64_t rpi, std::vector<Work>& wl, std::v
     const bool bigm = c->shape[b].m > kMMax;
     const int64_t Elin = (int64_t)M2 * (M2 + 1) / 2;
     const int parts = bigm ? (int)((Elin + kAsm64Span - 1) / kAsm64Span) : 1;
-    const int64_t rpb = bigm ? std::max<int64_t>(rpi, 512) : rpi;
+    int bw = 0, bu = 0;
+    if (band) {
+      band_plan(c, b, target, bw, bu);
+      c->band_w[b] = bw;
+      c->band_u[b] = bu;
+    }
+    const int64_t rpb = bw ? bu : (bigm ? std::max<int64_t>(rpi, 512) : rpi);
     const int chunks = (int)std::max<int64_t>(1, (nrows + rpb - 1) / rpb);
+    // band units: equal shares rounded up to whole windows
+    const int64_t ubw = bw ? ((nrows + chunks - 1) / chunks + bw - 1) / bw * bw : 0;
     // linear: [first landmark, count] + packed Gram over m + 2 columns;
     // Newton: packed Gram over m + 1 columns, two (m+1)-vectors, two scalars
     const int64_t E = std::max<int64_t>((int64_t)M2 * (M2 + 1) / 2 + 2,
@@ -567,12 +632,19 @@ static int64_t asm_layout(nys_ctx* c, int64_t rpi, std::vector<Work>& wl, std::v
       for (int pt = 0; pt < parts; ++pt) {
         Work w;
         w.inst = b;
-        w.r0 = 1 + (int)((int64_t)nrows * k / chunks);
-        w.r1 = 1 + (int)((int64_t)nrows * (k + 1) / chunks);
+        if (bw) {
+          w.r0 = 1 + (int)std::min<int64_t>(nrows, ubw * k);
+          w.r1 = 1 + (int)std::min<int64_t>(nrows, ubw * (k + 1));
+          w.e0 = bw;
+          w.e1 = 0;
+        } else {
+          w.r0 = 1 + (int)((int64_t)nrows * k / chunks);
+          w.r1 = 1 + (int)((int64_t)nrows * (k + 1) / chunks);
+          w.e0 = bigm ? (int)(Elin * pt / parts) : 0;
+          w.e1 = bigm ? (int)(Elin * (pt + 1) / parts) : INT32_MAX;
+        }
         w.slot = slot;
-        w.e0 = bigm ? (int)(Elin * pt / parts) : 0;
-        w.e1 = bigm ? (int)(Elin * (pt + 1) / parts) : INT32_MAX;
-        wl.push_back(w);
+        (bw ? bl : wl).push_back(w);
       }
       ++slot;
       soff.push_back(poff);
@@ -588,6 +660,11 @@ static int64_t asm_layout(nys_ctx* c, int64_t rpi, std::vector<Work>& wl, std::v
   std::stable_sort(wl.begin(), wl.end(), [&](const Work& a, const Work& b2) {
     return cost(a) > cost(b2);
   });
+  std::stable_sort(bl.begin(), bl.end(), [&](const Work& a, const Work& b2) {
+    return a.r1 - a.r0 > b2.r1 - b2.r0;
+  });
+  if (nband) *nband = (int)bl.size();
+  wl.insert(wl.begin(), bl.begin(), bl.end());
   return poff;
 }
 
@@ -605,7 +682,7 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
     return fail(NYS_EINVAL, "nys_setup: unknown precision %d", c->opt.precision);
   }
   if (c->opt.assembly != NYS_ASM_AUTO && c->opt.assembly != NYS_ASM_SIMT &&
-      c->opt.assembly != NYS_ASM_TUNE) {
+      c->opt.assembly != NYS_ASM_TUNE && c->opt.assembly != NYS_ASM_TC) {
     const int a = c->opt.assembly;
     delete c;
     return fail(NYS_EINVAL, "nys_setup: unknown assembly kernel %d", a);
@@ -690,21 +767,28 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   c->tc_rpi = asm_tc_unit_rows(total_rows, batch, c->num_sms);
   c->tune_pending = c->fp32 && c->opt.assembly == NYS_ASM_TUNE;
   if (c->opt.assembly == NYS_ASM_TUNE && !c->fp32) c->opt.assembly = NYS_ASM_AUTO;
-  const bool tc0 = c->fp32 && c->opt.assembly == NYS_ASM_AUTO;
-  // the assembly slot region holds the finest layout the tuner may pick (the
-  // CUDA-core kernel's 512-row items; the tensor-core units are never finer)
+  const bool hyb = c->fp32 && (c->opt.assembly == NYS_ASM_AUTO || c->tune_pending);
+  const bool tcu = hyb || (c->fp32 && c->opt.assembly == NYS_ASM_TC);
+  // the assembly slot region holds the largest layout this context may use:
+  // band units + tensor-core units (the layout in use, built last), the
+  // tensor-core units alone (used when a re-plan outgrows the region) and, with
+  // the tuner pending, the CUDA-core kernel's 512-row items
   std::vector<Work> wl;
   std::vector<int64_t> soff;
-  const int64_t first_rows = c->tune_pending ? std::min<int64_t>(rpi, 512) : (tc0 ? c->tc_rpi : rpi);
-  const int64_t asm_elems = asm_layout(c, first_rows, wl, soff);
-  const size_t asm_work_cap = wl.size();
-  c->asm_slots = (int)soff.size();
-  c->asm_rows = first_rows;
-  if (c->tune_pending) {
-    asm_layout(c, c->tc_rpi, wl, soff);
-    soff.resize((size_t)c->asm_slots, 0);
-    c->asm_rows = c->tc_rpi;
-  }
+  int64_t asm_elems = 0;
+  size_t asm_work_cap = 0, asm_slots = 0;
+  auto account = [&](int64_t el) {
+    asm_elems = std::max(asm_elems, el);
+    asm_work_cap = std::max(asm_work_cap, wl.size());
+    asm_slots = std::max(asm_slots, soff.size());
+  };
+  if (c->tune_pending) account(asm_layout(c, std::min<int64_t>(rpi, 512), wl, soff));
+  if (hyb) account(asm_layout(c, c->tc_rpi, wl, soff));
+  account(asm_layout(c, tcu ? c->tc_rpi : rpi, wl, soff, hyb, &c->nband));
+  soff.resize(asm_slots, 0);
+  c->asm_slots = (int)asm_slots;
+  c->asm_elems = asm_elems;
+  c->asm_rows = tcu ? c->tc_rpi : rpi;
   int64_t poff = asm_elems;
   int slot = c->asm_slots;
   // refinement work list: balance rule only (its per-item setup, a lag table
@@ -789,7 +873,7 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   if (c->any_lin && !c->fp32) A(c->adj.alloc((size_t)batch * grad_adj_stride(c->ZS)));
   A(c->st.alloc(batch));
   A(c->stinit.alloc(batch));
-  A(c->counter.alloc(1));
+  A(c->counter.alloc(2));
   A(c->err.alloc(1));
   if (c->any_nl) {
     A(c->yaux.alloc((size_t)ytot));
@@ -831,11 +915,35 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   return NYS_OK;
 }
 
+static int32_t set_asm_layout(nys_ctx* c, int64_t rpi, cudaStream_t s, bool band);
+
+// After a sigma change: rebuild the assembly work list if an instance's band
+// plan changed (captured graphs hold the old list's length).
+static int32_t replan_band(nys_ctx* c, cudaStream_t s) {
+  if (!c->fp32 || c->opt.assembly != NYS_ASM_AUTO || c->tune_pending) return NYS_OK;
+  bool same = ((int)c->band_w.size() == c->batch);
+  const int64_t target = band_target(c);
+  for (int b = 0; b < c->batch && same; ++b) {
+    int w = 0, u = 0;
+    band_plan(c, b, target, w, u);
+    same = (w == c->band_w[b] && u == c->band_u[b]);
+  }
+  if (same) return NYS_OK;
+  CK(cudaDeviceSynchronize());
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+  return set_asm_layout(c, c->tc_rpi, s, true);
+}
+
 int32_t nys_update(nys_ctx* c, const nys_instance* q, void* stream) {
   if (!c || !q) return fail(NYS_EINVAL, "nys_update: NULL argument");
   bool same_sets = false;
   int32_t r = pack(c, q, false, &same_sets);
   if (r != NYS_OK) return r;
+  if (!same_sets) {
+    r = replan_band(c, (cudaStream_t)stream);
+    if (r != NYS_OK) return r;
+  }
   // same landmark sets: the device descriptors (and the factor's m_eff, omode)
   // stay valid; otherwise new ones, factored before the next row pass
   return upload_and_setup(c, (cudaStream_t)stream, !same_sets, !same_sets);
@@ -844,24 +952,35 @@ int32_t nys_update(nys_ctx* c, const nys_instance* q, void* stream) {
 // ---- assembly autotuner ------------------------------------------------------
 // Rebuild the assembly work list for chunks of rpi rows (within the slot region
 // sized at setup) and upload it with the instances' slot ranges.
-static int32_t set_asm_layout(nys_ctx* c, int64_t rpi, cudaStream_t s) {
+static int32_t set_asm_layout(nys_ctx* c, int64_t rpi, cudaStream_t s, bool band) {
   std::vector<Work> wl;
   std::vector<int64_t> soff;
-  asm_layout(c, rpi, wl, soff);
-  if ((int)soff.size() > c->asm_slots) return fail(NYS_ESTATE, "assembly layout exceeds its slot region");
+  int nb = 0;
+  int64_t el = asm_layout(c, rpi, wl, soff, band, &nb);
+  if (band && ((int)soff.size() > c->asm_slots || el > c->asm_elems)) {
+    // tensor-core units only (sized into the region at setup); band_w / band_u
+    // keep the plan, so an unchanged plan is not laid out again
+    const std::vector<int> w0 = c->band_w, u0 = c->band_u;
+    el = asm_layout(c, rpi, wl, soff, false, &nb);
+    c->band_w = w0;
+    c->band_u = u0;
+  }
+  if ((int)soff.size() > c->asm_slots || el > c->asm_elems)
+    return fail(NYS_ESTATE, "assembly layout exceeds its slot region");
   CK(cudaStreamSynchronize(s));
   CK(cudaMemcpy(c->work.p, wl.data(), sizeof(Work) * wl.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c->slot_off.p, soff.data(), sizeof(int64_t) * soff.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c->inst.p, c->h_inst.data(), sizeof(Inst) * c->batch, cudaMemcpyHostToDevice));
   c->nwork = (int)wl.size();
+  c->nband = nb;
   c->asm_rows = rpi;
   return NYS_OK;
 }
 
-// Time every (kernel, rows per item) candidate on this batch -- the tensor-core
-// kernel on its long work units, the CUDA-core kernel with 512- and 1024-row
-// items -- one warm-up and three timed launches each; keep the fastest.  Runs
-// once, outside any graph.
+// Time every (kernel, rows per item) candidate on this batch -- band units plus
+// tensor-core units, tensor-core units alone, the older CUDA-core kernel with
+// 512- and 1024-row items -- one warm-up and three timed launches each; keep
+// the fastest.  Runs once, outside any graph.
 static int32_t tune_assembly(nys_ctx* c, cudaStream_t s) {
   c->tune_pending = false;
   if (c->factor_stale) {
@@ -873,23 +992,25 @@ static int32_t tune_assembly(nys_ctx* c, cudaStream_t s) {
     c->join_pending = false;
   }
   struct Cand { int kind; int64_t rows; };
-  const Cand cand[3] = {{NYS_ASM_AUTO, c->tc_rpi}, {NYS_ASM_SIMT, std::min<int64_t>(c->rpi, 512)},
-                        {NYS_ASM_SIMT, c->rpi}};
+  // NYS_ASM_AUTO: band units (CUDA cores) where the plan allows, tensor-core units elsewhere
+  const Cand cand[4] = {{NYS_ASM_AUTO, c->tc_rpi}, {NYS_ASM_TC, c->tc_rpi},
+                        {NYS_ASM_SIMT, std::min<int64_t>(c->rpi, 512)}, {NYS_ASM_SIMT, c->rpi}};
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
   int best_k = 0;
-  for (int k = 0; k < 3; ++k) {
-    if (k == 2 && cand[2].rows == cand[1].rows) continue;
-    int32_t r = set_asm_layout(c, cand[k].rows, s);
+  for (int k = 0; k < 4; ++k) {
+    if (k == 3 && cand[3].rows == cand[2].rows) continue;
+    if (k == 1 && c->nband == 0) continue;   // no band units: the same as candidate 0
+    int32_t r = set_asm_layout(c, cand[k].rows, s, cand[k].kind == NYS_ASM_AUTO);
     if (r != NYS_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return r; }
     float tot = 0.f;
     for (int rep = 0; rep < 4; ++rep) {
       CK(cudaEventRecord(e0, s));
       CK(launch_assemble(c->fp32, c->inst.p, c->lset.p, c->lag.p, c->W.p, c->work.p, c->nwork,
                          c->counter.p, c->lm.p, c->tab.p, c->part.p, c->slot_off.p, c->m_max,
-                         c->k_max, c->num_sms, s, cand[k].kind, c->err.p, c->bigset(), c->tc_wait));
+                         c->k_max, c->num_sms, s, cand[k].kind, c->err.p, c->bigset(), c->tc_wait, c->nband));
       CK(cudaEventRecord(e1, s));
       CK(cudaEventSynchronize(e1));
       float ms = 0.f;
@@ -901,7 +1022,7 @@ static int32_t tune_assembly(nys_ctx* c, cudaStream_t s) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   c->opt.assembly = cand[best_k].kind;
-  return set_asm_layout(c, cand[best_k].rows, s);
+  return set_asm_layout(c, cand[best_k].rows, s, cand[best_k].kind == NYS_ASM_AUTO);
 }
 
 int32_t nys_assembly_config(nys_ctx* c, void* stream, int32_t* kernel_out, int32_t* rows_out) {
@@ -912,6 +1033,14 @@ int32_t nys_assembly_config(nys_ctx* c, void* stream, int32_t* kernel_out, int32
   }
   if (kernel_out) *kernel_out = c->opt.assembly;
   if (rows_out) *rows_out = (int32_t)c->asm_rows;
+  return NYS_OK;
+}
+
+int32_t nys_assembly_items(const nys_ctx* c, int32_t* band_items, int32_t* other_items) {
+  if (!c || !band_items || !other_items) return fail(NYS_EINVAL, "nys_assembly_items: NULL argument");
+  const bool band = c->fp32 && c->opt.assembly == NYS_ASM_AUTO;
+  *band_items = band ? c->nband : 0;
+  *other_items = c->nwork - *band_items;
   return NYS_OK;
 }
 
@@ -930,7 +1059,7 @@ int32_t nys_assemble(nys_ctx* c, void* stream) {
   CK(launch_assemble(c->fp32, c->inst.p, c->lset.p, c->lag.p, c->W.p, c->work.p,
                      c->nwork, c->counter.p, c->lm.p, c->tab.p, c->part.p, c->slot_off.p, c->m_max,
                      c->k_max, c->num_sms, (cudaStream_t)stream, c->opt.assembly, c->err.p,
-                     c->bigset(), c->tc_wait));
+                     c->bigset(), c->tc_wait, c->nband));
   c->assembled = true;
   return NYS_OK;
 }
@@ -992,7 +1121,7 @@ int32_t nys_run(nys_ctx* c, void* stream, double* x_out, int32_t* status_out) {
         e2 = launch_assemble(c->fp32, c->inst.p, c->lset.p, c->lag.p, c->W.p,
                              c->work.p, c->nwork, c->counter.p, c->lm.p, c->tab.p, c->part.p,
                              c->slot_off.p, c->m_max, c->k_max, c->num_sms, cs, c->opt.assembly,
-                             c->err.p, c->bigset(), c->tc_wait);
+                             c->err.p, c->bigset(), c->tc_wait, c->nband);
       if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(cs, c->ev_join, 0);
       if (e2 != cudaSuccess) r = fail(NYS_ECUDA, "capture: assemble: %s", cudaGetErrorString(e2));
       if (r == NYS_OK) r = solve_impl(c, cs, x_out, status_out);

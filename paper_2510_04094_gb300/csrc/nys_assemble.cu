@@ -349,6 +349,10 @@ cudaError_t launch_assemble_tc(const Inst* insts, const Lset* lsets, const float
                                const Work* work, int nwork, int* counter, const int32_t* lm,
                                const double* tab, double* part, const int64_t* slot_off,
                                int32_t* err, int num_sms, int wait_iter, cudaStream_t st);
+cudaError_t launch_assemble_band(const Inst* insts, const Lset* lsets, const float* lag,
+                                 const Work* work, int nwork, int* counter, const int32_t* lm,
+                                 double* part, const int64_t* slot_off, int32_t* err, int num_sms,
+                                 cudaStream_t st);
 
 // Sum of the row-chunk partial Grams of each listed instance (Grams of more than
 // kMMax + 2 columns), into its first slot: a thread per packed entry, the slots
@@ -387,16 +391,26 @@ cudaError_t launch_assemble(bool fp32, const Inst* insts, const Lset* lsets, con
                             const int32_t* lm, const double* tab, double* part,
                             const int64_t* slot_off, int m_max, int k_max, int num_sms,
                             cudaStream_t st, int asm_kind, int32_t* err, BigSet big,
-                            int tc_wait) {
-  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+                            int tc_wait, int nband) {
+  // counter[0]: queue of the tensor-core / CUDA-core / FP64 kernel; counter[1]:
+  // queue of the band kernel (the first nband work items)
+  const bool band = fp32 && asm_kind == NYS_ASM_AUTO && err != nullptr && nband > 0;
+  cudaError_t e = cudaMemsetAsync(counter, 0, (band ? 2 : 1) * sizeof(int), st);
   if (e != cudaSuccess) return e;
-  if (err != nullptr) {  // error word read by the solve (NYS_ETIMEOUT)
+  if (err != nullptr) {  // error word read by the solve (NYS_ETIMEOUT / NYS_ESTATE)
     e = cudaMemsetAsync(err, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
   }
-  if (fp32 && asm_kind == NYS_ASM_AUTO && err != nullptr) {  // tensor-core Gram
-    return launch_assemble_tc(insts, lsets, lag, work, nwork, counter, lm, tab, part, slot_off, err,
-                              num_sms, tc_wait < 0 ? (1 << 22) : tc_wait, st);
+  if (fp32 && (asm_kind == NYS_ASM_AUTO || asm_kind == NYS_ASM_TC) && err != nullptr) {
+    // band units on the CUDA cores, the rest on the tensor cores
+    if (band) {
+      e = launch_assemble_band(insts, lsets, lag, work, nband, counter + 1, lm, part, slot_off, err,
+                               num_sms, st);
+      if (e != cudaSuccess || nband >= nwork) return e;
+    }
+    return launch_assemble_tc(insts, lsets, lag, work + (band ? nband : 0), nwork - (band ? nband : 0),
+                              counter, lm, tab, part, slot_off, err, num_sms,
+                              tc_wait < 0 ? (1 << 22) : tc_wait, st);
   }
   // k_cap: capacity of the shared-memory kappa table, fixed at launch (an update
   // that lengthens the lag tables makes those instances use computed features)

@@ -18,7 +18,7 @@
 // kTcMmaSteps MMA steps before the epilogue moves it into FP64.  This Gram only
 // feeds the FP32 factor that the FP64-accurate refinement then corrects, so a
 // window keeps the landmarks with exp(-u) >= e^-24 for one of its rows
-// (u = ((t_i - s_j)/sigma)^2 <= kTcBandU): the dropped values are below 2^-34
+// (u = ((t_i - s_j)/sigma)^2 <= kAsmBandU): the dropped values are below 2^-34
 // of the kernel's peak, under the FP32 accumulation's own rounding.  The
 // residual passes keep the FP64 band (u <= 80).
 //
@@ -93,7 +93,6 @@ constexpr int kTcLmCap = 128;            // landmark indices per sub-chunk buffe
 constexpr int kTcTabCap = 4096;          // kappa(lag) table entries (hi, lo)
 constexpr uint32_t kTcSetCols = 128;
 constexpr uint32_t kTcCols = kTcSub * kTcSetCols;   // the whole tensor memory of the SM
-constexpr double kTcBandU = 24.0;
 constexpr int kTcMmaSteps = 8;           // MMA steps per accumulator entry, at most
 constexpr int kTcDrainIter = 1 << 22;    // final wait for the MMAs in flight
 static_assert(kTcUnitsPerStage % kTcProducers == 0 && kTcProducers == 8,
@@ -189,26 +188,6 @@ __device__ __forceinline__ void acc_comp(float2* p, float x) {
 
 __device__ __forceinline__ int slot_block(int M2) {
   return (M2 <= 16) ? 16 : (M2 <= 32 ? 32 : (M2 <= 64 ? 64 : 128));
-}
-
-// sin and cos of theta_i = th0 + i dth (LIN right-hand side), argument in
-// float-float and reduced mod 2 pi as in lin_rhs_ff
-__device__ __forceinline__ void lin_sincos(const RowConst& K, int i, float& s, float& c) {
-  const float k2PiHi = 6.28318548202514648f;
-  const float k2PiLo = -1.74845553e-07f;
-  const float fi = (float)i;
-  const float p = fi * K.dth.hi;
-  float pe = fmaf(fi, K.dth.hi, -p);
-  pe = fmaf(fi, K.dth.lo, pe);
-  const ff th = ff_add(K.th0, ff{p, pe});
-  const float k = rintf(th.hi * 0.159154943091895336f);
-  const float a = fmaf(-k, k2PiHi, th.hi);
-  const float b = fmaf(-k, k2PiLo, th.lo);
-  const ff r = ff_two_sum(a, b);
-  float sn, cs;
-  sincosf(r.hi, &sn, &cs);
-  s = fmaf(cs, r.lo, sn);
-  c = fmaf(-sn, r.lo, cs);
 }
 
 // Operand offsets of unit k of producer warp `warp`: the row t0 of the stage,
@@ -452,8 +431,8 @@ k_assemble_tc(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         row = ur0 = wk.r0;
         r1 = wk.r1;
         uslot = slot_off[wk.slot];
-        // band of the sub-chunk windows: u = (k h / sigma)^2 <= kTcBandU
-        Kb = (int)fmin(ceil(sqrt(kTcBandU) / I.hs), (double)I.n);
+        // band of the sub-chunk windows: u = (k h / sigma)^2 <= kAsmBandU
+        Kb = asm_band_lag(I.hs, I.n);
         Kt = Kb + kTcSubRows - 1;
         mode = (I.kind == NYS_COEF_LIN) ? ((2 * Kt + 1 <= kTcTabCap && lag != nullptr) ? 0 : 1) : 2;
         if (I.kind == NYS_COEF_LIN) {

@@ -65,6 +65,19 @@ struct Lset {
   int64_t lag_off;     // lag tables (floats): 6 per lag k = 0..K, see k_setup_lag
   double hs;           // h / sigma
 };
+// Band of the FP32 assembly Grams: a window keeps the landmarks with
+// ((t_i - s_j)/sigma)^2 <= kAsmBandU for one of its rows (exp(-24) < 2^-34).
+constexpr double kAsmBandU = 24.0;
+__host__ __device__ __forceinline__ int asm_band_lag(double hs, int n) {
+  return (int)fmin(ceil(sqrt(kAsmBandU) / hs), (double)n);
+}
+// CUDA-core band assembly (k_assemble_band): landmark columns per window, kappa
+// table capacity per warp (floats: 2 (Kb + W - 1) + 1 lags and W zeros), unit
+// Gram columns (unit landmarks + 2).
+constexpr int kBandLm = 14;
+constexpr int kBandTabCap = 4096;
+constexpr int kBandUnitCols = 48;
+
 // Largest lag whose kernel value is kept: (K hs)^2 <= kLagU.
 constexpr double kLagU = 80.0;
 constexpr double kOmegaCond = 1e-7;
@@ -305,6 +318,26 @@ __device__ __forceinline__ float lin_rhs_ff(const RowConst& K, int i) {
   float s, cth;
   sincosf(r.hi, &s, &cth);
   return K.c * fmaf(cth, r.lo, s);
+}
+
+// sin and cos of theta_i = th0 + i dth (LIN right-hand side), argument in
+// float-float and reduced mod 2 pi as in lin_rhs_ff
+__device__ __forceinline__ void lin_sincos(const RowConst& K, int i, float& s, float& c) {
+  const float k2PiHi = 6.28318548202514648f;
+  const float k2PiLo = -1.74845553e-07f;
+  const float fi = (float)i;
+  const float p = fi * K.dth.hi;
+  float pe = fmaf(fi, K.dth.hi, -p);
+  pe = fmaf(fi, K.dth.lo, pe);
+  const ff th = ff_add(K.th0, ff{p, pe});
+  const float k = rintf(th.hi * 0.159154943091895336f);
+  const float a = fmaf(-k, k2PiHi, th.hi);
+  const float b = fmaf(-k, k2PiLo, th.lo);
+  const ff r = ff_two_sum(a, b);
+  float sn, cs;
+  sincosf(r.hi, &sn, &cs);
+  s = fmaf(cs, r.lo, sn);
+  c = fmaf(-sn, r.lo, cs);
 }
 
 // Operator coefficients of row i in float-float (TABLE kind reads the FP64

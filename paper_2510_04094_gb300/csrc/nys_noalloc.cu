@@ -31,7 +31,7 @@ cudaError_t launch_assemble(bool fp32, const Inst* insts, const Lset* lsets, con
                             const int32_t* lm, const double* tab, double* part,
                             const int64_t* slot_off, int m_max, int k_max, int num_sms,
                             cudaStream_t st, int asm_kind, int32_t* err,
-                            BigSet big = BigSet(), int tc_wait = -1);
+                            BigSet big = BigSet(), int tc_wait = -1, int nband = 0);
 cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const double* W,
                          const float* W32, const double* part, const int64_t* slot_off,
                          const int32_t* lm, void* fac, int64_t facs, double* xs, double* zs,

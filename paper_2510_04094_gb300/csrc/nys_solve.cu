@@ -56,6 +56,7 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   // more conditions than unknowns (m_eff + 1 < p after truncation): no solution
   const int st0 = (st_init[b] != NYS_OK) ? st_init[b]
                   : (om && sizeof(T) == sizeof(float)) ? NYS_EPRECISION
+                  : (asm_err != nullptr && *asm_err == 2) ? NYS_ESTATE   // stale band plan
                   : (asm_err != nullptr && *asm_err != 0) ? NYS_ETIMEOUT
                   : (LS.m_eff + 1 < I.p) ? NYS_ENOTSPD : NYS_OK;
   if (st0 != NYS_OK) {  // no solution: zero x and z, report the status

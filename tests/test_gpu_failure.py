@@ -1,6 +1,7 @@
 """Failure paths of the device code, exercised without a GPU fault.
 
-The tensor-core assembly bounds every mbarrier wait (nys_set_wait_limit).  With
+The tensor-core assembly (NYS_ASM_TC here, so that every instance runs on it)
+bounds every mbarrier wait (nys_set_wait_limit).  With
 the limit at 0 every wait gives up at once: the kernel records its error word,
 drains, frees its tensor memory and returns, the solve reports NYS_ETIMEOUT for
 every instance, and the same context then solves normally once the default limit
@@ -45,7 +46,7 @@ def test_expired_waits_report_timeout_and_context_recovers(api):
     import torch
     from paper_2510_04094_gb300 import _abi as A
     probs = ni.m0(6, n=2000, m=30) + ni.small_linear(4, sub=5)
-    bt = api.Batch(probs, precision="mixed")
+    bt = api.Batch(probs, precision="mixed", assembly="tc")
     A.nys_set_wait_limit(bt.ctx, 0)
     for step in (lambda: (bt.assemble(), bt.solve())[1], bt.run):
         st = step()[1]

@@ -25,9 +25,11 @@ def api():
 
 
 def _check(api, probs, precision, tol=None, refine=-1):
-    """precision: "fp64", "mixed" (tensor-core Gram) or "mixed-simt" (CUDA-core Gram)."""
+    """precision: "fp64", "mixed" (band units on the CUDA cores where the plan
+    allows, the tensor cores elsewhere), "mixed-tc" (tensor cores only) or
+    "mixed-simt" (the 8x8-block CUDA-core Gram)."""
     import torch
-    assembly = "simt" if precision.endswith("-simt") else "auto"
+    assembly = {"simt": "simt", "tc": "tc"}[precision.split("-")[1]] if "-" in precision else "auto"
     precision = precision.split("-")[0]
     tol = TOL[precision] if tol is None else tol
     bt = api.Batch(probs, precision=precision, refine_steps=refine, assembly=assembly)
@@ -109,21 +111,26 @@ def _sampled(api, probs, bt, pick, tol):
     return worst
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("precision", ["mixed", "mixed-tc", "fp64"])
 def test_metric_batch_full_size_sampled(api, precision):
     """The throughput workload itself, 4096 instances at n = 1e4, m = 50, in the
     launch configuration bench.py times (one nys_run graph; mixed: the default
-    single refinement pass), so that every CTA takes many work items and the
-    tensor-core kernel cycles through its accumulator sets; instances sampled
-    across the cost-sorted work list against the oracle."""
+    single refinement pass), so that every warp of the band kernel takes many
+    units (mixed), or the tensor-core kernel cycles through its accumulator sets
+    (mixed-tc); instances sampled across the cost-sorted work list against the
+    oracle."""
     import torch
     probs = ni.m0(4096)
-    bt = api.Batch(probs, precision=precision)
+    prec, _, asm = precision.partition("-")
+    bt = api.Batch(probs, precision=prec, assembly=asm or "auto")
+    if precision == "mixed":      # every unit of this workload is a band unit
+        band, other = bt.assembly_items()
+        assert band > 0 and other == 0, (band, other)
     for _ in range(2):          # the graph is captured once, then replayed
         x, st = bt.run()
     torch.cuda.synchronize()
     assert (st.cpu().numpy() == 0).all()
-    _sampled(api, probs, bt, [0, 1, 777, 2048, 4095], TOL[precision])
+    _sampled(api, probs, bt, [0, 1, 777, 2048, 4095], TOL[prec])
     bt.close()
 
 
@@ -141,24 +148,24 @@ def _cap_m_batch():
     return out
 
 
-@pytest.mark.parametrize("precision", ["mixed", "mixed-simt", "fp64"])
+@pytest.mark.parametrize("precision", ["mixed", "mixed-tc", "mixed-simt", "fp64"])
 def test_landmark_cap_wide_windows(api, precision):
     _check(api, _cap_m_batch(), precision)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed-simt"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed-tc", "mixed-simt"])
 def test_cfg2_linear_full_size(api, precision):
     _check(api, [ni.cfg2_linear()], precision)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed-simt"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed-tc", "mixed-simt"])
 def test_ragged_batch_all_m_values(api, precision):
     """The ragged family (m in {20, 32, 50, 64, 100}, sigma = T/m), n capped for the oracle."""
     probs = [q for q in ni.cfg3(40, n_hi=4000)]
     _check(api, probs, precision)
 
 
-@pytest.mark.parametrize("precision", ["mixed", "mixed-simt"])
+@pytest.mark.parametrize("precision", ["mixed", "mixed-tc", "mixed-simt"])
 def test_ragged_family_default_refinement(api, precision):
     """The ragged batched family (n log-uniform in [500, 2e4], m in {20..100},
     sigma = T/m) meets the mixed-path bar with the default single refinement pass."""
@@ -172,6 +179,7 @@ def test_table_coefficients_match_parametric(api):
               r=q["c"] * np.sin(q["omega"] * t + q["phi0"]))
     _check(api, [tq], "fp64")
     _check(api, [tq], "mixed")
+    _check(api, [tq], "mixed-tc")
     _check(api, [tq], "mixed-simt")
 
 
@@ -336,14 +344,15 @@ def test_truncated_landmark_kernel_mixed_reports_eprecision(api):
 
 
 def test_autotuned_assembly_keeps_parity(api):
-    """NYS_ASM_TUNE times the tensor-core and CUDA-core Gram with 512- and 1024-row
-    items on the batch itself and keeps the fastest; the result still matches the
-    oracle, through the graph path too."""
+    """NYS_ASM_TUNE times band + tensor-core units, tensor-core units alone and
+    the CUDA-core Gram with 512- and 1024-row items on the batch itself and
+    keeps the fastest; the result still matches the oracle, through the graph
+    path too."""
     import torch
     probs = ni.m0(64, n=3000, m=30) + ni.small_linear(6)
     bt = api.Batch(probs, precision="mixed", assembly="tune")
     kernel, rows = bt.assembly_config()
-    assert kernel in ("tensor-core", "simt") and rows in (512, 1024) or rows >= 64
+    assert kernel in ("auto", "tensor-core", "simt") and rows in (512, 1024) or rows >= 64
     x, st = bt.run()
     grids = [core.grid(q) for q in probs]
     y, _ = bt.eval(grids)
@@ -357,4 +366,68 @@ def test_autotuned_assembly_keeps_parity(api):
         assert err <= TOL["mixed"], err
         off += len(g)
     assert bt.assembly_config() == (kernel, rows)   # chosen once
+    bt.close()
+
+
+# ---- the band kernel (NYS_ASM_AUTO's CUDA-core path for narrow windows) -------
+def _band_family():
+    """Instances chosen for the band plan's corners: landmark spacings from 10 to
+    200 grid steps, windows of 32, 64, 128 and 256 rows, row counts that leave a
+    partial last window, and two instances with sigma of 2 and 1.5 landmark
+    spacings, whose windows are too wide for the band kernel (tensor cores)."""
+    fam = ni.linear_family(8, n=2000, m=40, T=12.0, name="band", sub=17)
+    shapes = [(2000, 40, 1.0), (9999, 50, 1.0), (1001, 100, 1.0), (1200, 64, 1.0),
+              (257, 20, 1.0), (4097, 25, 1.0), (3333, 64, 2.0), (800, 20, 1.5)]
+    out = []
+    for q, (n, m, k) in zip(fam, shapes):
+        out.append(dict(q, n=n, m=m, sigma=k * (q["t1"] - q["t0"]) / m))
+    return out
+
+
+def test_band_kernel_corner_shapes(api):
+    probs = _band_family()
+    bt = api.Batch(probs, precision="mixed")
+    band, other = bt.assembly_items()
+    assert band > 0, (band, other)
+    bt.close()
+    _check(api, probs, "mixed")
+
+
+def test_band_and_tensor_core_split_batch(api):
+    """One batch whose instances go to both kernels (narrow and wide windows);
+    both write their units into the same slot layout."""
+    probs = _band_family()[:4] + _cap_m_batch()[:3]
+    bt = api.Batch(probs, precision="mixed")
+    band, other = bt.assembly_items()
+    assert band > 0 and other > 0, (band, other)
+    bt.close()
+    _check(api, probs, "mixed")
+
+
+def test_band_replan_after_sigma_update(api):
+    """nys_update with a wider sigma widens every window's band: the work list is
+    re-planned (fewer rows per window or tensor-core units), and the next solve
+    still meets the mixed-path bar -- through a re-captured nys_run graph too."""
+    import torch
+    probs = ni.m0(8, n=4000, m=50)
+    bt = api.Batch(probs, precision="mixed")
+    before = bt.assembly_items()
+    bt.run()
+    wide = [dict(q, sigma=1.6 * q["sigma"]) for q in probs]   # about 2 landmark spacings
+    bt.update(wide)
+    after = bt.assembly_items()
+    assert after != before, (before, after)
+    for step in (lambda: (bt.assemble(), bt.solve())[1], bt.run):
+        x, st = step()
+        torch.cuda.synchronize()
+        assert (st.cpu().numpy() == 0).all()
+        grids = [core.grid(q) for q in wide]
+        y, _ = bt.eval(grids)
+        yc = y.cpu().numpy()
+        off = 0
+        for q, g in zip(wide, grids):
+            ref = core.solve_linear(q)["y"]
+            err = np.abs(yc[off:off + len(g)] - ref).max() / np.abs(ref).max()
+            assert err <= TOL["mixed"], err
+            off += len(g)
     bt.close()
