@@ -21,8 +21,8 @@ LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libnys.so")
 PEAK_LIB_PATH = os.path.join(LIB_DIR, "libnys_peak.so")
 SOURCES = ["nys_setup.cu", "nys_assemble.cu", "nys_assemble_tc.cu", "nys_assemble_band.cu",
-           "nys_solve.cu", "nys_eval.cu", "nys_newton.cu", "nys_grad.cu", "nys_noalloc.cu",
-           "nys_api.cu"]
+           "nys_solve.cu", "nys_refine_band.cu", "nys_eval.cu", "nys_newton.cu", "nys_grad.cu",
+           "nys_noalloc.cu", "nys_api.cu"]
 PEAK_SOURCES = ["nys_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INC_DIR, "-I" + SRC_DIR]

@@ -17,11 +17,13 @@ namespace nys {
 cudaError_t launch_setup(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
                          double* lam, float* lag, double tau, int m_max, cudaStream_t st,
                          int allow_chol, const int* m_bounds, int nclass,
-                         BigSet big = BigSet());
+                         BigSet big = BigSet(), double* crow = nullptr,
+                         const Inst* insts = nullptr);
 cudaError_t launch_lag(const Lset* lsets, int capacity, float* lag, cudaStream_t st);
 cudaError_t launch_eig(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
                        double* lam, double tau, int m_max, cudaStream_t st, int allow_chol,
-                       const int* m_bounds, int nclass, BigSet big = BigSet());
+                       const int* m_bounds, int nclass, BigSet big = BigSet(), double* crow = nullptr,
+                         const Inst* insts = nullptr);
 cudaError_t launch_assemble(bool fp32, const Inst* insts, const Lset* lsets, const float* lag,
                             const double* W, const Work* work, int nwork, int* counter,
                             const int32_t* lm, const double* tab, double* part,
@@ -33,14 +35,14 @@ cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const 
                          const int32_t* lm, void* fac, int64_t facs, double* xs, double* zs,
                          double* cws, int XS, int ZS, int M1S, const int32_t* st_init,
                          int32_t* st, double gamma_scale, int batch, int m_max, cudaStream_t s,
-                         const int32_t* asm_err, BigSet big = BigSet());
+                         const int32_t* asm_err, BigSet big = BigSet(), const double* crow = nullptr);
 cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W, const float* lag,
                           const Work* work, int nwork, int* counter, const int32_t* lm,
                           const double* tab,
                           double* part, const int64_t* slot_off, const void* fac, int64_t facs,
                           double* xs, double* zs, const double* cws, int XS, int ZS, int M1S,
                           int32_t* st, double gamma_scale, int batch, int m_max, int k_max,
-                          int num_sms, cudaStream_t s);
+                          int num_sms, cudaStream_t s, int nrband = 0);
 cudaError_t launch_eval(const Inst* insts, const double* zs, int ZS, const int32_t* lm,
                         const double* tq, const int64_t* tq_off, int deriv, double* yq, int batch,
                         cudaStream_t s);
@@ -119,6 +121,10 @@ struct DBuf {  // owning device buffer
     p = nullptr;
     n = 0;
   }
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { release(); }   // every buffer of a context goes with it
 };
 
 struct GraphKey {
@@ -163,6 +169,9 @@ struct nys_ctx {
   int asm_slots = 0;              // assembly slot region (capacity) in slot_off / part
   int64_t asm_elems = 0;          // its doubles in part
   int nband = 0;                  // leading items of the work list for the band kernel
+  std::vector<Work> h_rwork;      // refinement work list as built at setup (cost order)
+  std::vector<int> rband_w;       // refinement band plan per instance: window rows (0: k_refine_rows)
+  int nrband = 0;                 // leading items of the refinement list for k_refine_band
   std::vector<int> band_w;        // band plan per instance: window rows (0: tensor cores), unit
   std::vector<int> band_u;        // rows (the layout uses it unless the slot region is too small)
   bool tune_pending = false;      // NYS_ASM_TUNE: choose kernel and item size at first use
@@ -180,6 +189,7 @@ struct nys_ctx {
   DBuf<float> W32;
   DBuf<float> lag;
   DBuf<double> lam;
+  DBuf<double> crow;        // condition rows per landmark set (k_setup_crow): batch x 8 x m_max
   DBuf<unsigned char> fac;
   // instances with m > kMMax: ids and their global factor / solve workspace
   DBuf<int32_t> big_ids;
@@ -446,7 +456,8 @@ static int32_t repack_same_sets(nys_ctx* c, const nys_instance* q) {
 static cudaError_t enqueue_factor(nys_ctx* c, cudaStream_t s) {
   return launch_setup(c->lset.p, c->batch, c->lm.p, c->W.p, c->W32.p, c->lam.p, c->lag.p,
                       c->opt.eig_tau > 0 ? c->opt.eig_tau : 1e-12, c->m_max, s, c->fp32 ? 0 : 1,
-                      c->eig_bounds.data(), (int)c->eig_bounds.size(), c->bigset());
+                      c->eig_bounds.data(), (int)c->eig_bounds.size(), c->bigset(), c->crow.p,
+                      c->inst.p);
 }
 
 // The lag tables (read by the row passes) go on the caller's stream; the
@@ -459,7 +470,8 @@ static cudaError_t fork_factor(nys_ctx* c, cudaStream_t s) {
   if (e == cudaSuccess)
     e = launch_eig(c->lset.p, c->batch, c->lm.p, c->W.p, c->W32.p, c->lam.p,
                    c->opt.eig_tau > 0 ? c->opt.eig_tau : 1e-12, c->m_max, c->side,
-                   c->fp32 ? 0 : 1, c->eig_bounds.data(), (int)c->eig_bounds.size(), c->bigset());
+                   c->fp32 ? 0 : 1, c->eig_bounds.data(), (int)c->eig_bounds.size(), c->bigset(),
+                   c->crow.p, c->inst.p);
   if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
   return e;
 }
@@ -578,6 +590,48 @@ static void band_plan(const nys_ctx* c, int b, int64_t target, int& W, int& U) {
     if (lm_span_count(idx, I.m, u + 2LL * Kb) + 2 > kBandUnitCols) break;
     U = (int)u;
   }
+}
+
+// Refinement band plan of instance b for k_refine_band (mixed path, kind LIN):
+// a window W (512 down to 32 rows) whose rows see at most kRbLm landmarks within
+// its band lag K (u <= kRefBandU), with its float-float kappa table
+// (2 (K + W - 1) + 1 lags and W zeros) in kRbTabCap entries; 0: k_refine_rows.
+static int refine_band_plan(const nys_ctx* c, int b, int64_t unit_rows) {
+  const Inst& I = c->h_inst[b];
+  if (!c->fp32 || I.kind != NYS_COEF_LIN || I.m > kMMax) return 0;
+  const int K = std::min(refine_band_lag(I.hs, I.n), c->h_lset[b].K);
+  const int32_t* idx = c->h_lm.data() + c->h_lm_off[b];
+  // among the feasible windows, the one with the shortest unit time: its eight
+  // warps take ceil(windows / 8) windows each, a window costing W / 32 rows
+  // per lane plus its reduction (about one row's worth)
+  int best = 0;
+  double best_t = 0.0;
+  for (int w = kRbMaxW; w >= 32; w /= 2) {
+    if (2LL * (K + w - 1) + 1 + w > kRbTabCap || lm_span_count(idx, I.m, w + 2LL * K) > kRbLm)
+      continue;
+    const int64_t nwin = (std::max<int64_t>(1, unit_rows) + w - 1) / w;
+    const double t = (double)((nwin + 7) / 8) * (w / 32 + 1);
+    if (best == 0 || t < best_t) { best = w; best_t = t; }
+  }
+  return best;
+}
+
+// Refinement work list in use: the setup's list with the items of planned
+// instances first (window rows in Work::e0).  Returns whether the plan changed.
+static bool refine_layout(nys_ctx* c, std::vector<Work>& out) {
+  std::vector<int> wr(c->batch);
+  std::vector<int64_t> urows(c->batch, 0);       // longest refinement item per instance
+  for (const Work& w : c->h_rwork) urows[w.inst] = std::max<int64_t>(urows[w.inst], w.r1 - w.r0);
+  for (int b = 0; b < c->batch; ++b) wr[b] = refine_band_plan(c, b, urows[b]);
+  const bool changed = (wr != c->rband_w);
+  c->rband_w = wr;
+  out.clear();
+  for (const Work& w : c->h_rwork)
+    if (wr[w.inst]) { Work x = w; x.e0 = wr[w.inst]; x.e1 = 0; out.push_back(x); }
+  c->nrband = (int)out.size();
+  for (const Work& w : c->h_rwork)
+    if (!wr[w.inst]) out.push_back(w);
+  return changed;
 }
 
 // Band unit length aimed at: about 4 units per warp of the band kernel's
@@ -821,6 +875,8 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
     return ca > cb;
   };
   std::stable_sort(rwl.begin(), rwl.end(), by_cost);
+  c->h_rwork = rwl;
+  refine_layout(c, rwl);
   c->nwork = (int)wl.size();
   c->nrwork = (int)rwl.size();
   c->XS = c->m_max + 3;
@@ -851,6 +907,7 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   A(c->W32.alloc((size_t)batch * c->m_max * c->m_max));
   if (c->fp32) A(c->lag.alloc((size_t)c->lag_floats));
   A(c->lam.alloc((size_t)batch * NYS_M_MAX));
+  A(c->crow.alloc((size_t)batch * 8 * c->m_max));
   A(c->fac.alloc((size_t)batch * c->facs * (c->any_nl ? sizeof(double) : es)));
   {
     std::vector<int32_t> ids;
@@ -917,10 +974,21 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
 
 static int32_t set_asm_layout(nys_ctx* c, int64_t rpi, cudaStream_t s, bool band);
 
-// After a sigma change: rebuild the assembly work list if an instance's band
-// plan changed (captured graphs hold the old list's length).
+// After a sigma change: rebuild the assembly and refinement work lists if an
+// instance's band plan changed (captured graphs hold the old lists' lengths).
 static int32_t replan_band(nys_ctx* c, cudaStream_t s) {
-  if (!c->fp32 || c->opt.assembly != NYS_ASM_AUTO || c->tune_pending) return NYS_OK;
+  if (!c->fp32) return NYS_OK;
+  {
+    // refinement list: same items, planned ones first
+    std::vector<Work> rwl;
+    if (refine_layout(c, rwl)) {
+      CK(cudaDeviceSynchronize());
+      for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+      c->graphs.clear();
+      CK(cudaMemcpy(c->rwork.p, rwl.data(), sizeof(Work) * rwl.size(), cudaMemcpyHostToDevice));
+    }
+  }
+  if (c->opt.assembly != NYS_ASM_AUTO || c->tune_pending) return NYS_OK;
   bool same = ((int)c->band_w.size() == c->batch);
   const int64_t target = band_target(c);
   for (int b = 0; b < c->batch && same; ++b) {
@@ -1069,13 +1137,13 @@ static int32_t solve_impl(nys_ctx* c, cudaStream_t s, double* x_out, int32_t* st
   CK(launch_solve(c->fp32, c->inst.p, c->lset.p, c->W.p, c->W32.p, c->part.p, c->slot_off.p,
                   c->lm.p, c->fac.p, c->facs, c->xs.p, c->zs.p, c->cws.p, c->XS, c->ZS, c->M1S,
                   c->stinit.p, c->st.p, gscale, c->batch, c->m_max, s,
-                  c->fp32 ? c->err.p : nullptr, c->bigset()));
+                  c->fp32 ? c->err.p : nullptr, c->bigset(), c->crow.p));
   if (c->fp32) {
     for (int k = 0; k < c->opt.refine_steps; ++k)
       CK(launch_refine(c->inst.p, c->lset.p, c->W.p, c->lag.p, c->rwork.p, c->nrwork, c->counter.p,
                        c->lm.p, c->tab.p, c->part.p, c->slot_off.p, c->fac.p, c->facs, c->xs.p, c->zs.p,
                        c->cws.p, c->XS, c->ZS, c->M1S, c->st.p, gscale, c->batch, c->m_max,
-                       c->k_max, c->num_sms, s));
+                       c->k_max, c->num_sms, s, c->nrband));
   }
   if (x_out)
     CK(cudaMemcpyAsync(x_out, c->xs.p, sizeof(double) * c->batch * c->XS, cudaMemcpyDeviceToDevice, s));

@@ -139,13 +139,59 @@ __device__ bool cta_cholesky(T* A, int ld, int n, int* flag) {
   return !bad;
 }
 
-// Solve L L^T y = b in place (b overwritten), L lower (n x n, ld).  One warp
-// runs both substitutions (warp barriers only); the block waits for it.
+// In-place lower Cholesky of A (n x n, ld) by the calling warp alone (warp
+// barriers only, for small n where block barriers would dominate): lane l
+// owns rows l, l + 32, ...; per column k every lane scales its entries of
+// column k, then subtracts L_ik L_jk from its rows' trailing entries (column k
+// is read by all lanes at the same j: broadcast).  Returns false on a
+// non-positive pivot (replaced by 1).
 template <typename T>
-__device__ void cta_chol_solve(const T* L, int ld, int n, T* b) {
+__device__ bool warp_cholesky(T* A, int ld, int n) {
+  const int lane = threadIdx.x & 31;
+  bool bad = false;
+  for (int k = 0; k < n; ++k) {
+    T d = A[k * ld + k];
+    if (!(d > T(0))) { bad = true; d = T(1); }
+    const T lkk = sqrt(d), inv = T(1) / lkk;
+    for (int i = k + 1 + lane; i < n; i += 32) A[i * ld + k] *= inv;
+    __syncwarp();
+    if (lane == 0) A[k * ld + k] = lkk;
+    for (int i = k + 1 + lane; i < n; i += 32) {
+      const T lik = A[i * ld + k];
+      T* ai = A + i * ld;
+      for (int j = k + 1; j <= i; ++j) ai[j] -= lik * A[j * ld + k];
+    }
+    __syncwarp();
+  }
+  return !bad;
+}
+
+// Cholesky by the whole block: one warp for n <= kWarpCholMax (warp barriers
+// only), else cta_cholesky.  Every thread gets the outcome.  Measured on the
+// metric batch (n = 49, seven solve CTAs per SM) the block version is faster,
+// so the warp version is off (kWarpCholMax = 0).
+constexpr int kWarpCholMax = 0;
+template <typename T>
+__device__ bool block_cholesky(T* A, int ld, int n, int* flag) {
+  if (n > kWarpCholMax) return cta_cholesky(A, ld, n, flag);
   __syncthreads();
   if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
+    const bool ok = warp_cholesky(A, ld, n);
+    if (threadIdx.x == 0) *flag = ok ? 0 : 1;
+  }
+  __syncthreads();
+  return *flag == 0;
+}
+
+// Solve L L^T y = b in place by the calling warp (L lower, n x n, ld).  FP32:
+// the reciprocals of the diagonal first (all lanes at once), then the two
+// substitutions with one multiply per step on the critical path.  FP64 divides
+// (the correctly rounded quotients keep the FP64 path's results unchanged on
+// ill-conditioned systems).
+template <typename T>
+__device__ void warp_chol_solve(const T* L, int ld, int n, T* b) {
+  const int lane = threadIdx.x & 31;
+  if (sizeof(T) == sizeof(double)) {
     for (int k = 0; k < n; ++k) {
       const T yk = b[k] / L[k * ld + k];
       __syncwarp();
@@ -160,7 +206,47 @@ __device__ void cta_chol_solve(const T* L, int ld, int n, T* b) {
       if (lane == 0) b[k] = yk;
       __syncwarp();
     }
+    return;
   }
+  T rd[4];   // reciprocal diagonal entries of rows lane + 32 r (n <= 128 kept here)
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = lane + 32 * r;
+    rd[r] = (i < n) ? T(1) / L[i * ld + i] : T(0);
+  }
+  auto rdiag = [&](int k) -> T {
+    if (n > 128) return T(1) / L[k * ld + k];
+    const int q = k >> 5;
+    T v = rd[0];
+    if (q == 1) v = rd[1];
+    if (q == 2) v = rd[2];
+    if (q == 3) v = rd[3];
+    return __shfl_sync(0xffffffffu, v, k & 31);
+  };
+  for (int k = 0; k < n; ++k) {
+    const T inv = rdiag(k);
+    const T yk = b[k] * inv;
+    __syncwarp();
+    for (int i = k + 1 + lane; i < n; i += 32) b[i] -= L[i * ld + k] * yk;
+    if (lane == 0) b[k] = yk;
+    __syncwarp();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const T inv = rdiag(k);
+    const T yk = b[k] * inv;
+    __syncwarp();
+    for (int i = lane; i < k; i += 32) b[i] -= L[k * ld + i] * yk;
+    if (lane == 0) b[k] = yk;
+    __syncwarp();
+  }
+}
+
+// Solve L L^T y = b in place (b overwritten), L lower (n x n, ld).  One warp
+// runs both substitutions (warp barriers only); the block waits for it.
+template <typename T>
+__device__ void cta_chol_solve(const T* L, int ld, int n, T* b) {
+  __syncthreads();
+  if (threadIdx.x < 32) warp_chol_solve(L, ld, n, b);
   __syncthreads();
 }
 

@@ -77,6 +77,18 @@ __host__ __device__ __forceinline__ int asm_band_lag(double hs, int n) {
 constexpr int kBandLm = 14;
 constexpr int kBandTabCap = 4096;
 constexpr int kBandUnitCols = 48;
+// Band refinement pass (k_refine_band): its residuals keep the landmarks with
+// u = ((t_i - s_j)/sigma)^2 <= kRefBandU of a row (exp(-40) < 2^-57, below
+// FP64's unit roundoff relative to the kernel's peak); landmark columns per
+// window, float-float kappa table capacity per CTA (2 (K + W - 1) + 1 lags and
+// W zeros), longest window.
+constexpr double kRefBandU = 40.0;
+__host__ __device__ __forceinline__ int refine_band_lag(double hs, int n) {
+  return (int)fmin(ceil(sqrt(kRefBandU) / hs), (double)(n - 1));
+}
+constexpr int kRbLm = 20;
+constexpr int kRbTabCap = 8192;
+constexpr int kRbMaxW = 512;
 
 // Largest lag whose kernel value is kept: (K hs)^2 <= kLagU.
 constexpr double kLagU = 80.0;

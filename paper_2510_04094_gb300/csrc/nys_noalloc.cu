@@ -25,7 +25,8 @@ namespace nys {
 cudaError_t launch_setup(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
                          double* lam, float* lag, double tau, int m_max, cudaStream_t st,
                          int allow_chol, const int* m_bounds, int nclass,
-                         BigSet big = BigSet());
+                         BigSet big = BigSet(), double* crow = nullptr,
+                         const Inst* insts = nullptr);
 cudaError_t launch_assemble(bool fp32, const Inst* insts, const Lset* lsets, const float* lag,
                             const double* W, const Work* work, int nwork, int* counter,
                             const int32_t* lm, const double* tab, double* part,
@@ -37,7 +38,7 @@ cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const 
                          const int32_t* lm, void* fac, int64_t facs, double* xs, double* zs,
                          double* cws, int XS, int ZS, int M1S, const int32_t* st_init,
                          int32_t* st, double gamma_scale, int batch, int m_max, cudaStream_t s,
-                         const int32_t* asm_err, BigSet big = BigSet());
+                         const int32_t* asm_err, BigSet big = BigSet(), const double* crow = nullptr);
 int64_t fac_elems(int m_max);
 int32_t set_last_error(int32_t code, const char* msg);  // nys_api.cu: feeds nys_last_error()
 }  // namespace nys

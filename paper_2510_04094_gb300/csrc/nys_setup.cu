@@ -476,10 +476,79 @@ static cudaError_t launch_eig_class(Lset* lsets, int capacity, const int32_t* lm
 
 size_t setup_ws_doubles() { return setup_smem_bytes(kMLarge) / sizeof(double) + 1; }
 
+static cudaError_t launch_eig_sets(Lset* lsets, int capacity, const int32_t* lm_idx, double* W,
+                                   float* W32, double* lam, double tau, int m_max, cudaStream_t st,
+                                   int allow_chol, const int* m_bounds, int nclass, BigSet big);
+
+// Condition rows of every active landmark set in omega coordinates (FP64), at
+// the kernel width sigma of the set's first instance (Lemma 1's C, Appendix A.4):
+//     E[e][d][k] = sum_j W_kj (-1/sigma)^d H_d(x_j) exp(-x_j^2),  x_j = (tau_e - idx_j) h/sigma,
+// tau_0 = 0 (t_1), tau_1 = n - 1 (t_n), d = 0..3 (physicists' Hermite H_d),
+// rows k < m_eff (zero from m_eff on), summed as the solve would (a warp per
+// row, lanes over j, then a butterfly), so that the solve of every instance with
+// this set and sigma reads them instead of forming its own.
+__global__ void __launch_bounds__(128)
+k_setup_crow(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
+             const int32_t* __restrict__ lm_idx, const double* __restrict__ W_all,
+             double* __restrict__ crow, int CS) {
+  const Lset L = lsets[blockIdx.x];
+  if (!L.active) return;
+  __shared__ double s_e[8][kMLarge];
+  const int m = L.m, me = L.m_eff;
+  const double sigma = insts[blockIdx.x].sigma;
+  for (int e = threadIdx.x; e < 8 * m; e += blockDim.x) {
+    const int q = e / m, j = e - q * m, end = q >> 2, d = q & 3;
+    const double x = (double)((end ? L.n - 1 : 0) - lm_idx[L.lm_off + j]) * L.hs;
+    const double x2 = x * x;
+    double H;
+    if (d == 0) H = 1.0;
+    else if (d == 1) H = 2.0 * x;
+    else if (d == 2) H = 4.0 * x2 - 2.0;
+    else H = (8.0 * x2 - 12.0) * x;
+    double sc = 1.0;
+    for (int r = 0; r < d; ++r) sc *= -1.0 / sigma;
+    s_e[q][j] = sc * H * exp(-x2);
+  }
+  __syncthreads();
+  const double* W = W_all + L.w_off;
+  double* E = crow + (int64_t)blockIdx.x * 8 * CS;
+  const int lane = threadIdx.x & 31;
+  for (int k = threadIdx.x >> 5; k < m; k += blockDim.x >> 5) {
+    double sr[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if (k < me) {
+      for (int j = lane; j < m; j += 32) {
+        const double w = W[(int64_t)k * m + j];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) sr[q] += w * s_e[q][j];
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        for (int o = 16; o > 0; o >>= 1) sr[q] += __shfl_xor_sync(0xffffffffu, sr[q], o);
+    }
+    if (lane < 8) {
+      double v = sr[0];
+#pragma unroll
+      for (int q = 1; q < 8; ++q) if (lane == q) v = sr[q];
+      E[lane * CS + k] = v;
+    }
+  }
+}
+
 cudaError_t launch_eig(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
                        double* lam, double tau, int m_max, cudaStream_t st, int allow_chol,
-                       const int* m_bounds, int nclass, BigSet big) {
+                       const int* m_bounds, int nclass, BigSet big, double* crow,
+                       const Inst* insts) {
   if (capacity == 0) return cudaSuccess;
+  cudaError_t ec = launch_eig_sets(lsets, capacity, lm_idx, W, W32, lam, tau, m_max, st, allow_chol,
+                                   m_bounds, nclass, big);
+  if (ec != cudaSuccess || crow == nullptr || insts == nullptr) return ec;
+  k_setup_crow<<<capacity, 128, 0, st>>>(insts, lsets, lm_idx, W, crow, m_max);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_eig_sets(Lset* lsets, int capacity, const int32_t* lm_idx, double* W,
+                                   float* W32, double* lam, double tau, int m_max, cudaStream_t st,
+                                   int allow_chol, const int* m_bounds, int nclass, BigSet big) {
   int lo = 0;
   for (int k = 0; k < (nclass > 0 ? nclass : 1) && lo < kMMax; ++k) {
     const int hi = std::min((nclass > 0) ? m_bounds[k] : m_max, kMMax);
@@ -508,11 +577,12 @@ cudaError_t launch_eig(Lset* lsets, int capacity, const int32_t* lm_idx, double*
 
 cudaError_t launch_setup(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
                          double* lam, float* lag, double tau, int m_max, cudaStream_t st,
-                         int allow_chol, const int* m_bounds, int nclass, BigSet big) {
+                         int allow_chol, const int* m_bounds, int nclass, BigSet big, double* crow,
+                         const Inst* insts) {
   cudaError_t e = launch_lag(lsets, capacity, lag, st);
   if (e != cudaSuccess) return e;
   return launch_eig(lsets, capacity, lm_idx, W, W32, lam, tau, m_max, st, allow_chol, m_bounds,
-                    nclass, big);
+                    nclass, big, crow, insts);
 }
 
 }  // namespace nys

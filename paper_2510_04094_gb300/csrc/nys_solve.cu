@@ -43,7 +43,7 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         T* __restrict__ fac_all, int64_t facs, double* __restrict__ xs, double* __restrict__ zs,
         double* __restrict__ cws, int XS, int ZS, int M1S, const int32_t* __restrict__ st_init,
         int32_t* __restrict__ st_all, double gamma_scale, const int32_t* __restrict__ asm_err,
-        BigSet big) {
+        BigSet big, const double* __restrict__ crow) {
   constexpr bool kBig = MM > kMMax;
   const int b = kBig ? big.ids[blockIdx.x] : blockIdx.x;
   const Inst I = insts[b];
@@ -207,10 +207,29 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   //    initial values (Lemma 1) tau_r = t_1, d_r = r; boundary values (Appendix A.4)
   //    t_1 then t_n, d_r = 0 for p = 2, and d_r = 0, 1 at each end for p = 4
   //    (Problem 16).  k^(d)(tau) = (-1/sigma)^d H_d(x) exp(-x^2), x = (tau - s_j)/sigma.
-  __shared__ double s_e[4][MM];
   const bool bvp = (I.bc == NYS_BC_BVP);
   const int hp = bvp ? p / 2 : p;                       // conditions at t_1
-  for (int e = threadIdx.x; e < p * m; e += blockDim.x) {
+  // the set's rows (k_setup_crow) when this instance has the set's sigma: the
+  // same numbers this block would form
+  const bool use_crow = (crow != nullptr) && (I.sigma == insts[I.lset].sigma);
+  if (use_crow) {
+    const double* E = crow + (int64_t)I.lset * 8 * (XS - 3);
+    for (int k = threadIdx.x; k < M1; k += blockDim.x) {
+      double sr[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        if (r < p) {
+          const int at_n = (r >= hp), d = at_n ? r - hp : r;
+          sr[r] = (k < me) ? E[(4 * at_n + d) * (XS - 3) + k] : (d == 0 ? 1.0 : 0.0);
+          s_c[r][k] = sr[r];
+        }
+      }
+      cws[(int64_t)b * 2 * M1S + k] = sr[0];
+      cws[(int64_t)b * 2 * M1S + M1S + k] = sr[1];
+    }
+  }
+  __shared__ double s_e[4][MM];
+  for (int e = threadIdx.x; e < (use_crow ? 0 : p * m); e += blockDim.x) {
     const int r = e / m, j = e - r * m;
     const int at_n = (r >= hp), d = at_n ? r - hp : r;
     const double x = (double)((at_n ? I.n - 1 : 0) - lm_idx[I.lm_off + j]) * I.hs;
@@ -225,7 +244,7 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     s_e[r][j] = sc * H * exp(-x2);
   }
   __syncthreads();
-  for (int k = warp; k < M1; k += nw) {   // a warp per row of W (coalesced)
+  for (int k = warp; k < (use_crow ? 0 : M1); k += nw) {   // a warp per row of W (coalesced)
     double sr[4] = {0.0, 0.0, 0.0, 0.0};
     if (k < me) {
       for (int j = lane; j < m; j += 32) {
@@ -315,7 +334,7 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   __syncthreads();
   // 8. Cholesky of H'_22 and solve (rows 0..p-1 of H' stay as they are)
   T* A22 = Hs + p * ldh + p;
-  const bool ok = cta_cholesky(A22, ldh, N2, &s_flag);
+  const bool ok = block_cholesky(A22, ldh, N2, &s_flag);
   cta_chol_solve(A22, ldh, N2, y + p);
   if (p <= 2) {
     for (int e = threadIdx.x; e < N2 * N2; e += blockDim.x) {
@@ -939,7 +958,7 @@ k_newton_step(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   // keep the first p rows of H' for lambda before the factorisation
   for (int e = threadIdx.x; e < p * M1; e += blockDim.x) Yb[e] = Hs[(e / M1) * ldh + (e % M1)];
   double* A22 = Hs + p * ldh + p;
-  const bool ok = cta_cholesky(A22, ldh, N2, &s_flag);
+  const bool ok = block_cholesky(A22, ldh, N2, &s_flag);
   if (!ok) {
     if (threadIdx.x == 0) {
       if (mode == 0) { active[b] = 2; atomicOr(&flags[1], 1); }
@@ -1022,7 +1041,7 @@ cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const 
                          void* fac, int64_t facs, double* xs, double* zs, double* cws, int XS,
                          int ZS, int M1S, const int32_t* st_init, int32_t* st, double gamma_scale,
                          int batch, int m_max, cudaStream_t s, const int32_t* asm_err,
-                         BigSet big) {
+                         BigSet big, const double* crow) {
   const size_t sm = solve_smem_bytes(fp32, m_max < kMMax ? m_max : kMMax);
   cudaError_t e;
   if (fp32) {
@@ -1032,7 +1051,7 @@ cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const 
     k_solve<float, kMMax><<<batch, kSolveThreads, sm, s>>>(insts, lsets, W, W32, part, slot_off, lm,
                                                             (float*)fac, facs, xs, zs, cws, XS, ZS,
                                                             M1S, st_init, st, gamma_scale, asm_err,
-                                                            BigSet());
+                                                            BigSet(), crow);
   } else {
     e = cudaFuncSetAttribute(k_solve<double, kMMax>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sm);
@@ -1040,24 +1059,37 @@ cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const 
     k_solve<double, kMMax><<<batch, kSolveThreads, sm, s>>>(insts, lsets, W, W, part, slot_off, lm,
                                                              (double*)fac, facs, xs, zs, cws, XS,
                                                              ZS, M1S, st_init, st, gamma_scale,
-                                                             asm_err, BigSet());
+                                                             asm_err, BigSet(), crow);
     if (big.n > 0 && (e = cudaGetLastError()) == cudaSuccess)
       k_solve<double, kMLarge><<<big.n, kSolveThreadsBig, 0, s>>>(
           insts, lsets, W, W, part, slot_off, lm, (double*)fac, facs, xs, zs, cws, XS, ZS, M1S,
-          st_init, st, gamma_scale, asm_err, big);
+          st_init, st, gamma_scale, asm_err, big, crow);
   }
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
+
+cudaError_t launch_refine_band(const Inst* insts, const Lset* lsets, const float* lag,
+                               const Work* work, int nwork, int* counter, const int32_t* lm,
+                               const double* zs, int ZS, double* part, const int64_t* slot_off,
+                               int32_t* st, int num_sms, cudaStream_t s);
 
 cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W, const float* lag,
                           const Work* work, int nwork, int* counter, const int32_t* lm,
                           const double* tab, double* part, const int64_t* slot_off,
                           const void* fac, int64_t facs, double* xs, double* zs, const double* cws,
                           int XS, int ZS, int M1S, int32_t* st, double gamma_scale, int batch,
-                          int m_max, int k_max, int num_sms, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+                          int m_max, int k_max, int num_sms, cudaStream_t s, int nrband) {
+  // the first nrband items: k_refine_band (queue counter[1]); the rest k_refine_rows
+  cudaError_t e = cudaMemsetAsync(counter, 0, (nrband > 0 ? 2 : 1) * sizeof(int), s);
   if (e != cudaSuccess) return e;
+  if (nrband > 0) {
+    e = launch_refine_band(insts, lsets, lag, work, nrband, counter + 1, lm, zs, ZS, part, slot_off,
+                           st, num_sms, s);
+    if (e != cudaSuccess) return e;
+    work += nrband;
+    nwork -= nrband;
+  }
   const int k_cap = k_max < kRefLagMax ? k_max : kRefLagMax;
   const size_t sm = refine_smem_bytes(k_cap);
   e = cudaFuncSetAttribute(k_refine_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -1066,10 +1098,12 @@ cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W,
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_refine_rows, kRefThreads, sm);
   const int grid = min(nwork, num_sms * max(1, per_sm));
-  k_refine_rows<<<grid, kRefThreads, sm, s>>>(insts, lsets, lag, work, nwork, counter, lm, tab, zs,
-                                               ZS, part, slot_off, st, k_cap);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (grid > 0) {
+    k_refine_rows<<<grid, kRefThreads, sm, s>>>(insts, lsets, lag, work, nwork, counter, lm, tab, zs,
+                                                 ZS, part, slot_off, st, k_cap);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   k_refine_update<float><<<batch, kSolveThreads, 0, s>>>(insts, lsets, W, part, slot_off,
                                                           (const float*)fac, facs, xs, zs, cws,
                                                           XS, ZS, M1S, st, gamma_scale);
