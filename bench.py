@@ -442,6 +442,19 @@ def side_measurements(args, probs, bt, value, ws, local, stream, flush, peaks_ou
             "flop_count": "4m per row (residual and its projection), FP64-accurate (float-float)",
             "achieved_tflops": ach, "frac_of_dfma": ach / dfma, "frac_of_ffma": ach / ffma}
 
+    # the precision split: the same batch with the FP64 H and Cholesky factor
+    if args.precision == "mixed":
+        bf = Batch(probs, precision="mixed-f64f")
+        msf = ev_ms(bf.run, 3, stream, flush)
+        _, stf = bf.run()
+        torch.cuda.synchronize()
+        ex["mixed_fp64_factor"] = {
+            "ms_per_step": msf, "solves_s": B / (msf * 1e-3),
+            "fp32_factor_ms_per_step": B / value * 1e3 * ws,
+            "rel_err_vs_oracle_max": rel_err_sample(bf, probs, [0, 1, 777, 2048, B - 1] if B > 2048 else [0, B - 1]),
+            "status_ok": bool((stf.cpu().numpy() == 0).all())}
+        bf.close()
+
     # the plain FP64 path on the same batch: batched (one graph) and per instance
     b64 = Batch(probs, precision="fp64")
     ms64 = ev_ms(b64.run, 3, stream, flush)
@@ -582,8 +595,9 @@ def main():
     probs = rank_problems(rank, B, args.n, args.m)
     bt = Batch(probs, precision=args.precision)
     refine = 1 if args.precision == "mixed" else 0   # default refinement passes
-    # setup (lag tables [mixed] + eigendecomposition), assembly, solve, 2 per refinement pass
-    launches_per_step = (2 if args.precision == "mixed" else 1) + 2 + 2 * refine
+    # setup (lag tables, eigendecomposition, condition rows), assembly, solve, 2 per
+    # refinement pass (the band or row residual pass and the update)
+    launches_per_step = 3 + 2 + 2 * refine
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 

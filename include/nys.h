@@ -51,7 +51,11 @@ typedef enum {
   NYS_ESTATE = -9       /* call out of order (e.g. solve before assemble)       */
 } nys_status;
 
-typedef enum { NYS_FP64 = 0, NYS_MIXED = 1 } nys_precision;
+/* NYS_MIXED: FP32 assembly, FP32 H and Cholesky factor, float-float residual
+   refinement.  NYS_MIXED_F64F: the same FP32 assembly and refinement with the
+   H = D + gamma B G B^T formation and its Cholesky factor in FP64 (the split
+   that keeps the factorisation FP64); everything else as NYS_MIXED.          */
+typedef enum { NYS_FP64 = 0, NYS_MIXED = 1, NYS_MIXED_F64F = 2 } nys_precision;
 
 /* Coefficient families of the ODE (Section 2, Eq. 2.1; Section 3.1).       */
 typedef enum {

@@ -72,12 +72,14 @@ class Batch:
 
     def __init__(self, problems, precision="fp64", refine_steps=-1, eig_tau=0.0,
                  scale_sqrt_m=False, stream=None, assembly="auto"):
-        """assembly (mixed precision): "auto", "tc", "simt" or "tune" (nys_assembly)."""
+        """precision: "fp64", "mixed" or "mixed-f64f" (nys_precision); assembly (mixed
+        precisions): "auto", "tc", "simt" or "tune" (nys_assembly)."""
         self.problems = list(problems)
         self.B = len(self.problems)
         self.stream = stream
         opt = A.nys_options()
-        opt.precision = A.NYS_MIXED if precision == "mixed" else A.NYS_FP64
+        opt.precision = {"fp64": A.NYS_FP64, "mixed": A.NYS_MIXED,
+                         "mixed-f64f": A.NYS_MIXED_F64F}[precision]
         opt.refine_steps = int(refine_steps)
         opt.eig_tau = float(eig_tau)
         opt.scale_sqrt_m = 1 if scale_sqrt_m else 0

@@ -35,14 +35,15 @@ cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const 
                          const int32_t* lm, void* fac, int64_t facs, double* xs, double* zs,
                          double* cws, int XS, int ZS, int M1S, const int32_t* st_init,
                          int32_t* st, double gamma_scale, int batch, int m_max, cudaStream_t s,
-                         const int32_t* asm_err, BigSet big = BigSet(), const double* crow = nullptr);
+                         const int32_t* asm_err, BigSet big = BigSet(), const double* crow = nullptr,
+                         bool fac64 = false);
 cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W, const float* lag,
                           const Work* work, int nwork, int* counter, const int32_t* lm,
                           const double* tab,
                           double* part, const int64_t* slot_off, const void* fac, int64_t facs,
                           double* xs, double* zs, const double* cws, int XS, int ZS, int M1S,
                           int32_t* st, double gamma_scale, int batch, int m_max, int k_max,
-                          int num_sms, cudaStream_t s, int nrband = 0);
+                          int num_sms, cudaStream_t s, int nrband = 0, bool fac64 = false);
 cudaError_t launch_eval(const Inst* insts, const double* zs, int ZS, const int32_t* lm,
                         const double* tq, const int64_t* tq_off, int deriv, double* yq, int batch,
                         cudaStream_t s);
@@ -148,7 +149,8 @@ struct nys_ctx {
   int XS = 0, ZS = 0, M1S = 0;
   int64_t facs = 0;
   nys_options opt{};
-  bool fp32 = false;
+  bool fp32 = false;           // FP32 assembly (NYS_MIXED, NYS_MIXED_F64F)
+  bool fac64 = false;          // NYS_MIXED_F64F: FP64 H and Cholesky factor
   bool any_nl = false, any_lin = false;
   int nt_tiles = 4;            // shared tiles of the Newton row pass (6 with a beta term)
   bool solved = false, assembled = false;
@@ -731,7 +733,8 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   c->batch = batch;
   if (opt) c->opt = *opt;
   else { c->opt.precision = NYS_FP64; c->opt.refine_steps = -1; }
-  if (c->opt.precision != NYS_FP64 && c->opt.precision != NYS_MIXED) {
+  if (c->opt.precision != NYS_FP64 && c->opt.precision != NYS_MIXED &&
+      c->opt.precision != NYS_MIXED_F64F) {
     delete c;
     return fail(NYS_EINVAL, "nys_setup: unknown precision %d", c->opt.precision);
   }
@@ -751,7 +754,8 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
     c->opt.refine_steps = any_bvp ? 2 : 1;
   }
   if (c->opt.refine_steps > 8) { delete c; return fail(NYS_EINVAL, "nys_setup: refine_steps > 8"); }
-  c->fp32 = (c->opt.precision == NYS_MIXED);
+  c->fp32 = (c->opt.precision == NYS_MIXED || c->opt.precision == NYS_MIXED_F64F);
+  c->fac64 = (c->opt.precision == NYS_MIXED_F64F);
   for (int b = 0; b < batch && c->fp32; ++b)
     if (q[b].p > 2) {
       delete c;
@@ -883,7 +887,7 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   c->ZS = c->m_max + 1;
   c->M1S = c->m_max + 1;
   c->facs = fac_elems(c->m_max);
-  const size_t es = c->fp32 ? sizeof(float) : sizeof(double);
+  const size_t es = (c->fp32 && !c->fac64) ? sizeof(float) : sizeof(double);
   // Newton row offsets
   std::vector<int64_t> roff(batch);
   int64_t ytot = 0;
@@ -1137,13 +1141,13 @@ static int32_t solve_impl(nys_ctx* c, cudaStream_t s, double* x_out, int32_t* st
   CK(launch_solve(c->fp32, c->inst.p, c->lset.p, c->W.p, c->W32.p, c->part.p, c->slot_off.p,
                   c->lm.p, c->fac.p, c->facs, c->xs.p, c->zs.p, c->cws.p, c->XS, c->ZS, c->M1S,
                   c->stinit.p, c->st.p, gscale, c->batch, c->m_max, s,
-                  c->fp32 ? c->err.p : nullptr, c->bigset(), c->crow.p));
+                  c->fp32 ? c->err.p : nullptr, c->bigset(), c->crow.p, c->fac64));
   if (c->fp32) {
     for (int k = 0; k < c->opt.refine_steps; ++k)
       CK(launch_refine(c->inst.p, c->lset.p, c->W.p, c->lag.p, c->rwork.p, c->nrwork, c->counter.p,
                        c->lm.p, c->tab.p, c->part.p, c->slot_off.p, c->fac.p, c->facs, c->xs.p, c->zs.p,
                        c->cws.p, c->XS, c->ZS, c->M1S, c->st.p, gscale, c->batch, c->m_max,
-                       c->k_max, c->num_sms, s, c->nrband));
+                       c->k_max, c->num_sms, s, c->nrband, c->fac64));
   }
   if (x_out)
     CK(cudaMemcpyAsync(x_out, c->xs.p, sizeof(double) * c->batch * c->XS, cudaMemcpyDeviceToDevice, s));

@@ -86,7 +86,7 @@ constexpr double kRefBandU = 40.0;
 __host__ __device__ __forceinline__ int refine_band_lag(double hs, int n) {
   return (int)fmin(ceil(sqrt(kRefBandU) / hs), (double)(n - 1));
 }
-constexpr int kRbLm = 20;
+constexpr int kRbLm = 18;
 constexpr int kRbTabCap = 8192;
 constexpr int kRbMaxW = 512;
 

@@ -38,7 +38,8 @@ cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const 
                          const int32_t* lm, void* fac, int64_t facs, double* xs, double* zs,
                          double* cws, int XS, int ZS, int M1S, const int32_t* st_init,
                          int32_t* st, double gamma_scale, int batch, int m_max, cudaStream_t s,
-                         const int32_t* asm_err, BigSet big = BigSet(), const double* crow = nullptr);
+                         const int32_t* asm_err, BigSet big = BigSet(), const double* crow = nullptr,
+                         bool fac64 = false);
 int64_t fac_elems(int m_max);
 int32_t set_last_error(int32_t code, const char* msg);  // nys_api.cu: feeds nys_last_error()
 }  // namespace nys

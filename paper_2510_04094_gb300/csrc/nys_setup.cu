@@ -337,11 +337,15 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict_
     const bool well = red[0] != 0.0;
     __syncthreads();
     if (well) {
-      // W0 = Lambda^-1/2 U^T (descending), straight to the output
+      // W0 = Lambda^-1/2 U^T (descending), straight to the output (one square
+      // root and reciprocal per eigenvalue, in the free cosine area)
+      double* rsq = cs;
+      for (int k = tid; k < m; k += nt) rsq[k] = 1.0 / sqrt((double)Af[perm[k] * ld + perm[k]]);
+      __syncthreads();
       for (int e = tid; e < m * m; e += nt) {
         const int k = e / m, j = e % m;
         const int c = perm[k];
-        Wl[e] = (double)Vf[j * ld + c] / sqrt((double)Af[c * ld + c]);
+        Wl[e] = (double)Vf[j * ld + c] * rsq[k];
       }
       for (int k = tid; k < m; k += nt) lam_all[(int64_t)L * kMLarge + k] = (double)Af[perm[k] * ld + perm[k]];
       __syncthreads();

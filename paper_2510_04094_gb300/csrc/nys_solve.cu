@@ -55,7 +55,7 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   const bool om = (LS.omode != 0);
   // more conditions than unknowns (m_eff + 1 < p after truncation): no solution
   const int st0 = (st_init[b] != NYS_OK) ? st_init[b]
-                  : (om && sizeof(T) == sizeof(float)) ? NYS_EPRECISION
+                  : (om && (sizeof(T) == sizeof(float) || asm_err != nullptr)) ? NYS_EPRECISION
                   : (asm_err != nullptr && *asm_err == 2) ? NYS_ESTATE   // stale band plan
                   : (asm_err != nullptr && *asm_err != 0) ? NYS_ETIMEOUT
                   : (LS.m_eff + 1 < I.p) ? NYS_ENOTSPD : NYS_OK;
@@ -1041,7 +1041,10 @@ cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const 
                          void* fac, int64_t facs, double* xs, double* zs, double* cws, int XS,
                          int ZS, int M1S, const int32_t* st_init, int32_t* st, double gamma_scale,
                          int batch, int m_max, cudaStream_t s, const int32_t* asm_err,
-                         BigSet big, const double* crow) {
+                         BigSet big, const double* crow, bool fac64) {
+  // the factor's type: FP32 for NYS_MIXED, FP64 otherwise (a MIXED context with
+  // an FP64 factor passes fp32 with fac64; its asm_err marks it as mixed)
+  if (fac64) fp32 = false;
   const size_t sm = solve_smem_bytes(fp32, m_max < kMMax ? m_max : kMMax);
   cudaError_t e;
   if (fp32) {
@@ -1079,7 +1082,8 @@ cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W,
                           const double* tab, double* part, const int64_t* slot_off,
                           const void* fac, int64_t facs, double* xs, double* zs, const double* cws,
                           int XS, int ZS, int M1S, int32_t* st, double gamma_scale, int batch,
-                          int m_max, int k_max, int num_sms, cudaStream_t s, int nrband) {
+                          int m_max, int k_max, int num_sms, cudaStream_t s, int nrband,
+                          bool fac64) {
   // the first nrband items: k_refine_band (queue counter[1]); the rest k_refine_rows
   cudaError_t e = cudaMemsetAsync(counter, 0, (nrband > 0 ? 2 : 1) * sizeof(int), s);
   if (e != cudaSuccess) return e;
@@ -1104,9 +1108,14 @@ cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W,
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  k_refine_update<float><<<batch, kSolveThreads, 0, s>>>(insts, lsets, W, part, slot_off,
-                                                          (const float*)fac, facs, xs, zs, cws,
-                                                          XS, ZS, M1S, st, gamma_scale);
+  if (fac64)
+    k_refine_update<double><<<batch, kSolveThreads, 0, s>>>(insts, lsets, W, part, slot_off,
+                                                             (const double*)fac, facs, xs, zs, cws,
+                                                             XS, ZS, M1S, st, gamma_scale);
+  else
+    k_refine_update<float><<<batch, kSolveThreads, 0, s>>>(insts, lsets, W, part, slot_off,
+                                                            (const float*)fac, facs, xs, zs, cws,
+                                                            XS, ZS, M1S, st, gamma_scale);
   return cudaGetLastError();
 }
 

@@ -10,7 +10,7 @@ import nys_inputs as ni
 from oracle import core
 
 pytestmark = pytest.mark.gpu
-TOL = {"fp64": 1e-10, "mixed": 1e-6}
+TOL = {"fp64": 1e-10, "mixed": 1e-6, "mixed-f64f": 1e-6}
 
 
 @pytest.fixture(scope="module")
@@ -26,11 +26,12 @@ def api():
 
 def _check(api, probs, precision, tol=None, refine=-1):
     """precision: "fp64", "mixed" (band units on the CUDA cores where the plan
-    allows, the tensor cores elsewhere), "mixed-tc" (tensor cores only) or
-    "mixed-simt" (the 8x8-block CUDA-core Gram)."""
+    allows, the tensor cores elsewhere), "mixed-tc" (tensor cores only),
+    "mixed-simt" (the 8x8-block CUDA-core Gram) or "mixed-f64f" (mixed with an
+    FP64 H and Cholesky factor)."""
     import torch
-    assembly = {"simt": "simt", "tc": "tc"}[precision.split("-")[1]] if "-" in precision else "auto"
-    precision = precision.split("-")[0]
+    assembly = {"mixed-simt": "simt", "mixed-tc": "tc"}.get(precision, "auto")
+    precision = {"mixed-simt": "mixed", "mixed-tc": "mixed"}.get(precision, precision)
     tol = TOL[precision] if tol is None else tol
     bt = api.Batch(probs, precision=precision, refine_steps=refine, assembly=assembly)
     bt.assemble()
@@ -111,7 +112,7 @@ def _sampled(api, probs, bt, pick, tol):
     return worst
 
 
-@pytest.mark.parametrize("precision", ["mixed", "mixed-tc", "fp64"])
+@pytest.mark.parametrize("precision", ["mixed", "mixed-tc", "mixed-f64f", "fp64"])
 def test_metric_batch_full_size_sampled(api, precision):
     """The throughput workload itself, 4096 instances at n = 1e4, m = 50, in the
     launch configuration bench.py times (one nys_run graph; mixed: the default
@@ -121,8 +122,8 @@ def test_metric_batch_full_size_sampled(api, precision):
     oracle."""
     import torch
     probs = ni.m0(4096)
-    prec, _, asm = precision.partition("-")
-    bt = api.Batch(probs, precision=prec, assembly=asm or "auto")
+    prec = "mixed" if precision == "mixed-tc" else precision
+    bt = api.Batch(probs, precision=prec, assembly="tc" if precision == "mixed-tc" else "auto")
     if precision == "mixed":      # every unit of this workload is a band unit
         band, other = bt.assembly_items()
         assert band > 0 and other == 0, (band, other)
@@ -158,7 +159,7 @@ def test_cfg2_linear_full_size(api, precision):
     _check(api, [ni.cfg2_linear()], precision)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed-tc", "mixed-simt"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed-tc", "mixed-simt", "mixed-f64f"])
 def test_ragged_batch_all_m_values(api, precision):
     """The ragged family (m in {20, 32, 50, 64, 100}, sigma = T/m), n capped for the oracle."""
     probs = [q for q in ni.cfg3(40, n_hi=4000)]
