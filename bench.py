@@ -39,9 +39,10 @@ METRIC = "batched ODE solves/s at n=1e4, m=50"
 UNIT = "solves/s"
 LAG_U = 80.0   # kernel values exp(-u) with u > 80 (< 2e-35) are treated as zero
 # DRAM bytes (read + write) of one k_assemble_band launch per instance of the
-# metric family, from an ncu capture of the current kernel (None: no capture of
-# the current kernel yet)
-BAND_DRAM_BYTES_PER_INSTANCE = None
+# metric family, from an ncu capture of the current kernel at 512 instances
+# (517.1 KB + 0.8 KB; None once the kernel changes without a new capture).  The
+# unit Grams it writes stay in L2 during the launch.
+BAND_DRAM_BYTES_PER_INSTANCE = (517120 + 768) / 512
 
 
 def parse():
@@ -54,6 +55,11 @@ def parse():
     ap.add_argument("--n", type=int, default=10_000)
     ap.add_argument("--m", type=int, default=50)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--assembly", default="auto", choices=["auto", "tc", "simt"],
+                    help="MIXED assembly kernels (nys_assembly); the default is the library's")
+    ap.add_argument("--workload", default="metric", choices=["metric", "ragged"],
+                    help="ragged: the 4096-instance ragged family instead of the metric batch "
+                         "(for launch lists and profiles)")
     ap.add_argument("--no-extras", action="store_true", help="skip the side measurements")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--long-time", action="store_true",
@@ -303,6 +309,11 @@ def oracle_baseline(problems, seconds, workers):
 
 
 def workload_config(args, ws):
+    if args.workload == "ragged":
+        return {"workload": "ragged linear 2nd-order ODE batch, n log-uniform in [500, 2e4], "
+                            "m in {20,32,50,64,100}, sigma=T/m, gamma=1e10, %s" % args.precision,
+                "global_batch": ws * args.batch, "parallelism": "dp%d" % ws,
+                "l2": "flushed between steps (256 MB write)"}
     return {"workload": "linear 2nd-order ODE batch y''+ay'+by=c sin(wt), n=%d, m=%d, "
                         "sigma=0.5, gamma=1e10, %s" % (args.n, args.m, args.precision),
             "global_batch": ws * args.batch, "seq_len": args.n, "parallelism": "dp%d" % ws,
@@ -592,8 +603,9 @@ def main():
         return
 
     B = args.batch
-    probs = rank_problems(rank, B, args.n, args.m)
-    bt = Batch(probs, precision=args.precision)
+    probs = (rank_problems(rank, B, args.n, args.m) if args.workload == "metric"
+             else ni.cfg3(B))
+    bt = Batch(probs, precision=args.precision, assembly=args.assembly)
     refine = 1 if args.precision == "mixed" else 0   # default refinement passes
     # setup (lag tables, eigendecomposition, condition rows), assembly, solve, 2 per
     # refinement pass (the band or row residual pass and the update)
@@ -632,7 +644,9 @@ def main():
 
     # end to end through the public API: host instances -> H2D -> run -> D2H of x
     x_host = torch.empty_like(bt.x, device="cpu").pin_memory()
-    arr_next, keep = pack_instances(ni.linear_family(B, n=args.n, m=args.m, name="m0", sub=100 + rank))
+    arr_next, keep = pack_instances(
+        ni.linear_family(B, n=args.n, m=args.m, name="m0", sub=100 + rank) if args.workload == "metric"
+        else probs)
     arr_same, keep2 = pack_instances(probs)
     e2e_t = []
     for s in range(args.steps):

@@ -3,7 +3,7 @@
 The solver lives in the C-ABI library libnys.so (include/nys.h), built for
 sm_103a by ``build.build()``.  ``_abi`` exposes its entry points under their
 C names; ``api.Batch`` marshals problem dicts and torch tensors onto them;
-``autograd.NysSolve`` wires the adjoint gradient into torch.autograd.
+``api.NysSolve`` wires the adjoint gradient into torch.autograd.
 """
 from . import build  # noqa: F401
 

@@ -231,7 +231,8 @@ k_assemble_band(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
       }
       for (int e = ntab + lane; e < ntab + W; e += 32) tab[e] = 0.f;   // zero block
     }
-    const float w1 = I.rk.w1.hi, cr = I.rk.c;
+    const RowConst RK = I.rk;                          // in registers for the unit
+    const float w1 = RK.w1.hi, cr = RK.c;
     float C32, S32;
     {
       const double be = remainder(32.0 * I.dth, 6.283185307179586476925286766559);
@@ -255,7 +256,7 @@ k_assemble_band(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         base[j] = (j < A) ? Kt + row0 - uidx[wlo + j] : ntab;
       // exact argument every 8 windows, rotations by 32 dth in between (a
       // rotation adds about one FP32 rounding to sin and cos)
-      if ((win & 7) == 0) lin_sincos(I.rk, row0 + lane, sn, cs);
+      if ((win & 7) == 0) lin_sincos(RK, row0 + lane, sn, cs);
       float acc[kBandEnt];
 #pragma unroll
       for (int e = 0; e < kBandEnt; ++e) acc[e] = 0.f;
