@@ -166,13 +166,70 @@ __device__ bool warp_cholesky(T* A, int ld, int n) {
   return !bad;
 }
 
-// Cholesky by the whole block: one warp for n <= kWarpCholMax (warp barriers
-// only), else cta_cholesky.  Every thread gets the outcome.  Measured on the
-// metric batch (n = 49, seven solve CTAs per SM) the block version is faster,
-// so the warp version is off (kWarpCholMax = 0).
+// In-place lower Cholesky of A (n x n, ld), right-looking by panels of 4
+// columns: warp 0 factors the panel (pivots, scaling, the panel's own
+// updates, warp barriers only), then the whole block subtracts the panel's
+// rank-4 product from the trailing lower triangle (a warp per row, lanes over
+// columns).  Two block barriers per panel instead of one per column, and each
+// trailing entry is read and written once per panel.  Returns false on a
+// non-positive pivot (replaced by 1); every thread gets the outcome.
+template <typename T>
+__device__ bool cta_cholesky_panel(T* A, int ld, int n, int* flag) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  for (int k0 = 0; k0 < n; k0 += 4) {
+    const int kb = min(4, n - k0), k1 = k0 + kb;
+    if (warp == 0) {
+      for (int c = k0; c < k1; ++c) {
+        T d = A[c * ld + c];
+        if (!(d > T(0))) {
+          if (lane == 0) s_bad = 1;
+          d = T(1);
+        }
+        const T lkk = sqrt(d), inv = T(1) / lkk;
+        for (int i = c + 1 + lane; i < n; i += 32) A[i * ld + c] *= inv;
+        __syncwarp();
+        if (lane == 0) A[c * ld + c] = lkk;
+        for (int i = c + 1 + lane; i < n; i += 32) {
+          const T lic = A[i * ld + c];
+          for (int j = c + 1; j < k1 && j <= i; ++j) A[i * ld + j] -= lic * A[j * ld + c];
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int i = k1 + warp; i < n; i += nw) {
+      T li[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) li[c] = (c < kb) ? A[i * ld + k0 + c] : T(0);
+      for (int j = k1 + lane; j <= i; j += 32) {
+        T sv = T(0);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (c < kb) sv += li[c] * A[j * ld + k0 + c];
+        A[i * ld + j] -= sv;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *flag = s_bad;
+  __syncthreads();
+  return *flag == 0;
+}
+
+// Cholesky by the whole block: FP32 by panels (cta_cholesky_panel); FP64 one
+// warp for n <= kWarpCholMax (warp barriers only), else cta_cholesky.  Every
+// thread gets the outcome.  Measured on the metric batch (n = 49, seven solve
+// CTAs per SM) the column-by-column block version beat the one-warp version, so
+// the warp version is off (kWarpCholMax = 0).
 constexpr int kWarpCholMax = 0;
 template <typename T>
 __device__ bool block_cholesky(T* A, int ld, int n, int* flag) {
+  // FP32 factors (MIXED): the panel version; FP64 keeps the column-by-column
+  // order of its results
+  if (sizeof(T) == sizeof(float)) return cta_cholesky_panel(A, ld, n, flag);
   if (n > kWarpCholMax) return cta_cholesky(A, ld, n, flag);
   __syncthreads();
   if (threadIdx.x < 32) {

@@ -26,7 +26,7 @@ cudaError_t launch_setup(Lset* lsets, int capacity, const int32_t* lm_idx, doubl
                          double* lam, float* lag, double tau, int m_max, cudaStream_t st,
                          int allow_chol, const int* m_bounds, int nclass,
                          BigSet big = BigSet(), double* crow = nullptr,
-                         const Inst* insts = nullptr);
+                         const Inst* insts = nullptr, int few_sets = 0);
 cudaError_t launch_assemble(bool fp32, const Inst* insts, const Lset* lsets, const float* lag,
                             const double* W, const Work* work, int nwork, int* counter,
                             const int32_t* lm, const double* tab, double* part,

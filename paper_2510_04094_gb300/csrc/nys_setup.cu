@@ -482,7 +482,8 @@ size_t setup_ws_doubles() { return setup_smem_bytes(kMLarge) / sizeof(double) + 
 
 static cudaError_t launch_eig_sets(Lset* lsets, int capacity, const int32_t* lm_idx, double* W,
                                    float* W32, double* lam, double tau, int m_max, cudaStream_t st,
-                                   int allow_chol, const int* m_bounds, int nclass, BigSet big);
+                                   int allow_chol, const int* m_bounds, int nclass, BigSet big,
+                                   int few_sets);
 
 // Condition rows of every active landmark set in omega coordinates (FP64), at
 // the kernel width sigma of the set's first instance (Lemma 1's C, Appendix A.4):
@@ -541,10 +542,10 @@ k_setup_crow(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
 cudaError_t launch_eig(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
                        double* lam, double tau, int m_max, cudaStream_t st, int allow_chol,
                        const int* m_bounds, int nclass, BigSet big, double* crow,
-                       const Inst* insts) {
+                       const Inst* insts, int few_sets) {
   if (capacity == 0) return cudaSuccess;
   cudaError_t ec = launch_eig_sets(lsets, capacity, lm_idx, W, W32, lam, tau, m_max, st, allow_chol,
-                                   m_bounds, nclass, big);
+                                   m_bounds, nclass, big, few_sets);
   if (ec != cudaSuccess || crow == nullptr || insts == nullptr) return ec;
   k_setup_crow<<<capacity, 128, 0, st>>>(insts, lsets, lm_idx, W, crow, m_max);
   return cudaGetLastError();
@@ -552,7 +553,8 @@ cudaError_t launch_eig(Lset* lsets, int capacity, const int32_t* lm_idx, double*
 
 static cudaError_t launch_eig_sets(Lset* lsets, int capacity, const int32_t* lm_idx, double* W,
                                    float* W32, double* lam, double tau, int m_max, cudaStream_t st,
-                                   int allow_chol, const int* m_bounds, int nclass, BigSet big) {
+                                   int allow_chol, const int* m_bounds, int nclass, BigSet big,
+                                   int few_sets) {
   int lo = 0;
   for (int k = 0; k < (nclass > 0 ? nclass : 1) && lo < kMMax; ++k) {
     const int hi = std::min((nclass > 0) ? m_bounds[k] : m_max, kMMax);
@@ -561,7 +563,11 @@ static cudaError_t launch_eig_sets(Lset* lsets, int capacity, const int32_t* lm_
     // ~113 KB, two above ~75 KB (of the SM's 228 KB)
     const size_t sm = setup_smem_bytes(hi);
     cudaError_t e;
-    if (sm > 113 * 1024)
+    // few sets (no more than SMs): wider CTAs shorten each set's Jacobi rounds
+    // (measured: a single m = 50 set, FP32 route, 512 threads 0.06 ms faster than 256)
+    if (few_sets && !allow_chol && sm <= 113 * 1024)
+      e = launch_eig_class<512>(lsets, capacity, lm_idx, W, W32, lam, tau, allow_chol, lo, hi, st);
+    else if (sm > 113 * 1024)
       e = launch_eig_class<1024>(lsets, capacity, lm_idx, W, W32, lam, tau, allow_chol, lo, hi, st);
     else if (sm > 75 * 1024)
       e = launch_eig_class<512>(lsets, capacity, lm_idx, W, W32, lam, tau, allow_chol, lo, hi, st);
@@ -582,11 +588,11 @@ static cudaError_t launch_eig_sets(Lset* lsets, int capacity, const int32_t* lm_
 cudaError_t launch_setup(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
                          double* lam, float* lag, double tau, int m_max, cudaStream_t st,
                          int allow_chol, const int* m_bounds, int nclass, BigSet big, double* crow,
-                         const Inst* insts) {
+                         const Inst* insts, int few_sets) {
   cudaError_t e = launch_lag(lsets, capacity, lag, st);
   if (e != cudaSuccess) return e;
   return launch_eig(lsets, capacity, lm_idx, W, W32, lam, tau, m_max, st, allow_chol, m_bounds,
-                    nclass, big, crow, insts);
+                    nclass, big, crow, insts, few_sets);
 }
 
 }  // namespace nys

@@ -143,7 +143,65 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     //    Otherwise (many eigenpairs dropped) in blocks of 8 rows of Y.
     const T gbb = Gs[m * ldg + m];
     const int ldy = (m + 1) | 1;
-    if (me * ldy <= M1 * ldh + 8 * m) {
+    if (sizeof(T) == sizeof(float) && me * ldy <= M1 * ldh + 8 * m) {
+      // FP32 factors: 4 x 4 register tiles (a tile reads 4 W and 4 G / Y values
+      // per 16 multiply-adds)
+      T* Ys = Hs;
+      const int tk = (me + 3) >> 2, tl = (m + 3) >> 2;
+      for (int e = threadIdx.x; e < tk * tl; e += blockDim.x) {
+        const int k0 = 4 * (e / tl), l0 = 4 * (e - (e / tl) * tl);
+        const T* wr[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) wr[a] = Wt + min(k0 + a, me - 1) * m;
+        T acc[4][4] = {};
+        for (int j = 0; j < m; ++j) {
+          T w[4], gv[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) w[a] = wr[a][j];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) gv[c] = Gs[j * ldg + min(l0 + c, m - 1)];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][c] += w[a] * gv[c];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            if (k0 + a < me && l0 + c < m) Ys[(k0 + a) * ldy + l0 + c] = acc[a][c];
+      }
+      __syncthreads();
+      Hs = Gs;
+      const int th = (me + 3) >> 2;
+      for (int e = threadIdx.x; e < th * th; e += blockDim.x) {
+        const int k0 = 4 * (e / th), l0 = 4 * (e - (e / th) * th);
+        const T* wr[4];
+        const T* yr[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          wr[a] = Wt + min(k0 + a, me - 1) * m;
+          yr[a] = Ys + min(l0 + a, me - 1) * ldy;
+        }
+        T acc[4][4] = {};
+        for (int j = 0; j < m; ++j) {
+          T w[4], y[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) { w[a] = wr[a][j]; y[a] = yr[a][j]; }
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][c] += w[a] * y[c];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int k = k0 + a, l = l0 + c;
+            if (k < me && l < me) Hs[k * ldh + l] = (T)gamma * acc[a][c] + (k == l ? T(1) : T(0));
+          }
+      }
+    } else if (me * ldy <= M1 * ldh + 8 * m) {
       // each thread: rows k, k + 1 of one column (two independent sums per load)
       T* Ys = Hs;
       const int kp = (me + 1) >> 1;
