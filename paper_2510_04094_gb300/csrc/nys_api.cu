@@ -23,7 +23,7 @@ cudaError_t launch_lag(const Lset* lsets, int capacity, float* lag, cudaStream_t
 cudaError_t launch_eig(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
                        double* lam, double tau, int m_max, cudaStream_t st, int allow_chol,
                        const int* m_bounds, int nclass, BigSet big = BigSet(), double* crow = nullptr,
-                         const Inst* insts = nullptr, int few_sets = 0);
+                       const Inst* insts = nullptr, int few_sets = 0, const float* lag = nullptr);
 cudaError_t launch_assemble(bool fp32, const Inst* insts, const Lset* lsets, const float* lag,
                             const double* W, const Work* work, int nwork, int* counter,
                             const int32_t* lm, const double* tab, double* part,
@@ -473,7 +473,7 @@ static cudaError_t fork_factor(nys_ctx* c, cudaStream_t s) {
     e = launch_eig(c->lset.p, c->batch, c->lm.p, c->W.p, c->W32.p, c->lam.p,
                    c->opt.eig_tau > 0 ? c->opt.eig_tau : 1e-12, c->m_max, c->side,
                    c->fp32 ? 0 : 1, c->eig_bounds.data(), (int)c->eig_bounds.size(), c->bigset(),
-                   c->crow.p, c->inst.p, c->nlset <= c->num_sms ? 1 : 0);
+                   c->crow.p, c->inst.p, c->nlset <= c->num_sms ? 1 : 0, c->lag.p);
   if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
   return e;
 }

@@ -64,7 +64,7 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 // longer shrinks it fourfold: the rounding floor of the working precision.
 __device__ __forceinline__ int rr_pos(int k, int r, int N) {
   if (k == 0) return 0;
-  int t = (k - 1 - r) % (N - 1);
+  int t = k - 1 - r;   // 0 <= k - 1, r < N - 1
   if (t < 0) t += N - 1;
   return 1 + t;
 }
@@ -185,6 +185,246 @@ __device__ void sort_desc(const T* A, int ld, int m, int* perm) {
   __syncthreads();
 }
 
+// ---- FP32 route eigensolver --------------------------------------------------
+// Rotation annihilating apq of the symmetric block [[app, apq], [apq, aqq]]
+// (Golub & Van Loan's symmetric Schur step): tau = (aqq - app) / (2 apq),
+// t = sign(tau) / (|tau| + sqrt(1 + tau^2)) (t -> 0 once tau^2 overflows),
+// c = 1 / sqrt(1 + t^2), s = t c.  The two divisions are the approximate ones
+// (a small error in t only perturbs the angle); c is the approximate reciprocal
+// square root refined by one Newton-Raphson step, so that c^2 + s^2 = 1 to
+// FP32 rounding, which keeps the accumulated V orthogonal.
+__device__ __forceinline__ void f32_rotation(float app, float aqq, float apq, float& c, float& s) {
+  c = 1.f;
+  s = 0.f;
+  if (fabsf(apq) > 1e-30f) {
+    const float tau = __fdividef(aqq - app, 2.f * apq);
+    const float t = __fdividef(copysignf(1.f, tau), fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
+    if (t != 0.f) {
+      const float x = fmaf(t, t, 1.f);
+      const float y = rsqrtf(x);
+      c = y * fmaf(-0.5f * x * y, y, 1.5f);
+      s = t * c;
+    }
+  }
+}
+
+// (sh, sl) += u (w.x + w.y): the product u w.x split exactly (FMA), summed by
+// Knuth's two-sum, the low parts gathered in sl (float-float accumulation)
+__device__ __forceinline__ void ff_fma(float& sh, float& sl, float u, float2 w) {
+  const float p = u * w.x;
+  const float pe = fmaf(u, w.x, -p);
+  const float t = sh + p;
+  const float z = t - sh;
+  const float err = (sh - (t - z)) + (p - z);
+  sh = t;
+  sl = fmaf(u, w.y, sl + (err + pe));
+}
+
+__device__ __forceinline__ int upk(int i, int j, int ld) { return min(i, j) * ld + max(i, j); }
+
+// Rotates the 2x2 block of rows (r1, r2) and columns (c1, c2) of A (packed
+// upper addresses e0..e3 of (r1,c1), (r1,c2), (r2,c1), (r2,c2)): the column
+// rotation (c2, s2), then the row rotation (c1, s1).
+__device__ __forceinline__ void f32_block(float* A, int e0, int e1, int e2, int e3, float c1,
+                                          float s1, float c2, float s2) {
+  const float x0 = A[e0], x1 = A[e1], x2 = A[e2], x3 = A[e3];
+  const float y00 = c2 * x0 - s2 * x1, y01 = s2 * x0 + c2 * x1;
+  const float y10 = c2 * x2 - s2 * x3, y11 = s2 * x2 + c2 * x3;
+  A[e0] = c1 * y00 - s1 * y10;
+  A[e1] = c1 * y01 - s1 * y11;
+  A[e2] = s1 * y00 + c1 * y10;
+  A[e3] = s1 * y01 + c1 * y11;
+}
+
+// Parallel cyclic Jacobi in FP32 on one CTA of NW warps (the same tournament
+// ordering as jacobi_sweeps).  A: the even-padded N x N matrix in shared
+// memory, only its upper triangle stored and updated (entry (i, j) at
+// min(i,j) ldf + max(i,j)); the bye player of an odd m is a zero row and
+// column.  A round: warp 0 computes the rotations of the pairs into
+// prm[b] = (p | swapped << 16, q, c, s) (p < q the pair's players, swapped:
+// slot b holds q); a barrier; the upper 2x2 blocks (a, b), a < b, are rotated
+// by the warp of row pair a, folded with row pair half-1-a so that each lane
+// has one block, and the diagonal blocks by the last warp; a second barrier.
+// The accumulated rotations V live in registers: lane b holds the tournament
+// slots (b, N-1-b) of the rows w + NW u of warp w.  After each round the
+// players move one slot (k -> k+1 over 1..N-1, slot 0 fixed), two shuffles per
+// register row, so every lane keeps rotating its own pair of slots; after a
+// whole sweep each player is back in its own slot and V (m rows, ldf) is
+// written to Vout in player order.  Stopping rule as jacobi_sweeps.  Returns
+// false (nothing done) when N > NW U (not enough register rows).
+template <int NW, int HB, int U>
+__device__ bool jacobi_f32(float* A, float* Vout, int ldf, int m, float4* prm, float* red,
+                           double tol, int max_sweeps, double stall) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int N = m + (m & 1), half = N >> 1, nfold = (half + 1) >> 1;
+  if (N > NW * U || half > 32 * HB) return false;
+  float vf[U][HB], vs[U][HB];
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+#pragma unroll
+    for (int hb = 0; hb < HB; ++hb) {
+      const int i = warp + NW * u, b = lane + 32 * hb;
+      vf[u][hb] = (i == b) ? 1.f : 0.f;
+      vs[u][hb] = (i == N - 1 - b) ? 1.f : 0.f;
+    }
+  double prev = 1e300;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    float off = 0.f, dg = 0.f;
+    for (int j = warp; j < m; j += NW)
+      for (int l = j + lane; l < m; l += 32) {
+        const float a = A[j * ldf + l];
+        if (l == j) dg = fmaf(a, a, dg);
+        else off = fmaf(a, a, off);
+      }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      dg += __shfl_xor_sync(0xffffffffu, dg, o);
+    }
+    if (lane == 0) { red[warp] = off; red[NW + warp] = dg; }
+    __syncthreads();
+    off = 0.f;
+    dg = 0.f;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) { off += red[w]; dg += red[NW + w]; }
+    __syncthreads();
+    off *= 2.f;
+    const double offd = off, totd = (double)off + (double)dg;
+    if (offd <= tol * totd) break;
+    if (stall > 0.0 && offd <= stall * totd && offd > 0.25 * prev) break;
+    prev = offd;
+    for (int r = 0; r < N - 1; ++r) {
+      if (warp == 0) {
+#pragma unroll
+        for (int hb = 0; hb < HB; ++hb) {
+          const int b = lane + 32 * hb;
+          if (b < half) {
+            const int f = rr_pos(b, r, N), g = rr_pos(N - 1 - b, r, N);
+            const int p = min(f, g), q = max(f, g);
+            float c, sn;
+            f32_rotation(A[p * ldf + p], A[q * ldf + q], A[p * ldf + q], c, sn);
+            prm[b] = make_float4(__int_as_float(p | (f > g ? 0x10000 : 0)), __int_as_float(q), c, sn);
+          }
+        }
+      }
+      __syncthreads();
+      int pp[HB], qq[HB];
+      float cc[HB], ss[HB], se[HB];
+#pragma unroll
+      for (int hb = 0; hb < HB; ++hb) {
+        const float4 P = prm[min(lane + 32 * hb, half - 1)];
+        const int pe = __float_as_int(P.x);
+        pp[hb] = pe & 0xffff;
+        qq[hb] = __float_as_int(P.y);
+        cc[hb] = P.z;
+        ss[hb] = P.w;
+        se[hb] = (pe & 0x10000) ? -P.w : P.w;   // the sine in slot order
+      }
+      // off-diagonal upper blocks: lane b takes (a, b) for b > a, else
+      // (half-1-a, half-1-b) (none for the middle row pair of an odd half)
+      for (int a = warp; a < nfold; a += NW) {
+        const int a2 = half - 1 - a;
+        const float4 PA = prm[a], PB = prm[a2];
+#pragma unroll
+        for (int hb = 0; hb < HB; ++hb) {
+          const int b = lane + 32 * hb;
+          const bool up = b > a;
+          const bool ok = b < half && (up || (b < a && a2 != a));
+          const float4 PC = prm[up ? min(b, half - 1) : half - 1 - b];
+          const float4 PR = up ? PA : PB;
+          const int r1 = __float_as_int(PR.x) & 0xffff, r2 = __float_as_int(PR.y);
+          const int c1 = __float_as_int(PC.x) & 0xffff, c2 = __float_as_int(PC.y);
+          if (ok)
+            f32_block(A, upk(r1, c1, ldf), upk(r1, c2, ldf), upk(r2, c1, ldf), upk(r2, c2, ldf),
+                      PR.z, PR.w, PC.z, PC.w);
+        }
+      }
+      // diagonal blocks (p, q) x (p, q): the same two-sided rotation; (q, p)
+      // is the stored (p, q)
+      if (warp == NW - 1) {
+#pragma unroll
+        for (int hb = 0; hb < HB; ++hb) {
+          if (lane + 32 * hb < half) {
+            const int ep = pp[hb] * ldf + pp[hb], eq = qq[hb] * ldf + qq[hb];
+            const int e = pp[hb] * ldf + qq[hb];
+            const float c = cc[hb], sn = ss[hb];
+            const float x0 = A[ep], x1 = A[e], x3 = A[eq];
+            const float y00 = c * x0 - sn * x1, y01 = sn * x0 + c * x1;
+            const float y10 = c * x1 - sn * x3, y11 = sn * x1 + c * x3;
+            A[ep] = c * y00 - sn * y10;
+            A[e] = c * y01 - sn * y11;
+            A[eq] = sn * y01 + c * y11;
+          }
+        }
+      }
+      // V <- V J (lanes past the pairs rotate copies of the last pair's slots,
+      // never read), then the slot shift: first(b) <- first(b-1), first(1) <-
+      // second(0), first(0) stays; second(b) <- second(b+1), second(half-1) <-
+      // first(half-1)
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int hb = 0; hb < HB; ++hb) {
+          const float f = vf[u][hb], g = vs[u][hb];
+          vf[u][hb] = cc[hb] * f - se[hb] * g;
+          vs[u][hb] = se[hb] * f + cc[hb] * g;
+        }
+      const int src_up = (lane + 31) & 31, src_dn = (lane + 1) & 31;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (HB == 1) {
+          const float x = lane == 0 ? vs[u][0] : vf[u][0];
+          const float up = __shfl_sync(0xffffffffu, x, src_up);
+          const float dn = __shfl_sync(0xffffffffu, vs[u][0], src_dn);
+          const float nf = lane == 0 ? vf[u][0] : up;
+          const float ns = lane == half - 1 ? vf[u][0] : dn;
+          vf[u][0] = nf;
+          vs[u][0] = ns;
+        } else {
+          const float x0 = lane == 0 ? vs[u][0] : vf[u][0];
+          const float r0 = __shfl_sync(0xffffffffu, x0, src_up);
+          const float r1 = __shfl_sync(0xffffffffu, vf[u][HB - 1], src_up);
+          const float d0 = __shfl_sync(0xffffffffu, vs[u][0], src_dn);
+          const float d1 = __shfl_sync(0xffffffffu, vs[u][HB - 1], src_dn);
+          const float nf0 = lane == 0 ? vf[u][0] : r0;
+          const float nf1 = lane == 0 ? r0 : r1;
+          float ns0 = lane == 31 ? d1 : d0;
+          float ns1 = d1;
+          if (lane == half - 1) ns0 = vf[u][0];
+          if (lane + 32 == half - 1) ns1 = vf[u][HB - 1];
+          vf[u][0] = nf0;
+          vf[u][HB - 1] = nf1;
+          vs[u][0] = ns0;
+          vs[u][HB - 1] = ns1;
+        }
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+#pragma unroll
+    for (int hb = 0; hb < HB; ++hb) {
+      const int i = warp + NW * u, b = lane + 32 * hb;
+      if (i < m && b < half) {
+        if (b < m) Vout[i * ldf + b] = vf[u][hb];
+        if (N - 1 - b < m) Vout[i * ldf + N - 1 - b] = vs[u][hb];
+      }
+    }
+  __syncthreads();
+  return true;
+}
+
+// doubles of k_setup_eig's V area: m (m+1), or (N + m)(N + 1) floats for odd m
+__host__ __device__ constexpr int eig_v_doubles(int m) { return m * (m + 1) + 2 * m + 2; }
+
+// register rows of jacobi_f32 per warp for the CTA widths of k_setup_eig: the
+// widths' FP32-route landmark classes (256: m <= 64, 512: m <= 83, 1024:
+// m <= kMMax) bound N
+template <int NT, int HB>
+__host__ __device__ constexpr int f32_vrows() {
+  return HB == 1 ? 64 / (NT / 32) : (NT == 512 ? 6 : 4);
+}
+
 // NT threads per CTA: 256 for the small landmark counts (several CTAs per SM),
 // 512 / 1024 for the large ones, whose shared memory leaves room for 2 / 1 CTAs.
 // kG: landmark counts above kMMax, whose matrices do not fit in shared memory,
@@ -193,7 +433,7 @@ template <int NT, bool kG>
 __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1))
 k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict__ W_all,
             float* __restrict__ W32_all, double* __restrict__ lam_all, double tau, int allow_chol,
-            int m_lo, int m_hi, BigSet big) {
+            int m_lo, int m_hi, BigSet big, const float* __restrict__ lag) {
   // the grid covers every slot; inactive slots (instances that share another
   // instance's set) return at once, so a captured graph stays valid when an
   // update changes which instances share
@@ -205,11 +445,13 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict_
   const int m = S.m;
   const int N = m + (m & 1);  // even player count; index m (if present) is a bye
   const int ld = m + 1;
-  extern __shared__ double smem_eig[];
+  extern __shared__ __align__(16) double smem_eig[];
   double* sm = kG ? big.ws + (int64_t)blockIdx.x * big.stride : smem_eig;
   double* A = sm;
   double* V = A + m * ld;
-  double* cs = V + m * ld;                 // N/2 cosines then N/2 sines
+  // V's area holds m x ld doubles, or the FP32 route's two N x (N+1) and
+  // m x (N+1) float matrices (even size: cs stays 16-byte aligned)
+  double* cs = V + eig_v_doubles(m);       // N/2 cosines then N/2 sines
   double* red = cs + N;                    // 32
   int* pos = reinterpret_cast<int*>(red + 32);   // N: the round's pairs (p then q)
   int* perm = pos + N;                     // m
@@ -304,89 +546,145 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict_
       }
     }
   }
-  // FP32 route (mixed contexts): Jacobi sweeps in FP32 (64x the FP64 rate), then
-  // one FP64 correction that makes W an exact whitening again: with W0 from the
-  // FP32 eigenpairs, M = W0 Omega W0^T = I + E and W = (I - E/2) W0 satisfies
-  // W^T W = Omega^-1 up to O(E^2); its rows stay nearly orthogonal, which the
-  // FP32 factor of the mixed path needs.  Used when lambda_min > 1e-5 lambda_max
-  // (nothing truncated) and |E| <= 1e-5; otherwise the FP64 Jacobi below.
-  if (!allow_chol) {
+  // FP32 route (mixed contexts): Jacobi sweeps in FP32 (jacobi_f32), then one
+  // correction that makes W an exact whitening again: with W0 = D U^T from the
+  // FP32 eigenpairs (D = Lambda^-1/2), M = W0 Omega W0^T = I + E and
+  // W = (I - E/2) W0 satisfies W^T W = Omega^-1 up to O(E^2); its rows stay
+  // nearly orthogonal, which the FP32 factor of the mixed path needs.  The
+  // products U^T Omega U run in float-float on the FP32 pipe (Omega's entries
+  // are the lag table's float-float b0, exact FP64 kernel values to 2^-48);
+  // the diagonal of E in FP64; E's off-diagonal entries (of size ~1e-6) and
+  // the correction E W0 in FP32, whose relative error leaves W exact to ~1e-13.
+  // Used when lambda_min > 1e-5 lambda_max (nothing truncated) and |E| <= 1e-5;
+  // otherwise the FP64 Jacobi below.
+  if (!kG && !allow_chol) {
+    const int ldf = N + 1;
+    float2* Om = reinterpret_cast<float2*>(A);   // Omega, then T: m x ld float-float
+    float* Af = reinterpret_cast<float*>(V);     // N x ldf, upper triangle; then G
+    float* Vf = Af + N * ldf;                    // m x ldf
+    const float* lagS = lag != nullptr ? lag + S.lag_off : nullptr;
     for (int e = tid; e < m * m; e += nt) {
       const int j = e / m, l = e % m;
-      const double d = (double)(idx[j] - idx[l]) * S.hs;
-      A[j * ld + l] = exp(-d * d);
-    }
-    float* Af = reinterpret_cast<float*>(V);   // two m x ld float matrices in V's space
-    float* Vf = Af + m * ld;
-    __syncthreads();
-    for (int e = tid; e < m * m; e += nt) {
-      const int j = e / m, l = e % m;
-      Af[j * ld + l] = (float)A[j * ld + l];
-      Vf[j * ld + l] = (j == l) ? 1.f : 0.f;
-    }
-    __syncthreads();
-    // FP32 sweeps reach off(A)^2 ~ 1e-13 tot(A)^2; the correction below absorbs the rest
-    jacobi_sweeps<float, NT / 32>(Af, Vf, ld, m, N, reinterpret_cast<float*>(cs), pos, red, 1e-13,
-                                  kMaxSweeps, 1e-9);
-    sort_desc(Af, ld, m, perm);
-    if (tid == 0) {
-      const double lmax = Af[perm[0] * ld + perm[0]], lmin = Af[perm[m - 1] * ld + perm[m - 1]];
-      red[0] = (lmin > 1e-5 * lmax && lmin > 0.0) ? 1.0 : 0.0;
-    }
-    __syncthreads();
-    const bool well = red[0] != 0.0;
-    __syncthreads();
-    if (well) {
-      // W0 = Lambda^-1/2 U^T (descending), straight to the output (one square
-      // root and reciprocal per eigenvalue, in the free cosine area)
-      double* rsq = cs;
-      for (int k = tid; k < m; k += nt) rsq[k] = 1.0 / sqrt((double)Af[perm[k] * ld + perm[k]]);
-      __syncthreads();
-      for (int e = tid; e < m * m; e += nt) {
-        const int k = e / m, j = e % m;
-        const int c = perm[k];
-        Wl[e] = (double)Vf[j * ld + c] * rsq[k];
+      const int k = abs(idx[j] - idx[l]);
+      float2 w = make_float2(0.f, 0.f);
+      if (lagS != nullptr) {
+        if (k <= S.K) w = make_float2(lagS[6 * k], lagS[6 * k + 1]);
+      } else {
+        const double d = (double)k * S.hs, x = exp(-d * d);
+        w.x = (float)x;
+        w.y = (float)(x - (double)w.x);
       }
-      for (int k = tid; k < m; k += nt) lam_all[(int64_t)L * kMLarge + k] = (double)Af[perm[k] * ld + perm[k]];
-      __syncthreads();
-      double* Tm = V;                           // T = W0 Omega (the FP32 matrices are done)
-      for (int e = tid; e < m * m; e += nt) {
-        const int k = e / m, j = e % m;
-        double sv = 0.0;
-        for (int i = 0; i < m; ++i) sv += Wl[k * m + i] * A[i * ld + j];
-        Tm[k * ld + j] = sv;
+      Om[j * ld + l] = w;
+      if (j <= l) Af[j * ldf + l] = w.x;
+    }
+    if (N > m)
+      for (int i = tid; i < N; i += nt) Af[i * ldf + m] = 0.f;
+    __syncthreads();
+    float4* prm = reinterpret_cast<float4*>(cs);
+    float* redf = reinterpret_cast<float*>(red);
+    // FP32 sweeps reach off(A)^2 ~ 1e-13 tot(A)^2; the correction absorbs the rest
+    // two slot pairs per lane (N > 64) only on the 512- and 1024-thread CTAs
+    // (the launcher sends the FP32 route's classes above m = 64 there)
+    bool ran = false;
+    if (N <= 64)
+      ran = jacobi_f32<NT / 32, 1, f32_vrows<NT, 1>()>(Af, Vf, ldf, m, prm, redf, 1e-13,
+                                                       kMaxSweeps, 1e-9);
+    else if constexpr (NT >= 512)
+      ran = jacobi_f32<NT / 32, 2, f32_vrows<NT, 2>()>(Af, Vf, ldf, m, prm, redf, 1e-13,
+                                                       kMaxSweeps, 1e-9);
+    if (ran) {
+      sort_desc(Af, ldf, m, perm);
+      if (tid == 0) {
+        const double lmax = Af[perm[0] * ldf + perm[0]];
+        const double lmin = Af[perm[m - 1] * ldf + perm[m - 1]];
+        red[0] = (lmin > 1e-5 * lmax && lmin > 0.0) ? 1.0 : 0.0;
       }
       __syncthreads();
-      for (int e = tid; e < m * m; e += nt) {   // E = T W0^T - I, into A
-        const int k = e / m, l = e % m;
-        double sv = 0.0;
-        for (int j = 0; j < m; ++j) sv += Tm[k * ld + j] * Wl[l * m + j];
-        A[k * ld + l] = sv - (k == l ? 1.0 : 0.0);
-      }
+      const bool well = red[0] != 0.0;
       __syncthreads();
-      double emax = 0.0;
-      for (int e = tid; e < m * m; e += nt) emax = fmax(emax, fabs(A[(e / m) * ld + (e % m)]));
-      emax = block_max(emax, red);
-      if (emax <= 1e-5) {
-        for (int e = tid; e < m * m; e += nt) {   // W = W0 - E W0 / 2, into V
-          const int k = e / m, j = e % m;
-          double sv = 0.0;
-          for (int l = 0; l < m; ++l) sv += A[k * ld + l] * Wl[l * m + j];
-          Tm[k * ld + j] = Wl[k * m + j] - 0.5 * sv;
+      if (well) {
+        // D as float-float (hi, lo) in the rotation area
+        float2* rsq = reinterpret_cast<float2*>(cs);
+        for (int k = tid; k < m; k += nt) {
+          const double l = Af[perm[k] * ldf + perm[k]];
+          const double r = 1.0 / sqrt(l);
+          const float h = (float)r;
+          rsq[k] = make_float2(h, (float)(r - (double)h));
+          lam_all[(int64_t)L * kMLarge + k] = l;
         }
         __syncthreads();
+        // T = U^T Omega (U_ik = Vf[i][perm[k]]): float-float, by column blocks
+        // of Omega, each overwritten by the same columns of T
+        constexpr int kTE = 8;
+        const int cw = max(1, (kTE * nt) / m);
+        for (int j0 = 0; j0 < m; j0 += cw) {
+          const int jn = min(cw, m - j0);
+          float2 acc[kTE];
+#pragma unroll
+          for (int q = 0; q < kTE; ++q) {
+            const int e = tid + q * nt;
+            float sh = 0.f, sl = 0.f;
+            if (e < m * jn) {
+              const int k = e / jn, j = j0 + e % jn;
+              const int c = perm[k];
+              for (int i = 0; i < m; ++i) ff_fma(sh, sl, Vf[i * ldf + c], Om[i * ld + j]);
+            }
+            acc[q] = make_float2(sh, sl);
+          }
+          __syncthreads();
+#pragma unroll
+          for (int q = 0; q < kTE; ++q) {
+            const int e = tid + q * nt;
+            if (e < m * jn) {
+              const float h = acc[q].x + acc[q].y;
+              Om[(e / jn) * ld + j0 + e % jn] = make_float2(h, acc[q].y - (h - acc[q].x));
+            }
+          }
+          __syncthreads();
+        }
+        // M = T U, E = D M D - I; G[k][perm[l]] = E_kl D_l (FP32) over Af
+        float* G = Af;
+        float emax = 0.f;
         for (int e = tid; e < m * m; e += nt) {
-          const double w = Tm[(e / m) * ld + (e % m)];
-          Wl[e] = w;
-          W32l[e] = (float)w;
+          const int k = e / m, l = e % m;
+          const int c = perm[l];
+          float sh = 0.f, sl = 0.f;
+          for (int j = 0; j < m; ++j) ff_fma(sh, sl, Vf[j * ldf + c], Om[k * ld + j]);
+          float E;
+          if (k == l) {
+            const double r = (double)rsq[k].x + (double)rsq[k].y;
+            E = (float)(((double)sh + (double)sl) * r * r - 1.0);
+          } else {
+            E = (sh + sl) * rsq[k].x * rsq[l].x;
+          }
+          emax = fmaxf(emax, fabsf(E));
+          G[k * m + c] = E * rsq[l].x;
         }
-        if (tid == 0) {
-          lsets[L].m_eff = m;
-          lsets[L].omode = 0;
+        emax = (float)block_max((double)emax, red);
+        if (emax <= 1e-5f) {
+          // W = W0 - (E W0) / 2, W0_kj = D_k U_jk (D_k U_jk as an exact
+          // float-float product)
+          for (int e = tid; e < m * m; e += nt) {
+            const int k = e / m, j = e % m;
+            float corr = 0.f;
+            for (int c = 0; c < m; ++c) corr = fmaf(G[k * m + c], Vf[j * ldf + c], corr);
+            const float u = Vf[j * ldf + perm[k]];
+            const float2 r = rsq[k];
+            const float ph = r.x * u;
+            const float pl = fmaf(r.x, u, -ph) + r.y * u - 0.5f * corr;
+            const double w = (double)ph + (double)pl;
+            Wl[e] = w;
+            W32l[e] = (float)w;
+          }
+          if (tid == 0) {
+            lsets[L].m_eff = m;
+            lsets[L].omode = 0;
+          }
+          return;
         }
-        return;
       }
     }
+    __syncthreads();
   }
   // FP64 Jacobi route: the landmark kernel again, V = I
   for (int e = tid; e < m * m; e += nt) {
@@ -453,7 +751,8 @@ k_setup_lag(const Lset* __restrict__ lsets, float* __restrict__ lag) {
 
 size_t setup_smem_bytes(int m) {
   const int N = m + (m & 1);
-  return sizeof(double) * (2 * (size_t)m * (m + 1) + N + 32) + sizeof(int) * (N + 2 * m);
+  return sizeof(double) * ((size_t)m * (m + 1) + eig_v_doubles(m) + N + 32) +
+         sizeof(int) * (N + 2 * m);
 }
 
 // The lag tables feed the row passes; the eigendecomposition only the solve.
@@ -468,13 +767,13 @@ cudaError_t launch_lag(const Lset* lsets, int capacity, float* lag, cudaStream_t
 template <int NT>
 static cudaError_t launch_eig_class(Lset* lsets, int capacity, const int32_t* lm_idx, double* W,
                                     float* W32, double* lam, double tau, int allow_chol, int lo,
-                                    int hi, cudaStream_t st) {
+                                    int hi, cudaStream_t st, const float* lag) {
   const size_t sm = setup_smem_bytes(hi);
   cudaError_t e = cudaFuncSetAttribute(k_setup_eig<NT, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   k_setup_eig<NT, false><<<capacity, NT, sm, st>>>(lsets, lm_idx, W, W32, lam, tau, allow_chol, lo,
-                                                   hi, BigSet());
+                                                   hi, BigSet(), lag);
   return cudaGetLastError();
 }
 
@@ -483,7 +782,7 @@ size_t setup_ws_doubles() { return setup_smem_bytes(kMLarge) / sizeof(double) + 
 static cudaError_t launch_eig_sets(Lset* lsets, int capacity, const int32_t* lm_idx, double* W,
                                    float* W32, double* lam, double tau, int m_max, cudaStream_t st,
                                    int allow_chol, const int* m_bounds, int nclass, BigSet big,
-                                   int few_sets);
+                                   int few_sets, const float* lag);
 
 // Condition rows of every active landmark set in omega coordinates (FP64), at
 // the kernel width sigma of the set's first instance (Lemma 1's C, Appendix A.4):
@@ -542,10 +841,10 @@ k_setup_crow(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
 cudaError_t launch_eig(Lset* lsets, int capacity, const int32_t* lm_idx, double* W, float* W32,
                        double* lam, double tau, int m_max, cudaStream_t st, int allow_chol,
                        const int* m_bounds, int nclass, BigSet big, double* crow,
-                       const Inst* insts, int few_sets) {
+                       const Inst* insts, int few_sets, const float* lag) {
   if (capacity == 0) return cudaSuccess;
   cudaError_t ec = launch_eig_sets(lsets, capacity, lm_idx, W, W32, lam, tau, m_max, st, allow_chol,
-                                   m_bounds, nclass, big, few_sets);
+                                   m_bounds, nclass, big, few_sets, lag);
   if (ec != cudaSuccess || crow == nullptr || insts == nullptr) return ec;
   k_setup_crow<<<capacity, 128, 0, st>>>(insts, lsets, lm_idx, W, crow, m_max);
   return cudaGetLastError();
@@ -554,7 +853,7 @@ cudaError_t launch_eig(Lset* lsets, int capacity, const int32_t* lm_idx, double*
 static cudaError_t launch_eig_sets(Lset* lsets, int capacity, const int32_t* lm_idx, double* W,
                                    float* W32, double* lam, double tau, int m_max, cudaStream_t st,
                                    int allow_chol, const int* m_bounds, int nclass, BigSet big,
-                                   int few_sets) {
+                                   int few_sets, const float* lag) {
   int lo = 0;
   for (int k = 0; k < (nclass > 0 ? nclass : 1) && lo < kMMax; ++k) {
     const int hi = std::min((nclass > 0) ? m_bounds[k] : m_max, kMMax);
@@ -566,19 +865,19 @@ static cudaError_t launch_eig_sets(Lset* lsets, int capacity, const int32_t* lm_
     // few sets (no more than SMs): wider CTAs shorten each set's Jacobi rounds
     // (measured: a single m = 50 set, FP32 route, 512 threads 0.06 ms faster than 256)
     if (few_sets && !allow_chol && sm <= 113 * 1024)
-      e = launch_eig_class<512>(lsets, capacity, lm_idx, W, W32, lam, tau, allow_chol, lo, hi, st);
+      e = launch_eig_class<512>(lsets, capacity, lm_idx, W, W32, lam, tau, allow_chol, lo, hi, st, lag);
     else if (sm > 113 * 1024)
-      e = launch_eig_class<1024>(lsets, capacity, lm_idx, W, W32, lam, tau, allow_chol, lo, hi, st);
-    else if (sm > 75 * 1024)
-      e = launch_eig_class<512>(lsets, capacity, lm_idx, W, W32, lam, tau, allow_chol, lo, hi, st);
+      e = launch_eig_class<1024>(lsets, capacity, lm_idx, W, W32, lam, tau, allow_chol, lo, hi, st, lag);
+    else if (sm > 75 * 1024 || (!allow_chol && hi > 64))
+      e = launch_eig_class<512>(lsets, capacity, lm_idx, W, W32, lam, tau, allow_chol, lo, hi, st, lag);
     else
-      e = launch_eig_class<256>(lsets, capacity, lm_idx, W, W32, lam, tau, allow_chol, lo, hi, st);
+      e = launch_eig_class<256>(lsets, capacity, lm_idx, W, W32, lam, tau, allow_chol, lo, hi, st, lag);
     if (e != cudaSuccess) return e;
     lo = hi;
   }
   if (big.n > 0) {   // landmark counts above kMMax: global workspace
     k_setup_eig<1024, true><<<big.n, 1024, 0, st>>>(lsets, lm_idx, W, W32, lam, tau, allow_chol,
-                                                     kMMax, kMLarge, big);
+                                                     kMMax, kMLarge, big, nullptr);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -592,7 +891,7 @@ cudaError_t launch_setup(Lset* lsets, int capacity, const int32_t* lm_idx, doubl
   cudaError_t e = launch_lag(lsets, capacity, lag, st);
   if (e != cudaSuccess) return e;
   return launch_eig(lsets, capacity, lm_idx, W, W32, lam, tau, m_max, st, allow_chol, m_bounds,
-                    nclass, big, crow, insts, few_sets);
+                    nclass, big, crow, insts, few_sets, lag);
 }
 
 }  // namespace nys
