@@ -33,6 +33,7 @@ constexpr int kRbSmemBytes =
     kRbTabCap * 8 + kM1Max * 8 + kRbWarps * kM1Max * 8 + kMMax * 4 + kRbWarps * kRbMaxW * 8;
 static_assert((kRbTabCap * 8 + kM1Max * 8 + kRbWarps * kM1Max * 8 + kMMax * 4) % 8 == 0, "scratch alignment");
 static_assert(kRbLm + 1 <= 32, "one reduced column per lane");
+static_assert(kRbLm % 2 == 0, "columns in packed pairs");
 static_assert(2 * (kRbSmemBytes + 1024) <= 228 * 1024, "two CTAs per SM");
 
 size_t refine_band_smem_bytes() { return (size_t)kRbSmemBytes; }
@@ -56,14 +57,33 @@ __device__ __forceinline__ ff rb_norm(ff a) {
   return {hi, a.lo - (hi - a.hi)};
 }
 
+// Two independent float-float multiply-adds in the packed FP32 pipe
+// instructions (f32x2: one issue slot for both lanes of the pair, the same
+// IEEE operations per element as rb_fma): acc.k += a.k * b.k, k = x, y.
+struct ff2 { float2 hi, lo; };
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ void rb_fma2(ff2& acc, const ff2& a, const ff2& b) {
+  const float2 p = __fmul2_rn(a.hi, b.hi);
+  float2 e = __ffma2_rn(a.hi, b.hi, neg2(p));
+  e = __ffma2_rn(a.hi, b.lo, e);
+  e = __ffma2_rn(a.lo, b.hi, e);
+  const float2 sm = __fadd2_rn(acc.hi, p);
+  const float2 bb = __fadd2_rn(sm, neg2(acc.hi));
+  const float2 err = __fadd2_rn(__fadd2_rn(acc.hi, neg2(__fadd2_rn(sm, neg2(bb)))),
+                                __fadd2_rn(p, neg2(bb)));
+  acc.hi = sm;
+  acc.lo = __fadd2_rn(acc.lo, __fadd2_rn(err, e));
+}
+
 // One window (R = W / 32 rows per lane), in two passes over its rows so that
 // few registers are live (four warps per scheduler hide the latencies):
 //   1. s_i = r_i - sum_j kappa_ij z~_j - w1 z~_b (two interleaved chains), kept
 //      in the warp's scratch (rows past r1 get s = 0);
-//   2. acc_j += kappa_ij s_i, sum_s += s_i.
+//   2. acc_j += kappa_ij s_i (columns j, j+1 in packed instructions),
+//      sum_s += s_i.
 // Table loads are conflict-free: the lanes read consecutive lags.
-__device__ __forceinline__ void rb_window(ff* acc, ff& sum_s, const float2* __restrict__ tab,
-                                          const int* base, const ff* zr, ff w1zb,
+__device__ __forceinline__ void rb_window(ff2* acc, ff& sum_s, const float2* __restrict__ tab,
+                                          const int* base, const ff2* zr, ff w1zb,
                                           const RowConst& RK, int row0, int r1, int R, int lane,
                                           float2* scr) {
 #pragma unroll 2
@@ -74,23 +94,24 @@ __device__ __forceinline__ void rb_window(ff* acc, ff& sum_s, const float2* __re
     for (int j = 0; j < kRbLm; j += 2) {
       const float2 k0 = tab[base[j] + lane + 32 * q];
       const float2 k1 = tab[base[j + 1] + lane + 32 * q];
-      rb_fma(sp0, ff{k0.x, k0.y}, zr[j]);
-      rb_fma(sp1, ff{k1.x, k1.y}, zr[j + 1]);
+      rb_fma(sp0, ff{k0.x, k0.y}, ff{zr[j >> 1].hi.x, zr[j >> 1].lo.x});
+      rb_fma(sp1, ff{k1.x, k1.y}, ff{zr[j >> 1].hi.y, zr[j >> 1].lo.y});
     }
-    const ff sp = ff_add(ff_add(rb_norm(sp0), rb_norm(sp1)), w1zb);
+    const ff spv = ff_add(ff_add(rb_norm(sp0), rb_norm(sp1)), w1zb);
     ff sv = {0.f, 0.f};
-    if (i < r1) sv = ff_add(ff{lin_rhs_ff(RK, i), 0.f}, ff{-sp.hi, -sp.lo});
+    if (i < r1) sv = ff_add(ff{lin_rhs_ff(RK, i), 0.f}, ff{-spv.hi, -spv.lo});
     scr[32 * q + lane] = make_float2(sv.hi, sv.lo);
     sum_s = ff_add(sum_s, sv);
   }
 #pragma unroll 2
   for (int q = 0; q < R; ++q) {
     const float2 s2 = scr[32 * q + lane];
-    const ff sv = {s2.x, s2.y};
+    const ff2 sv = {make_float2(s2.x, s2.x), make_float2(s2.y, s2.y)};
 #pragma unroll
-    for (int j = 0; j < kRbLm; ++j) {
-      const float2 k = tab[base[j] + lane + 32 * q];
-      rb_fma(acc[j], ff{k.x, k.y}, sv);
+    for (int j = 0; j < kRbLm; j += 2) {
+      const float2 k0 = tab[base[j] + lane + 32 * q];
+      const float2 k1 = tab[base[j + 1] + lane + 32 * q];
+      rb_fma2(acc[j >> 1], ff2{make_float2(k0.x, k1.x), make_float2(k0.y, k1.y)}, sv);
     }
   }
 }
@@ -191,14 +212,18 @@ k_refine_band(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
           break;
         }
         int base[kRbLm];
-        ff zr[kRbLm], acc[kRbLm];
+        ff2 zr[kRbLm / 2], acc[kRbLm / 2];
 #pragma unroll
-        for (int j = 0; j < kRbLm; ++j) {
-          const bool in = j < A;
-          base[j] = in ? Kt + row0 - sidx[wlo + j] : ntab;
-          const float2 z = in ? zsh[wlo + j] : make_float2(0.f, 0.f);
-          zr[j] = ff{z.x, z.y};
-          acc[j] = ff{0.f, 0.f};
+        for (int j = 0; j < kRbLm; j += 2) {
+          float2 z[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const bool in = j + h < A;
+            base[j + h] = in ? Kt + row0 - sidx[wlo + j + h] : ntab;
+            z[h] = in ? zsh[wlo + j + h] : make_float2(0.f, 0.f);
+          }
+          zr[j >> 1] = ff2{make_float2(z[0].x, z[1].x), make_float2(z[0].y, z[1].y)};
+          acc[j >> 1] = ff2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
         }
         ff sum_s = {0.f, 0.f};
         rb_window(acc, sum_s, tab, base, zr, w1zb, RK, row0, r1, R, lane, scr);
@@ -206,7 +231,9 @@ k_refine_band(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         ff v[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j)
-          v[j] = (j < kRbLm) ? rb_norm(acc[j]) : (j == kRbLm ? rb_norm(sum_s) : ff{0.f, 0.f});
+          v[j] = (j < kRbLm) ? rb_norm((j & 1) ? ff{acc[j >> 1].hi.y, acc[j >> 1].lo.y}
+                                               : ff{acc[j >> 1].hi.x, acc[j >> 1].lo.x})
+                             : (j == kRbLm ? rb_norm(sum_s) : ff{0.f, 0.f});
         rb_rs_level<16>(v, lane);
         rb_rs_level<8>(v, lane);
         rb_rs_level<4>(v, lane);
