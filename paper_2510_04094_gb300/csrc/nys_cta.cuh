@@ -265,37 +265,70 @@ __device__ void warp_chol_solve(const T* L, int ld, int n, T* b) {
     }
     return;
   }
-  T rd[4];   // reciprocal diagonal entries of rows lane + 32 r (n <= 128 kept here)
+  if (n > 128) {
+    for (int k = 0; k < n; ++k) {
+      const T yk = b[k] / L[k * ld + k];
+      __syncwarp();
+      for (int i = k + 1 + lane; i < n; i += 32) b[i] -= L[i * ld + k] * yk;
+      if (lane == 0) b[k] = yk;
+      __syncwarp();
+    }
+    for (int k = n - 1; k >= 0; --k) {
+      const T yk = b[k] / L[k * ld + k];
+      __syncwarp();
+      for (int i = lane; i < k; i += 32) b[i] -= L[k * ld + i] * yk;
+      if (lane == 0) b[k] = yk;
+      __syncwarp();
+    }
+    return;
+  }
+  // b and the reciprocal diagonal in registers (lane: rows lane + 32 r); per
+  // step one shuffle and one multiply on the critical path, the L loads off it
+  T bv[4], rd[4];
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     const int i = lane + 32 * r;
+    bv[r] = (i < n) ? b[i] : T(0);
     rd[r] = (i < n) ? T(1) / L[i * ld + i] : T(0);
   }
-  auto rdiag = [&](int k) -> T {
-    if (n > 128) return T(1) / L[k * ld + k];
-    const int q = k >> 5;
-    T v = rd[0];
-    if (q == 1) v = rd[1];
-    if (q == 2) v = rd[2];
-    if (q == 3) v = rd[3];
-    return __shfl_sync(0xffffffffu, v, k & 31);
-  };
-  for (int k = 0; k < n; ++k) {
-    const T inv = rdiag(k);
-    const T yk = b[k] * inv;
-    __syncwarp();
-    for (int i = k + 1 + lane; i < n; i += 32) b[i] -= L[i * ld + k] * yk;
-    if (lane == 0) b[k] = yk;
-    __syncwarp();
+  // L y = b
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int kn = min(32, n - 32 * c);
+#pragma unroll 4
+    for (int kk = 0; kk < kn; ++kk) {
+      const int k = 32 * c + kk;
+      const T yk = __shfl_sync(0xffffffffu, bv[c], kk) * __shfl_sync(0xffffffffu, rd[c], kk);
+#pragma unroll
+      for (int r = c; r < 4; ++r) {
+        const int i = lane + 32 * r;
+        if (i > k && i < n) bv[r] -= L[i * ld + k] * yk;
+      }
+      if (lane == kk) bv[c] = yk;
+    }
   }
-  for (int k = n - 1; k >= 0; --k) {
-    const T inv = rdiag(k);
-    const T yk = b[k] * inv;
-    __syncwarp();
-    for (int i = lane; i < k; i += 32) b[i] -= L[k * ld + i] * yk;
-    if (lane == 0) b[k] = yk;
-    __syncwarp();
+  // L^T x = y
+#pragma unroll
+  for (int c = 3; c >= 0; --c) {
+    const int kn = min(32, n - 32 * c);
+#pragma unroll 4
+    for (int kk = kn - 1; kk >= 0; --kk) {
+      const int k = 32 * c + kk;
+      const T xk = __shfl_sync(0xffffffffu, bv[c], kk) * __shfl_sync(0xffffffffu, rd[c], kk);
+#pragma unroll
+      for (int r = 0; r <= c; ++r) {
+        const int i = lane + 32 * r;
+        if (i < k) bv[r] -= L[k * ld + i] * xk;
+      }
+      if (lane == kk) bv[c] = xk;
+    }
   }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = lane + 32 * r;
+    if (i < n) b[i] = bv[r];
+  }
+  __syncwarp();
 }
 
 // Solve L L^T y = b in place (b overwritten), L lower (n x n, ld).  One warp
@@ -310,9 +343,17 @@ __device__ void cta_chol_solve(const T* L, int ld, int n, T* b) {
 // Apply the stored factor: given residuals (h: M1, cr: p) return the KKT
 // solution (dx: M1, dl: p) of [H C^T; C 0][dx; dl] = [h; cr].  All arrays in
 // shared memory; h is overwritten.
+// Ls (or nullptr): shared memory for a copy of the N2 x N2 factor L, which the
+// substitutions then read there instead of in the global arena.
 template <typename T>
 __device__ void kkt_apply(const FacView<T>& F, int M1, int p, T* h, const T* cr, T* dx, T* dl,
-                          T* red) {
+                          T* red, T* Ls = nullptr) {
+  const T* Lf = F.L;
+  if (Ls != nullptr) {   // copied while the reflections run; the barriers below order it
+    const int ne = (M1 - p) * (M1 - p);
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) Ls[e] = F.L[e];
+    Lf = Ls;
+  }
   // h' = Q^T h = H_p .. H_1 h
   for (int k = 0; k < p; ++k) apply_house_vec(h, M1, F.V + k * M1, F.beta[k], red);
   // y1 = R^{-T} cr
@@ -330,7 +371,7 @@ __device__ void kkt_apply(const FacView<T>& F, int M1, int p, T* h, const T* cr,
     dx[p + i] = s;
   }
   __syncthreads();
-  cta_chol_solve(F.L, N2, N2, dx + p);
+  cta_chol_solve(Lf, N2, N2, dx + p);
   // lambda: R lam = h'[:p] - H'[:p, :] y
   if (threadIdx.x < 2 && threadIdx.x < p) dx[threadIdx.x] = y1s[threadIdx.x];
   __syncthreads();

@@ -733,7 +733,8 @@ k_refine_update(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   }
   __syncthreads();
   const FacView<T> F = fac_view(const_cast<T*>(fac_all) + (int64_t)b * facs, M1);
-  kkt_apply(F, M1, p, h, cr, dx, dl, red);
+  extern __shared__ __align__(16) unsigned char upd_raw[];   // the factor L, N2 x N2
+  kkt_apply(F, M1, p, h, cr, dx, dl, red, reinterpret_cast<T*>(upd_raw));
   for (int k = threadIdx.x; k < M1; k += blockDim.x) {
     const int slot = (k < me) ? k : XS - 3;
     xb[slot] += (double)dx[k];
@@ -1166,14 +1167,23 @@ cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W,
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  if (fac64)
-    k_refine_update<double><<<batch, kSolveThreads, 0, s>>>(insts, lsets, W, part, slot_off,
-                                                             (const double*)fac, facs, xs, zs, cws,
-                                                             XS, ZS, M1S, st, gamma_scale);
-  else
-    k_refine_update<float><<<batch, kSolveThreads, 0, s>>>(insts, lsets, W, part, slot_off,
-                                                            (const float*)fac, facs, xs, zs, cws,
-                                                            XS, ZS, M1S, st, gamma_scale);
+  // shared memory for the factor L (N2 = m_eff + 1 - p <= m_max)
+  const size_t lsm = (size_t)m_max * m_max * (fac64 ? sizeof(double) : sizeof(float));
+  if (fac64) {
+    e = cudaFuncSetAttribute(k_refine_update<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)lsm);
+    if (e != cudaSuccess) return e;
+    k_refine_update<double><<<batch, kSolveThreads, lsm, s>>>(insts, lsets, W, part, slot_off,
+                                                               (const double*)fac, facs, xs, zs,
+                                                               cws, XS, ZS, M1S, st, gamma_scale);
+  } else {
+    e = cudaFuncSetAttribute(k_refine_update<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)lsm);
+    if (e != cudaSuccess) return e;
+    k_refine_update<float><<<batch, kSolveThreads, lsm, s>>>(insts, lsets, W, part, slot_off,
+                                                              (const float*)fac, facs, xs, zs, cws,
+                                                              XS, ZS, M1S, st, gamma_scale);
+  }
   return cudaGetLastError();
 }
 
