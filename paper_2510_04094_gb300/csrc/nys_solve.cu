@@ -34,8 +34,10 @@ int64_t fac_elems(int m_max) { return fac_elems_inline(m_max); }
 // more landmarks are left to MM = kMLarge: one CTA per listed instance, the same
 // steps on its own global (L2-resident) area, whose row chunks k_gram_reduce has
 // already summed into the first slot.
+// (FP32, shared memory: seven CTAs of 128 threads per SM)
 template <typename T, int MM>
-__global__ void __launch_bounds__(MM > kMMax ? kSolveThreadsBig : kSolveThreads)
+__global__ void __launch_bounds__(MM > kMMax ? kSolveThreadsBig : kSolveThreads,
+                                  (MM <= kMMax && sizeof(T) == sizeof(float)) ? 7 : 1)
 k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         const double* __restrict__ W_all, const T* __restrict__ Wt_all,
         const double* __restrict__ part,
@@ -84,9 +86,13 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   T* w = Vh + 4 * M1;                                // M1 scratch
   T* y = w + M1;                                     // M1
   T* red = y + M1;                                   // 40
+  // condition rows in omega coordinates (4 x (m+1)) and their kernel-coordinate
+  // forms (4 x m), FP64, 16-byte aligned after the T area
+  double* s_c = reinterpret_cast<double*>(
+      (reinterpret_cast<uintptr_t>(red + 40) + 15) & ~static_cast<uintptr_t>(15));
+  double* s_e = s_c + 4 * (m + 1);
   __shared__ int s_flag;
   __shared__ T s_beta[4], s_Rm[4][4];               // reflector scales, R (upper, p x p)
-  __shared__ double s_c[4][MM + 1];                 // condition rows, omega coordinates
 
   // 1. add the partial Grams of the row chunks into G (symmetric, full).  A slot
   //    holds [first column jlo (-1: omega coordinates, all me columns), count A,
@@ -279,14 +285,13 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         if (r < p) {
           const int at_n = (r >= hp), d = at_n ? r - hp : r;
           sr[r] = (k < me) ? E[(4 * at_n + d) * (XS - 3) + k] : (d == 0 ? 1.0 : 0.0);
-          s_c[r][k] = sr[r];
+          s_c[r * (m + 1) + k] = sr[r];
         }
       }
       cws[(int64_t)b * 2 * M1S + k] = sr[0];
       cws[(int64_t)b * 2 * M1S + M1S + k] = sr[1];
     }
   }
-  __shared__ double s_e[4][MM];
   for (int e = threadIdx.x; e < (use_crow ? 0 : p * m); e += blockDim.x) {
     const int r = e / m, j = e - r * m;
     const int at_n = (r >= hp), d = at_n ? r - hp : r;
@@ -299,7 +304,7 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     else H = (8.0 * x2 - 12.0) * x;
     double sc = 1.0;                                    // (-1/sigma)^d
     for (int q = 0; q < d; ++q) sc *= -1.0 / I.sigma;
-    s_e[r][j] = sc * H * exp(-x2);
+    s_e[r * m + j] = sc * H * exp(-x2);
   }
   __syncthreads();
   for (int k = warp; k < (use_crow ? 0 : M1); k += nw) {   // a warp per row of W (coalesced)
@@ -309,7 +314,7 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         const double wkj = W[k * m + j];
 #pragma unroll
         for (int r = 0; r < 4; ++r)
-          if (r < p) sr[r] += wkj * s_e[r][j];
+          if (r < p) sr[r] += wkj * s_e[r * m + j];
       }
 #pragma unroll
       for (int r = 0; r < 4; ++r)
@@ -321,7 +326,7 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     if (lane == 0) {
 #pragma unroll
       for (int r = 0; r < 4; ++r)
-        if (r < p) s_c[r][k] = sr[r];
+        if (r < p) s_c[r * (m + 1) + k] = sr[r];
       // rows 0, 1 for the refinement and gradient passes (orders <= 2)
       cws[(int64_t)b * 2 * M1S + k] = sr[0];
       cws[(int64_t)b * 2 * M1S + M1S + k] = sr[1];
@@ -333,7 +338,7 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   T* cr = Yb;                                           // p x M1
   for (int e = threadIdx.x; e < p * M1; e += blockDim.x) {
     const int k = e / M1, i = e - k * M1;
-    cr[e] = (T)s_c[k][i];
+    cr[e] = (T)s_c[k * (m + 1) + i];
     Vh[e] = T(0);
   }
   __syncthreads();
@@ -453,7 +458,8 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
 size_t solve_smem_bytes(bool fp32, int m_max) {
   const int m = m_max, M1 = m + 1;
   const size_t es = fp32 ? sizeof(float) : sizeof(double);
-  return es * ((size_t)(m + 1) * (m + 2) + (size_t)M1 * M1 + 8 * m + 8 * M1 + 40);
+  return es * ((size_t)(m + 1) * (m + 2) + (size_t)M1 * M1 + 8 * m + 8 * M1 + 40) + 16 +
+         sizeof(double) * (4 * (size_t)(m + 1) + 4 * (size_t)m);
 }
 
 size_t solve_ws_doubles() { return solve_smem_bytes(false, kMLarge) / sizeof(double) + 1; }
