@@ -51,6 +51,7 @@ constexpr int kBandGuEnt = kBandGuCols * (kBandGuCols + 1) / 2;
 constexpr int kBandWarpBytes = kBandTabCap * 4 + kBandGuEnt * 8 + kBandGuCols * 4;
 static_assert(kBandWarpBytes % 16 == 0, "warp area alignment");
 static_assert(kBandWarps * kBandWarpBytes <= 227 * 1024, "shared memory of one CTA");
+static_assert(kBandSlots == 16 && kBandLm % 2 == 0, "the accumulator pairing of BandAcc");
 
 size_t asm_band_smem_bytes() { return (size_t)kBandWarps * kBandWarpBytes; }
 
@@ -82,13 +83,42 @@ __device__ __forceinline__ void band_rs_level(float* v, int lane) {
   }
 }
 
-// Products of one row's features into the 136 accumulators.
-__device__ __forceinline__ void band_row(float* acc, const float* f) {
-  int e = 0;
+// The 136 accumulators of a window in registers: row j of the upper triangle
+// (columns l >= j) as pairs (l, l+1) for even l, which the packed FP32
+// instructions update two at a time, and for odd j the single (j, j) first.
+// pr[] and sg[] hold the entries in the packed row-major order below.
+struct BandAcc {
+  float2 pr[64];
+  float sg[8];
+};
+// flat packed row-major index of (j, l) -> position in BandAcc (compile-time)
+__host__ __device__ constexpr int band_flat(int j, int l) { return j * kBandSlots - j * (j - 1) / 2 + (l - j); }
+
+// Products of one row's features (fp[c] = (f[2c], f[2c+1])) into the accumulators
+__device__ __forceinline__ void band_row(BandAcc& A, const float2* fp) {
+  int q = 0;
 #pragma unroll
-  for (int j = 0; j < kBandSlots; ++j)
+  for (int j = 0; j < kBandSlots; ++j) {
+    const float fj = (j & 1) ? fp[j >> 1].y : fp[j >> 1].x;
+    if (j & 1) A.sg[j >> 1] = fmaf(fj, fj, A.sg[j >> 1]);
+    const float2 fjj = make_float2(fj, fj);
 #pragma unroll
-    for (int l = j; l < kBandSlots; ++l, ++e) acc[e] = fmaf(f[j], f[l], acc[e]);
+    for (int l = (j + 1) & ~1; l < kBandSlots; l += 2, ++q) A.pr[q] = __ffma2_rn(fjj, fp[l >> 1], A.pr[q]);
+  }
+}
+
+// The accumulators in the packed row-major order (a register renaming)
+__device__ __forceinline__ void band_flatten(const BandAcc& A, float* v) {
+  int q = 0;
+#pragma unroll
+  for (int j = 0; j < kBandSlots; ++j) {
+    if (j & 1) v[band_flat(j, j)] = A.sg[j >> 1];
+#pragma unroll
+    for (int l = (j + 1) & ~1; l < kBandSlots; l += 2, ++q) {
+      v[band_flat(j, l)] = A.pr[q].x;
+      v[band_flat(j, l + 1)] = A.pr[q].y;
+    }
+  }
 }
 
 // theta advances by 32 dth to the lane's next row
@@ -102,7 +132,7 @@ __device__ __forceinline__ void band_rotate(float& sn, float& cs, float C32, flo
 // at compile time: the table loads use immediate offsets and can be issued
 // ahead of the previous row's products).
 template <int R>
-__device__ __forceinline__ void band_window_full(float* acc, const float* __restrict__ tl,
+__device__ __forceinline__ void band_window_full(BandAcc& acc, const float* __restrict__ tl,
                                                  const int* base, int lane, float w1, float cr,
                                                  float& sn, float& cs, float C32, float S32) {
   const float* p[kBandLm];
@@ -110,31 +140,30 @@ __device__ __forceinline__ void band_window_full(float* acc, const float* __rest
   for (int j = 0; j < kBandLm; ++j) p[j] = tl + base[j] + lane;
 #pragma unroll
   for (int q = 0; q < R; ++q) {
-    float f[kBandSlots];
+    float2 fp[kBandSlots / 2];
 #pragma unroll
-    for (int j = 0; j < kBandLm; ++j) f[j] = p[j][32 * q];
-    f[kBandLm] = w1;
-    f[kBandLm + 1] = cr * sn;
-    band_row(acc, f);
+    for (int j = 0; j < kBandLm; j += 2) fp[j >> 1] = make_float2(p[j][32 * q], p[j + 1][32 * q]);
+    fp[kBandLm >> 1] = make_float2(w1, cr * sn);
+    band_row(acc, fp);
     band_rotate(sn, cs, C32, S32);
   }
 }
 
 // The last window of a unit, which runs past its last row r1: rows >= r1
 // contribute nothing.
-__device__ __forceinline__ void band_window_tail(float* acc, const float* __restrict__ tl,
+__device__ __forceinline__ void band_window_tail(BandAcc& acc, const float* __restrict__ tl,
                                               const int* base, int R, int lane, int row0, int r1,
                                               float w1, float cr, float& sn, float& cs, float C32,
                                               float S32) {
   for (int q = 0; q < R; ++q) {
     const int o = lane + 32 * q;
     const bool ok = row0 + o < r1;
-    float f[kBandSlots];
+    float2 fp[kBandSlots / 2];
 #pragma unroll
-    for (int j = 0; j < kBandLm; ++j) f[j] = ok ? tl[base[j] + o] : 0.f;
-    f[kBandLm] = ok ? w1 : 0.f;
-    f[kBandLm + 1] = ok ? cr * sn : 0.f;
-    band_row(acc, f);
+    for (int j = 0; j < kBandLm; j += 2)
+      fp[j >> 1] = ok ? make_float2(tl[base[j] + o], tl[base[j + 1] + o]) : make_float2(0.f, 0.f);
+    fp[kBandLm >> 1] = ok ? make_float2(w1, cr * sn) : make_float2(0.f, 0.f);
+    band_row(acc, fp);
     band_rotate(sn, cs, C32, S32);
   }
 }
@@ -257,19 +286,23 @@ k_assemble_band(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
       // exact argument every 8 windows, rotations by 32 dth in between (a
       // rotation adds about one FP32 rounding to sin and cos)
       if ((win & 7) == 0) lin_sincos(RK, row0 + lane, sn, cs);
-      float acc[kBandEnt];
+      BandAcc bacc;
 #pragma unroll
-      for (int e = 0; e < kBandEnt; ++e) acc[e] = 0.f;
+      for (int q = 0; q < 64; ++q) bacc.pr[q] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) bacc.sg[q] = 0.f;
       if (row0 + W <= r1) {
         switch (R) {
-          case 8: band_window_full<8>(acc, tab, base, lane, w1, cr, sn, cs, C32, S32); break;
-          case 4: band_window_full<4>(acc, tab, base, lane, w1, cr, sn, cs, C32, S32); break;
-          case 2: band_window_full<2>(acc, tab, base, lane, w1, cr, sn, cs, C32, S32); break;
-          default: band_window_full<1>(acc, tab, base, lane, w1, cr, sn, cs, C32, S32); break;
+          case 8: band_window_full<8>(bacc, tab, base, lane, w1, cr, sn, cs, C32, S32); break;
+          case 4: band_window_full<4>(bacc, tab, base, lane, w1, cr, sn, cs, C32, S32); break;
+          case 2: band_window_full<2>(bacc, tab, base, lane, w1, cr, sn, cs, C32, S32); break;
+          default: band_window_full<1>(bacc, tab, base, lane, w1, cr, sn, cs, C32, S32); break;
         }
       } else {
-        band_window_tail(acc, tab, base, R, lane, row0, r1, w1, cr, sn, cs, C32, S32);
+        band_window_tail(bacc, tab, base, R, lane, row0, r1, w1, cr, sn, cs, C32, S32);
       }
+      float acc[kBandEnt];
+      band_flatten(bacc, acc);
       // reduce-scatter: 136 -> 68 -> 34 -> 17 -> 9 -> 5 entries per lane
       band_rs_level<136, 16>(acc, lane);
       band_rs_level<68, 8>(acc, lane);
