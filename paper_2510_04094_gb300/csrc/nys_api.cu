@@ -603,16 +603,16 @@ static int refine_band_plan(const nys_ctx* c, int b, int64_t unit_rows) {
   if (!c->fp32 || I.kind != NYS_COEF_LIN || I.m > kMMax) return 0;
   const int K = std::min(refine_band_lag(I.hs, I.n), c->h_lset[b].K);
   const int32_t* idx = c->h_lm.data() + c->h_lm_off[b];
-  // among the feasible windows, the one with the shortest unit time: its eight
-  // warps take ceil(windows / 8) windows each, a window costing W / 32 rows
-  // per lane plus its reduction (about one row's worth)
+  // among the feasible windows, the one with the shortest unit time: its
+  // kRbWarps warps take ceil(windows / kRbWarps) windows each, a window costing
+  // W / 32 rows per lane plus its reduction (about one row's worth)
   int best = 0;
   double best_t = 0.0;
   for (int w = kRbMaxW; w >= 32; w /= 2) {
     if (2LL * (K + w - 1) + 1 + w > kRbTabCap || lm_span_count(idx, I.m, w + 2LL * K) > kRbLm)
       continue;
     const int64_t nwin = (std::max<int64_t>(1, unit_rows) + w - 1) / w;
-    const double t = (double)((nwin + 7) / 8) * (w / 32 + 1);
+    const double t = (double)((nwin + kRbWarps - 1) / kRbWarps) * (w / 32 + 1);
     if (best == 0 || t < best_t) { best = w; best_t = t; }
   }
   return best;

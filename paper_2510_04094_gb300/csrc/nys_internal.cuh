@@ -78,17 +78,20 @@ constexpr int kBandLm = 14;
 constexpr int kBandTabCap = 4096;
 constexpr int kBandUnitCols = 48;
 // Band refinement pass (k_refine_band): its residuals keep the landmarks with
-// u = ((t_i - s_j)/sigma)^2 <= kRefBandU of a row (exp(-40) < 2^-57, below
-// FP64's unit roundoff relative to the kernel's peak); landmark columns per
-// window, float-float kappa table capacity per CTA (2 (K + W - 1) + 1 lags and
-// W zeros), longest window.
-constexpr double kRefBandU = 40.0;
+// u = ((t_i - s_j)/sigma)^2 <= kRefBandU of a row (exp(-32) < 2^-46 relative
+// to the kernel's peak: 2^22 below the FP32 factor's rounding, which the
+// refinement removes, and 2^26 below the MIXED path's error bar); landmark
+// columns per window, float-float kappa table capacity per CTA
+// (2 (K + W - 1) + 1 lags and W zeros), longest window.
+constexpr double kRefBandU = 32.0;
 __host__ __device__ __forceinline__ int refine_band_lag(double hs, int n) {
   return (int)fmin(ceil(sqrt(kRefBandU) / hs), (double)(n - 1));
 }
-constexpr int kRbLm = 18;
+constexpr int kRbLm = 16;
 constexpr int kRbTabCap = 8192;
 constexpr int kRbMaxW = 512;
+// warps per CTA of k_refine_band (two CTAs per SM)
+constexpr int kRbWarps = 8;
 
 // Largest lag whose kernel value is kept: (K hs)^2 <= kLagU.
 constexpr double kLagU = 80.0;

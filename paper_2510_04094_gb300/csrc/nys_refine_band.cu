@@ -5,12 +5,12 @@
 //     s_i = r_i - sum_j kappa_ij z~_j - w1 z~_b,   acc_j = sum_i kappa_ij s_i,
 //     acc_b = w1 sum_i s_i,
 // with kappa_ij = kappa(i - idx_j) over the landmarks within the band
-// u = ((t_i - s_j)/sigma)^2 <= kRefBandU (kernel values below 2^-57 of the
+// u = ((t_i - s_j)/sigma)^2 <= kRefBandU (kernel values below 2^-46 of the
 // peak dropped; k_refine_rows keeps u <= kLagU) and float-float arithmetic
 // throughout, as in k_refine_rows; the unit's slot receives acc (m + 1
 // doubles).
 //
-// A CTA (eight warps) takes one unit at a time:
+// A CTA (kRbWarps = 8 warps) takes one unit at a time:
 //   * it folds kappa(lag), lag = -Kt..Kt (Kt = K + W - 1), into a float-float
 //     table in shared memory, followed by W zeros, and loads z~;
 //   * warp w takes windows w, w + 8, ... of W rows; lane l takes rows
@@ -19,7 +19,7 @@
 //     forms s_i, a second adds kappa_ij s_i into per-lane accumulators;
 //   * a float-float reduce-scatter over the warp leaves lane j with window
 //     column j's sum (lane kRbLm with sum_i s_i), which it adds into the
-//     warp's unit accumulator; after the unit the four warps' accumulators
+//     warp's unit accumulator; after the unit the eight warps' accumulators
 //     are added in a fixed order and stored.
 // A window that breaks the plan (more landmarks than planned, a table larger
 // than its space: a stale plan) sets the instance's status to NYS_ESTATE.
@@ -27,7 +27,6 @@
 
 namespace nys {
 
-constexpr int kRbWarps = 8;
 constexpr int kRbThreads = 32 * kRbWarps;
 constexpr int kRbSmemBytes =
     kRbTabCap * 8 + kM1Max * 8 + kRbWarps * kM1Max * 8 + kMMax * 4 + kRbWarps * kRbMaxW * 8;
