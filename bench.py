@@ -15,7 +15,7 @@ Prints one JSON line (rank 0).  Under torchrun each rank solves its own batch
 Roofline (mixed path): the fused assembly of the metric workload runs on the band
 kernel (FP32 FMAs on the CUDA cores); its rate counts the banded Gram each row
 needs -- (a_i + 2)(a_i + 3) + 6 a_i FLOPs with a_i the landmarks within
-u = ((t_i - s_j)/sigma)^2 <= 24 of row i -- and divides it by the measured FP32
+u = ((t_i - s_j)/sigma)^2 <= 16 of row i -- and divides it by the measured FP32
 FMA peak (include/nys_peak.h probes, run in the same process).  The method's
 dense count per row, F(m) = 2m^2 (projection phi = W k) + (m+1)(m+2)
 (upper-triangle Gram) + 2(m+1) (right-hand side) + 10m (operator), is reported
@@ -40,9 +40,9 @@ UNIT = "solves/s"
 LAG_U = 80.0   # kernel values exp(-u) with u > 80 (< 2e-35) are treated as zero
 # DRAM bytes (read + write) of one k_assemble_band launch per instance of the
 # metric family, from an ncu capture of the current kernel at 512 instances
-# (517.1 KB + 0.8 KB; None once the kernel changes without a new capture).  The
-# unit Grams it writes stay in L2 during the launch.
-BAND_DRAM_BYTES_PER_INSTANCE = (517120 + 768) / 512
+# (None once the kernel changes without a new capture).  The unit Grams it
+# writes stay in L2 during the launch.
+BAND_DRAM_BYTES_PER_INSTANCE = None
 
 
 def parse():
@@ -195,7 +195,7 @@ def banded_flops(problems, u=None):
     return tot
 
 
-BAND_U = 24.0         # the FP32 assembly Grams keep the landmarks with u <= 24
+BAND_U = 16.0         # the FP32 assembly Grams keep the landmarks with u <= 16
 TC_BAND_U = BAND_U    # the tensor-core Gram's sub-chunk windows
 TC_SUB_ROWS = 256
 TC_MMA_STEPS = 8      # MMA steps per tensor-memory accumulator entry, at most
@@ -208,7 +208,7 @@ def slot_block(M2):
 def tc_issued_flops(problems, num_sms=152):
     """TF32 MMA FLOPs k_assemble_tc issues for the batch.  Work units of
     max(256, rows / max(B, 4 SMs)) rows per instance are cut into sub-chunks of
-    up to 256 rows; a sub-chunk whose landmark window (rows within u <= 24) has
+    up to 256 rows; a sub-chunk whose landmark window (rows within u <= 16) has
     M2 = A + 2 columns uses slot blocks of Bs = 16, 32, 64 (M2 <= Bs) and 4 MMAs
     of 128 x 128 x 8 per stage of 2048 / Bs rows, or, for M2 > 64, 6 MMAs of
     128 x N x 8 (N = M2 rounded up to 16) per stage of 16 rows; sub-chunks are
@@ -674,7 +674,7 @@ def main():
         band_items, other_items = bt.assembly_items() if mixed else (0, 1)
         if mixed and other_items == 0:
             # the band kernel: FP32 FMAs on the CUDA cores; its algorithmic work is
-            # the banded Gram of every row (landmarks within u <= 24 of the row)
+            # the banded Gram of every row (landmarks within u <= 16 of the row)
             bfl = banded_flops(probs, u=BAND_U)
             peak = pk["ffma"]["tflops"]
             roof = {"bound": "alu", "kernel": "k_assemble_band",
@@ -682,7 +682,7 @@ def main():
                     "frac": bfl / (asm_ms * 1e-3) / 1e12 / peak,
                     "peak_source": "measured in this run: FFMA probe, burst",
                     "flop_count": "banded Gram per collocation row, (a_i+2)(a_i+3) + 6 a_i with a_i "
-                                  "the landmarks within u = ((t_i - s_j)/sigma)^2 <= 24 of row i",
+                                  "the landmarks within u = ((t_i - s_j)/sigma)^2 <= 16 of row i",
                     "flops_per_launch": bfl, "ms_per_launch": asm_ms,
                     "traffic": (BAND_DRAM_BYTES_PER_INSTANCE * B if BAND_DRAM_BYTES_PER_INSTANCE
                                 and args.n == 10_000 and args.m == 50 else None),

@@ -568,7 +568,7 @@ static int lm_span_count(const int32_t* idx, int m, int64_t len) {
 }
 
 // Band plan of instance b for k_assemble_band (kind LIN): the longest window W
-// (256, 128, 64 or 32 rows) whose rows see at most kBandLm landmarks within the
+// (512, 256, 128, 64 or 32 rows) whose rows see at most kBandLm landmarks within the
 // band lag Kb, with its kappa table (2 (Kb + W - 1) + 1 lags and W zeros) in
 // kBandTabCap floats; then unit rows U, a multiple of W of at most
 // max(W, target) rows, whose landmarks + 2 fit kBandUnitCols.  W = 0: the
@@ -579,7 +579,7 @@ static void band_plan(const nys_ctx* c, int b, int64_t target, int& W, int& U) {
   if (I.kind != NYS_COEF_LIN || I.m > kMMax) return;
   const int32_t* idx = c->h_lm.data() + c->h_lm_off[b];
   const int Kb = asm_band_lag(I.hs, I.n);
-  for (int w = 256; w >= 32; w /= 2) {
+  for (int w = 512; w >= 32; w /= 2) {
     if (2LL * (Kb + w - 1) + 1 + w <= kBandTabCap && lm_span_count(idx, I.m, w + 2LL * Kb) <= kBandLm) {
       W = w;
       break;

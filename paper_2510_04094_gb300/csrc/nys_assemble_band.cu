@@ -18,8 +18,8 @@
 //   * lane l takes rows row0 + l + 32 q (q < W / 32) of each window: features
 //     from the table (one conflict-free load per landmark column, the 32 lanes
 //     reading consecutive lags), -f_p, and r(t_i) = c sin(theta_i) (exact
-//     float-float argument every 8 windows, rotations by 32 rows in between);
-//     its 136 products accumulate in FP32 registers;
+//     float-float argument every 64 rows per lane, rotations by 32 rows in
+//     between); its 136 products accumulate in FP32 registers (packed pairs);
 //   * after the window a butterfly reduce-scatter over the warp (shuffles) sums
 //     the 32 lanes' accumulators, leaving each lane at most 5 distinct entries,
 //     which it adds into the unit's Gram in shared memory in compensated FP32
@@ -29,7 +29,7 @@
 //     format of the tensor-core kernel, read by k_solve.
 // Column layout of a window: slots 0..13 landmarks (slots past the window's
 // landmark count read the zero block of the table), slot 14 = -f_p, slot 15 =
-// r.  The per-row accumulation depth is W / 32 <= 8 products per lane before
+// r.  The per-row accumulation depth is W / 32 <= 16 products per lane before
 // the exact-order reduction, well inside FP32's accuracy for a preconditioner
 // Gram that the FP64-accurate refinement corrects.
 //
@@ -225,7 +225,7 @@ k_assemble_band(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     while (a < b) { const int c = (a + b) >> 1; if (idx[c] <= r1 - 1 + Kb) a = c + 1; else b = c; }
     const int Au = a - jlo_u, M2u = Au + 2, Eu = M2u * (M2u + 1) / 2;
     if (M2u > kBandGuCols || ntab + W > kBandTabCap ||
-        (W != 32 && W != 64 && W != 128 && W != 256)) {
+        (W != 32 && W != 64 && W != 128 && W != 256 && W != 512)) {
       if (lane == 0) atomicExch(err, 2);
       continue;
     }
@@ -283,9 +283,10 @@ k_assemble_band(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
 #pragma unroll
       for (int j = 0; j < kBandLm; ++j)
         base[j] = (j < A) ? Kt + row0 - uidx[wlo + j] : ntab;
-      // exact argument every 8 windows, rotations by 32 dth in between (a
-      // rotation adds about one FP32 rounding to sin and cos)
-      if ((win & 7) == 0) lin_sincos(RK, row0 + lane, sn, cs);
+      // exact argument every 64 rows per lane (every 8 windows below 256
+      // rows), rotations by 32 dth in between (a rotation adds about one FP32
+      // rounding to sin and cos)
+      if (win % (R >= 8 ? 64 / R : 8) == 0) lin_sincos(RK, row0 + lane, sn, cs);
       BandAcc bacc;
 #pragma unroll
       for (int q = 0; q < 64; ++q) bacc.pr[q] = make_float2(0.f, 0.f);
@@ -293,6 +294,7 @@ k_assemble_band(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
       for (int q = 0; q < 8; ++q) bacc.sg[q] = 0.f;
       if (row0 + W <= r1) {
         switch (R) {
+          case 16: band_window_full<16>(bacc, tab, base, lane, w1, cr, sn, cs, C32, S32); break;
           case 8: band_window_full<8>(bacc, tab, base, lane, w1, cr, sn, cs, C32, S32); break;
           case 4: band_window_full<4>(bacc, tab, base, lane, w1, cr, sn, cs, C32, S32); break;
           case 2: band_window_full<2>(bacc, tab, base, lane, w1, cr, sn, cs, C32, S32); break;

@@ -66,8 +66,9 @@ struct Lset {
   double hs;           // h / sigma
 };
 // Band of the FP32 assembly Grams: a window keeps the landmarks with
-// ((t_i - s_j)/sigma)^2 <= kAsmBandU for one of its rows (exp(-24) < 2^-34).
-constexpr double kAsmBandU = 24.0;
+// ((t_i - s_j)/sigma)^2 <= kAsmBandU for one of its rows (exp(-16) < 2^-23,
+// FP32's rounding: these Grams only precondition the FP64-accurate refinement).
+constexpr double kAsmBandU = 16.0;
 __host__ __device__ __forceinline__ int asm_band_lag(double hs, int n) {
   return (int)fmin(ceil(sqrt(kAsmBandU) / hs), (double)n);
 }
