@@ -126,7 +126,7 @@ typedef struct {
   int32_t assembly;      /* MIXED only, nys_assembly: NYS_ASM_AUTO (0) runs the
                             Gram of every kind-LIN instance whose landmark
                             windows are narrow (at most 14 landmarks per window
-                            of 32..256 rows within the band u <= 24) on the CUDA
+                            of 32..512 rows within the band u <= 16) on the CUDA
                             cores, one warp per work unit (FP32 products, 16 x
                             16 window Grams, compensated unit sums), and every
                             other instance on the tensor cores (tcgen05, TF32
