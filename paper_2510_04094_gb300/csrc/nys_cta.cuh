@@ -344,14 +344,17 @@ __device__ void cta_chol_solve(const T* L, int ld, int n, T* b) {
 // solution (dx: M1, dl: p) of [H C^T; C 0][dx; dl] = [h; cr].  All arrays in
 // shared memory; h is overwritten.
 // Ls (or nullptr): shared memory for a copy of the N2 x N2 factor L, which the
-// substitutions then read there instead of in the global arena.
+// substitutions then read there instead of in the global arena; copied here
+// unless the caller has staged it (Ls_ready; ordered by the barriers below).
 template <typename T>
 __device__ void kkt_apply(const FacView<T>& F, int M1, int p, T* h, const T* cr, T* dx, T* dl,
-                          T* red, T* Ls = nullptr) {
+                          T* red, T* Ls = nullptr, bool Ls_ready = false) {
   const T* Lf = F.L;
-  if (Ls != nullptr) {   // copied while the reflections run; the barriers below order it
-    const int ne = (M1 - p) * (M1 - p);
-    for (int e = threadIdx.x; e < ne; e += blockDim.x) Ls[e] = F.L[e];
+  if (Ls != nullptr) {
+    if (!Ls_ready) {
+      const int ne = (M1 - p) * (M1 - p);
+      for (int e = threadIdx.x; e < ne; e += blockDim.x) Ls[e] = F.L[e];
+    }
     Lf = Ls;
   }
   // h' = Q^T h = H_p .. H_1 h

@@ -699,7 +699,7 @@ k_refine_update(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
                 int XS, int ZS, int M1S, int32_t* __restrict__ st_all, double gamma_scale) {
   const int b = blockIdx.x;
   if (st_all[b] != NYS_OK) return;
-  const Inst I = insts[b];
+  const Inst& I = insts[b];   // a reference: I.v[tid] would copy the struct to local memory
   const Lset LS = lsets[I.lset];
   const int m = I.m, p = I.p, me = LS.m_eff, M1 = me + 1;
   const double* W = W_all + LS.w_off;
@@ -707,22 +707,41 @@ k_refine_update(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   __shared__ double acc[kM1Max + 1];
   __shared__ T h[kM1Max + 1], dx[kM1Max + 1], red[40];
   __shared__ T cr[2], dl[2];
+  __shared__ double xsh[kM1Max + 3];   // x = (omega, b, lambda)
   double* xb = xs + (int64_t)b * XS;
   const double* C0 = cws + (int64_t)b * 2 * M1S;
   const double* C1 = C0 + M1S;
+  // the stored factor L into shared memory first: its loads overlap the rest
+  const FacView<T> F = fac_view(const_cast<T*>(fac_all) + (int64_t)b * facs, M1);
+  extern __shared__ __align__(16) unsigned char upd_raw[];   // the factor L, N2 x N2
+  T* Ls = reinterpret_cast<T*>(upd_raw);
+  {
+    const int ne = (M1 - p) * (M1 - p);
+#pragma unroll 4
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) Ls[e] = F.L[e];
+  }
+  for (int j = threadIdx.x; j < XS; j += blockDim.x) xsh[j] = xb[j];
   for (int j = threadIdx.x; j <= m; j += blockDim.x) {
     double s = 0.0;
     for (int q = 0; q < I.rslot_count; ++q) s += part[slot_off[I.rslot_begin + q] + j];
     acc[j] = s;
   }
   __syncthreads();
-  const double lam0 = xb[XS - 2], lam1 = (p == 2) ? xb[XS - 1] : 0.0;
+  const double lam0 = xsh[XS - 2], lam1 = (p == 2) ? xsh[XS - 1] : 0.0;
   for (int k = threadIdx.x; k < M1; k += blockDim.x) {
     double s;
     if (k < me) {
-      s = 0.0;
-      for (int j = 0; j < m; ++j) s += W[k * m + j] * acc[j];
-      s = gamma * s - xb[k];
+      // two interleaved partial sums (the DFMA chain halved)
+      double s0 = 0.0, s1 = 0.0;
+      const double* wk = W + k * m;
+      int j = 0;
+#pragma unroll 4
+      for (; j + 1 < m; j += 2) {
+        s0 += wk[j] * acc[j];
+        s1 += wk[j + 1] * acc[j + 1];
+      }
+      if (j < m) s0 += wk[j] * acc[j];
+      s = gamma * (s0 + s1) - xsh[k];
     } else {
       s = gamma * acc[m];
     }
@@ -733,30 +752,42 @@ k_refine_update(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   if (threadIdx.x < p) {
     const double* Ck = threadIdx.x == 0 ? C0 : C1;
     double s = I.v[threadIdx.x];
-    for (int k = 0; k < me; ++k) s -= Ck[k] * xb[k];
-    s -= Ck[me] * xb[XS - 3];
+    for (int k = 0; k < me; ++k) s -= Ck[k] * xsh[k];
+    s -= Ck[me] * xsh[XS - 3];
     cr[threadIdx.x] = (T)s;
   }
   __syncthreads();
-  const FacView<T> F = fac_view(const_cast<T*>(fac_all) + (int64_t)b * facs, M1);
-  extern __shared__ __align__(16) unsigned char upd_raw[];   // the factor L, N2 x N2
-  kkt_apply(F, M1, p, h, cr, dx, dl, red, reinterpret_cast<T*>(upd_raw));
+  kkt_apply(F, M1, p, h, cr, dx, dl, red, Ls, true);
   for (int k = threadIdx.x; k < M1; k += blockDim.x) {
     const int slot = (k < me) ? k : XS - 3;
-    xb[slot] += (double)dx[k];
+    const double v = xsh[slot] + (double)dx[k];
+    xsh[slot] = v;
+    xb[slot] = v;
   }
   if (threadIdx.x == 0) {
-    xb[XS - 2] += (double)dl[0];
-    if (p == 2) xb[XS - 1] += (double)dl[1];
+    xsh[XS - 2] += (double)dl[0];
+    xb[XS - 2] = xsh[XS - 2];
+    if (p == 2) {
+      xsh[XS - 1] += (double)dl[1];
+      xb[XS - 1] = xsh[XS - 1];
+    }
   }
   __syncthreads();
   double* zb = zs + (int64_t)b * ZS;
   for (int j = threadIdx.x; j <= m; j += blockDim.x) {
     double s = 0.0;
     if (j < m) {
-      for (int k = 0; k < me; ++k) s += W[k * m + j] * xb[k];
+      double s0 = 0.0, s1 = 0.0;
+      int k = 0;
+#pragma unroll 4
+      for (; k + 1 < me; k += 2) {
+        s0 += W[k * m + j] * xsh[k];
+        s1 += W[(k + 1) * m + j] * xsh[k + 1];
+      }
+      if (k < me) s0 += W[k * m + j] * xsh[k];
+      s = s0 + s1;
     } else {
-      s = xb[XS - 3];
+      s = xsh[XS - 3];
     }
     zb[j] = s;
   }
@@ -1173,6 +1204,8 @@ cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W,
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
+  // x is staged in kM1Max + 3 doubles of shared memory (mixed contexts: m_max <= kMMax)
+  if (XS > kM1Max + 3) return cudaErrorInvalidValue;
   // shared memory for the factor L (N2 = m_eff + 1 - p <= m_max)
   const size_t lsm = (size_t)m_max * m_max * (fac64 ? sizeof(double) : sizeof(float));
   if (fac64) {
