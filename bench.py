@@ -40,9 +40,9 @@ UNIT = "solves/s"
 LAG_U = 80.0   # kernel values exp(-u) with u > 80 (< 2e-35) are treated as zero
 # DRAM bytes (read + write) of one k_assemble_band launch per instance of the
 # metric family, from an ncu capture of the current kernel at 512 instances
-# (None once the kernel changes without a new capture).  The unit Grams it
-# writes stay in L2 during the launch.
-BAND_DRAM_BYTES_PER_INSTANCE = None
+# (527.1 KB + 0 B; None once the kernel changes without a new capture).  The
+# unit Grams it writes stay in L2 during the launch.
+BAND_DRAM_BYTES_PER_INSTANCE = (527104 + 0) / 512
 
 
 def parse():
@@ -449,7 +449,8 @@ def side_measurements(args, probs, bt, value, ws, local, stream, flush, peaks_ou
         t = max(1e-6, solve1 - solve0)
         ach = ref_fl / (t * 1e-3) / 1e12
         rows["refinement_pass"] = {
-            "kernels": "k_refine_rows + k_refine_update", "ms": t,
+            "kernels": "k_refine_band (k_refine_rows for unplanned instances) + k_refine_update",
+            "ms": t,
             "flop_count": "4m per row (residual and its projection), FP64-accurate (float-float)",
             "achieved_tflops": ach, "frac_of_dfma": ach / dfma, "frac_of_ffma": ach / ffma}
 
