@@ -433,15 +433,17 @@ template <int NT, bool kG>
 __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1))
 k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict__ W_all,
             float* __restrict__ W32_all, double* __restrict__ lam_all, double tau, int allow_chol,
-            int m_lo, int m_hi, BigSet big, const float* __restrict__ lag) {
+            int m_lo, int m_hi, BigSet big, const float* __restrict__ lag, int fb_only) {
   // the grid covers every slot; inactive slots (instances that share another
   // instance's set) return at once, so a captured graph stays valid when an
   // update changes which instances share
   const int L = kG ? big.ids[blockIdx.x] : blockIdx.x;
   const Lset S = lsets[L];
   // one launch per landmark-count class (m_lo, m_hi], each with shared memory
-  // for its own largest m
+  // for its own largest m; fb_only: only the sets that k_setup_eig_f32 handed
+  // over (m_eff = -1), by the FP64 Jacobi route
   if (!S.active || S.m <= m_lo || S.m > m_hi) return;
+  if (fb_only && S.m_eff != -1) return;
   const int m = S.m;
   const int N = m + (m & 1);  // even player count; index m (if present) is a bye
   const int ld = m + 1;
@@ -557,7 +559,7 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict_
   // the correction E W0 in FP32, whose relative error leaves W exact to ~1e-13.
   // Used when lambda_min > 1e-5 lambda_max (nothing truncated) and |E| <= 1e-5;
   // otherwise the FP64 Jacobi below.
-  if (!kG && !allow_chol) {
+  if (!kG && !allow_chol && !fb_only) {
     const int ldf = N + 1;
     float2* Om = reinterpret_cast<float2*>(A);   // Omega, then T: m x ld float-float
     float* Af = reinterpret_cast<float*>(V);     // N x ldf, upper triangle; then G
@@ -749,6 +751,155 @@ k_setup_lag(const Lset* __restrict__ lsets, float* __restrict__ lag) {
   }
 }
 
+// MIXED route for the large landmark counts on a compact shared-memory area
+// (two CTAs per SM where the FP64 fallback's area would hold one): Omega's
+// upper triangle and V as in k_setup_eig's FP32 route, Omega's float-float
+// entries read from the lag table by column blocks, T = U^T Omega kept in the
+// set's W area (global, L2-resident; W overwrites it at the end) and read back
+// by row blocks.  Sets the route cannot take (nothing truncated: lambda_min >
+// 1e-5 lambda_max, |E| <= 1e-5; the lag table present) get m_eff = -1 and are
+// factored by k_setup_eig's FP64 route in a second launch (fb_only).
+constexpr int kF32Blk = 8;   // columns of Omega / rows of T staged per block
+constexpr int kF32cThreads = 256;
+__host__ __device__ inline size_t f32c_smem_bytes(int m) {
+  const int N = m + (m & 1);
+  return 4 * (size_t)(N + m) * (N + 1) + 16 + 8 * (size_t)kF32Blk * m + 16 + 8 * (size_t)(N + 32) +
+         4 * (size_t)(2 * m);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 2)
+k_setup_eig_f32(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict__ W_all,
+                float* __restrict__ W32_all, double* __restrict__ lam_all, int m_lo, int m_hi,
+                const float* __restrict__ lag) {
+  const int L = blockIdx.x;
+  const Lset S = lsets[L];
+  if (!S.active || S.m <= m_lo || S.m > m_hi) return;
+  const int m = S.m, N = m + (m & 1), ldf = N + 1, tid = threadIdx.x, nt = blockDim.x;
+  extern __shared__ __align__(16) unsigned char f32c_raw[];
+  float* Af = reinterpret_cast<float*>(f32c_raw);   // N x ldf, upper triangle; then G (m x m)
+  float* Vf = Af + N * ldf;                          // m x ldf
+  // (N + m)(N + 1) floats end on a 4-byte boundary for odd m: align the float2 scratch
+  float2* scr = reinterpret_cast<float2*>(
+      (reinterpret_cast<uintptr_t>(Vf + m * ldf) + 15) & ~static_cast<uintptr_t>(15));   // kF32Blk x m
+  double* cs = reinterpret_cast<double*>(
+      (reinterpret_cast<uintptr_t>(scr + kF32Blk * m) + 15) & ~static_cast<uintptr_t>(15));
+  double* red = cs + N;
+  int* perm = reinterpret_cast<int*>(red + 32);
+  int* idx = perm + m;
+  for (int j = tid; j < m; j += nt) idx[j] = lm_idx[S.lm_off + j];
+  __syncthreads();
+  double* Wl = W_all + S.w_off;
+  float* W32l = W32_all + S.w_off;
+  const float* lagS = lag + S.lag_off;
+  auto omega = [&](int j, int l) -> float2 {
+    const int k = abs(idx[j] - idx[l]);
+    return k <= S.K ? make_float2(lagS[6 * k], lagS[6 * k + 1]) : make_float2(0.f, 0.f);
+  };
+  bool done = false;
+  if (lag != nullptr) {
+    for (int e = tid; e < m * m; e += nt) {
+      const int j = e / m, l = e % m;
+      if (j <= l) Af[j * ldf + l] = omega(j, l).x;
+    }
+    if (N > m)
+      for (int i = tid; i < N; i += nt) Af[i * ldf + m] = 0.f;
+    __syncthreads();
+    float4* prm = reinterpret_cast<float4*>(cs);
+    float* redf = reinterpret_cast<float*>(red);
+    bool ran = false;
+    if (N <= 64)
+      ran = jacobi_f32<NT / 32, 1, (64 + NT / 32 - 1) / (NT / 32)>(Af, Vf, ldf, m, prm, redf,
+                                                                   1e-13, kMaxSweeps, 1e-9);
+    else
+      ran = jacobi_f32<NT / 32, 2, (kMMax + (kMMax & 1) + NT / 32 - 1) / (NT / 32)>(Af, Vf, ldf, m, prm, redf,
+                                                                          1e-13, kMaxSweeps, 1e-9);
+    if (ran) {
+      sort_desc(Af, ldf, m, perm);
+      if (tid == 0) {
+        const double lmax = Af[perm[0] * ldf + perm[0]];
+        const double lmin = Af[perm[m - 1] * ldf + perm[m - 1]];
+        red[0] = (lmin > 1e-5 * lmax && lmin > 0.0) ? 1.0 : 0.0;
+      }
+      __syncthreads();
+      const bool well = red[0] != 0.0;
+      __syncthreads();
+      if (well) {
+        float2* rsq = reinterpret_cast<float2*>(cs);
+        for (int k = tid; k < m; k += nt) {
+          const double l = Af[perm[k] * ldf + perm[k]];
+          const double r = 1.0 / sqrt(l);
+          const float h = (float)r;
+          rsq[k] = make_float2(h, (float)(r - (double)h));
+          lam_all[(int64_t)L * kMLarge + k] = l;
+        }
+        __syncthreads();
+        // T = U^T Omega in float-float, by blocks of Omega's columns staged from
+        // the lag table, into the W area (m x m float2)
+        float2* Tg = reinterpret_cast<float2*>(Wl);
+        for (int j0 = 0; j0 < m; j0 += kF32Blk) {
+          const int jn = min(kF32Blk, m - j0);
+          for (int e = tid; e < m * jn; e += nt) scr[e] = omega(e / jn, j0 + e % jn);
+          __syncthreads();
+          for (int e = tid; e < m * jn; e += nt) {
+            const int k = e / jn, jj = e % jn;
+            const int c = perm[k];
+            float sh = 0.f, sl = 0.f;
+            for (int i = 0; i < m; ++i) ff_fma(sh, sl, Vf[i * ldf + c], scr[i * jn + jj]);
+            const float h = sh + sl;
+            Tg[k * m + j0 + jj] = make_float2(h, sl - (h - sh));
+          }
+          __syncthreads();
+        }
+        // M = T U by blocks of T's rows, E = D M D - I; G[k][perm[l]] = E_kl D_l
+        float* G = Af;
+        float emax = 0.f;
+        for (int k0 = 0; k0 < m; k0 += kF32Blk) {
+          const int kn = min(kF32Blk, m - k0);
+          for (int e = tid; e < kn * m; e += nt) scr[e] = Tg[k0 * m + e];
+          __syncthreads();
+          for (int e = tid; e < kn * m; e += nt) {
+            const int kk = e / m, l = e % m, k = k0 + kk;
+            const int c = perm[l];
+            float sh = 0.f, sl = 0.f;
+            for (int j = 0; j < m; ++j) ff_fma(sh, sl, Vf[j * ldf + c], scr[kk * m + j]);
+            float E;
+            if (k == l) {
+              const double r = (double)rsq[k].x + (double)rsq[k].y;
+              E = (float)(((double)sh + (double)sl) * r * r - 1.0);
+            } else {
+              E = (sh + sl) * rsq[k].x * rsq[l].x;
+            }
+            emax = fmaxf(emax, fabsf(E));
+            G[k * m + c] = E * rsq[l].x;
+          }
+          __syncthreads();
+        }
+        emax = (float)block_max((double)emax, red);
+        if (emax <= 1e-5f) {
+          for (int e = tid; e < m * m; e += nt) {
+            const int k = e / m, j = e % m;
+            float corr = 0.f;
+            for (int c = 0; c < m; ++c) corr = fmaf(G[k * m + c], Vf[j * ldf + c], corr);
+            const float u = Vf[j * ldf + perm[k]];
+            const float2 r = rsq[k];
+            const float ph = r.x * u;
+            const float pl = fmaf(r.x, u, -ph) + r.y * u - 0.5f * corr;
+            const double w = (double)ph + (double)pl;
+            Wl[e] = w;
+            W32l[e] = (float)w;
+          }
+          done = true;
+        }
+      }
+    }
+  }
+  if (tid == 0) {
+    lsets[L].m_eff = done ? m : -1;
+    if (done) lsets[L].omode = 0;
+  }
+}
+
 size_t setup_smem_bytes(int m) {
   const int N = m + (m & 1);
   return sizeof(double) * ((size_t)m * (m + 1) + eig_v_doubles(m) + N + 32) +
@@ -767,13 +918,13 @@ cudaError_t launch_lag(const Lset* lsets, int capacity, float* lag, cudaStream_t
 template <int NT>
 static cudaError_t launch_eig_class(Lset* lsets, int capacity, const int32_t* lm_idx, double* W,
                                     float* W32, double* lam, double tau, int allow_chol, int lo,
-                                    int hi, cudaStream_t st, const float* lag) {
+                                    int hi, cudaStream_t st, const float* lag, int fb_only = 0) {
   const size_t sm = setup_smem_bytes(hi);
   cudaError_t e = cudaFuncSetAttribute(k_setup_eig<NT, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   k_setup_eig<NT, false><<<capacity, NT, sm, st>>>(lsets, lm_idx, W, W32, lam, tau, allow_chol, lo,
-                                                   hi, BigSet(), lag);
+                                                   hi, BigSet(), lag, fb_only);
   return cudaGetLastError();
 }
 
@@ -864,7 +1015,21 @@ static cudaError_t launch_eig_sets(Lset* lsets, int capacity, const int32_t* lm_
     cudaError_t e;
     // few sets (no more than SMs): wider CTAs shorten each set's Jacobi rounds
     // (measured: a single m = 50 set, FP32 route, 512 threads 0.06 ms faster than 256)
-    if (few_sets && !allow_chol && sm <= 113 * 1024)
+    if (!allow_chol && lag != nullptr && sm > 113 * 1024 && f32c_smem_bytes(hi) <= 113 * 1024) {
+      // MIXED, large m: the compact FP32 route two CTAs per SM, then the FP64
+      // route for the sets it hands over (m_eff = -1; none when it succeeds)
+      const size_t sc = f32c_smem_bytes(hi);
+      e = cudaFuncSetAttribute(k_setup_eig_f32<kF32cThreads>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
+      if (e == cudaSuccess) {
+        k_setup_eig_f32<kF32cThreads><<<capacity, kF32cThreads, sc, st>>>(lsets, lm_idx, W, W32, lam,
+                                                                          lo, hi, lag);
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess)
+        e = launch_eig_class<1024>(lsets, capacity, lm_idx, W, W32, lam, tau, allow_chol, lo, hi,
+                                   st, lag, 1);
+    } else if (few_sets && !allow_chol && sm <= 113 * 1024)
       e = launch_eig_class<512>(lsets, capacity, lm_idx, W, W32, lam, tau, allow_chol, lo, hi, st, lag);
     else if (sm > 113 * 1024)
       e = launch_eig_class<1024>(lsets, capacity, lm_idx, W, W32, lam, tau, allow_chol, lo, hi, st, lag);
@@ -877,7 +1042,7 @@ static cudaError_t launch_eig_sets(Lset* lsets, int capacity, const int32_t* lm_
   }
   if (big.n > 0) {   // landmark counts above kMMax: global workspace
     k_setup_eig<1024, true><<<big.n, 1024, 0, st>>>(lsets, lm_idx, W, W32, lam, tau, allow_chol,
-                                                     kMMax, kMLarge, big, nullptr);
+                                                     kMMax, kMLarge, big, nullptr, 0);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
