@@ -48,7 +48,10 @@ typedef enum {
   NYS_EPRECISION = -8,  /* per instance, MIXED: landmark kernel too ill-conditioned
                            for the FP32 factor (kept lambda_min < 1e-7 lambda_max);
                            solve that instance with NYS_FP64                   */
-  NYS_ESTATE = -9       /* call out of order (e.g. solve before assemble)       */
+  NYS_ESTATE = -9,      /* call out of order (e.g. solve before assemble)       */
+  NYS_EBOUNDS = -10     /* per instance, library built with NYS_DEBUG_CHECKS
+                           only: a kernel's index check failed and the access
+                           was skipped (the release build carries no checks)  */
 } nys_status;
 
 /* NYS_MIXED: FP32 assembly, FP32 H and Cholesky factor, float-float residual

@@ -12,6 +12,7 @@ from . import build as _build
 NYS_OK, NYS_EINVAL, NYS_ENOMEM, NYS_ECUDA = 0, -1, -2, -3
 NYS_ENOTSPD, NYS_ENOCONV, NYS_ENONFINITE, NYS_ETIMEOUT = -4, -5, -6, -7
 NYS_EPRECISION, NYS_ESTATE = -8, -9
+NYS_EBOUNDS = -10   # builds with NYS_DEBUG_CHECKS only
 NYS_FP64, NYS_MIXED, NYS_MIXED_F64F = 0, 1, 2
 NYS_ASM_AUTO, NYS_ASM_SIMT, NYS_ASM_TUNE, NYS_ASM_TC = 0, 1, 2, 3
 NYS_COEF_TABLE, NYS_COEF_LIN, NYS_COEF_POLY_NL = 0, 1, 2

@@ -530,6 +530,7 @@ const char* nys_status_str(int32_t s) {
     case NYS_ETIMEOUT: return "device wait timed out";
     case NYS_EPRECISION: return "landmark kernel too ill-conditioned for the mixed path";
     case NYS_ESTATE: return "call out of order";
+    case NYS_EBOUNDS: return "index check failed (debug build)";
     default: return "unknown status";
   }
 }

@@ -268,7 +268,7 @@ k_assemble_band(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
       sincosf((float)be, &S32, &C32);
     }
     __syncwarp();
-    bool bad = false;
+    bool bad = false, dbad = false;
     int wlo = 0, whi = 0;                              // unit landmarks [wlo, whi) of the window
     float sn = 0.f, cs = 1.f;                          // sin, cos of theta at the lane's next row
     for (int row0 = r0, win = 0; row0 < r1; row0 += W, ++win) {
@@ -280,9 +280,13 @@ k_assemble_band(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
       // table position of lane 0's first row per column: kappa(i - s_j) sits at
       // Kt + i - idx_j; empty columns read the zero block at ntab
       int base[kBandLm];
+      bool tab_ok = true;   // every table read inside the warp's table (debug builds)
 #pragma unroll
-      for (int j = 0; j < kBandLm; ++j)
+      for (int j = 0; j < kBandLm; ++j) {
         base[j] = (j < A) ? Kt + row0 - uidx[wlo + j] : ntab;
+        tab_ok = tab_ok && NYS_IDX_OK(base[j] >= 0 && base[j] + W <= kBandTabCap);
+      }
+      if (!tab_ok) { dbad = true; break; }
       // exact argument every 64 rows per lane (every 8 windows below 256
       // rows), rotations by 32 dth in between (a rotation adds about one FP32
       // rounding to sin and cos)
@@ -319,9 +323,15 @@ k_assemble_band(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         const int ju = (j < kBandLm) ? ((j < A) ? wlo + j : -1) : Au + (j - kBandLm);
         const int lu = (l < kBandLm) ? ((l < A) ? wlo + l : -1) : Au + (l - kBandLm);
         if (ju < 0 || lu < 0) continue;
+        if (!NYS_IDX_OK(ju <= lu && lu < M2u)) { dbad = true; continue; }
         band_acc(&Gu[ju * M2u - ju * (ju - 1) / 2 + (lu - ju)], acc[p]);
       }
       __syncwarp();   // Gu entries move between lanes from one window to the next
+    }
+    dbad = __any_sync(0xffffffffu, dbad);
+    if (dbad) {
+      if (lane == 0) atomicExch(err, kErrBounds);
+      continue;
     }
     if (bad) {
       if (lane == 0) atomicExch(err, 2);

@@ -8,6 +8,21 @@
 
 namespace nys {
 
+// Index checks of the debug build (compiled with NYS_DEBUG_CHECKS, see
+// build.build(debug=True)): NYS_IDX_OK(cond) is the condition there and the
+// constant true otherwise, so the release kernels carry no check.  A failed
+// check skips its access and is reported per instance as NYS_EBOUNDS (the
+// assembly through its error word, value kErrBounds; the setup through
+// m_eff = kMeffBounds).
+#ifdef NYS_DEBUG_CHECKS
+#define NYS_IDX_OK(cond) (cond)
+#else
+#define NYS_IDX_OK(cond) true
+#endif
+constexpr int kErrBounds = 3;
+constexpr int kMeffBounds = -2;
+
+
 constexpr int kMMax = NYS_M_MAX_MIXED;    // landmarks, shared-memory kernels
 constexpr int kMLarge = NYS_M_MAX;        // landmarks, global-workspace kernels (FP64)
 constexpr int kNtRowState = 5;            // Newton row state: Fy, d, f_y, f_u + delta, e f_yu

@@ -142,11 +142,11 @@ k_refine_band(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   float2* uacc = zsh + kM1Max;                                    // [kRbWarps][kM1Max]
   int* sidx = reinterpret_cast<int*>(uacc + kRbWarps * kM1Max);   // [kMMax]
   float2* scr = reinterpret_cast<float2*>(sidx + kMMax) + (threadIdx.x >> 5) * kRbMaxW;   // s_i of a window
-  __shared__ int s_item, s_bad;
+  __shared__ int s_item, s_bad, s_dbad;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   for (;;) {
-    if (tid == 0) { s_item = atomicAdd(counter, 1); s_bad = 0; }
+    if (tid == 0) { s_item = atomicAdd(counter, 1); s_bad = 0; s_dbad = 0; }
     __syncthreads();
     const int w = s_item;
     if (w >= nwork) break;
@@ -212,6 +212,7 @@ k_refine_band(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         }
         int base[kRbLm];
         ff2 zr[kRbLm / 2], acc[kRbLm / 2];
+        bool tab_ok = true;   // every table read inside the CTA's table (debug builds)
 #pragma unroll
         for (int j = 0; j < kRbLm; j += 2) {
           float2 z[2];
@@ -219,10 +220,15 @@ k_refine_band(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
           for (int h = 0; h < 2; ++h) {
             const bool in = j + h < A;
             base[j + h] = in ? Kt + row0 - sidx[wlo + j + h] : ntab;
+            tab_ok = tab_ok && NYS_IDX_OK(base[j + h] >= 0 && base[j + h] + W <= kRbTabCap);
             z[h] = in ? zsh[wlo + j + h] : make_float2(0.f, 0.f);
           }
           zr[j >> 1] = ff2{make_float2(z[0].x, z[1].x), make_float2(z[0].y, z[1].y)};
           acc[j >> 1] = ff2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        }
+        if (!tab_ok) {
+          if (lane == 0) s_dbad = 1;
+          break;
         }
         ff sum_s = {0.f, 0.f};
         rb_window(acc, sum_s, tab, base, zr, w1zb, RK, row0, r1, R, lane, scr);
@@ -239,7 +245,7 @@ k_refine_band(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
         rb_rs_level<2>(v, lane);
         rb_rs_level<1>(v, lane);
         const int col = (lane < A) ? wlo + lane : (lane == kRbLm ? m : -1);
-        if (col >= 0) {
+        if (col >= 0 && NYS_IDX_OK(col <= m)) {
           ff add = v[0];
           if (lane == kRbLm) add = ff_mul_ff(RK.w1, add);     // acc_b = w1 sum_i s_i
           const float2 cur = ua[col];
@@ -251,6 +257,7 @@ k_refine_band(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     }
     __syncthreads();
     if (tid == 0 && !skip && (!fits || s_bad)) st_all[wk.inst] = NYS_ESTATE;
+    if (tid == 0 && !skip && s_dbad) st_all[wk.inst] = NYS_EBOUNDS;
     double* out = part + slot_off[wk.slot];
     for (int j = tid; j <= m; j += kRbThreads) {
       double v = 0.0;

@@ -250,14 +250,17 @@ __device__ __forceinline__ void f32_block(float* A, int e0, int e1, int e2, int 
 // players move one slot (k -> k+1 over 1..N-1, slot 0 fixed), two shuffles per
 // register row, so every lane keeps rotating its own pair of slots; after a
 // whole sweep each player is back in its own slot and V (m rows, ldf) is
-// written to Vout in player order.  Stopping rule as jacobi_sweeps.  Returns
-// false (nothing done) when N > NW U (not enough register rows).
+// written to Vout in player order.  Stopping rule as jacobi_sweeps.  Returns 1;
+// 0 (nothing done) when N > NW U (not enough register rows); -1 when an index
+// check of a debug build failed.
 template <int NW, int HB, int U>
-__device__ bool jacobi_f32(float* A, float* Vout, int ldf, int m, float4* prm, float* red,
-                           double tol, int max_sweeps, double stall) {
+__device__ int jacobi_f32(float* A, float* Vout, int ldf, int m, float4* prm, float* red,
+                          double tol, int max_sweeps, double stall) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int N = m + (m & 1), half = N >> 1, nfold = (half + 1) >> 1;
-  if (N > NW * U || half > 32 * HB) return false;
+  if (N > NW * U || half > 32 * HB) return 0;
+  __shared__ int s_jbad;
+  if (threadIdx.x == 0) s_jbad = 0;
   float vf[U][HB], vs[U][HB];
 #pragma unroll
   for (int u = 0; u < U; ++u)
@@ -333,7 +336,8 @@ __device__ bool jacobi_f32(float* A, float* Vout, int ldf, int m, float4* prm, f
           const float4 PR = up ? PA : PB;
           const int r1 = __float_as_int(PR.x) & 0xffff, r2 = __float_as_int(PR.y);
           const int c1 = __float_as_int(PC.x) & 0xffff, c2 = __float_as_int(PC.y);
-          if (ok)
+          if (ok && !NYS_IDX_OK(r1 < r2 && r2 < N && c1 < c2 && c2 < N)) s_jbad = 1;
+          else if (ok)
             f32_block(A, upk(r1, c1, ldf), upk(r1, c2, ldf), upk(r2, c1, ldf), upk(r2, c2, ldf),
                       PR.z, PR.w, PC.z, PC.w);
         }
@@ -411,7 +415,7 @@ __device__ bool jacobi_f32(float* A, float* Vout, int ldf, int m, float4* prm, f
       }
     }
   __syncthreads();
-  return true;
+  return s_jbad ? -1 : 1;
 }
 
 // doubles of k_setup_eig's V area: m (m+1), or (N + m)(N + 1) floats for odd m
@@ -587,14 +591,18 @@ k_setup_eig(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restrict_
     // FP32 sweeps reach off(A)^2 ~ 1e-13 tot(A)^2; the correction absorbs the rest
     // two slot pairs per lane (N > 64) only on the 512- and 1024-thread CTAs
     // (the launcher sends the FP32 route's classes above m = 64 there)
-    bool ran = false;
+    int jr = 0;
     if (N <= 64)
-      ran = jacobi_f32<NT / 32, 1, f32_vrows<NT, 1>()>(Af, Vf, ldf, m, prm, redf, 1e-13,
-                                                       kMaxSweeps, 1e-9);
+      jr = jacobi_f32<NT / 32, 1, f32_vrows<NT, 1>()>(Af, Vf, ldf, m, prm, redf, 1e-13,
+                                                      kMaxSweeps, 1e-9);
     else if constexpr (NT >= 512)
-      ran = jacobi_f32<NT / 32, 2, f32_vrows<NT, 2>()>(Af, Vf, ldf, m, prm, redf, 1e-13,
-                                                       kMaxSweeps, 1e-9);
-    if (ran) {
+      jr = jacobi_f32<NT / 32, 2, f32_vrows<NT, 2>()>(Af, Vf, ldf, m, prm, redf, 1e-13,
+                                                      kMaxSweeps, 1e-9);
+    if (jr < 0) {
+      if (tid == 0) lsets[L].m_eff = kMeffBounds;
+      return;
+    }
+    if (jr > 0) {
       sort_desc(Af, ldf, m, perm);
       if (tid == 0) {
         const double lmax = Af[perm[0] * ldf + perm[0]];
@@ -807,14 +815,18 @@ k_setup_eig_f32(Lset* lsets, const int32_t* __restrict__ lm_idx, double* __restr
     __syncthreads();
     float4* prm = reinterpret_cast<float4*>(cs);
     float* redf = reinterpret_cast<float*>(red);
-    bool ran = false;
+    int jr = 0;
     if (N <= 64)
-      ran = jacobi_f32<NT / 32, 1, (64 + NT / 32 - 1) / (NT / 32)>(Af, Vf, ldf, m, prm, redf,
-                                                                   1e-13, kMaxSweeps, 1e-9);
+      jr = jacobi_f32<NT / 32, 1, (64 + NT / 32 - 1) / (NT / 32)>(Af, Vf, ldf, m, prm, redf,
+                                                                  1e-13, kMaxSweeps, 1e-9);
     else
-      ran = jacobi_f32<NT / 32, 2, (kMMax + (kMMax & 1) + NT / 32 - 1) / (NT / 32)>(Af, Vf, ldf, m, prm, redf,
-                                                                          1e-13, kMaxSweeps, 1e-9);
-    if (ran) {
+      jr = jacobi_f32<NT / 32, 2, (kMMax + (kMMax & 1) + NT / 32 - 1) / (NT / 32)>(
+          Af, Vf, ldf, m, prm, redf, 1e-13, kMaxSweeps, 1e-9);
+    if (jr < 0) {
+      if (tid == 0) lsets[L].m_eff = kMeffBounds;
+      return;
+    }
+    if (jr > 0) {
       sort_desc(Af, ldf, m, perm);
       if (tid == 0) {
         const double lmax = Af[perm[0] * ldf + perm[0]];

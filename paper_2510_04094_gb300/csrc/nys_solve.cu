@@ -59,7 +59,9 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   const int st0 = (st_init[b] != NYS_OK) ? st_init[b]
                   : (om && (sizeof(T) == sizeof(float) || asm_err != nullptr)) ? NYS_EPRECISION
                   : (asm_err != nullptr && *asm_err == 2) ? NYS_ESTATE   // stale band plan
+                  : (asm_err != nullptr && *asm_err == kErrBounds) ? NYS_EBOUNDS
                   : (asm_err != nullptr && *asm_err != 0) ? NYS_ETIMEOUT
+                  : (LS.m_eff == kMeffBounds) ? NYS_EBOUNDS
                   : (LS.m_eff + 1 < I.p) ? NYS_ENOTSPD : NYS_OK;
   if (st0 != NYS_OK) {  // no solution: zero x and z, report the status
     for (int k = threadIdx.x; k < XS; k += blockDim.x) xs[(int64_t)b * XS + k] = 0.0;
@@ -102,9 +104,14 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   for (int e = threadIdx.x; e < (Dg + 1) * ldg; e += blockDim.x) Gs[e] = T(0);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  bool dbg_bad = false;   // a slot whose column range leaves G (debug builds)
   for (int q = 0; q < (kBig ? 1 : I.slot_count); ++q) {
     const double* P = part + slot_off[I.slot_begin + q];
     const int jlo = (int)P[0] < 0 ? 0 : (int)P[0], A = (int)P[1], M2l = A + 2;
+    if (!NYS_IDX_OK(A >= 0 && jlo + A <= Dg)) {
+      dbg_bad = true;
+      continue;
+    }
     // a warp per packed row a (local columns bb >= a start at a M2l - a (a-1) / 2);
     // row A + 1 holds only the (r, r) entry, which is not needed
     for (int a = warp; a <= A; a += nw) {
@@ -451,6 +458,7 @@ k_solve(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
 #pragma unroll
     for (int k = 0; k < 4; ++k) fin = fin && (k >= p || isfinite(lam[k]));
     if (ok && !fin) st = NYS_ENONFINITE;
+    if (dbg_bad) st = NYS_EBOUNDS;
     st_all[b] = st;
   }
 }
@@ -717,6 +725,12 @@ k_refine_update(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   T* Ls = reinterpret_cast<T*>(upd_raw);
   {
     const int ne = (M1 - p) * (M1 - p);
+    unsigned dyn = 0;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    if (!NYS_IDX_OK((size_t)ne * sizeof(T) <= dyn)) {
+      if (threadIdx.x == 0) st_all[b] = NYS_EBOUNDS;
+      return;
+    }
 #pragma unroll 4
     for (int e = threadIdx.x; e < ne; e += blockDim.x) Ls[e] = F.L[e];
   }

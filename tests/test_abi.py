@@ -198,3 +198,16 @@ def test_peak_probe_library_exports_its_header(abi, tmp_path):
                  '  return f ? 0 : 1;\n}\n')
     subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-c", "-I", os.path.join(ROOT, "include"),
                     str(c), "-o", str(tmp_path / "peak.o")], check=True, capture_output=True)
+
+
+def test_debug_build_links_and_exports_the_same_entry_points():
+    """build(debug=True) (NYS_DEBUG_CHECKS) compiles every translation unit and
+    links a library with the release library's entry points."""
+    from paper_2510_04094_gb300 import build
+    path = build.build(debug=True)
+    assert path.endswith("libnys_debug.so") and os.path.exists(path)
+    lib = C.CDLL(path)
+    for name in _declared():
+        assert hasattr(lib, name), name
+    status = open(os.path.join(ROOT, "include", "nys.h")).read()
+    assert re.search(r"NYS_EBOUNDS\s*=\s*-10", status)
