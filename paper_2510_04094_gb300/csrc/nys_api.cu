@@ -155,6 +155,7 @@ struct nys_ctx {
   int nt_tiles = 4;            // shared tiles of the Newton row pass (6 with a beta term)
   bool solved = false, assembled = false;
   std::vector<nys_instance> shape;        // p, n, m, kind per instance (for update checks)
+  std::vector<uint8_t> lm_dflt;           // 1: instance b's landmarks are default_landmarks(n, m)
   std::vector<int32_t> h_lm;               // landmark indices (host)
   std::vector<int64_t> h_lm_off;
   std::vector<Inst> h_inst;
@@ -360,6 +361,7 @@ static int32_t pack_all(nys_ctx* c, const nys_instance* q, bool first) {
   if (first) {
     c->h_lm.clear();
     c->h_lm_off.assign(B, 0);
+    c->lm_dflt.assign(B, 0);
   }
   c->h_tab.clear();
   std::map<std::vector<int64_t>, int> keys;
@@ -381,6 +383,10 @@ static int32_t pack_all(nys_ctx* c, const nys_instance* q, bool first) {
     if (first) {
       c->h_lm_off[b] = (int64_t)c->h_lm.size();
       c->h_lm.insert(c->h_lm.end(), lm.begin(), lm.end());
+      bool dflt = true;
+      for (int j = 0; j < s.m && dflt; ++j)
+        dflt = lm[j] == (int32_t)(((int64_t)j * (s.n - 1) + (s.m - 1) / 2) / (s.m - 1));
+      c->lm_dflt[b] = dflt ? 1 : 0;
     } else {
       if (std::memcmp(lm.data(), c->h_lm.data() + c->h_lm_off[b], sizeof(int32_t) * s.m) != 0)
         return fail(NYS_EINVAL, "nys_update: instance %d changed its landmarks", b);
@@ -433,6 +439,8 @@ static int32_t repack_same_sets(nys_ctx* c, const nys_instance* q) {
     const nys_instance& o = c->shape[b];
     if (o.p != s.p || o.n != s.n || o.m != s.m || o.kind != s.kind || o.bc != s.bc)
       return fail(NYS_EINVAL, "nys_update: instance %d changed p, n, m, kind or bc", b);
+    // default landmarks of an unchanged (n, m) over stored defaults: equal by construction
+    if (!s.landmarks && c->lm_dflt[b]) continue;
     int32_t dflt[NYS_M_MAX];
     const int32_t* lm = s.landmarks;
     if (!lm) {
