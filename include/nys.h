@@ -46,7 +46,12 @@ typedef enum {
   NYS_ETIMEOUT = -7,    /* per instance: a bounded device wait gave up (the
                            tensor-core assembly); the GPU context stays usable */
   NYS_EPRECISION = -8,  /* per instance, MIXED: landmark kernel too ill-conditioned
-                           for the FP32 factor (kept lambda_min < 1e-7 lambda_max);
+                           for the FP32 factor (kept lambda_min < 1e-7 lambda_max),
+                           or refinement that leaves an estimated error above
+                           1e-4 of (omega, b): rho * d, d the last pass's
+                           max|correction| / max|x|, rho the passes' contraction
+                           (the first pass's d, else the ratio of the last two
+                           d; not checked when refine_steps is 0);
                            solve that instance with NYS_FP64                   */
   NYS_ESTATE = -9,      /* call out of order (e.g. solve before assemble)       */
   NYS_EBOUNDS = -10     /* per instance, library built with NYS_DEBUG_CHECKS

@@ -43,7 +43,8 @@ cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W,
                           double* part, const int64_t* slot_off, const void* fac, int64_t facs,
                           double* xs, double* zs, const double* cws, int XS, int ZS, int M1S,
                           int32_t* st, double gamma_scale, int batch, int m_max, int k_max,
-                          int num_sms, cudaStream_t s, int nrband = 0, bool fac64 = false);
+                          int num_sms, cudaStream_t s, int nrband, bool fac64, double* rcorr,
+                          int pass, bool last);
 cudaError_t launch_eval(const Inst* insts, const double* zs, int ZS, const int32_t* lm,
                         const double* tq, const int64_t* tq_off, int deriv, double* yq, int batch,
                         cudaStream_t s);
@@ -208,6 +209,7 @@ struct nys_ctx {
     return g;
   }
   DBuf<double> xs, zs, dzs, cws;
+  DBuf<double> rcorr;       // MIXED: each instance's last relative refinement correction
   DBuf<int32_t> st, stinit, counter, err;
   // Newton state
   DBuf<double> yaux, rowstate, nrm;
@@ -940,6 +942,7 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   A(c->zs.alloc((size_t)batch * c->ZS));
   A(c->dzs.alloc((size_t)batch * c->ZS));
   A(c->cws.alloc((size_t)batch * 2 * c->M1S));
+  if (c->fp32) A(c->rcorr.alloc(batch));
   if (c->any_lin && !c->fp32) A(c->adj.alloc((size_t)batch * grad_adj_stride(c->ZS)));
   A(c->st.alloc(batch));
   A(c->stinit.alloc(batch));
@@ -1156,7 +1159,8 @@ static int32_t solve_impl(nys_ctx* c, cudaStream_t s, double* x_out, int32_t* st
       CK(launch_refine(c->inst.p, c->lset.p, c->W.p, c->lag.p, c->rwork.p, c->nrwork, c->counter.p,
                        c->lm.p, c->tab.p, c->part.p, c->slot_off.p, c->fac.p, c->facs, c->xs.p, c->zs.p,
                        c->cws.p, c->XS, c->ZS, c->M1S, c->st.p, gscale, c->batch, c->m_max,
-                       c->k_max, c->num_sms, s, c->nrband, c->fac64));
+                       c->k_max, c->num_sms, s, c->nrband, c->fac64, c->rcorr.p, k,
+                       k == c->opt.refine_steps - 1));
   }
   if (x_out)
     CK(cudaMemcpyAsync(x_out, c->xs.p, sizeof(double) * c->batch * c->XS, cudaMemcpyDeviceToDevice, s));

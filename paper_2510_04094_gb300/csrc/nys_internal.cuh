@@ -20,6 +20,9 @@ namespace nys {
 #define NYS_IDX_OK(cond) true
 #endif
 constexpr int kErrBounds = 3;
+// Largest estimated error, relative to the solution (omega, b), that the mixed
+// path's last refinement pass may leave
+constexpr double kRefineTrust = 1e-4;
 constexpr int kMeffBounds = -2;
 
 

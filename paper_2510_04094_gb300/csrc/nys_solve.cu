@@ -704,7 +704,8 @@ k_refine_update(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
                 const double* __restrict__ W_all, const double* __restrict__ part,
                 const int64_t* __restrict__ slot_off, const T* __restrict__ fac_all, int64_t facs,
                 double* __restrict__ xs, double* __restrict__ zs, const double* __restrict__ cws,
-                int XS, int ZS, int M1S, int32_t* __restrict__ st_all, double gamma_scale) {
+                int XS, int ZS, int M1S, int32_t* __restrict__ st_all, double gamma_scale,
+                double* __restrict__ rcorr, int pass, int last) {
   const int b = blockIdx.x;
   if (st_all[b] != NYS_OK) return;
   const Inst& I = insts[b];   // a reference: I.v[tid] would copy the struct to local memory
@@ -772,11 +773,45 @@ k_refine_update(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   }
   __syncthreads();
   kkt_apply(F, M1, p, h, cr, dx, dl, red, Ls, true);
+  double dmax = 0.0, xmax = 0.0;   // largest correction and solution entry (omega, b)
   for (int k = threadIdx.x; k < M1; k += blockDim.x) {
     const int slot = (k < me) ? k : XS - 3;
     const double v = xsh[slot] + (double)dx[k];
     xsh[slot] = v;
     xb[slot] = v;
+    dmax = fmax(dmax, fabs((double)dx[k]));
+    xmax = fmax(xmax, fabs(v));
+  }
+  {
+    // Refinement trust.  d = max|dx| / max|x| over (omega, b) is this pass's
+    // relative correction.  A pass contracts the error by a factor rho that is
+    // about the relative error of the FP32 solve itself, i.e. the first pass's d,
+    // and, once two passes ran, the ratio of the last two corrections; the error
+    // left after the last pass is then about rho * d.  Above kRefineTrust the
+    // factor is too coarse (an ill-conditioned landmark kernel through the FP32
+    // Gram, e.g.; rho >= 1 means the passes diverge) and the instance reports
+    // NYS_EPRECISION instead of a solution that does not converge.
+    for (int o = 16; o > 0; o >>= 1) {
+      dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+      xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+    }
+    __shared__ double s_dx[kSolveThreads / 32], s_x[kSolveThreads / 32];
+    if ((threadIdx.x & 31) == 0) {
+      s_dx[threadIdx.x >> 5] = dmax;
+      s_x[threadIdx.x >> 5] = xmax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        dmax = fmax(dmax, s_dx[w]);
+        xmax = fmax(xmax, s_x[w]);
+      }
+      const double d = dmax > 0.0 ? dmax / xmax : 0.0;   // NaN / inf when x is 0 or not finite
+      const double prev = rcorr[b];
+      const double rho = pass == 0 ? d : (prev > 0.0 ? d / prev : (d > 0.0 ? 1.0 : 0.0));
+      rcorr[b] = d;
+      if (last && !(rho * d <= kRefineTrust)) st_all[b] = NYS_EPRECISION;
+    }
   }
   if (threadIdx.x == 0) {
     xsh[XS - 2] += (double)dl[0];
@@ -1193,7 +1228,7 @@ cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W,
                           const void* fac, int64_t facs, double* xs, double* zs, const double* cws,
                           int XS, int ZS, int M1S, int32_t* st, double gamma_scale, int batch,
                           int m_max, int k_max, int num_sms, cudaStream_t s, int nrband,
-                          bool fac64) {
+                          bool fac64, double* rcorr, int pass, bool last) {
   // the first nrband items: k_refine_band (queue counter[1]); the rest k_refine_rows
   cudaError_t e = cudaMemsetAsync(counter, 0, (nrband > 0 ? 2 : 1) * sizeof(int), s);
   if (e != cudaSuccess) return e;
@@ -1228,14 +1263,16 @@ cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W,
     if (e != cudaSuccess) return e;
     k_refine_update<double><<<batch, kSolveThreads, lsm, s>>>(insts, lsets, W, part, slot_off,
                                                                (const double*)fac, facs, xs, zs,
-                                                               cws, XS, ZS, M1S, st, gamma_scale);
+                                                               cws, XS, ZS, M1S, st, gamma_scale,
+                                                               rcorr, pass, last ? 1 : 0);
   } else {
     e = cudaFuncSetAttribute(k_refine_update<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)lsm);
     if (e != cudaSuccess) return e;
     k_refine_update<float><<<batch, kSolveThreads, lsm, s>>>(insts, lsets, W, part, slot_off,
                                                               (const float*)fac, facs, xs, zs, cws,
-                                                              XS, ZS, M1S, st, gamma_scale);
+                                                              XS, ZS, M1S, st, gamma_scale,
+                                                              rcorr, pass, last ? 1 : 0);
   }
   return cudaGetLastError();
 }

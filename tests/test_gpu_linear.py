@@ -154,6 +154,43 @@ def test_landmark_cap_wide_windows(api, precision):
     _check(api, _cap_m_batch(), precision)
 
 
+def test_mixed_large_m_fp64_fallback(api):
+    """MIXED sets with m >= 84 run the compact FP32 eigendecomposition; a landmark
+    kernel with lambda_min / lambda_max = 4.5e-6 (sigma = 2.3 landmark spacings) is
+    handed over to the FP64 Jacobi launch (m_eff as the oracle's), beside a
+    well-conditioned set of the same class (sigma = 1.2 spacings) that meets the
+    mixed bar.  The FP32 Gram projected through so ill-conditioned a kernel is too
+    coarse a preconditioner (measured: first corrections 4.5e-2 and 1.0 of the
+    solution, errors 2.7e-3 and 31 after one pass, growing with more), so the
+    refinement check reports NYS_EPRECISION for those instances instead of a
+    wrong solution, after one pass and after three; the FP64 path solves them."""
+    import torch
+    fam = ni.linear_family(3, n=2000, m=90, T=10.0, name="small", sub=41)
+    probs = []
+    for q, spc in zip(fam, (2.3, 1.2, 2.3)):
+        probs.append(dict(q, sigma=spc * (q["t1"] - q["t0"]) / (q["m"] - 1)))
+    for refine in (1, 3):
+        bt = api.Batch(probs, precision="mixed", refine_steps=refine)
+        x, st = bt.run()
+        torch.cuda.synchronize()
+        assert st.cpu().numpy().tolist() == [-8, 0, -8], refine
+        assert bt.m_eff().tolist() == [core.solve_linear(q)["m_eff"] for q in probs]
+        bt.close()
+    _check(api, [probs[1]], "mixed")
+    _check(api, probs, "fp64")
+
+
+def test_mixed_refinement_to_the_rounding_floor(api):
+    """Eight refinement passes bring the corrections of well-conditioned instances
+    down to FP64 rounding, where the ratio of the last two is about 1: the
+    refinement check's error estimate (that ratio times the last correction)
+    stays at rounding level and no instance is flagged.  The sigma = 2.4 landmark
+    spacings family (first corrections up to 4e-3 of the solution) passes too."""
+    _check(api, ni.cfg3(12, n_hi=4000), "mixed", refine=8)
+    wide = [dict(q, sigma=1.6 * q["sigma"]) for q in ni.m0(8, n=4000, m=50)]
+    _check(api, wide, "mixed", refine=8)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed-tc", "mixed-simt"])
 def test_cfg2_linear_full_size(api, precision):
     _check(api, [ni.cfg2_linear()], precision)
