@@ -39,10 +39,10 @@ METRIC = "batched ODE solves/s at n=1e4, m=50"
 UNIT = "solves/s"
 LAG_U = 80.0   # kernel values exp(-u) with u > 80 (< 2e-35) are treated as zero
 # DRAM bytes (read + write) of one k_assemble_band launch per instance of the
-# metric family, from an ncu capture of the current kernel at 512 instances
-# (527.1 KB + 0 B; None once the kernel changes without a new capture).  The
-# unit Grams it writes stay in L2 during the launch.
-BAND_DRAM_BYTES_PER_INSTANCE = (527104 + 0) / 512
+# metric family, from an ncu capture of the current kernel at 2048 instances
+# (1285.9 KB + 5.6 KB; None once the kernel changes without a new capture).
+# The unit Grams it writes stay in L2 during the launch.
+BAND_DRAM_BYTES_PER_INSTANCE = (1285888 + 5632) / 2048
 
 
 def parse():
