@@ -718,6 +718,8 @@ k_refine_update(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   __shared__ T cr[2], dl[2];
   __shared__ double xsh[kM1Max + 3];   // x = (omega, b, lambda)
   double* xb = xs + (int64_t)b * XS;
+  // the previous pass's relative correction, read early (used at the end)
+  const double prev_d = (threadIdx.x == 0 && pass > 0) ? rcorr[b] : 0.0;
   const double* C0 = cws + (int64_t)b * 2 * M1S;
   const double* C1 = C0 + M1S;
   // the stored factor L into shared memory first: its loads overlap the rest
@@ -773,45 +775,27 @@ k_refine_update(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
   }
   __syncthreads();
   kkt_apply(F, M1, p, h, cr, dx, dl, red, Ls, true);
-  double dmax = 0.0, xmax = 0.0;   // largest correction and solution entry (omega, b)
+  // largest correction (FP32) and solution entry (high word of |x|: the exponent
+  // and 20 mantissa bits, an integer max) over (omega, b), for the trust check
+  float dmax = 0.f;
+  int xhi = 0;
   for (int k = threadIdx.x; k < M1; k += blockDim.x) {
     const int slot = (k < me) ? k : XS - 3;
     const double v = xsh[slot] + (double)dx[k];
     xsh[slot] = v;
     xb[slot] = v;
-    dmax = fmax(dmax, fabs((double)dx[k]));
-    xmax = fmax(xmax, fabs(v));
+    dmax = fmaxf(dmax, fabsf((float)dx[k]));
+    xhi = max(xhi, __double2hiint(v) & 0x7fffffff);
   }
-  {
-    // Refinement trust.  d = max|dx| / max|x| over (omega, b) is this pass's
-    // relative correction.  A pass contracts the error by a factor rho that is
-    // about the relative error of the FP32 solve itself, i.e. the first pass's d,
-    // and, once two passes ran, the ratio of the last two corrections; the error
-    // left after the last pass is then about rho * d.  Above kRefineTrust the
-    // factor is too coarse (an ill-conditioned landmark kernel through the FP32
-    // Gram, e.g.; rho >= 1 means the passes diverge) and the instance reports
-    // NYS_EPRECISION instead of a solution that does not converge.
-    for (int o = 16; o > 0; o >>= 1) {
-      dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-      xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
-    }
-    __shared__ double s_dx[kSolveThreads / 32], s_x[kSolveThreads / 32];
-    if ((threadIdx.x & 31) == 0) {
-      s_dx[threadIdx.x >> 5] = dmax;
-      s_x[threadIdx.x >> 5] = xmax;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-        dmax = fmax(dmax, s_dx[w]);
-        xmax = fmax(xmax, s_x[w]);
-      }
-      const double d = dmax > 0.0 ? dmax / xmax : 0.0;   // NaN / inf when x is 0 or not finite
-      const double prev = rcorr[b];
-      const double rho = pass == 0 ? d : (prev > 0.0 ? d / prev : (d > 0.0 ? 1.0 : 0.0));
-      rcorr[b] = d;
-      if (last && !(rho * d <= kRefineTrust)) st_all[b] = NYS_EPRECISION;
-    }
+  for (int o = 16; o > 0; o >>= 1) {
+    dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    xhi = max(xhi, __shfl_xor_sync(0xffffffffu, xhi, o));
+  }
+  __shared__ float s_dx[kSolveThreads / 32];
+  __shared__ int s_xh[kSolveThreads / 32];
+  if ((threadIdx.x & 31) == 0) {
+    s_dx[threadIdx.x >> 5] = dmax;
+    s_xh[threadIdx.x >> 5] = xhi;
   }
   if (threadIdx.x == 0) {
     xsh[XS - 2] += (double)dl[0];
@@ -822,6 +806,25 @@ k_refine_update(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     }
   }
   __syncthreads();
+  if (threadIdx.x == 0) {
+    // Refinement trust.  d = max|dx| / max|x| over (omega, b) is this pass's
+    // relative correction.  A pass contracts the error by a factor rho that is
+    // about the relative error of the FP32 solve itself, i.e. the first pass's d,
+    // and, once two passes ran, the ratio of the last two corrections; the error
+    // left after the last pass is then about rho * d.  Above kRefineTrust the
+    // factor is too coarse (an ill-conditioned landmark kernel through the FP32
+    // Gram, e.g.; rho >= 1 means the passes diverge) and the instance reports
+    // NYS_EPRECISION instead of a solution that does not converge.
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      dmax = fmaxf(dmax, s_dx[w]);
+      xhi = max(xhi, s_xh[w]);
+    }
+    const double xmax = __hiloint2double(xhi, 0);
+    const double d = dmax > 0.f ? (double)dmax / xmax : 0.0;   // NaN / inf when x is 0 or not finite
+    const double rho = pass == 0 ? d : (prev_d > 0.0 ? d / prev_d : (d > 0.0 ? 1.0 : 0.0));
+    rcorr[b] = d;
+    if (last && !(rho * d <= kRefineTrust)) st_all[b] = NYS_EPRECISION;
+  }
   double* zb = zs + (int64_t)b * ZS;
   for (int j = threadIdx.x; j <= m; j += blockDim.x) {
     double s = 0.0;
