@@ -607,7 +607,9 @@ def main():
     probs = (rank_problems(rank, B, args.n, args.m) if args.workload == "metric"
              else ni.cfg3(B))
     bt = Batch(probs, precision=args.precision, assembly=args.assembly)
-    refine = 1 if args.precision == "mixed" else 0   # default refinement passes
+    # default refinement: one pass and the adaptive pass (launched for every
+    # batch; instances already converged skip it)
+    refine = 2 if args.precision == "mixed" else 0
     # setup (lag tables, eigendecomposition, condition rows), assembly, solve, 2 per
     # refinement pass (the band or row residual pass and the update)
     launches_per_step = 3 + 2 + 2 * refine

@@ -124,10 +124,12 @@ typedef struct {
 typedef struct {
   int32_t precision;     /* nys_precision.  MIXED: FP32 assembly and FP32 factor,
                             refined against FP64-accurate residuals.             */
-  int32_t refine_steps;  /* MIXED: residual passes after the first solve (0..8;
-                            default when negative: 1, which brings every initial
-                            value workload to <= 2e-7 of the FP64 solution; 2 if
-                            any instance has boundary values (NYS_BC_BVP))     */
+  int32_t refine_steps;  /* MIXED: residual passes after the first solve (0..8,
+                            every instance).  Default when negative: 1 (2 if
+                            any instance has boundary values, NYS_BC_BVP), then
+                            one adaptive pass for the instances whose estimated
+                            error (rho * d, see NYS_EPRECISION) is above 1e-8;
+                            the others skip it                                 */
   double eig_tau;        /* drop eigenpairs with lambda <= tau * lambda_max
                             (default 1e-12 when <= 0)                            */
   int32_t scale_sqrt_m;  /* 1: eq32's sqrt(m) feature scale (== gamma * m)      */

@@ -44,7 +44,7 @@ cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W,
                           double* xs, double* zs, const double* cws, int XS, int ZS, int M1S,
                           int32_t* st, double gamma_scale, int batch, int m_max, int k_max,
                           int num_sms, cudaStream_t s, int nrband, bool fac64, double* rcorr,
-                          int pass, bool last);
+                          int pass, bool last, const int32_t* skip_in, int32_t* skip_out);
 cudaError_t launch_eval(const Inst* insts, const double* zs, int ZS, const int32_t* lm,
                         const double* tq, const int64_t* tq_off, int deriv, double* yq, int batch,
                         cudaStream_t s);
@@ -210,6 +210,8 @@ struct nys_ctx {
   }
   DBuf<double> xs, zs, dzs, cws;
   DBuf<double> rcorr;       // MIXED: each instance's last relative refinement correction
+  DBuf<int32_t> rskip;      // MIXED, default refinement: 1 = the instance skips the adaptive pass
+  int refine_adapt = 0;     // default refinement: one adaptive pass after opt.refine_steps
   DBuf<int32_t> st, stinit, counter, err;
   // Newton state
   DBuf<double> yaux, rowstate, nrm;
@@ -755,14 +757,17 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
     delete c;
     return fail(NYS_EINVAL, "nys_setup: unknown assembly kernel %d", a);
   }
-  // default refinement: one pass (every initial value workload lands at <= 2e-7
-  // of the FP64 solution); two when the batch holds boundary value instances,
-  // whose FP32 factor contracts the error more slowly (one pass leaves up to
-  // ~3e-6 on the boundary value family, two <= 2e-7)
+  // default refinement: one pass for every instance (two when the batch holds
+  // boundary value instances, whose FP32 factor contracts the error more
+  // slowly), then an adaptive pass for the instances whose estimated error is
+  // still above kRefineAgain: a landmark kernel near the conditioning limit
+  // (sigma about one landmark spacing at m = 64..100, n up to 2e4) can leave a
+  // few 1e-6 after one pass
   if (c->opt.refine_steps < 0) {
     bool any_bvp = false;
     for (int b = 0; b < batch; ++b) any_bvp = any_bvp || (q[b].bc == NYS_BC_BVP);
     c->opt.refine_steps = any_bvp ? 2 : 1;
+    c->refine_adapt = 1;
   }
   if (c->opt.refine_steps > 8) { delete c; return fail(NYS_EINVAL, "nys_setup: refine_steps > 8"); }
   c->fp32 = (c->opt.precision == NYS_MIXED || c->opt.precision == NYS_MIXED_F64F);
@@ -943,6 +948,7 @@ int32_t nys_setup(nys_ctx** out, const nys_instance* q, int32_t batch, const nys
   A(c->dzs.alloc((size_t)batch * c->ZS));
   A(c->cws.alloc((size_t)batch * 2 * c->M1S));
   if (c->fp32) A(c->rcorr.alloc(batch));
+  if (c->fp32) A(c->rskip.alloc(batch));
   if (c->any_lin && !c->fp32) A(c->adj.alloc((size_t)batch * grad_adj_stride(c->ZS)));
   A(c->st.alloc(batch));
   A(c->stinit.alloc(batch));
@@ -1155,12 +1161,18 @@ static int32_t solve_impl(nys_ctx* c, cudaStream_t s, double* x_out, int32_t* st
                   c->stinit.p, c->st.p, gscale, c->batch, c->m_max, s,
                   c->fp32 ? c->err.p : nullptr, c->bigset(), c->crow.p, c->fac64));
   if (c->fp32) {
-    for (int k = 0; k < c->opt.refine_steps; ++k)
+    // the base passes, then (default refinement) the adaptive pass, which the
+    // instances marked by the pass before it skip
+    const int passes = c->opt.refine_steps + c->refine_adapt;
+    for (int k = 0; k < passes; ++k) {
+      const bool adaptive = c->refine_adapt && k == passes - 1;
+      const bool decides = c->refine_adapt && k == passes - 2;
       CK(launch_refine(c->inst.p, c->lset.p, c->W.p, c->lag.p, c->rwork.p, c->nrwork, c->counter.p,
                        c->lm.p, c->tab.p, c->part.p, c->slot_off.p, c->fac.p, c->facs, c->xs.p, c->zs.p,
                        c->cws.p, c->XS, c->ZS, c->M1S, c->st.p, gscale, c->batch, c->m_max,
-                       c->k_max, c->num_sms, s, c->nrband, c->fac64, c->rcorr.p, k,
-                       k == c->opt.refine_steps - 1));
+                       c->k_max, c->num_sms, s, c->nrband, c->fac64, c->rcorr.p, k, k == passes - 1,
+                       adaptive ? c->rskip.p : nullptr, decides ? c->rskip.p : nullptr));
+    }
   }
   if (x_out)
     CK(cudaMemcpyAsync(x_out, c->xs.p, sizeof(double) * c->batch * c->XS, cudaMemcpyDeviceToDevice, s));

@@ -23,6 +23,10 @@ constexpr int kErrBounds = 3;
 // Largest estimated error, relative to the solution (omega, b), that the mixed
 // path's last refinement pass may leave
 constexpr double kRefineTrust = 1e-4;
+// Default refinement: an instance whose estimated error after the base passes is
+// above kRefineAgain (relative to (omega, b)) takes one more pass; the others
+// skip it
+constexpr double kRefineAgain = 1e-8;
 constexpr int kMeffBounds = -2;
 
 

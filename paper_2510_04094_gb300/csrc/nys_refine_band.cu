@@ -135,7 +135,8 @@ k_refine_band(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
               const float* __restrict__ lag, const Work* __restrict__ work, int nwork,
               int* __restrict__ counter, const int32_t* __restrict__ lm_idx,
               const double* __restrict__ zs, int ZS, double* __restrict__ part,
-              const int64_t* __restrict__ slot_off, int32_t* __restrict__ st_all) {
+              const int64_t* __restrict__ slot_off, int32_t* __restrict__ st_all,
+              const int32_t* __restrict__ skip_in) {
   extern __shared__ __align__(16) unsigned char rb_raw[];
   float2* tab = reinterpret_cast<float2*>(rb_raw);                // [kRbTabCap]
   float2* zsh = tab + kRbTabCap;                                  // [kM1Max] z~ (float-float)
@@ -156,7 +157,8 @@ k_refine_band(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     const int m = I.m, K = min(refine_band_lag(I.hs, I.n), L.K), W = wk.e0, R = W >> 5;
     const int r0 = wk.r0, r1 = wk.r1;
     const int Kt = K + W - 1, ntab = 2 * Kt + 1;
-    const bool skip = (st_all[wk.inst] != NYS_OK);
+    // instances that failed, or that an adaptive pass leaves out (skip_in)
+    const bool skip = (st_all[wk.inst] != NYS_OK) || (skip_in && skip_in[wk.inst]);
     const bool fits = ntab + W <= kRbTabCap && W >= 32 && W <= kRbMaxW && (W & (W - 1)) == 0 &&
                       m <= kMMax;
     if (!skip && fits) {
@@ -278,7 +280,7 @@ k_refine_band(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
 cudaError_t launch_refine_band(const Inst* insts, const Lset* lsets, const float* lag,
                                const Work* work, int nwork, int* counter, const int32_t* lm,
                                const double* zs, int ZS, double* part, const int64_t* slot_off,
-                               int32_t* st, int num_sms, cudaStream_t s) {
+                               int32_t* st, const int32_t* skip_in, int num_sms, cudaStream_t s) {
   if (nwork <= 0) return cudaSuccess;
   const size_t sm = refine_band_smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(k_refine_band, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -286,7 +288,7 @@ cudaError_t launch_refine_band(const Inst* insts, const Lset* lsets, const float
   if (e != cudaSuccess) return e;
   const int grid = min(nwork, 2 * num_sms);
   k_refine_band<<<grid, kRbThreads, sm, s>>>(insts, lsets, lag, work, nwork, counter, lm, zs, ZS,
-                                             part, slot_off, st);
+                                             part, slot_off, st, skip_in);
   return cudaGetLastError();
 }
 

@@ -533,7 +533,7 @@ k_refine_rows(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
               int* __restrict__ counter, const int32_t* __restrict__ lm_idx,
               const double* __restrict__ tab, const double* __restrict__ zs, int ZS,
               double* __restrict__ part, const int64_t* __restrict__ slot_off,
-              const int32_t* __restrict__ st_all, int k_cap) {
+              const int32_t* __restrict__ st_all, const int32_t* __restrict__ skip_in, int k_cap) {
   // k_cap: capacity of the shared-memory kappa table (fixed at launch, so a
   // graph captured earlier stays safe when an update lengthens the tables)
   extern __shared__ __align__(16) float2 smr[];
@@ -561,7 +561,8 @@ k_refine_rows(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
       const ff z = ff_from_double(zs[(int64_t)wk.inst * ZS + j]);
       s_zj[j] = make_float4(z.hi, z.lo, __int_as_float(j < m ? lm_idx[I.lm_off + j] : 0), 0.f);
     }
-    const bool skip = (st_all[wk.inst] != NYS_OK);
+    // instances that failed, or that an adaptive pass leaves out (skip_in)
+    const bool skip = (st_all[wk.inst] != NYS_OK) || (skip_in && skip_in[wk.inst]);
     const RowConst RK = I.rk;
     if (folded && !skip) {  // constant operator: kappa(k) for k = -K..K
       // (zero beyond lag K, so the padding holds zeros)
@@ -705,9 +706,10 @@ k_refine_update(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
                 const int64_t* __restrict__ slot_off, const T* __restrict__ fac_all, int64_t facs,
                 double* __restrict__ xs, double* __restrict__ zs, const double* __restrict__ cws,
                 int XS, int ZS, int M1S, int32_t* __restrict__ st_all, double gamma_scale,
-                double* __restrict__ rcorr, int pass, int last) {
+                double* __restrict__ rcorr, int pass, int last,
+                const int32_t* __restrict__ skip_in, int32_t* __restrict__ skip_out) {
   const int b = blockIdx.x;
-  if (st_all[b] != NYS_OK) return;
+  if (st_all[b] != NYS_OK || (skip_in && skip_in[b])) return;
   const Inst& I = insts[b];   // a reference: I.v[tid] would copy the struct to local memory
   const Lset LS = lsets[I.lset];
   const int m = I.m, p = I.p, me = LS.m_eff, M1 = me + 1;
@@ -824,6 +826,8 @@ k_refine_update(const Inst* __restrict__ insts, const Lset* __restrict__ lsets,
     const double rho = pass == 0 ? d : (prev_d > 0.0 ? d / prev_d : (d > 0.0 ? 1.0 : 0.0));
     rcorr[b] = d;
     if (last && !(rho * d <= kRefineTrust)) st_all[b] = NYS_EPRECISION;
+    // the adaptive pass that follows: only instances still above kRefineAgain
+    if (skip_out) skip_out[b] = (rho * d <= kRefineAgain) ? 1 : 0;
   }
   double* zb = zs + (int64_t)b * ZS;
   for (int j = threadIdx.x; j <= m; j += blockDim.x) {
@@ -1223,7 +1227,7 @@ cudaError_t launch_solve(bool fp32, const Inst* insts, const Lset* lsets, const 
 cudaError_t launch_refine_band(const Inst* insts, const Lset* lsets, const float* lag,
                                const Work* work, int nwork, int* counter, const int32_t* lm,
                                const double* zs, int ZS, double* part, const int64_t* slot_off,
-                               int32_t* st, int num_sms, cudaStream_t s);
+                               int32_t* st, const int32_t* skip_in, int num_sms, cudaStream_t s);
 
 cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W, const float* lag,
                           const Work* work, int nwork, int* counter, const int32_t* lm,
@@ -1231,13 +1235,14 @@ cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W,
                           const void* fac, int64_t facs, double* xs, double* zs, const double* cws,
                           int XS, int ZS, int M1S, int32_t* st, double gamma_scale, int batch,
                           int m_max, int k_max, int num_sms, cudaStream_t s, int nrband,
-                          bool fac64, double* rcorr, int pass, bool last) {
+                          bool fac64, double* rcorr, int pass, bool last, const int32_t* skip_in,
+                          int32_t* skip_out) {
   // the first nrband items: k_refine_band (queue counter[1]); the rest k_refine_rows
   cudaError_t e = cudaMemsetAsync(counter, 0, (nrband > 0 ? 2 : 1) * sizeof(int), s);
   if (e != cudaSuccess) return e;
   if (nrband > 0) {
     e = launch_refine_band(insts, lsets, lag, work, nrband, counter + 1, lm, zs, ZS, part, slot_off,
-                           st, num_sms, s);
+                           st, skip_in, num_sms, s);
     if (e != cudaSuccess) return e;
     work += nrband;
     nwork -= nrband;
@@ -1252,7 +1257,7 @@ cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W,
   const int grid = min(nwork, num_sms * max(1, per_sm));
   if (grid > 0) {
     k_refine_rows<<<grid, kRefThreads, sm, s>>>(insts, lsets, lag, work, nwork, counter, lm, tab, zs,
-                                                 ZS, part, slot_off, st, k_cap);
+                                                 ZS, part, slot_off, st, skip_in, k_cap);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -1267,7 +1272,8 @@ cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W,
     k_refine_update<double><<<batch, kSolveThreads, lsm, s>>>(insts, lsets, W, part, slot_off,
                                                                (const double*)fac, facs, xs, zs,
                                                                cws, XS, ZS, M1S, st, gamma_scale,
-                                                               rcorr, pass, last ? 1 : 0);
+                                                               rcorr, pass, last ? 1 : 0, skip_in,
+                                                              skip_out);
   } else {
     e = cudaFuncSetAttribute(k_refine_update<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)lsm);
@@ -1275,7 +1281,8 @@ cudaError_t launch_refine(const Inst* insts, const Lset* lsets, const double* W,
     k_refine_update<float><<<batch, kSolveThreads, lsm, s>>>(insts, lsets, W, part, slot_off,
                                                               (const float*)fac, facs, xs, zs, cws,
                                                               XS, ZS, M1S, st, gamma_scale,
-                                                              rcorr, pass, last ? 1 : 0);
+                                                              rcorr, pass, last ? 1 : 0, skip_in,
+                                                              skip_out);
   }
   return cudaGetLastError();
 }

@@ -180,6 +180,33 @@ def test_mixed_large_m_fp64_fallback(api):
     _check(api, probs, "fp64")
 
 
+def test_ragged_full_batch_adaptive_refinement(api):
+    """The ragged family at full size (4096 instances, n log-uniform up to 2e4), in
+    the launch configuration of the benchmark's ragged step, with the default
+    refinement.  Instances near the conditioning limit (sigma about one landmark
+    spacing at m = 64 and 100) were left at 1.5e-6 .. 7.2e-6 of the oracle by a
+    single pass (measured, status OK); the adaptive pass (instances whose
+    estimated error is above 1e-8) brings them, and the sampled others, within
+    the mixed bar."""
+    import torch
+    probs = ni.cfg3()
+    bt = api.Batch(probs, precision="mixed")
+    x, st = bt.run()
+    torch.cuda.synchronize()
+    assert (st.cpu().numpy() == 0).all()
+    picks = [3370, 3371, 1725, 461, 2109, 2394, 0, 1, 2, 4095]
+    tq = [core.grid(probs[k]) if k in picks else np.empty(0) for k in range(max(picks) + 1)]
+    y, off = bt.eval(tq)
+    torch.cuda.synchronize()
+    yc, off = y.cpu().numpy(), off.cpu().numpy()
+    for k in picks:
+        ref = core.solve_linear(probs[k])["y"]
+        got = yc[off[k]:off[k + 1]]
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        assert err <= TOL["mixed"], (k, err)
+    bt.close()
+
+
 def test_mixed_refinement_to_the_rounding_floor(api):
     """Eight refinement passes bring the corrections of well-conditioned instances
     down to FP64 rounding, where the ratio of the last two is about 1: the
