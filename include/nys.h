@@ -195,7 +195,8 @@ int32_t nys_assemble(nys_ctx* c, void* stream);
    null-space elimination of the initial-condition rows, Cholesky.  Landmark
    sets whose kept eigenvalues span more than 1e7 are assembled in omega
    coordinates instead (each row projected through W; FP64 only).  MIXED adds
-   refine_steps residual passes.  x_out: device, batch x nys_x_stride(c)
+   refine_steps residual passes (the default: its base passes and the adaptive
+   pass, see nys_options.refine_steps).  x_out: device, batch x nys_x_stride(c)
    doubles, per instance [omega (m_eff, zero padded to m_max), b, lambda_1,
    lambda_2] (orders 3 and 4 report the first two of their p multipliers).
    status_out: device, batch int32 (NYS_OK / NYS_ENOTSPD /
