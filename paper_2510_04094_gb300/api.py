@@ -73,7 +73,10 @@ class Batch:
     def __init__(self, problems, precision="fp64", refine_steps=-1, eig_tau=0.0,
                  scale_sqrt_m=False, stream=None, assembly="auto"):
         """precision: "fp64", "mixed" or "mixed-f64f" (nys_precision); assembly (mixed
-        precisions): "auto", "tc", "simt" or "tune" (nys_assembly)."""
+        precisions): "auto", "tc", "simt" or "tune" (nys_assembly).  refine_steps
+        (mixed): residual passes for every instance; negative selects the default,
+        one pass (two with boundary values) and then an adaptive pass for the
+        instances whose estimated error is still above 1e-8."""
         self.problems = list(problems)
         self.B = len(self.problems)
         self.stream = stream
