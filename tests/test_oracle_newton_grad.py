@@ -207,3 +207,33 @@ def test_jacobian_is_derivative_of_F_with_nonlinear_derivative_term():
     a = newton.step_dense(pc, x, False)
     b = newton.step_reduced(pc, x, False)
     assert np.abs(a - b).max() <= 1e-8 * max(1.0, np.abs(a).max())
+
+
+def test_duffing_matches_an_independent_integrator():
+    """The Duffing equation y'' = 0.7 y - 1.2 y^3 - 0.25 y' + 0.6 cos(1.1 t) on [0, 6],
+    y(0) = 0.4, y'(0) = -0.3, has no closed form.  The oracle's Newton fit (Lemma 2)
+    is compared with an explicit Runge-Kutta integration of order 8 (scipy's DOP853,
+    tolerances 1e-13), an independent method.  Measured: 1.0e-6 relative at n = 2000,
+    m = 50, sigma = 1 and 5.2e-7 at n = 4000, m = 100.  That is the method's
+    discretisation error, shrinking with resolution.  A wrong sign of the damping, the
+    linear, the cubic or the forcing term, or of y'(0), moves the error to 0.8 or more
+    (or the integration blows up)."""
+    integrate = pytest.importorskip("scipy.integrate")
+
+    def rhs(t, s):
+        y, u = s
+        return [u, 0.7 * y - 1.2 * y ** 3 - 0.25 * u + 0.6 * math.cos(1.1 * t)]
+
+    errs = []
+    for n, m in ((2000, 50), (4000, 100)):
+        prob = dict(p=2, n=n, m=m, t0=0.0, t1=6.0, sigma=1.0, gamma=1e10, v=[0.4, -0.3],
+                    kind="nl", P=[0.0, 0.7, 0.0, -1.2], delta=0.25, g=0.6, omega=1.1)
+        sol = newton.solve(prob)
+        assert sol["converged"]
+        t = core.grid(prob)
+        ref = integrate.solve_ivp(rhs, [0.0, 6.0], [0.4, -0.3], method="DOP853", rtol=1e-13,
+                                  atol=1e-13, t_eval=t)
+        assert ref.success and ref.y.shape[1] == len(t)
+        errs.append(np.abs(sol["y"] - ref.y[0]).max() / np.abs(ref.y[0]).max())
+    assert errs[0] <= 5e-6, errs
+    assert errs[1] <= 2e-6 and errs[1] < errs[0], errs
