@@ -116,7 +116,7 @@ def _sampled(api, probs, bt, pick, tol):
 def test_metric_batch_full_size_sampled(api, precision):
     """The throughput workload itself, 4096 instances at n = 1e4, m = 50, in the
     launch configuration bench.py times (one nys_run graph; mixed: the default
-    single refinement pass), so that every warp of the band kernel takes many
+    refinement, one pass and the adaptive pass), so that every warp of the band kernel takes many
     units (mixed), or the tensor-core kernel cycles through its accumulator sets
     (mixed-tc); instances sampled across the cost-sorted work list against the
     oracle."""
@@ -233,7 +233,7 @@ def test_ragged_batch_all_m_values(api, precision):
 @pytest.mark.parametrize("precision", ["mixed", "mixed-tc", "mixed-simt"])
 def test_ragged_family_default_refinement(api, precision):
     """The ragged batched family (n log-uniform in [500, 2e4], m in {20..100},
-    sigma = T/m) meets the mixed-path bar with the default single refinement pass."""
+    sigma = T/m) meets the mixed-path bar with the default refinement."""
     _check(api, ni.cfg3(8), precision)
 
 
